@@ -1,0 +1,774 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the black-box FMM (Laplace 1/r,
+ * potentials and forces) of Agullo et al., "Pipelining the Fast Multipole
+ * Method over a Runtime System" (2012).
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, the smoke check and the benchmark's CPU
+ * baseline).  It is written to be read against the paper, not to be fast:
+ * every operator is the formula of Sec. 2 evaluated with plain loops in
+ * double precision.  Compile with -ffp-contract=off so that the Morton
+ * quantisation is the IEEE operation sequence stated below.
+ *
+ * Paper references:
+ *   eq. 1  pairwise summation f_i = sum_j P(x_i, y_j) w_j          (Sec. 2)
+ *   eq. 2  P = 1/|x-y|, F = (x-y)/|x-y|^3                          (Sec. 2.1)
+ *   eq. 3  P ~ sum_m S_m(x) sum_n P(xbar_m, ybar_n) S_n(y); F moves the
+ *          gradient onto S_m(x)                                     (Sec. 2.1)
+ *   eq. 4  S_m(x) = S_m1(x1) S_m2(x2) S_m3(x3)                      (Sec. 2.1.1)
+ *   eq. 5  S(xbar, x) = 1/l + 2/l sum_{n=1}^{l-1} T_n(xbar) T_n(x),
+ *          xbar the Chebyshev roots                                 (Sec. 2.1.1)
+ *   Sec. 2.1.2  M2L over the children of the parent's neighbours that are not
+ *          neighbours themselves (at most 189), 316 distinct transfer
+ *          vectors, computed once thanks to the homogeneity of 1/r.
+ *   Sec. 3.2  bottom-up P2M, M2M; top-down M2L, L2L, L2P; P2P at the leaves.
+ *   Sec. 4.2  cells in Morton order.
+ *
+ * Pins: each function is checked against closed forms, invariants or brute
+ * force in tests/test_oracle.py (no function is left unpinned).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXH 12
+#define MAXP 12
+
+struct ofmm {
+  int height, order, leaf, ncoef;
+  int64_t n;
+  double lo[3], width;
+  int64_t* perm;   /* Morton rank -> input index */
+  double* x;       /* [n][3], Morton order */
+  double* q;       /* [n], Morton order */
+  int64_t ncell[MAXH];
+  uint64_t* key[MAXH];   /* sorted non-empty cell keys per level */
+  int64_t* first[MAXH];  /* leaf level: first particle; else first child */
+  int64_t* count[MAXH];  /* leaf level: particle count; else child count */
+  int64_t* parent[MAXH]; /* index of the parent cell (level - 1) */
+  double* M[MAXH];       /* multipole expansions [ncell][ncoef] */
+  double* L[MAXH];       /* local expansions [ncell][ncoef] */
+  double xbar[MAXP];     /* Chebyshev roots */
+  double* K;             /* M2L operators for unit half-width, see m2l_operators() */
+};
+
+/* ------------------------------------------------------------------------ */
+/* Chebyshev interpolation, eq. 5                                            */
+/* ------------------------------------------------------------------------ */
+
+void ofmm_cheb_nodes(int order, double* xbar) {
+  /* Roots of T_order: cos((2k+1) pi / (2 order)).  The upper half is taken
+   * as the exact negation of the lower half and the middle root of an odd
+   * order is exactly 0, so the node set is symmetric bit for bit. */
+  for (int k = 0; k < order; ++k) xbar[k] = 0.0;
+  for (int k = 0; 2 * k + 1 < order; ++k) {
+    xbar[k] = cos((2.0 * k + 1.0) * M_PI / (2.0 * order));
+    xbar[order - 1 - k] = -xbar[k];
+  }
+}
+
+/* T_0..T_{p-1} at x by the three-term recurrence. */
+static void cheb_T(int p, double x, double* T) {
+  T[0] = 1.0;
+  if (p > 1) T[1] = x;
+  for (int n = 2; n < p; ++n) T[n] = 2.0 * x * T[n - 1] - T[n - 2];
+}
+
+/* dT_n/dx = n U_{n-1}(x) for n = 0..p-1. */
+static void cheb_dT(int p, double x, double* dT) {
+  double U[MAXP];
+  U[0] = 1.0;
+  if (p > 1) U[1] = 2.0 * x;
+  for (int k = 2; k < p; ++k) U[k] = 2.0 * x * U[k - 1] - U[k - 2];
+  dT[0] = 0.0;
+  for (int n = 1; n < p; ++n) dT[n] = n * U[n - 1];
+}
+
+double ofmm_cheb_S(int p, double xbar, double xi) {
+  double Tb[MAXP], Tx[MAXP], s = 0.0;
+  cheb_T(p, xbar, Tb);
+  cheb_T(p, xi, Tx);
+  for (int n = 1; n < p; ++n) s += Tb[n] * Tx[n];
+  return 1.0 / p + 2.0 / p * s;
+}
+
+double ofmm_cheb_dS(int p, double xbar, double xi) {
+  double Tb[MAXP], dTx[MAXP], s = 0.0;
+  cheb_T(p, xbar, Tb);
+  cheb_dT(p, xi, dTx);
+  for (int n = 1; n < p; ++n) s += Tb[n] * dTx[n];
+  return 2.0 / p * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Root cube, Morton keys, sort (Sec. 3.2 subdivision; Sec. 4.2 Morton order) */
+/* ------------------------------------------------------------------------ */
+
+void ofmm_bounding_cube(int64_t n, const double* xyz, double* lo, double* width) {
+  double hi[3];
+  if (n <= 0) {
+    lo[0] = lo[1] = lo[2] = 0.0;
+    *width = 1.0;
+    return;
+  }
+  for (int d = 0; d < 3; ++d) lo[d] = hi[d] = xyz[d];
+  for (int64_t i = 1; i < n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      double v = xyz[3 * i + d];
+      if (v < lo[d]) lo[d] = v;
+      if (v > hi[d]) hi[d] = v;
+    }
+  double w = 0.0;
+  for (int d = 0; d < 3; ++d)
+    if (hi[d] - lo[d] > w) w = hi[d] - lo[d];
+  *width = (w > 0.0) ? w : 1.0;
+}
+
+/* Integer cell coordinate along one axis at the leaf level:
+ * floor(((x - lo) / W) * 2^leaf), clamped to [0, 2^leaf - 1].  The product by
+ * a power of two is exact, so the only roundings are the IEEE subtraction and
+ * division. */
+static int64_t leaf_coord(double x, double lo, double width, int leaf) {
+  double t = (x - lo) / width;
+  double u = ldexp(t, leaf);
+  int64_t i = (int64_t)floor(u);
+  int64_t top = ((int64_t)1 << leaf) - 1;
+  if (i < 0) i = 0;
+  if (i > top) i = top;
+  return i;
+}
+
+static uint64_t morton_encode(int64_t ix, int64_t iy, int64_t iz, int bits) {
+  uint64_t k = 0;
+  for (int b = 0; b < bits; ++b) {
+    k |= (uint64_t)((ix >> b) & 1) << (3 * b + 2);
+    k |= (uint64_t)((iy >> b) & 1) << (3 * b + 1);
+    k |= (uint64_t)((iz >> b) & 1) << (3 * b);
+  }
+  return k;
+}
+
+static void morton_decode(uint64_t k, int bits, int64_t* c) {
+  c[0] = c[1] = c[2] = 0;
+  for (int b = 0; b < bits; ++b) {
+    c[0] |= (int64_t)((k >> (3 * b + 2)) & 1) << b;
+    c[1] |= (int64_t)((k >> (3 * b + 1)) & 1) << b;
+    c[2] |= (int64_t)((k >> (3 * b)) & 1) << b;
+  }
+}
+
+void ofmm_keys(int64_t n, const double* xyz, const double* lo, double width, int leaf,
+               uint64_t* keys) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c[3];
+    for (int d = 0; d < 3; ++d) c[d] = leaf_coord(xyz[3 * i + d], lo[d], width, leaf);
+    keys[i] = morton_encode(c[0], c[1], c[2], leaf);
+  }
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} keyed;
+
+static int cmp_keyed(const void* a, const void* b) {
+  const keyed* x = (const keyed*)a;
+  const keyed* y = (const keyed*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+/* Index of `k` among the sorted keys of a level, or -1. */
+static int64_t find_cell(const ofmm* c, int level, uint64_t k) {
+  int64_t a = 0, b = c->ncell[level] - 1;
+  const uint64_t* keys = c->key[level];
+  while (a <= b) {
+    int64_t m = a + (b - a) / 2;
+    if (keys[m] == k) return m;
+    if (keys[m] < k) a = m + 1;
+    else b = m - 1;
+  }
+  return -1;
+}
+
+static void cell_coords(const ofmm* c, int level, int64_t cell, int64_t* ic) {
+  morton_decode(c->key[level][cell], level, ic);
+}
+
+/* Centre and half-width of a cell: the root cube halved `level` times. */
+static void cell_geometry(const ofmm* c, int level, int64_t cell, double* centre, double* a) {
+  int64_t ic[3];
+  cell_coords(c, level, cell, ic);
+  double w = ldexp(c->width, -level);
+  for (int d = 0; d < 3; ++d) centre[d] = c->lo[d] + ((double)ic[d] + 0.5) * w;
+  *a = 0.5 * w;
+}
+
+/* M2L operator for transfer vector t (in cell widths, |t|_inf in {2, 3}) and
+ * unit half-width: K_t[m][n] = 1 / |2t + xbar_n - xbar_m|.  With cell
+ * half-width a the operator is K_t / a (1/r is homogeneous of degree -1,
+ * Sec. 2.1.2), because the target node is c_T + a xbar_m, the source node is
+ * c_S + a xbar_n and c_S - c_T = 2 a t. */
+static int tslot(int tx, int ty, int tz) { return ((tx + 3) * 7 + (ty + 3)) * 7 + (tz + 3); }
+
+static void m2l_operators(ofmm* c) {
+  int p = c->order, C = c->ncoef;
+  c->K = (double*)calloc((size_t)343 * C * C, sizeof(double));
+#pragma omp parallel for schedule(dynamic)
+  for (int s = 0; s < 343; ++s) {
+    int t[3] = {s / 49 - 3, (s / 7) % 7 - 3, s % 7 - 3};
+    int far = abs(t[0]) >= 2 || abs(t[1]) >= 2 || abs(t[2]) >= 2;
+    if (!far) continue;
+    double* K = c->K + (size_t)s * C * C;
+    for (int m = 0; m < C; ++m) {
+      int mi[3] = {m / (p * p), (m / p) % p, m % p};
+      for (int nn = 0; nn < C; ++nn) {
+        int ni[3] = {nn / (p * p), (nn / p) % p, nn % p};
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          double r = 2.0 * t[d] + c->xbar[ni[d]] - c->xbar[mi[d]];
+          r2 += r * r;
+        }
+        K[(size_t)m * C + nn] = 1.0 / sqrt(r2);
+      }
+    }
+  }
+}
+
+ofmm* ofmm_create(int64_t n, const double* xyz, const double* q, int height, int order) {
+  if (height < 1 || height > MAXH || order < 2 || order > MAXP || n < 0) return NULL;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!isfinite(q[i])) return NULL;
+    for (int d = 0; d < 3; ++d)
+      if (!isfinite(xyz[3 * i + d])) return NULL;
+  }
+  ofmm* c = (ofmm*)calloc(1, sizeof(ofmm));
+  c->height = height;
+  c->order = order;
+  c->leaf = height - 1;
+  c->ncoef = order * order * order;
+  c->n = n;
+  ofmm_cheb_nodes(order, c->xbar);
+  ofmm_bounding_cube(n, xyz, c->lo, &c->width);
+
+  /* keys and the stable sort: ties keep input order */
+  uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+  ofmm_keys(n, xyz, c->lo, c->width, c->leaf, keys);
+  keyed* kv = (keyed*)malloc(sizeof(keyed) * (n ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    kv[i].key = keys[i];
+    kv[i].idx = i;
+  }
+  qsort(kv, (size_t)n, sizeof(keyed), cmp_keyed);
+  c->perm = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  c->x = (double*)malloc(sizeof(double) * 3 * (n ? n : 1));
+  c->q = (double*)malloc(sizeof(double) * (n ? n : 1));
+  for (int64_t r = 0; r < n; ++r) {
+    int64_t i = kv[r].idx;
+    c->perm[r] = i;
+    for (int d = 0; d < 3; ++d) c->x[3 * r + d] = xyz[3 * i + d];
+    c->q[r] = q[i];
+  }
+
+  /* leaf level: runs of equal keys */
+  int Lf = c->leaf;
+  int64_t nl = 0;
+  for (int64_t r = 0; r < n; ++r)
+    if (r == 0 || kv[r].key != kv[r - 1].key) ++nl;
+  c->ncell[Lf] = nl;
+  c->key[Lf] = (uint64_t*)malloc(sizeof(uint64_t) * (nl ? nl : 1));
+  c->first[Lf] = (int64_t*)malloc(sizeof(int64_t) * (nl ? nl : 1));
+  c->count[Lf] = (int64_t*)calloc(nl ? nl : 1, sizeof(int64_t));
+  int64_t li = -1;
+  for (int64_t r = 0; r < n; ++r) {
+    if (r == 0 || kv[r].key != kv[r - 1].key) {
+      ++li;
+      c->key[Lf][li] = kv[r].key;
+      c->first[Lf][li] = r;
+    }
+    c->count[Lf][li]++;
+  }
+  /* coarser levels: parent key = child key >> 3 */
+  for (int l = Lf - 1; l >= 0; --l) {
+    int64_t nc = c->ncell[l + 1], np = 0;
+    for (int64_t i = 0; i < nc; ++i)
+      if (i == 0 || (c->key[l + 1][i] >> 3) != (c->key[l + 1][i - 1] >> 3)) ++np;
+    c->ncell[l] = np;
+    c->key[l] = (uint64_t*)malloc(sizeof(uint64_t) * (np ? np : 1));
+    c->first[l] = (int64_t*)malloc(sizeof(int64_t) * (np ? np : 1));
+    c->count[l] = (int64_t*)calloc(np ? np : 1, sizeof(int64_t));
+    c->parent[l + 1] = (int64_t*)malloc(sizeof(int64_t) * (nc ? nc : 1));
+    int64_t pi = -1;
+    for (int64_t i = 0; i < nc; ++i) {
+      uint64_t pk = c->key[l + 1][i] >> 3;
+      if (i == 0 || pk != (c->key[l + 1][i - 1] >> 3)) {
+        ++pi;
+        c->key[l][pi] = pk;
+        c->first[l][pi] = i;
+      }
+      c->count[l][pi]++;
+      c->parent[l + 1][i] = pi;
+    }
+  }
+  c->parent[0] = (int64_t*)calloc(c->ncell[0] ? c->ncell[0] : 1, sizeof(int64_t));
+  for (int l = 0; l <= Lf; ++l) {
+    size_t sz = (size_t)(c->ncell[l] ? c->ncell[l] : 1) * c->ncoef;
+    c->M[l] = (double*)calloc(sz, sizeof(double));
+    c->L[l] = (double*)calloc(sz, sizeof(double));
+  }
+  free(keys);
+  free(kv);
+  if (Lf >= 2) m2l_operators(c);
+  return c;
+}
+
+void ofmm_destroy(ofmm* c) {
+  if (!c) return;
+  for (int l = 0; l <= c->leaf; ++l) {
+    free(c->key[l]);
+    free(c->first[l]);
+    free(c->count[l]);
+    free(c->parent[l]);
+    free(c->M[l]);
+    free(c->L[l]);
+  }
+  free(c->perm);
+  free(c->x);
+  free(c->q);
+  free(c->K);
+  free(c);
+}
+
+void ofmm_box(const ofmm* c, double* lo, double* width) {
+  for (int d = 0; d < 3; ++d) lo[d] = c->lo[d];
+  *width = c->width;
+}
+
+int64_t ofmm_level_size(const ofmm* c, int level) {
+  if (level < 0 || level > c->leaf) return -1;
+  return c->ncell[level];
+}
+
+void ofmm_level_keys(const ofmm* c, int level, uint64_t* keys) {
+  memcpy(keys, c->key[level], sizeof(uint64_t) * c->ncell[level]);
+}
+
+void ofmm_level_ranges(const ofmm* c, int level, int64_t* first, int64_t* count) {
+  memcpy(first, c->first[level], sizeof(int64_t) * c->ncell[level]);
+  memcpy(count, c->count[level], sizeof(int64_t) * c->ncell[level]);
+}
+
+void ofmm_perm(const ofmm* c, int64_t* perm) { memcpy(perm, c->perm, sizeof(int64_t) * c->n); }
+
+void ofmm_expansion(const ofmm* c, int level, int which, double* out) {
+  const double* src = which ? c->L[level] : c->M[level];
+  memcpy(out, src, sizeof(double) * c->ncell[level] * c->ncoef);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interaction lists (Sec. 2.1.2, Sec. 3.3)                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Near field of a leaf: the existing leaves whose coordinates differ from the
+ * target's by at most 1 on every axis (the target itself included). */
+static int near_list(const ofmm* c, int64_t cell, int64_t* src) {
+  int Lf = c->leaf, ns = 0;
+  int64_t ic[3], top = ((int64_t)1 << Lf) - 1;
+  cell_coords(c, Lf, cell, ic);
+  for (int dx = -1; dx <= 1; ++dx)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dz = -1; dz <= 1; ++dz) {
+        int64_t s[3] = {ic[0] + dx, ic[1] + dy, ic[2] + dz};
+        if (s[0] < 0 || s[1] < 0 || s[2] < 0 || s[0] > top || s[1] > top || s[2] > top) continue;
+        int64_t j = find_cell(c, Lf, morton_encode(s[0], s[1], s[2], Lf));
+        if (j >= 0) src[ns++] = j;
+      }
+  return ns;
+}
+
+/* Far field of a cell at `level`: the existing children of the parent's
+ * neighbours (the parent included) that are not neighbours of the cell.
+ * Returns the count; src[] the cells, t[] their transfer vectors
+ * (source minus target coordinates). */
+static int far_list(const ofmm* c, int level, int64_t cell, int64_t* src, int* t) {
+  int nf = 0;
+  if (level < 2) return 0;
+  int64_t ic[3], pc[3], ptop = ((int64_t)1 << (level - 1)) - 1;
+  cell_coords(c, level, cell, ic);
+  for (int d = 0; d < 3; ++d) pc[d] = ic[d] >> 1;
+  for (int dx = -1; dx <= 1; ++dx)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dz = -1; dz <= 1; ++dz) {
+        int64_t pn[3] = {pc[0] + dx, pc[1] + dy, pc[2] + dz};
+        if (pn[0] < 0 || pn[1] < 0 || pn[2] < 0 || pn[0] > ptop || pn[1] > ptop || pn[2] > ptop)
+          continue;
+        for (int ch = 0; ch < 8; ++ch) {
+          int64_t s[3] = {2 * pn[0] + ((ch >> 2) & 1), 2 * pn[1] + ((ch >> 1) & 1),
+                          2 * pn[2] + (ch & 1)};
+          int64_t tv[3] = {s[0] - ic[0], s[1] - ic[1], s[2] - ic[2]};
+          if (llabs(tv[0]) <= 1 && llabs(tv[1]) <= 1 && llabs(tv[2]) <= 1) continue;
+          int64_t j = find_cell(c, level, morton_encode(s[0], s[1], s[2], level));
+          if (j < 0) continue;
+          src[nf] = j;
+          t[3 * nf + 0] = (int)tv[0];
+          t[3 * nf + 1] = (int)tv[1];
+          t[3 * nf + 2] = (int)tv[2];
+          ++nf;
+        }
+      }
+  return nf;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Operators (Sec. 2.1, eq. 3-5)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* P2M: M_m = sum_j q_j S_m((y_j - c)/a), S_m the tensor product of eq. 4. */
+void ofmm_p2m(ofmm* c) {
+  int p = c->order, C = c->ncoef, Lf = c->leaf;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t cell = 0; cell < c->ncell[Lf]; ++cell) {
+    double ctr[3], a, S[3][MAXP];
+    cell_geometry(c, Lf, cell, ctr, &a);
+    double* M = c->M[Lf] + (size_t)cell * C;
+    for (int m = 0; m < C; ++m) M[m] = 0.0;
+    for (int64_t r = c->first[Lf][cell]; r < c->first[Lf][cell] + c->count[Lf][cell]; ++r) {
+      for (int d = 0; d < 3; ++d) {
+        double xi = (c->x[3 * r + d] - ctr[d]) / a;
+        for (int k = 0; k < p; ++k) S[d][k] = ofmm_cheb_S(p, c->xbar[k], xi);
+      }
+      for (int m = 0; m < C; ++m)
+        M[m] += c->q[r] * S[0][m / (p * p)] * S[1][(m / p) % p] * S[2][m % p];
+    }
+  }
+}
+
+/* 1-D interpolation weights between a child and its parent along axis d:
+ * A[m][m'] = S(xbar_m, (c_child + a_child xbar_m' - c_parent) / a_parent). */
+static void child_weights(const ofmm* c, const double* cc, double ac, const double* cp, double ap,
+                          double A[3][MAXP][MAXP]) {
+  int p = c->order;
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < p; ++m)
+      for (int mm = 0; mm < p; ++mm)
+        A[d][m][mm] = ofmm_cheb_S(p, c->xbar[m], (cc[d] + ac * c->xbar[mm] - cp[d]) / ap);
+}
+
+/* M2M: the parent's multipole expansion interpolates its children's at the
+ * parent's nodes: M_P[m] = sum_children sum_m' S_m(xi_P(child node m')) M_C[m']. */
+void ofmm_m2m(ofmm* c) {
+  int p = c->order, C = c->ncoef;
+  for (int l = c->leaf - 1; l >= 2; --l) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t P = 0; P < c->ncell[l]; ++P) {
+      double cp[3], ap, cc[3], ac, A[3][MAXP][MAXP];
+      cell_geometry(c, l, P, cp, &ap);
+      double* MP = c->M[l] + (size_t)P * C;
+      for (int m = 0; m < C; ++m) MP[m] = 0.0;
+      for (int64_t ch = c->first[l][P]; ch < c->first[l][P] + c->count[l][P]; ++ch) {
+        cell_geometry(c, l + 1, ch, cc, &ac);
+        child_weights(c, cc, ac, cp, ap, A);
+        const double* MC = c->M[l + 1] + (size_t)ch * C;
+        for (int m = 0; m < C; ++m) {
+          int mx = m / (p * p), my = (m / p) % p, mz = m % p;
+          double s = 0.0;
+          for (int mm = 0; mm < C; ++mm)
+            s += A[0][mx][mm / (p * p)] * A[1][my][(mm / p) % p] * A[2][mz][mm % p] * MC[mm];
+          MP[m] += s;
+        }
+      }
+    }
+  }
+}
+
+/* M2L at one cell: L_T[m] = sum_{S in far field} sum_n P(xbar^T_m, ybar^S_n) M_S[n],
+ * with P(xbar^T_m, ybar^S_n) = K_t[m][n] / a. */
+static void m2l_cell(ofmm* c, int l, int64_t T, int64_t* src, int* tv) {
+  int C = c->ncoef;
+  double a = ldexp(c->width, -l - 1);
+  double* LT = c->L[l] + (size_t)T * C;
+  for (int m = 0; m < C; ++m) LT[m] = 0.0;
+  int nf = far_list(c, l, T, src, tv);
+  for (int k = 0; k < nf; ++k) {
+    const double* K = c->K + (size_t)tslot(tv[3 * k], tv[3 * k + 1], tv[3 * k + 2]) * C * C;
+    const double* MS = c->M[l] + (size_t)src[k] * C;
+    for (int m = 0; m < C; ++m) {
+      double s = 0.0;
+      for (int nn = 0; nn < C; ++nn) s += K[(size_t)m * C + nn] * MS[nn];
+      LT[m] += s / a;
+    }
+  }
+}
+
+void ofmm_m2l(ofmm* c) {
+  for (int l = 2; l <= c->leaf; ++l) {
+#pragma omp parallel
+    {
+      int64_t src[216];
+      int tv[3 * 216];
+#pragma omp for schedule(dynamic, 4)
+      for (int64_t T = 0; T < c->ncell[l]; ++T) m2l_cell(c, l, T, src, tv);
+    }
+  }
+}
+
+/* L2L: the child's local expansion adds the parent's evaluated at the
+ * child's nodes: L_C[m'] += sum_m S_m(xi_P(child node m')) L_P[m]. */
+static void l2l_cell(ofmm* c, int l, int64_t ch) {
+  int p = c->order, C = c->ncoef;
+  double cp[3], ap, cc[3], ac, A[3][MAXP][MAXP];
+  int64_t P = c->parent[l + 1][ch];
+  cell_geometry(c, l, P, cp, &ap);
+  cell_geometry(c, l + 1, ch, cc, &ac);
+  child_weights(c, cc, ac, cp, ap, A);
+  const double* LP = c->L[l] + (size_t)P * C;
+  double* LC = c->L[l + 1] + (size_t)ch * C;
+  for (int mm = 0; mm < C; ++mm) {
+    int ax = mm / (p * p), ay = (mm / p) % p, az = mm % p;
+    double s = 0.0;
+    for (int m = 0; m < C; ++m)
+      s += A[0][m / (p * p)][ax] * A[1][(m / p) % p][ay] * A[2][m % p][az] * LP[m];
+    LC[mm] += s;
+  }
+}
+
+void ofmm_l2l(ofmm* c) {
+  for (int l = 2; l <= c->leaf - 1; ++l) {
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t ch = 0; ch < c->ncell[l + 1]; ++ch) l2l_cell(c, l, ch);
+  }
+}
+
+/* L2P for one particle of leaf `cell`: phi = sum_m S_m(xi) L_m and
+ * F = -grad phi = -(1/a) sum_m grad_xi S_m(xi) L_m (eq. 3, gradient on S). */
+static void l2p_particle(const ofmm* c, int64_t cell, int64_t r, double* phi, double* F) {
+  int p = c->order, C = c->ncoef, Lf = c->leaf;
+  double ctr[3], a, S[3][MAXP], dS[3][MAXP];
+  cell_geometry(c, Lf, cell, ctr, &a);
+  for (int d = 0; d < 3; ++d) {
+    double xi = (c->x[3 * r + d] - ctr[d]) / a;
+    for (int k = 0; k < p; ++k) {
+      S[d][k] = ofmm_cheb_S(p, c->xbar[k], xi);
+      dS[d][k] = ofmm_cheb_dS(p, c->xbar[k], xi);
+    }
+  }
+  const double* L = c->L[Lf] + (size_t)cell * C;
+  double f = 0.0, g[3] = {0.0, 0.0, 0.0};
+  for (int m = 0; m < C; ++m) {
+    int mx = m / (p * p), my = (m / p) % p, mz = m % p;
+    f += L[m] * S[0][mx] * S[1][my] * S[2][mz];
+    g[0] += L[m] * dS[0][mx] * S[1][my] * S[2][mz];
+    g[1] += L[m] * S[0][mx] * dS[1][my] * S[2][mz];
+    g[2] += L[m] * S[0][mx] * S[1][my] * dS[2][mz];
+  }
+  *phi = f;
+  for (int d = 0; d < 3; ++d) F[d] = -g[d] / a;
+}
+
+void ofmm_l2p(const ofmm* c, double* phi, double* F) {
+  int Lf = c->leaf;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t cell = 0; cell < c->ncell[Lf]; ++cell)
+    for (int64_t r = c->first[Lf][cell]; r < c->first[Lf][cell] + c->count[Lf][cell]; ++r)
+      l2p_particle(c, cell, r, &phi[r], &F[3 * r]);
+}
+
+/* P2P for one particle: eq. 1 with the kernels of eq. 2 over the particles of
+ * the near-field leaves, skipping the particle itself and r = 0. */
+static void p2p_particle(const ofmm* c, const int64_t* src, int ns, int64_t r, double* phi,
+                         double* F) {
+  int Lf = c->leaf;
+  double f = 0.0, g[3] = {0.0, 0.0, 0.0};
+  const double* xi = c->x + 3 * r;
+  for (int k = 0; k < ns; ++k)
+    for (int64_t j = c->first[Lf][src[k]]; j < c->first[Lf][src[k]] + c->count[Lf][src[k]]; ++j) {
+      if (j == r) continue;
+      double d[3] = {xi[0] - c->x[3 * j], xi[1] - c->x[3 * j + 1], xi[2] - c->x[3 * j + 2]};
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (r2 == 0.0) continue;
+      double rr = sqrt(r2);
+      f += c->q[j] / rr;
+      for (int e = 0; e < 3; ++e) g[e] += c->q[j] * d[e] / (rr * r2);
+    }
+  *phi = f;
+  for (int e = 0; e < 3; ++e) F[e] = g[e];
+}
+
+void ofmm_p2p(const ofmm* c, double* phi, double* F) {
+  int Lf = c->leaf;
+#pragma omp parallel
+  {
+    int64_t src[27];
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t cell = 0; cell < c->ncell[Lf]; ++cell) {
+      int ns = near_list(c, cell, src);
+      for (int64_t r = c->first[Lf][cell]; r < c->first[Lf][cell] + c->count[Lf][cell]; ++r)
+        p2p_particle(c, src, ns, r, &phi[r], &F[3 * r]);
+    }
+  }
+}
+
+void ofmm_evaluate(ofmm* c, double* phi, double* F) {
+  int64_t n = c->n;
+  double* pf = (double*)calloc(n ? n : 1, sizeof(double));
+  double* Ff = (double*)calloc(3 * (n ? n : 1), sizeof(double));
+  double* pn = (double*)calloc(n ? n : 1, sizeof(double));
+  double* Fn = (double*)calloc(3 * (n ? n : 1), sizeof(double));
+  if (c->leaf >= 2) {
+    ofmm_p2m(c);
+    ofmm_m2m(c);
+    ofmm_m2l(c);
+    ofmm_l2l(c);
+    ofmm_l2p(c, pf, Ff);
+  }
+  ofmm_p2p(c, pn, Fn);
+  for (int64_t r = 0; r < n; ++r) {
+    int64_t i = c->perm[r];
+    phi[i] = pf[r] + pn[r];
+    for (int d = 0; d < 3; ++d) F[3 * i + d] = Ff[3 * r + d] + Fn[3 * r + d];
+  }
+  free(pf);
+  free(Ff);
+  free(pn);
+  free(Fn);
+}
+
+/* Leaf cell holding Morton rank r (binary search over leaf first ranks). */
+static int64_t leaf_of_rank(const ofmm* c, int64_t r) {
+  int Lf = c->leaf;
+  int64_t a = 0, b = c->ncell[Lf] - 1;
+  while (a < b) {
+    int64_t m = a + (b - a + 1) / 2;
+    if (c->first[Lf][m] <= r) a = m;
+    else b = m - 1;
+  }
+  return a;
+}
+
+void ofmm_evaluate_sampled(ofmm* c, int64_t ns, const int64_t* idx, double* phi, double* F) {
+  int Lf = c->leaf;
+  int64_t n = c->n;
+  int64_t* rank = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
+  for (int64_t r = 0; r < n; ++r) rank[c->perm[r]] = r;
+  if (Lf >= 2) {
+    ofmm_p2m(c);
+    ofmm_m2m(c);
+    /* mark the ancestors of every sampled particle's leaf */
+    char* need[MAXH];
+    for (int l = 0; l <= Lf; ++l) need[l] = (char*)calloc(c->ncell[l] ? c->ncell[l] : 1, 1);
+    for (int64_t s = 0; s < ns; ++s) {
+      int64_t cell = leaf_of_rank(c, rank[idx[s]]);
+      for (int l = Lf; l >= 2; --l) {
+        need[l][cell] = 1;
+        cell = c->parent[l][cell];
+      }
+    }
+    for (int l = 2; l <= Lf; ++l) {
+#pragma omp parallel
+      {
+        int64_t src[216];
+        int tv[3 * 216];
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t T = 0; T < c->ncell[l]; ++T)
+          if (need[l][T]) m2l_cell(c, l, T, src, tv);
+      }
+      if (l > 2) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t T = 0; T < c->ncell[l]; ++T)
+          if (need[l][T]) l2l_cell(c, l - 1, T);
+      }
+    }
+    for (int l = 0; l <= Lf; ++l) free(need[l]);
+  }
+#pragma omp parallel
+  {
+    int64_t src[27];
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t s = 0; s < ns; ++s) {
+      int64_t r = rank[idx[s]];
+      int64_t cell = leaf_of_rank(c, r);
+      double pf = 0.0, Ff[3] = {0.0, 0.0, 0.0}, pn, Fn[3];
+      if (Lf >= 2) l2p_particle(c, cell, r, &pf, Ff);
+      int nsrc = near_list(c, cell, src);
+      p2p_particle(c, src, nsrc, r, &pn, Fn);
+      phi[s] = pf + pn;
+      for (int d = 0; d < 3; ++d) F[3 * s + d] = Ff[d] + Fn[d];
+    }
+  }
+  free(rank);
+}
+
+int64_t ofmm_m2l_pair_count(const ofmm* c, int level) {
+  int64_t total = 0;
+  if (level < 2 || level > c->leaf) return 0;
+#pragma omp parallel reduction(+ : total)
+  {
+    int64_t src[216];
+    int tv[3 * 216];
+#pragma omp for schedule(static)
+    for (int64_t T = 0; T < c->ncell[level]; ++T) total += far_list(c, level, T, src, tv);
+  }
+  return total;
+}
+
+void ofmm_coverage(const ofmm* c, int32_t* counts) {
+  int Lf = c->leaf;
+  int64_t nl = c->ncell[Lf];
+  memset(counts, 0, sizeof(int32_t) * nl * nl);
+  int64_t* anc = (int64_t*)malloc(sizeof(int64_t) * (nl ? nl : 1) * (Lf + 1));
+  for (int64_t i = 0; i < nl; ++i) {
+    int64_t cell = i;
+    for (int l = Lf; l >= 0; --l) {
+      anc[i * (Lf + 1) + l] = cell;
+      if (l > 0) cell = c->parent[l][cell];
+    }
+  }
+  int64_t src[216];
+  int tv[3 * 216];
+  for (int64_t T = 0; T < nl; ++T) {
+    int ns = near_list(c, T, src);
+    for (int k = 0; k < ns; ++k) counts[T * nl + src[k]]++;
+    for (int l = 2; l <= Lf; ++l) {
+      int nf = far_list(c, l, anc[T * (Lf + 1) + l], src, tv);
+      for (int k = 0; k < nf; ++k)
+        for (int64_t S = 0; S < nl; ++S)
+          if (anc[S * (Lf + 1) + l] == src[k]) counts[T * nl + S]++;
+    }
+  }
+  free(anc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct summation, eq. 1 with eq. 2                                        */
+/* ------------------------------------------------------------------------ */
+
+static void direct_one(int64_t n, const double* xyz, const double* q, int64_t i, double* phi,
+                       double* F) {
+  double f = 0.0, g[3] = {0.0, 0.0, 0.0};
+  for (int64_t j = 0; j < n; ++j) {
+    if (j == i) continue;
+    double d[3] = {xyz[3 * i] - xyz[3 * j], xyz[3 * i + 1] - xyz[3 * j + 1],
+                   xyz[3 * i + 2] - xyz[3 * j + 2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 == 0.0) continue;
+    double r = sqrt(r2);
+    f += q[j] / r;
+    for (int e = 0; e < 3; ++e) g[e] += q[j] * d[e] / (r * r2);
+  }
+  *phi = f;
+  for (int e = 0; e < 3; ++e) F[e] = g[e];
+}
+
+void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) direct_one(n, xyz, q, i, &phi[i], &F[3 * i]);
+}
+
+void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
+                         const int64_t* idx, double* phi, double* F) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, idx[s], &phi[s], &F[3 * s]);
+}
