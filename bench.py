@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the black-box FMM on B300: particles per second for one full
+pass (tree build + evaluation of potentials and forces) over 1e6 points
+uniform in the unit cube, height 6, order 7, mixed precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  A step is fmm_set_particles + fmm_evaluate
+on device-resident inputs (all hot-path stages: box, Morton keys, sort, tree,
+P2M, M2M, M2L, L2L, L2P, P2P, output).  Each step is bracketed by CUDA events
+on the library's stream; between steps a 512 MB buffer is rewritten to flush
+the 126 MB L2 (outside the events).  `e2e` repeats the step through the same
+C calls with pinned host buffers, host<->device copies inside the timed
+region.  With N > 1 (torchrun) every rank solves its own independent problem
+(replicas: the FMM itself is not sharded), and value = all particles / the
+slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on
+a density-matched bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cube_n1m_h6_p7"
+METRIC = "FMM particles/s at rel.err<=1e-5 vs FP64 direct; P2P/M2L % roofline; p50/p99 ms"
+UNIT = "particles/s"
+# the CPU oracle is timed once on the full workload (about 30 s on 16 cores);
+# the reference arm's steps use a density-matched sample (same particles per
+# leaf: N / 8^k with height - k) so that K steps stay within minutes
+CPU_BASELINE_SAMPLE = dict(n=1_000_000, height=6, order=7, dist="cube", qkind="sym", seed=2)
+REFERENCE_STEP_SAMPLE = dict(n=15_625, height=4, order=7, dist="cube", qkind="sym", seed=2)
+
+FP32_LANES_PER_SM = 128
+NUM_SMS = 148
+TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d.get("bf16_tflops_sustained"),
+                    sm_max_mhz=d.get("sm_max_mhz", 2032.0), src="measured")
+    return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, sm_max_mhz=2032.0, src="fallback")
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(sample: dict, reps: int = 1):
+    """The FP64 oracle's FMM on a bounded, density-matched sample."""
+    import oracle
+    from paper_1206_0115_b300 import inputs
+    xyz, q = inputs.particles(sample["n"], sample["seed"], sample["dist"], sample["qkind"])
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        with oracle.OracleFMM(xyz, q, sample["height"], sample["order"]) as o:
+            o.evaluate()
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": sample["n"] / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"N={sample['n']} uniform cube, h={sample['height']}, p={sample['order']} "
+                       f"(the timed workload itself), FP64 oracle FMM incl. tree build, {reps} run(s), "
+                       f"{t:.2f} s")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    s = REFERENCE_STEP_SAMPLE
+    import oracle
+    from paper_1206_0115_b300 import inputs
+    xyz, q = inputs.particles(s["n"], s["seed"], s["dist"], s["qkind"])
+
+    def step():
+        with oracle.OracleFMM(xyz, q, s["height"], s["order"]) as o:
+            o.evaluate()
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = s["n"] * args.steps / tot
+    sample = (f"each step: N={s['n']} uniform cube, h={s['height']}, p={s['order']} (same particles per "
+              f"leaf as {args.workload}), FP64 oracle FMM incl. tree build")
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1206_0115_b300 import build, inputs
+    build.build()
+    from paper_1206_0115_b300 import fmm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = dict(inputs.WORKLOADS[args.workload])
+    xyz_np, q_np = inputs.particles(w["n"], w["seed"] + 1000 * rank, w["dist"], w["qkind"])
+    n, h, p = w["n"], w["height"], w["order"]
+    prec = fmm.FMM_MIXED if args.precision == "mixed" else fmm.FMM_FP64
+    stream = torch.cuda.Stream(device=dev)
+    f = fmm.FMM(h, p, prec, stream=stream)
+    xyz = torch.from_numpy(xyz_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fmm.fmm_set_timing(f.h, True)
+
+    def step():
+        f.set_particles(xyz, q)
+        f.evaluate(phi, F)
+
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    work = fmm.fmm_get_work(f.h)
+    stats = f.stats()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = []
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+        stage.append(fmm.fmm_get_stage_times(f.h).tolist())
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * ws * args.steps / (total_ms / 1e3)
+
+    # end to end through the same calls with pinned host buffers
+    xyz_h = torch.from_numpy(xyz_np).pin_memory()
+    q_h = torch.from_numpy(q_np).pin_memory()
+    phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.set_particles(xyz_h, q_h)
+        f.evaluate(phi_h, F_h)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = n * ws * len(e_ms) / (e2e_total / 1e3)
+
+    if rank != 0:
+        f.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    pk = peaks()
+    C = p ** 3
+    stage = np.array(stage)
+    m2l_leaf_ms = float(np.mean(stage[:, 2]))
+    p2p_ms = float(np.mean(stage[:, 5]))
+    m2l_pairs_leaf = int(work[1 + (h - 1)])
+    m2l_flop = 2.0 * C * C * m2l_pairs_leaf
+    p2p_pairs = int(work[0])
+    m2l_kind = int(stats[4])  # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
+    tc_path = m2l_kind == 2
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    if tc_path:
+        bound, peak, peak_note = "tensor", pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
+    elif m2l_kind == 1:
+        bound, peak, peak_note = "alu", fp32_peak, "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock"
+    else:
+        bound, peak, peak_note = "alu", fp32_peak / 64.0, "FP64 FMA: FP32 rate / 64 (nominal ratio)"
+    achieved = m2l_flop / (m2l_leaf_ms / 1e3) / 1e12
+    p2p_gflop = 20.0 * p2p_pairs / 1e9
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "height": h, "order": p, "precision": args.precision,
+                   "distribution": w["dist"], "charges": w["qkind"], "seed": w["seed"],
+                   "l2": "flushed between steps (512 MB rewrite outside the timed events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "stage_ms": {"upward": float(np.mean(stage[:, 0])), "m2l_all": float(np.mean(stage[:, 1])),
+                     "m2l_leaf": m2l_leaf_ms, "m2l_coarse": float(np.mean(stage[:, 3])),
+                     "l2l": float(np.mean(stage[:, 4])), "p2p": p2p_ms, "l2p_out": float(np.mean(stage[:, 6])),
+                     "evaluate": float(np.mean(stage[:, 7]))},
+        "roofline": {"kernel": ["k_m2l_fp64_simt", "k_m2l_simt (FP32 CUDA cores)", "k_m2l_tc (tcgen05)"][m2l_kind]
+                     + ", leaf level", "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic": f"2 x {C}^2 flop x {m2l_pairs_leaf} pairs = {m2l_flop:.4g} flop per launch",
+                     "peak_source": peak_note},
+        "roofline_p2p": {"bound": "alu", "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
+                         "interactions": p2p_pairs,
+                         "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
+                         "peak_fp32_tflops": fp32_peak},
+        "gpu_launches": int((stats[0] + stats[1]) * args.steps),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
+                "d2h_bytes_per_step": int(32 * n), "steps": len(e_ms)},
+        "clocks": clk,
+        "wall_s": t_wall,
+    }
+    f.close()
+    if ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLE)
+    print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

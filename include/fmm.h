@@ -1,0 +1,159 @@
+/*
+ * fmm.h -- C ABI of the B300 (sm_103a) black-box FMM library libfmm_b300.so.
+ *
+ * The library evaluates, for N charged particles x_i with charges q_i, the
+ * pairwise sums of the paper's eq. 1 with the Laplace kernels of eq. 2
+ * (Agullo et al., "Pipelining the Fast Multipole Method over a Runtime
+ * System", 2012, Sec. 2 and Sec. 2.1):
+ *
+ *     phi_i = sum_{j != i} q_j / |x_i - x_j|
+ *     F_i   = sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3      (= -grad phi_i)
+ *
+ * by the black-box FMM of Sec. 2.1: an octree of `height` levels (0 .. h-1,
+ * leaf level h-1), Chebyshev interpolation with `order` roots per axis
+ * (eq. 3-5; the paper's l, so a cell carries order^3 coefficients), P2M,
+ * M2M, M2L (the up to 189 far cells of Sec. 2.1.2), L2L, L2P, and P2P over
+ * the up to 27 near leaves.  Pairs at distance zero (a particle with itself,
+ * coincident particles) contribute nothing.  F is the field per unit target
+ * charge; the force on particle i is q_i F_i.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an fmm_status; no exception or signal crosses the
+ *    ABI.  On failure the handle's message is available from fmm_last_error.
+ *  - Pointers to particle data may be device pointers (cudaMalloc, PyTorch
+ *    CUDA tensors, managed memory) or host pointers (pageable or pinned); the
+ *    library tells them apart with cudaPointerGetAttributes.  With host
+ *    pointers the call copies through the device and returns only when the
+ *    copy is complete.  Arrays are dense, row-major, FP64.
+ *  - Work is enqueued on the handle's stream (fmm_set_stream).
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef FMM_B300_H
+#define FMM_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx* fmm_handle;
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_ARG = -1,     /* invalid argument (range, null pointer, non-finite input) */
+  FMM_ERR_OOM = -2,     /* device allocation failed */
+  FMM_ERR_CUDA = -3,    /* a CUDA runtime call or a kernel launch failed */
+  FMM_ERR_STATE = -4,   /* call out of order (e.g. evaluate before set_particles) */
+  FMM_ERR_TIMEOUT = -5  /* a bounded device-side wait ran out (kernel returned early) */
+} fmm_status;
+
+typedef enum {
+  FMM_FP64 = 0,   /* every stage in FP64 on the GPU */
+  FMM_MIXED = 1   /* FP32 P2P and expansions, split-TF32 tensor-core M2L, FP32 accumulate */
+} fmm_precision;
+
+/* Creates a handle for trees of `height` levels (1..11) and interpolation
+ * order `order` (2..10 roots per axis; Sec. 2.1.1, the paper's l).  Allocates
+ * the translation operators of Sec. 2.1.1-2.1.2 on the current CUDA device
+ * and computes them there in FP64 (the 316 M2L operators for unit cell
+ * half-width, scaled per level by homogeneity).  *out receives the handle
+ * (NULL on failure).  Errors: FMM_ERR_ARG (range, out == NULL),
+ * FMM_ERR_CUDA (no device), FMM_ERR_OOM. */
+fmm_status fmm_create(int height, int order, fmm_handle* out);
+
+/* Releases every device buffer, stream and graph the handle owns.  NULL is
+ * accepted.  Synchronises the handle's stream first. */
+fmm_status fmm_destroy(fmm_handle h);
+
+/* Sets the CUDA stream (a cudaStream_t, NULL = legacy default stream) on
+ * which later calls enqueue their work.  The caller keeps the stream alive. */
+fmm_status fmm_set_stream(fmm_handle h, void* cuda_stream);
+
+/* Chooses the arithmetic of later evaluations (default FMM_MIXED). */
+fmm_status fmm_set_precision(fmm_handle h, int precision);
+
+/* Loads n particles and builds the tree (Sec. 3.2 subdivision, Sec. 4.2
+ * Morton order): root cube = per-axis minimum corner and largest extent
+ * (side 1 if all points coincide), leaf-level Morton keys
+ * floor(((x - lo) / W) * 2^(h-1)) clamped to the cube with x the most
+ * significant bit of each triple, a stable radix sort (ties keep input
+ * order), leaf ranges and the non-empty cells of every level.
+ *   xyz: [n][3] FP64, q: [n] FP64 (device or host).  The data are copied;
+ *   the caller may release both after the call returns (the call
+ *   synchronises the stream: the per-level cell counts come back to the host).
+ *   n = 0 is valid.  n <= 2^30.
+ * Errors: FMM_ERR_ARG (n out of range, NULL with n > 0, a non-finite
+ * coordinate or charge -- detected on the device), FMM_ERR_OOM, FMM_ERR_CUDA. */
+fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const double* q);
+
+/* Runs one FMM pass over the particles of the last fmm_set_particles:
+ * P2M, M2M, M2L, L2L, L2P on one branch and P2P on another (Sec. 3.2), and
+ * writes phi [n] and F [n][3] (FP64) in the caller's input order.
+ * Device outputs: the call returns after enqueueing (stream-ordered).
+ * Host outputs: the call returns after the results are in host memory.
+ * Errors: FMM_ERR_STATE (no particles loaded), FMM_ERR_ARG (NULL with
+ * n > 0), FMM_ERR_CUDA. */
+fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
+
+/* Morton permutation of the last fmm_set_particles: perm[r] = input index of
+ * the particle with Morton rank r.  perm: [n] int64, device or host. */
+fmm_status fmm_get_order(fmm_handle h, int64_t* perm);
+
+/* Root cube of the last fmm_set_particles: out[0..2] = lower corner,
+ * out[3] = side.  out: 4 doubles, host. */
+fmm_status fmm_get_box(fmm_handle h, double* out);
+
+/* Number of non-empty cells at `level` (0 .. height-1) of the current tree,
+ * host int64. */
+fmm_status fmm_get_level_size(fmm_handle h, int level, int64_t* out);
+
+/* Sorted Morton keys (at that level's resolution) of the non-empty cells of
+ * `level`; keys: [level_size] uint64, device or host. */
+fmm_status fmm_get_level_keys(fmm_handle h, int level, uint64_t* keys);
+
+/* Leaf level: first particle (Morton rank) and particle count per leaf;
+ * other levels: first child index (at level+1) and child count per cell.
+ * first, count: [level_size] int64, device or host. */
+fmm_status fmm_get_level_ranges(fmm_handle h, int level, int64_t* first, int64_t* count);
+
+/* Multipole (which = 0) or local (which = 1) expansion of every non-empty
+ * cell of `level` after the last fmm_evaluate, widened to FP64:
+ * out [level_size][order^3], coefficient index (mx * p + my) * p + mz.
+ * Levels below 2 carry none (FMM_ERR_ARG).  Synchronises the stream. */
+fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
+
+/* Counters of the handle: out[0] = kernel launches enqueued by the last
+ * fmm_set_particles, out[1] = kernels launched by one fmm_evaluate
+ * (nodes of its CUDA graph + the output launch), out[2] = 1 if evaluations
+ * replay a CUDA graph, out[3] = bytes of device memory the handle holds,
+ * out[4] = M2L kernel of the current precision (0 = FP64 CUDA cores,
+ * 1 = FP32 CUDA cores on split operands, 2 = tcgen05 tensor cores),
+ * out[5..7] = 0 (reserved).  out: 8 int64, host. */
+fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
+
+/* Algorithmic work of one evaluation on the current tree (Sec. 4.3 counts
+ * work the same way): out[0] = directed P2P particle pairs (each target with
+ * every particle of its up to 27 near leaves, itself excluded), out[1 + l] =
+ * M2L (target, source) cell pairs at level l for l = 0 .. 10 (zero outside
+ * 2 .. height-1).  Synchronises the stream.  out: 12 int64, host. */
+fmm_status fmm_get_work(fmm_handle h, int64_t* out);
+
+/* Per-stage device times of the last fmm_evaluate in milliseconds (CUDA
+ * events recorded inside the evaluation when timing is on), in this order:
+ * [0] upward pass (P2M + M2M), [1] M2L (all levels), [2] M2L at the leaf
+ * level alone, [3] M2L at the coarser levels, [4] L2L (all levels),
+ * [5] P2P (on the parallel branch), [6] L2P + output, [7] whole evaluation.  fmm_set_timing(h, 1) turns the events on (the
+ * evaluation graph is rebuilt); this call synchronises the stream.
+ * out: 8 floats, host. */
+fmm_status fmm_set_timing(fmm_handle h, int on);
+fmm_status fmm_get_stage_times(fmm_handle h, float* out);
+
+/* Message of the last failed call on this handle ("" if none).  With
+ * h == NULL: the message of the last failed fmm_create in this thread. */
+const char* fmm_last_error(fmm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_B300_H */

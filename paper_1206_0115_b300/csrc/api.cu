@@ -1,0 +1,472 @@
+// api.cu -- the C ABI of include/fmm.h.
+//
+// Evaluation schedule (Sec. 3.2's two traversals plus the independent P2P):
+// one CUDA graph per tree shape and precision, captured on an internal stream
+// and replayed on the caller's stream:
+//
+//     fork --> P2P ------------------------------------------.
+//       \--> P2M --> M2M (leaf-1 .. 2) --> M2L (all levels) --> L2L (2 .. leaf-1) --> join
+//
+// followed by one plain launch of L2P, which adds the near field and scatters
+// phi and F to the caller's order (its arguments are the caller's output
+// pointers, which change from call to call).
+#include <cstdarg>
+#include <cstdlib>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+
+static thread_local char g_create_err[512] = "";
+
+fmm_status set_err(Ctx* c, fmm_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c ? c->err : g_create_err, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+fmm_status cuda_err(Ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FMM_OK;
+  if (e == cudaErrorMemoryAllocation) return set_err(c, FMM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_err(c, FMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+fmm_status dalloc(Ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_err(c, e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA,
+                   "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  c->bytes += (int64_t)bytes;
+  return FMM_OK;
+}
+
+void dfree(Ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  c->bytes -= (int64_t)(bytes ? bytes : 16);
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+fmm_status ensure_stage(Ctx* c, double** buf, int64_t* cap, int64_t count) {
+  if (count <= *cap) return FMM_OK;
+  dfree(c, *buf, sizeof(double) * (size_t)*cap);
+  *buf = nullptr;
+  *cap = 0;
+  void* p;
+  int64_t nc = count + count / 8 + 64;
+  FMM_TRY(dalloc(c, &p, sizeof(double) * (size_t)nc));
+  *buf = (double*)p;
+  *cap = nc;
+  return FMM_OK;
+}
+
+__global__ void k_widen_i32(int64_t n, const int32_t* __restrict__ a, int64_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i];
+}
+__global__ void k_widen_u32(int64_t n, const uint32_t* __restrict__ a, uint64_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i];
+}
+
+// copies n 8-byte values from a device temp to the caller (device or host)
+fmm_status deliver(Ctx* c, void* dst, const void* devsrc, int64_t n) {
+  if (n == 0) return FMM_OK;
+  FMM_CUDA(c, cudaMemcpyAsync(dst, devsrc, 8 * (size_t)n, cudaMemcpyDefault, c->stream));
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FMM_OK;
+}
+
+fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
+  FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
+  FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], c->side, cudaEventRecordExternal));
+  FMM_TRY(launch_p2p(c, c->side));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], c->side, cudaEventRecordExternal));
+  FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
+  FMM_TRY(launch_upward(c, s));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
+  FMM_TRY(launch_m2l_level(c, s, 0, c->leaf_tile_end()));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[2], s, cudaEventRecordExternal));
+  FMM_TRY(launch_m2l_level(c, s, c->leaf_tile_end(), c->ntiles - c->leaf_tile_end()));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
+  FMM_TRY(launch_l2l(c, s));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[4], s, cudaEventRecordExternal));
+  FMM_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+  return FMM_OK;
+}
+
+// Everything the captured evaluation graph bakes into its kernel arguments.
+std::vector<int64_t> graph_signature(const Ctx* c) {
+  std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n};
+  for (int l = 0; l <= c->leaf; ++l) {
+    s.push_back(c->lv.ncell[l]);
+    s.push_back(c->lv.row_off[l]);
+    for (const void* p : {(const void*)c->lv.key[l], (const void*)c->lv.first[l], (const void*)c->lv.count[l],
+                          (const void*)c->lv.parent[l], (const void*)c->lv.grid[l], (const void*)c->lv.cls[l]})
+      s.push_back((int64_t)(uintptr_t)p);
+  }
+  for (const void* p : {(const void*)c->pos32, (const void*)c->pos32lo, (const void*)c->pos64, (const void*)c->near32,
+                        (const void*)c->near64, (const void*)c->Mhi, (const void*)c->Mlo, (const void*)c->L32,
+                        (const void*)c->M64, (const void*)c->L64, (const void*)c->tiles, (const void*)c->tile_src,
+                        (const void*)c->tile_act, (const void*)c->tile_nact, (const void*)c->K64,
+                        (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm})
+    s.push_back((int64_t)(uintptr_t)p);
+  return s;
+}
+
+void drop_graph(Ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  c->graph_ok = false;
+}
+
+fmm_status build_graph(Ctx* c) {
+  drop_graph(c);
+  cudaStream_t cap = c->cap;
+  FMM_CUDA(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  fmm_status st = enqueue_eval(c, cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (st != FMM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  FMM_CUDA(c, e);
+  c->graph = g;
+  FMM_CUDA(c, cudaGraphInstantiate(&c->gexec, g, 0));
+  size_t nn = 0;
+  FMM_CUDA(c, cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  FMM_CUDA(c, cudaGraphGetNodes(g, nodes.data(), &nn));
+  int64_t kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  c->launches_eval = kernels + 1;  // + the L2P/output launch
+  c->graph_sig = graph_signature(c);
+  c->graph_ok = true;
+  c->graph_precision = c->precision;
+  return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+fmm_status fmm_create(int height, int order, fmm_handle* out) {
+  if (!out) return set_err(nullptr, FMM_ERR_ARG, "fmm_create: out is NULL");
+  *out = nullptr;
+  if (height < 1 || height > FMM_MAX_LEVELS)
+    return set_err(nullptr, FMM_ERR_ARG, "fmm_create: height %d outside 1..%d", height, FMM_MAX_LEVELS);
+  if (order < 2 || order > FMM_MAX_ORDER)
+    return set_err(nullptr, FMM_ERR_ARG, "fmm_create: order %d outside 2..%d", order, FMM_MAX_ORDER);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaFree(nullptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(nullptr, FMM_ERR_CUDA, "fmm_create: no usable CUDA device (%s)", cudaGetErrorString(e));
+  }
+  Ctx* c = new Ctx();
+  c->dev = dev;
+  c->height = height;
+  c->order = order;
+  c->leaf = height - 1;
+  c->ncoef = order * order * order;
+  c->cpad = (c->ncoef + 1 + 31) / 32 * 32;  // + the mean slot of mixed local expansions
+  fmm_status st = FMM_OK;
+  auto fail = [&](fmm_status s) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", c->err);
+    fmm_destroy(c);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cuda_err(c, cudaGetLastError(), "fmm_create: stream/event creation");
+    return fail(FMM_ERR_CUDA);
+  }
+  for (int k = 0; k < 10; ++k)
+    if (cudaEventCreate(&c->tev[k]) != cudaSuccess) {
+      cuda_err(c, cudaGetLastError(), "fmm_create: event creation");
+      return fail(FMM_ERR_CUDA);
+    }
+  void* p;
+  if ((st = dalloc(c, &p, 4 * sizeof(double))) != FMM_OK) return fail(st);
+  c->box = (double*)p;
+  if ((st = dalloc(c, &p, 128 * sizeof(int32_t))) != FMM_OK) return fail(st);
+  c->counters = (int32_t*)p;
+  if (cudaMallocHost((void**)&c->counters_h, 128 * sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->box_h, 4 * sizeof(double)) != cudaSuccess) {
+    cuda_err(c, cudaGetLastError(), "fmm_create: pinned host buffers");
+    return fail(FMM_ERR_OOM);
+  }
+  for (int l = 0; l <= c->leaf; ++l) {
+    size_t bytes = sizeof(int32_t) * ((size_t)1 << (3 * l));
+    if ((st = dalloc(c, &p, bytes)) != FMM_OK) return fail(st);
+    c->lv.grid[l] = (int32_t*)p;
+    if (cudaMemset(p, 0xFF, bytes) != cudaSuccess) {
+      cuda_err(c, cudaGetLastError(), "fmm_create: grid memset");
+      return fail(FMM_ERR_CUDA);
+    }
+  }
+  if ((st = operators_init(c)) != FMM_OK) return fail(st);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cuda_err(c, cudaGetLastError(), "fmm_create");
+    return fail(FMM_ERR_CUDA);
+  }
+  *out = c;
+  return FMM_OK;
+}
+
+fmm_status fmm_destroy(fmm_handle h) {
+  Ctx* c = h;
+  if (!c) return FMM_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
+  drop_graph(c);
+  void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pos64, c->pos32, c->pos32lo, c->near32,
+                  c->near64,
+                  c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
+                  c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
+                  c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
+    void* lb[] = {c->lv.key[l], c->lv.first[l], c->lv.count[l], c->lv.parent[l], c->lv.grid[l], c->lv.cls[l]};
+    for (void* b : lb)
+      if (b) cudaFree(b);
+  }
+  if (c->counters_h) cudaFreeHost(c->counters_h);
+  if (c->box_h) cudaFreeHost(c->box_h);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (int k = 0; k < 10; ++k)
+    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+  delete c;
+  return FMM_OK;
+}
+
+fmm_status fmm_set_stream(fmm_handle h, void* stream) {
+  if (!h) return FMM_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return FMM_OK;
+}
+
+fmm_status fmm_set_precision(fmm_handle h, int precision) {
+  if (!h) return FMM_ERR_ARG;
+  if (precision != FMM_FP64 && precision != FMM_MIXED)
+    return set_err(h, FMM_ERR_ARG, "fmm_set_precision: unknown precision %d", precision);
+  if (precision != h->precision) {
+    h->precision = precision;
+    h->graph_ok = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const double* q) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (n < 0 || n > ((int64_t)1 << 30))
+    return set_err(c, FMM_ERR_ARG, "fmm_set_particles: n = %lld outside 0..2^30", (long long)n);
+  if (n > 0 && (!xyz || !q)) return set_err(c, FMM_ERR_ARG, "fmm_set_particles: NULL input with n > 0");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  const double* dxyz = xyz;
+  const double* dq = q;
+  if (n > 0 && !(is_device_ptr(xyz) && is_device_ptr(q))) {
+    FMM_TRY(ensure_stage(c, &c->stage_in, &c->stage_in_cap, 4 * n));
+    FMM_CUDA(c, cudaMemcpyAsync(c->stage_in, xyz, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->stage_in + 3 * n, q, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+    dxyz = c->stage_in;
+    dq = c->stage_in + 3 * n;
+  }
+  FMM_TRY(tree_build(c, n, dxyz, dq));
+  return FMM_OK;
+}
+
+fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_evaluate: no particles loaded");
+  const int64_t n = c->n;
+  if (n == 0) return FMM_OK;
+  if (!phi || !F) return set_err(c, FMM_ERR_ARG, "fmm_evaluate: NULL output");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  FMM_TRY(operators_m2l(c, c->precision));
+  const bool dev_out = is_device_ptr(phi) && is_device_ptr(F);
+  double *dphi = phi, *dF = F;
+  if (!dev_out) {
+    FMM_TRY(ensure_stage(c, &c->stage_out, &c->stage_out_cap, 4 * n));
+    dphi = c->stage_out;
+    dF = c->stage_out + n;
+  }
+  if (c->use_graph) {
+    if (!c->graph_ok || c->graph_sig != graph_signature(c)) FMM_TRY(build_graph(c));
+    FMM_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+  } else {
+    FMM_TRY(enqueue_eval(c, c->stream));
+  }
+  if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[7], c->stream));
+  FMM_TRY(launch_l2p_out(c, c->stream, dphi, dF));
+  if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[8], c->stream));
+  c->tev_recorded = c->timing;
+  if (!dev_out) {
+    FMM_CUDA(c, cudaMemcpyAsync(phi, dphi, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(F, dF, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+    FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_get_order(fmm_handle h, int64_t* perm) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_get_order: no particles loaded");
+  if (c->n == 0) return FMM_OK;
+  if (!perm) return set_err(c, FMM_ERR_ARG, "fmm_get_order: NULL output");
+  FMM_TRY(ensure_stage(c, &c->stage_out, &c->stage_out_cap, c->n));
+  k_widen_i32<<<ceil_div(c->n, 256), 256, 0, c->stream>>>(c->n, c->perm, (int64_t*)c->stage_out);
+  FMM_CUDA(c, cudaGetLastError());
+  return deliver(c, perm, c->stage_out, c->n);
+}
+
+fmm_status fmm_get_box(fmm_handle h, double* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  if (!h->loaded) return set_err(h, FMM_ERR_STATE, "fmm_get_box: no particles loaded");
+  for (int d = 0; d < 4; ++d) out[d] = h->box_host[d];
+  return FMM_OK;
+}
+
+fmm_status fmm_get_level_size(fmm_handle h, int level, int64_t* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  if (!h->loaded) return set_err(h, FMM_ERR_STATE, "fmm_get_level_size: no particles loaded");
+  if (level < 0 || level > h->leaf) return set_err(h, FMM_ERR_ARG, "level %d outside 0..%d", level, h->leaf);
+  *out = h->lv.ncell[level];
+  return FMM_OK;
+}
+
+fmm_status fmm_get_level_keys(fmm_handle h, int level, uint64_t* keys) {
+  int64_t nc;
+  FMM_TRY(fmm_get_level_size(h, level, &nc));
+  Ctx* c = h;
+  if (nc == 0) return FMM_OK;
+  if (!keys) return set_err(c, FMM_ERR_ARG, "NULL output");
+  FMM_TRY(ensure_stage(c, &c->stage_out, &c->stage_out_cap, nc));
+  k_widen_u32<<<ceil_div(nc, 256), 256, 0, c->stream>>>(nc, c->lv.key[level], (uint64_t*)c->stage_out);
+  FMM_CUDA(c, cudaGetLastError());
+  return deliver(c, keys, c->stage_out, nc);
+}
+
+fmm_status fmm_get_level_ranges(fmm_handle h, int level, int64_t* first, int64_t* count) {
+  int64_t nc;
+  FMM_TRY(fmm_get_level_size(h, level, &nc));
+  Ctx* c = h;
+  if (nc == 0) return FMM_OK;
+  if (!first || !count) return set_err(c, FMM_ERR_ARG, "NULL output");
+  FMM_TRY(ensure_stage(c, &c->stage_out, &c->stage_out_cap, nc));
+  k_widen_i32<<<ceil_div(nc, 256), 256, 0, c->stream>>>(nc, c->lv.first[level], (int64_t*)c->stage_out);
+  FMM_CUDA(c, cudaGetLastError());
+  FMM_TRY(deliver(c, first, c->stage_out, nc));
+  k_widen_i32<<<ceil_div(nc, 256), 256, 0, c->stream>>>(nc, c->lv.count[level], (int64_t*)c->stage_out);
+  FMM_CUDA(c, cudaGetLastError());
+  return deliver(c, count, c->stage_out, nc);
+}
+
+fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out) {
+  int64_t nc;
+  FMM_TRY(fmm_get_level_size(h, level, &nc));
+  Ctx* c = h;
+  if (level < 2 || (which != 0 && which != 1))
+    return set_err(c, FMM_ERR_ARG, "fmm_get_expansion: level %d / which %d invalid", level, which);
+  if (nc == 0) return FMM_OK;
+  if (!out) return set_err(c, FMM_ERR_ARG, "NULL output");
+  const int64_t total = nc * c->ncoef;
+  FMM_TRY(ensure_stage(c, &c->stage_out, &c->stage_out_cap, total));
+  FMM_TRY(expansion_to_f64(c, level, which, c->stage_out));
+  return deliver(c, out, c->stage_out, total);
+}
+
+fmm_status fmm_get_stats(fmm_handle h, int64_t* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  out[0] = h->launches_set;
+  out[1] = h->graph_ok ? h->launches_eval : count_launches_eval(h);
+  out[2] = h->use_graph ? 1 : 0;
+  out[3] = h->bytes;
+  out[4] = m2l_kind(h);
+  out[5] = out[6] = out[7] = 0;
+  return FMM_OK;
+}
+
+fmm_status fmm_get_work(fmm_handle h, int64_t* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  if (!h->loaded) return set_err(h, FMM_ERR_STATE, "fmm_get_work: no particles loaded");
+  return work_counts(h, out);
+}
+
+fmm_status fmm_set_timing(fmm_handle h, int on) {
+  if (!h) return FMM_ERR_ARG;
+  if ((on != 0) != h->timing) {
+    h->timing = on != 0;
+    h->graph_ok = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_get_stage_times(fmm_handle h, float* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  Ctx* c = h;
+  if (!c->tev_recorded) return set_err(c, FMM_ERR_STATE, "fmm_get_stage_times: no timed evaluation");
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  auto el = [&](int a, int b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->tev[a], c->tev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    return ms;
+  };
+  out[0] = el(0, 1);  // P2M + M2M
+  out[1] = el(1, 3);  // M2L, all levels
+  out[2] = el(1, 2);  // M2L, leaf level
+  out[3] = el(2, 3);  // M2L, coarser levels
+  out[4] = el(3, 4);  // L2L
+  out[5] = el(5, 6);  // P2P
+  out[6] = el(7, 8);  // L2P + output
+  out[7] = el(0, 8);  // whole evaluation (from the branch start)
+  return FMM_OK;
+}
+
+const char* fmm_last_error(fmm_handle h) { return h ? h->err : g_create_err; }
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// common.cuh -- internal declarations of libfmm_b300 (not part of the ABI).
+//
+// Data layout in HBM (one handle):
+//   particles, Morton order: pos64 [n] double4 (x, y, z, q), pos32 [n] float4
+//     ((x - c_leaf) / w_leaf, ..., q) -- coordinates in leaf widths relative to
+//     the leaf centre, so P2P offsets between neighbouring leaves are exact
+//     integers and xi = 2 * pos32 for P2M / L2P; pos32lo [n] float4 holds the
+//     FP32 rounding residual of each coordinate (used for close pairs).
+//   cells per level l: key (uint32 Morton key at level resolution), first and
+//     count (leaf: particle range; other levels: child range at l+1), parent,
+//     a dense grid[8^l] key -> cell index (-1 = empty) for neighbour lookups,
+//     and the level's cells grouped by child class (key & 7) for M2L.
+//   expansions: one buffer per kind, rows of `cpad` coefficients
+//     (order^3 rounded up to 32, pad columns zero), level l occupying rows
+//     row_off[l] .. row_off[l] + ncell[l], the last row of each level all zero
+//     (the source row of a missing M2L neighbour).
+//   M2L operators: 316 transfer vectors t (|t|_inf in {2,3}) in lexicographic
+//     order; K_t[m][n] = 1 / |2t + xbar_n - xbar_m| for unit half-width.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fmm.h"
+
+#define FMM_MAX_LEVELS 11
+#define FMM_MAX_ORDER 10
+#define FMM_NT 316       // transfer vectors
+#define FMM_NT_CLASS 189 // transfer vectors of one child class
+#define FMM_TILE 128     // M2L target rows per tile
+
+namespace fmm {
+
+struct Tile {
+  int level;  // tree level (2 .. leaf)
+  int cls;    // child class of every target (key & 7)
+  int first;  // offset into the level's class-grouped cell list
+  int count;  // targets in the tile (<= FMM_TILE)
+};
+
+// Per-level device pointers handed to kernels by value.
+struct LevelPtrs {
+  uint32_t* key[FMM_MAX_LEVELS];
+  int32_t* first[FMM_MAX_LEVELS];
+  int32_t* count[FMM_MAX_LEVELS];
+  int32_t* parent[FMM_MAX_LEVELS];
+  int32_t* grid[FMM_MAX_LEVELS];
+  int32_t* cls[FMM_MAX_LEVELS];
+  int64_t row_off[FMM_MAX_LEVELS];
+  int32_t ncell[FMM_MAX_LEVELS];  // host-known sizes (valid after the readback)
+};
+
+}  // namespace fmm
+
+// The handle of include/fmm.h.
+struct fmm_ctx {
+  using Tile = fmm::Tile;
+  using LevelPtrs = fmm::LevelPtrs;
+  int height = 0, order = 0, leaf = 0, ncoef = 0, cpad = 0;
+  int precision = FMM_MIXED;
+  int dev = 0;
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t side = nullptr;    // P2P branch
+  cudaStream_t cap = nullptr;     // graph capture
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  char err[512] = {0};
+
+  // particles
+  int64_t n = 0, ncap = 0;
+  bool loaded = false;
+  uint32_t *key_a = nullptr, *key_b = nullptr, *idx_a = nullptr, *idx_b = nullptr;
+  uint32_t* skey = nullptr;  // sorted keys (points at key_a or key_b)
+  int32_t* perm = nullptr;
+  double4* pos64 = nullptr;
+  float4* pos32 = nullptr;
+  float4* pos32lo = nullptr;  // rounding residuals of pos32's coordinates (x = hi + lo to ~2^-48)
+  float4* near32 = nullptr;
+  double4* near64 = nullptr;
+  double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
+  int64_t stage_in_cap = 0, stage_out_cap = 0;
+
+  // scratch
+  uint32_t* scratch = nullptr;
+  int64_t scratch_cap = 0;  // in uint32 words
+  double* box = nullptr;    // lo[3], W
+  int32_t* counters = nullptr;   // device: [0..L) ncell, [16 + 8 l + c] class counts, [127] bad input
+  int32_t* counters_h = nullptr; // pinned host mirror
+  double* box_h = nullptr;       // pinned
+
+  // tree
+  LevelPtrs lv;
+  int64_t lcap[FMM_MAX_LEVELS] = {0};  // capacity (cells) of the per-level arrays
+  int32_t cls_off[FMM_MAX_LEVELS][9] = {{0}};
+  int prev_ncell[FMM_MAX_LEVELS] = {0};
+  bool have_prev = false;
+  double box_host[4] = {0, 0, 0, 1};
+
+  // expansions
+  int64_t rows = 0, rows_cap = 0;
+  float *Mhi = nullptr, *Mlo = nullptr, *L32 = nullptr;
+  double *M64 = nullptr, *L64 = nullptr;
+
+  // M2L work
+  Tile* tiles = nullptr;
+  int ntiles = 0, tiles_cap = 0;
+  int32_t* tile_src = nullptr;  // [tile][189][128]
+  int16_t* tile_act = nullptr;  // [tile][189]
+  int32_t* tile_nact = nullptr; // [tile]
+  int leaf_tiles = 0;           // tiles [0, leaf_tiles) belong to the leaf level
+  int leaf_tile_end() const { return leaf_tiles; }
+
+  // operators
+  double* nodes64 = nullptr;   // [p]
+  double* cheb64 = nullptr;    // [p][p]: T_n(xbar_m)
+  float* cheb32 = nullptr;
+  double* m2m64 = nullptr;     // [2][p][p]: S(xbar_m, (s + xbar_m')/2), s = -1, +1
+  float* m2m32 = nullptr;
+  int8_t* tvec = nullptr;      // [316][3]
+  int16_t* cls_t = nullptr;    // [8][189] -> transfer vector index
+  double* K64 = nullptr;       // [316][C][C]
+  float *Khi = nullptr, *Klo = nullptr;  // [316][cpad][cpad], TF32 split
+  bool ops64 = false, ops32 = false;
+
+  // evaluation schedule
+  std::vector<int64_t> graph_sig;  // what the captured graph depends on
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+  int graph_precision = -1;
+  bool use_graph = true;
+  bool timing = false;
+  cudaEvent_t tev[10] = {nullptr};
+  bool tev_recorded = false;
+
+  // stats
+  int64_t launches_set = 0, launches_eval = 0, bytes = 0;
+};
+
+namespace fmm {
+
+using Ctx = ::fmm_ctx;
+
+// ---- error plumbing --------------------------------------------------------
+fmm_status set_err(Ctx* c, fmm_status s, const char* fmt, ...);
+fmm_status cuda_err(Ctx* c, cudaError_t e, const char* what);
+#define FMM_CUDA(c, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_err((c), e_, #call); \
+  } while (0)
+#define FMM_TRY(expr)               \
+  do {                              \
+    fmm_status s_ = (expr);         \
+    if (s_ != FMM_OK) return s_;    \
+  } while (0)
+
+fmm_status dalloc(Ctx* c, void** p, size_t bytes);
+void dfree(Ctx* c, void* p, size_t bytes);
+
+// ---- stages (host launchers) -------------------------------------------------
+fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q);
+fmm_status operators_init(Ctx* c);
+fmm_status operators_m2l(Ctx* c, int precision);
+fmm_status launch_p2p(Ctx* c, cudaStream_t s);
+fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
+fmm_status launch_m2l_level(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
+fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
+fmm_status launch_l2l(Ctx* c, cudaStream_t s);
+fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F);
+fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out);
+int64_t count_launches_eval(const Ctx* c);
+fmm_status work_counts(Ctx* c, int64_t* out);
+int m2l_kind(const Ctx* c);  // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
+
+// ---- device helpers ----------------------------------------------------------
+// Spreads the low 10 bits of v so that bit b lands at bit 3b.
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__host__ __device__ inline uint32_t compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030C30C3u;
+  v = (v | (v >> 4)) & 0x0300F00Fu;
+  v = (v | (v >> 8)) & 0x030000FFu;
+  v = (v | (v >> 16)) & 0x000003FFu;
+  return v;
+}
+// Morton key with x the most significant bit of each (x, y, z) triple.
+__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+}
+__host__ __device__ inline void demorton3(uint32_t k, int& x, int& y, int& z) {
+  x = (int)compact3(k >> 2);
+  y = (int)compact3(k >> 1);
+  z = (int)compact3(k);
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace fmm

@@ -1,0 +1,627 @@
+// farfield.cu -- P2M, M2M, L2L, L2P (+ final sum and scatter) and the SIMT
+// M2L of the black-box FMM (Sec. 2.1, eq. 3-5; Sec. 3.2 traversal order).
+//
+// Interpolation: S(xbar_m, xi) = 1/p + 2/p sum_{n=1}^{p-1} T_n(xbar_m) T_n(xi)
+// (eq. 5) with T_n(xbar_m) from a table and T_n(xi) by the recurrence;
+// S_m(x) is the tensor product of eq. 4 (multi-index z fastest).
+//   P2M (leaf)  M_m = sum_j q_j S_m((y_j - c)/a)
+//   M2M         M_P = sum_children (A_sx (x) A_sy (x) A_sz) M_C, applied as three
+//               1-D contractions (the tensor-product reformulation of Sec. 2.1.1)
+//   M2L         L_T = (1/a) sum_{far S} K_t M_S            (Sec. 2.1.2)
+//   L2L         L_C += (A_sx (x) A_sy (x) A_sz)^T L_P
+//   L2P         phi = sum_m S_m(xi) L_m, F = -(1/a) sum_m grad_xi S_m(xi) L_m
+// Mixed precision keeps multipoles as a TF32 hi/lo pair (hi + lo = M to FP32
+// rounding) for the tensor-core M2L, and a local expansion as its cell mean
+// (slot C of the row) plus FP32 deviations from it: with like-signed charges
+// the far potential is large and smooth, and node values stored whole in FP32
+// would lose the gradient (the force) to rounding by a factor that doubles
+// per level.  FP64 keeps both whole in FP64.
+#include "common.cuh"
+
+namespace fmm {
+
+namespace {
+
+__device__ inline float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// S(xbar_m, xi) for m < P, and optionally dS/dxi.
+template <int P, typename T, bool DERIV>
+__device__ inline void interp_weights(const T* __restrict__ sC, T xi, T* S, T* dS) {
+  T Tn[P], dTn[P];
+  Tn[0] = T(1);
+  if (P > 1) Tn[1] = xi;
+#pragma unroll
+  for (int n = 2; n < P; ++n) Tn[n] = T(2) * xi * Tn[n - 1] - Tn[n - 2];
+  if (DERIV) {
+    // dT_n/dxi = n U_{n-1}(xi)
+    T U0 = T(1), U1 = T(2) * xi;
+    dTn[0] = T(0);
+    if (P > 1) dTn[1] = T(1);
+#pragma unroll
+    for (int n = 2; n < P; ++n) {
+      dTn[n] = T(n) * U1;
+      T U2 = T(2) * xi * U1 - U0;
+      U0 = U1;
+      U1 = U2;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    T s = T(0), ds = T(0);
+#pragma unroll
+    for (int n = 1; n < P; ++n) {
+      s += sC[m * P + n] * Tn[n];
+      if (DERIV) ds += sC[m * P + n] * dTn[n];
+    }
+    S[m] = T(1) / T(P) + T(2) / T(P) * s;
+    if (DERIV) dS[m] = T(2) / T(P) * ds;
+  }
+}
+
+__device__ inline void cell_centre(const double* box, int level, uint32_t key, double* c, double& a) {
+  int ix, iy, iz;
+  demorton3(key, ix, iy, iz);
+  double w = ldexp(box[3], -level);
+  c[0] = box[0] + ((double)ix + 0.5) * w;
+  c[1] = box[1] + ((double)iy + 0.5) * w;
+  c[2] = box[2] + ((double)iz + 0.5) * w;
+  a = 0.5 * w;
+}
+
+// ---------------------------------------------------------------- P2M
+
+template <int P, typename T, bool MIXED>
+__global__ void __launch_bounds__(128)
+k_p2m(LevelPtrs lv, int leaf, const double* __restrict__ box, const T* __restrict__ cheb, int cpad,
+      const double4* __restrict__ pos64, const float4* __restrict__ pos32, T* __restrict__ Mout,
+      T* __restrict__ Mlo) {
+  constexpr int C = P * P * P, NB = 32, NPER = (C + 127) / 128;
+  __shared__ T sS[NB][3][P];
+  __shared__ T sq[NB];
+  __shared__ T sC[P * P];
+  const int cell = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < P * P; i += 128) sC[i] = cheb[i];
+  const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
+  double ctr[3], a = 1.0;
+  if (!MIXED) cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  T acc[NPER];
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) acc[k] = T(0);
+  __syncthreads();
+  for (int b0 = 0; b0 < cnt; b0 += NB) {
+    const int nb = min(NB, cnt - b0);
+    if (tid < 3 * nb) {
+      const int j = tid / 3, d = tid - 3 * j;
+      T xi, qq;
+      if (MIXED) {
+        float4 pp = pos32[first + b0 + j];
+        xi = T(2) * (d == 0 ? pp.x : d == 1 ? pp.y : pp.z);
+        qq = pp.w;
+      } else {
+        double4 pp = pos64[first + b0 + j];
+        double v = d == 0 ? pp.x : d == 1 ? pp.y : pp.z;
+        xi = (T)((v - ctr[d]) / a);
+        qq = (T)pp.w;
+      }
+      T S[P];
+      interp_weights<P, T, false>(sC, xi, S, nullptr);
+#pragma unroll
+      for (int m = 0; m < P; ++m) sS[j][d][m] = S[m];
+      if (d == 0) sq[j] = qq;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+      const int m = tid + 128 * k;
+      if (m < C) {
+        const int mx = m / (P * P), my = (m / P) % P, mz = m % P;
+        T s = acc[k];
+        for (int j = 0; j < nb; ++j) s += sq[j] * sS[j][0][mx] * sS[j][1][my] * sS[j][2][mz];
+        acc[k] = s;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t row = lv.row_off[leaf] + cell;
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) {
+    const int m = tid + 128 * k;
+    if (m < C) {
+      if (MIXED) {
+        float hi = tf32_rna((float)acc[k]);
+        Mout[row * cpad + m] = hi;
+        Mlo[row * cpad + m] = tf32_rna((float)acc[k] - hi);
+      } else {
+        Mout[row * cpad + m] = acc[k];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- M2M
+
+template <int P, typename T, bool MIXED>
+__global__ void __launch_bounds__(256)
+k_m2m(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, const T* __restrict__ Mhi,
+      const T* __restrict__ Mlo, T* __restrict__ Mout_hi, T* __restrict__ Mout_lo) {
+  constexpr int C = P * P * P, NPER = (C + 255) / 256;
+  __shared__ T sA[2 * P * P];
+  __shared__ T sin_[C], su[C], sv[C];
+  const int cell = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < 2 * P * P; i += 256) sA[i] = A[i];
+  T acc[NPER];
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) acc[k] = T(0);
+  const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
+  for (int ch = c0; ch < c0 + nc; ++ch) {
+    const uint32_t b = lv.key[l + 1][ch] & 7u;
+    const T* Ax = sA + ((b >> 2) & 1) * P * P;
+    const T* Ay = sA + ((b >> 1) & 1) * P * P;
+    const T* Az = sA + (b & 1) * P * P;
+    const int64_t row = lv.row_off[l + 1] + ch;
+    __syncthreads();
+    for (int m = tid; m < C; m += 256) {
+      T v = Mhi[row * cpad + m];
+      if (MIXED) v += Mlo[row * cpad + m];
+      sin_[m] = v;
+    }
+    __syncthreads();
+    // z: u[x][y][mz] = sum_k Az[mz][k] in[x][y][k]
+    for (int m = tid; m < C; m += 256) {
+      const int xy = m / P, mz = m % P;
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += Az[mz * P + k] * sin_[xy * P + k];
+      su[m] = s;
+    }
+    __syncthreads();
+    // y: v[x][my][z] = sum_k Ay[my][k] u[x][k][z]
+    for (int m = tid; m < C; m += 256) {
+      const int x = m / (P * P), my = (m / P) % P, z = m % P;
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += Ay[my * P + k] * su[(x * P + k) * P + z];
+      sv[m] = s;
+    }
+    __syncthreads();
+    // x: acc[mx][y][z] += sum_k Ax[mx][k] v[k][y][z]
+#pragma unroll
+    for (int kk = 0; kk < NPER; ++kk) {
+      const int m = tid + 256 * kk;
+      if (m < C) {
+        const int mx = m / (P * P), yz = m % (P * P);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < P; ++k) s += Ax[mx * P + k] * sv[k * P * P + yz];
+        acc[kk] += s;
+      }
+    }
+  }
+  const int64_t row = lv.row_off[l] + cell;
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) {
+    const int m = tid + 256 * k;
+    if (m < C) {
+      if (MIXED) {
+        float hi = tf32_rna((float)acc[k]);
+        Mout_hi[row * cpad + m] = hi;
+        Mout_lo[row * cpad + m] = tf32_rna((float)acc[k] - hi);
+      } else {
+        Mout_hi[row * cpad + m] = acc[k];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- L2L
+
+template <int P, typename T, bool MEAN>
+__global__ void __launch_bounds__(256)
+k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lbuf) {
+  constexpr int C = P * P * P;
+  __shared__ T sA[2 * P * P];
+  __shared__ T sin_[C], su[C], sv[C];
+  const int cell = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < 2 * P * P; i += 256) sA[i] = A[i];
+  const int64_t prow = lv.row_off[l] + cell;
+  for (int m = tid; m < C; m += 256) sin_[m] = Lbuf[prow * cpad + m];
+  // interpolation reproduces constants, so the parent's mean passes to each
+  // child unchanged and only the deviations go through the L2L matrices
+  const T mean = MEAN ? Lbuf[prow * cpad + C] : T(0);
+  const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
+  for (int ch = c0; ch < c0 + nc; ++ch) {
+    const uint32_t b = lv.key[l + 1][ch] & 7u;
+    const T* Ax = sA + ((b >> 2) & 1) * P * P;
+    const T* Ay = sA + ((b >> 1) & 1) * P * P;
+    const T* Az = sA + (b & 1) * P * P;
+    __syncthreads();
+    // z: u[mx][my][z'] = sum_k Az[k][z'] in[mx][my][k]
+    for (int m = tid; m < C; m += 256) {
+      const int xy = m / P, zp = m % P;
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += Az[k * P + zp] * sin_[xy * P + k];
+      su[m] = s;
+    }
+    __syncthreads();
+    // y: v[mx][y'][z'] = sum_k Ay[k][y'] u[mx][k][z']
+    for (int m = tid; m < C; m += 256) {
+      const int x = m / (P * P), yp = (m / P) % P, z = m % P;
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += Ay[k * P + yp] * su[(x * P + k) * P + z];
+      sv[m] = s;
+    }
+    __syncthreads();
+    // x: L_C[x'][y'][z'] += sum_k Ax[k][x'] v[k][y'][z']
+    const int64_t crow = lv.row_off[l + 1] + ch;
+    for (int m = tid; m < C; m += 256) {
+      const int xp = m / (P * P), yz = m % (P * P);
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += Ax[k * P + xp] * sv[k * P * P + yz];
+      Lbuf[crow * cpad + m] += s;
+    }
+    if (MEAN && tid == 0) Lbuf[crow * cpad + C] += mean;
+  }
+}
+
+// ---------------------------------------------------------------- L2P + output
+
+template <int P, typename T, bool MIXED>
+__global__ void __launch_bounds__(128)
+k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const T* __restrict__ cheb,
+          int cpad, const T* __restrict__ L, int has_far, const double4* __restrict__ pos64,
+          const float4* __restrict__ pos32, const float4* __restrict__ near32,
+          const double4* __restrict__ near64, const int32_t* __restrict__ perm, double* __restrict__ phi,
+          double* __restrict__ F) {
+  constexpr int C = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sL = (T*)smem_raw;
+  __shared__ T sC[P * P];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < P * P; i += 128) sC[i] = cheb[i];
+  __syncthreads();
+  const int cell = blockIdx.x * 4 + warp;
+  if (cell >= nleaf) return;
+  T* myL = sL + warp * cpad;
+  if (has_far) {
+    const int64_t row = lv.row_off[leaf] + cell;
+    for (int m = lane; m <= C; m += 32) myL[m] = (MIXED || m < C) ? L[row * cpad + m] : T(0);
+  }
+  __syncwarp();
+  const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
+  double ctr[3], a;
+  cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  for (int r = first + lane; r < first + cnt; r += 32) {
+    double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    if (has_far) {
+      T xi[3];
+      if (MIXED) {
+        float4 pp = pos32[r];
+        xi[0] = T(2) * pp.x;
+        xi[1] = T(2) * pp.y;
+        xi[2] = T(2) * pp.z;
+      } else {
+        double4 pp = pos64[r];
+        xi[0] = (T)((pp.x - ctr[0]) / a);
+        xi[1] = (T)((pp.y - ctr[1]) / a);
+        xi[2] = (T)((pp.z - ctr[2]) / a);
+      }
+      T Sx[P], Sy[P], Sz[P], dSx[P], dSy[P], dSz[P];
+      interp_weights<P, T, true>(sC, xi[0], Sx, dSx);
+      interp_weights<P, T, true>(sC, xi[1], Sy, dSy);
+      interp_weights<P, T, true>(sC, xi[2], Sz, dSz);
+      T f = T(0), ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+      for (int mx = 0; mx < P; ++mx) {
+#pragma unroll
+        for (int my = 0; my < P; ++my) {
+          const T* Lr = myL + (mx * P + my) * P;
+          T sz = T(0), dz = T(0);
+#pragma unroll
+          for (int mz = 0; mz < P; ++mz) {
+            sz += Lr[mz] * Sz[mz];
+            dz += Lr[mz] * dSz[mz];
+          }
+          const T sxy = Sx[mx] * Sy[my];
+          f += sxy * sz;
+          ax += dSx[mx] * Sy[my] * sz;
+          ay += Sx[mx] * dSy[my] * sz;
+          az += sxy * dz;
+        }
+      }
+      pf = (double)f + (MIXED ? (double)myL[C] : 0.0);  // mixed: cell mean + deviations
+      gx = -(double)ax / a;
+      gy = -(double)ay / a;
+      gz = -(double)az / a;
+    }
+    double nphi, nx, ny, nz;
+    if (MIXED) {
+      float4 nr = near32[r];
+      nphi = nr.x;
+      nx = nr.y;
+      ny = nr.z;
+      nz = nr.w;
+    } else {
+      double4 nr = near64[r];
+      nphi = nr.x;
+      nx = nr.y;
+      ny = nr.z;
+      nz = nr.w;
+    }
+    const int64_t i = perm[r];
+    phi[i] = pf + nphi;
+    F[3 * i] = gx + nx;
+    F[3 * i + 1] = gy + ny;
+    F[3 * i + 2] = gz + nz;
+  }
+}
+
+// ---------------------------------------------------------------- M2L (SIMT)
+// One CTA computes 64 target rows x 64 coefficients of a tile's local
+// expansions: a GEMM whose K dimension runs over (active transfer vector t,
+// source coefficient n), the A operand gathered from the source cells'
+// multipoles and B = K_t^T.  SPLIT: operands are TF32 hi/lo pairs (used as
+// FP32 sums), the operator bank has row stride cpad.
+
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(256)
+k_m2l_simt(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
+           const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
+           const int16_t* __restrict__ cls_t, const T* __restrict__ Khi, const T* __restrict__ Klo,
+           int kstride, int C, int cpad, const T* __restrict__ Mhi, const T* __restrict__ Mlo,
+           T* __restrict__ Lout, const double* __restrict__ box) {
+  __shared__ T As[16][64];
+  __shared__ T Bs[16][64 + 1];
+  __shared__ int srow[64];
+  const int tile = blockIdx.x, half = blockIdx.y, col0 = blockIdx.z * 64;
+  const int ncol = SPLIT ? C + 1 : C;  // mixed: deviations + the cell mean (row C of the bank)
+  if (col0 >= ncol) return;
+  const Tile tl = tiles[tile];
+  if (half * 64 >= tl.count) return;
+  const int l = tl.level;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nact = tile_nact[tile];
+  const int64_t rbase = lv.row_off[l];
+  // Per transfer vector the products are summed in T; the running total over
+  // transfer vectors is compensated (Kahan) so that the long sum, whose terms
+  // largely cancel in the deviation columns, keeps FP32 precision.
+  T acc[4][4], tot[4][4], cmp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tot[i][j] = cmp[i][j] = T(0);
+  for (int a = 0; a < nact; ++a) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int k = tile_act[(int64_t)tile * FMM_NT_CLASS + a];
+    const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
+    __syncthreads();
+    if (tid < 64) srow[tid] = tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + half * 64 + tid];
+    const T* Kh = Khi + (int64_t)slot * kstride * kstride;
+    const T* Kl = SPLIT ? Klo + (int64_t)slot * kstride * kstride : nullptr;
+    for (int n0 = 0; n0 < C; n0 += 16) {
+      __syncthreads();
+      // A: 64 rows x 16 coefficients (16 consecutive threads read one row segment)
+#pragma unroll
+      for (int e = tid; e < 64 * 16; e += 256) {
+        const int r = e >> 4, kk = e & 15;
+        const int64_t off = (rbase + srow[r]) * cpad + n0 + kk;
+        T v = Mhi[off];
+        if (SPLIT) v += Mlo[off];
+        As[kk][r] = v;
+      }
+      // B: Bs[kk][c] = K_t[col0 + c][n0 + kk]
+#pragma unroll
+      for (int e = tid; e < 64 * 16; e += 256) {
+        const int cc = e >> 4, kk = e & 15;
+        const int m = col0 + cc, nn = n0 + kk;
+        T v = T(0);
+        if (m < ncol && nn < C) {
+          v = Kh[(int64_t)m * kstride + nn];
+          if (SPLIT) v += Kl[(int64_t)m * kstride + nn];
+        }
+        Bs[kk][cc] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T y = acc[i][j] - cmp[i][j];
+        const T s = tot[i][j] + y;
+        cmp[i][j] = (s - tot[i][j]) - y;
+        tot[i][j] = s;
+      }
+  }
+  const double inv_a = ldexp(1.0, l + 1) / box[3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = half * 64 + ty + 16 * i;
+    if (r >= tl.count) continue;
+    const int cell = lv.cls[l][tl.first + r];
+    const int64_t row = rbase + cell;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = col0 + tx + 16 * j;
+      if (m < ncol) Lout[row * cpad + m] = (T)((double)tot[i][j] * inv_a);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- readout
+
+// b: second half of a split pair; add_mean: add the row's mean slot (column C)
+template <typename T>
+__global__ void k_rows_to_f64(int64_t nrows, int64_t row0, int C, int cpad, const T* __restrict__ a,
+                              const T* __restrict__ b, int add_mean, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * C) return;
+  int64_t r = i / C;
+  int m = (int)(i - r * C);
+  double v = (double)a[(row0 + r) * cpad + m];
+  if (b) v += (double)b[(row0 + r) * cpad + m];
+  if (add_mean) v += (double)a[(row0 + r) * cpad + C];
+  out[i] = v;
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <int P>
+fmm_status upward_p(Ctx* c, cudaStream_t s) {
+  const int Lf = c->leaf;
+  if (c->precision == FMM_MIXED) {
+    k_p2m<P, float, true><<<c->lv.ncell[Lf], 128, 0, s>>>(c->lv, Lf, c->box, c->cheb32, c->cpad, c->pos64,
+                                                          c->pos32, c->Mhi, c->Mlo);
+    for (int l = Lf - 1; l >= 2; --l)
+      k_m2m<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo, c->Mhi,
+                                                           c->Mlo);
+  } else {
+    k_p2m<P, double, false><<<c->lv.ncell[Lf], 128, 0, s>>>(c->lv, Lf, c->box, c->cheb64, c->cpad, c->pos64,
+                                                            c->pos32, c->M64, nullptr);
+    for (int l = Lf - 1; l >= 2; --l)
+      k_m2m<P, double, false><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m64, c->cpad, c->M64, nullptr,
+                                                             c->M64, nullptr);
+  }
+  return cuda_err(c, cudaGetLastError(), "upward pass launch");
+}
+
+template <int P>
+fmm_status l2l_p(Ctx* c, cudaStream_t s) {
+  for (int l = 2; l <= c->leaf - 1; ++l) {
+    if (c->precision == FMM_MIXED)
+      k_l2l<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->L32);
+    else
+      k_l2l<P, double, false><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m64, c->cpad, c->L64);
+  }
+  return cuda_err(c, cudaGetLastError(), "L2L launch");
+}
+
+template <int P>
+fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
+  const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
+  const int has_far = Lf >= 2;
+  if (nleaf == 0) return FMM_OK;
+  if (c->precision == FMM_MIXED)
+    k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
+        c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
+        c->perm, phi, F);
+  else
+    k_l2p_out<P, double, false><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(double), s>>>(
+        c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32, c->near64,
+        c->perm, phi, F);
+  return cuda_err(c, cudaGetLastError(), "L2P launch");
+}
+
+}  // namespace
+
+fmm_status launch_upward(Ctx* c, cudaStream_t s) {
+  if (c->leaf < 2 || c->n == 0) return FMM_OK;
+#define CALL(P) upward_p<P>(c, s)
+  switch (c->order) {
+    case 2: return CALL(2);
+    case 3: return CALL(3);
+    case 4: return CALL(4);
+    case 5: return CALL(5);
+    case 6: return CALL(6);
+    case 7: return CALL(7);
+    case 8: return CALL(8);
+    case 9: return CALL(9);
+    case 10: return CALL(10);
+  }
+#undef CALL
+  return FMM_ERR_ARG;
+}
+
+fmm_status launch_l2l(Ctx* c, cudaStream_t s) {
+  if (c->leaf < 3 || c->n == 0) return FMM_OK;
+#define CALL(P) l2l_p<P>(c, s)
+  switch (c->order) {
+    case 2: return CALL(2);
+    case 3: return CALL(3);
+    case 4: return CALL(4);
+    case 5: return CALL(5);
+    case 6: return CALL(6);
+    case 7: return CALL(7);
+    case 8: return CALL(8);
+    case 9: return CALL(9);
+    case 10: return CALL(10);
+  }
+#undef CALL
+  return FMM_ERR_ARG;
+}
+
+fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F) {
+  if (c->n == 0) return FMM_OK;
+#define CALL(P) l2p_p<P>(c, s, phi, F)
+  switch (c->order) {
+    case 2: return CALL(2);
+    case 3: return CALL(3);
+    case 4: return CALL(4);
+    case 5: return CALL(5);
+    case 6: return CALL(6);
+    case 7: return CALL(7);
+    case 8: return CALL(8);
+    case 9: return CALL(9);
+    case 10: return CALL(10);
+  }
+#undef CALL
+  return FMM_ERR_ARG;
+}
+
+fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
+  if (ntiles <= 0) return FMM_OK;
+  dim3 grid(ntiles, 2, ceil_div(c->ncoef + 1, 64));
+  const Tile* tiles = c->tiles + first_tile;
+  const int32_t* src = c->tile_src + (int64_t)first_tile * FMM_NT_CLASS * FMM_TILE;
+  const int16_t* act = c->tile_act + (int64_t)first_tile * FMM_NT_CLASS;
+  const int32_t* nact = c->tile_nact + first_tile;
+  if (c->precision == FMM_MIXED)
+    k_m2l_simt<float, true><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->Khi, c->Klo, c->cpad,
+                                                 c->ncoef, c->cpad, c->Mhi, c->Mlo, c->L32, c->box);
+  else
+    k_m2l_simt<double, false><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->K64, nullptr,
+                                                   c->ncoef, c->ncoef, c->cpad, c->M64, nullptr, c->L64,
+                                                   c->box);
+  return cuda_err(c, cudaGetLastError(), "M2L launch");
+}
+
+fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out) {
+  const int64_t nrows = c->lv.ncell[level];
+  if (nrows == 0) return FMM_OK;
+  const int64_t row0 = c->lv.row_off[level];
+  const int64_t total = nrows * c->ncoef;
+  const int grid = ceil_div(total, 256);
+  if (c->precision == FMM_MIXED) {
+    if (which == 0)
+      k_rows_to_f64<float><<<grid, 256, 0, c->stream>>>(nrows, row0, c->ncoef, c->cpad, c->Mhi, c->Mlo, 0, out);
+    else
+      k_rows_to_f64<float><<<grid, 256, 0, c->stream>>>(nrows, row0, c->ncoef, c->cpad, c->L32, nullptr, 1, out);
+  } else {
+    k_rows_to_f64<double><<<grid, 256, 0, c->stream>>>(nrows, row0, c->ncoef, c->cpad,
+                                                       which == 0 ? c->M64 : c->L64, nullptr, 0, out);
+  }
+  return cuda_err(c, cudaGetLastError(), "expansion readout");
+}
+
+}  // namespace fmm

@@ -1,0 +1,79 @@
+// m2l.cu -- M2L dispatch (Sec. 2.1.2): the FP64 path runs the SIMT kernel in
+// FP64; the mixed path runs the SIMT kernel on FP32 sums of the TF32 pairs.
+#include "common.cuh"
+
+namespace fmm {
+
+int m2l_kind(const Ctx* c) { return c->precision == FMM_FP64 ? 0 : 1; }
+
+fmm_status launch_m2l_level(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
+  if (ntiles <= 0 || c->n == 0) return FMM_OK;
+  return launch_m2l_simt(c, s, first_tile, ntiles);
+}
+
+namespace {
+
+__global__ void __launch_bounds__(FMM_TILE)
+k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
+                  const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
+                  unsigned long long* __restrict__ out) {
+  const Tile tl = tiles[blockIdx.x];
+  const int row = threadIdx.x, zero = lv.ncell[tl.level];
+  const int nact = tile_nact[blockIdx.x];
+  unsigned long long cnt = 0;
+  for (int a = 0; a < nact; ++a) {
+    const int k = tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a];
+    const int s = tile_src[((int64_t)blockIdx.x * FMM_NT_CLASS + k) * FMM_TILE + row];
+    cnt += (row < tl.count && s != zero);
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((row & 31) == 0) atomicAdd(&out[1 + tl.level], cnt);
+}
+
+__global__ void k_count_p2p_pairs(LevelPtrs lv, int leaf, int nleaf, unsigned long long* __restrict__ out) {
+  const int T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= nleaf) return;
+  int ix, iy, iz;
+  demorton3(lv.key[leaf][T], ix, iy, iz);
+  const int top = (1 << leaf) - 1;
+  unsigned long long src = 0;
+  for (int k = 0; k < 27; ++k) {
+    const int sx = ix + k / 9 - 1, sy = iy + (k / 3) % 3 - 1, sz = iz + k % 3 - 1;
+    if (sx < 0 || sy < 0 || sz < 0 || sx > top || sy > top || sz > top) continue;
+    const int g = lv.grid[leaf][morton3(sx, sy, sz)];
+    if (g >= 0) src += lv.count[leaf][g];
+  }
+  const unsigned long long nt = lv.count[leaf][T];
+  atomicAdd(&out[0], nt * src - nt);
+}
+
+}  // namespace
+
+fmm_status work_counts(Ctx* c, int64_t* out) {
+  for (int k = 0; k < 12; ++k) out[k] = 0;
+  if (c->n == 0) return FMM_OK;
+  unsigned long long* d = (unsigned long long*)c->scratch;
+  FMM_CUDA(c, cudaMemsetAsync(d, 0, 12 * sizeof(unsigned long long), c->stream));
+  const int nleaf = c->lv.ncell[c->leaf];
+  k_count_p2p_pairs<<<ceil_div(nleaf, 128), 128, 0, c->stream>>>(c->lv, c->leaf, nleaf, d);
+  if (c->ntiles > 0)
+    k_count_m2l_pairs<<<c->ntiles, FMM_TILE, 0, c->stream>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact,
+                                                             c->lv, d);
+  FMM_CUDA(c, cudaGetLastError());
+  FMM_CUDA(c, cudaMemcpyAsync(out, d, 12 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FMM_OK;
+}
+
+int64_t count_launches_eval(const Ctx* c) {
+  const int Lf = c->leaf;
+  int64_t k = 2;  // P2P, L2P/output
+  if (Lf >= 2 && c->n > 0) {
+    k += 1 + (Lf - 2);                                      // P2M, M2M
+    k += (c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles);  // M2L
+    k += (Lf - 2);                                          // L2L
+  }
+  return k;
+}
+
+}  // namespace fmm

@@ -1,0 +1,697 @@
+// tree.cu -- octree construction on the device (Sec. 3.2 hierarchical
+// subdivision into cells; Sec. 4.2 Morton ordering of cells).
+//
+// Steps: bounding cube (exact FP64 min/max) -> leaf-level Morton keys
+// (IEEE FP64 quantisation, no contraction) -> stable LSD radix sort of
+// (key, input index) -> gather into Morton order -> per level, the unique
+// cell keys with particle / child ranges -> dense key -> cell grids ->
+// cells grouped by child class -> M2L tiles and their source lists.
+// Every step is integer or exact, so the tree is bit-identical to any other
+// implementation of the same rules.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int BB_THREADS = 256;
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int U_THREADS = 256;
+constexpr int U_ITEMS = 8;
+constexpr int U_CHUNK = U_THREADS * U_ITEMS;
+constexpr int CNT_BAD = 127;  // counters[] slot of the non-finite-input flag
+constexpr int CNT_CLS = 16;   // counters[16 + 8 l + c] = cells of class c at level l
+
+__device__ inline double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ inline double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Per-block min/max of each coordinate; raises the flag on non-finite input.
+__global__ void __launch_bounds__(BB_THREADS)
+k_bbox_partial(int64_t n, const double* __restrict__ xyz, const double* __restrict__ q,
+               double* __restrict__ part, int32_t* __restrict__ counters) {
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int d = 0; d < 3; ++d) {
+      double v = xyz[3 * i + d];
+      bad |= !isfinite(v);
+      mn[d] = fmin(mn[d], v);
+      mx[d] = fmax(mx[d], v);
+    }
+    bad |= !isfinite(q[i]);
+  }
+  __shared__ double s[2][3][BB_THREADS / 32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = 0; d < 3; ++d) {
+    double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    if (lane == 0) {
+      s[0][d][w] = a;
+      s[1][d][w] = b;
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 3; ++d) {
+      double a = s[0][d][0], b = s[1][d][0];
+      for (int k = 1; k < BB_THREADS / 32; ++k) {
+        a = fmin(a, s[0][d][k]);
+        b = fmax(b, s[1][d][k]);
+      }
+      part[6 * blockIdx.x + d] = a;
+      part[6 * blockIdx.x + 3 + d] = b;
+    }
+    if (bad) atomicOr(&counters[CNT_BAD], 1);
+  }
+}
+
+// Root cube: corner = minimum per axis, side = largest extent (1 if zero).
+__global__ void k_bbox_final(int nblocks, const double* __restrict__ part, double* __restrict__ box) {
+  if (threadIdx.x != 0) return;
+  double mn[3], mx[3];
+  for (int d = 0; d < 3; ++d) {
+    mn[d] = part[d];
+    mx[d] = part[3 + d];
+  }
+  for (int b = 1; b < nblocks; ++b)
+    for (int d = 0; d < 3; ++d) {
+      mn[d] = fmin(mn[d], part[6 * b + d]);
+      mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
+    }
+  double w = 0.0;
+  for (int d = 0; d < 3; ++d) w = fmax(w, __dsub_rn(mx[d], mn[d]));
+  for (int d = 0; d < 3; ++d) box[d] = mn[d];
+  box[3] = (w > 0.0) ? w : 1.0;
+}
+
+// Leaf-level key: per axis floor(((x - lo) / W) * 2^leaf) clamped to the cube.
+// Multiplying by 2^leaf is exact; the subtraction and the division are the
+// IEEE round-to-nearest operations, written out so nothing is contracted.
+__global__ void k_morton(int64_t n, const double* __restrict__ xyz, const double* __restrict__ box,
+                         int leaf, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double W = box[3];
+  const double scale = (double)(1u << leaf);
+  const int top = (1 << leaf) - 1;
+  uint32_t c[3];
+  for (int d = 0; d < 3; ++d) {
+    double t = __ddiv_rn(__dsub_rn(xyz[3 * i + d], box[d]), W);
+    double u = floor(__dmul_rn(t, scale));
+    int v = (u >= 0.0) ? (u <= (double)top ? (int)u : top) : 0;
+    c[d] = (uint32_t)v;
+  }
+  key[i] = morton3(c[0], c[1], c[2]);
+  idx[i] = (uint32_t)i;
+}
+
+// ---- stable LSD radix sort (8-bit digits) -------------------------------------
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_radix_hist(int64_t n, const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist,
+             int ntiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
+    int64_t g = base + k;
+    if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `count` words in one block; the total goes to *total.
+template <typename W>
+__global__ void __launch_bounds__(1024) k_scan1(W* __restrict__ data, int64_t count, W* total) {
+  __shared__ W part[1024];
+  const int t = threadIdx.x;
+  int64_t per = (count + 1023) / 1024;
+  int64_t b = t * per, e = b + per < count ? b + per : count;
+  W s = 0;
+  for (int64_t i = b; i < e; ++i) s += data[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    W v = (t >= o) ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  W run = part[t] - s;
+  for (int64_t i = b; i < e; ++i) {
+    W v = data[i];
+    data[i] = run;
+    run += v;
+  }
+  if (t == 1023 && total) *total = part[1023];
+}
+
+// Scatter of one digit pass.  The tile is walked in order, 256 keys at a time;
+// within a round a key's rank among equal digits is (earlier rounds) +
+// (earlier warps of this round) + (lower lanes of its warp), so equal keys
+// keep their input order.
+__global__ void __launch_bounds__(RS_THREADS)
+k_radix_scatter(int64_t n, const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+                const uint32_t* __restrict__ offs, int ntiles) {
+  __shared__ uint32_t base_off[256];
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  base_off[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+  run[tid] = 0;
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    for (int i = tid; i < (RS_THREADS / 32) * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    int64_t g = tile0 + (int64_t)r * RS_THREADS + tid;
+    bool valid = g < n;
+    uint32_t k = valid ? kin[g] : 0u, v = valid ? vin[g] : 0u;
+    uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+    __syncthreads();
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int wrank = __popc(peers & lt);
+    if (valid && wrank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = run[tid];
+      for (int w = 0; w < RS_THREADS / 32; ++w) {
+        uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = acc;
+        acc += c;
+      }
+      run[tid] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = base_off[d] + wcnt[warp][d] + (uint32_t)wrank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();  // the next round clears wcnt, which this round's scatter still reads
+  }
+}
+
+// Morton-ordered particle copies: FP64 (x, y, z, q) and FP32 leaf-local
+// coordinates ((x - c) / w, ..., q) computed in FP64 and rounded once, plus
+// the rounding residual of each coordinate.
+__global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
+                         const double* __restrict__ xyz, const double* __restrict__ q,
+                         const double* __restrict__ box, int leaf, int32_t* __restrict__ perm,
+                         double4* __restrict__ pos64, float4* __restrict__ pos32, float4* __restrict__ pos32lo) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  uint32_t i = sidx[r];
+  perm[r] = (int32_t)i;
+  double x = xyz[3 * (int64_t)i], y = xyz[3 * (int64_t)i + 1], z = xyz[3 * (int64_t)i + 2];
+  double qq = q[i];
+  pos64[r] = make_double4(x, y, z, qq);
+  int ix, iy, iz;
+  demorton3(skey[r], ix, iy, iz);
+  double w = ldexp(box[3], -leaf);
+  double cx = box[0] + ((double)ix + 0.5) * w;
+  double cy = box[1] + ((double)iy + 0.5) * w;
+  double cz = box[2] + ((double)iz + 0.5) * w;
+  const double vx = (x - cx) / w, vy = (y - cy) / w, vz = (z - cz) / w;
+  const float hx = (float)vx, hy = (float)vy, hz = (float)vz;
+  pos32[r] = make_float4(hx, hy, hz, (float)qq);
+  pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
+}
+
+// ---- unique prefixes of a sorted key list --------------------------------------
+
+__device__ inline int64_t load_n(const int32_t* p, int64_t s) { return p ? (int64_t)*p : s; }
+
+__device__ inline int block_sum(int v) {
+  __shared__ int ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  int t = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws[k];
+  return t;
+}
+
+__global__ void __launch_bounds__(U_THREADS)
+k_unique_count(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ in, int shift,
+               int32_t* __restrict__ bsum) {
+  const int64_t n = load_n(n_ptr, n_static);
+  const int64_t base = (int64_t)blockIdx.x * U_CHUNK;
+  int cnt = 0;
+  for (int k = threadIdx.x; k < U_CHUNK; k += U_THREADS) {
+    int64_t i = base + k;
+    if (i < n) cnt += (i == 0) || ((in[i] >> shift) != (in[i - 1] >> shift));
+  }
+  cnt = block_sum(cnt);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = cnt;
+}
+
+// Writes each new prefix (key >> shift) with the index of its first element;
+// parent[i] (optional) receives the output index of element i's prefix.
+__global__ void __launch_bounds__(U_THREADS)
+k_unique_write(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ in, int shift,
+               const int32_t* __restrict__ boff, uint32_t* __restrict__ out_key,
+               int32_t* __restrict__ out_first, int32_t* __restrict__ parent) {
+  const int64_t n = load_n(n_ptr, n_static);
+  const int64_t base = (int64_t)blockIdx.x * U_CHUNK + (int64_t)threadIdx.x * U_ITEMS;
+  int flags = 0, cnt = 0;
+  for (int k = 0; k < U_ITEMS; ++k) {
+    int64_t i = base + k;
+    int h = (i < n) && ((i == 0) || ((in[i] >> shift) != (in[i - 1] >> shift)));
+    flags |= h << k;
+    cnt += h;
+  }
+  // block-wide exclusive scan of cnt
+  __shared__ int ws[U_THREADS / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) ws[w] = incl;
+  __syncthreads();
+  int woff = 0;
+  for (int k = 0; k < w; ++k) woff += ws[k];
+  int pos = boff[blockIdx.x] + woff + incl - cnt;
+  for (int k = 0; k < U_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i >= n) break;
+    if ((flags >> k) & 1) {
+      out_key[pos] = in[i] >> shift;
+      out_first[pos] = (int32_t)i;
+      ++pos;
+    }
+    if (parent) parent[i] = pos - 1;
+  }
+}
+
+__global__ void k_counts(const int32_t* __restrict__ nout_ptr, const int32_t* nin_ptr, int64_t nin_static,
+                         const int32_t* __restrict__ first, int32_t* __restrict__ count) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t nout = *nout_ptr, nin = load_n(nin_ptr, nin_static);
+  if (j >= nout) return;
+  int64_t e = (j + 1 < nout) ? first[j + 1] : nin;
+  count[j] = (int32_t)(e - first[j]);
+}
+
+__global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
+                           int32_t* __restrict__ grid, int clear) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= load_n(n_ptr, n_static)) return;
+  grid[keys[i]] = clear ? -1 : (int32_t)i;
+}
+
+struct ClassArgs {
+  uint32_t* key[FMM_MAX_LEVELS];
+  int32_t* out[FMM_MAX_LEVELS];
+};
+
+// Groups the cells of levels lmin.. by child class (key & 7), keeping Morton
+// order inside each class; one block per level.
+__global__ void __launch_bounds__(1024)
+k_class_partition(int lmin, int32_t* __restrict__ counters, ClassArgs a) {
+  const int l = lmin + blockIdx.x;
+  const int n = counters[l];
+  const uint32_t* key = a.key[l];
+  const int tid = threadIdx.x;
+  const int per = (n + 1023) / 1024;
+  const int b = min(n, tid * per), e = min(n, b + per);
+  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = b; i < e; ++i) cnt[key[i] & 7]++;
+  __shared__ int s[8][1024];
+  __shared__ int tot[8];
+  __shared__ int cbase[9];
+  for (int c = 0; c < 8; ++c) s[c][tid] = cnt[c];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp < 8) {
+    int* row = s[warp];
+    int sum = 0;
+    for (int k = 0; k < 32; ++k) sum += row[lane * 32 + k];
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - sum;
+    for (int k = 0; k < 32; ++k) {
+      int v = row[lane * 32 + k];
+      row[lane * 32 + k] = run;
+      run += v;
+    }
+    if (lane == 31) tot[warp] = incl;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    cbase[0] = 0;
+    for (int c = 0; c < 8; ++c) {
+      cbase[c + 1] = cbase[c] + tot[c];
+      counters[CNT_CLS + 8 * l + c] = tot[c];
+    }
+  }
+  __syncthreads();
+  int pos[8];
+  for (int c = 0; c < 8; ++c) pos[c] = cbase[c] + s[c][tid];
+  for (int i = b; i < e; ++i) a.out[l][pos[key[i] & 7]++] = i;
+}
+
+// Per M2L tile: for each of the class's 189 transfer vectors the source cell
+// of every target row (the level's zero row when the source is absent or
+// outside the cube) and the list of transfer vectors with at least one
+// source.  One block of 128 threads (one per target row) per tile.
+__global__ void __launch_bounds__(FMM_TILE)
+k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ cls_t,
+            const int8_t* __restrict__ tvec, int32_t* __restrict__ tile_src,
+            int16_t* __restrict__ tile_act, int32_t* __restrict__ tile_nact) {
+  const Tile tl = tiles[blockIdx.x];
+  const int l = tl.level, row = threadIdx.x;
+  const bool valid = row < tl.count;
+  const int zero_row = lv.ncell[l];
+  int ix = 0, iy = 0, iz = 0;
+  if (valid) {
+    int cell = lv.cls[l][tl.first + row];
+    demorton3(lv.key[l][cell], ix, iy, iz);
+  }
+  const int top = (1 << l) - 1;
+  __shared__ int16_t act[FMM_NT_CLASS];
+  __shared__ int nact;
+  if (row == 0) nact = 0;
+  __syncthreads();
+  for (int k = 0; k < FMM_NT_CLASS; ++k) {
+    int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
+    int sx = ix + tvec[3 * slot], sy = iy + tvec[3 * slot + 1], sz = iz + tvec[3 * slot + 2];
+    int src = zero_row;
+    if (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
+      int g = lv.grid[l][morton3(sx, sy, sz)];
+      if (g >= 0) src = g;
+    }
+    tile_src[((int64_t)blockIdx.x * FMM_NT_CLASS + k) * FMM_TILE + row] = src;
+    if (__syncthreads_or(src != zero_row) && row == 0) act[nact++] = (int16_t)k;
+  }
+  __syncthreads();
+  for (int k = row; k < nact; k += FMM_TILE) tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + k] = act[k];
+  if (row == 0) tile_nact[blockIdx.x] = nact;
+}
+
+__global__ void k_zero_rows(int nrows, const int64_t* __restrict__ rows, int cpad, float* a, float* b,
+                            float* c, double* d, double* e) {
+  int r = blockIdx.x;
+  if (r >= nrows) return;
+  int64_t o = rows[r] * cpad;
+  for (int k = threadIdx.x; k < cpad; k += blockDim.x) {
+    if (a) a[o + k] = 0.f;
+    if (b) b[o + k] = 0.f;
+    if (c) c[o + k] = 0.f;
+    if (d) d[o + k] = 0.0;
+    if (e) e[o + k] = 0.0;
+  }
+}
+
+int64_t pow8(int l) { return (int64_t)1 << (3 * l); }
+
+fmm_status ensure_particles(Ctx* c, int64_t n) {
+  if (n <= c->ncap) return FMM_OK;
+  int64_t cap = n + n / 8 + 1024;
+  void* p;
+#define REALLOC(field, T, count)                                  \
+  dfree(c, c->field, sizeof(T) * (size_t)c->ncap * (count));      \
+  c->field = nullptr;                                             \
+  FMM_TRY(dalloc(c, &p, sizeof(T) * (size_t)cap * (count)));      \
+  c->field = (decltype(c->field))p;
+  REALLOC(key_a, uint32_t, 1)
+  REALLOC(key_b, uint32_t, 1)
+  REALLOC(idx_a, uint32_t, 1)
+  REALLOC(idx_b, uint32_t, 1)
+  REALLOC(perm, int32_t, 1)
+  REALLOC(pos64, double4, 1)
+  REALLOC(pos32, float4, 1)
+  REALLOC(pos32lo, float4, 1)
+  REALLOC(near32, float4, 1)
+  REALLOC(near64, double4, 1)
+#undef REALLOC
+  c->ncap = cap;
+  int64_t words = 65536 + cap / 8 + 4096;
+  if (words > c->scratch_cap) {
+    dfree(c, c->scratch, sizeof(uint32_t) * (size_t)c->scratch_cap);
+    c->scratch = nullptr;
+    FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * (size_t)words));
+    c->scratch = (uint32_t*)p;
+    c->scratch_cap = words;
+  }
+  return FMM_OK;
+}
+
+fmm_status ensure_level(Ctx* c, int l, int64_t cells) {
+  if (cells <= c->lcap[l]) return FMM_OK;
+  int64_t cap = cells + cells / 8 + 64;
+  int64_t old = c->lcap[l];
+  void* p;
+  dfree(c, c->lv.key[l], 4 * (size_t)old);
+  dfree(c, c->lv.first[l], 4 * (size_t)old);
+  dfree(c, c->lv.count[l], 4 * (size_t)old);
+  dfree(c, c->lv.parent[l], 4 * (size_t)old);
+  dfree(c, c->lv.cls[l], 4 * (size_t)old);
+  c->lv.key[l] = nullptr;
+  c->lv.first[l] = c->lv.count[l] = c->lv.parent[l] = c->lv.cls[l] = nullptr;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->lv.key[l] = (uint32_t*)p;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->lv.first[l] = (int32_t*)p;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->lv.count[l] = (int32_t*)p;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->lv.parent[l] = (int32_t*)p;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->lv.cls[l] = (int32_t*)p;
+  c->lcap[l] = cap;
+  return FMM_OK;
+}
+
+// unique prefixes of in[0..n) (n from n_ptr on the device, bounded by n_ub)
+fmm_status unique_level(Ctx* c, cudaStream_t s, const int32_t* n_ptr, int64_t n_ub, const uint32_t* in,
+                        int shift, int lout, int32_t* parent) {
+  if (n_ub <= 0) return FMM_OK;
+  int nb = ceil_div(n_ub, U_CHUNK);
+  int32_t* bsum = (int32_t*)c->scratch;
+  k_unique_count<<<nb, U_THREADS, 0, s>>>(n_ptr, n_ub, in, shift, bsum);
+  k_scan1<int32_t><<<1, 1024, 0, s>>>(bsum, nb, c->counters + lout);
+  k_unique_write<<<nb, U_THREADS, 0, s>>>(n_ptr, n_ub, in, shift, bsum, c->lv.key[lout], c->lv.first[lout],
+                                          parent);
+  int64_t out_ub = n_ub < pow8(lout) ? n_ub : pow8(lout);
+  k_counts<<<ceil_div(out_ub, 256), 256, 0, s>>>(c->counters + lout, n_ptr, n_ub, c->lv.first[lout],
+                                                 c->lv.count[lout]);
+  c->launches_set += 4;
+  return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
+  cudaStream_t s = c->stream;
+  const int Lf = c->leaf;
+  c->launches_set = 0;
+  c->loaded = false;
+  FMM_TRY(ensure_particles(c, n > 0 ? n : 1));
+
+  // forget the previous tree in the dense grids
+  if (c->have_prev) {
+    for (int l = 0; l <= Lf; ++l)
+      if (c->prev_ncell[l] > 0) {
+        k_grid_set<<<ceil_div(c->prev_ncell[l], 256), 256, 0, s>>>(nullptr, c->prev_ncell[l], c->lv.key[l],
+                                                                   c->lv.grid[l], 1);
+        c->launches_set++;
+      }
+    c->have_prev = false;
+  }
+  FMM_CUDA(c, cudaMemsetAsync(c->counters, 0, 128 * sizeof(int32_t), s));
+
+  // per-level capacities from upper bounds
+  int64_t ub[FMM_MAX_LEVELS];
+  for (int l = Lf; l >= 0; --l) {
+    int64_t b = (l == Lf) ? n : ub[l + 1];
+    ub[l] = b < pow8(l) ? b : pow8(l);
+    FMM_TRY(ensure_level(c, l, ub[l] > 0 ? ub[l] : 1));
+  }
+
+  if (n > 0) {
+    // bounding cube
+    int nbb = ceil_div(n, BB_THREADS * 8);
+    if (nbb > 1184) nbb = 1184;
+    double* part = (double*)c->scratch;
+    k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, q, part, c->counters);
+    k_bbox_final<<<1, 32, 0, s>>>(nbb, part, c->box);
+    // keys
+    k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, c->box, Lf, c->key_a, c->idx_a);
+    c->launches_set += 3;
+    // sort
+    uint32_t *ka = c->key_a, *kb = c->key_b, *va = c->idx_a, *vb = c->idx_b;
+    int bits = 3 * Lf;
+    int ntiles = ceil_div(n, RS_TILE);
+    uint32_t* hist = c->scratch;
+    for (int sh = 0; sh < bits; sh += 8) {
+      k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(n, ka, sh, hist, ntiles);
+      k_scan1<uint32_t><<<1, 1024, 0, s>>>(hist, (int64_t)256 * ntiles, nullptr);
+      k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, kb, vb, sh, hist, ntiles);
+      c->launches_set += 3;
+      uint32_t* t = ka;
+      ka = kb;
+      kb = t;
+      t = va;
+      va = vb;
+      vb = t;
+    }
+    c->skey = ka;
+    k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, Lf, c->perm, c->pos64, c->pos32,
+                                              c->pos32lo);
+    c->launches_set++;
+    // levels
+    FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, nullptr));
+    for (int l = Lf - 1; l >= 0; --l)
+      FMM_TRY(unique_level(c, s, c->counters + l + 1, ub[l + 1], c->lv.key[l + 1], 3, l, c->lv.parent[l + 1]));
+    for (int l = 0; l <= Lf; ++l) {
+      k_grid_set<<<ceil_div(ub[l], 256), 256, 0, s>>>(c->counters + l, ub[l], c->lv.key[l], c->lv.grid[l], 0);
+      c->launches_set++;
+    }
+    if (Lf >= 2) {
+      ClassArgs ca;
+      for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
+        ca.key[l] = c->lv.key[l];
+        ca.out[l] = c->lv.cls[l];
+      }
+      k_class_partition<<<Lf - 1, 1024, 0, s>>>(2, c->counters, ca);
+      c->launches_set++;
+    }
+    FMM_CUDA(c, cudaGetLastError());
+  }
+
+  FMM_CUDA(c, cudaMemcpyAsync(c->counters_h, c->counters, 128 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(c, cudaMemcpyAsync(c->box_h, c->box, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(c, cudaStreamSynchronize(s));
+  if (c->counters_h[CNT_BAD]) {
+    for (int l = 0; l <= Lf; ++l) c->prev_ncell[l] = n > 0 ? c->counters_h[l] : 0;
+    c->have_prev = n > 0;
+    return set_err(c, FMM_ERR_ARG, "fmm_set_particles: non-finite coordinate or charge");
+  }
+  c->n = n;
+  if (n > 0) {
+    for (int d = 0; d < 4; ++d) c->box_host[d] = c->box_h[d];
+  } else {
+    c->box_host[0] = c->box_host[1] = c->box_host[2] = 0.0;
+    c->box_host[3] = 1.0;
+  }
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) c->lv.ncell[l] = (l <= Lf && n > 0) ? c->counters_h[l] : 0;
+  for (int l = 0; l <= Lf; ++l) c->prev_ncell[l] = c->lv.ncell[l];
+  c->have_prev = n > 0;
+  for (int l = 0; l <= Lf; ++l) {
+    c->cls_off[l][0] = 0;
+    for (int k = 0; k < 8; ++k)
+      c->cls_off[l][k + 1] = c->cls_off[l][k] + ((l >= 2) ? c->counters_h[CNT_CLS + 8 * l + k] : 0);
+  }
+
+  // expansion rows: levels 2..leaf, each followed by one zero row
+  int64_t rows = 0;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) c->lv.row_off[l] = 0;
+  for (int l = 2; l <= Lf; ++l) {
+    c->lv.row_off[l] = rows;
+    rows += c->lv.ncell[l] + 1;
+  }
+  c->rows = rows;
+  if (rows > c->rows_cap) {
+    int64_t cap = rows + rows / 8 + 16;
+    size_t cp = (size_t)c->cpad;
+    dfree(c, c->Mhi, 4 * cp * c->rows_cap);
+    dfree(c, c->Mlo, 4 * cp * c->rows_cap);
+    dfree(c, c->L32, 4 * cp * c->rows_cap);
+    dfree(c, c->M64, 8 * cp * c->rows_cap);
+    dfree(c, c->L64, 8 * cp * c->rows_cap);
+    c->Mhi = c->Mlo = c->L32 = nullptr;
+    c->M64 = c->L64 = nullptr;
+    c->rows_cap = 0;
+    void* p;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->Mhi = (float*)p;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->Mlo = (float*)p;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->L32 = (float*)p;
+    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
+    c->M64 = (double*)p;
+    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
+    c->L64 = (double*)p;
+    FMM_CUDA(c, cudaMemsetAsync(c->Mhi, 0, 4 * cp * cap, s));
+    FMM_CUDA(c, cudaMemsetAsync(c->Mlo, 0, 4 * cp * cap, s));
+    FMM_CUDA(c, cudaMemsetAsync(c->L32, 0, 4 * cp * cap, s));
+    FMM_CUDA(c, cudaMemsetAsync(c->M64, 0, 8 * cp * cap, s));
+    FMM_CUDA(c, cudaMemsetAsync(c->L64, 0, 8 * cp * cap, s));
+    c->rows_cap = cap;
+  }
+
+  // M2L tiles, leaf level first (largest first for the combined launch)
+  std::vector<Tile> tiles;
+  c->leaf_tiles = 0;
+  for (int l = Lf; l >= 2; --l)
+    for (int k = 0; k < 8; ++k) {
+      int b = c->cls_off[l][k], e = c->cls_off[l][k + 1];
+      for (int f = b; f < e; f += FMM_TILE) tiles.push_back(Tile{l, k, f, (e - f) < FMM_TILE ? e - f : FMM_TILE});
+    }
+  c->ntiles = (int)tiles.size();
+  for (const Tile& tl : tiles) c->leaf_tiles += tl.level == Lf;
+  if (c->ntiles > c->tiles_cap) {
+    int cap = c->ntiles + c->ntiles / 8 + 16;
+    dfree(c, c->tiles, sizeof(Tile) * (size_t)c->tiles_cap);
+    dfree(c, c->tile_src, sizeof(int32_t) * (size_t)c->tiles_cap * FMM_NT_CLASS * FMM_TILE);
+    dfree(c, c->tile_act, sizeof(int16_t) * (size_t)c->tiles_cap * FMM_NT_CLASS);
+    dfree(c, c->tile_nact, sizeof(int32_t) * (size_t)c->tiles_cap);
+    c->tiles = nullptr;
+    c->tile_src = nullptr;
+    c->tile_act = nullptr;
+    c->tile_nact = nullptr;
+    c->tiles_cap = 0;
+    void* p;
+    FMM_TRY(dalloc(c, &p, sizeof(Tile) * (size_t)cap));
+    c->tiles = (Tile*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int32_t) * (size_t)cap * FMM_NT_CLASS * FMM_TILE));
+    c->tile_src = (int32_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int16_t) * (size_t)cap * FMM_NT_CLASS));
+    c->tile_act = (int16_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int32_t) * (size_t)cap));
+    c->tile_nact = (int32_t*)p;
+    c->tiles_cap = cap;
+  }
+  if (c->ntiles > 0) {
+    FMM_CUDA(c, cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    k_m2l_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->lv, c->cls_t, c->tvec, c->tile_src, c->tile_act,
+                                               c->tile_nact);
+    c->launches_set++;
+  }
+  if (rows > 0) {
+    std::vector<int64_t> zr;
+    for (int l = 2; l <= Lf; ++l) zr.push_back(c->lv.row_off[l] + c->lv.ncell[l]);
+    int64_t* dz = (int64_t*)c->scratch;
+    FMM_CUDA(c, cudaMemcpyAsync(dz, zr.data(), sizeof(int64_t) * zr.size(), cudaMemcpyHostToDevice, s));
+    k_zero_rows<<<(int)zr.size(), 128, 0, s>>>((int)zr.size(), dz, c->cpad, c->Mhi, c->Mlo, c->L32, c->M64, c->L64);
+    c->launches_set++;
+  }
+  // (host->device copies from pageable vectors are staged before returning)
+  FMM_CUDA(c, cudaGetLastError());
+  c->loaded = true;
+  return FMM_OK;
+}
+
+}  // namespace fmm

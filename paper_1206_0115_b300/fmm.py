@@ -1,0 +1,230 @@
+"""Python binding of libfmm_b300.so (include/fmm.h), argument marshalling only.
+
+Every function keeps its C name and returns what the C call returns; the
+arrays are passed as raw pointers.  Device arrays are torch CUDA tensors
+(PyTorch serves only as the device allocator and stream owner here); host
+arrays are numpy arrays or CPU tensors.  There is no fallback: importing this
+module fails if the shared library is absent, and a failing C call raises
+FMMError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmm_b300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
+
+FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+FMM_FP64, FMM_MIXED = 0, 1
+STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
+                -5: "FMM_ERR_TIMEOUT"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1206_0115_b300/build.py "
+                      "(the package has no CPU fallback)")
+
+lib = C.CDLL(LIB_PATH)
+
+_vp = C.c_void_p
+_SIGS = {
+    "fmm_create": [C.c_int, C.c_int, C.POINTER(_vp)],
+    "fmm_destroy": [_vp],
+    "fmm_set_stream": [_vp, _vp],
+    "fmm_set_precision": [_vp, C.c_int],
+    "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
+    "fmm_evaluate": [_vp, _vp, _vp],
+    "fmm_get_order": [_vp, _vp],
+    "fmm_get_box": [_vp, _vp],
+    "fmm_get_level_size": [_vp, C.c_int, _vp],
+    "fmm_get_level_keys": [_vp, C.c_int, _vp],
+    "fmm_get_level_ranges": [_vp, C.c_int, _vp, _vp],
+    "fmm_get_expansion": [_vp, C.c_int, C.c_int, _vp],
+    "fmm_get_stats": [_vp, _vp],
+    "fmm_get_work": [_vp, _vp],
+    "fmm_set_timing": [_vp, C.c_int],
+    "fmm_get_stage_times": [_vp, _vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+lib.fmm_last_error.argtypes = [_vp]
+lib.fmm_last_error.restype = C.c_char_p
+
+
+class FMMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(h, status: int):
+    if status != FMM_OK:
+        msg = lib.fmm_last_error(h)
+        raise FMMError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a torch tensor or numpy array (None for None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays passed to the FMM library must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the FMM library must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+# ---- the C entry points, same names --------------------------------------------
+
+def fmm_create(height: int, order: int) -> int:
+    h = _vp()
+    _check(None, lib.fmm_create(height, order, C.byref(h)))
+    return h.value
+
+
+def fmm_destroy(h) -> int:
+    return _check(h, lib.fmm_destroy(h))
+
+
+def fmm_set_stream(h, stream) -> int:
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return _check(h, lib.fmm_set_stream(h, handle))
+
+
+def fmm_set_precision(h, precision: int) -> int:
+    return _check(h, lib.fmm_set_precision(h, precision))
+
+
+def fmm_set_particles(h, n: int, xyz, q) -> int:
+    return _check(h, lib.fmm_set_particles(h, n, _ptr(xyz), _ptr(q)))
+
+
+def fmm_evaluate(h, phi, F) -> int:
+    return _check(h, lib.fmm_evaluate(h, _ptr(phi), _ptr(F)))
+
+
+def fmm_get_order(h, perm) -> int:
+    return _check(h, lib.fmm_get_order(h, _ptr(perm)))
+
+
+def fmm_get_box(h) -> np.ndarray:
+    out = np.zeros(4)
+    _check(h, lib.fmm_get_box(h, _ptr(out)))
+    return out
+
+
+def fmm_get_level_size(h, level: int) -> int:
+    out = np.zeros(1, dtype=np.int64)
+    _check(h, lib.fmm_get_level_size(h, level, _ptr(out)))
+    return int(out[0])
+
+
+def fmm_get_level_keys(h, level: int, keys) -> int:
+    return _check(h, lib.fmm_get_level_keys(h, level, _ptr(keys)))
+
+
+def fmm_get_level_ranges(h, level: int, first, count) -> int:
+    return _check(h, lib.fmm_get_level_ranges(h, level, _ptr(first), _ptr(count)))
+
+
+def fmm_get_expansion(h, level: int, which: int, out) -> int:
+    return _check(h, lib.fmm_get_expansion(h, level, which, _ptr(out)))
+
+
+def fmm_get_stats(h) -> np.ndarray:
+    out = np.zeros(8, dtype=np.int64)
+    _check(h, lib.fmm_get_stats(h, _ptr(out)))
+    return out
+
+
+def fmm_get_work(h) -> np.ndarray:
+    out = np.zeros(12, dtype=np.int64)
+    _check(h, lib.fmm_get_work(h, _ptr(out)))
+    return out
+
+
+def fmm_set_timing(h, on: bool) -> int:
+    return _check(h, lib.fmm_set_timing(h, 1 if on else 0))
+
+
+def fmm_get_stage_times(h) -> np.ndarray:
+    out = np.zeros(8, dtype=np.float32)
+    _check(h, lib.fmm_get_stage_times(h, _ptr(out)))
+    return out
+
+
+def fmm_last_error(h) -> str:
+    m = lib.fmm_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class FMM:
+    """Owns one handle.  Inputs/outputs are torch tensors (CUDA or CPU) or numpy
+    arrays; every step runs in the CUDA library."""
+
+    def __init__(self, height: int, order: int, precision: int = FMM_MIXED, stream=None):
+        self.h = fmm_create(height, order)
+        self.height, self.order = height, order
+        fmm_set_precision(self.h, precision)
+        if stream is not None:
+            fmm_set_stream(self.h, stream)
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            fmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_precision(self, precision: int):
+        fmm_set_precision(self.h, precision)
+
+    def set_particles(self, xyz, q):
+        n = int(xyz.shape[0])
+        fmm_set_particles(self.h, n, xyz, q)
+        self.n = n
+
+    def evaluate(self, phi, F):
+        fmm_evaluate(self.h, phi, F)
+
+    def order_perm(self, out):
+        fmm_get_order(self.h, out)
+
+    def level_size(self, level: int) -> int:
+        return fmm_get_level_size(self.h, level)
+
+    def box(self) -> np.ndarray:
+        return fmm_get_box(self.h)
+
+    def stats(self) -> np.ndarray:
+        return fmm_get_stats(self.h)
+
+
+def exported_symbols_of_header(path: str = HEADER) -> list[str]:
+    """Names of the functions include/fmm.h declares."""
+    import re
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:fmm_status|const char\*)\s+(fmm_\w+)\s*\(", text, re.M)))

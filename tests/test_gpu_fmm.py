@@ -1,0 +1,328 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars:
+  * tree (box, Morton permutation, cell keys, particle / child ranges):
+    bit-exact;
+  * FP64 path: relative L2 error against the oracle's FMM (same h, p) <= 1e-10
+    for phi and for F, per-stage expansions <= 1e-11;
+  * mixed path: relative L2 error <= 1e-5 against the oracle's FMM with the
+    same h and p (arithmetic error), and against the exact direct sum
+    wherever the interpolation order keeps the method's own error below it
+    (p = 7 on the unit-cube workloads).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_0115_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10
+TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1206_0115_b300 import build
+    build.build()
+    from paper_1206_0115_b300 import fmm
+    return fmm
+
+
+def _run(F, xyz, q, h, p, precision, host=False):
+    import torch
+    n = len(q)
+    with F.FMM(h, p, precision) as f:
+        if host:
+            f.set_particles(np.ascontiguousarray(xyz), np.ascontiguousarray(q))
+            phi = np.zeros(n)
+            Fo = np.zeros((n, 3))
+            f.evaluate(phi, Fo)
+        else:
+            dx = torch.from_numpy(xyz).cuda()
+            dq = torch.from_numpy(q).cuda()
+            f.set_particles(dx, dq)
+            phi_t = torch.zeros(n, dtype=torch.float64, device="cuda")
+            F_t = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+            f.evaluate(phi_t, F_t)
+            torch.cuda.synchronize()
+            phi, Fo = phi_t.cpu().numpy(), F_t.cpu().numpy()
+    return phi, Fo
+
+
+def _tree(F, xyz, q, h):
+    import torch
+    out = {}
+    with F.FMM(h, 3, F.FMM_FP64) as f:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        n = len(q)
+        perm = torch.zeros(n, dtype=torch.int64, device="cuda")
+        if n:
+            F.fmm_get_order(f.h, perm)
+        out["perm"] = perm.cpu().numpy()
+        out["box"] = f.box()
+        for lev in range(h):
+            nc = f.level_size(lev)
+            keys = np.zeros(nc, dtype=np.uint64)
+            first = np.zeros(nc, dtype=np.int64)
+            count = np.zeros(nc, dtype=np.int64)
+            if nc:
+                F.fmm_get_level_keys(f.h, lev, keys)
+                F.fmm_get_level_ranges(f.h, lev, first, count)
+            out[lev] = (keys, first, count)
+    return out
+
+
+TREE_CASES = [
+    ("cube_n20k_h4", lambda: inputs.particles(20000, 1, "cube", "pos"), 4),
+    ("ellipsoid_n30k_h6", lambda: inputs.particles(30000, 3, "ellipsoid", "pos"), 6),
+    ("cube_n5k_h8", lambda: inputs.particles(5000, 4, "cube", "sym"), 8),
+    ("n1", lambda: (np.array([[0.3, 0.2, 0.1]]), np.array([1.0])), 4),
+    ("n2_same_point", lambda: (np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.5]]), np.array([1.0, 2.0])), 4),
+]
+
+
+def _golden_points():
+    from conftest import read_golden
+    rows = [r for r in read_golden("morton_keys.txt") if r[0] == "3"]
+    xyz = np.array([[float(v) for v in r[1:4]] for r in rows] + [[0, 0, 0], [1, 1, 1]])
+    return xyz, np.ones(len(xyz))
+
+
+def _dup_faces():
+    xyz, q = inputs.particles(4000, 8, "cube", "pos")
+    xyz[:50] = xyz[60]              # 50 coincident points
+    xyz[100:130, 0] = 1.0           # on the upper face
+    xyz[130:160, 1] = xyz[:, 1].min()
+    xyz[200:260] = np.round(xyz[200:260] * 8) / 8   # on interior cell faces
+    return xyz, q
+
+
+@pytest.mark.parametrize("name,make,h", TREE_CASES + [("golden_faces", _golden_points, 4),
+                                                     ("duplicates_faces", _dup_faces, 4),
+                                                     ("h1", lambda: inputs.particles(300, 5, "cube", "pos"), 1),
+                                                     ("h2", lambda: inputs.particles(300, 5, "cube", "pos"), 2)])
+def test_tree_bit_exact(F, name, make, h):
+    xyz, q = make()
+    g = _tree(F, xyz, q, h)
+    with oracle.OracleFMM(xyz, q, h, 3) as o:
+        lo, w = o.box()
+        assert np.array_equal(g["box"], np.array([*lo, w]))
+        assert np.array_equal(g["perm"], o.perm())
+        for lev in range(h):
+            keys, first, count = g[lev]
+            of, oc = o.level_ranges(lev)
+            assert np.array_equal(keys, o.level_keys(lev)), lev
+            assert np.array_equal(first, of), lev
+            assert np.array_equal(count, oc), lev
+
+
+def test_golden_morton_keys_on_device(F):
+    """The hand-computed keys of tests/golden/morton_keys.txt (leaf 3) come out
+    of the GPU tree: corner points fix the root cube to [0,1]^3."""
+    from conftest import read_golden
+    xyz, q = _golden_points()
+    g = _tree(F, xyz, q, 4)
+    keys, first, count = g[3]
+    want = sorted({int(r[7]) for r in read_golden("morton_keys.txt") if r[0] == "3"} | {0, 511})
+    assert keys.tolist() == want
+
+
+FP64_CASES = [
+    ("cube_n20k_h4_p5", lambda: inputs.particles(20000, 1, "cube", "pos"), 4, 5),
+    ("cube_sym_n8k_h4_p4", lambda: inputs.particles(8000, 12, "cube", "sym"), 4, 4),
+    ("ellipsoid_n20k_h5_p5", lambda: inputs.particles(20000, 13, "ellipsoid", "pos"), 5, 5),
+    ("cube_n3k_h3_p7", lambda: inputs.particles(3000, 14, "cube", "sym"), 3, 7),
+    ("cube_n3k_h3_p2", lambda: inputs.particles(3000, 15, "cube", "pos"), 3, 2),
+    ("cube_n2k_h4_p8", lambda: inputs.particles(2000, 16, "cube", "pos"), 4, 8),
+    ("cube_n1k_h3_p10", lambda: inputs.particles(1000, 17, "cube", "pos"), 3, 10),
+    ("dups_h4_p3", _dup_faces, 4, 3),
+]
+
+
+@pytest.mark.parametrize("name,make,h,p", FP64_CASES)
+def test_fp64_matches_oracle_fmm(F, name, make, h, p):
+    xyz, q = make()
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_FP64)
+    with oracle.OracleFMM(xyz, q, h, p) as o:
+        pr, Fr = o.evaluate()
+    assert oracle.rel_l2(phi, pr) <= TOL_FP64
+    assert oracle.rel_l2(Fo, Fr) <= TOL_FP64
+
+
+def test_fp64_stage_expansions(F):
+    """Per-stage parity: M (P2M, M2M) and L (M2L + L2L) at every level."""
+    import torch
+    xyz, q = inputs.particles(12000, 21, "cube", "sym")
+    h, p = 5, 4
+    with F.FMM(h, p, F.FMM_FP64) as f, oracle.OracleFMM(xyz, q, h, p) as o:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
+        f.evaluate(phi, Fo)
+        o.p2m(); o.m2m(); o.m2l(); o.l2l()
+        for lev in range(2, h):
+            for which, wi in (("M", 0), ("L", 1)):
+                got = np.zeros((f.level_size(lev), p ** 3))
+                F.fmm_get_expansion(f.h, lev, wi, got)
+                ref = o.expansion(lev, which)
+                assert oracle.rel_l2(got, ref) <= 1e-11, (lev, which)
+
+
+MIXED_CASES = [
+    ("cube_n20k_h4_p5", lambda: inputs.particles(20000, 1, "cube", "pos"), 4, 5),
+    ("cube_sym_n20k_h4_p7", lambda: inputs.particles(20000, 31, "cube", "sym"), 4, 7),
+    ("ellipsoid_n40k_h6_p5", lambda: inputs.particles(40000, 32, "ellipsoid", "pos"), 6, 5),
+    ("cube_n3k_h3_p3", lambda: inputs.particles(3000, 33, "cube", "pos"), 3, 3),
+    ("cube_n2k_h4_p8", lambda: inputs.particles(2000, 16, "cube", "pos"), 4, 8),
+    ("cube_n1k_h3_p10", lambda: inputs.particles(1000, 17, "cube", "pos"), 3, 10),
+    ("dups_h4_p4", _dup_faces, 4, 4),
+]
+
+
+@pytest.mark.parametrize("name,make,h,p", MIXED_CASES)
+def test_mixed_matches_oracle_fmm(F, name, make, h, p):
+    xyz, q = make()
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
+    with oracle.OracleFMM(xyz, q, h, p) as o:
+        pr, Fr = o.evaluate()
+    assert oracle.rel_l2(phi, pr) <= TOL_MIXED
+    assert oracle.rel_l2(Fo, Fr) <= TOL_MIXED
+
+
+def test_mixed_p7_matches_direct_sum(F):
+    xyz, q = inputs.particles(20000, 41, "cube", "sym")
+    phi, Fo = _run(F, xyz, q, 4, 7, F.FMM_MIXED)
+    pd, Fd = oracle.direct(xyz, q)
+    assert oracle.rel_l2(phi, pd) <= TOL_MIXED
+    assert oracle.rel_l2(Fo, Fd) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("h", [1, 2])
+def test_shallow_trees_are_direct_sums(F, precision, h):
+    xyz, q = inputs.particles(2500, 51, "cube", "sym")
+    phi, Fo = _run(F, xyz, q, h, 4, precision)
+    pd, Fd = oracle.direct(xyz, q)
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED
+    assert oracle.rel_l2(phi, pd) <= tol
+    assert oracle.rel_l2(Fo, Fd) <= tol
+
+
+def test_host_pointers_match_device_pointers(F):
+    xyz, q = inputs.particles(5000, 61, "cube", "pos")
+    a = _run(F, xyz, q, 4, 4, F.FMM_MIXED, host=False)
+    b = _run(F, xyz, q, 4, 4, F.FMM_MIXED, host=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_degenerate_inputs(F):
+    import torch
+    with F.FMM(4, 3, F.FMM_MIXED) as f:
+        with pytest.raises(F.FMMError) as e:
+            f.evaluate(np.zeros(1), np.zeros(3))
+        assert e.value.status == F.FMM_ERR_STATE
+        f.set_particles(np.zeros((0, 3)), np.zeros(0))
+        f.evaluate(np.zeros(0), np.zeros((0, 3)))
+        for n in (1, 7):
+            xyz = np.tile([[0.25, 0.5, 0.75]], (n, 1))
+            f.set_particles(xyz, np.ones(n))
+            phi = np.full(n, 9.0)
+            Fo = np.full((n, 3), 9.0)
+            f.evaluate(phi, Fo)
+            assert np.all(phi == 0.0) and np.all(Fo == 0.0)
+        bad = np.array([[0.1, np.nan, 0.2], [0.3, 0.3, 0.3]])
+        with pytest.raises(F.FMMError) as e:
+            f.set_particles(bad, np.ones(2))
+        assert e.value.status == F.FMM_ERR_ARG
+        with pytest.raises(F.FMMError) as e:
+            f.set_particles(np.zeros((2, 3)), np.array([1.0, np.inf]))
+        assert e.value.status == F.FMM_ERR_ARG
+        # the handle is still usable afterwards
+        xyz, q = inputs.particles(3000, 62, "cube", "pos")
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        phi = np.zeros(3000)
+        Fo = np.zeros((3000, 3))
+        f.evaluate(phi, Fo)
+        with oracle.OracleFMM(xyz, q, 4, 3) as o:
+            pr, Fr = o.evaluate()
+        assert oracle.rel_l2(phi, pr) <= TOL_MIXED
+
+
+def test_reload_changes_tree(F):
+    """Loading a different particle set on the same handle rebuilds the tree
+    (stale grid entries of the previous tree must not leak)."""
+    with F.FMM(5, 4, F.FMM_FP64) as f:
+        for seed, dist, n in [(71, "cube", 9000), (72, "ellipsoid", 4000), (73, "cube", 20000), (71, "cube", 9000)]:
+            xyz, q = inputs.particles(n, seed, dist, "pos")
+            f.set_particles(xyz, q)
+            phi = np.zeros(n)
+            Fo = np.zeros((n, 3))
+            f.evaluate(phi, Fo)
+            with oracle.OracleFMM(xyz, q, 5, 4) as o:
+                pr, Fr = o.evaluate()
+            assert oracle.rel_l2(phi, pr) <= TOL_FP64
+            assert oracle.rel_l2(Fo, Fr) <= TOL_FP64
+
+
+def test_evaluate_is_repeatable_and_precision_switch(F):
+    xyz, q = inputs.particles(10000, 81, "cube", "sym")
+    with F.FMM(4, 5, F.FMM_MIXED) as f:
+        f.set_particles(xyz, q)
+        out = []
+        for prec in (F.FMM_MIXED, F.FMM_MIXED, F.FMM_FP64, F.FMM_MIXED):
+            f.set_precision(prec)
+            phi = np.zeros(len(q))
+            Fo = np.zeros((len(q), 3))
+            f.evaluate(phi, Fo)
+            out.append((phi, Fo))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[3][0])
+    assert oracle.rel_l2(out[0][0], out[2][0]) <= TOL_MIXED
+
+
+# ------------------------------------------------------------------ full sizes
+
+def _sample_idx(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
+
+
+@pytest.mark.slow
+def test_cube_n1m_h6_p7_full_size(F):
+    """The benchmark workload (1e6 points, h = 6, p = 7): mixed path vs the
+    exact sum on 2000 sampled targets; FP64 path vs the oracle's FMM at 300
+    sampled targets; the Morton permutation bit-exact."""
+    xyz, q, h, p = inputs.workload("cube_n1m_h6_p7")
+    idx = _sample_idx(len(q), 2000, 5)
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
+    pd, Fd = oracle.direct_sampled(xyz, q, idx)
+    assert oracle.rel_l2(phi[idx], pd) <= TOL_MIXED
+    assert oracle.rel_l2(Fo[idx], Fd) <= TOL_MIXED
+    phi64, F64 = _run(F, xyz, q, h, p, F.FMM_FP64)
+    with oracle.OracleFMM(xyz, q, h, p) as o:
+        perm = o.perm()
+        idx2 = idx[:300]
+        pr, Fr = o.evaluate_sampled(idx2)
+    assert oracle.rel_l2(phi64[idx2], pr) <= TOL_FP64
+    assert oracle.rel_l2(F64[idx2], Fr) <= TOL_FP64
+    g = _tree(F, xyz, q, h)
+    assert np.array_equal(g["perm"], perm)
+
+
+@pytest.mark.slow
+def test_ellipsoid_n10m_h8_p7_full_size(F):
+    """1e7 points on the ellipsoid surface, h = 8, p = 7, mixed path: against
+    the oracle's FMM (same h, p) and the exact sum on sampled targets."""
+    xyz, q, h, p = inputs.workload("ellipsoid_n10m_h8_p7")
+    idx = _sample_idx(len(q), 256, 6)
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
+    with oracle.OracleFMM(xyz, q, h, p) as o:
+        pr, Fr = o.evaluate_sampled(idx)
+    assert oracle.rel_l2(phi[idx], pr) <= TOL_MIXED
+    assert oracle.rel_l2(Fo[idx], Fr) <= TOL_MIXED
+    pd, Fd = oracle.direct_sampled(xyz, q, idx)
+    print("ellipsoid mixed vs direct: phi %.3e F %.3e" % (oracle.rel_l2(phi[idx], pd), oracle.rel_l2(Fo[idx], Fd)))
