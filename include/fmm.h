@@ -149,6 +149,31 @@ fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 fmm_status fmm_set_timing(fmm_handle h, int on);
 fmm_status fmm_get_stage_times(fmm_handle h, float* out);
 
+/* Allocation-free Morton ordering (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they
+ * run -- processes whose HBM is owned by a pool reserved at start-up, such as
+ * a serving loop that must never stall in the driver's allocator, and
+ * plug-ins that only receive buffers from their host application).
+ * It computes the first steps of fmm_set_particles for a tree of `height`
+ * levels (1..11) -- root cube, leaf-level Morton keys, stable sort -- and
+ * writes, for Morton rank r, keys[r] = leaf key and perm[r] = input index:
+ * the same permutation fmm_get_order returns and the keys of
+ * fmm_get_level_keys(height-1) repeated over each leaf's particles.
+ *   xyz: [n][3] FP64 device; keys: [n] uint64 device; perm: [n] int64 device;
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ *   n <= 262144 (2^18); larger n -> FMM_ERR_ARG with a message.
+ * It allocates nothing: every intermediate lives in one fixed array of about
+ * 4.3 MB compiled into the library, which each GPU that loads the library
+ * holds until the process exits.  All calls on a GPU share that array, so
+ * calls whose work overlaps on the GPU race and must be serialised by the
+ * caller.  The first call on each device looks the array's address up (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  The call synchronises `stream` before it returns (it reads back
+ * the input check).  Errors (message from fmm_last_error(NULL)):
+ * FMM_ERR_ARG (range, NULL, non-finite coordinate), FMM_ERR_CUDA. */
+fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int height, uint64_t* keys, int64_t* perm,
+                                    void* stream);
+
 /* Message of the last failed call on this handle ("" if none).  With
  * h == NULL: the message of the last failed fmm_create in this thread. */
 const char* fmm_last_error(fmm_handle h);

@@ -9,6 +9,7 @@
 // Every step is integer or exact, so the tree is bit-identical to any other
 // implementation of the same rules.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -501,6 +502,134 @@ fmm_status unique_level(Ctx* c, cudaStream_t s, const int32_t* n_ptr, int64_t n_
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Allocation-free Morton ordering.
+//
+// For callers that cannot allocate device memory while they run: processes
+// whose HBM is owned by a pool they reserved at start-up (a serving loop that
+// must not stall in the driver's allocator, or a framework allocator that
+// holds nearly all of the device), and plug-ins that only ever receive
+// buffers from their host application.  This entry point computes what the
+// front of fmm_set_particles computes -- the root cube, the leaf-level Morton
+// keys and the stable sort -- with every intermediate in one fixed array
+// compiled into the library, so it never calls cudaMalloc or cudaFree.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the
+// library holds it (about 4.3 MB) until the process exits, and every call on
+// that GPU reuses it.  Calls whose work overlaps on the same GPU (different
+// streams, or host threads) therefore race on it and must be serialised by
+// the caller.  Host code cannot use the variable's name as a device address;
+// the first call on each device looks the address up (cudaGetSymbolAddress)
+// with that device current and caches it, so make that first call before any
+// stream capture.
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = (int64_t)1 << 18;
+constexpr int64_t NOALLOC_TILES = (NOALLOC_MAX_N + RS_TILE - 1) / RS_TILE;
+constexpr int NOALLOC_BBOX_BLOCKS = 128;
+// word offsets inside the array
+constexpr int64_t NA_KEY_A = 0;
+constexpr int64_t NA_KEY_B = NA_KEY_A + NOALLOC_MAX_N;
+constexpr int64_t NA_IDX_A = NA_KEY_B + NOALLOC_MAX_N;
+constexpr int64_t NA_IDX_B = NA_IDX_A + NOALLOC_MAX_N;
+constexpr int64_t NA_HIST = NA_IDX_B + NOALLOC_MAX_N;
+constexpr int64_t NA_PART = NA_HIST + 256 * NOALLOC_TILES;          // doubles: 8-byte aligned
+constexpr int64_t NA_BOX = NA_PART + 2 * 6 * NOALLOC_BBOX_BLOCKS;   // 4 doubles
+constexpr int64_t NA_COUNTERS = NA_BOX + 2 * 4;                     // 128 int32
+constexpr int64_t NA_WORDS = NA_COUNTERS + 128;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+std::mutex g_noalloc_mutex;
+uint32_t* g_noalloc_addr[64] = {nullptr};
+
+__global__ void k_noalloc_out(int64_t n, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
+                              uint64_t* __restrict__ keys, int64_t* __restrict__ perm) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  keys[r] = skey[r];
+  perm[r] = sidx[r];
+}
+
+}  // namespace
+}  // namespace fmm
+
+extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int height, uint64_t* keys,
+                                               int64_t* perm, void* stream) {
+  using namespace fmm;
+  if (height < 1 || height > FMM_MAX_LEVELS)
+    return set_err(nullptr, FMM_ERR_ARG, "fmm_morton_order_noalloc: height %d outside 1..%d", height,
+                   FMM_MAX_LEVELS);
+  if (n < 0 || n > NOALLOC_MAX_N)
+    return set_err(nullptr, FMM_ERR_ARG,
+                   "fmm_morton_order_noalloc: n = %lld outside 0..%lld (the fixed scratch array holds %lld points)",
+                   (long long)n, (long long)NOALLOC_MAX_N, (long long)NOALLOC_MAX_N);
+  if (n == 0) return FMM_OK;
+  if (!xyz || !keys || !perm) return set_err(nullptr, FMM_ERR_ARG, "fmm_morton_order_noalloc: NULL pointer");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: no current device (%s)", cudaGetErrorString(e));
+  }
+  uint32_t* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      e = cudaGetSymbolAddress((void**)&g_noalloc_addr[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;
+        cudaGetLastError();
+        return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: cudaGetSymbolAddress: %s",
+                       cudaGetErrorString(e));
+      }
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *ka = base + NA_KEY_A, *kb = base + NA_KEY_B, *va = base + NA_IDX_A, *vb = base + NA_IDX_B;
+  uint32_t* hist = base + NA_HIST;
+  double* part = (double*)(base + NA_PART);
+  double* box = (double*)(base + NA_BOX);
+  int32_t* counters = (int32_t*)(base + NA_COUNTERS);
+  const int Lf = height - 1;
+  // the array keeps the previous call's contents: clear the input-error flag
+  e = cudaMemsetAsync(counters, 0, 128 * sizeof(int32_t), s);
+  int nbb = ceil_div(n, BB_THREADS * 8);
+  if (nbb > NOALLOC_BBOX_BLOCKS) nbb = NOALLOC_BBOX_BLOCKS;
+  // positions only: the charge check of the cube kernel re-reads coordinates
+  if (e == cudaSuccess) {
+    k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, xyz, part, counters);
+    k_bbox_final<<<1, 32, 0, s>>>(nbb, part, box);
+    k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, box, Lf, ka, va);
+    const int ntiles = ceil_div(n, RS_TILE);
+    for (int sh = 0; sh < 3 * Lf; sh += 8) {
+      k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(n, ka, sh, hist, ntiles);
+      k_scan1<uint32_t><<<1, 1024, 0, s>>>(hist, (int64_t)256 * ntiles, nullptr);
+      k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, kb, vb, sh, hist, ntiles);
+      uint32_t* tmp = ka;
+      ka = kb;
+      kb = tmp;
+      tmp = va;
+      va = vb;
+      vb = tmp;
+    }
+    k_noalloc_out<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, keys, perm);
+    e = cudaGetLastError();
+  }
+  int32_t bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, counters + CNT_BAD, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: %s", cudaGetErrorString(e));
+  }
+  if (bad) return set_err(nullptr, FMM_ERR_ARG, "fmm_morton_order_noalloc: non-finite coordinate");
+  return FMM_OK;
+}
+
+namespace fmm {
 
 fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   cudaStream_t s = c->stream;

@@ -47,6 +47,7 @@ _SIGS = {
     "fmm_get_work": [_vp, _vp],
     "fmm_set_timing": [_vp, C.c_int],
     "fmm_get_stage_times": [_vp, _vp],
+    "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -161,6 +162,11 @@ def fmm_get_stage_times(h) -> np.ndarray:
     out = np.zeros(8, dtype=np.float32)
     _check(h, lib.fmm_get_stage_times(h, _ptr(out)))
     return out
+
+
+def fmm_morton_order_noalloc(n: int, xyz, height: int, keys, perm, stream=None) -> int:
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return _check(None, lib.fmm_morton_order_noalloc(n, _ptr(xyz), height, _ptr(keys), _ptr(perm), handle))
 
 
 def fmm_last_error(h) -> str:
