@@ -93,7 +93,10 @@ fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const d
  * Device outputs: the call returns after enqueueing (stream-ordered).
  * Host outputs: the call returns after the results are in host memory.
  * Errors: FMM_ERR_STATE (no particles loaded), FMM_ERR_ARG (NULL with
- * n > 0), FMM_ERR_CUDA. */
+ * n > 0), FMM_ERR_CUDA, FMM_ERR_TIMEOUT (a bounded wait inside the previous
+ * evaluation's tensor-core M2L ran out: that evaluation's results are
+ * invalid; the flag travels with the stream, so it is reported by the next
+ * call on the handle). */
 fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
 
 /* Morton permutation of the last fmm_set_particles: perm[r] = input index of
@@ -141,8 +144,10 @@ fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 
 /* Per-stage device times of the last fmm_evaluate in milliseconds (CUDA
  * events recorded inside the evaluation when timing is on), in this order:
- * [0] upward pass (P2M + M2M), [1] M2L (all levels), [2] M2L at the leaf
- * level alone, [3] M2L at the coarser levels, [4] L2L (all levels),
+ * [0] upward pass (P2M + M2M), [1] M2L (all levels), [2] the main M2L
+ * kernel (CUDA-core kernels: the leaf level; tensor-core kernel: every
+ * level), [3] the rest of M2L (coarser levels; or the FP64 reduction of the
+ * tensor-core partial sums), [4] L2L (all levels),
  * [5] P2P (on the parallel branch), [6] L2P + output, [7] whole evaluation.  fmm_set_timing(h, 1) turns the events on (the
  * evaluation graph is rebuilt); this call synchronises the stream.
  * out: 8 floats, host. */

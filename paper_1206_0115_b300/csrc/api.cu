@@ -105,9 +105,7 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
   FMM_TRY(launch_upward(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
-  FMM_TRY(launch_m2l_level(c, s, 0, c->leaf_tile_end()));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[2], s, cudaEventRecordExternal));
-  FMM_TRY(launch_m2l_level(c, s, c->leaf_tile_end(), c->ntiles - c->leaf_tile_end()));
+  FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
   FMM_TRY(launch_l2l(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[4], s, cudaEventRecordExternal));
@@ -117,7 +115,7 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 
 // Everything the captured evaluation graph bakes into its kernel arguments.
 std::vector<int64_t> graph_signature(const Ctx* c) {
-  std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n};
+  std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -129,7 +127,8 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                         (const void*)c->near64, (const void*)c->Mhi, (const void*)c->Mlo, (const void*)c->L32,
                         (const void*)c->M64, (const void*)c->L64, (const void*)c->tiles, (const void*)c->tile_src,
                         (const void*)c->tile_act, (const void*)c->tile_nact, (const void*)c->K64,
-                        (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm})
+                        (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm,
+                        (const void*)c->tc_partial, (const void*)c->tc_err})
     s.push_back((int64_t)(uintptr_t)p);
   return s;
 }
@@ -140,6 +139,18 @@ void drop_graph(Ctx* c) {
   c->gexec = nullptr;
   c->graph = nullptr;
   c->graph_ok = false;
+}
+
+// A tensor-core M2L wait that ran out is reported by the next call (the flag
+// comes back with the previous evaluation's stream work).
+fmm_status check_device_error(Ctx* c) {
+  if (c->tc_err_h && *(volatile int32_t*)c->tc_err_h) {
+    *(volatile int32_t*)c->tc_err_h = 0;
+    if (c->tc_err) cudaMemsetAsync(c->tc_err, 0, sizeof(int32_t), c->stream);
+    return set_err(c, FMM_ERR_TIMEOUT, "M2L tensor-core kernel: a pipeline wait ran out and the kernel returned "
+                                       "early; the previous evaluation's results are invalid");
+  }
+  return FMM_OK;
 }
 
 fmm_status build_graph(Ctx* c) {
@@ -200,6 +211,10 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   c->leaf = height - 1;
   c->ncoef = order * order * order;
   c->cpad = (c->ncoef + 1 + 31) / 32 * 32;  // + the mean slot of mixed local expansions
+  {
+    const char* e = getenv("FMM_M2L_KERNEL");  // "simt": CUDA-core M2L in mixed precision too
+    c->use_tc = !(e && strcmp(e, "simt") == 0);
+  }
   fmm_status st = FMM_OK;
   auto fail = [&](fmm_status s) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", c->err);
@@ -224,7 +239,8 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   if ((st = dalloc(c, &p, 128 * sizeof(int32_t))) != FMM_OK) return fail(st);
   c->counters = (int32_t*)p;
   if (cudaMallocHost((void**)&c->counters_h, 128 * sizeof(int32_t)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->box_h, 4 * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost((void**)&c->box_h, 4 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->tc_err_h, sizeof(int32_t)) != cudaSuccess) {
     cuda_err(c, cudaGetLastError(), "fmm_create: pinned host buffers");
     return fail(FMM_ERR_OOM);
   }
@@ -256,7 +272,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->near64,
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
-                  c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo};
+                  c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
@@ -265,6 +281,7 @@ fmm_status fmm_destroy(fmm_handle h) {
       if (b) cudaFree(b);
   }
   if (c->counters_h) cudaFreeHost(c->counters_h);
+  if (c->tc_err_h) cudaFreeHost(c->tc_err_h);
   if (c->box_h) cudaFreeHost(c->box_h);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -323,7 +340,9 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   if (n == 0) return FMM_OK;
   if (!phi || !F) return set_err(c, FMM_ERR_ARG, "fmm_evaluate: NULL output");
   FMM_CUDA(c, cudaSetDevice(c->dev));
+  FMM_TRY(check_device_error(c));
   FMM_TRY(operators_m2l(c, c->precision));
+  if (m2l_kind(c) == 2) FMM_TRY(m2l_tc_prepare(c));
   const bool dev_out = is_device_ptr(phi) && is_device_ptr(F);
   double *dphi = phi, *dF = F;
   if (!dev_out) {
@@ -341,6 +360,8 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   FMM_TRY(launch_l2p_out(c, c->stream, dphi, dF));
   if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[8], c->stream));
   c->tev_recorded = c->timing;
+  if (c->tc_err && m2l_kind(c) == 2)
+    FMM_CUDA(c, cudaMemcpyAsync(c->tc_err_h, c->tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   if (!dev_out) {
     FMM_CUDA(c, cudaMemcpyAsync(phi, dphi, sizeof(double) * n, cudaMemcpyDefault, c->stream));
     FMM_CUDA(c, cudaMemcpyAsync(F, dF, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
@@ -458,8 +479,8 @@ fmm_status fmm_get_stage_times(fmm_handle h, float* out) {
   };
   out[0] = el(0, 1);  // P2M + M2M
   out[1] = el(1, 3);  // M2L, all levels
-  out[2] = el(1, 2);  // M2L, leaf level
-  out[3] = el(2, 3);  // M2L, coarser levels
+  out[2] = el(1, 2);  // main M2L kernel
+  out[3] = el(2, 3);  // rest of M2L
   out[4] = el(3, 4);  // L2L
   out[5] = el(5, 6);  // P2P
   out[6] = el(7, 8);  // L2P + output

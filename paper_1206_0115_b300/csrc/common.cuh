@@ -136,6 +136,17 @@ struct fmm_ctx {
   cudaEvent_t tev[10] = {nullptr};
   bool tev_recorded = false;
 
+  // tensor-core M2L
+  bool use_tc = true;
+  float* tc_partial = nullptr;
+  int64_t tc_partial_cap = 0;
+  int32_t* tc_err = nullptr;      // device error word of the tensor-core kernel
+  int32_t* tc_err_h = nullptr;    // pinned mirror, copied after every evaluation
+  alignas(64) unsigned char tm_khi[128], tm_klo[128];  // CUtensorMap of the operator bank
+  int64_t tm_rows = -1;
+  const void* tm_khi_ptr = nullptr;
+  int tc_smem_set = 0, tc_nst = 0, num_sms = 0;
+
   // stats
   int64_t launches_set = 0, launches_eval = 0, bytes = 0;
 };
@@ -167,8 +178,12 @@ fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
 fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
-fmm_status launch_m2l_level(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
+bool m2l_tc_supported(const Ctx* c);
+fmm_status m2l_tc_prepare(Ctx* c);
+fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
+// M2L of every level; `mid` separates the main kernel from the rest (see fmm_get_stage_times)
+fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 fmm_status launch_l2l(Ctx* c, cudaStream_t s);
 fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F);
 fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out);

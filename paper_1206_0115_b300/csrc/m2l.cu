@@ -1,14 +1,26 @@
-// m2l.cu -- M2L dispatch (Sec. 2.1.2): the FP64 path runs the SIMT kernel in
-// FP64; the mixed path runs the SIMT kernel on FP32 sums of the TF32 pairs.
+// m2l.cu -- M2L dispatch (Sec. 2.1.2): the FP64 path runs the CUDA-core
+// kernel in FP64; the mixed path runs the tcgen05 kernel (3xTF32) when the
+// order allows it (p <= 7) and otherwise the CUDA-core kernel on FP32 sums of
+// the TF32 pairs.
 #include "common.cuh"
 
 namespace fmm {
 
-int m2l_kind(const Ctx* c) { return c->precision == FMM_FP64 ? 0 : 1; }
+int m2l_kind(const Ctx* c) {
+  if (c->precision == FMM_FP64) return 0;
+  return (c->use_tc && m2l_tc_supported(c)) ? 2 : 1;
+}
 
-fmm_status launch_m2l_level(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
-  if (ntiles <= 0 || c->n == 0) return FMM_OK;
-  return launch_m2l_simt(c, s, first_tile, ntiles);
+fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
+  if (c->ntiles <= 0 || c->n == 0) {
+    if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
+    return FMM_OK;
+  }
+  if (m2l_kind(c) == 2) return launch_m2l_tc(c, s, mid);
+  // CUDA cores: leaf level, then the coarser levels
+  FMM_TRY(launch_m2l_simt(c, s, 0, c->leaf_tiles));
+  if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
+  return launch_m2l_simt(c, s, c->leaf_tiles, c->ntiles - c->leaf_tiles);
 }
 
 namespace {
@@ -70,7 +82,7 @@ int64_t count_launches_eval(const Ctx* c) {
   int64_t k = 2;  // P2P, L2P/output
   if (Lf >= 2 && c->n > 0) {
     k += 1 + (Lf - 2);                                      // P2M, M2M
-    k += (c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles);  // M2L
+    k += m2l_kind(c) == 2 ? 2 * (c->ntiles > 0) : (c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles);  // M2L
     k += (Lf - 2);                                          // L2L
   }
   return k;

@@ -1,0 +1,560 @@
+// m2l_tc.cu -- M2L (Sec. 2.1.2) on the sm_103a tensor cores.
+//
+// For one level and one child class every target cell T needs
+//     L_T = (1/a) sum_{t in the class's 189 transfer vectors} K_t M_{T+t},
+// a GEMM whose rows are target cells (128 per tile), whose columns are the
+// output coefficients (the mean-split bank: deviations + cell mean, padded to
+// cpad), and whose K dimension runs over (t, source coefficient).  The A
+// operand is gathered: row r of a tile holds M of the source cell T_r + t
+// (the level's zero row when absent).
+//
+// Work unit = (tile, half of the output columns, group of TC_GT consecutive
+// active transfer vectors).  The tensor cores' FP32 accumulation rounds
+// toward zero, so its error grows linearly with the accumulation chain
+// (measured: x11 longer chain, x13 larger error).  Each transfer vector
+// therefore gets a fresh TMEM accumulator (one of two, alternating), which the
+// epilogue adds into a running sum in shared memory with ordinary FP32
+// round-to-nearest additions while the next transfer vector accumulates; a
+// unit's sum goes to its own partial slice and k_m2l_tc_reduce adds the
+// slices of a tile in FP64.
+//
+// Precision: 3xTF32 -- multipoles and operators are TF32 hi/lo pairs and each
+// K-step issues hi*hi + hi*lo + lo*hi into the same FP32 accumulator.
+//
+// Roles (one CTA per SM, 288 threads, persistent over the units):
+//   warps 0-3  producers: per stage (16 source coefficients of one t) each
+//              thread loads its target row's 16 multipole coefficients (hi and
+//              lo, four 16-byte loads each) and stores them in the 64-byte
+//              swizzle pattern, then fences the async proxy and arrives; one
+//              thread also issues the B slab K_t[0..cpad)[k0..k0+16) as 2-D
+//              tiled TMA loads (64-byte swizzle, 512-byte aligned targets).
+//              A 4-row TMA gather would land on 256-byte boundaries, short of
+//              the 512-byte alignment a 64-byte-swizzled TMA target needs;
+//   warps 4-7  epilogue: tcgen05.ld of each accumulator into the running
+//              sums, stores of the sums to the unit's slice;
+//   warp 8     TMEM allocation and the tcgen05.mma issuer (one thread).
+// Every mbarrier wait is bounded in time; on expiry the CTA raises the error
+// word, drains what it has in flight (again bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int TC_THREADS = 288;  // warps 0-3 producers, 4-7 epilogue, 8 MMA issuer
+constexpr int TC_MMA_WARP = 8;
+constexpr int TC_KC = 16;      // K elements per stage (64-byte rows)
+constexpr int TC_MAXST = 4;    // pipeline stages at most
+constexpr int TC_A_BYTES = FMM_TILE * TC_KC * 4;   // one half (hi or lo) of A: 8 KB
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;     // 2 s per wait: far beyond any real stage
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ inline void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ inline void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ inline bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of parity `parity` to complete; false after TC_WAIT_NS.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (!mbar_test(bar, parity))
+    if (gtime() - t0 > TC_WAIT_NS) return false;
+  return true;
+}
+// Warp-uniform wait: lane 0 waits, the whole warp gets its verdict (and the
+// CTA's abort flag), so warp-collective instructions that follow stay converged.
+__device__ inline bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity) && !*abort_flag;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ inline void tma_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, 64-byte swizzle: rows of 64 B,
+// 8-row groups 512 B apart.
+__device__ inline uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // 64-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulate, TF32 A and B, both
+// K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ inline void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ inline void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ inline void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ inline void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  const Tile* tiles;
+  const int32_t* tile_src;
+  const int16_t* tile_act;
+  const int32_t* tile_nact;
+  const int16_t* cls_t;
+  float* partial;  // [group][tile][128][cpad]
+  int32_t* err;    // nonzero after a timed-out wait
+  int ntiles, groups, gt, cpad, nh, nhalf, kchunks, nst;
+  uint32_t tmem_cols;  // power of two >= 2 * nhalf (two accumulators)
+};
+
+// Work unit u -> (group g, column half h, tile): groups outermost so that the
+// CTAs running at the same time share transfer vectors (operator slabs stay
+// in L2).
+__device__ inline void unit_coords(const TcArgs& a, int u, int& g, int& h, int& tile) {
+  const int per_g = a.ntiles * a.nh;
+  g = u / per_g;
+  const int rem = u - g * per_g;
+  h = rem / a.ntiles;
+  tile = rem - h * a.ntiles;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUtensorMap tm_klo, TcArgs a,
+         LevelPtrs lv, const float* __restrict__ Mhi, const float* __restrict__ Mlo) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+  const uint32_t b_bytes = (uint32_t)a.nhalf * TC_KC * 4;      // one half (hi or lo) of B
+  const uint32_t stage_bytes = 2u * TC_A_BYTES + 2u * b_bytes;
+  const uint32_t sum_off = (uint32_t)a.nst * stage_bytes;     // running sums S[col][row], FP32
+  const uint32_t bars = base + sum_off + (uint32_t)a.nhalf * FMM_TILE * 4u;
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (TC_MAXST + s); };
+  auto acc_full = [&](int b) { return bars + 8u * (2 * TC_MAXST + b); };
+  auto acc_empty = [&](int b) { return bars + 8u * (2 * TC_MAXST + 2 + b); };
+  const uint32_t mma_done = bars + 8u * (2 * TC_MAXST + 4);
+  unsigned char* gbase = smem_raw + (base - raw);
+  float* S = (float*)(gbase + sum_off);
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(gbase + (bars - base) + 8u * (2 * TC_MAXST + 6));
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_MAXST; ++s) {
+      mbar_init(full(s), FMM_TILE + 1);  // 128 A-row producers + the B copy's expect_tx
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 128);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == TC_MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nunits = a.ntiles * a.nh * a.groups;
+
+  if (warp < 4) {
+    // ------------------------------------------------------------ producers
+    // thread r gathers A row r (the source multipole of target r for the
+    // current t) with plain 16-byte loads and stores it in the 64-byte swizzle
+    // pattern: chunk c of row r goes to chunk c ^ ((r >> 1) & 3).
+    const int r = threadIdx.x;
+    const uint32_t rsw = (uint32_t)((r >> 1) & 3);
+    uint32_t it = 0;
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, h, tile;
+      unit_coords(a, unit, g, h, tile);
+      const int nact = a.tile_nact[tile];
+      const int a0 = g * a.gt, a1 = min(nact, a0 + a.gt);
+      if (a0 >= a1) continue;
+      const Tile tl = a.tiles[tile];
+      const int64_t rbase = lv.row_off[tl.level];
+      for (int ai = a0; ai < a1 && ok; ++ai) {
+        const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
+        const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
+        const int64_t src = rbase + a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
+        const float4* ghi = (const float4*)(Mhi + src * a.cpad);
+        const float4* glo = (const float4*)(Mlo + src * a.cpad);
+        for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+          float4 vh[4], vl[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            vh[c] = ghi[kc * 4 + c];
+            vl[c] = glo[kc * 4 + c];
+          }
+          const int s = (int)(it % a.nst);
+          const uint32_t ph = (it / a.nst) & 1u;
+          if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + (uint32_t)s * stage_bytes;
+          if (r == 0) {
+            mbar_expect_tx(full(s), 2u * b_bytes);
+            const int y = slot * a.cpad + h * a.nhalf;
+            tma_2d(st + 2u * TC_A_BYTES, &tm_khi, kc * TC_KC, y, full(s));
+            tma_2d(st + 2u * TC_A_BYTES + b_bytes, &tm_klo, kc * TC_KC, y, full(s));
+          }
+          unsigned char* sa = gbase + (st - base) + (uint32_t)r * 64u;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t o = (((uint32_t)c ^ rsw) << 4);
+            *(float4*)(sa + o) = vh[c];
+            *(float4*)(sa + TC_A_BYTES + o) = vl[c];
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(full(s));
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+    }
+    // let the operator copies already issued land before the CTA leaves (bounded)
+    if (!ok && r == 0) {
+      const uint32_t issued = it;
+      for (uint32_t j = issued > (uint32_t)a.nst ? issued - a.nst : 0; j < issued; ++j)
+        mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == TC_MMA_WARP) {
+    // ------------------------------------------------------------ MMA issuer
+    // one accumulator per transfer vector, alternating between two TMEM
+    // buffers so that the epilogue drains t while t+1 accumulates
+    uint32_t it = 0, tt = 0;
+    bool ok = true;
+    const uint32_t idesc = idesc_tf32(FMM_TILE, a.nhalf);
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, h, tile;
+      unit_coords(a, unit, g, h, tile);
+      const int nact = a.tile_nact[tile];
+      const int a0 = g * a.gt, a1 = min(nact, a0 + a.gt);
+      if (a0 >= a1) continue;
+      for (int ai = a0; ai < a1 && ok; ++ai, ++tt) {
+        const int b = (int)(tt & 1u);
+        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * a.nhalf);
+        for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+          const int s = (int)(it % a.nst);
+          const uint32_t ph = (it / a.nst) & 1u;
+          if (!warp_wait(full(s), ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t st = base + (uint32_t)s * stage_bytes;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t ahi = sdesc_sw64(st + ks * 32u);
+              const uint64_t alo = sdesc_sw64(st + TC_A_BYTES + ks * 32u);
+              const uint64_t bhi = sdesc_sw64(st + 2u * TC_A_BYTES + ks * 32u);
+              const uint64_t blo = sdesc_sw64(st + 2u * TC_A_BYTES + b_bytes + ks * 32u);
+              mma_tf32(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+              mma_tf32(d, ahi, blo, idesc, 1u);
+              mma_tf32(d, alo, bhi, idesc, 1u);
+            }
+            mma_commit(empty(s));
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit(acc_full(b));
+        __syncwarp();
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+    }
+    // every MMA issued so far has finished before TMEM is freed (bounded)
+    if (lane == 0) {
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------------------ epilogue (warps 4-7)
+    // S[col][row] += accumulator of each transfer vector (FP32, round to
+    // nearest); at the end of the unit S goes to the unit's partial slice.
+    const int q = warp & 3, row = q * 32 + lane;
+    uint32_t tt = 0;
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, h, tile;
+      unit_coords(a, unit, g, h, tile);
+      const int nact = a.tile_nact[tile];
+      const int a0 = g * a.gt, a1 = min(nact, a0 + a.gt);
+      if (a0 >= a1) continue;
+      for (int ai = a0; ai < a1; ++ai, ++tt) {
+        const int b = (int)(tt & 1u);
+        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * a.nhalf);
+        const bool first = ai == a0;
+        int cb = 0;
+        for (; cb + 32 <= a.nhalf; cb += 32) {
+          float v[32];
+          tmem_ld32(tbase + (uint32_t)cb, v);
+          float* sp = S + cb * FMM_TILE + row;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) sp[i * FMM_TILE] = first ? v[i] : sp[i * FMM_TILE] + v[i];
+        }
+        if (cb < a.nhalf) {  // nhalf is a multiple of 16
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)cb, v);
+          float* sp = S + cb * FMM_TILE + row;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sp[i * FMM_TILE] = first ? v[i] : sp[i * FMM_TILE] + v[i];
+        }
+        tc_fence_before();
+        mbar_arrive(acc_empty(b));
+      }
+      if (!ok) break;
+      float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
+      for (int c = 0; c < a.nhalf; c += 4)
+        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row], S[(c + 1) * FMM_TILE + row],
+                                          S[(c + 2) * FMM_TILE + row], S[(c + 3) * FMM_TILE + row]);
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == TC_MMA_WARP)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// L_T[m] = (1/a) * sum over the tile's groups of the partial sums (FP64).
+__global__ void __launch_bounds__(256)
+k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_nact, LevelPtrs lv, int ntiles,
+                int gt, int cpad, int ncol, const float* __restrict__ partial, float* __restrict__ L,
+                const double* __restrict__ box) {
+  const int tile = blockIdx.x;
+  const Tile tl = tiles[tile];
+  const int ng = (tile_nact[tile] + gt - 1) / gt;
+  const double inv_a = ldexp(1.0, tl.level + 1) / box[3];
+  const int64_t rbase = lv.row_off[tl.level];
+  for (int idx = threadIdx.x; idx < tl.count * ncol; idx += blockDim.x) {
+    const int row = idx / ncol, col = idx - row * ncol;
+    double s = 0.0;
+    for (int g = 0; g < ng; ++g) s += (double)partial[(((int64_t)g * ntiles + tile) * FMM_TILE + row) * cpad + col];
+    const int cell = lv.cls[tl.level][tl.first + row];
+    L[(rbase + cell) * cpad + col] = (float)(s * inv_a);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* tm, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+               uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// The tensor-core path serves the mixed precision when the accumulator
+// (cpad FP32 columns) fits the 512 TMEM columns: order <= 7.
+bool m2l_tc_supported(const Ctx* c) { return c->cpad <= 512 && c->cpad % 32 == 0; }
+
+namespace {
+constexpr int TC_GT = 64;  // transfer vectors per work unit
+constexpr int TC_GROUPS = (FMM_NT_CLASS + TC_GT - 1) / TC_GT;
+int tc_nh(int cp) { return cp > 256 ? 2 : 1; }
+int tc_stage_bytes(int cp) { return 2 * TC_A_BYTES + 2 * (cp / tc_nh(cp)) * TC_KC * 4; }
+int tc_fixed_bytes(int cp) { return (cp / tc_nh(cp)) * FMM_TILE * 4 + 1024 + 256; }  // sums, alignment, barriers
+}  // namespace
+
+// Buffers, tensor maps and kernel attributes of the tensor-core M2L for the
+// current tree: called before an evaluation is captured or launched (it may
+// allocate, which a stream capture forbids).
+fmm_status m2l_tc_prepare(Ctx* c) {
+  if (c->ntiles == 0) return FMM_OK;
+  const int cp = c->cpad;
+  const int nh = cp > 256 ? 2 : 1, nhalf = cp / nh;
+  if (nhalf % 16 != 0 || nhalf > 256) return set_err(c, FMM_ERR_ARG, "M2L tensor path: unsupported cpad %d", cp);
+  const int64_t need = (int64_t)c->ntiles * TC_GROUPS * FMM_TILE * cp;
+  if (need > c->tc_partial_cap) {
+    dfree(c, c->tc_partial, 4 * (size_t)c->tc_partial_cap);
+    c->tc_partial = nullptr;
+    c->tc_partial_cap = 0;
+    void* p;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)need));
+    c->tc_partial = (float*)p;
+    c->tc_partial_cap = need;
+  }
+  if (!c->tc_err) {
+    void* p;
+    FMM_TRY(dalloc(c, &p, 64));
+    c->tc_err = (int32_t*)p;
+    FMM_CUDA(c, cudaMemset(c->tc_err, 0, 64));
+  }
+  if (c->tm_khi_ptr != c->Khi) {
+    bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, cp, (uint64_t)FMM_NT * cp, TC_KC, nhalf) &&
+              encode_2d((CUtensorMap*)c->tm_klo, c->Klo, cp, (uint64_t)FMM_NT * cp, TC_KC, nhalf);
+    if (!ok) return set_err(c, FMM_ERR_CUDA, "M2L tensor path: cuTensorMapEncodeTiled failed");
+    c->tm_khi_ptr = c->Khi;
+  }
+  int nst = (227 * 1024 - tc_fixed_bytes(cp)) / tc_stage_bytes(cp);
+  if (nst > TC_MAXST) nst = TC_MAXST;
+  if (nst < 2) return set_err(c, FMM_ERR_ARG, "M2L tensor path: stage too large for cpad %d", cp);
+  c->tc_nst = nst;
+  const int smem = nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
+  if (smem > c->tc_smem_set) {
+    FMM_CUDA(c, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    c->tc_smem_set = smem;
+  }
+  if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+  return FMM_OK;
+}
+
+// Launches the tensor-core M2L over every tile of every level and the
+// reduction of its partial sums; `mid` (optional) is recorded between them.
+fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
+  if (c->ntiles == 0) return FMM_OK;
+  const int cp = c->cpad;
+  const int nh = cp > 256 ? 2 : 1, nhalf = cp / nh;
+  TcArgs a;
+  a.tiles = c->tiles;
+  a.tile_src = c->tile_src;
+  a.tile_act = c->tile_act;
+  a.tile_nact = c->tile_nact;
+  a.cls_t = c->cls_t;
+  a.partial = c->tc_partial;
+  a.err = c->tc_err;
+  a.ntiles = c->ntiles;
+  a.groups = TC_GROUPS;
+  a.gt = TC_GT;
+  a.cpad = cp;
+  a.nh = nh;
+  a.nhalf = nhalf;
+  a.kchunks = cp / TC_KC;
+  a.nst = c->tc_nst;
+  a.tmem_cols = 32;
+  while ((int)a.tmem_cols < 2 * nhalf) a.tmem_cols <<= 1;
+  const int smem = c->tc_nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
+  const int nunits = c->ntiles * nh * TC_GROUPS;
+  const int grid = nunits < c->num_sms ? nunits : c->num_sms;
+  k_m2l_tc<<<grid, TC_THREADS, smem, s>>>(*(const CUtensorMap*)c->tm_khi, *(const CUtensorMap*)c->tm_klo, a,
+                                          c->lv, c->Mhi, c->Mlo);
+  FMM_CUDA(c, cudaGetLastError());
+  if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
+  k_m2l_tc_reduce<<<c->ntiles, 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, TC_GT, cp, c->ncoef + 1,
+                                            c->tc_partial, c->L32, c->box);
+  return cuda_err(c, cudaGetLastError(), "M2L tensor-core launch");
+}
+
+}  // namespace fmm
