@@ -250,7 +250,7 @@ def run_ours(args):
     phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
     F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     e_ms = []
-    for k in range(args.e2e_steps + 1):
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -261,12 +261,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         if k > 0:
             e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e_ms)
+    e2e_total = sum(e_ms) if e_ms else float("nan")
     if ws > 1:
         t = torch.tensor([e2e_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = n * ws * len(e_ms) / (e2e_total / 1e3)
+    e2e_value = n * ws * len(e_ms) / (e2e_total / 1e3) if e_ms else None
 
     if rank != 0:
         f.close()
@@ -279,10 +279,12 @@ def run_ours(args):
     stage = np.array(stage)
     m2l_leaf_ms = float(np.mean(stage[:, 2]))
     p2p_ms = float(np.mean(stage[:, 5]))
-    m2l_pairs_leaf = int(work[1 + (h - 1)])
-    m2l_flop = 2.0 * C * C * m2l_pairs_leaf
-    p2p_pairs = int(work[0])
     m2l_kind = int(stats[4])  # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
+    # the tensor-core kernel covers every level in one launch, the CUDA-core
+    # kernels time the leaf level separately (stage [2] of fmm_get_stage_times)
+    m2l_pairs = int(work[1:12].sum()) if m2l_kind == 2 else int(work[1 + (h - 1)])
+    m2l_flop = 2.0 * C * C * m2l_pairs
+    p2p_pairs = int(work[0])
     tc_path = m2l_kind == 2
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if tc_path:
@@ -293,6 +295,15 @@ def run_ours(args):
         bound, peak, peak_note = "alu", fp32_peak / 64.0, "FP64 FMA: FP32 rate / 64 (nominal ratio)"
     achieved = m2l_flop / (m2l_leaf_ms / 1e3) / 1e12
     p2p_gflop = 20.0 * p2p_pairs / 1e9
+    tensor_pipe = None
+    if tc_path:
+        # MMAs actually issued: every (tile, active transfer vector) runs a full
+        # 128-row x cpad-column x cpad-deep product three times (3xTF32)
+        cpad = ((C + 1 + 31) // 32) * 32
+        tile_t = int(work[12])
+        hw_flop = 3 * 2.0 * 128 * cpad * cpad * tile_t
+        tensor_pipe = {"mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_leaf_ms / 1e3) / 1e12,
+                       "frac_of_tf32_peak": hw_flop / (m2l_leaf_ms / 1e3) / 1e12 / peak}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -308,11 +319,13 @@ def run_ours(args):
                      "m2l_leaf": m2l_leaf_ms, "m2l_coarse": float(np.mean(stage[:, 3])),
                      "l2l": float(np.mean(stage[:, 4])), "p2p": p2p_ms, "l2p_out": float(np.mean(stage[:, 6])),
                      "evaluate": float(np.mean(stage[:, 7]))},
-        "roofline": {"kernel": ["k_m2l_fp64_simt", "k_m2l_simt (FP32 CUDA cores)", "k_m2l_tc (tcgen05)"][m2l_kind]
-                     + ", leaf level", "bound": bound, "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), leaf level",
+                                "k_m2l_simt<float> (FP32 CUDA cores), leaf level",
+                                "k_m2l_tc (tcgen05, 3xTF32), all levels"][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "algorithmic": f"2 x {C}^2 flop x {m2l_pairs_leaf} pairs = {m2l_flop:.4g} flop per launch",
+                     "algorithmic": f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per launch",
                      "peak_source": peak_note},
+        "tensor_pipe": tensor_pipe,
         "roofline_p2p": {"bound": "alu", "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
                          "interactions": p2p_pairs,
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),

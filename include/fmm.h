@@ -139,7 +139,9 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
  * work the same way): out[0] = directed P2P particle pairs (each target with
  * every particle of its up to 27 near leaves, itself excluded), out[1 + l] =
  * M2L (target, source) cell pairs at level l for l = 0 .. 10 (zero outside
- * 2 .. height-1).  Synchronises the stream.  out: 12 int64, host. */
+ * 2 .. height-1), out[12] = (M2L tile, transfer vector) pairs with at least
+ * one source (each is one 128-row block of M2L products), out[13..15] = 0.
+ * Synchronises the stream.  out: 16 int64, host. */
 fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 
 /* Per-stage device times of the last fmm_evaluate in milliseconds (CUDA

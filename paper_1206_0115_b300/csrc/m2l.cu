@@ -40,6 +40,7 @@ k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ ti
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if ((row & 31) == 0) atomicAdd(&out[1 + tl.level], cnt);
+  if (row == 0) atomicAdd(&out[12], (unsigned long long)nact);
 }
 
 __global__ void k_count_p2p_pairs(LevelPtrs lv, int leaf, int nleaf, unsigned long long* __restrict__ out) {
@@ -62,17 +63,17 @@ __global__ void k_count_p2p_pairs(LevelPtrs lv, int leaf, int nleaf, unsigned lo
 }  // namespace
 
 fmm_status work_counts(Ctx* c, int64_t* out) {
-  for (int k = 0; k < 12; ++k) out[k] = 0;
+  for (int k = 0; k < 16; ++k) out[k] = 0;
   if (c->n == 0) return FMM_OK;
   unsigned long long* d = (unsigned long long*)c->scratch;
-  FMM_CUDA(c, cudaMemsetAsync(d, 0, 12 * sizeof(unsigned long long), c->stream));
+  FMM_CUDA(c, cudaMemsetAsync(d, 0, 16 * sizeof(unsigned long long), c->stream));
   const int nleaf = c->lv.ncell[c->leaf];
   k_count_p2p_pairs<<<ceil_div(nleaf, 128), 128, 0, c->stream>>>(c->lv, c->leaf, nleaf, d);
   if (c->ntiles > 0)
     k_count_m2l_pairs<<<c->ntiles, FMM_TILE, 0, c->stream>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact,
                                                              c->lv, d);
   FMM_CUDA(c, cudaGetLastError());
-  FMM_CUDA(c, cudaMemcpyAsync(out, d, 12 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(out, d, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   return FMM_OK;
 }

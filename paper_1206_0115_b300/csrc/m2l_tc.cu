@@ -21,18 +21,18 @@
 // Precision: 3xTF32 -- multipoles and operators are TF32 hi/lo pairs and each
 // K-step issues hi*hi + hi*lo + lo*hi into the same FP32 accumulator.
 //
-// Roles (one CTA per SM, 288 threads, persistent over the units):
-//   warps 0-3  producers: per stage (16 source coefficients of one t) each
-//              thread loads its target row's 16 multipole coefficients (hi and
-//              lo, four 16-byte loads each) and stores them in the 64-byte
-//              swizzle pattern, then fences the async proxy and arrives; one
+// Roles (one CTA per SM, 544 threads, persistent over the units):
+//   warps 0-11 producers in three sets of four warps taking turns per stage
+//              (16 source coefficients of one t): thread r loads its target
+//              row's 16 multipole coefficients (hi and lo, two 32-byte loads
+//              each) and writes them into its own TMEM lane r (tcgen05.st), so
+//              the gathered operand A never passes through shared memory; one
 //              thread also issues the B slab K_t[0..cpad)[k0..k0+16) as 2-D
-//              tiled TMA loads (64-byte swizzle, 512-byte aligned targets).
-//              A 4-row TMA gather would land on 256-byte boundaries, short of
-//              the 512-byte alignment a 64-byte-swizzled TMA target needs;
-//   warps 4-7  epilogue: tcgen05.ld of each accumulator into the running
-//              sums, stores of the sums to the unit's slice;
-//   warp 8     TMEM allocation and the tcgen05.mma issuer (one thread).
+//              tiled TMA loads into shared memory (64-byte swizzle).  The MMA
+//              reads A from TMEM and B from shared memory;
+//   warps 12-15 epilogue (one per TMEM lane quarter): tcgen05.ld of each
+//              accumulator into the running sums, the sums to the unit's slice;
+//   warp 16    TMEM allocation and the tcgen05.mma issuer (one thread).
 // Every mbarrier wait is bounded in time; on expiry the CTA raises the error
 // word, drains what it has in flight (again bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -46,8 +46,10 @@ namespace fmm {
 
 namespace {
 
-constexpr int TC_THREADS = 288;  // warps 0-3 producers, 4-7 epilogue, 8 MMA issuer
-constexpr int TC_MMA_WARP = 8;
+constexpr int TC_SETS = 3;                      // producer sets of 4 warps, one stage each in turn
+constexpr int TC_EPI_WARP = 4 * TC_SETS;         // first of the 4 epilogue warps
+constexpr int TC_MMA_WARP = TC_EPI_WARP + 4;     // the MMA issuer
+constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);
 constexpr int TC_KC = 16;      // K elements per stage (64-byte rows)
 constexpr int TC_MAXST = 4;    // pipeline stages at most
 constexpr int TC_A_BYTES = FMM_TILE * TC_KC * 4;   // one half (hi or lo) of A: 8 KB
@@ -128,6 +130,30 @@ __device__ inline void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, 
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
+// D (+)= A * B with A in tensor memory (rows = lanes, one TF32 per column).
+__device__ inline void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 bytes from global memory (read-only path); the address must be 32-byte aligned.
+__device__ inline void ld_v8(const float* p, uint32_t* v) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "l"(p));
+}
+// Each thread of the warp writes 16 consecutive columns of its own TMEM lane.
+__device__ inline void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 __device__ inline void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -172,7 +198,8 @@ struct TcArgs {
   float* partial;  // [group][tile][128][cpad]
   int32_t* err;    // nonzero after a timed-out wait
   int ntiles, groups, gt, cpad, nh, nhalf, kchunks, nst;
-  uint32_t tmem_cols;  // power of two >= 2 * nhalf (two accumulators)
+  uint32_t acol;       // first TMEM column of the A stages (after the two accumulators)
+  uint32_t tmem_cols;  // power of two >= 2 * nhalf + 32 * nst
 };
 
 // Work unit u -> (group g, column half h, tile): groups outermost so that the
@@ -193,7 +220,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
   const uint32_t b_bytes = (uint32_t)a.nhalf * TC_KC * 4;      // one half (hi or lo) of B
-  const uint32_t stage_bytes = 2u * TC_A_BYTES + 2u * b_bytes;
+  const uint32_t stage_bytes = 2u * b_bytes;
   const uint32_t sum_off = (uint32_t)a.nst * stage_bytes;     // running sums S[col][row], FP32
   const uint32_t bars = base + sum_off + (uint32_t)a.nhalf * FMM_TILE * 4u;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -234,14 +261,17 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
   const uint32_t tmem = *tmem_slot;
   const int nunits = a.ntiles * a.nh * a.groups;
 
-  if (warp < 4) {
+  if (warp < TC_EPI_WARP) {
     // ------------------------------------------------------------ producers
-    // thread r gathers A row r (the source multipole of target r for the
+    // Set k (warps 4k .. 4k+3) fills the stages j with j % TC_SETS == k, so
+    // three stages' worth of gathered loads are in flight at once.  Thread r
+    // of a set gathers A row r (the source multipole of target r for the
     // current t) with plain 16-byte loads and stores it in the 64-byte swizzle
     // pattern: chunk c of row r goes to chunk c ^ ((r >> 1) & 3).
-    const int r = threadIdx.x;
+    const int set = warp >> 2;
+    const int r = threadIdx.x & (FMM_TILE - 1);
     const uint32_t rsw = (uint32_t)((r >> 1) & 3);
-    uint32_t it = 0;
+    uint32_t it = 0, last = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
       int g, h, tile;
@@ -252,20 +282,26 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       const Tile tl = a.tiles[tile];
       const int64_t rbase = lv.row_off[tl.level];
       for (int ai = a0; ai < a1 && ok; ++ai) {
+        // stages of this transfer vector owned by the set
+        const uint32_t kc0 = (uint32_t)((set - (int)(it % TC_SETS) + TC_SETS) % TC_SETS);
+        if ((int)kc0 >= a.kchunks) {
+          it += a.kchunks;
+          continue;
+        }
         const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
         const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
         const int64_t src = rbase + a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
-        const float4* ghi = (const float4*)(Mhi + src * a.cpad);
-        const float4* glo = (const float4*)(Mlo + src * a.cpad);
-        for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
-          float4 vh[4], vl[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            vh[c] = ghi[kc * 4 + c];
-            vl[c] = glo[kc * 4 + c];
-          }
-          const int s = (int)(it % a.nst);
-          const uint32_t ph = (it / a.nst) & 1u;
+        const float* ghi = Mhi + src * a.cpad;
+        const float* glo = Mlo + src * a.cpad;
+        for (int kc = (int)kc0; kc < a.kchunks; kc += TC_SETS) {
+          const uint32_t j = it + (uint32_t)kc;
+          uint32_t vh[16], vl[16];
+          ld_v8((const float*)ghi + kc * TC_KC, vh);
+          ld_v8((const float*)ghi + kc * TC_KC + 8, vh + 8);
+          ld_v8((const float*)glo + kc * TC_KC, vl);
+          ld_v8((const float*)glo + kc * TC_KC + 8, vl + 8);
+          const int s = (int)(j % a.nst);
+          const uint32_t ph = (j / a.nst) & 1u;
           if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
             ok = false;
             break;
@@ -274,30 +310,29 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
           if (r == 0) {
             mbar_expect_tx(full(s), 2u * b_bytes);
             const int y = slot * a.cpad + h * a.nhalf;
-            tma_2d(st + 2u * TC_A_BYTES, &tm_khi, kc * TC_KC, y, full(s));
-            tma_2d(st + 2u * TC_A_BYTES + b_bytes, &tm_klo, kc * TC_KC, y, full(s));
+            tma_2d(st, &tm_khi, kc * TC_KC, y, full(s));
+            tma_2d(st + b_bytes, &tm_klo, kc * TC_KC, y, full(s));
           }
-          unsigned char* sa = gbase + (st - base) + (uint32_t)r * 64u;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint32_t o = (((uint32_t)c ^ rsw) << 4);
-            *(float4*)(sa + o) = vh[c];
-            *(float4*)(sa + TC_A_BYTES + o) = vl[c];
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          // A row r -> TMEM lane r: hi in columns [0, 16), lo in [16, 32) of the stage's slot
+          const uint32_t ta = tmem + ((uint32_t)(r & ~31) << 16) + a.acol + (uint32_t)s * 32u;
+          tmem_st16(ta, vh);
+          tmem_st16(ta + 16u, vl);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tc_fence_before();
           mbar_arrive(full(s));
+          last = j + 1;
         }
+        it += a.kchunks;
       }
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
       atomicOr(a.err, 1);
     }
-    // let the operator copies already issued land before the CTA leaves (bounded)
+    // let the operator copies this set issued land before the CTA leaves (bounded)
     if (!ok && r == 0) {
-      const uint32_t issued = it;
-      for (uint32_t j = issued > (uint32_t)a.nst ? issued - a.nst : 0; j < issued; ++j)
-        mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
+      for (uint32_t j = last > (uint32_t)a.nst ? last - a.nst : 0; j < last; ++j)
+        if ((int)(j % TC_SETS) == set) mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
     }
     __syncwarp();
   } else if (warp == TC_MMA_WARP) {
@@ -331,15 +366,15 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
           tc_fence_after();
           if (lane == 0) {
             const uint32_t st = base + (uint32_t)s * stage_bytes;
+            const uint32_t ahi0 = tmem + a.acol + (uint32_t)s * 32u;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t ahi = sdesc_sw64(st + ks * 32u);
-              const uint64_t alo = sdesc_sw64(st + TC_A_BYTES + ks * 32u);
-              const uint64_t bhi = sdesc_sw64(st + 2u * TC_A_BYTES + ks * 32u);
-              const uint64_t blo = sdesc_sw64(st + 2u * TC_A_BYTES + b_bytes + ks * 32u);
-              mma_tf32(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-              mma_tf32(d, ahi, blo, idesc, 1u);
-              mma_tf32(d, alo, bhi, idesc, 1u);
+              const uint32_t ahi = ahi0 + ks * 8u, alo = ahi0 + 16u + ks * 8u;
+              const uint64_t bhi = sdesc_sw64(st + ks * 32u);
+              const uint64_t blo = sdesc_sw64(st + b_bytes + ks * 32u);
+              mma_tf32_ta(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+              mma_tf32_ta(d, ahi, blo, idesc, 1u);
+              mma_tf32_ta(d, alo, bhi, idesc, 1u);
             }
             mma_commit(empty(s));
           }
@@ -360,8 +395,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       mbar_wait(mma_done, 0);
     }
     __syncwarp();
-  } else if (warp >= 4 && warp < 8) {
-    // ------------------------------------------------------------ epilogue (warps 4-7)
+  } else if (warp < TC_MMA_WARP) {
+    // ------------------------------------------------------------ epilogue (warps 12-15)
     // S[col][row] += accumulator of each transfer vector (FP32, round to
     // nearest); at the end of the unit S goes to the unit's partial slice.
     const int q = warp & 3, row = q * 32 + lane;
@@ -474,7 +509,7 @@ namespace {
 constexpr int TC_GT = 64;  // transfer vectors per work unit
 constexpr int TC_GROUPS = (FMM_NT_CLASS + TC_GT - 1) / TC_GT;
 int tc_nh(int cp) { return cp > 256 ? 2 : 1; }
-int tc_stage_bytes(int cp) { return 2 * TC_A_BYTES + 2 * (cp / tc_nh(cp)) * TC_KC * 4; }
+int tc_stage_bytes(int cp) { return 2 * (cp / tc_nh(cp)) * TC_KC * 4; }
 int tc_fixed_bytes(int cp) { return (cp / tc_nh(cp)) * FMM_TILE * 4 + 1024 + 256; }  // sums, alignment, barriers
 }  // namespace
 
@@ -509,6 +544,8 @@ fmm_status m2l_tc_prepare(Ctx* c) {
     c->tm_khi_ptr = c->Khi;
   }
   int nst = (227 * 1024 - tc_fixed_bytes(cp)) / tc_stage_bytes(cp);
+  const int tmem_stages = (512 - 2 * (cp / tc_nh(cp))) / 32;  // A stages beside the two accumulators
+  if (nst > tmem_stages) nst = tmem_stages;
   if (nst > TC_MAXST) nst = TC_MAXST;
   if (nst < 2) return set_err(c, FMM_ERR_ARG, "M2L tensor path: stage too large for cpad %d", cp);
   c->tc_nst = nst;
@@ -543,8 +580,9 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   a.nhalf = nhalf;
   a.kchunks = cp / TC_KC;
   a.nst = c->tc_nst;
+  a.acol = (uint32_t)(2 * nhalf);
   a.tmem_cols = 32;
-  while ((int)a.tmem_cols < 2 * nhalf) a.tmem_cols <<= 1;
+  while ((int)a.tmem_cols < 2 * nhalf + 32 * c->tc_nst) a.tmem_cols <<= 1;
   const int smem = c->tc_nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
   const int nunits = c->ntiles * nh * TC_GROUPS;
   const int grid = nunits < c->num_sms ? nunits : c->num_sms;

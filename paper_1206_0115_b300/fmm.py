@@ -149,7 +149,7 @@ def fmm_get_stats(h) -> np.ndarray:
 
 
 def fmm_get_work(h) -> np.ndarray:
-    out = np.zeros(12, dtype=np.int64)
+    out = np.zeros(16, dtype=np.int64)
     _check(h, lib.fmm_get_work(h, _ptr(out)))
     return out
 
