@@ -4,8 +4,8 @@
 // one CUDA graph per tree shape and precision, captured on an internal stream
 // and replayed on the caller's stream:
 //
-//     fork --> P2P ------------------------------------------.
-//       \--> P2M --> M2M (leaf-1 .. 2) --> M2L (all levels) --> L2L (2 .. leaf-1) --> join
+//     P2M --> M2M (leaf-1 .. 2) --> fork --> M2L (all levels) --> L2L (2 .. leaf-1) --> join
+//                                      \--> P2P -------------------------------------'
 //
 // followed by one plain launch of L2P, which adds the near field and scatters
 // phi and F to the caller's order (its arguments are the caller's output
@@ -96,16 +96,18 @@ fmm_status deliver(Ctx* c, void* dst, const void* devsrc, int64_t n) {
 }
 
 fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
+  // upward pass first; then P2P on the side branch overlaps M2L and L2L (the
+  // persistent tensor-core M2L leaves room on every SM for P2P blocks)
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
+  FMM_TRY(launch_upward(c, s));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
   FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
+  FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
   FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], c->side, cudaEventRecordExternal));
   FMM_TRY(launch_p2p(c, c->side));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], c->side, cudaEventRecordExternal));
   FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
-  FMM_TRY(launch_upward(c, s));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
-  FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
   FMM_TRY(launch_l2l(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[4], s, cudaEventRecordExternal));

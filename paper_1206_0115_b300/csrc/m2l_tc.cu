@@ -454,17 +454,20 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
 }
 
 // L_T[m] = (1/a) * sum over the tile's groups of the partial sums (FP64).
+// Block (tile, slice): rows 16*slice .. 16*slice+15 of the tile.
 __global__ void __launch_bounds__(256)
 k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_nact, LevelPtrs lv, int ntiles,
                 int gt, int cpad, int ncol, const float* __restrict__ partial, float* __restrict__ L,
                 const double* __restrict__ box) {
-  const int tile = blockIdx.x;
+  const int tile = blockIdx.x, r0 = blockIdx.y * 16;
   const Tile tl = tiles[tile];
+  if (r0 >= tl.count) return;
+  const int nrow = min(16, tl.count - r0);
   const int ng = (tile_nact[tile] + gt - 1) / gt;
   const double inv_a = ldexp(1.0, tl.level + 1) / box[3];
   const int64_t rbase = lv.row_off[tl.level];
-  for (int idx = threadIdx.x; idx < tl.count * ncol; idx += blockDim.x) {
-    const int row = idx / ncol, col = idx - row * ncol;
+  for (int idx = threadIdx.x; idx < nrow * ncol; idx += blockDim.x) {
+    const int row = r0 + idx / ncol, col = idx % ncol;
     double s = 0.0;
     for (int g = 0; g < ng; ++g) s += (double)partial[(((int64_t)g * ntiles + tile) * FMM_TILE + row) * cpad + col];
     const int cell = lv.cls[tl.level][tl.first + row];
@@ -590,7 +593,7 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
                                           c->lv, c->Mhi, c->Mlo);
   FMM_CUDA(c, cudaGetLastError());
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
-  k_m2l_tc_reduce<<<c->ntiles, 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, TC_GT, cp, c->ncoef + 1,
+  k_m2l_tc_reduce<<<dim3(c->ntiles, FMM_TILE / 16), 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, TC_GT, cp, c->ncoef + 1,
                                             c->tc_partial, c->L32, c->box);
   return cuda_err(c, cudaGetLastError(), "M2L tensor-core launch");
 }

@@ -78,22 +78,38 @@ k_bbox_partial(int64_t n, const double* __restrict__ xyz, const double* __restri
 }
 
 // Root cube: corner = minimum per axis, side = largest extent (1 if zero).
-__global__ void k_bbox_final(int nblocks, const double* __restrict__ part, double* __restrict__ box) {
-  if (threadIdx.x != 0) return;
-  double mn[3], mx[3];
-  for (int d = 0; d < 3; ++d) {
-    mn[d] = part[d];
-    mx[d] = part[3 + d];
-  }
-  for (int b = 1; b < nblocks; ++b)
+// One block reduces the per-block partials (min and max are exact in any order).
+__global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* __restrict__ part,
+                                                    double* __restrict__ box) {
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
     for (int d = 0; d < 3; ++d) {
       mn[d] = fmin(mn[d], part[6 * b + d]);
       mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
     }
-  double w = 0.0;
-  for (int d = 0; d < 3; ++d) w = fmax(w, __dsub_rn(mx[d], mn[d]));
-  for (int d = 0; d < 3; ++d) box[d] = mn[d];
-  box[3] = (w > 0.0) ? w : 1.0;
+  __shared__ double s[2][3][8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = 0; d < 3; ++d) {
+    const double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    if (lane == 0) {
+      s[0][d][w] = a;
+      s[1][d][w] = b;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double w3 = 0.0, lo[3];
+  for (int d = 0; d < 3; ++d) {
+    double a = s[0][d][0], b = s[1][d][0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      a = fmin(a, s[0][d][k]);
+      b = fmax(b, s[1][d][k]);
+    }
+    lo[d] = a;
+    w3 = fmax(w3, __dsub_rn(b, a));
+  }
+  for (int d = 0; d < 3; ++d) box[d] = lo[d];
+  box[3] = (w3 > 0.0) ? w3 : 1.0;
 }
 
 // Leaf-level key: per axis floor(((x - lo) / W) * 2^leaf) clamped to the cube.
@@ -601,7 +617,7 @@ extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int
   // positions only: the charge check of the cube kernel re-reads coordinates
   if (e == cudaSuccess) {
     k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, xyz, part, counters);
-    k_bbox_final<<<1, 32, 0, s>>>(nbb, part, box);
+    k_bbox_final<<<1, 256, 0, s>>>(nbb, part, box);
     k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, box, Lf, ka, va);
     const int ntiles = ceil_div(n, RS_TILE);
     for (int sh = 0; sh < 3 * Lf; sh += 8) {
@@ -664,7 +680,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     if (nbb > 1184) nbb = 1184;
     double* part = (double*)c->scratch;
     k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, q, part, c->counters);
-    k_bbox_final<<<1, 32, 0, s>>>(nbb, part, c->box);
+    k_bbox_final<<<1, 256, 0, s>>>(nbb, part, c->box);
     // keys
     k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, c->box, Lf, c->key_a, c->idx_a);
     c->launches_set += 3;
