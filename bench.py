@@ -124,6 +124,41 @@ def dist_env():
     return ws, rank, local
 
 
+def profiled_traffic(kernel_file: str, profile: str, marker: str):
+    """DRAM bytes per launch recorded in a profiles/ summary, or None when the
+    kernel source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        src = open(os.path.join(ROOT, kernel_file)).read()
+        text = open(os.path.join(ROOT, profile)).read()
+    except OSError:
+        return None
+    cut = src.find(marker)
+    h = hashlib.sha256((src[:cut] if cut >= 0 else src).encode()).hexdigest()
+    m = re.search(r"kernel-source-sha256: ([0-9a-f]{64})", text)
+    t = re.search(r"dram-traffic-bytes-per-launch \| (\d+)", text)
+    if not m or not t or m.group(1) != h:
+        return None
+    return int(t.group(1))
+
+
+def replica_throughput(n_local: int, steps: int, local_ms: float, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank solved `steps`
+    problems of n_local particles in local_ms; the job took as long as the
+    slowest rank.  Returns (particles per second, max ms over ranks)."""
+    ws = 1
+    max_ms = float(local_ms)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        t = torch.tensor([max_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    return n_local * ws * steps / (max_ms / 1e3), max_ms
+
+
 def cpu_baseline(sample: dict, reps: int = 1):
     """The FP64 oracle's FMM on a bounded, density-matched sample."""
     import oracle
@@ -237,12 +272,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * ws * args.steps / (total_ms / 1e3)
+    value, total_ms = replica_throughput(n, args.steps, sum(ms), device=dev)
 
     # end to end through the same calls with pinned host buffers
     xyz_h = torch.from_numpy(xyz_np).pin_memory()
@@ -261,12 +291,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if k > 0:
             e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e_ms) if e_ms else float("nan")
-    if ws > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * ws * len(e_ms) / (e2e_total / 1e3) if e_ms else None
+    e2e_value = replica_throughput(n, len(e_ms), sum(e_ms), device=dev)[0] if e_ms else None
 
     if rank != 0:
         f.close()
@@ -322,7 +347,11 @@ def run_ours(args):
         "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), leaf level",
                                 "k_m2l_simt<float> (FP32 CUDA cores), leaf level",
                                 "k_m2l_tc (tcgen05, 3xTF32), all levels"][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu",
+                                                 "profiles/m2l_tc_cube_n1m_h6_p7.md",
+                                                 "// L_T[m] = (1/a) * sum over the tile's groups")
+                     if tc_path and args.workload == WORKLOAD else None,
                      "algorithmic": f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per launch",
                      "peak_source": peak_note},
         "tensor_pipe": tensor_pipe,
