@@ -44,6 +44,10 @@ REFERENCE_STEP_SAMPLE = dict(n=15_625, height=4, order=7, dist="cube", qkind="sy
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates
+# FP32-pipe operations of one P2P interaction in k_p2p: 3 subtractions, the
+# squared distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential
+# sum (1) and the field sums (3 FMA); 1/sqrt runs on the MUFU pipe
+P2P_FP32_OPS = 13
 
 
 def parse():
@@ -249,6 +253,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     work = fmm.fmm_get_work(f.h)
     stats = f.stats()
+    # stage times with every stage run alone (P2P normally overlaps M2L), for
+    # the per-kernel rooflines; outside the timed region
+    fmm.fmm_set_timing(f.h, 2)
+    iso = []
+    for _ in range(3):
+        step()
+        iso.append(fmm.fmm_get_stage_times(f.h).tolist())
+    iso = np.median(np.array(iso), axis=0)
+    fmm.fmm_set_timing(f.h, 1)
+    step()
+    torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -303,7 +318,7 @@ def run_ours(args):
     C = p ** 3
     stage = np.array(stage)
     m2l_leaf_ms = float(np.mean(stage[:, 2]))
-    p2p_ms = float(np.mean(stage[:, 5]))
+    p2p_ms = float(iso[5])  # P2P alone
     m2l_kind = int(stats[4])  # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
     # the tensor-core kernel covers every level in one launch, the CUDA-core
     # kernels time the leaf level separately (stage [2] of fmm_get_stage_times)
@@ -344,6 +359,8 @@ def run_ours(args):
                      "m2l_leaf": m2l_leaf_ms, "m2l_coarse": float(np.mean(stage[:, 3])),
                      "l2l": float(np.mean(stage[:, 4])), "p2p": p2p_ms, "l2p_out": float(np.mean(stage[:, 6])),
                      "evaluate": float(np.mean(stage[:, 7]))},
+        "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
+                              "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
         "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), leaf level",
                                 "k_m2l_simt<float> (FP32 CUDA cores), leaf level",
                                 "k_m2l_tc (tcgen05, 3xTF32), all levels"][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
@@ -355,9 +372,12 @@ def run_ours(args):
                      "algorithmic": f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per launch",
                      "peak_source": peak_note},
         "tensor_pipe": tensor_pipe,
-        "roofline_p2p": {"bound": "alu", "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
+        "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)",
+                         "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
                          "interactions": p2p_pairs,
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
+                         "fp32_ops_per_interaction": P2P_FP32_OPS,
+                         "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2),
                          "peak_fp32_tflops": fp32_peak},
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),

@@ -149,11 +149,15 @@ fmm_status fmm_get_work(fmm_handle h, int64_t* out);
  * [0] upward pass (P2M + M2M), [1] M2L (all levels), [2] the main M2L
  * kernel (CUDA-core kernels: the leaf level; tensor-core kernel: every
  * level), [3] the rest of M2L (coarser levels; or the FP64 reduction of the
- * tensor-core partial sums), [4] L2L (all levels),
- * [5] P2P (on the parallel branch), [6] L2P + output, [7] whole evaluation.  fmm_set_timing(h, 1) turns the events on (the
- * evaluation graph is rebuilt); this call synchronises the stream.
- * out: 8 floats, host. */
-fmm_status fmm_set_timing(fmm_handle h, int on);
+ * tensor-core partial sums), [4] L2L (all levels), [5] P2P, [6] L2P +
+ * output, [7] whole evaluation.
+ * fmm_set_timing(h, mode) turns the events on (the evaluation graph is
+ * rebuilt): mode 1 keeps the normal schedule, where P2P overlaps M2L and its
+ * time [5] is that of the overlapped branch; mode 2 runs P2P alone before
+ * M2L so that every stage is timed in isolation; mode 0 turns the events
+ * off (FMM_ERR_ARG outside 0..2).  fmm_get_stage_times synchronises the
+ * stream.  out: 8 floats, host. */
+fmm_status fmm_set_timing(fmm_handle h, int mode);
 fmm_status fmm_get_stage_times(fmm_handle h, float* out);
 
 /* Allocation-free Morton ordering (the paper has no counterpart: this entry

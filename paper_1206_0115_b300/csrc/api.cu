@@ -101,12 +101,19 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
   FMM_TRY(launch_upward(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
+  // timing mode 2 runs P2P alone (no overlap) so that every stage is timed in isolation
+  cudaStream_t ps = c->timing == 2 ? s : c->side;
+  if (c->timing == 2) {
+    FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], s, cudaEventRecordExternal));
+    FMM_TRY(launch_p2p(c, s));
+    FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], s, cudaEventRecordExternal));
+  }
   FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
   FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
   FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], c->side, cudaEventRecordExternal));
-  FMM_TRY(launch_p2p(c, c->side));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], c->side, cudaEventRecordExternal));
+  if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], ps, cudaEventRecordExternal));
+  if (c->timing != 2) FMM_TRY(launch_p2p(c, ps));
+  if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], ps, cudaEventRecordExternal));
   FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
   FMM_TRY(launch_l2l(c, s));
@@ -457,10 +464,11 @@ fmm_status fmm_get_work(fmm_handle h, int64_t* out) {
   return work_counts(h, out);
 }
 
-fmm_status fmm_set_timing(fmm_handle h, int on) {
+fmm_status fmm_set_timing(fmm_handle h, int mode) {
   if (!h) return FMM_ERR_ARG;
-  if ((on != 0) != h->timing) {
-    h->timing = on != 0;
+  if (mode < 0 || mode > 2) return set_err(h, FMM_ERR_ARG, "fmm_set_timing: mode %d outside 0..2", mode);
+  if (mode != h->timing) {
+    h->timing = mode;
     h->graph_ok = false;
   }
   return FMM_OK;

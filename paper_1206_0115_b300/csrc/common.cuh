@@ -132,7 +132,7 @@ struct fmm_ctx {
   bool graph_ok = false;
   int graph_precision = -1;
   bool use_graph = true;
-  bool timing = false;
+  int timing = 0;  // 0 off, 1 events in the overlapped schedule, 2 events with P2P run alone
   cudaEvent_t tev[10] = {nullptr};
   bool tev_recorded = false;
 

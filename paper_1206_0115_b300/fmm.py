@@ -154,8 +154,9 @@ def fmm_get_work(h) -> np.ndarray:
     return out
 
 
-def fmm_set_timing(h, on: bool) -> int:
-    return _check(h, lib.fmm_set_timing(h, 1 if on else 0))
+def fmm_set_timing(h, mode) -> int:
+    """0 off, 1 (or True) events in the normal schedule, 2 every stage alone."""
+    return _check(h, lib.fmm_set_timing(h, int(mode)))
 
 
 def fmm_get_stage_times(h) -> np.ndarray:
