@@ -98,16 +98,16 @@ fmm_status deliver(Ctx* c, void* dst, const void* devsrc, int64_t n) {
 fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   // upward pass first; then P2P on the side branch overlaps M2L and L2L (the
   // persistent tensor-core M2L leaves room on every SM for P2P blocks)
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
-  FMM_TRY(launch_upward(c, s));
-  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
-  // timing mode 2 runs P2P alone (no overlap) so that every stage is timed in isolation
+  // timing mode 2 runs P2P alone first (no overlap) so that every stage is timed in isolation
   cudaStream_t ps = c->timing == 2 ? s : c->side;
   if (c->timing == 2) {
     FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], s, cudaEventRecordExternal));
     FMM_TRY(launch_p2p(c, s));
     FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], s, cudaEventRecordExternal));
   }
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
+  FMM_TRY(launch_upward(c, s));
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
   FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
   FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
   FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -124,7 +124,8 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 
 // Everything the captured evaluation graph bakes into its kernel arguments.
 std::vector<int64_t> graph_signature(const Ctx* c) {
-  std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst};
+  std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
+                            c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -277,7 +278,8 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
-  void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pos64, c->pos32, c->pos32lo, c->near32,
+  void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pos64, c->pos32, c->pos32lo, c->p2p_items,
+                  c->near32,
                   c->near64,
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,

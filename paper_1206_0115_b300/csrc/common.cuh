@@ -79,6 +79,9 @@ struct fmm_ctx {
   float4* pos32 = nullptr;
   float4* pos32lo = nullptr;  // rounding residuals of pos32's coordinates (x = hi + lo to ~2^-48)
   float4* near32 = nullptr;
+  int32_t* p2p_items = nullptr;  // per leaf: first P2P work item (batches of 32 targets)
+  int64_t p2p_items_cap = 0;
+  int p2p_nitems = 0;
   double4* near64 = nullptr;
   double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
   int64_t stage_in_cap = 0, stage_out_cap = 0;

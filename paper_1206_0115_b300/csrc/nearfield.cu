@@ -2,7 +2,11 @@
 // the up to 27 near leaves of every leaf (Sec. 2.1.2 near field; Sec. 5's GPU
 // P2P kernel does the same work per group of cells).
 //
-// One warp per target leaf.  The 27 neighbour ranges are looked up in the
+// One warp per work item = one batch of up to 32 targets of a leaf (leaves on
+// a surface differ in occupancy by orders of magnitude, and the per-leaf work
+// grows like its square, so whole leaves per warp leave a long tail of heavy
+// leaves; batches keep the items within a factor of ~27 of each other and
+// let the block scheduler balance them).  The 27 neighbour ranges are looked up in the
 // leaf grid by lanes 0..26 and prefix-summed with shuffles; the warp then
 // streams the concatenated source list through shared memory in chunks
 // (coalesced loads), each lane holding one target.  A leaf with fewer than
@@ -78,17 +82,29 @@ __device__ __forceinline__ void p2p_chunk(const float4* shi, const float4* slo, 
 }
 
 __global__ void __launch_bounds__(P2P_WARPS * 32)
-k_p2p32(LevelPtrs lv, int leaf, int nleaf, const float4* __restrict__ pos32, const float4* __restrict__ pos32lo,
-        const double* __restrict__ box, float4* __restrict__ out) {
+k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+        const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
+        float4* __restrict__ out) {
   __shared__ float4 shi[P2P_WARPS][P2P_CH];
   __shared__ float4 slo[P2P_WARPS][P2P_CH];
   __shared__ int nb_first[P2P_WARPS][27];
   __shared__ int nb_pre[P2P_WARPS][28];
   __shared__ int8_t nb_off[P2P_WARPS][27][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int T = blockIdx.x * P2P_WARPS + warp;
-  if (T >= nleaf) return;
+  const int item = blockIdx.x * P2P_WARPS + warp;
+  if (item >= nitems) return;
+  int T;  // the leaf holding this item: last leaf with items[T] <= item
+  {
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    T = lo;
+  }
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int tb = (item - items[T]) * 32;
   int ix, iy, iz;
   demorton3(lv.key[leaf][T], ix, iy, iz);
   const int top = (1 << leaf) - 1;
@@ -125,7 +141,7 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const float4* __restrict__ pos32, con
   __syncwarp();
   const int own = tc;  // sources [0, own) are the target leaf's particles
 
-  for (int tb = 0; tb < tc; tb += 32) {
+  {
     const int nt = min(32, tc - tb);
     int lg = 0;
     while ((nt << (lg + 1)) <= 32) ++lg;
@@ -191,14 +207,26 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const float4* __restrict__ pos32, con
 
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
-k_p2p64(LevelPtrs lv, int leaf, int nleaf, const double4* __restrict__ pos64, double4* __restrict__ out) {
+k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+        const double4* __restrict__ pos64, double4* __restrict__ out) {
   __shared__ double4 src[P2P_WARPS][P2P_CH];
   __shared__ int nb_first[P2P_WARPS][27];
   __shared__ int nb_pre[P2P_WARPS][28];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int T = blockIdx.x * P2P_WARPS + warp;
-  if (T >= nleaf) return;
+  const int item = blockIdx.x * P2P_WARPS + warp;
+  if (item >= nitems) return;
+  int T;  // the leaf holding this item: last leaf with items[T] <= item
+  {
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    T = lo;
+  }
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int tb = (item - items[T]) * 32;
   int ix, iy, iz;
   demorton3(lv.key[leaf][T], ix, iy, iz);
   const int top = (1 << leaf) - 1;
@@ -225,7 +253,7 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const double4* __restrict__ pos64, do
   }
   if (lane == 0) nb_pre[warp][27] = total;
   __syncwarp();
-  for (int tb = 0; tb < tc; tb += 32) {
+  {
     const int nt = min(32, tc - tb);
     int lg = 0;
     while ((nt << (lg + 1)) <= 32) ++lg;
@@ -275,12 +303,14 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const double4* __restrict__ pos64, do
 
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
-  if (nleaf == 0) return FMM_OK;
+  if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
   if (c->precision == FMM_MIXED)
-    k_p2p32<<<ceil_div(nleaf, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->pos32, c->pos32lo, c->box,
-                                                                  c->near32);
+    k_p2p32<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
+                                                                          c->p2p_nitems, c->pos32, c->pos32lo,
+                                                                          c->box, c->near32);
   else
-    k_p2p64<<<ceil_div(nleaf, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->pos64, c->near64);
+    k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
+                                                                          c->p2p_nitems, c->pos64, c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");
 }
 

@@ -27,6 +27,7 @@ constexpr int U_ITEMS = 8;
 constexpr int U_CHUNK = U_THREADS * U_ITEMS;
 constexpr int CNT_BAD = 127;  // counters[] slot of the non-finite-input flag
 constexpr int CNT_CLS = 16;   // counters[16 + 8 l + c] = cells of class c at level l
+constexpr int CNT_ITEMS = 120;  // counters[120] = P2P work items (leaf, 32-target batch)
 
 __device__ inline double warp_min(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -325,6 +326,16 @@ __global__ void k_counts(const int32_t* __restrict__ nout_ptr, const int32_t* ni
   if (j >= nout) return;
   int64_t e = (j + 1 < nout) ? first[j + 1] : nin;
   count[j] = (int32_t)(e - first[j]);
+}
+
+// Work items of P2P: one per batch of up to 32 targets of a leaf.
+// Slots past the leaf count (up to the capacity bound `cap`) get 0 so the
+// scan over the whole bound yields the right total.
+__global__ void k_p2p_items(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
+                            int32_t* __restrict__ items) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cap) return;
+  items[j] = j < *nleaf_ptr ? (count[j] + 31) >> 5 : 0;
 }
 
 __global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
@@ -673,6 +684,16 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     ub[l] = b < pow8(l) ? b : pow8(l);
     FMM_TRY(ensure_level(c, l, ub[l] > 0 ? ub[l] : 1));
   }
+  if (ub[Lf] + 1 > c->p2p_items_cap) {
+    dfree(c, c->p2p_items, 4 * (size_t)c->p2p_items_cap);
+    c->p2p_items = nullptr;
+    c->p2p_items_cap = 0;
+    void* p;
+    const int64_t cap = ub[Lf] + ub[Lf] / 8 + 64;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+    c->p2p_items = (int32_t*)p;
+    c->p2p_items_cap = cap;
+  }
 
   if (n > 0) {
     // bounding cube
@@ -713,6 +734,10 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       k_grid_set<<<ceil_div(ub[l], 256), 256, 0, s>>>(c->counters + l, ub[l], c->lv.key[l], c->lv.grid[l], 0);
       c->launches_set++;
     }
+    // P2P items: exclusive offsets per leaf, total in counters[CNT_ITEMS]
+    k_p2p_items<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items);
+    k_scan1<int32_t><<<1, 1024, 0, s>>>(c->p2p_items, ub[Lf], c->counters + CNT_ITEMS);
+    c->launches_set += 2;
     if (Lf >= 2) {
       ClassArgs ca;
       for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
@@ -734,6 +759,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     return set_err(c, FMM_ERR_ARG, "fmm_set_particles: non-finite coordinate or charge");
   }
   c->n = n;
+  c->p2p_nitems = n > 0 ? c->counters_h[CNT_ITEMS] : 0;
   if (n > 0) {
     for (int d = 0; d < 4; ++d) c->box_host[d] = c->box_h[d];
   } else {

@@ -99,6 +99,9 @@ WORKLOADS = {
     "cube_n20k_h4_p5": dict(n=20_000, height=4, order=5, dist="cube", qkind="pos", seed=1),
     # 1e6 points in the unit cube, charges in [-1, 1), h = 6, p = 7.
     "cube_n1m_h6_p7": dict(n=1_000_000, height=6, order=7, dist="cube", qkind="sym", seed=2),
+    # 1.25e6 points on the same ellipsoid, h = 7, p = 7 (about the same particles per leaf
+    # as the 1e7-point case one level deeper; a medium-size profiling case).
+    "ellipsoid_n1250k_h7_p7": dict(n=1_250_000, height=7, order=7, dist="ellipsoid", qkind="pos", seed=3),
     # 1e7 points on the (0.5, 0.25, 0.125) ellipsoid, charges in (0, 1], h = 8, p = 7.
     "ellipsoid_n10m_h8_p7": dict(n=10_000_000, height=8, order=7, dist="ellipsoid", qkind="pos", seed=3),
 }
