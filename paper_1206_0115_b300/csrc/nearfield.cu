@@ -13,15 +13,17 @@
 // 16 targets gives each target g = 2, 4, ... lanes that split the sources and
 // are combined with shuffles at the end, so lanes stay busy on sparse leaves.
 //
-// Mixed precision: positions are offsets from the target leaf's centre in
-// leaf widths, held as FP32 hi + FP32 lo (the rounding residual of hi), so a
-// position is known to ~2^-48 leaf widths.  Every pair takes
+// Mixed precision: positions are offsets from the particle's own leaf centre
+// in leaf widths, held as FP32 hi (a multiple of 2^-23, |hi| <= 1/2) + FP32
+// lo (the remainder), so a position is known to ~2^-48 leaf widths.  Every
+// pair takes
 //     d = (x_t,hi - x_s,hi) + (x_t,lo - x_s,lo),
-// the shift of a neighbouring leaf being an exact integer added to x_s,hi
-// when the source is staged; the hi difference of a close pair is exact
-// (Sterbenz), so the distance keeps full FP32 relative accuracy however
-// small it is (a plain FP32 position would carry 2^-25 leaf widths of error,
-// which dominates the force of a particle with a very close neighbour).
+// the shift of a neighbouring leaf (an integer in -1..1) being added to
+// x_s,hi when the source is staged.  On the 2^-23 grid that sum and the hi
+// difference (|.| <= 2) are exact, so the distance keeps full FP32 relative
+// accuracy however small it is, also across leaf faces (a plain FP32
+// position would carry up to 2^-25 leaf widths of error, which dominates the
+// force of a particle with a very close neighbour).
 // 1/r by rsqrtf; per-chunk FP32 sums are added into FP32 totals with Kahan
 // compensation; results are scaled by 1/w (phi) and 1/w^2 (F) at the end.
 // Sources are staged with the target's own leaf first: only those can hold

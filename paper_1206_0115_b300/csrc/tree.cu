@@ -244,8 +244,13 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uin
   double cy = box[1] + ((double)iy + 0.5) * w;
   double cz = box[2] + ((double)iz + 0.5) * w;
   const double vx = (x - cx) / w, vy = (y - cy) / w, vz = (z - cz) / w;
-  const float hx = (float)vx, hy = (float)vy, hz = (float)vz;
-  pos32[r] = make_float4(hx, hy, hz, (float)qq);
+  // hi on the grid of multiples of 2^-23 leaf widths: with |hi| <= 1/2, hi
+  // plus a neighbour shift of +-1 and the difference of two such values
+  // (|.| <= 2) are exact in FP32, which the near field relies on; lo = the
+  // remainder (|lo| <= 2^-24) rounded to FP32.
+  const double Q = 8388608.0, iQ = 1.0 / 8388608.0;
+  const double hx = rint(vx * Q) * iQ, hy = rint(vy * Q) * iQ, hz = rint(vz * Q) * iQ;
+  pos32[r] = make_float4((float)hx, (float)hy, (float)hz, (float)qq);
   pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
 }
 

@@ -202,6 +202,27 @@ def test_mixed_p7_matches_direct_sum(F):
     assert oracle.rel_l2(Fo, Fd) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("shift", [(1, 0, 0), (1, 1, 1), (0, 0, 0)])
+def test_mixed_close_pair_across_leaf_faces(F, shift):
+    """A pair 1e-7 leaf widths apart, straddling the faces of leaves in the
+    directions `shift` ((0, 0, 0): both in one leaf), among 400 others.  The
+    pair dominates both particles' fields, so their per-particle error shows
+    how well the near field resolves the distance of the pair."""
+    h = 4
+    w = 1.0 / 8                     # leaf width: the box is the unit cube
+    xyz, q = inputs.particles(400, 81, "cube", "pos")
+    xyz[0], xyz[1] = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    face = np.array([3 * w, 5 * w, 2 * w]) + np.where(np.array(shift) > 0, 0.0, 0.37 * w)
+    d = 1e-7 * w * np.array([1.0, 0.6, 0.3])
+    xyz[2], xyz[3] = face - 0.5 * d, face + 0.5 * d
+    phi, Fo = _run(F, xyz, q, h, 7, F.FMM_MIXED)
+    pd, Fd = oracle.direct(xyz, q)
+    for i in (2, 3):
+        assert abs(phi[i] - pd[i]) <= TOL_MIXED * abs(pd[i])
+        assert np.linalg.norm(Fo[i] - Fd[i]) <= TOL_MIXED * np.linalg.norm(Fd[i])
+    assert oracle.rel_l2(Fo[4:], Fd[4:]) <= TOL_MIXED
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("h", [1, 2])
 def test_shallow_trees_are_direct_sums(F, precision, h):
