@@ -47,6 +47,13 @@ def lib():
             "ofmm_expansion": (None, [C.c_void_p, C.c_int, C.c_int, _d]),
             "ofmm_evaluate": (None, [C.c_void_p, _d, _d]),
             "ofmm_evaluate_sampled": (None, [C.c_void_p, C.c_int64, _i64, _d, _d]),
+            "ofmm_transfer_symmetry": (None, [_i32, _i32, _i32, _i32]),
+            "ofmm_canonical_index": (C.c_int, [_i32]),
+            "ofmm_node_permutation": (None, [C.c_int, _i32, _i32, _i32]),
+            "ofmm_jacobi_svd": (C.c_int, [C.c_int, _d, _d, _d, _d]),
+            "ofmm_set_m2l_svd": (C.c_int, [C.c_void_p, C.c_double]),
+            "ofmm_svd_rank": (C.c_int, [C.c_void_p, C.c_int]),
+            "ofmm_m2l_apply": (None, [C.c_void_p, _i32, _d, _d]),
             "ofmm_m2l_pair_count": (C.c_int64, [C.c_void_p, C.c_int]),
             "ofmm_coverage": (None, [C.c_void_p, _i32]),
             "ofmm_direct": (None, [C.c_int64, _d, _d, _d, _d]),
@@ -120,10 +127,57 @@ def direct_sampled(xyz, q, idx):
     return phi, F
 
 
-class OracleFMM:
-    """One tree of the oracle: box, keys, sort and levels are built on creation."""
+# SVD-compressed M2L (Sec. 2.1.2): cube symmetries, canonical vectors, Jacobi SVD
 
-    def __init__(self, xyz, q, height: int, order: int):
+def canonical_vectors():
+    """The 16 canonical transfer vectors (0 <= a <= b <= c <= 3, c >= 2), in
+    the order of their index."""
+    return [(a, b, c) for a in range(4) for b in range(a, 4) for c in range(b, 4) if c >= 2]
+
+
+def transfer_symmetry(t):
+    """(that, axis, sign) with t_d = sign[d] * that[axis[d]]."""
+    ti = np.ascontiguousarray(t, dtype=np.int32)
+    that = np.zeros(3, dtype=np.int32)
+    axis = np.zeros(3, dtype=np.int32)
+    sign = np.zeros(3, dtype=np.int32)
+    lib().ofmm_transfer_symmetry(_p(ti, _i32), _p(that, _i32), _p(axis, _i32), _p(sign, _i32))
+    return tuple(int(v) for v in that), axis, sign
+
+
+def canonical_index(that) -> int:
+    a = np.ascontiguousarray(that, dtype=np.int32)
+    return int(lib().ofmm_canonical_index(_p(a, _i32)))
+
+
+def node_permutation(order: int, axis, sign) -> np.ndarray:
+    axis = np.ascontiguousarray(axis, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int32)
+    out = np.zeros(order ** 3, dtype=np.int32)
+    lib().ofmm_node_permutation(order, _p(axis, _i32), _p(sign, _i32), _p(out, _i32))
+    return out
+
+
+def jacobi_svd(A):
+    """(U, s, V, sweeps) with A = U diag(s) V^T (square A)."""
+    A = _f64(A)
+    n = A.shape[0]
+    U = np.zeros((n, n))
+    V = np.zeros((n, n))
+    s = np.zeros(n)
+    sweeps = lib().ofmm_jacobi_svd(n, _p(A, _d), _p(U, _d), _p(s, _d), _p(V, _d))
+    return U, s, V, int(sweeps)
+
+
+class OracleFMM:
+    """One tree of the oracle: box, keys, sort and levels are built on creation.
+
+    svd_eps: None for the full-rank M2L operators; a positive number switches
+    M2L to the 16 SVD-compressed operators truncated at s_i >= svd_eps * s_0
+    (the paper's pairing is svd_eps = 10^-order).
+    """
+
+    def __init__(self, xyz, q, height: int, order: int, svd_eps=None):
         self.xyz = _f64(xyz).reshape(-1, 3)
         self.q = _f64(q)
         self.n = self.xyz.shape[0]
@@ -132,6 +186,20 @@ class OracleFMM:
         self._h = lib().ofmm_create(self.n, _p(self.xyz, _d), _p(self.q, _d), height, order)
         if not self._h:
             raise ValueError("oracle rejected the arguments")
+        self.svd_eps = svd_eps
+        if svd_eps is not None and lib().ofmm_set_m2l_svd(self._h, float(svd_eps)) != 0:
+            raise ValueError("oracle: the compression needs height >= 3 and a converged SVD")
+
+    def svd_ranks(self) -> np.ndarray:
+        return np.array([lib().ofmm_svd_rank(self._h, k) for k in range(16)])
+
+    def m2l_apply(self, t, M) -> np.ndarray:
+        """(operator of transfer vector t at unit half-width) @ M."""
+        ti = np.ascontiguousarray(t, dtype=np.int32)
+        M = _f64(M)
+        out = np.zeros(self.ncoef)
+        lib().ofmm_m2l_apply(self._h, _p(ti, _i32), _p(M, _d), _p(out, _d))
+        return out
 
     def close(self):
         if self._h:

@@ -51,6 +51,13 @@ struct ofmm {
   double* L[MAXH];       /* local expansions [ncell][ncoef] */
   double xbar[MAXP];     /* Chebyshev roots */
   double* K;             /* M2L operators for unit half-width, see m2l_operators() */
+  /* SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator"); svd_eps > 0
+   * selects it.  For the 16 canonical transfer vectors: rank, U_k Sigma_k
+   * [C][rank] and V_k [C][rank]. */
+  double svd_eps;
+  int svd_rank[16];
+  double* svd_US[16];
+  double* svd_V[16];
 };
 
 /* ------------------------------------------------------------------------ */
@@ -339,6 +346,10 @@ void ofmm_destroy(ofmm* c) {
   free(c->x);
   free(c->q);
   free(c->K);
+  for (int k = 0; k < 16; ++k) {
+    free(c->svd_US[k]);
+    free(c->svd_V[k]);
+  }
   free(c);
 }
 
@@ -503,14 +514,253 @@ static void m2l_cell(ofmm* c, int l, int64_t T, int64_t* src, int* tv) {
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator", Table 1)         */
+/* ------------------------------------------------------------------------ */
+
+/* Symmetries of the cube.  A symmetry sigma permutes the axes and flips
+ * signs: (sigma v)_d = sign[d] * v[axis[d]].  Every far transfer vector t is
+ * sigma(that) for the canonical that = |t| sorted ascending (16 distinct
+ * vectors); axis[d] is the position of |t_d| in that ordering (ties by axis
+ * order) and sign[d] = -1 where t_d < 0, else +1. */
+void ofmm_transfer_symmetry(const int* t, int* that, int* axis, int* sign) {
+  int used[3] = {0, 0, 0};
+  int a[3] = {abs(t[0]), abs(t[1]), abs(t[2])};
+  int s[3] = {a[0], a[1], a[2]};
+  /* ascending sort of three values */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j)
+      if (s[j] < s[i]) {
+        int x = s[i];
+        s[i] = s[j];
+        s[j] = x;
+      }
+  for (int d = 0; d < 3; ++d) {
+    that[d] = s[d];
+    sign[d] = t[d] < 0 ? -1 : 1;
+    for (int j = 0; j < 3; ++j)
+      if (!used[j] && s[j] == a[d]) {
+        axis[d] = j;
+        used[j] = 1;
+        break;
+      }
+  }
+}
+
+/* Position of a canonical vector (0 <= a <= b <= c <= 3, c >= 2) in the
+ * lexicographic list (0,0,2), (0,0,3), (0,1,2), ..., (3,3,3); -1 otherwise. */
+int ofmm_canonical_index(const int* that) {
+  int k = 0;
+  for (int a = 0; a <= 3; ++a)
+    for (int b = a; b <= 3; ++b)
+      for (int cc = b; cc <= 3; ++cc) {
+        if (cc < 2) continue;
+        if (that[0] == a && that[1] == b && that[2] == cc) return k;
+        ++k;
+      }
+  return -1;
+}
+
+/* Node multi-index map of a symmetry: sigma maps the node xbar_m to the node
+ * xbar_{sm[m]}, because the roots are symmetric (xbar_{p-1-j} = -xbar_j):
+ * (sigma.m)_d = m_{axis[d]}, or p-1-m_{axis[d]} where sign[d] = -1. */
+void ofmm_node_permutation(int order, const int* axis, const int* sign, int32_t* sm) {
+  int p = order, C = p * p * p;
+  for (int m = 0; m < C; ++m) {
+    int mi[3] = {m / (p * p), (m / p) % p, m % p}, r[3];
+    for (int d = 0; d < 3; ++d) r[d] = sign[d] > 0 ? mi[axis[d]] : p - 1 - mi[axis[d]];
+    sm[m] = (r[0] * p + r[1]) * p + r[2];
+  }
+}
+
+/* One-sided Jacobi SVD (Hestenes): A (n x n, row-major) = U diag(s) V^T with
+ * s descending.  Column pairs (i, j) are rotated, in cyclic order, until
+ * every pair is orthogonal to |a_i . a_j| <= 1e-15 |a_i| |a_j|; then s_j are
+ * the column norms, U the normalised columns and V the accumulated
+ * rotations.  Returns the number of sweeps, or -1 without convergence in 60. */
+int ofmm_jacobi_svd(int n, const double* A, double* U, double* s, double* V) {
+  double* W = (double*)malloc(sizeof(double) * n * n);  /* W[j] = column j */
+  double* Z = (double*)malloc(sizeof(double) * n * n);  /* Z[j] = column j of V */
+  double* nrm = (double*)malloc(sizeof(double) * n);
+  int* ord = (int*)malloc(sizeof(int) * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      W[(size_t)j * n + i] = A[(size_t)i * n + j];
+      Z[(size_t)j * n + i] = i == j ? 1.0 : 0.0;
+    }
+  int sweeps = -1;
+  for (int sweep = 1; sweep <= 60; ++sweep) {
+    int rotated = 0;
+    for (int i = 0; i < n - 1; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        double* wi = W + (size_t)i * n;
+        double* wj = W + (size_t)j * n;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = 0; k < n; ++k) {
+          al += wi[k] * wi[k];
+          be += wj[k] * wj[k];
+          ga += wi[k] * wj[k];
+        }
+        if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+        rotated = 1;
+        /* the rotation that zeroes a_i . a_j */
+        double zeta = (be - al) / (2.0 * ga);
+        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        double* zi = Z + (size_t)i * n;
+        double* zj = Z + (size_t)j * n;
+        for (int k = 0; k < n; ++k) {
+          double x = wi[k], y = wj[k];
+          wi[k] = cs * x - sn * y;
+          wj[k] = sn * x + cs * y;
+          x = zi[k];
+          y = zj[k];
+          zi[k] = cs * x - sn * y;
+          zj[k] = sn * x + cs * y;
+        }
+      }
+    if (!rotated) {
+      sweeps = sweep;
+      break;
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    double q = 0.0;
+    for (int k = 0; k < n; ++k) q += W[(size_t)j * n + k] * W[(size_t)j * n + k];
+    nrm[j] = sqrt(q);
+    ord[j] = j;
+  }
+  /* descending by norm, ties by index (insertion sort) */
+  for (int i = 1; i < n; ++i) {
+    int x = ord[i], k = i - 1;
+    while (k >= 0 && nrm[ord[k]] < nrm[x]) {
+      ord[k + 1] = ord[k];
+      --k;
+    }
+    ord[k + 1] = x;
+  }
+  for (int c = 0; c < n; ++c) {
+    int j = ord[c];
+    s[c] = nrm[j];
+    for (int k = 0; k < n; ++k) {
+      U[(size_t)k * n + c] = nrm[j] > 0.0 ? W[(size_t)j * n + k] / nrm[j] : 0.0;
+      V[(size_t)k * n + c] = Z[(size_t)j * n + k];
+    }
+  }
+  free(W);
+  free(Z);
+  free(nrm);
+  free(ord);
+  return sweeps;
+}
+
+/* The 16 canonical operators K_that (unit half-width, the formula of
+ * m2l_operators), each compressed by its own SVD to the rank
+ * r = #{ i : s_i >= eps * s_0 } (Sec. 2.1.2 with (l, eps) = (Acc, 10^-Acc)). */
+int ofmm_set_m2l_svd(ofmm* c, double eps) {
+  int C = c->ncoef, bad = 0;
+  if (c->leaf < 2 || eps <= 0.0) return -1;
+  c->svd_eps = eps;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+  for (int k = 0; k < 16; ++k) {
+    int that[3], kk = 0;
+    for (int a = 0; a <= 3; ++a)
+      for (int b = a; b <= 3; ++b)
+        for (int cc = b; cc <= 3; ++cc)
+          if (cc >= 2) {
+            if (kk == k) {
+              that[0] = a;
+              that[1] = b;
+              that[2] = cc;
+            }
+            ++kk;
+          }
+    const double* K = c->K + (size_t)tslot(that[0], that[1], that[2]) * C * C;
+    double* U = (double*)malloc(sizeof(double) * C * C);
+    double* V = (double*)malloc(sizeof(double) * C * C);
+    double* s = (double*)malloc(sizeof(double) * C);
+    if (ofmm_jacobi_svd(C, K, U, s, V) < 0) bad += 1;
+    int r = 0;
+    while (r < C && s[r] >= eps * s[0]) ++r;
+    free(c->svd_US[k]);
+    free(c->svd_V[k]);
+    c->svd_rank[k] = r;
+    c->svd_US[k] = (double*)malloc(sizeof(double) * C * (r ? r : 1));
+    c->svd_V[k] = (double*)malloc(sizeof(double) * C * (r ? r : 1));
+    for (int m = 0; m < C; ++m)
+      for (int i = 0; i < r; ++i) {
+        c->svd_US[k][(size_t)m * r + i] = U[(size_t)m * C + i] * s[i];
+        c->svd_V[k][(size_t)m * r + i] = V[(size_t)m * C + i];
+      }
+    free(U);
+    free(V);
+    free(s);
+  }
+  return bad ? -1 : 0;
+}
+
+int ofmm_svd_rank(const ofmm* c, int k) { return (k >= 0 && k < 16 && c->svd_eps > 0.0) ? c->svd_rank[k] : -1; }
+
+/* out += K_t M for transfer vector t at unit half-width, with the operator
+ * the FMM applies: the full K_t, or, with the compression on,
+ *     (K_t M)[sigma.m] = (U_k Sigma_k V_k^T Mt)[m],  Mt[n] = M[sigma.n],
+ * where t = sigma(that) and k indexes that (K_t[sigma.m][sigma.n] = K_that[m][n]
+ * because sigma is an isometry that maps the nodes onto the nodes). */
+void ofmm_m2l_apply(const ofmm* c, const int* t, const double* M, double* out) {
+  int C = c->ncoef;
+  if (c->svd_eps <= 0.0) {
+    const double* K = c->K + (size_t)tslot(t[0], t[1], t[2]) * C * C;
+    for (int m = 0; m < C; ++m) {
+      double s = 0.0;
+      for (int nn = 0; nn < C; ++nn) s += K[(size_t)m * C + nn] * M[nn];
+      out[m] += s;
+    }
+    return;
+  }
+  int that[3], axis[3], sign[3];
+  ofmm_transfer_symmetry(t, that, axis, sign);
+  int k = ofmm_canonical_index(that), r = c->svd_rank[k];
+  int32_t* sm = (int32_t*)malloc(sizeof(int32_t) * C);
+  double* y = (double*)calloc(r ? r : 1, sizeof(double));
+  ofmm_node_permutation(c->order, axis, sign, sm);
+  for (int nn = 0; nn < C; ++nn)
+    for (int i = 0; i < r; ++i) y[i] += c->svd_V[k][(size_t)nn * r + i] * M[sm[nn]];
+  for (int m = 0; m < C; ++m) {
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s += c->svd_US[k][(size_t)m * r + i] * y[i];
+    out[sm[m]] += s;
+  }
+  free(sm);
+  free(y);
+}
+
+/* M2L at one cell with the compressed operators (same sum as m2l_cell). */
+static void m2l_cell_svd(ofmm* c, int l, int64_t T, int64_t* src, int* tv, double* z) {
+  int C = c->ncoef;
+  double a = ldexp(c->width, -l - 1);
+  double* LT = c->L[l] + (size_t)T * C;
+  for (int m = 0; m < C; ++m) LT[m] = 0.0;
+  int nf = far_list(c, l, T, src, tv);
+  for (int k = 0; k < nf; ++k) {
+    for (int m = 0; m < C; ++m) z[m] = 0.0;
+    ofmm_m2l_apply(c, tv + 3 * k, c->M[l] + (size_t)src[k] * C, z);
+    for (int m = 0; m < C; ++m) LT[m] += z[m] / a;
+  }
+}
+
 void ofmm_m2l(ofmm* c) {
   for (int l = 2; l <= c->leaf; ++l) {
 #pragma omp parallel
     {
       int64_t src[216];
       int tv[3 * 216];
+      double* z = (double*)malloc(sizeof(double) * c->ncoef);
 #pragma omp for schedule(dynamic, 4)
-      for (int64_t T = 0; T < c->ncell[l]; ++T) m2l_cell(c, l, T, src, tv);
+      for (int64_t T = 0; T < c->ncell[l]; ++T) {
+        if (c->svd_eps > 0.0) m2l_cell_svd(c, l, T, src, tv, z);
+        else m2l_cell(c, l, T, src, tv);
+      }
+      free(z);
     }
   }
 }
@@ -671,9 +921,14 @@ void ofmm_evaluate_sampled(ofmm* c, int64_t ns, const int64_t* idx, double* phi,
       {
         int64_t src[216];
         int tv[3 * 216];
+        double* z = (double*)malloc(sizeof(double) * c->ncoef);
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t T = 0; T < c->ncell[l]; ++T)
-          if (need[l][T]) m2l_cell(c, l, T, src, tv);
+        for (int64_t T = 0; T < c->ncell[l]; ++T) {
+          if (!need[l][T]) continue;
+          if (c->svd_eps > 0.0) m2l_cell_svd(c, l, T, src, tv, z);
+          else m2l_cell(c, l, T, src, tv);
+        }
+        free(z);
       }
       if (l > 2) {
 #pragma omp parallel for schedule(dynamic, 1)

@@ -77,6 +77,25 @@ void ofmm_evaluate(ofmm* c, double* phi, double* F);
  * downward pass along the sampled leaves' ancestors). */
 void ofmm_evaluate_sampled(ofmm* c, int64_t ns, const int64_t* idx, double* phi, double* F);
 
+/* SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator").
+ * Cube symmetry taking the canonical vector that (|t| sorted ascending) to t:
+ * t_d = sign[d] * that[axis[d]]. */
+void ofmm_transfer_symmetry(const int* t, int* that, int* axis, int* sign);
+/* Index 0..15 of a canonical vector in lexicographic order, else -1. */
+int ofmm_canonical_index(const int* that);
+/* sm[m] = the node index the symmetry (axis, sign) maps node m to. */
+void ofmm_node_permutation(int order, const int* axis, const int* sign, int32_t* sm);
+/* A = U diag(s) V^T, n x n row-major, s descending (one-sided Jacobi).
+ * Returns the number of sweeps, -1 if it did not converge. */
+int ofmm_jacobi_svd(int n, const double* A, double* U, double* s, double* V);
+/* Switches the context's M2L to the 16 compressed operators truncated at
+ * s_i >= eps * s_0 (0 on success; needs height >= 3). */
+int ofmm_set_m2l_svd(ofmm* c, double eps);
+/* Rank of canonical operator k (0..15), -1 if the compression is off. */
+int ofmm_svd_rank(const ofmm* c, int k);
+/* out[C] += (operator of transfer vector t at unit half-width) M[C]. */
+void ofmm_m2l_apply(const ofmm* c, const int* t, const double* M, double* out);
+
 /* Number of ordered (target, source) cell pairs M2L visits at `level`. */
 int64_t ofmm_m2l_pair_count(const ofmm* c, int level);
 /* For every ordered pair of leaves (T, S): how many times the near field

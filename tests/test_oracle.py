@@ -7,6 +7,7 @@ library routines (numpy polynomials, numpy's stable sort), invariants
 (Newton's third law, moment conservation, translation/permutation/scale
 invariance) and brute force on tiny inputs.
 """
+import itertools
 from fractions import Fraction
 
 import numpy as np
@@ -376,3 +377,158 @@ def test_degenerate_inputs():
         oracle.OracleFMM(np.array([[np.nan, 0, 0]]), np.ones(1), 4, 3)
     with pytest.raises(ValueError):
         oracle.OracleFMM(np.zeros((1, 3)), np.ones(1), 0, 3)
+
+
+# ---- SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator", Table 1) ----
+
+def _far_vectors():
+    return [t for t in itertools.product(range(-3, 4), repeat=3) if max(map(abs, t)) >= 2]
+
+
+def _K_formula(t, p):
+    """K_t[m][n] = 1/|2t + xbar_n - xbar_m| (unit half-width), from numpy's
+    Chebyshev roots, for checks of the symmetry map only."""
+    x = np.polynomial.chebyshev.chebpts1(p)[::-1]
+    P = np.array(list(itertools.product(x, x, x)))
+    d = 2.0 * np.asarray(t, dtype=float)[None, None, :] + P[None, :, :] - P[:, None, :]
+    return 1.0 / np.linalg.norm(d, axis=2)
+
+
+def test_jacobi_svd_matches_numpy():
+    """The oracle's one-sided Jacobi SVD against LAPACK (numpy): singular
+    values, reconstruction and orthogonality, on a full-rank matrix and on a
+    numerically rank-10 one (the shape of the M2L operators' spectra)."""
+    rng = np.random.default_rng(7)
+    for A in (rng.standard_normal((40, 40)),
+              rng.standard_normal((40, 10)) @ rng.standard_normal((10, 40))):
+        U, s, V, sweeps = oracle.jacobi_svd(A)
+        assert sweeps > 0
+        ref = np.linalg.svd(A, compute_uv=False)
+        assert np.abs(s - ref).max() <= 1e-13 * ref[0]
+        assert np.all(np.diff(s) <= 0)
+        assert np.abs(U @ np.diag(s) @ V.T - A).max() <= 1e-13 * ref[0]
+        assert np.abs(V.T @ V - np.eye(40)).max() <= 1e-13
+        k = int((s > 1e-10 * s[0]).sum())
+        assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 1e-12
+
+
+def test_canonical_vectors_and_symmetry_orbits():
+    """Sec. 2.1.2: the 316 transfer vectors are images of 16 under the cube's
+    symmetries.  Each t is sign * that[axis] with that sorted, and the number
+    of t per canonical vector equals its orbit size under the 48 symmetries
+    (brute force)."""
+    cv = oracle.canonical_vectors()
+    assert len(cv) == 16 and len(set(cv)) == 16
+    count = {}
+    for t in _far_vectors():
+        that, axis, sign = oracle.transfer_symmetry(t)
+        assert list(that) == sorted(map(abs, t))
+        assert sorted(axis) == [0, 1, 2]
+        assert [sign[d] * that[axis[d]] for d in range(3)] == list(t)
+        k = oracle.canonical_index(that)
+        assert cv[k] == that
+        count[k] = count.get(k, 0) + 1
+    assert sum(count.values()) == 316
+    for k, that in enumerate(cv):
+        orbit = {tuple(s[d] * that[perm[d]] for d in range(3))
+                 for perm in itertools.permutations(range(3))
+                 for s in itertools.product((-1, 1), repeat=3)}
+        assert count[k] == len(orbit)
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_symmetry_maps_canonical_operators(p):
+    """K_t[sigma.m][sigma.n] = K_that[m][n] for every far t: the node map
+    of the symmetry is the one under which the operators coincide (a wrong
+    axis, sign or direction of the map breaks it)."""
+    for t in _far_vectors():
+        that, axis, sign = oracle.transfer_symmetry(t)
+        sm = oracle.node_permutation(p, axis, sign)
+        assert sorted(sm) == list(range(p ** 3))
+        Kt, Kc = _K_formula(t, p), _K_formula(that, p)
+        assert np.abs(Kt[np.ix_(sm, sm)] - Kc).max() <= 1e-15 * Kc.max()
+
+
+@pytest.mark.parametrize("p", [4, 5])
+def test_compressed_operator_error_bound(p):
+    """For every far t, the compressed operator differs from K_t by at most
+    the first dropped singular value: |(K~_t - K_t) M| <= eps s_0 |M| (with
+    eps = 10^-p, truncation at s_i >= eps s_0); the uncompressed operator is
+    K_t itself."""
+    eps = 10.0 ** -p
+    xyz, q = inputs.particles(500, 3, "cube", "pos")
+    rng = np.random.default_rng(p)
+    full = oracle.OracleFMM(xyz, q, 3, p)
+    comp = oracle.OracleFMM(xyz, q, 3, p, svd_eps=eps)
+    try:
+        for t in _far_vectors():
+            M = rng.standard_normal(p ** 3)
+            K = _K_formula(t, p)
+            s0 = np.linalg.svd(K, compute_uv=False)[0]
+            exact = K @ M
+            assert np.abs(full.m2l_apply(t, M) - exact).max() <= 1e-13 * np.abs(exact).max()
+            assert np.linalg.norm(comp.m2l_apply(t, M) - exact) <= 1.01 * eps * s0 * np.linalg.norm(M)
+    finally:
+        full.close()
+        comp.close()
+
+
+def test_svd_ranks_match_table1():
+    """Table 1: the weighted rank of the 16 compressed operators (weights =
+    how many of the 316 transfer vectors each one serves) with (l, eps) =
+    (Acc, 10^-Acc) lies within 5% of the paper's 4.6 / 11.2 / 22.2, and the
+    cost ratio 2 l^3 r16 / r316^2 formed with the paper's r316 within 0.05 of
+    its last column."""
+    xyz, q = inputs.particles(500, 3, "cube", "pos")
+    weight = np.zeros(16)
+    for t in _far_vectors():
+        weight[oracle.canonical_index(oracle.transfer_symmetry(t)[0])] += 1
+    for acc, r316, r16, ratio in (map(float, r) for r in read_golden("svd_ranks_table1.txt")):
+        p = int(acc)
+        with oracle.OracleFMM(xyz, q, 3, p, svd_eps=10.0 ** -p) as o:
+            ranks = o.svd_ranks()
+        # the ranks equal the count of LAPACK singular values above the threshold
+        for k, that in enumerate(oracle.canonical_vectors()):
+            s = np.linalg.svd(_K_formula(that, p), compute_uv=False)
+            assert ranks[k] == int((s >= 10.0 ** -p * s[0]).sum())
+        w = float((weight * ranks).sum() / 316)
+        assert abs(w - r16) <= 0.05 * r16, (p, w)
+        assert abs(2 * p ** 3 * w / r316 ** 2 - ratio) <= 0.05, (p, w)
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6, 7])
+def test_svd_rank_decisions_have_margin(p):
+    """No singular value of a canonical operator lies within 1e-6 (relative)
+    of the threshold 10^-p s_0, so any accurate SVD (the oracle's Jacobi, the
+    CUDA path's) truncates at the same rank."""
+    eps = 10.0 ** -p
+    for that in oracle.canonical_vectors():
+        s = np.linalg.svd(_K_formula(that, p), compute_uv=False)
+        assert np.abs(s / s[0] - eps).min() > 1e-6 * eps
+
+
+def test_svd_fmm_close_to_full_rank_fmm():
+    """The compressed M2L changes the FMM result by less than eps_SVD = 10^-p
+    (relative L2, phi and F) and leaves its error against the direct sum
+    within 10% of the full-rank FMM's."""
+    xyz, q = inputs.particles(6000, 41, "cube", "pos")
+    pd, Fd = oracle.direct(xyz, q)
+    for p in (3, 4, 5, 6):
+        with oracle.OracleFMM(xyz, q, 4, p) as o:
+            pf, Ff = o.evaluate()
+        with oracle.OracleFMM(xyz, q, 4, p, svd_eps=10.0 ** -p) as o:
+            ps, Fs = o.evaluate()
+        assert oracle.rel_l2(ps, pf) <= 10.0 ** -p and oracle.rel_l2(Fs, Ff) <= 10.0 ** -p
+        assert oracle.rel_l2(ps, pd) <= 1.1 * oracle.rel_l2(pf, pd)
+        assert oracle.rel_l2(Fs, Fd) <= 1.1 * oracle.rel_l2(Ff, Fd)
+
+
+def test_svd_sampled_evaluation_matches_full():
+    xyz, q = inputs.particles(4000, 52, "ellipsoid", "sym")
+    idx = np.arange(0, 4000, 37)
+    with oracle.OracleFMM(xyz, q, 5, 4, svd_eps=1e-4) as o:
+        phi, F = o.evaluate()
+    with oracle.OracleFMM(xyz, q, 5, 4, svd_eps=1e-4) as o:
+        ps, Fs = o.evaluate_sampled(idx)
+    assert np.abs(ps - phi[idx]).max() <= 1e-12 * np.abs(phi).max()
+    assert np.abs(Fs - F[idx]).max() <= 1e-12 * np.abs(F).max()
