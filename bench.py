@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--m2l", choices=["full", "svd"], default="full",
+                    help="M2L operators: full-rank K_t, or the SVD-compressed canonical operators (eps = 10^-p)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -163,21 +165,35 @@ def replica_throughput(n_local: int, steps: int, local_ms: float, device="cpu"):
     return n_local * ws * steps / (max_ms / 1e3), max_ms
 
 
-def cpu_baseline(sample: dict, reps: int = 1):
-    """The FP64 oracle's FMM on a bounded, density-matched sample."""
+def oracle_operators(s: dict, m2l: str):
+    """An oracle tree whose compressed M2L operators later trees reuse (the
+    operators depend on the order only, as the GPU path's are computed once
+    per handle); None for the full-rank operators."""
+    if m2l != "svd":
+        return None
+    import oracle
+    from paper_1206_0115_b300 import inputs
+    xyz, q = inputs.particles(64, 1, "cube", "pos")
+    return oracle.OracleFMM(xyz, q, 3, s["order"], svd_eps=10.0 ** -s["order"])
+
+
+def cpu_baseline(sample: dict, m2l: str, reps: int = 1):
+    """The FP64 oracle's FMM on the timed workload (same M2L operators)."""
     import oracle
     from paper_1206_0115_b300 import inputs
     xyz, q = inputs.particles(sample["n"], sample["seed"], sample["dist"], sample["qkind"])
+    ops = oracle_operators(sample, m2l)
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        with oracle.OracleFMM(xyz, q, sample["height"], sample["order"]) as o:
+        with oracle.OracleFMM(xyz, q, sample["height"], sample["order"], svd_from=ops) as o:
             o.evaluate()
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
     return {"value": sample["n"] / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"N={sample['n']} uniform cube, h={sample['height']}, p={sample['order']} "
-                       f"(the timed workload itself), FP64 oracle FMM incl. tree build, {reps} run(s), "
+                       f"(the timed workload itself), FP64 oracle FMM ({m2l} M2L operators, computed "
+                       f"beforehand) incl. tree build, {reps} run(s), "
                        f"{t:.2f} s")}
 
 
@@ -190,8 +206,10 @@ def run_reference(args):
     from paper_1206_0115_b300 import inputs
     xyz, q = inputs.particles(s["n"], s["seed"], s["dist"], s["qkind"])
 
+    ops = oracle_operators(s, args.m2l)
+
     def step():
-        with oracle.OracleFMM(xyz, q, s["height"], s["order"]) as o:
+        with oracle.OracleFMM(xyz, q, s["height"], s["order"], svd_from=ops) as o:
             o.evaluate()
 
     for _ in range(args.warmup):
@@ -204,7 +222,8 @@ def run_reference(args):
     tot = sum(times)
     value = s["n"] * args.steps / tot
     sample = (f"each step: N={s['n']} uniform cube, h={s['height']}, p={s['order']} (same particles per "
-              f"leaf as {args.workload}), FP64 oracle FMM incl. tree build")
+              f"leaf as {args.workload}), FP64 oracle FMM ({args.m2l} M2L operators, computed beforehand) "
+              f"incl. tree build")
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
@@ -235,7 +254,8 @@ def run_ours(args):
     n, h, p = w["n"], w["height"], w["order"]
     prec = fmm.FMM_MIXED if args.precision == "mixed" else fmm.FMM_FP64
     stream = torch.cuda.Stream(device=dev)
-    f = fmm.FMM(h, p, prec, stream=stream)
+    method = fmm.FMM_M2L_SVD if args.m2l == "svd" else fmm.FMM_M2L_FULL
+    f = fmm.FMM(h, p, prec, stream=stream, m2l=method)
     xyz = torch.from_numpy(xyz_np).to(dev)
     q = torch.from_numpy(q_np).to(dev)
     phi = torch.empty(n, dtype=torch.float64, device=dev)
@@ -319,21 +339,30 @@ def run_ours(args):
     stage = np.array(stage)
     m2l_leaf_ms = float(np.mean(stage[:, 2]))
     p2p_ms = float(iso[5])  # P2P alone
-    m2l_kind = int(stats[4])  # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
-    # the tensor-core kernel covers every level in one launch, the CUDA-core
-    # kernels time the leaf level separately (stage [2] of fmm_get_stage_times)
-    m2l_pairs = int(work[1:12].sum()) if m2l_kind == 2 else int(work[1 + (h - 1)])
-    m2l_flop = 2.0 * C * C * m2l_pairs
+    # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank K_t); 3 FP64 SIMT, 4 FP32 SIMT (compressed)
+    m2l_kind = int(stats[4])
+    m2l_pairs = int(work[1:12].sum())
+    if m2l_kind >= 3:
+        # compressed: y = V^T M (2 C r flop) and L += U y (2 C r flop) per pair
+        m2l_flop = 4.0 * C * int(work[13])
+        m2l_alg = f"4 x {C} x sum of pair ranks {int(work[13])} = {m2l_flop:.4g} flop per evaluation"
+    else:
+        m2l_flop = 2.0 * C * C * m2l_pairs
+        m2l_alg = f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per evaluation"
+    # the tensor-core kernel covers every level in one launch (stage [2]; the
+    # FP64 reduction of its partial sums is stage [3]); the CUDA-core kernels
+    # are timed over all levels (stage [1])
+    m2l_ms = m2l_leaf_ms if m2l_kind == 2 else float(np.mean(stage[:, 1]))
     p2p_pairs = int(work[0])
     tc_path = m2l_kind == 2
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if tc_path:
         bound, peak, peak_note = "tensor", pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
-    elif m2l_kind == 1:
+    elif m2l_kind in (1, 4):
         bound, peak, peak_note = "alu", fp32_peak, "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock"
     else:
         bound, peak, peak_note = "alu", fp32_peak / 64.0, "FP64 FMA: FP32 rate / 64 (nominal ratio)"
-    achieved = m2l_flop / (m2l_leaf_ms / 1e3) / 1e12
+    achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
     p2p_gflop = 20.0 * p2p_pairs / 1e9
     tensor_pipe = None
     if tc_path:
@@ -351,6 +380,7 @@ def run_ours(args):
         "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "height": h, "order": p, "precision": args.precision,
+                   "m2l": args.m2l,
                    "distribution": w["dist"], "charges": w["qkind"], "seed": w["seed"],
                    "l2": "flushed between steps (512 MB rewrite outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -361,15 +391,18 @@ def run_ours(args):
                      "evaluate": float(np.mean(stage[:, 7]))},
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
-        "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), leaf level",
-                                "k_m2l_simt<float> (FP32 CUDA cores), leaf level",
-                                "k_m2l_tc (tcgen05, 3xTF32), all levels"][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
+                                "k_m2l_simt<float> (FP32 CUDA cores), all levels",
+                                "k_m2l_tc (tcgen05, 3xTF32), all levels",
+                                "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
+                                "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels",
+                                ][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu",
                                                  "profiles/m2l_tc_cube_n1m_h6_p7.md",
                                                  "// L_T[m] = (1/a) * sum over the tile's groups")
                      if tc_path and args.workload == WORKLOAD else None,
-                     "algorithmic": f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per launch",
+                     "algorithmic": m2l_alg,
                      "peak_source": peak_note},
         "tensor_pipe": tensor_pipe,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)",
@@ -387,7 +420,7 @@ def run_ours(args):
     }
     f.close()
     if ws == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLE)
+        result["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLE, args.m2l)
     print(json.dumps(result))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -53,6 +53,11 @@ typedef enum {
   FMM_MIXED = 1   /* FP32 P2P and expansions, split-TF32 tensor-core M2L, FP32 accumulate */
 } fmm_precision;
 
+typedef enum {
+  FMM_M2L_FULL = 0,  /* the 316 full-rank operators K_t (l^3 x l^3 each) */
+  FMM_M2L_SVD = 1    /* the paper's compressed operators (default), see fmm_set_m2l */
+} fmm_m2l_method;
+
 /* Creates a handle for trees of `height` levels (1..11) and interpolation
  * order `order` (2..10 roots per axis; Sec. 2.1.1, the paper's l).  Allocates
  * the translation operators of Sec. 2.1.1-2.1.2 on the current CUDA device
@@ -72,6 +77,29 @@ fmm_status fmm_set_stream(fmm_handle h, void* cuda_stream);
 
 /* Chooses the arithmetic of later evaluations (default FMM_MIXED). */
 fmm_status fmm_set_precision(fmm_handle h, int precision);
+
+/* Chooses the M2L operators of later evaluations (Sec. 2.1.2).
+ *   FMM_M2L_SVD (default): the "improved M2L operator" of Sec. 2.1.2.  The
+ *     316 operators are images of 16 canonical ones (transfer vectors with
+ *     0 <= t1 <= t2 <= t3) under the cube's symmetries, which permute the
+ *     interpolation nodes; each canonical operator is compressed by its own
+ *     SVD, keeping the singular values s_i >= eps * s_0, and M2L applies
+ *     y = V^T (permuted M), L += (1/a) (permuted U Sigma y).  eps <= 0 selects
+ *     10^-order, the pairing (l, eps) = (Acc, 10^-Acc) of Table 1.  The SVDs
+ *     run once per handle and eps, on the device in FP64 (one-sided Jacobi),
+ *     inside the first evaluation (or fmm_get_svd_ranks).
+ *   FMM_M2L_FULL: the full-rank K_t, so that the order alone sets the
+ *     approximation.
+ * Errors: FMM_ERR_ARG (unknown method, eps >= 1 or NaN). */
+fmm_status fmm_set_m2l(fmm_handle h, int method, double eps);
+
+/* Ranks of the 16 compressed canonical operators, in lexicographic order of
+ * their transfer vectors ((0,0,2), (0,0,3), (0,1,2), ..., (3,3,3)), for the
+ * handle's order and the eps of fmm_set_m2l; computes the SVDs if they are
+ * not there yet (synchronises the stream).  ranks: 16 int32, host.
+ * Errors: FMM_ERR_STATE (height < 3: no M2L), FMM_ERR_CUDA (an SVD did not
+ * converge). */
+fmm_status fmm_get_svd_ranks(fmm_handle h, int32_t* ranks);
 
 /* Loads n particles and builds the tree (Sec. 3.2 subdivision, Sec. 4.2
  * Morton order): root cube = per-axis minimum corner and largest extent
@@ -130,8 +158,10 @@ fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
  * fmm_set_particles, out[1] = kernels launched by one fmm_evaluate
  * (nodes of its CUDA graph + the output launch), out[2] = 1 if evaluations
  * replay a CUDA graph, out[3] = bytes of device memory the handle holds,
- * out[4] = M2L kernel of the current precision (0 = FP64 CUDA cores,
- * 1 = FP32 CUDA cores on split operands, 2 = tcgen05 tensor cores),
+ * out[4] = M2L kernels of the current precision and method (full-rank
+ * operators: 0 = FP64 CUDA cores, 1 = FP32 CUDA cores on split operands,
+ * 2 = tcgen05 tensor cores; compressed operators: 3 = FP64 CUDA cores,
+ * 4 = FP32 CUDA cores),
  * out[5..7] = 0 (reserved).  out: 8 int64, host. */
 fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
 
@@ -140,7 +170,10 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
  * every particle of its up to 27 near leaves, itself excluded), out[1 + l] =
  * M2L (target, source) cell pairs at level l for l = 0 .. 10 (zero outside
  * 2 .. height-1), out[12] = (M2L tile, transfer vector) pairs with at least
- * one source (each is one 128-row block of M2L products), out[13..15] = 0.
+ * one source (each is one 128-row block of M2L products), out[13] = sum
+ * over the M2L pairs of the rank of their compressed operator (0 until the
+ * compressed operators exist; one pair costs 4 * order^3 * rank flop),
+ * out[14..15] = 0.
  * Synchronises the stream.  out: 16 int64, host. */
 fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 

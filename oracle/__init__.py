@@ -53,6 +53,7 @@ def lib():
             "ofmm_jacobi_svd": (C.c_int, [C.c_int, _d, _d, _d, _d]),
             "ofmm_set_m2l_svd": (C.c_int, [C.c_void_p, C.c_double]),
             "ofmm_svd_rank": (C.c_int, [C.c_void_p, C.c_int]),
+            "ofmm_copy_m2l_svd": (C.c_int, [C.c_void_p, C.c_void_p]),
             "ofmm_m2l_apply": (None, [C.c_void_p, _i32, _d, _d]),
             "ofmm_m2l_pair_count": (C.c_int64, [C.c_void_p, C.c_int]),
             "ofmm_coverage": (None, [C.c_void_p, _i32]),
@@ -177,7 +178,7 @@ class OracleFMM:
     (the paper's pairing is svd_eps = 10^-order).
     """
 
-    def __init__(self, xyz, q, height: int, order: int, svd_eps=None):
+    def __init__(self, xyz, q, height: int, order: int, svd_eps=None, svd_from=None):
         self.xyz = _f64(xyz).reshape(-1, 3)
         self.q = _f64(q)
         self.n = self.xyz.shape[0]
@@ -187,7 +188,12 @@ class OracleFMM:
         if not self._h:
             raise ValueError("oracle rejected the arguments")
         self.svd_eps = svd_eps
-        if svd_eps is not None and lib().ofmm_set_m2l_svd(self._h, float(svd_eps)) != 0:
+        if svd_from is not None:
+            # reuse another tree's compressed operators (they depend on order and eps only)
+            self.svd_eps = svd_from.svd_eps
+            if lib().ofmm_copy_m2l_svd(self._h, svd_from._h) != 0:
+                raise ValueError("oracle: cannot share the compressed operators")
+        elif svd_eps is not None and lib().ofmm_set_m2l_svd(self._h, float(svd_eps)) != 0:
             raise ValueError("oracle: the compression needs height >= 3 and a converged SVD")
 
     def svd_ranks(self) -> np.ndarray:

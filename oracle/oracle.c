@@ -699,6 +699,26 @@ int ofmm_set_m2l_svd(ofmm* c, double eps) {
   return bad ? -1 : 0;
 }
 
+/* Copies the compressed operators of `src` (same order) into `dst`, so that a
+ * sequence of trees can share one set of SVDs, as the operators depend on
+ * the order and eps only.  0 on success. */
+int ofmm_copy_m2l_svd(ofmm* dst, const ofmm* src) {
+  int C = dst->ncoef;
+  if (src->svd_eps <= 0.0 || src->order != dst->order || dst->leaf < 2) return -1;
+  dst->svd_eps = src->svd_eps;
+  for (int k = 0; k < 16; ++k) {
+    int r = src->svd_rank[k];
+    free(dst->svd_US[k]);
+    free(dst->svd_V[k]);
+    dst->svd_rank[k] = r;
+    dst->svd_US[k] = (double*)malloc(sizeof(double) * C * (r ? r : 1));
+    dst->svd_V[k] = (double*)malloc(sizeof(double) * C * (r ? r : 1));
+    memcpy(dst->svd_US[k], src->svd_US[k], sizeof(double) * C * r);
+    memcpy(dst->svd_V[k], src->svd_V[k], sizeof(double) * C * r);
+  }
+  return 0;
+}
+
 int ofmm_svd_rank(const ofmm* c, int k) { return (k >= 0 && k < 16 && c->svd_eps > 0.0) ? c->svd_rank[k] : -1; }
 
 /* out += K_t M for transfer vector t at unit half-width, with the operator

@@ -91,6 +91,8 @@ int ofmm_jacobi_svd(int n, const double* A, double* U, double* s, double* V);
 /* Switches the context's M2L to the 16 compressed operators truncated at
  * s_i >= eps * s_0 (0 on success; needs height >= 3). */
 int ofmm_set_m2l_svd(ofmm* c, double eps);
+/* Copies the compressed operators of src (same order) into dst; 0 on success. */
+int ofmm_copy_m2l_svd(ofmm* dst, const ofmm* src);
 /* Rank of canonical operator k (0..15), -1 if the compression is off. */
 int ofmm_svd_rank(const ofmm* c, int k);
 /* out[C] += (operator of transfer vector t at unit half-width) M[C]. */

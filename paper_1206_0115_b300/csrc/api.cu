@@ -138,8 +138,12 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                         (const void*)c->M64, (const void*)c->L64, (const void*)c->tiles, (const void*)c->tile_src,
                         (const void*)c->tile_act, (const void*)c->tile_nact, (const void*)c->K64,
                         (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm,
-                        (const void*)c->tc_partial, (const void*)c->tc_err})
+                        (const void*)c->tc_partial, (const void*)c->tc_err, (const void*)c->svd_Y,
+                        (const void*)c->svd_ybase, (const void*)c->svd_ry, (const void*)c->svd_V64,
+                        (const void*)c->svd_U64, (const void*)c->svd_VThi, (const void*)c->svd_Uhi})
     s.push_back((int64_t)(uintptr_t)p);
+  s.push_back(c->svd_rmax);
+  s.push_back(c->svd_rp);
   return s;
 }
 
@@ -283,7 +287,9 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->near64,
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
-                  c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err};
+                  c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
+                  c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi, c->svd_VTlo,
+                  c->svd_Uhi, c->svd_Ulo, c->svd_ry, c->svd_ybase, c->svd_Y};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
@@ -321,6 +327,30 @@ fmm_status fmm_set_precision(fmm_handle h, int precision) {
   return FMM_OK;
 }
 
+fmm_status fmm_set_m2l(fmm_handle h, int method, double eps) {
+  if (!h) return FMM_ERR_ARG;
+  if (method != FMM_M2L_FULL && method != FMM_M2L_SVD)
+    return set_err(h, FMM_ERR_ARG, "fmm_set_m2l: unknown method %d", method);
+  if (!(eps < 1.0) || eps != eps) return set_err(h, FMM_ERR_ARG, "fmm_set_m2l: eps must be < 1");
+  if (method != h->m2l_method || eps != h->svd_eps) {
+    h->m2l_method = method;
+    h->svd_eps = eps;
+    h->graph_ok = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_get_svd_ranks(fmm_handle h, int32_t* ranks) {
+  if (!h || !ranks) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (c->leaf < 2) return set_err(c, FMM_ERR_STATE, "fmm_get_svd_ranks: height < 3 has no M2L");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  FMM_TRY(svd_prepare(c));
+  for (int k = 0; k < 16; ++k) ranks[k] = c->svd_rank[k];
+  return FMM_OK;
+}
+
 fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const double* q) {
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
@@ -352,8 +382,12 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   if (!phi || !F) return set_err(c, FMM_ERR_ARG, "fmm_evaluate: NULL output");
   FMM_CUDA(c, cudaSetDevice(c->dev));
   FMM_TRY(check_device_error(c));
-  FMM_TRY(operators_m2l(c, c->precision));
-  if (m2l_kind(c) == 2) FMM_TRY(m2l_tc_prepare(c));
+  if (c->m2l_method == FMM_M2L_SVD) {
+    if (c->leaf >= 2) FMM_TRY(m2l_svd_prepare(c));
+  } else {
+    FMM_TRY(operators_m2l(c, c->precision));
+    if (m2l_kind(c) == 2) FMM_TRY(m2l_tc_prepare(c));
+  }
   const bool dev_out = is_device_ptr(phi) && is_device_ptr(F);
   double *dphi = phi, *dF = F;
   if (!dev_out) {

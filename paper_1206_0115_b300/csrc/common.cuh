@@ -150,6 +150,34 @@ struct fmm_ctx {
   const void* tm_khi_ptr = nullptr;
   int tc_smem_set = 0, tc_nst = 0, num_sms = 0;
 
+  // SVD-compressed M2L (m2l_svd.cu)
+  int m2l_method = FMM_M2L_SVD;
+  double svd_eps = 0.0;       // <= 0: 10^-order
+  bool svd_ready = false, svd64 = false, svd32 = false;
+  double svd_eps_used = 0.0;
+  int64_t svd_gen = 0;
+  int svd_rank[16] = {0};
+  int t_rank_h[FMM_NT] = {0};
+  int svd_rmax = 0, svd_rp = 0;
+  double *svd_W = nullptr, *svd_Z = nullptr, *svd_vals = nullptr, *svd_colmean = nullptr;
+  int32_t *svd_ord = nullptr, *svd_rank_d = nullptr, *svd_sweeps_d = nullptr;
+  int16_t* svd_sm = nullptr;
+  int8_t *svd_canon = nullptr, *svd_tcanon = nullptr;
+  double *svd_V64 = nullptr, *svd_U64 = nullptr;  // [316][C][rmax]
+  size_t svd_bank64_bytes = 0;
+  float *svd_VThi = nullptr, *svd_VTlo = nullptr;  // [316][rp][cpad]
+  float *svd_Uhi = nullptr, *svd_Ulo = nullptr;    // [316][cpad][rp], mean-split
+  size_t svd_bank32_bytes = 0;
+  int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_kyoff = nullptr;
+  int64_t* svd_ybase = nullptr;
+  int64_t svd_ybase_cap = 0;
+  void* svd_Y = nullptr;
+  size_t svd_Y_cap = 0;
+  std::vector<int64_t> svd_ysig;
+  std::vector<Tile> tiles_h;     // host copy of the M2L tiles
+  std::vector<int16_t> cls_t_h;  // host copy of cls_t
+  int64_t tree_gen = 0;          // bumped by every tree build
+
   // stats
   int64_t launches_set = 0, launches_eval = 0, bytes = 0;
 };
@@ -182,6 +210,9 @@ fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
 fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
+fmm_status svd_prepare(Ctx* c);        // SVD of the canonical operators (ranks to the host)
+fmm_status m2l_svd_prepare(Ctx* c);    // + factor banks and the Y layout of the current tree
+fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
 bool m2l_tc_supported(const Ctx* c);
 fmm_status m2l_tc_prepare(Ctx* c);
 fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
@@ -192,7 +223,8 @@ fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F);
 fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out);
 int64_t count_launches_eval(const Ctx* c);
 fmm_status work_counts(Ctx* c, int64_t* out);
-int m2l_kind(const Ctx* c);  // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05
+// 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank operators); 3 FP64 SIMT, 4 FP32 SIMT (SVD-compressed)
+int m2l_kind(const Ctx* c);
 
 // ---- device helpers ----------------------------------------------------------
 // Spreads the low 10 bits of v so that bit b lands at bit 3b.

@@ -7,6 +7,7 @@
 namespace fmm {
 
 int m2l_kind(const Ctx* c) {
+  if (c->m2l_method == FMM_M2L_SVD) return c->precision == FMM_FP64 ? 3 : 4;
   if (c->precision == FMM_FP64) return 0;
   return (c->use_tc && m2l_tc_supported(c)) ? 2 : 1;
 }
@@ -16,11 +17,13 @@ fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
     return FMM_OK;
   }
-  if (m2l_kind(c) == 2) return launch_m2l_tc(c, s, mid);
+  const int kind = m2l_kind(c);
+  if (kind == 2) return launch_m2l_tc(c, s, mid);
+  auto run = kind >= 3 ? launch_m2l_svd_simt : launch_m2l_simt;
   // CUDA cores: leaf level, then the coarser levels
-  FMM_TRY(launch_m2l_simt(c, s, 0, c->leaf_tiles));
+  FMM_TRY(run(c, s, 0, c->leaf_tiles));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
-  return launch_m2l_simt(c, s, c->leaf_tiles, c->ntiles - c->leaf_tiles);
+  return run(c, s, c->leaf_tiles, c->ntiles - c->leaf_tiles);
 }
 
 namespace {
@@ -28,18 +31,27 @@ namespace {
 __global__ void __launch_bounds__(FMM_TILE)
 k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
                   const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
+                  const int16_t* __restrict__ cls_t, const int32_t* __restrict__ trank,
                   unsigned long long* __restrict__ out) {
   const Tile tl = tiles[blockIdx.x];
   const int row = threadIdx.x, zero = lv.ncell[tl.level];
   const int nact = tile_nact[blockIdx.x];
-  unsigned long long cnt = 0;
+  unsigned long long cnt = 0, rsum = 0;
   for (int a = 0; a < nact; ++a) {
     const int k = tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a];
     const int s = tile_src[((int64_t)blockIdx.x * FMM_NT_CLASS + k) * FMM_TILE + row];
-    cnt += (row < tl.count && s != zero);
+    const bool pair = row < tl.count && s != zero;
+    cnt += pair;
+    if (trank && pair) rsum += trank[cls_t[tl.cls * FMM_NT_CLASS + k]];
   }
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((row & 31) == 0) atomicAdd(&out[1 + tl.level], cnt);
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+  }
+  if ((row & 31) == 0) {
+    atomicAdd(&out[1 + tl.level], cnt);
+    atomicAdd(&out[13], rsum);
+  }
   if (row == 0) atomicAdd(&out[12], (unsigned long long)nact);
 }
 
@@ -71,7 +83,8 @@ fmm_status work_counts(Ctx* c, int64_t* out) {
   k_count_p2p_pairs<<<ceil_div(nleaf, 128), 128, 0, c->stream>>>(c->lv, c->leaf, nleaf, d);
   if (c->ntiles > 0)
     k_count_m2l_pairs<<<c->ntiles, FMM_TILE, 0, c->stream>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact,
-                                                             c->lv, d);
+                                                             c->lv, c->cls_t, c->svd_ready ? c->svd_trank : nullptr,
+                                                             d);
   FMM_CUDA(c, cudaGetLastError());
   FMM_CUDA(c, cudaMemcpyAsync(out, d, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -83,7 +96,8 @@ int64_t count_launches_eval(const Ctx* c) {
   int64_t k = 2;  // P2P, L2P/output
   if (Lf >= 2 && c->n > 0) {
     k += 1 + (Lf - 2);                                      // P2M, M2M
-    k += m2l_kind(c) == 2 ? 2 * (c->ntiles > 0) : (c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles);  // M2L
+    const int kind = m2l_kind(c), per = kind >= 3 ? 2 : 1;
+    k += kind == 2 ? 2 * (c->ntiles > 0) : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));  // M2L
     k += (Lf - 2);                                          // L2L
   }
   return k;

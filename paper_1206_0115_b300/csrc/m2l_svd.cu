@@ -1,0 +1,654 @@
+// m2l_svd.cu -- the SVD-compressed M2L of Sec. 2.1.2 ("Improved M2L operator").
+//
+// The 316 operators K_t are images of 16 canonical ones under the symmetries
+// of the cube.  With t = sigma(that), sigma permuting the axes and flipping
+// signs ((sigma v)_d = sign_d v_{axis_d}, that = |t| sorted ascending),
+//     K_t[sigma.m][sigma.n] = K_that[m][n],
+// where sigma.m is the node index sigma maps node m to (the Chebyshev roots
+// are symmetric, xbar_{p-1-j} = -xbar_j, so sigma maps nodes onto nodes and
+// distances are unchanged).  Each K_that is compressed by its own SVD,
+// truncated at s_i >= eps s_0 (eps = 10^-p unless the caller sets it: the
+// pairing (l, eps) = (Acc, 10^-Acc) of Table 1).  Per (target T, source S,
+// transfer vector t) the M2L becomes
+//     y = V_t^T M_S,           V_t[sigma.n][i] = V_that[n][i]      (r_t values)
+//     L_T += (1/a) U_t y,      U_t[sigma.m][i] = s_i U_that[m][i],
+// the paper's "16 matrix-matrix products coupled with permutations", with
+// the permutations folded into 316 permuted copies of the 16 factor pairs.
+//
+// Precompute (once per handle and eps; FP64 on the GPU):
+//   k_canon_ops64   the 16 canonical K_that (the formula of operators.cu);
+//   k_svd_jacobi    a one-sided Jacobi SVD per operator: one block, the
+//                   column pairs in round-robin order so that the warps of a
+//                   block rotate disjoint pairs at once, sweeps until no pair
+//                   needs a rotation (|a_i . a_j| <= 1e-15 |a_i| |a_j|), at
+//                   most 60 (a bounded loop; a non-converged operator is an
+//                   error the host reports);
+//   k_svd_order     singular values (column norms), their descending order,
+//                   the rank and, for the mixed banks, the mean of every
+//                   column of U Sigma;
+//   k_svd_banks64 / k_svd_banks32   the permuted factors of all 316 t.
+// Evaluation, per M2L tile (128 targets of one level and child class):
+//   k_m2l_proj    Y[tile][t][row][i] = sum_n V_t[n][i] M_{src(row, t)}[n]
+//   k_m2l_expand  L[row] = (1/a) sum_t sum_i U_t[.][i] Y[tile][t][row][i]
+// The mixed path stores U in the mean-split form of the local expansions
+// (row C = the mean over m of U_t[m][.], rows m < C the deviations), its
+// factors as TF32 hi/lo pairs, and pads every rank to a multiple of 16 with
+// zero factors (the tensor-core granule) -- the result is that of rank r_t.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int SVD_THREADS = 1024;
+constexpr int SVD_MAX_SWEEPS = 60;
+
+__device__ inline float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// K_that[m][n] = 1 / |2 that + xbar_n - xbar_m| for the 16 canonical vectors.
+__global__ void k_canon_ops64(int p, int C, const double* __restrict__ nodes, const int8_t* __restrict__ canon,
+                              double* __restrict__ K) {
+  const int64_t total = (int64_t)16 * C * C;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ((int64_t)C * C));
+    const int rem = (int)(e - (int64_t)k * C * C);
+    const int m = rem / C, nn = rem - m * C;
+    const int mi[3] = {m / (p * p), (m / p) % p, m % p};
+    const int ni[3] = {nn / (p * p), (nn / p) % p, nn % p};
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double r = 2.0 * canon[3 * k + d] + nodes[ni[d]] - nodes[mi[d]];
+      r2 += r * r;
+    }
+    K[e] = 1.0 / sqrt(r2);
+  }
+}
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided Jacobi SVD of the 16 operators (block k = operator k).  W[k][j]
+// starts as column j of K and Z[k][j] as column j of the identity; rotating
+// the pair (i, j) by the angle that makes columns i and j of W orthogonal
+// and applying the same rotation to Z keeps K Z = W.  At convergence the
+// columns of W are s_j u_j and those of Z are v_j.
+__global__ void __launch_bounds__(SVD_THREADS)
+k_svd_jacobi(int C, const double* __restrict__ K, double* __restrict__ W, double* __restrict__ Z,
+             int32_t* __restrict__ sweeps_out) {
+  const int k = blockIdx.x;
+  const double* A = K + (size_t)k * C * C;
+  double* Wk = W + (size_t)k * C * C;
+  double* Zk = Z + (size_t)k * C * C;
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const int j = e / C, i = e - j * C;
+    Wk[e] = A[(size_t)i * C + j];
+    Zk[e] = i == j ? 1.0 : 0.0;
+  }
+  __shared__ int rotated;
+  const int n2 = C + (C & 1);  // an odd C gets a dummy column, paired with nobody
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int done = -1;
+  __syncthreads();
+  for (int sweep = 1; sweep <= SVD_MAX_SWEEPS && done < 0; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < n2 - 1; ++r) {
+      // round r of the circle method: every column in exactly one pair
+      for (int q = warp; q < n2 / 2; q += nw) {
+        int i = q == 0 ? n2 - 1 : (r + q) % (n2 - 1);
+        int j = q == 0 ? r : (r - q + n2 - 1) % (n2 - 1);
+        if (i >= C || j >= C) continue;
+        if (i > j) {
+          const int x = i;
+          i = j;
+          j = x;
+        }
+        double* wi = Wk + (size_t)i * C;
+        double* wj = Wk + (size_t)j * C;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int e = lane; e < C; e += 32) {
+          const double x = wi[e], y = wj[e];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        // butterfly sums: every lane holds the same totals, so the branch is warp-uniform
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        if (lane == 0) rotated = 1;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double* zi = Zk + (size_t)i * C;
+        double* zj = Zk + (size_t)j * C;
+        for (int e = lane; e < C; e += 32) {
+          double x = wi[e], y = wj[e];
+          wi[e] = cs * x - sn * y;
+          wj[e] = sn * x + cs * y;
+          x = zi[e];
+          y = zj[e];
+          zi[e] = cs * x - sn * y;
+          zj[e] = sn * x + cs * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated == 0) done = sweep;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sweeps_out[k] = done;
+}
+
+// Singular values s_j = |W[k][j]|, the descending order ord (ties by index),
+// the rank #{s >= eps s_max}, and the column means of U Sigma (mixed banks).
+__global__ void __launch_bounds__(SVD_THREADS)
+k_svd_order(int C, double eps, const double* __restrict__ W, double* __restrict__ svals,
+            int32_t* __restrict__ ord, int32_t* __restrict__ rank, double* __restrict__ colmean) {
+  __shared__ double sv[FMM_MAX_ORDER * FMM_MAX_ORDER * FMM_MAX_ORDER];
+  const int k = blockIdx.x;
+  const double* Wk = W + (size_t)k * C * C;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    double s = 0.0;
+    for (int e = 0; e < C; ++e) s += Wk[(size_t)j * C + e] * Wk[(size_t)j * C + e];
+    sv[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    int r = 0;
+    for (int i = 0; i < C; ++i) r += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+    ord[k * C + r] = j;
+    svals[k * C + r] = sv[j];
+  }
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int j = 0; j < C; ++j) smax = fmax(smax, sv[j]);
+    int r = 0;
+    for (int j = 0; j < C; ++j) r += sv[j] >= eps * smax;
+    rank[k] = r;
+  }
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    double s = 0.0;
+    for (int e = 0; e < C; ++e) s += Wk[(size_t)j * C + e];
+    colmean[k * C + j] = s / C;
+  }
+}
+
+// FP64 banks [316][C][R]: V_t[sigma.n][i] = Z[k][ord_i][n], U_t[sigma.n][i] =
+// W[k][ord_i][n] for i < rank, 0 beyond.  One thread per (t, n).
+__global__ void k_svd_banks64(int C, int R, const int8_t* __restrict__ t_canon, const int16_t* __restrict__ sm,
+                              const int32_t* __restrict__ ord, const int32_t* __restrict__ rank,
+                              const double* __restrict__ W, const double* __restrict__ Z, double* __restrict__ V64,
+                              double* __restrict__ U64) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)FMM_NT * C) return;
+  const int t = (int)(e / C), n = (int)(e - (int64_t)t * C);
+  const int k = t_canon[t], r = rank[k];
+  const int np = sm[e];
+  for (int i = 0; i < R; ++i) {
+    const int j = i < r ? ord[k * C + i] : 0;
+    V64[((int64_t)t * C + np) * R + i] = i < r ? Z[((size_t)k * C + j) * C + n] : 0.0;
+    U64[((int64_t)t * C + np) * R + i] = i < r ? W[((size_t)k * C + j) * C + n] : 0.0;
+  }
+}
+
+// Mixed banks (TF32 hi/lo; zero-initialised by the caller):
+//   VT[t][i][sigma.n] = V_t, [316][Rp][cpad]  (the projection's B operand, K-major)
+//   U[t][sigma.m][i]  = U_t - mean_m U_t (rows < C), U[t][C][i] = the mean,
+//                       [316][cpad][Rp]       (the expansion's B operand, K-major)
+__global__ void k_svd_banks32(int C, int cpad, int Rp, const int8_t* __restrict__ t_canon,
+                              const int16_t* __restrict__ sm, const int32_t* __restrict__ ord,
+                              const int32_t* __restrict__ rank, const double* __restrict__ W,
+                              const double* __restrict__ Z, const double* __restrict__ colmean,
+                              float* __restrict__ VThi, float* __restrict__ VTlo, float* __restrict__ Uhi,
+                              float* __restrict__ Ulo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)FMM_NT * C) return;
+  const int t = (int)(e / C), n = (int)(e - (int64_t)t * C);
+  const int k = t_canon[t], r = rank[k];
+  const int np = sm[e];
+  for (int i = 0; i < r; ++i) {
+    const int j = ord[k * C + i];
+    const double v = Z[((size_t)k * C + j) * C + n];
+    const double u = W[((size_t)k * C + j) * C + n] - colmean[k * C + j];
+    const int64_t ov = ((int64_t)t * Rp + i) * cpad + np;
+    const int64_t ou = ((int64_t)t * cpad + np) * Rp + i;
+    float h = tf32_rna((float)v);
+    VThi[ov] = h;
+    VTlo[ov] = tf32_rna((float)(v - (double)h));
+    h = tf32_rna((float)u);
+    Uhi[ou] = h;
+    Ulo[ou] = tf32_rna((float)(u - (double)h));
+    if (n == 0) {  // the mean row
+      const double mu = colmean[k * C + j];
+      const int64_t om = ((int64_t)t * cpad + C) * Rp + i;
+      h = tf32_rna((float)mu);
+      Uhi[om] = h;
+      Ulo[om] = tf32_rna((float)(mu - (double)h));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- evaluation
+
+struct SvdArgs {
+  const Tile* tiles;
+  const int32_t* tile_src;
+  const int16_t* tile_act;
+  const int32_t* tile_nact;
+  const int16_t* cls_t;
+  const int32_t* t_ry;       // [316] Y row length (rank; mixed: rounded up to 16)
+  const int32_t* kyoff;      // [8][189] offset of transfer vector k's block in a tile's Y, in rows of 1 value
+  const int64_t* tile_ybase; // [tile] first element of the tile's Y
+};
+
+// Projection: one block per (tile, active transfer vector), one thread per
+// target row: y[i] = sum_n V_t[n][i] M_src[n], V staged in shared memory in
+// chunks of 32 n x 16 i.  FP64 bank [316][C][R]; mixed bank VT hi/lo
+// [316][Rp][cpad], used as the FP32 sum hi + lo.
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(FMM_TILE)
+k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict__ Vb, const T* __restrict__ Vlo,
+           const T* __restrict__ Mhi, const T* __restrict__ Mlo, T* __restrict__ Y) {
+  __shared__ T sV[32][16];
+  const int tile = blockIdx.x, ai = blockIdx.y, row = threadIdx.x;
+  if (ai >= a.tile_nact[tile]) return;
+  const Tile tl = a.tiles[tile];
+  const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
+  const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
+  const int ry = a.t_ry[slot];
+  const int src = a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + row];
+  const int64_t mrow = (lv.row_off[tl.level] + src) * cpad;
+  T* yout = Y + a.tile_ybase[tile] + (int64_t)FMM_TILE * a.kyoff[tl.cls * FMM_NT_CLASS + k] + (int64_t)row * ry;
+  for (int i0 = 0; i0 < ry; i0 += 16) {
+    T acc[16];
+#pragma unroll
+    for (int ii = 0; ii < 16; ++ii) acc[ii] = T(0);
+    for (int n0 = 0; n0 < C; n0 += 32) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * 16; e += FMM_TILE) {
+        const int nn = e >> 4, ii = e & 15, n = n0 + nn, i = i0 + ii;
+        T v = T(0);
+        if (n < C) {
+          if (MIXED) {
+            if (i < R) {
+              const int64_t o = ((int64_t)slot * R + i) * cpad + n;
+              v = Vb[o] + Vlo[o];
+            }
+          } else if (i < R) {
+            v = Vb[((int64_t)slot * C + n) * R + i];
+          }
+        }
+        sV[nn][ii] = v;
+      }
+      __syncthreads();
+      const int nmax = min(32, C - n0);
+      for (int nn = 0; nn < nmax; ++nn) {
+        T m = Mhi[mrow + n0 + nn];
+        if (MIXED) m += Mlo[mrow + n0 + nn];
+#pragma unroll
+        for (int ii = 0; ii < 16; ++ii) acc[ii] += sV[nn][ii] * m;
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < 16; ++ii)
+      if (i0 + ii < ry) yout[i0 + ii] = acc[ii];
+  }
+}
+
+// Expansion: one CTA computes 64 target rows x 64 coefficients, a GEMM whose
+// K dimension runs over (active transfer vector t, i < ry_t): A = the tile's
+// Y rows (no gather), B = U_t.  Per transfer vector the products are summed
+// in T and added into a Kahan-compensated total.  FP64 bank [316][C][R];
+// mixed bank U hi/lo [316][cpad][Rp] with the mean row C.
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(256)
+k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict__ Ub, const T* __restrict__ Ulo,
+             const T* __restrict__ Y, T* __restrict__ Lout, const double* __restrict__ box) {
+  __shared__ T As[16][64];
+  __shared__ T Bs[16][64 + 1];
+  const int tile = blockIdx.x, half = blockIdx.y, col0 = blockIdx.z * 64;
+  const int ncol = MIXED ? C + 1 : C;
+  if (col0 >= ncol) return;
+  const Tile tl = a.tiles[tile];
+  if (half * 64 >= tl.count) return;
+  const int l = tl.level;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nact = a.tile_nact[tile];
+  const int64_t ybase = a.tile_ybase[tile];
+  T acc[4][4], tot[4][4], cmp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tot[i][j] = cmp[i][j] = T(0);
+  for (int ai = 0; ai < nact; ++ai) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
+    const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
+    const int ry = a.t_ry[slot];
+    const T* yb = Y + ybase + (int64_t)FMM_TILE * a.kyoff[tl.cls * FMM_NT_CLASS + k];
+    for (int i0 = 0; i0 < ry; i0 += 16) {
+      __syncthreads();
+      for (int e = tid; e < 64 * 16; e += 256) {
+        const int r = e >> 4, kk = e & 15;
+        As[kk][r] = i0 + kk < ry ? yb[(int64_t)(half * 64 + r) * ry + i0 + kk] : T(0);
+      }
+      for (int e = tid; e < 64 * 16; e += 256) {
+        const int cc = e >> 4, kk = e & 15;
+        const int m = col0 + cc, i = i0 + kk;
+        T v = T(0);
+        if (m < ncol && i < ry && i < R) {
+          if (MIXED) {
+            const int64_t o = ((int64_t)slot * cpad + m) * R + i;
+            v = Ub[o] + Ulo[o];
+          } else {
+            v = Ub[((int64_t)slot * C + m) * R + i];
+          }
+        }
+        Bs[kk][cc] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T y = acc[i][j] - cmp[i][j];
+        const T s = tot[i][j] + y;
+        cmp[i][j] = (s - tot[i][j]) - y;
+        tot[i][j] = s;
+      }
+  }
+  const double inv_a = ldexp(1.0, l + 1) / box[3];
+  const int64_t rbase = lv.row_off[l];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = half * 64 + ty + 16 * i;
+    if (r >= tl.count) continue;
+    const int64_t row = rbase + lv.cls[l][tl.first + r];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = col0 + tx + 16 * j;
+      if (m < ncol) Lout[row * cpad + m] = (T)((double)tot[i][j] * inv_a);
+    }
+  }
+}
+
+// Host symmetry tables: canonical index of every transfer vector (in the
+// lexicographic slot order of operators.cu) and its node map sigma.
+void symmetry_tables(int p, std::vector<int8_t>& canon, std::vector<int8_t>& t_canon, std::vector<int16_t>& sm) {
+  std::vector<std::array<int, 3>> cv;
+  for (int a = 0; a <= 3; ++a)
+    for (int b = a; b <= 3; ++b)
+      for (int c = b; c <= 3; ++c)
+        if (c >= 2) cv.push_back({a, b, c});
+  canon.clear();
+  for (auto& v : cv)
+    for (int d = 0; d < 3; ++d) canon.push_back((int8_t)v[d]);
+  const int C = p * p * p;
+  t_canon.assign(FMM_NT, 0);
+  sm.assign((size_t)FMM_NT * C, 0);
+  int slot = 0;
+  for (int x = -3; x <= 3; ++x)
+    for (int y = -3; y <= 3; ++y)
+      for (int z = -3; z <= 3; ++z) {
+        if (std::abs(x) < 2 && std::abs(y) < 2 && std::abs(z) < 2) continue;
+        const int t[3] = {x, y, z};
+        int av[3] = {std::abs(x), std::abs(y), std::abs(z)};
+        std::array<int, 3> th = {av[0], av[1], av[2]};
+        std::sort(th.begin(), th.end());
+        int axis[3], sign[3];
+        bool used[3] = {false, false, false};
+        for (int d = 0; d < 3; ++d) {
+          sign[d] = t[d] < 0 ? -1 : 1;
+          for (int j = 0; j < 3; ++j)
+            if (!used[j] && th[j] == av[d]) {
+              axis[d] = j;
+              used[j] = true;
+              break;
+            }
+        }
+        int k = 0;
+        while (cv[k] != th) ++k;
+        t_canon[slot] = (int8_t)k;
+        for (int m = 0; m < C; ++m) {
+          const int mi[3] = {m / (p * p), (m / p) % p, m % p};
+          int r[3];
+          for (int d = 0; d < 3; ++d) r[d] = sign[d] > 0 ? mi[axis[d]] : p - 1 - mi[axis[d]];
+          sm[(size_t)slot * C + m] = (int16_t)((r[0] * p + r[1]) * p + r[2]);
+        }
+        ++slot;
+      }
+}
+
+}  // namespace
+
+double svd_eps_of(const Ctx* c) { return c->svd_eps > 0.0 ? c->svd_eps : std::pow(10.0, -c->order); }
+
+// SVD of the 16 canonical operators for the handle's order and eps; ranks
+// read back to the host.  Synchronous (once per handle and eps).
+fmm_status svd_prepare(Ctx* c) {
+  const double eps = svd_eps_of(c);
+  if (c->svd_ready && c->svd_eps_used == eps) return FMM_OK;
+  const int p = c->order, C = c->ncoef;
+  cudaStream_t s = c->stream;
+  std::vector<int8_t> canon, t_canon;
+  std::vector<int16_t> sm;
+  symmetry_tables(p, canon, t_canon, sm);
+  // work buffers: K, W, Z [16][C][C], singular values, order, colmean, ranks, sweeps
+  const size_t mat = (size_t)16 * C * C;
+  void* ptr;
+  if (!c->svd_W) {
+    FMM_TRY(dalloc(c, &ptr, sizeof(double) * mat * 2));
+    c->svd_W = (double*)ptr;
+    c->svd_Z = c->svd_W + mat;
+    FMM_TRY(dalloc(c, &ptr, sizeof(double) * 16 * C * 2 + sizeof(int32_t) * (16 * C + 64)));
+    c->svd_vals = (double*)ptr;
+    c->svd_colmean = c->svd_vals + 16 * C;
+    c->svd_ord = (int32_t*)(c->svd_colmean + 16 * C);
+    c->svd_rank_d = c->svd_ord + 16 * C;
+    c->svd_sweeps_d = c->svd_rank_d + 16;
+    FMM_TRY(dalloc(c, &ptr, (size_t)FMM_NT * C * sizeof(int16_t) + 64 + FMM_NT));
+    c->svd_sm = (int16_t*)ptr;
+    c->svd_canon = (int8_t*)(c->svd_sm + (size_t)FMM_NT * C);
+    c->svd_tcanon = c->svd_canon + 48;
+    FMM_CUDA(c, cudaMemcpy(c->svd_sm, sm.data(), sm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpy(c->svd_canon, canon.data(), canon.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpy(c->svd_tcanon, t_canon.data(), t_canon.size(), cudaMemcpyHostToDevice));
+  }
+  double* K;
+  FMM_TRY(dalloc(c, &ptr, sizeof(double) * mat));
+  K = (double*)ptr;
+  k_canon_ops64<<<ceil_div(mat, 256), 256, 0, s>>>(p, C, c->nodes64, c->svd_canon, K);
+  k_svd_jacobi<<<16, SVD_THREADS, 0, s>>>(C, K, c->svd_W, c->svd_Z, c->svd_sweeps_d);
+  k_svd_order<<<16, SVD_THREADS, 0, s>>>(C, eps, c->svd_W, c->svd_vals, c->svd_ord, c->svd_rank_d, c->svd_colmean);
+  FMM_CUDA(c, cudaGetLastError());
+  int32_t hr[32];
+  FMM_CUDA(c, cudaMemcpyAsync(hr, c->svd_rank_d, sizeof(int32_t) * 32, cudaMemcpyDeviceToHost, s));
+  FMM_CUDA(c, cudaStreamSynchronize(s));
+  dfree(c, K, sizeof(double) * mat);
+  for (int k = 0; k < 16; ++k)
+    if (hr[16 + k] < 0) return set_err(c, FMM_ERR_CUDA, "SVD of canonical M2L operator %d did not converge", k);
+  int rmax = 0;
+  for (int k = 0; k < 16; ++k) {
+    c->svd_rank[k] = hr[k];
+    rmax = std::max(rmax, hr[k]);
+  }
+  for (int t = 0; t < FMM_NT; ++t) c->t_rank_h[t] = c->svd_rank[t_canon[t]];
+  c->svd_rmax = rmax;
+  c->svd_rp = (rmax + 15) / 16 * 16;
+  c->svd_ready = true;
+  c->svd_eps_used = eps;
+  c->svd_gen++;
+  c->svd64 = c->svd32 = false;
+  return FMM_OK;
+}
+
+// Factor banks for the current precision (after svd_prepare).
+fmm_status svd_banks(Ctx* c) {
+  const int C = c->ncoef, cp = c->cpad;
+  cudaStream_t s = c->stream;
+  void* ptr;
+  const int grid = ceil_div((int64_t)FMM_NT * C, 128);
+  if (c->precision == FMM_FP64 && !c->svd64) {
+    const int R = c->svd_rmax;
+    const size_t bytes = sizeof(double) * (size_t)FMM_NT * C * R;
+    dfree(c, c->svd_V64, c->svd_bank64_bytes);
+    dfree(c, c->svd_U64, c->svd_bank64_bytes);
+    c->svd_V64 = c->svd_U64 = nullptr;
+    FMM_TRY(dalloc(c, &ptr, bytes));
+    c->svd_V64 = (double*)ptr;
+    FMM_TRY(dalloc(c, &ptr, bytes));
+    c->svd_U64 = (double*)ptr;
+    c->svd_bank64_bytes = bytes;
+    k_svd_banks64<<<grid, 128, 0, s>>>(C, R, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d, c->svd_W, c->svd_Z,
+                                       c->svd_V64, c->svd_U64);
+    FMM_CUDA(c, cudaGetLastError());
+    FMM_CUDA(c, cudaStreamSynchronize(s));
+    c->svd64 = true;
+  }
+  if (c->precision == FMM_MIXED && !c->svd32) {
+    const int Rp = c->svd_rp;
+    const size_t bytes = sizeof(float) * (size_t)FMM_NT * Rp * cp;
+    for (float** b : {&c->svd_VThi, &c->svd_VTlo, &c->svd_Uhi, &c->svd_Ulo}) {
+      dfree(c, *b, c->svd_bank32_bytes);
+      *b = nullptr;
+    }
+    for (float** b : {&c->svd_VThi, &c->svd_VTlo, &c->svd_Uhi, &c->svd_Ulo}) {
+      FMM_TRY(dalloc(c, &ptr, bytes));
+      *b = (float*)ptr;
+      FMM_CUDA(c, cudaMemsetAsync(ptr, 0, bytes, s));
+    }
+    c->svd_bank32_bytes = bytes;
+    k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, Rp, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d, c->svd_W,
+                                       c->svd_Z, c->svd_colmean, c->svd_VThi, c->svd_VTlo, c->svd_Uhi, c->svd_Ulo);
+    FMM_CUDA(c, cudaGetLastError());
+    FMM_CUDA(c, cudaStreamSynchronize(s));
+    c->svd32 = true;
+  }
+  return FMM_OK;
+}
+
+// Y layout of the current tree and precision: row length per transfer
+// vector, offsets of each transfer vector's block within a tile, and the
+// tiles' bases; grows the Y buffer.  Called before an evaluation is captured.
+fmm_status m2l_svd_prepare(Ctx* c) {
+  FMM_TRY(svd_prepare(c));
+  FMM_TRY(svd_banks(c));
+  const std::vector<int64_t> sig = {c->tree_gen, c->precision, c->svd_gen, c->ntiles};
+  if (sig == c->svd_ysig) return FMM_OK;
+  const bool mixed = c->precision == FMM_MIXED;
+  std::vector<int32_t> ry(FMM_NT), kyoff(8 * FMM_NT_CLASS), rank(FMM_NT);
+  for (int t = 0; t < FMM_NT; ++t) {
+    rank[t] = c->t_rank_h[t];
+    ry[t] = mixed ? (rank[t] + 15) / 16 * 16 : rank[t];
+  }
+  int64_t ysum[8];
+  for (int cls = 0; cls < 8; ++cls) {
+    int64_t o = 0;
+    for (int k = 0; k < FMM_NT_CLASS; ++k) {
+      kyoff[cls * FMM_NT_CLASS + k] = (int32_t)o;
+      o += ry[c->cls_t_h[cls * FMM_NT_CLASS + k]];
+    }
+    ysum[cls] = o;
+  }
+  std::vector<int64_t> base(c->ntiles > 0 ? c->ntiles : 1, 0);
+  int64_t total = 0;
+  for (int i = 0; i < c->ntiles; ++i) {
+    base[i] = total;
+    total += (int64_t)FMM_TILE * ysum[c->tiles_h[i].cls];
+  }
+  const size_t esz = mixed ? sizeof(float) : sizeof(double);
+  const size_t ybytes = (size_t)(total > 0 ? total : 1) * esz;
+  void* ptr;
+  if (ybytes > c->svd_Y_cap) {
+    dfree(c, c->svd_Y, c->svd_Y_cap);
+    c->svd_Y = nullptr;
+    c->svd_Y_cap = 0;
+    const size_t cap = ybytes + ybytes / 8;
+    FMM_TRY(dalloc(c, &ptr, cap));
+    c->svd_Y = ptr;
+    c->svd_Y_cap = cap;
+  }
+  if ((int64_t)base.size() > c->svd_ybase_cap) {
+    dfree(c, c->svd_ybase, sizeof(int64_t) * c->svd_ybase_cap);
+    c->svd_ybase = nullptr;
+    c->svd_ybase_cap = 0;
+    const int64_t cap = (int64_t)base.size() + 64;
+    FMM_TRY(dalloc(c, &ptr, sizeof(int64_t) * cap));
+    c->svd_ybase = (int64_t*)ptr;
+    c->svd_ybase_cap = cap;
+  }
+  if (!c->svd_ry) {
+    FMM_TRY(dalloc(c, &ptr, sizeof(int32_t) * (2 * FMM_NT + 8 * FMM_NT_CLASS)));
+    c->svd_ry = (int32_t*)ptr;
+    c->svd_trank = c->svd_ry + FMM_NT;
+    c->svd_kyoff = c->svd_trank + FMM_NT;
+  }
+  FMM_CUDA(c, cudaMemcpy(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->svd_kyoff, kyoff.data(), sizeof(int32_t) * kyoff.size(), cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->svd_ybase, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice));
+  c->svd_ysig = sig;
+  return FMM_OK;
+}
+
+fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
+  if (ntiles <= 0) return FMM_OK;
+  SvdArgs a;
+  a.tiles = c->tiles + first_tile;
+  a.tile_src = c->tile_src + (int64_t)first_tile * FMM_NT_CLASS * FMM_TILE;
+  a.tile_act = c->tile_act + (int64_t)first_tile * FMM_NT_CLASS;
+  a.tile_nact = c->tile_nact + first_tile;
+  a.cls_t = c->cls_t;
+  a.t_ry = c->svd_ry;
+  a.kyoff = c->svd_kyoff;
+  a.tile_ybase = c->svd_ybase + first_tile;
+  const int C = c->ncoef, cp = c->cpad;
+  dim3 gp(ntiles, FMM_NT_CLASS);
+  if (c->precision == FMM_MIXED) {
+    dim3 ge(ntiles, 2, ceil_div(C + 1, 64));
+    float* Y = (float*)c->svd_Y;
+    k_m2l_proj<float, true><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_VThi, c->svd_VTlo, c->Mhi,
+                                                     c->Mlo, Y);
+    k_m2l_expand<float, true><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_Uhi, c->svd_Ulo, Y, c->L32,
+                                                 c->box);
+  } else {
+    dim3 ge(ntiles, 2, ceil_div(C, 64));
+    double* Y = (double*)c->svd_Y;
+    k_m2l_proj<double, false><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rmax, c->svd_V64, nullptr, c->M64,
+                                                       nullptr, Y);
+    k_m2l_expand<double, false><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rmax, c->svd_U64, nullptr, Y, c->L64,
+                                                   c->box);
+  }
+  return cuda_err(c, cudaGetLastError(), "compressed M2L launch");
+}
+
+}  // namespace fmm

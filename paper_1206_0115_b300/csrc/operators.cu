@@ -151,6 +151,7 @@ fmm_status operators_init(Ctx* c) {
   }
   if ((int)tv.size() != 3 * FMM_NT || (int)ct.size() != 8 * FMM_NT_CLASS)
     return set_err(c, FMM_ERR_CUDA, "internal: transfer-vector tables have the wrong size");
+  c->cls_t_h = ct;
 
   std::vector<float> cheb32(cheb.begin(), cheb.end()), A32(A.begin(), A.end());
   void* ptr;

@@ -828,6 +828,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     }
   c->ntiles = (int)tiles.size();
   for (const Tile& tl : tiles) c->leaf_tiles += tl.level == Lf;
+  c->tiles_h = tiles;
+  c->tree_gen++;
   if (c->ntiles > c->tiles_cap) {
     int cap = c->ntiles + c->ntiles / 8 + 16;
     dfree(c, c->tiles, sizeof(Tile) * (size_t)c->tiles_cap);

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
 
 FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FMM_FP64, FMM_MIXED = 0, 1
+FMM_M2L_FULL, FMM_M2L_SVD = 0, 1
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
                 -5: "FMM_ERR_TIMEOUT"}
 
@@ -35,6 +36,8 @@ _SIGS = {
     "fmm_destroy": [_vp],
     "fmm_set_stream": [_vp, _vp],
     "fmm_set_precision": [_vp, C.c_int],
+    "fmm_set_m2l": [_vp, C.c_int, C.c_double],
+    "fmm_get_svd_ranks": [_vp, _vp],
     "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
     "fmm_evaluate": [_vp, _vp, _vp],
     "fmm_get_order": [_vp, _vp],
@@ -104,6 +107,16 @@ def fmm_set_stream(h, stream) -> int:
 
 def fmm_set_precision(h, precision: int) -> int:
     return _check(h, lib.fmm_set_precision(h, precision))
+
+
+def fmm_set_m2l(h, method: int, eps: float = 0.0) -> int:
+    return _check(h, lib.fmm_set_m2l(h, method, float(eps)))
+
+
+def fmm_get_svd_ranks(h) -> np.ndarray:
+    out = np.zeros(16, dtype=np.int32)
+    _check(h, lib.fmm_get_svd_ranks(h, _ptr(out)))
+    return out
 
 
 def fmm_set_particles(h, n: int, xyz, q) -> int:
@@ -181,10 +194,12 @@ class FMM:
     """Owns one handle.  Inputs/outputs are torch tensors (CUDA or CPU) or numpy
     arrays; every step runs in the CUDA library."""
 
-    def __init__(self, height: int, order: int, precision: int = FMM_MIXED, stream=None):
+    def __init__(self, height: int, order: int, precision: int = FMM_MIXED, stream=None,
+                 m2l: int = FMM_M2L_SVD, svd_eps: float = 0.0):
         self.h = fmm_create(height, order)
         self.height, self.order = height, order
         fmm_set_precision(self.h, precision)
+        fmm_set_m2l(self.h, m2l, svd_eps)
         if stream is not None:
             fmm_set_stream(self.h, stream)
         self.n = 0
@@ -208,6 +223,12 @@ class FMM:
 
     def set_precision(self, precision: int):
         fmm_set_precision(self.h, precision)
+
+    def set_m2l(self, method: int, eps: float = 0.0):
+        fmm_set_m2l(self.h, method, eps)
+
+    def svd_ranks(self) -> np.ndarray:
+        return fmm_get_svd_ranks(self.h)
 
     def set_particles(self, xyz, q):
         n = int(xyz.shape[0])

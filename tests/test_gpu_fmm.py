@@ -33,10 +33,18 @@ def F():
     return fmm
 
 
-def _run(F, xyz, q, h, p, precision, host=False):
+SVD, FULL = 1, 0   # M2L methods (FMM_M2L_SVD is the library default)
+
+
+def _oracle(xyz, q, h, p, m2l=SVD):
+    """The oracle FMM with the same M2L operators as the CUDA path's method."""
+    return oracle.OracleFMM(xyz, q, h, p, svd_eps=10.0 ** -p if m2l == SVD else None)
+
+
+def _run(F, xyz, q, h, p, precision, host=False, m2l=SVD):
     import torch
     n = len(q)
-    with F.FMM(h, p, precision) as f:
+    with F.FMM(h, p, precision, m2l=m2l) as f:
         if host:
             f.set_particles(np.ascontiguousarray(xyz), np.ascontiguousarray(q))
             phi = np.zeros(n)
@@ -144,22 +152,44 @@ FP64_CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,make,h,p", FP64_CASES)
-def test_fp64_matches_oracle_fmm(F, name, make, h, p):
+def _cases_by_method(cases):
+    """Every case with the full-rank operators; with the compressed ones up
+    to p = 8 (the oracle's Jacobi SVDs at p = 10 take minutes on the CPU)."""
+    out = []
+    for c in cases:
+        out.append(pytest.param(*c, FULL, id=c[0] + "-full"))
+        if c[3] <= 8:
+            out.append(pytest.param(*c, SVD, id=c[0] + "-svd"))
+    return out
+
+
+@pytest.mark.parametrize("name,make,h,p,m2l", _cases_by_method(FP64_CASES))
+def test_fp64_matches_oracle_fmm(F, name, make, h, p, m2l):
     xyz, q = make()
-    phi, Fo = _run(F, xyz, q, h, p, F.FMM_FP64)
-    with oracle.OracleFMM(xyz, q, h, p) as o:
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_FP64, m2l=m2l)
+    with _oracle(xyz, q, h, p, m2l) as o:
         pr, Fr = o.evaluate()
     assert oracle.rel_l2(phi, pr) <= TOL_FP64
     assert oracle.rel_l2(Fo, Fr) <= TOL_FP64
 
 
-def test_fp64_stage_expansions(F):
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
+def test_svd_ranks_match_oracle(F, p):
+    """The ranks of the 16 compressed operators (GPU Jacobi SVD) equal the
+    oracle's (CPU Jacobi SVD); the truncation has margin at these orders (a
+    CPU test), so equal ranks are expected, not lucky."""
+    xyz, q = inputs.particles(300, 3, "cube", "pos")
+    with F.FMM(3, p, F.FMM_FP64) as f, _oracle(xyz, q, 3, p) as o:
+        assert f.svd_ranks().tolist() == o.svd_ranks().tolist()
+
+
+@pytest.mark.parametrize("m2l", [FULL, SVD])
+def test_fp64_stage_expansions(F, m2l):
     """Per-stage parity: M (P2M, M2M) and L (M2L + L2L) at every level."""
     import torch
     xyz, q = inputs.particles(12000, 21, "cube", "sym")
     h, p = 5, 4
-    with F.FMM(h, p, F.FMM_FP64) as f, oracle.OracleFMM(xyz, q, h, p) as o:
+    with F.FMM(h, p, F.FMM_FP64, m2l=m2l) as f, _oracle(xyz, q, h, p, m2l) as o:
         f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
         phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
         Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
@@ -184,11 +214,11 @@ MIXED_CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,make,h,p", MIXED_CASES)
-def test_mixed_matches_oracle_fmm(F, name, make, h, p):
+@pytest.mark.parametrize("name,make,h,p,m2l", _cases_by_method(MIXED_CASES))
+def test_mixed_matches_oracle_fmm(F, name, make, h, p, m2l):
     xyz, q = make()
-    phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
-    with oracle.OracleFMM(xyz, q, h, p) as o:
+    phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED, m2l=m2l)
+    with _oracle(xyz, q, h, p, m2l) as o:
         pr, Fr = o.evaluate()
     assert oracle.rel_l2(phi, pr) <= TOL_MIXED
     assert oracle.rel_l2(Fo, Fr) <= TOL_MIXED
@@ -269,7 +299,7 @@ def test_degenerate_inputs(F):
         phi = np.zeros(3000)
         Fo = np.zeros((3000, 3))
         f.evaluate(phi, Fo)
-        with oracle.OracleFMM(xyz, q, 4, 3) as o:
+        with _oracle(xyz, q, 4, 3) as o:
             pr, Fr = o.evaluate()
         assert oracle.rel_l2(phi, pr) <= TOL_MIXED
 
@@ -284,7 +314,7 @@ def test_reload_changes_tree(F):
             phi = np.zeros(n)
             Fo = np.zeros((n, 3))
             f.evaluate(phi, Fo)
-            with oracle.OracleFMM(xyz, q, 5, 4) as o:
+            with _oracle(xyz, q, 5, 4) as o:
                 pr, Fr = o.evaluate()
             assert oracle.rel_l2(phi, pr) <= TOL_FP64
             assert oracle.rel_l2(Fo, Fr) <= TOL_FP64
@@ -324,7 +354,7 @@ def test_cube_n1m_h6_p7_full_size(F):
     assert oracle.rel_l2(phi[idx], pd) <= TOL_MIXED
     assert oracle.rel_l2(Fo[idx], Fd) <= TOL_MIXED
     phi64, F64 = _run(F, xyz, q, h, p, F.FMM_FP64)
-    with oracle.OracleFMM(xyz, q, h, p) as o:
+    with _oracle(xyz, q, h, p) as o:
         perm = o.perm()
         idx2 = idx[:300]
         pr, Fr = o.evaluate_sampled(idx2)
@@ -341,7 +371,7 @@ def test_ellipsoid_n10m_h8_p7_full_size(F):
     xyz, q, h, p = inputs.workload("ellipsoid_n10m_h8_p7")
     idx = _sample_idx(len(q), 256, 6)
     phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
-    with oracle.OracleFMM(xyz, q, h, p) as o:
+    with _oracle(xyz, q, h, p) as o:
         pr, Fr = o.evaluate_sampled(idx)
     assert oracle.rel_l2(phi[idx], pr) <= TOL_MIXED
     assert oracle.rel_l2(Fo[idx], Fr) <= TOL_MIXED

@@ -532,3 +532,16 @@ def test_svd_sampled_evaluation_matches_full():
         ps, Fs = o.evaluate_sampled(idx)
     assert np.abs(ps - phi[idx]).max() <= 1e-12 * np.abs(phi).max()
     assert np.abs(Fs - F[idx]).max() <= 1e-12 * np.abs(F).max()
+
+
+def test_shared_svd_operators_give_the_same_result():
+    """A tree that copies another tree's compressed operators evaluates
+    exactly as one that computed its own."""
+    xyz, q = inputs.particles(3000, 53, "cube", "sym")
+    xyz2, q2 = inputs.particles(64, 1, "cube", "pos")
+    with oracle.OracleFMM(xyz2, q2, 3, 4, svd_eps=1e-4) as src, oracle.OracleFMM(xyz, q, 4, 4, svd_eps=1e-4) as a, \
+            oracle.OracleFMM(xyz, q, 4, 4, svd_from=src) as b:
+        pa, Fa = a.evaluate()
+        pb, Fb = b.evaluate()
+        assert b.svd_ranks().tolist() == a.svd_ranks().tolist()
+    assert np.array_equal(pa, pb) and np.array_equal(Fa, Fb)
