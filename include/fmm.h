@@ -161,7 +161,7 @@ fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
  * out[4] = M2L kernels of the current precision and method (full-rank
  * operators: 0 = FP64 CUDA cores, 1 = FP32 CUDA cores on split operands,
  * 2 = tcgen05 tensor cores; compressed operators: 3 = FP64 CUDA cores,
- * 4 = FP32 CUDA cores),
+ * 4 = FP32 CUDA cores, 5 = tcgen05 tensor cores),
  * out[5..7] = 0 (reserved).  out: 8 int64, host. */
 fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
 

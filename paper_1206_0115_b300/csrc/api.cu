@@ -139,11 +139,12 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                         (const void*)c->tile_act, (const void*)c->tile_nact, (const void*)c->K64,
                         (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm,
                         (const void*)c->tc_partial, (const void*)c->tc_err, (const void*)c->svd_Y,
-                        (const void*)c->svd_ybase, (const void*)c->svd_ry, (const void*)c->svd_V64,
+                        (const void*)c->src_act, (const void*)c->svd_ry, (const void*)c->svd_V64,
                         (const void*)c->svd_U64, (const void*)c->svd_VThi, (const void*)c->svd_Uhi})
     s.push_back((int64_t)(uintptr_t)p);
   s.push_back(c->svd_rmax);
   s.push_back(c->svd_rp);
+  s.push_back(c->svd_YS);
   return s;
 }
 
@@ -289,7 +290,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi, c->svd_VTlo,
-                  c->svd_Uhi, c->svd_Ulo, c->svd_ry, c->svd_ybase, c->svd_Y};
+                  c->svd_Uhi, c->svd_Ulo, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
@@ -384,6 +385,7 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   FMM_TRY(check_device_error(c));
   if (c->m2l_method == FMM_M2L_SVD) {
     if (c->leaf >= 2) FMM_TRY(m2l_svd_prepare(c));
+    if (c->leaf >= 2 && m2l_kind(c) == 5) FMM_TRY(m2l_svd_tc_prepare(c));
   } else {
     FMM_TRY(operators_m2l(c, c->precision));
     if (m2l_kind(c) == 2) FMM_TRY(m2l_tc_prepare(c));
@@ -405,7 +407,7 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   FMM_TRY(launch_l2p_out(c, c->stream, dphi, dF));
   if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[8], c->stream));
   c->tev_recorded = c->timing;
-  if (c->tc_err && m2l_kind(c) == 2)
+  if (c->tc_err && (m2l_kind(c) == 2 || m2l_kind(c) == 5))
     FMM_CUDA(c, cudaMemcpyAsync(c->tc_err_h, c->tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   if (!dev_out) {
     FMM_CUDA(c, cudaMemcpyAsync(phi, dphi, sizeof(double) * n, cudaMemcpyDefault, c->stream));

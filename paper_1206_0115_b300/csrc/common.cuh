@@ -113,6 +113,8 @@ struct fmm_ctx {
   int32_t* tile_src = nullptr;  // [tile][189][128]
   int16_t* tile_act = nullptr;  // [tile][189]
   int32_t* tile_nact = nullptr; // [tile]
+  int16_t* src_act = nullptr;   // [tile][189]: indices into src_t of the tile's cells as sources with a target
+  int32_t* src_nact = nullptr;  // [tile]
   int leaf_tiles = 0;           // tiles [0, leaf_tiles) belong to the leaf level
   int leaf_tile_end() const { return leaf_tiles; }
 
@@ -124,6 +126,7 @@ struct fmm_ctx {
   float* m2m32 = nullptr;
   int8_t* tvec = nullptr;      // [316][3]
   int16_t* cls_t = nullptr;    // [8][189] -> transfer vector index
+  int16_t* src_t = nullptr;    // [8][189]: transfer vectors with which a source of the class serves a target
   double* K64 = nullptr;       // [316][C][C]
   float *Khi = nullptr, *Klo = nullptr;  // [316][cpad][cpad], TF32 split
   bool ops64 = false, ops32 = false;
@@ -147,6 +150,9 @@ struct fmm_ctx {
   int32_t* tc_err_h = nullptr;    // pinned mirror, copied after every evaluation
   alignas(64) unsigned char tm_khi[128], tm_klo[128];  // CUtensorMap of the operator bank
   int64_t tm_rows = -1;
+  alignas(64) unsigned char tm_vthi[128], tm_vtlo[128], tm_uhi[128], tm_ulo[128];  // compressed banks
+  const void* tm_svd_ptr = nullptr;
+  int svd_tc_smem_set[2] = {0, 0}, svd_tc_nst = 0;
   const void* tm_khi_ptr = nullptr;
   int tc_smem_set = 0, tc_nst = 0, num_sms = 0;
 
@@ -168,14 +174,14 @@ struct fmm_ctx {
   float *svd_VThi = nullptr, *svd_VTlo = nullptr;  // [316][rp][cpad]
   float *svd_Uhi = nullptr, *svd_Ulo = nullptr;    // [316][cpad][rp], mean-split
   size_t svd_bank32_bytes = 0;
-  int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_kyoff = nullptr;
-  int64_t* svd_ybase = nullptr;
-  int64_t svd_ybase_cap = 0;
-  void* svd_Y = nullptr;
+  int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_yoff = nullptr;  // [316], [316], [8][316]
+  int64_t svd_YS = 0;            // Y values per cell row
+  void* svd_Y = nullptr;         // Y[row][YS]: the projections of each cell's M, row = the expansion row
   size_t svd_Y_cap = 0;
   std::vector<int64_t> svd_ysig;
   std::vector<Tile> tiles_h;     // host copy of the M2L tiles
   std::vector<int16_t> cls_t_h;  // host copy of cls_t
+  std::vector<int16_t> src_t_h;  // host copy of src_t
   int64_t tree_gen = 0;          // bumped by every tree build
 
   // stats
@@ -216,6 +222,10 @@ fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntile
 bool m2l_tc_supported(const Ctx* c);
 fmm_status m2l_tc_prepare(Ctx* c);
 fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
+fmm_status launch_m2l_tc_reduce(Ctx* c, cudaStream_t s, const float* partial, int gt);
+bool m2l_svd_tc_supported(const Ctx* c);
+fmm_status m2l_svd_tc_prepare(Ctx* c);
+fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 // M2L of every level; `mid` separates the main kernel from the rest (see fmm_get_stage_times)
 fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 fmm_status launch_l2l(Ctx* c, cudaStream_t s);
@@ -223,7 +233,8 @@ fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F);
 fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out);
 int64_t count_launches_eval(const Ctx* c);
 fmm_status work_counts(Ctx* c, int64_t* out);
-// 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank operators); 3 FP64 SIMT, 4 FP32 SIMT (SVD-compressed)
+// 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank operators); 3 FP64 SIMT, 4 FP32 SIMT,
+// 5 tcgen05 (SVD-compressed)
 int m2l_kind(const Ctx* c);
 
 // ---- device helpers ----------------------------------------------------------

@@ -7,7 +7,10 @@
 namespace fmm {
 
 int m2l_kind(const Ctx* c) {
-  if (c->m2l_method == FMM_M2L_SVD) return c->precision == FMM_FP64 ? 3 : 4;
+  if (c->m2l_method == FMM_M2L_SVD) {
+    if (c->precision == FMM_FP64) return 3;
+    return (c->use_tc && m2l_svd_tc_supported(c)) ? 5 : 4;
+  }
   if (c->precision == FMM_FP64) return 0;
   return (c->use_tc && m2l_tc_supported(c)) ? 2 : 1;
 }
@@ -19,6 +22,7 @@ fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   }
   const int kind = m2l_kind(c);
   if (kind == 2) return launch_m2l_tc(c, s, mid);
+  if (kind == 5) return launch_m2l_svd_tc(c, s, mid);
   auto run = kind >= 3 ? launch_m2l_svd_simt : launch_m2l_simt;
   // CUDA cores: leaf level, then the coarser levels
   FMM_TRY(run(c, s, 0, c->leaf_tiles));
@@ -97,7 +101,8 @@ int64_t count_launches_eval(const Ctx* c) {
   if (Lf >= 2 && c->n > 0) {
     k += 1 + (Lf - 2);                                      // P2M, M2M
     const int kind = m2l_kind(c), per = kind >= 3 ? 2 : 1;
-    k += kind == 2 ? 2 * (c->ntiles > 0) : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));  // M2L
+    k += kind == 2 ? 2 * (c->ntiles > 0)
+                   : kind == 5 ? 3 * (c->ntiles > 0) : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));
     k += (Lf - 2);                                          // L2L
   }
   return k;

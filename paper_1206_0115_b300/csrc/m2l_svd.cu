@@ -27,9 +27,12 @@
 //                   the rank and, for the mixed banks, the mean of every
 //                   column of U Sigma;
 //   k_svd_banks64 / k_svd_banks32   the permuted factors of all 316 t.
-// Evaluation, per M2L tile (128 targets of one level and child class):
-//   k_m2l_proj    Y[tile][t][row][i] = sum_n V_t[n][i] M_{src(row, t)}[n]
-//   k_m2l_expand  L[row] = (1/a) sum_t sum_i U_t[.][i] Y[tile][t][row][i]
+// Evaluation, per M2L tile (128 cells of one level and child class):
+//   k_m2l_proj    from the sources: Y[S][t] = V_t^T M_S for each cell S of the
+//                 tile and each t with which S serves a target (src_t, src_act),
+//                 so that every M row is read once per (tile, t) without a gather
+//   k_m2l_expand  at the targets: L_T = (1/a) sum_t U_t Y[T + t][t] (the short
+//                 Y rows are gathered, not the multipoles)
 // The mixed path stores U in the mean-split form of the local expansions
 // (row C = the mean over m of U_t[m][.], rows m < C the deviations), its
 // factors as TF32 hi/lo pairs, and pads every rank to a multiple of 16 with
@@ -248,30 +251,35 @@ struct SvdArgs {
   const int32_t* tile_src;
   const int16_t* tile_act;
   const int32_t* tile_nact;
+  const int16_t* src_act;
+  const int32_t* src_nact;
   const int16_t* cls_t;
-  const int32_t* t_ry;       // [316] Y row length (rank; mixed: rounded up to 16)
-  const int32_t* kyoff;      // [8][189] offset of transfer vector k's block in a tile's Y, in rows of 1 value
-  const int64_t* tile_ybase; // [tile] first element of the tile's Y
+  const int16_t* src_t;
+  const int32_t* t_ry;   // [316] Y values per (cell, t): the rank (mixed: rounded up to 16)
+  const int32_t* yoff;   // [8][316] offset of t's values in a cell's Y row (class of the cell), -1 if none
+  int64_t YS;            // Y row length
 };
 
-// Projection: one block per (tile, active transfer vector), one thread per
-// target row: y[i] = sum_n V_t[n][i] M_src[n], V staged in shared memory in
-// chunks of 32 n x 16 i.  FP64 bank [316][C][R]; mixed bank VT hi/lo
-// [316][Rp][cpad], used as the FP32 sum hi + lo.
+// Projection, from the sources: one block per (tile, active source transfer
+// vector), one thread per cell S of the tile: Y[S][t] = V_t^T M_S (ry values),
+// V staged in shared memory in chunks of 32 n x 16 i.  FP64 bank
+// [316][C][R]; mixed bank VT hi/lo [316][Rp][cpad], used as the FP32 sum.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(FMM_TILE)
 k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict__ Vb, const T* __restrict__ Vlo,
            const T* __restrict__ Mhi, const T* __restrict__ Mlo, T* __restrict__ Y) {
   __shared__ T sV[32][16];
   const int tile = blockIdx.x, ai = blockIdx.y, row = threadIdx.x;
-  if (ai >= a.tile_nact[tile]) return;
+  if (ai >= a.src_nact[tile]) return;
   const Tile tl = a.tiles[tile];
-  const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
-  const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
+  const int l = tl.level;
+  const int k = a.src_act[(int64_t)tile * FMM_NT_CLASS + ai];
+  const int slot = a.src_t[tl.cls * FMM_NT_CLASS + k];
   const int ry = a.t_ry[slot];
-  const int src = a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + row];
-  const int64_t mrow = (lv.row_off[tl.level] + src) * cpad;
-  T* yout = Y + a.tile_ybase[tile] + (int64_t)FMM_TILE * a.kyoff[tl.cls * FMM_NT_CLASS + k] + (int64_t)row * ry;
+  const bool valid = row < tl.count;
+  const int64_t cellrow = lv.row_off[l] + (valid ? lv.cls[l][tl.first + row] : lv.ncell[l]);
+  const int64_t mrow = cellrow * cpad;
+  T* yout = Y + cellrow * a.YS + a.yoff[tl.cls * FMM_NT + slot];
   for (int i0 = 0; i0 < ry; i0 += 16) {
     T acc[16];
 #pragma unroll
@@ -281,13 +289,11 @@ k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict_
       for (int e = threadIdx.x; e < 32 * 16; e += FMM_TILE) {
         const int nn = e >> 4, ii = e & 15, n = n0 + nn, i = i0 + ii;
         T v = T(0);
-        if (n < C) {
+        if (n < C && i < R) {
           if (MIXED) {
-            if (i < R) {
-              const int64_t o = ((int64_t)slot * R + i) * cpad + n;
-              v = Vb[o] + Vlo[o];
-            }
-          } else if (i < R) {
+            const int64_t o = ((int64_t)slot * R + i) * cpad + n;
+            v = Vb[o] + Vlo[o];
+          } else {
             v = Vb[((int64_t)slot * C + n) * R + i];
           }
         }
@@ -302,23 +308,27 @@ k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict_
         for (int ii = 0; ii < 16; ++ii) acc[ii] += sV[nn][ii] * m;
       }
     }
+    if (valid) {
 #pragma unroll
-    for (int ii = 0; ii < 16; ++ii)
-      if (i0 + ii < ry) yout[i0 + ii] = acc[ii];
+      for (int ii = 0; ii < 16; ++ii)
+        if (i0 + ii < ry) yout[i0 + ii] = acc[ii];
+    }
   }
 }
 
-// Expansion: one CTA computes 64 target rows x 64 coefficients, a GEMM whose
-// K dimension runs over (active transfer vector t, i < ry_t): A = the tile's
-// Y rows (no gather), B = U_t.  Per transfer vector the products are summed
-// in T and added into a Kahan-compensated total.  FP64 bank [316][C][R];
-// mixed bank U hi/lo [316][cpad][Rp] with the mean row C.
+// Expansion, at the targets: one CTA computes 64 target rows x 64
+// coefficients, a GEMM whose K dimension runs over (active transfer vector t,
+// i < ry_t): A = the sources' Y values for t (gathered; the level's zero row,
+// an absent source, gives zeros), B = U_t.  Per transfer vector the products
+// are summed in T and added into a Kahan-compensated total.  FP64 bank
+// [316][C][R]; mixed bank U hi/lo [316][cpad][Rp] with the mean row C.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(256)
 k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict__ Ub, const T* __restrict__ Ulo,
              const T* __restrict__ Y, T* __restrict__ Lout, const double* __restrict__ box) {
   __shared__ T As[16][64];
   __shared__ T Bs[16][64 + 1];
+  __shared__ int64_t sy[64];
   const int tile = blockIdx.x, half = blockIdx.y, col0 = blockIdx.z * 64;
   const int ncol = MIXED ? C + 1 : C;
   if (col0 >= ncol) return;
@@ -327,7 +337,8 @@ k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restric
   const int l = tl.level;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int nact = a.tile_nact[tile];
-  const int64_t ybase = a.tile_ybase[tile];
+  const int64_t rbase = lv.row_off[l];
+  const int zero = lv.ncell[l];
   T acc[4][4], tot[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -341,12 +352,16 @@ k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restric
     const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
     const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
     const int ry = a.t_ry[slot];
-    const T* yb = Y + ybase + (int64_t)FMM_TILE * a.kyoff[tl.cls * FMM_NT_CLASS + k];
+    __syncthreads();
+    if (tid < 64) {
+      const int s = a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + half * 64 + tid];
+      sy[tid] = s == zero ? -1 : (rbase + s) * a.YS + a.yoff[(lv.key[l][s] & 7) * FMM_NT + slot];
+    }
     for (int i0 = 0; i0 < ry; i0 += 16) {
       __syncthreads();
       for (int e = tid; e < 64 * 16; e += 256) {
         const int r = e >> 4, kk = e & 15;
-        As[kk][r] = i0 + kk < ry ? yb[(int64_t)(half * 64 + r) * ry + i0 + kk] : T(0);
+        As[kk][r] = (i0 + kk < ry && sy[r] >= 0) ? Y[sy[r] + i0 + kk] : T(0);
       }
       for (int e = tid; e < 64 * 16; e += 256) {
         const int cc = e >> 4, kk = e & 15;
@@ -387,7 +402,6 @@ k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restric
       }
   }
   const double inv_a = ldexp(1.0, l + 1) / box[3];
-  const int64_t rbase = lv.row_off[l];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = half * 64 + ty + 16 * i;
@@ -556,38 +570,46 @@ fmm_status svd_banks(Ctx* c) {
   return FMM_OK;
 }
 
-// Y layout of the current tree and precision: row length per transfer
-// vector, offsets of each transfer vector's block within a tile, and the
-// tiles' bases; grows the Y buffer.  Called before an evaluation is captured.
+// Y layout for the current precision and ranks (row length per transfer
+// vector, offsets within a cell's row by the cell's class), and the Y buffer
+// for the current tree (one row per expansion row).  Called before an
+// evaluation is captured.
 fmm_status m2l_svd_prepare(Ctx* c) {
   FMM_TRY(svd_prepare(c));
   FMM_TRY(svd_banks(c));
-  const std::vector<int64_t> sig = {c->tree_gen, c->precision, c->svd_gen, c->ntiles};
-  if (sig == c->svd_ysig) return FMM_OK;
   const bool mixed = c->precision == FMM_MIXED;
-  std::vector<int32_t> ry(FMM_NT), kyoff(8 * FMM_NT_CLASS), rank(FMM_NT);
-  for (int t = 0; t < FMM_NT; ++t) {
-    rank[t] = c->t_rank_h[t];
-    ry[t] = mixed ? (rank[t] + 15) / 16 * 16 : rank[t];
-  }
-  int64_t ysum[8];
-  for (int cls = 0; cls < 8; ++cls) {
-    int64_t o = 0;
-    for (int k = 0; k < FMM_NT_CLASS; ++k) {
-      kyoff[cls * FMM_NT_CLASS + k] = (int32_t)o;
-      o += ry[c->cls_t_h[cls * FMM_NT_CLASS + k]];
+  const std::vector<int64_t> sig = {c->precision, c->svd_gen};
+  void* ptr;
+  if (sig != c->svd_ysig) {
+    std::vector<int32_t> ry(FMM_NT), rank(FMM_NT), yoff(8 * FMM_NT, -1);
+    for (int t = 0; t < FMM_NT; ++t) {
+      rank[t] = c->t_rank_h[t];
+      ry[t] = mixed ? (rank[t] + 15) / 16 * 16 : rank[t];
     }
-    ysum[cls] = o;
-  }
-  std::vector<int64_t> base(c->ntiles > 0 ? c->ntiles : 1, 0);
-  int64_t total = 0;
-  for (int i = 0; i < c->ntiles; ++i) {
-    base[i] = total;
-    total += (int64_t)FMM_TILE * ysum[c->tiles_h[i].cls];
+    int64_t ys = 0;
+    for (int cls = 0; cls < 8; ++cls) {
+      int64_t o = 0;
+      for (int k = 0; k < FMM_NT_CLASS; ++k) {
+        const int slot = c->src_t_h[cls * FMM_NT_CLASS + k];
+        yoff[cls * FMM_NT + slot] = (int32_t)o;
+        o += ry[slot];
+      }
+      ys = std::max(ys, o);
+    }
+    c->svd_YS = (ys + 15) / 16 * 16;  // 64-byte aligned rows (FP32)
+    if (!c->svd_ry) {
+      FMM_TRY(dalloc(c, &ptr, sizeof(int32_t) * (2 * FMM_NT + 8 * FMM_NT)));
+      c->svd_ry = (int32_t*)ptr;
+      c->svd_trank = c->svd_ry + FMM_NT;
+      c->svd_yoff = c->svd_trank + FMM_NT;
+    }
+    FMM_CUDA(c, cudaMemcpy(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpy(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpy(c->svd_yoff, yoff.data(), sizeof(int32_t) * yoff.size(), cudaMemcpyHostToDevice));
+    c->svd_ysig = sig;
   }
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
-  const size_t ybytes = (size_t)(total > 0 ? total : 1) * esz;
-  void* ptr;
+  const size_t ybytes = (size_t)(c->rows > 0 ? c->rows : 1) * c->svd_YS * esz;
   if (ybytes > c->svd_Y_cap) {
     dfree(c, c->svd_Y, c->svd_Y_cap);
     c->svd_Y = nullptr;
@@ -597,26 +619,6 @@ fmm_status m2l_svd_prepare(Ctx* c) {
     c->svd_Y = ptr;
     c->svd_Y_cap = cap;
   }
-  if ((int64_t)base.size() > c->svd_ybase_cap) {
-    dfree(c, c->svd_ybase, sizeof(int64_t) * c->svd_ybase_cap);
-    c->svd_ybase = nullptr;
-    c->svd_ybase_cap = 0;
-    const int64_t cap = (int64_t)base.size() + 64;
-    FMM_TRY(dalloc(c, &ptr, sizeof(int64_t) * cap));
-    c->svd_ybase = (int64_t*)ptr;
-    c->svd_ybase_cap = cap;
-  }
-  if (!c->svd_ry) {
-    FMM_TRY(dalloc(c, &ptr, sizeof(int32_t) * (2 * FMM_NT + 8 * FMM_NT_CLASS)));
-    c->svd_ry = (int32_t*)ptr;
-    c->svd_trank = c->svd_ry + FMM_NT;
-    c->svd_kyoff = c->svd_trank + FMM_NT;
-  }
-  FMM_CUDA(c, cudaMemcpy(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->svd_kyoff, kyoff.data(), sizeof(int32_t) * kyoff.size(), cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->svd_ybase, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice));
-  c->svd_ysig = sig;
   return FMM_OK;
 }
 
@@ -627,10 +629,13 @@ fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntile
   a.tile_src = c->tile_src + (int64_t)first_tile * FMM_NT_CLASS * FMM_TILE;
   a.tile_act = c->tile_act + (int64_t)first_tile * FMM_NT_CLASS;
   a.tile_nact = c->tile_nact + first_tile;
+  a.src_act = c->src_act + (int64_t)first_tile * FMM_NT_CLASS;
+  a.src_nact = c->src_nact + first_tile;
   a.cls_t = c->cls_t;
+  a.src_t = c->src_t;
   a.t_ry = c->svd_ry;
-  a.kyoff = c->svd_kyoff;
-  a.tile_ybase = c->svd_ybase + first_tile;
+  a.yoff = c->svd_yoff;
+  a.YS = c->svd_YS;
   const int C = c->ncoef, cp = c->cpad;
   dim3 gp(ntiles, FMM_NT_CLASS);
   if (c->precision == FMM_MIXED) {

@@ -152,6 +152,20 @@ fmm_status operators_init(Ctx* c) {
   if ((int)tv.size() != 3 * FMM_NT || (int)ct.size() != 8 * FMM_NT_CLASS)
     return set_err(c, FMM_ERR_CUDA, "internal: transfer-vector tables have the wrong size");
   c->cls_t_h = ct;
+  // the same pairs seen from the source: for a source of class cs, the t with
+  // which it is a far-field source of some target T = S - t (T's class is cs
+  // with the parities of t flipped, and t must be in T's class list)
+  std::vector<int16_t> st;
+  for (int cs = 0; cs < 8; ++cs)
+    for (int sl = 0; sl < FMM_NT; ++sl) {
+      const int ctg = cs ^ (((tv[3 * sl] & 1) << 2) | ((tv[3 * sl + 1] & 1) << 1) | (tv[3 * sl + 2] & 1));
+      bool in = false;
+      for (int k = 0; k < FMM_NT_CLASS; ++k) in = in || ct[ctg * FMM_NT_CLASS + k] == sl;
+      if (in) st.push_back((int16_t)sl);
+    }
+  if ((int)st.size() != 8 * FMM_NT_CLASS)
+    return set_err(c, FMM_ERR_CUDA, "internal: source-side transfer-vector tables have the wrong size");
+  c->src_t_h = st;
 
   std::vector<float> cheb32(cheb.begin(), cheb.end()), A32(A.begin(), A.end());
   void* ptr;
@@ -169,6 +183,8 @@ fmm_status operators_init(Ctx* c) {
   c->tvec = (int8_t*)ptr;
   FMM_TRY(dalloc(c, &ptr, sizeof(int16_t) * ct.size()));
   c->cls_t = (int16_t*)ptr;
+  FMM_TRY(dalloc(c, &ptr, sizeof(int16_t) * st.size()));
+  c->src_t = (int16_t*)ptr;
   FMM_CUDA(c, cudaMemcpy(c->nodes64, nodes.data(), sizeof(double) * p, cudaMemcpyHostToDevice));
   FMM_CUDA(c, cudaMemcpy(c->cheb64, cheb.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice));
   FMM_CUDA(c, cudaMemcpy(c->cheb32, cheb32.data(), sizeof(float) * p * p, cudaMemcpyHostToDevice));
@@ -176,6 +192,7 @@ fmm_status operators_init(Ctx* c) {
   FMM_CUDA(c, cudaMemcpy(c->m2m32, A32.data(), sizeof(float) * 2 * p * p, cudaMemcpyHostToDevice));
   FMM_CUDA(c, cudaMemcpy(c->tvec, tv.data(), tv.size(), cudaMemcpyHostToDevice));
   FMM_CUDA(c, cudaMemcpy(c->cls_t, ct.data(), sizeof(int16_t) * ct.size(), cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->src_t, st.data(), sizeof(int16_t) * st.size(), cudaMemcpyHostToDevice));
   return FMM_OK;
 }
 

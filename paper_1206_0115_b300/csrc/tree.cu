@@ -442,6 +442,35 @@ k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restr
   if (row == 0) tile_nact[blockIdx.x] = nact;
 }
 
+// The same for the tile's cells as sources: the transfer vectors of the
+// class's source list (src_t) for which at least one cell S of the tile has a
+// target T = S - t in the tree.
+__global__ void __launch_bounds__(FMM_TILE)
+k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ src_t,
+                const int8_t* __restrict__ tvec, int16_t* __restrict__ src_act, int32_t* __restrict__ src_nact) {
+  const Tile tl = tiles[blockIdx.x];
+  const int l = tl.level, row = threadIdx.x;
+  const bool valid = row < tl.count;
+  int ix = 0, iy = 0, iz = 0;
+  if (valid) demorton3(lv.key[l][lv.cls[l][tl.first + row]], ix, iy, iz);
+  const int top = (1 << l) - 1;
+  __shared__ int16_t act[FMM_NT_CLASS];
+  __shared__ int nact;
+  if (row == 0) nact = 0;
+  __syncthreads();
+  for (int k = 0; k < FMM_NT_CLASS; ++k) {
+    const int slot = src_t[tl.cls * FMM_NT_CLASS + k];
+    const int tx = ix - tvec[3 * slot], ty = iy - tvec[3 * slot + 1], tz = iz - tvec[3 * slot + 2];
+    bool has = false;
+    if (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top)
+      has = lv.grid[l][morton3(tx, ty, tz)] >= 0;
+    if (__syncthreads_or(has) && row == 0) act[nact++] = (int16_t)k;
+  }
+  __syncthreads();
+  for (int k = row; k < nact; k += FMM_TILE) src_act[(int64_t)blockIdx.x * FMM_NT_CLASS + k] = act[k];
+  if (row == 0) src_nact[blockIdx.x] = nact;
+}
+
 __global__ void k_zero_rows(int nrows, const int64_t* __restrict__ rows, int cpad, float* a, float* b,
                             float* c, double* d, double* e) {
   int r = blockIdx.x;
@@ -836,6 +865,10 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     dfree(c, c->tile_src, sizeof(int32_t) * (size_t)c->tiles_cap * FMM_NT_CLASS * FMM_TILE);
     dfree(c, c->tile_act, sizeof(int16_t) * (size_t)c->tiles_cap * FMM_NT_CLASS);
     dfree(c, c->tile_nact, sizeof(int32_t) * (size_t)c->tiles_cap);
+    dfree(c, c->src_act, sizeof(int16_t) * (size_t)c->tiles_cap * FMM_NT_CLASS);
+    dfree(c, c->src_nact, sizeof(int32_t) * (size_t)c->tiles_cap);
+    c->src_act = nullptr;
+    c->src_nact = nullptr;
     c->tiles = nullptr;
     c->tile_src = nullptr;
     c->tile_act = nullptr;
@@ -850,13 +883,18 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     c->tile_act = (int16_t*)p;
     FMM_TRY(dalloc(c, &p, sizeof(int32_t) * (size_t)cap));
     c->tile_nact = (int32_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int16_t) * (size_t)cap * FMM_NT_CLASS));
+    c->src_act = (int16_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int32_t) * (size_t)cap));
+    c->src_nact = (int32_t*)p;
     c->tiles_cap = cap;
   }
   if (c->ntiles > 0) {
     FMM_CUDA(c, cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
     k_m2l_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->lv, c->cls_t, c->tvec, c->tile_src, c->tile_act,
                                                c->tile_nact);
-    c->launches_set++;
+    k_m2l_src_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->lv, c->src_t, c->tvec, c->src_act, c->src_nact);
+    c->launches_set += 2;
   }
   if (rows > 0) {
     std::vector<int64_t> zr;
