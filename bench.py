@@ -352,9 +352,9 @@ def run_ours(args):
     # the tensor-core kernel covers every level in one launch (stage [2]; the
     # FP64 reduction of its partial sums is stage [3]); the CUDA-core kernels
     # are timed over all levels (stage [1])
-    m2l_ms = m2l_leaf_ms if m2l_kind == 2 else float(np.mean(stage[:, 1]))
+    m2l_ms = m2l_leaf_ms if m2l_kind in (2, 5) else float(np.mean(stage[:, 1]))
     p2p_pairs = int(work[0])
-    tc_path = m2l_kind == 2
+    tc_path = m2l_kind in (2, 5)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if tc_path:
         bound, peak, peak_note = "tensor", pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
@@ -366,11 +366,14 @@ def run_ours(args):
     p2p_gflop = 20.0 * p2p_pairs / 1e9
     tensor_pipe = None
     if tc_path:
-        # MMAs actually issued: every (tile, active transfer vector) runs a full
-        # 128-row x cpad-column x cpad-deep product three times (3xTF32)
         cpad = ((C + 1 + 31) // 32) * 32
-        tile_t = int(work[12])
-        hw_flop = 3 * 2.0 * 128 * cpad * cpad * tile_t
+        if m2l_kind == 2:
+            # MMAs actually issued: every (tile, active transfer vector) runs a
+            # full 128-row x cpad-column x cpad-deep product three times (3xTF32)
+            hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
+        else:
+            # projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, 3xTF32
+            hw_flop = 3 * 2.0 * 128 * cpad * (int(work[14]) + int(work[15]))
         tensor_pipe = {"mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_leaf_ms / 1e3) / 1e12,
                        "frac_of_tf32_peak": hw_flop / (m2l_leaf_ms / 1e3) / 1e12 / peak}
     result = {
@@ -396,12 +399,13 @@ def run_ours(args):
                                 "k_m2l_tc (tcgen05, 3xTF32), all levels",
                                 "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
                                 "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels",
+                                "k_svd_proj_tc + k_svd_expand_tc (compressed, tcgen05, 3xTF32), all levels",
                                 ][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu",
                                                  "profiles/m2l_tc_cube_n1m_h6_p7.md",
                                                  "// L_T[m] = (1/a) * sum over the tile's groups")
-                     if tc_path and args.workload == WORKLOAD else None,
+                     if m2l_kind == 2 and args.workload == WORKLOAD else None,
                      "algorithmic": m2l_alg,
                      "peak_source": peak_note},
         "tensor_pipe": tensor_pipe,

@@ -173,7 +173,12 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
  * one source (each is one 128-row block of M2L products), out[13] = sum
  * over the M2L pairs of the rank of their compressed operator (0 until the
  * compressed operators exist; one pair costs 4 * order^3 * rank flop),
- * out[14..15] = 0.
+ * out[14] / out[15] = sum over the (M2L tile, transfer vector) blocks of the
+ * compressed projection / expansion of the Y columns per cell (the rank,
+ * rounded up to 16 on the mixed path; 0 until the compressed operators
+ * exist): the projection multiplies 128 x order^3 by order^3 x out[14]
+ * columns, the expansion 128 x out[15] by out[15] x order^3 (summed over
+ * blocks).
  * Synchronises the stream.  out: 16 int64, host. */
 fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 

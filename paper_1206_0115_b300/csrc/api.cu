@@ -129,6 +129,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
+    for (int k = 0; k < 9; ++k) s.push_back(c->cls_off[l][k]);  // baked into the compressed M2L's launches
     for (const void* p : {(const void*)c->lv.key[l], (const void*)c->lv.first[l], (const void*)c->lv.count[l],
                           (const void*)c->lv.parent[l], (const void*)c->lv.grid[l], (const void*)c->lv.cls[l]})
       s.push_back((int64_t)(uintptr_t)p);
@@ -140,6 +141,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                         (const void*)c->Khi, (const void*)c->Klo, (const void*)c->perm,
                         (const void*)c->tc_partial, (const void*)c->tc_err, (const void*)c->svd_Y,
                         (const void*)c->src_act, (const void*)c->svd_ry, (const void*)c->svd_V64,
+                        (const void*)c->svd_recs, (const void*)c->svd_Mcls, (const void*)c->svd_yidx,
                         (const void*)c->svd_U64, (const void*)c->svd_VThi, (const void*)c->svd_Uhi})
     s.push_back((int64_t)(uintptr_t)p);
   s.push_back(c->svd_rmax);
@@ -160,10 +162,14 @@ void drop_graph(Ctx* c) {
 // comes back with the previous evaluation's stream work).
 fmm_status check_device_error(Ctx* c) {
   if (c->tc_err_h && *(volatile int32_t*)c->tc_err_h) {
+    const int32_t e = *(volatile int32_t*)c->tc_err_h;
     *(volatile int32_t*)c->tc_err_h = 0;
     if (c->tc_err) cudaMemsetAsync(c->tc_err, 0, sizeof(int32_t), c->stream);
-    return set_err(c, FMM_ERR_TIMEOUT, "M2L tensor-core kernel: a pipeline wait ran out and the kernel returned "
-                                       "early; the previous evaluation's results are invalid");
+    if (e & 1)
+      return set_err(c, FMM_ERR_TIMEOUT, "M2L tensor-core kernel: a pipeline wait ran out and the kernel returned "
+                                         "early; the previous evaluation's results are invalid");
+    return set_err(c, FMM_ERR_CUDA, "M2L tensor-core path: internal work-table overflow (error word %d); the "
+                                    "previous evaluation's results are invalid", e);
   }
   return FMM_OK;
 }
@@ -289,8 +295,9 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
-                  c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi, c->svd_VTlo,
-                  c->svd_Uhi, c->svd_Ulo, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact};
+                  c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
+                  c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
+                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {

@@ -153,6 +153,17 @@ struct fmm_ctx {
   alignas(64) unsigned char tm_vthi[128], tm_vtlo[128], tm_uhi[128], tm_ulo[128];  // compressed banks
   const void* tm_svd_ptr = nullptr;
   int svd_tc_smem_set[2] = {0, 0}, svd_tc_nst = 0;
+  float* svd_Mcls = nullptr;       // multipoles in class order, interleaved hi/lo slabs
+  int svd_mcbase[FMM_MAX_LEVELS][8] = {{0}};  // first row of each (level, class) segment
+  int64_t svd_mcls_rows = 0;
+  alignas(64) unsigned char tm_mchi[128], tm_mclo[128];
+  const void* tm_mcls_ptr = nullptr;
+  void* svd_recs = nullptr;      // projection work units (records of k_svd_groups)
+  int16_t* svd_eslot = nullptr;  // expansion tables (k_svd_exp_setup)
+  int8_t* svd_ekch = nullptr;
+  int64_t* svd_yidx = nullptr;
+  int64_t svd_ecap = 0;
+  int64_t svd_gcap = 0;
   const void* tm_khi_ptr = nullptr;
   int tc_smem_set = 0, tc_nst = 0, num_sms = 0;
 
@@ -171,9 +182,10 @@ struct fmm_ctx {
   int8_t *svd_canon = nullptr, *svd_tcanon = nullptr;
   double *svd_V64 = nullptr, *svd_U64 = nullptr;  // [316][C][rmax]
   size_t svd_bank64_bytes = 0;
-  float *svd_VThi = nullptr, *svd_VTlo = nullptr;  // [316][rp][cpad]
-  float *svd_Uhi = nullptr, *svd_Ulo = nullptr;    // [316][cpad][rp], mean-split
-  size_t svd_bank32_bytes = 0;
+  float* svd_VThi = nullptr;  // mixed projection factors, interleaved hi/lo slabs per class (m2l_svd.cu)
+  float* svd_Uhi = nullptr;   // mixed expansion factors, interleaved hi/lo slabs, mean-split
+  size_t svd_vt_bytes = 0, svd_u_bytes = 0;
+  std::vector<int32_t> svd_yoff_h;
   int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_yoff = nullptr;  // [316], [316], [8][316]
   int64_t svd_YS = 0;            // Y values per cell row
   void* svd_Y = nullptr;         // Y[row][YS]: the projections of each cell's M, row = the expansion row

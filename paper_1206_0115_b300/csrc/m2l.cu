@@ -36,6 +36,8 @@ __global__ void __launch_bounds__(FMM_TILE)
 k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
                   const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
                   const int16_t* __restrict__ cls_t, const int32_t* __restrict__ trank,
+                  const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
+                  const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
                   unsigned long long* __restrict__ out) {
   const Tile tl = tiles[blockIdx.x];
   const int row = threadIdx.x, zero = lv.ncell[tl.level];
@@ -57,6 +59,18 @@ k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ ti
     atomicAdd(&out[13], rsum);
   }
   if (row == 0) atomicAdd(&out[12], (unsigned long long)nact);
+  if (row == 0 && t_ry) {
+    // 128-row blocks of the compressed M2L, in Y columns: projection (the
+    // tile's cells as sources) and expansion (as targets)
+    unsigned long long yp = 0, ye = 0;
+    const int ns = src_nact[blockIdx.x];
+    for (int a = 0; a < ns; ++a)
+      yp += t_ry[src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a]]];
+    for (int a = 0; a < nact; ++a)
+      ye += t_ry[cls_t[tl.cls * FMM_NT_CLASS + tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a]]];
+    atomicAdd(&out[14], yp);
+    atomicAdd(&out[15], ye);
+  }
 }
 
 __global__ void k_count_p2p_pairs(LevelPtrs lv, int leaf, int nleaf, unsigned long long* __restrict__ out) {
@@ -88,7 +102,8 @@ fmm_status work_counts(Ctx* c, int64_t* out) {
   if (c->ntiles > 0)
     k_count_m2l_pairs<<<c->ntiles, FMM_TILE, 0, c->stream>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact,
                                                              c->lv, c->cls_t, c->svd_ready ? c->svd_trank : nullptr,
-                                                             d);
+                                                             c->src_act, c->src_nact, c->src_t,
+                                                             c->svd_ready ? c->svd_ry : nullptr, d);
   FMM_CUDA(c, cudaGetLastError());
   FMM_CUDA(c, cudaMemcpyAsync(out, d, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -102,7 +117,7 @@ int64_t count_launches_eval(const Ctx* c) {
     k += 1 + (Lf - 2);                                      // P2M, M2M
     const int kind = m2l_kind(c), per = kind >= 3 ? 2 : 1;
     k += kind == 2 ? 2 * (c->ntiles > 0)
-                   : kind == 5 ? 3 * (c->ntiles > 0) : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));
+                   : kind == 5 ? (5 + (Lf - 1)) * (c->ntiles > 0) : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));
     k += (Lf - 2);                                          // L2L
   }
   return k;

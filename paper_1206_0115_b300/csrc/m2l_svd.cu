@@ -42,7 +42,7 @@
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmm {
 
@@ -51,11 +51,7 @@ namespace {
 constexpr int SVD_THREADS = 1024;
 constexpr int SVD_MAX_SWEEPS = 60;
 
-__device__ inline float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
+using tc::tf32_rna;
 
 // K_that[m][n] = 1 / |2 that + xbar_n - xbar_m| for the 16 canonical vectors.
 __global__ void k_canon_ops64(int p, int C, const double* __restrict__ nodes, const int8_t* __restrict__ canon,
@@ -207,39 +203,47 @@ __global__ void k_svd_banks64(int C, int R, const int8_t* __restrict__ t_canon, 
   }
 }
 
-// Mixed banks (TF32 hi/lo; zero-initialised by the caller):
-//   VT[t][i][sigma.n] = V_t, [316][Rp][cpad]  (the projection's B operand, K-major)
-//   U[t][sigma.m][i]  = U_t - mean_m U_t (rows < C), U[t][C][i] = the mean,
-//                       [316][cpad][Rp]       (the expansion's B operand, K-major)
-__global__ void k_svd_banks32(int C, int cpad, int Rp, const int8_t* __restrict__ t_canon,
+// Mixed banks (TF32 hi/lo, zero-initialised by the caller), in interleaved
+// hi/lo slabs of 64-byte rows (il_idx) along chunks of 16 of the contracted
+// index, so that a tensor-core operand slab is one contiguous block:
+//   VT (projection B, K = n): per source class, the class's transfer
+//     vectors stacked in the order of its Y rows: row G = (cls * (cpad / 16)
+//     + n / 16) * YS + yoff[cls][t] + i holds V_t[sigma.n][i];
+//   U (expansion B, K = i): row G = ((i / 16) * 316 + t) * cpad + sigma.m
+//     holds U_t - mean_m U_t (rows m < C) and the mean (row C).
+__global__ void k_svd_banks32(int C, int cpad, int64_t YS, const int8_t* __restrict__ t_canon,
                               const int16_t* __restrict__ sm, const int32_t* __restrict__ ord,
                               const int32_t* __restrict__ rank, const double* __restrict__ W,
                               const double* __restrict__ Z, const double* __restrict__ colmean,
-                              float* __restrict__ VThi, float* __restrict__ VTlo, float* __restrict__ Uhi,
-                              float* __restrict__ Ulo) {
+                              const int32_t* __restrict__ yoff, float* __restrict__ VT, float* __restrict__ U) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)FMM_NT * C) return;
   const int t = (int)(e / C), n = (int)(e - (int64_t)t * C);
   const int k = t_canon[t], r = rank[k];
   const int np = sm[e];
+  const int kch = cpad / 16;
   for (int i = 0; i < r; ++i) {
     const int j = ord[k * C + i];
     const double v = Z[((size_t)k * C + j) * C + n];
     const double u = W[((size_t)k * C + j) * C + n] - colmean[k * C + j];
-    const int64_t ov = ((int64_t)t * Rp + i) * cpad + np;
-    const int64_t ou = ((int64_t)t * cpad + np) * Rp + i;
-    float h = tf32_rna((float)v);
-    VThi[ov] = h;
-    VTlo[ov] = tf32_rna((float)(v - (double)h));
-    h = tf32_rna((float)u);
-    Uhi[ou] = h;
-    Ulo[ou] = tf32_rna((float)(u - (double)h));
+    const float vh = tf32_rna((float)v), vl = tf32_rna((float)(v - (double)vh));
+    for (int cls = 0; cls < 8; ++cls) {
+      const int yo = yoff[cls * FMM_NT + t];
+      if (yo < 0) continue;
+      const int64_t G = ((int64_t)cls * kch + (np >> 4)) * YS + yo + i;
+      VT[tc::il_idx(G, 0, np & 15)] = vh;
+      VT[tc::il_idx(G, 1, np & 15)] = vl;
+    }
+    const int64_t Gu = ((int64_t)(i >> 4) * FMM_NT + t) * cpad + np;
+    float h = tf32_rna((float)u);
+    U[tc::il_idx(Gu, 0, i & 15)] = h;
+    U[tc::il_idx(Gu, 1, i & 15)] = tf32_rna((float)(u - (double)h));
     if (n == 0) {  // the mean row
       const double mu = colmean[k * C + j];
-      const int64_t om = ((int64_t)t * cpad + C) * Rp + i;
+      const int64_t Gm = ((int64_t)(i >> 4) * FMM_NT + t) * cpad + C;
       h = tf32_rna((float)mu);
-      Uhi[om] = h;
-      Ulo[om] = tf32_rna((float)(mu - (double)h));
+      U[tc::il_idx(Gm, 0, i & 15)] = h;
+      U[tc::il_idx(Gm, 1, i & 15)] = tf32_rna((float)(mu - (double)h));
     }
   }
 }
@@ -291,8 +295,8 @@ k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict_
         T v = T(0);
         if (n < C && i < R) {
           if (MIXED) {
-            const int64_t o = ((int64_t)slot * R + i) * cpad + n;
-            v = Vb[o] + Vlo[o];
+            const int64_t G = ((int64_t)tl.cls * (cpad / 16) + (n >> 4)) * a.YS + a.yoff[tl.cls * FMM_NT + slot] + i;
+            v = Vb[tc::il_idx(G, 0, n & 15)] + Vb[tc::il_idx(G, 1, n & 15)];
           } else {
             v = Vb[((int64_t)slot * C + n) * R + i];
           }
@@ -369,8 +373,8 @@ k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restric
         T v = T(0);
         if (m < ncol && i < ry && i < R) {
           if (MIXED) {
-            const int64_t o = ((int64_t)slot * cpad + m) * R + i;
-            v = Ub[o] + Ulo[o];
+            const int64_t G = ((int64_t)(i >> 4) * FMM_NT + slot) * cpad + m;
+            v = Ub[tc::il_idx(G, 0, i & 15)] + Ub[tc::il_idx(G, 1, i & 15)];
           } else {
             v = Ub[((int64_t)slot * C + m) * R + i];
           }
@@ -549,20 +553,23 @@ fmm_status svd_banks(Ctx* c) {
     c->svd64 = true;
   }
   if (c->precision == FMM_MIXED && !c->svd32) {
+    // VT: 8 classes x cpad/16 chunks x YS rows; U: Rp/16 chunks x 316 x cpad rows; 2 halves x 16 floats per row
     const int Rp = c->svd_rp;
-    const size_t bytes = sizeof(float) * (size_t)FMM_NT * Rp * cp;
-    for (float** b : {&c->svd_VThi, &c->svd_VTlo, &c->svd_Uhi, &c->svd_Ulo}) {
-      dfree(c, *b, c->svd_bank32_bytes);
-      *b = nullptr;
-    }
-    for (float** b : {&c->svd_VThi, &c->svd_VTlo, &c->svd_Uhi, &c->svd_Ulo}) {
-      FMM_TRY(dalloc(c, &ptr, bytes));
-      *b = (float*)ptr;
-      FMM_CUDA(c, cudaMemsetAsync(ptr, 0, bytes, s));
-    }
-    c->svd_bank32_bytes = bytes;
-    k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, Rp, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d, c->svd_W,
-                                       c->svd_Z, c->svd_colmean, c->svd_VThi, c->svd_VTlo, c->svd_Uhi, c->svd_Ulo);
+    const size_t vbytes = sizeof(float) * 32 * (size_t)8 * (cp / 16) * c->svd_YS;
+    const size_t ubytes = sizeof(float) * 32 * (size_t)(Rp / 16) * FMM_NT * cp;
+    dfree(c, c->svd_VThi, c->svd_vt_bytes);
+    dfree(c, c->svd_Uhi, c->svd_u_bytes);
+    c->svd_VThi = c->svd_Uhi = nullptr;
+    FMM_TRY(dalloc(c, &ptr, vbytes));
+    c->svd_VThi = (float*)ptr;
+    FMM_CUDA(c, cudaMemsetAsync(ptr, 0, vbytes, s));
+    FMM_TRY(dalloc(c, &ptr, ubytes));
+    c->svd_Uhi = (float*)ptr;
+    FMM_CUDA(c, cudaMemsetAsync(ptr, 0, ubytes, s));
+    c->svd_vt_bytes = vbytes;
+    c->svd_u_bytes = ubytes;
+    k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
+                                       c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, c->svd_VThi, c->svd_Uhi);
     FMM_CUDA(c, cudaGetLastError());
     FMM_CUDA(c, cudaStreamSynchronize(s));
     c->svd32 = true;
@@ -576,7 +583,6 @@ fmm_status svd_banks(Ctx* c) {
 // evaluation is captured.
 fmm_status m2l_svd_prepare(Ctx* c) {
   FMM_TRY(svd_prepare(c));
-  FMM_TRY(svd_banks(c));
   const bool mixed = c->precision == FMM_MIXED;
   const std::vector<int64_t> sig = {c->precision, c->svd_gen};
   void* ptr;
@@ -607,7 +613,9 @@ fmm_status m2l_svd_prepare(Ctx* c) {
     FMM_CUDA(c, cudaMemcpy(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
     FMM_CUDA(c, cudaMemcpy(c->svd_yoff, yoff.data(), sizeof(int32_t) * yoff.size(), cudaMemcpyHostToDevice));
     c->svd_ysig = sig;
+    c->svd_yoff_h = yoff;
   }
+  FMM_TRY(svd_banks(c));  // the mixed factor bank is laid out by the Y offsets
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   const size_t ybytes = (size_t)(c->rows > 0 ? c->rows : 1) * c->svd_YS * esz;
   if (ybytes > c->svd_Y_cap) {
@@ -641,9 +649,9 @@ fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntile
   if (c->precision == FMM_MIXED) {
     dim3 ge(ntiles, 2, ceil_div(C + 1, 64));
     float* Y = (float*)c->svd_Y;
-    k_m2l_proj<float, true><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_VThi, c->svd_VTlo, c->Mhi,
+    k_m2l_proj<float, true><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_VThi, nullptr, c->Mhi,
                                                      c->Mlo, Y);
-    k_m2l_expand<float, true><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_Uhi, c->svd_Ulo, Y, c->L32,
+    k_m2l_expand<float, true><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_Uhi, nullptr, Y, c->L32,
                                                  c->box);
   } else {
     dim3 ge(ntiles, 2, ceil_div(C, 64));

@@ -3,27 +3,34 @@
 // sm_103a tensor cores, mixed precision, 3xTF32 (hi*hi + hi*lo + lo*hi).
 //
 // k_svd_proj_tc -- projection from the sources.  Work unit = (tile of 128
-//   cells of one level and class, group of up to G active source transfer
-//   vectors).  The A operand is the tile's multipoles (one row per cell),
-//   K = the cpad coefficients; B is the group's V_t factors side by side
-//   (VT bank rows, N = ry_t each), so each A chunk is loaded once for the G
-//   products.  Each t accumulates into its own columns of a TMEM accumulator
-//   (two buffers of SP_ACC columns alternate between units) and the epilogue
-//   writes them to the cells' Y rows.
+//   cells of one level and class, group of consecutive active source
+//   transfer vectors whose ranks add up to at most SP_ACC columns).  The A
+//   operand is the tile's multipoles, K = the cpad coefficients, copied from
+//   a class-ordered, pre-swizzled copy of M (k_gather_cls: a tile's slab of
+//   16 coefficients is one contiguous block); B is the group's V_t factors
+//   stacked (VT bank rows, also pre-swizzled); every slab arrives by one
+//   linear bulk copy, so the copy engine is not limited by per-row requests;
+//   so one MMA of N = sum of the ranks computes every product of the group
+//   and each A chunk is loaded once for all of them.  Each t owns a column
+//   range of the TMEM accumulator (two buffers of SP_ACC columns alternate
+//   between units); the epilogue writes the ranges to the cells' Y rows with
+//   streaming stores (Y is read once more, by the expansion).
 // k_svd_expand_tc -- expansion at the targets, the layout of k_m2l_tc
 //   (m2l_tc.cu): work unit = (target tile, half of the output columns, group
 //   of EX_GT active transfer vectors); the A operand is gathered from the
 //   sources' Y rows (ry_t values per t, split into TF32 hi/lo on the way into
 //   tensor memory; an absent source gives zeros), B = U_t (mean-split rows)
-//   by TMA, ry_t / 16 pipeline stages per t.  The tensor cores' FP32
+//   by linear bulk copies of pre-swizzled slabs, ry_t / 16 pipeline stages
+//   per t.  The tensor cores' FP32
 //   accumulation does not round to nearest, so an accumulator takes at most
 //   EX_TPA transfer vectors (a chain no longer than that of one full-rank
 //   operator) before the epilogue adds it into FP32 running sums in shared
 //   memory; k_m2l_tc_reduce adds a tile's group slices in FP64 and scales by
 //   1/a.
-// Roles per CTA (one CTA per SM, persistent): producer warps in sets of four
-// (one thread per row), four epilogue warps (one per TMEM lane quarter), one
-// MMA warp (one elected thread issues).  Every mbarrier wait is bounded in
+// Roles per CTA (one CTA per SM, persistent): producers (the projection: one
+// TMA thread; the expansion: warps in sets of four, one thread per row), four
+// epilogue warps (one per TMEM lane quarter), one MMA warp (one elected
+// thread issues).  Every mbarrier wait is bounded in
 // time; on expiry the CTA raises the error word, drains what it has in
 // flight (bounded), frees TMEM and returns.
 #include "tc_ptx.cuh"
@@ -38,55 +45,131 @@ constexpr int KC = 16;          // K elements per pipeline stage (64-byte rows)
 constexpr int MAXST = 4;        // pipeline stages at most
 
 // ---- projection -------------------------------------------------------------
-constexpr int SP_SETS = 2;                    // producer sets of four warps
-constexpr int SP_EPI = 4 * SP_SETS;           // first epilogue warp
-constexpr int SP_MMA = SP_EPI + 4;            // the MMA warp
-constexpr int SP_THREADS = 32 * (SP_MMA + 1);
-constexpr int SP_ACC = 192;                   // accumulator columns per buffer (two buffers)
-constexpr int SP_MAXG = 12;                   // transfer vectors per unit at most
+constexpr int SP_PROD = 0;                    // TMA producer warp (one thread issues)
+constexpr int SP_MMA = 1;                     // the MMA warp
+constexpr int SP_EPI = 2;                     // first of the four epilogue warps
+constexpr int SP_THREADS = 32 * (SP_EPI + 4);
+constexpr int SP_ACC = 256;                   // accumulator columns per buffer (two buffers: all of TMEM)
+constexpr int SP_MAXG = SP_ACC / 16;          // transfer vectors per group at most (ranks >= 16)
+constexpr int SP_A_BYTES = FMM_TILE * KC * 4; // one half (hi or lo) of a stage's A: 8 KB
+constexpr int SP_B_BYTES = SP_ACC * KC * 4;   // one half of a stage's B: 16 KB
+
+// One projection unit: a tile and a group of its active source transfer
+// vectors (consecutive, sum of ranks <= SP_ACC columns), written by
+// k_svd_groups so that the kernel's roles read one 64-byte record per unit
+// instead of chains of dependent index loads.
+struct __align__(16) ProjRec {
+  int32_t crow;            // row_off[level]: cell rows are crow + cls[level][first + r]
+  int32_t first;           // the tile's first position in the level's class list
+  int32_t arow;            // the tile's first row in the class-ordered multipole copy
+  int16_t count;           // cells in the tile
+  int8_t cls, level, n;    // child class, level, transfer vectors in the group (0: no unit)
+  uint8_t cols16;          // sum of ranks / 16
+  int16_t slot[SP_MAXG];   // transfer vectors
+  int16_t yo16[SP_MAXG];   // their Y offsets in the class's rows / 16 (= their factor rows)
+  uint8_t ry16[SP_MAXG];   // their ranks / 16
+  int32_t pad[7];
+};
+static_assert(sizeof(ProjRec) == 128, "one record = 128 bytes");
+
+// Where each (level, class) segment of the class-ordered multipole copy
+// starts (multiples of 128 rows, so that every tile starts a swizzle block).
+struct McBase {
+  int base[FMM_MAX_LEVELS][8];
+  int clsoff[FMM_MAX_LEVELS][8];
+};
 
 struct ProjArgs {
-  const Tile* tiles;
-  const int16_t* src_act;
-  const int32_t* src_nact;
-  const int16_t* src_t;
-  const int32_t* t_ry;
-  const int32_t* yoff;
+  const ProjRec* recs;   // [ntiles][ngroups]: unit u = tile * ngroups + group, so that CTAs running
+                         // at the same time share a tile's multipoles in L2
   float* Y;
   int32_t* err;
   int64_t YS;
-  int ntiles, G, ngroups, cpad, kchunks, nst, Rp;
+  int64_t mrows;         // rows of the class-ordered multipole copy per chunk of 16 coefficients
+  const float *Mc, *VT;  // interleaved hi/lo slabs (il_idx)
+  int ntiles, ngroups, kchunks, nst;
 };
 
-struct Group {
-  int n, cols;
-  int slot[SP_MAXG], ry[SP_MAXG], off[SP_MAXG];
-};
-
-__device__ inline void proj_group(const ProjArgs& a, int cls, int tile, int a0, int a1, Group& g) {
-  g.n = a1 - a0;
-  int o = 0;
-  for (int j = 0; j < SP_MAXG; ++j) {
-    if (j < g.n) {
-      const int k = a.src_act[(int64_t)tile * FMM_NT_CLASS + a0 + j];
-      const int slot = a.src_t[cls * FMM_NT_CLASS + k];
-      g.slot[j] = slot;
-      g.ry[j] = a.t_ry[slot];
-      g.off[j] = o;
-      o += g.ry[j];
+// Greedy grouping of each tile's active source transfer vectors into units
+// (one thread per tile; every record of the tile is written, n = 0 past the
+// last group).
+__global__ void k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs lv, McBase mb,
+                             const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
+                             const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
+                             const int32_t* __restrict__ yoff, ProjRec* __restrict__ recs,
+                             int32_t* __restrict__ err) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= ntiles) return;
+  const Tile tl = tiles[tile];
+  const int nact = src_nact[tile];
+  ProjRec r;
+  r.crow = (int32_t)lv.row_off[tl.level];
+  r.first = tl.first;
+  r.arow = mb.base[tl.level][tl.cls] + (tl.first - mb.clsoff[tl.level][tl.cls]);
+  r.count = (int16_t)tl.count;
+  r.cls = (int8_t)tl.cls;
+  r.level = (int8_t)tl.level;
+  int gi = 0, ai = 0;
+  while (gi < ngroups) {
+    int n = 0, cols = 0;
+    while (ai < nact && n < SP_MAXG) {
+      const int slot = src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)tile * FMM_NT_CLASS + ai]];
+      const int ry = t_ry[slot];
+      if (cols + ry > SP_ACC) break;
+      r.slot[n] = (int16_t)slot;
+      r.ry16[n] = (uint8_t)(ry / 16);
+      r.yo16[n] = (int16_t)(yoff[tl.cls * FMM_NT + slot] / 16);
+      cols += ry;
+      ++n;
+      ++ai;
     }
+    r.n = (int8_t)n;
+    r.cols16 = (uint8_t)(cols / 16);
+    recs[(int64_t)tile * ngroups + gi] = r;
+    ++gi;
   }
-  g.cols = o;
+  if (ai < nact) atomicOr(err, 2);  // more groups than the bound (cannot happen with ranks >= 16)
+}
+
+// The multipoles of each level in class order (the order of lv.cls), each
+// (level, class) segment starting at a multiple of 128 rows, so that the 128
+// cells of a tile are 128 consecutive rows of a swizzle-aligned slab:
+// Mc row (kc * rows + base[l][c] + j - clsoff[l][c]) = coefficients 16 kc ..
+// 16 kc + 15 of M[row_off + cls[j]], hi and lo interleaved (il_idx).  One
+// block per cell.
+__global__ void k_gather_cls(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
+                             const float* __restrict__ Mlo, float* __restrict__ Mc) {
+  const int j = blockIdx.x;
+  const int cell = lv.cls[l][j];
+  const int c = lv.key[l][cell] & 7;
+  const int64_t row = mb.base[l][c] + (j - mb.clsoff[l][c]), src = (lv.row_off[l] + cell) * cpad;
+  for (int k = threadIdx.x; k < cpad; k += blockDim.x) {
+    const int64_t G = (int64_t)(k >> 4) * rows + row;
+    Mc[il_idx(G, 0, k & 15)] = Mhi[src + k];
+    Mc[il_idx(G, 1, k & 15)] = Mlo[src + k];
+  }
+}
+
+__device__ inline ProjRec load_rec(const ProjRec* p) {
+  ProjRec r;
+  const int4* s = (const int4*)p;
+  int4* d = (int4*)&r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = s[i];
+  return r;
+}
+
+__device__ inline void st_cs_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
 __global__ void __launch_bounds__(SP_THREADS, 1)
-k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant__ CUtensorMap tm_vlo, ProjArgs a,
-              LevelPtrs lv, const float* __restrict__ Mhi, const float* __restrict__ Mlo) {
+k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t half_bytes = (uint32_t)SP_ACC * KC * 4;  // one half (hi or lo) of a stage's B
-  const uint32_t stage_bytes = 2u * half_bytes;
+  // stage s: A (128 rows, hi/lo interleaved) | B (stacked factor rows, hi/lo interleaved)
+  const uint32_t stage_bytes = 2u * SP_A_BYTES + 2u * SP_B_BYTES;
   const uint32_t bars = base + (uint32_t)a.nst * stage_bytes;
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (MAXST + s); };
@@ -96,12 +179,12 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
   unsigned char* gbase = smem_raw + (base - raw);
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(gbase + (bars - base) + 8u * (2 * MAXST + 6));
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  const uint32_t acol = 2u * SP_ACC, tmem_cols = 512;
+  const uint32_t tmem_cols = 2u * SP_ACC;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < MAXST; ++s) {
-      mbar_init(full(s), FMM_TILE + 1);  // 128 A-row producers + the B copies' expect_tx
+      mbar_init(full(s), 1);  // the producer's expect_tx
       mbar_init(empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -126,66 +209,59 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
   const uint32_t tmem = *tmem_slot;
   const int nunits = a.ntiles * a.ngroups;
 
-  if (warp < SP_EPI) {
-    // ---------------------------------------------------------- producers
-    const int set = warp >> 2;
-    const int r = threadIdx.x & (FMM_TILE - 1);
+  if (warp == SP_PROD) {
+    // ---------------------------------------------------------- copy producer
+    // per stage: the tile's slab of 16 coefficients (128 rows, one copy) and
+    // the group's factor rows (one copy per run of transfer vectors that are
+    // consecutive in the class's rows), issued by lanes after lane 0 has
+    // posted the stage's byte count
     uint32_t it = 0, last = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
-      const int gi = unit / a.ntiles, tile = unit - gi * a.ntiles;
-      const int nact = a.src_nact[tile];
-      const int a0 = gi * a.G, a1 = min(nact, a0 + a.G);
-      if (a0 >= a1) continue;
-      const Tile tl = a.tiles[tile];
-      Group g;
-      if (r == 0) proj_group(a, tl.cls, tile, a0, a1, g);
-      const int l = tl.level;
-      const int64_t cellrow = lv.row_off[l] + (r < tl.count ? lv.cls[l][tl.first + r] : lv.ncell[l]);
-      const float* ghi = Mhi + cellrow * a.cpad;
-      const float* glo = Mlo + cellrow * a.cpad;
-      const int kc0 = (set - (int)(it % SP_SETS) + SP_SETS) % SP_SETS;
-      for (int kc = kc0; kc < a.kchunks; kc += SP_SETS) {
-        const uint32_t j = it + (uint32_t)kc;
-        uint32_t vh[16], vl[16];
-        ld_v8(ghi + kc * KC, vh);
-        ld_v8(ghi + kc * KC + 8, vh + 8);
-        ld_v8(glo + kc * KC, vl);
-        ld_v8(glo + kc * KC + 8, vl + 8);
-        const int s = (int)(j % a.nst);
-        const uint32_t ph = (j / a.nst) & 1u;
+      const ProjRec g = load_rec(a.recs + unit);
+      if (g.n == 0) continue;
+      // lane q < n: the run of transfer vectors starting at q (if one starts there)
+      int off = 0, run = 0;
+      bool starts = false;
+      if (lane < g.n) {
+        for (int q = 0; q < lane; ++q) off += 16 * g.ry16[q];
+        starts = lane == 0 || g.yo16[lane] != g.yo16[lane - 1] + g.ry16[lane - 1];
+        if (starts) {
+          int q = lane;
+          do {
+            run += 16 * g.ry16[q];
+            ++q;
+          } while (q < g.n && g.yo16[q] == g.yo16[q - 1] + g.ry16[q - 1]);
+        }
+      }
+      for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+        const int s = (int)(it % a.nst);
+        const uint32_t ph = (it / a.nst) & 1u;
         if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
           ok = false;
           break;
         }
         const uint32_t st = base + (uint32_t)s * stage_bytes;
-        if (r == 0) {
-          mbar_expect_tx(full(s), 2u * (uint32_t)g.cols * KC * 4u);
-          for (int q = 0; q < g.n; ++q)
-            for (int b16 = 0; b16 < g.ry[q]; b16 += 16) {
-              const uint32_t dst = st + (uint32_t)(g.off[q] + b16) * (KC * 4);
-              const int y = g.slot[q] * a.Rp + b16;
-              tma_2d(dst, &tm_vhi, kc * KC, y, full(s));
-              tma_2d(dst + half_bytes, &tm_vlo, kc * KC, y, full(s));
-            }
+        const uint32_t sb = st + 2u * SP_A_BYTES;
+        if (lane == 0) mbar_expect_tx(full(s), 2u * SP_A_BYTES + (uint32_t)g.cols16 * 16u * 128u);
+        __syncwarp();
+        if (lane == SP_MAXG) {
+          bulk_g2s(st, a.Mc + ((int64_t)kc * a.mrows + g.arow) * 32, 2u * SP_A_BYTES, full(s));
+        } else if (starts) {
+          const int64_t G = ((int64_t)g.cls * a.kchunks + kc) * a.YS + 16 * g.yo16[lane];
+          bulk_g2s(sb + (uint32_t)off * 128u, a.VT + G * 32, (uint32_t)run * 128u, full(s));
         }
-        const uint32_t ta = tmem + ((uint32_t)(r & ~31) << 16) + acol + (uint32_t)s * 32u;
-        tmem_st16(ta, vh);
-        tmem_st16(ta + 16u, vl);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        mbar_arrive(full(s));
-        last = j + 1;
+        last = it + 1;
       }
-      it += (uint32_t)a.kchunks;
     }
-    if (!ok && lane == 0) {
-      *abort_flag = 1;
-      atomicOr(a.err, 1);
-    }
-    if (!ok && r == 0) {
-      for (uint32_t j = last > (uint32_t)a.nst ? last - a.nst : 0; j < last; ++j)
-        if ((int)(j % SP_SETS) == set) mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
+    if (!ok) {
+      if (lane == 0) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1);
+        // let the copies already issued land before the CTA leaves (bounded)
+        for (uint32_t j = last > (uint32_t)a.nst ? last - a.nst : 0; j < last; ++j)
+          mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
+      }
     }
     __syncwarp();
   } else if (warp == SP_MMA) {
@@ -193,13 +269,8 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
     uint32_t it = 0, uu = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
-      const int gi = unit / a.ntiles, tile = unit - gi * a.ntiles;
-      const int nact = a.src_nact[tile];
-      const int a0 = gi * a.G, a1 = min(nact, a0 + a.G);
-      if (a0 >= a1) continue;
-      const Tile tl = a.tiles[tile];
-      Group g;
-      proj_group(a, tl.cls, tile, a0, a1, g);
+      const int n = a.recs[unit].n, cols = 16 * a.recs[unit].cols16;
+      if (n == 0) continue;
       const int b = (int)(uu & 1u);
       if (!warp_wait(acc_empty(b), ((uu >> 1) & 1u) ^ 1u, abort_flag)) {
         ok = false;
@@ -207,6 +278,9 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
       }
       tc_fence_after();
       const uint32_t d0 = tmem + (uint32_t)(b * SP_ACC);
+      // the group's factors are stacked in the stage, so one MMA of
+      // N = sum of the ranks covers every transfer vector of the group
+      const uint32_t idesc = idesc_tf32(FMM_TILE, cols);
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
         const int s = (int)(it % a.nst);
         const uint32_t ph = (it / a.nst) & 1u;
@@ -217,20 +291,14 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
         tc_fence_after();
         if (lane == 0) {
           const uint32_t st = base + (uint32_t)s * stage_bytes;
-          const uint32_t a_hi = tmem + acol + (uint32_t)s * 32u;
-          for (int q = 0; q < g.n; ++q) {
-            const uint32_t idesc = idesc_tf32(FMM_TILE, g.ry[q]);
-            const uint32_t d = d0 + (uint32_t)g.off[q];
-            const uint32_t bq = st + (uint32_t)g.off[q] * (KC * 4);
+          const uint32_t sb = st + 2u * SP_A_BYTES;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint32_t ahi = a_hi + ks * 8u, alo = a_hi + 16u + ks * 8u;
-              const uint64_t bhi = sdesc_sw64(bq + ks * 32u);
-              const uint64_t blo = sdesc_sw64(bq + half_bytes + ks * 32u);
-              mma_tf32_ta(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-              mma_tf32_ta(d, ahi, blo, idesc, 1u);
-              mma_tf32_ta(d, alo, bhi, idesc, 1u);
-            }
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ahi = sdesc_sw64s(st + ks * 32u, 1024), alo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
+            const uint64_t bhi = sdesc_sw64s(sb + ks * 32u, 1024), blo = sdesc_sw64s(sb + 512u + ks * 32u, 1024);
+            mma_tf32(d0, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(d0, ahi, blo, idesc, 1u);
+            mma_tf32(d0, alo, bhi, idesc, 1u);
           }
           mma_commit(empty(s));
         }
@@ -250,42 +318,38 @@ k_svd_proj_tc(const __grid_constant__ CUtensorMap tm_vhi, const __grid_constant_
       mbar_wait(mma_done, 0);
     }
     __syncwarp();
-  } else if (warp < SP_MMA) {
+  } else {
     // ---------------------------------------------------------- epilogue
+    // TMEM lane quarter = warp % 4; row = the cell's position in the tile
     const int qd = warp & 3, row = qd * 32 + lane;
     uint32_t uu = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
-      const int gi = unit / a.ntiles, tile = unit - gi * a.ntiles;
-      const int nact = a.src_nact[tile];
-      const int a0 = gi * a.G, a1 = min(nact, a0 + a.G);
-      if (a0 >= a1) continue;
-      const Tile tl = a.tiles[tile];
-      Group g;
-      proj_group(a, tl.cls, tile, a0, a1, g);
+      const ProjRec g = load_rec(a.recs + unit);
+      if (g.n == 0) continue;
+      const bool valid = row < g.count;
+      const int64_t cellrow = valid ? (int64_t)g.crow + lv.cls[g.level][g.first + row] : 0;
       const int b = (int)(uu & 1u);
       if (!warp_wait(acc_full(b), (uu >> 1) & 1u, abort_flag)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const int l = tl.level;
-      const bool valid = row < tl.count;
-      const int64_t cellrow = lv.row_off[l] + (valid ? lv.cls[l][tl.first + row] : lv.ncell[l]);
       const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * SP_ACC);
+      int off = 0;
       for (int q = 0; q < g.n; ++q) {
-        float* y = a.Y + cellrow * a.YS + a.yoff[tl.cls * FMM_NT + g.slot[q]];
-        for (int c16 = 0; c16 < g.ry[q]; c16 += 16) {
+        float* y = a.Y + cellrow * a.YS + 16 * g.yo16[q];
+        for (int c16 = 0; c16 < 16 * g.ry16[q]; c16 += 16) {
           float v[16];
-          tmem_ld16(tb + (uint32_t)(g.off[q] + c16), v);
+          tmem_ld16(tb + (uint32_t)(off + c16), v);
           if (valid) {
-            float4* o = (float4*)(y + c16);
-            o[0] = make_float4(v[0], v[1], v[2], v[3]);
-            o[1] = make_float4(v[4], v[5], v[6], v[7]);
-            o[2] = make_float4(v[8], v[9], v[10], v[11]);
-            o[3] = make_float4(v[12], v[13], v[14], v[15]);
+            st_cs_v4(y + c16, v[0], v[1], v[2], v[3]);
+            st_cs_v4(y + c16 + 4, v[4], v[5], v[6], v[7]);
+            st_cs_v4(y + c16 + 8, v[8], v[9], v[10], v[11]);
+            st_cs_v4(y + c16 + 12, v[12], v[13], v[14], v[15]);
           }
         }
+        off += 16 * g.ry16[q];
       }
       tc_fence_before();
       mbar_arrive(acc_empty(b));
@@ -313,14 +377,12 @@ constexpr int EX_GROUPS = (FMM_NT_CLASS + EX_GT - 1) / EX_GT;
 constexpr int EX_TPA = 4;    // transfer vectors per accumulator before it is drained
 
 struct ExpArgs {
-  const Tile* tiles;
-  const int32_t* tile_src;
-  const int16_t* tile_act;
   const int32_t* tile_nact;
-  const int16_t* cls_t;
-  const int32_t* t_ry;
-  const int32_t* yoff;
+  const int16_t* eslot;   // [tile][189] operator slot of active transfer vector ai
+  const int8_t* ekch;     // [tile][189] its pipeline stages
+  const int64_t* yidx;    // [tile][189][128] first Y value of the row's source, -1 if none
   const float* Y;
+  const float* U;  // interleaved hi/lo slabs (il_idx)
   float* partial;  // [group][tile][128][cpad]
   int32_t* err;
   int64_t YS;
@@ -328,17 +390,44 @@ struct ExpArgs {
   uint32_t acol, tmem_cols;
 };
 
+// Per (tile, active transfer vector): the operator slot, its pipeline stages
+// (rank / 16), and per target row the first Y value of its source for t (-1:
+// no source), so that the expansion's roles read flat tables.  One block per
+// tile, one thread per row.
+__global__ void __launch_bounds__(FMM_TILE)
+k_svd_exp_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
+                const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
+                const int16_t* __restrict__ cls_t, const int32_t* __restrict__ t_ry, const int32_t* __restrict__ yoff,
+                int64_t YS, int16_t* __restrict__ eslot, int8_t* __restrict__ ekch, int64_t* __restrict__ yidx) {
+  const int tile = blockIdx.x, r = threadIdx.x;
+  const Tile tl = tiles[tile];
+  const int l = tl.level, zero = lv.ncell[l], nact = tile_nact[tile];
+  const int64_t rbase = lv.row_off[l];
+  for (int ai = 0; ai < nact; ++ai) {
+    const int k = tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
+    const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
+    if (r == 0) {
+      eslot[(int64_t)tile * FMM_NT_CLASS + ai] = (int16_t)slot;
+      ekch[(int64_t)tile * FMM_NT_CLASS + ai] = (int8_t)(t_ry[slot] / KC);
+    }
+    const int src = tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
+    yidx[((int64_t)tile * FMM_NT_CLASS + ai) * FMM_TILE + r] =
+        src == zero ? -1 : (rbase + src) * YS + yoff[(lv.key[l][src] & 7) * FMM_NT + slot];
+  }
+}
+
+// Unit u -> (group g, tile, column half h), the halves of a tile adjacent so
+// that CTAs running at the same time gather the same Y rows (L2 reuse).
 __device__ inline void exp_unit(const ExpArgs& a, int u, int& g, int& h, int& tile) {
   const int per_g = a.ntiles * a.nh;
   g = u / per_g;
   const int rem = u - g * per_g;
-  h = rem / a.ntiles;
-  tile = rem - h * a.ntiles;
+  tile = rem / a.nh;
+  h = rem - tile * a.nh;
 }
 
 __global__ void __launch_bounds__(EX_THREADS, 1)
-k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constant__ CUtensorMap tm_ulo, ExpArgs a,
-                LevelPtrs lv) {
+k_svd_expand_tc(ExpArgs a) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -399,18 +488,22 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
       const int nact = a.tile_nact[tile];
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
-      const Tile tl = a.tiles[tile];
-      const int l = tl.level, zero = lv.ncell[l];
-      const int64_t rbase = lv.row_off[l];
+      const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
+      // the next transfer vector's slot, stages and source offset are loaded
+      // while the current one is being copied
+      int nslot = a.eslot[tb + a0], nkch = a.ekch[tb + a0];
+      int64_t nyi = a.yidx[(tb + a0) * FMM_TILE + r];
       for (int ai = a0; ai < a1 && ok; ++ai) {
-        const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
-        const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
-        const int kch = a.t_ry[slot] / KC;
+        const int slot = nslot, kch = nkch;
+        const int64_t yi = nyi;
+        if (ai + 1 < a1) {
+          nslot = a.eslot[tb + ai + 1];
+          nkch = a.ekch[tb + ai + 1];
+          nyi = a.yidx[(tb + ai + 1) * FMM_TILE + r];
+        }
         const int kc0 = (set - (int)(it % EX_SETS) + EX_SETS) % EX_SETS;
         if (kc0 < kch) {
-          const int src = a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
-          const float* yr =
-              src == zero ? nullptr : a.Y + (rbase + src) * a.YS + a.yoff[(lv.key[l][src] & 7) * FMM_NT + slot];
+          const float* yr = yi < 0 ? nullptr : a.Y + yi;
           for (int kc = kc0; kc < kch; kc += EX_SETS) {
             const uint32_t j = it + (uint32_t)kc;
             uint32_t vh[16], vl[16];
@@ -437,9 +530,8 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
             const uint32_t st = base + (uint32_t)s * stage_bytes;
             if (r == 0) {
               mbar_expect_tx(full(s), 2u * b_bytes);
-              const int y = slot * a.cpad + h * a.nhalf;
-              tma_2d(st, &tm_uhi, kc * KC, y, full(s));
-              tma_2d(st + b_bytes, &tm_ulo, kc * KC, y, full(s));
+              const int64_t G = ((int64_t)kc * FMM_NT + slot) * a.cpad + h * a.nhalf;
+              bulk_g2s(st, a.U + G * 32, 2u * b_bytes, full(s));
             }
             const uint32_t ta = tmem + ((uint32_t)(r & ~31) << 16) + a.acol + (uint32_t)s * 32u;
             tmem_st16(ta, vh);
@@ -473,7 +565,10 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
       const int nact = a.tile_nact[tile];
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
-      const Tile tl = a.tiles[tile];
+      // stages of the unit's transfer vectors, two per lane (EX_GT = 64)
+      const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
+      const int kA = a0 + lane < a1 ? a.ekch[tb + a0 + lane] : 0;
+      const int kB = a0 + 32 + lane < a1 ? a.ekch[tb + a0 + 32 + lane] : 0;
       for (int ag = a0; ag < a1 && ok; ag += EX_TPA, ++tt) {
         const int ae = min(a1, ag + EX_TPA);
         const int b = (int)(tt & 1u);
@@ -485,8 +580,8 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
         const uint32_t d = tmem + (uint32_t)(b * a.nhalf);
         bool first = true;
         for (int ai = ag; ai < ae && ok; ++ai) {
-          const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
-          const int kch = a.t_ry[a.cls_t[tl.cls * FMM_NT_CLASS + k]] / KC;
+          const int u = ai - a0;
+          const int kch = __shfl_sync(0xffffffffu, u < 32 ? kA : kB, u & 31);
           for (int kc = 0; kc < kch; ++kc, ++it) {
             const int s = (int)(it % a.nst);
             const uint32_t ph = (it / a.nst) & 1u;
@@ -501,8 +596,8 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
                 const uint32_t ahi = ahi0 + ks * 8u, alo = ahi0 + 16u + ks * 8u;
-                const uint64_t bhi = sdesc_sw64(st + ks * 32u);
-                const uint64_t blo = sdesc_sw64(st + b_bytes + ks * 32u);
+                const uint64_t bhi = sdesc_sw64s(st + ks * 32u, 1024);
+                const uint64_t blo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
                 mma_tf32_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
                 mma_tf32_ta(d, ahi, blo, idesc, 1u);
                 mma_tf32_ta(d, alo, bhi, idesc, 1u);
@@ -583,8 +678,10 @@ k_svd_expand_tc(const __grid_constant__ CUtensorMap tm_uhi, const __grid_constan
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
-int sp_group(int Rp) { return std::max(1, std::min(SP_MAXG, SP_ACC / Rp)); }
-int sp_stage_bytes() { return 2 * SP_ACC * KC * 4; }
+// groups per tile at most: every group but the last holds more than SP_ACC - Rp columns
+int sp_ngroups(int Rp) { return (FMM_NT_CLASS * Rp + (SP_ACC - Rp)) / (SP_ACC - Rp + 1) + 1; }
+int sp_stage_bytes() { return 2 * SP_A_BYTES + 2 * SP_B_BYTES; }
+int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256) / sp_stage_bytes()); }
 int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256; }
 int ex_nhalf(int cp) { return cp > 256 ? cp / 2 : cp; }
 int ex_stage_bytes(int cp) { return 2 * ex_nhalf(cp) * KC * 4; }
@@ -621,19 +718,59 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     FMM_CUDA(c, cudaMemset(c->tc_err, 0, 64));
   }
   if (!c->tc_err_h) return set_err(c, FMM_ERR_STATE, "internal: no host error word");
-  if (c->tm_svd_ptr != c->svd_VThi) {
-    bool ok = encode_2d((CUtensorMap*)c->tm_vthi, c->svd_VThi, cp, (uint64_t)FMM_NT * Rp, KC, 16) &&
-              encode_2d((CUtensorMap*)c->tm_vtlo, c->svd_VTlo, cp, (uint64_t)FMM_NT * Rp, KC, 16) &&
-              encode_2d((CUtensorMap*)c->tm_uhi, c->svd_Uhi, Rp, (uint64_t)FMM_NT * cp, KC, nhalf) &&
-              encode_2d((CUtensorMap*)c->tm_ulo, c->svd_Ulo, Rp, (uint64_t)FMM_NT * cp, KC, nhalf);
-    if (!ok) return set_err(c, FMM_ERR_CUDA, "compressed M2L tensor path: cuTensorMapEncodeTiled failed");
-    c->tm_svd_ptr = c->svd_VThi;
+  const int64_t gneed = (int64_t)c->ntiles * sp_ngroups(Rp);
+  if (gneed > c->svd_gcap) {
+    dfree(c, c->svd_recs, sizeof(ProjRec) * (size_t)c->svd_gcap);
+    c->svd_recs = nullptr;
+    c->svd_gcap = 0;
+    void* p;
+    FMM_TRY(dalloc(c, &p, sizeof(ProjRec) * (size_t)gneed));
+    c->svd_recs = p;
+    c->svd_gcap = gneed;
+  }
+  // class-ordered copy of the multipoles (rows as M) and its tensor maps
+  if (c->ntiles > c->svd_ecap) {
+    dfree(c, c->svd_eslot, sizeof(int16_t) * (size_t)c->svd_ecap * FMM_NT_CLASS);
+    dfree(c, c->svd_ekch, sizeof(int8_t) * (size_t)c->svd_ecap * FMM_NT_CLASS);
+    dfree(c, c->svd_yidx, sizeof(int64_t) * (size_t)c->svd_ecap * FMM_NT_CLASS * FMM_TILE);
+    c->svd_eslot = nullptr;
+    c->svd_ekch = nullptr;
+    c->svd_yidx = nullptr;
+    c->svd_ecap = 0;
+    const int64_t cap = c->tiles_cap;
+    void* p;
+    FMM_TRY(dalloc(c, &p, sizeof(int16_t) * (size_t)cap * FMM_NT_CLASS));
+    c->svd_eslot = (int16_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int8_t) * (size_t)cap * FMM_NT_CLASS));
+    c->svd_ekch = (int8_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(int64_t) * (size_t)cap * FMM_NT_CLASS * FMM_TILE));
+    c->svd_yidx = (int64_t*)p;
+    c->svd_ecap = cap;
+  }
+  // class-ordered multipole copy: (level, class) segments rounded up to 128 rows
+  int64_t mrows = 0;
+  for (int l = 2; l <= c->leaf; ++l)
+    for (int k = 0; k < 8; ++k) {
+      c->svd_mcbase[l][k] = (int)mrows;
+      mrows += (c->cls_off[l][k + 1] - c->cls_off[l][k] + FMM_TILE - 1) / FMM_TILE * FMM_TILE;
+    }
+  mrows += FMM_TILE;
+  if (mrows > c->svd_mcls_rows) {
+    dfree(c, c->svd_Mcls, 8 * (size_t)c->svd_mcls_rows * cp);
+    c->svd_Mcls = nullptr;
+    c->svd_mcls_rows = 0;
+    const int64_t cap = (mrows + mrows / 8 + FMM_TILE - 1) / FMM_TILE * FMM_TILE;  // chunks start on 8-row groups
+    void* p;
+    FMM_TRY(dalloc(c, &p, 8 * (size_t)cap * cp));
+    FMM_CUDA(c, cudaMemset(p, 0, 8 * (size_t)cap * cp));
+    c->svd_Mcls = (float*)p;
+    c->svd_mcls_rows = cap;
   }
   // stages: shared memory and the TMEM columns beside the accumulators
   int nst = (227 * 1024 - ex_smem(cp, 0)) / ex_stage_bytes(cp);
   nst = std::min(nst, (512 - 2 * nhalf) / 32);
   nst = std::min(nst, MAXST);
-  const int nst_p = std::min(MAXST, (512 - 2 * SP_ACC) / 32);
+  const int nst_p = sp_nst();
   if (nst < 2 || nst_p < 2) return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: no room for 2 stages");
   c->svd_tc_nst = nst;
   if (sp_smem(nst_p) > c->svd_tc_smem_set[0]) {
@@ -654,36 +791,45 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp;
+  // multipoles in class order, every level with far field
+  const int64_t mrows = c->svd_mcls_rows;
+  McBase mb;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l)
+    for (int k = 0; k < 8; ++k) {
+      mb.base[l][k] = l >= 2 && l <= c->leaf ? c->svd_mcbase[l][k] : 0;
+      mb.clsoff[l][k] = c->cls_off[l][k];
+    }
+  for (int l = 2; l <= c->leaf; ++l)
+    if (c->lv.ncell[l] > 0)
+      k_gather_cls<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo, c->svd_Mcls);
   ProjArgs p;
-  p.tiles = c->tiles;
-  p.src_act = c->src_act;
-  p.src_nact = c->src_nact;
-  p.src_t = c->src_t;
-  p.t_ry = c->svd_ry;
-  p.yoff = c->svd_yoff;
   p.Y = (float*)c->svd_Y;
   p.err = c->tc_err;
   p.YS = c->svd_YS;
   p.ntiles = c->ntiles;
-  p.G = sp_group(Rp);
-  p.ngroups = (FMM_NT_CLASS + p.G - 1) / p.G;
-  p.cpad = cp;
+  p.ngroups = sp_ngroups(Rp);
+  p.recs = (const ProjRec*)c->svd_recs;
   p.kchunks = cp / KC;
-  p.nst = std::min(MAXST, (512 - 2 * SP_ACC) / 32);
-  p.Rp = Rp;
+  p.mrows = mrows;
+  p.Mc = c->svd_Mcls;
+  p.VT = c->svd_VThi;
+  p.nst = sp_nst();
+  k_svd_groups<<<ceil_div(c->ntiles, 128), 128, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
+                                                       c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
+                                                       (ProjRec*)c->svd_recs, c->tc_err);
   const int up = p.ntiles * p.ngroups;
-  k_svd_proj_tc<<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(
-      *(const CUtensorMap*)c->tm_vthi, *(const CUtensorMap*)c->tm_vtlo, p, c->lv, c->Mhi, c->Mlo);
+  k_svd_proj_tc<<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
   FMM_CUDA(c, cudaGetLastError());
+  k_svd_exp_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
+                                                 c->svd_ry, c->svd_yoff, c->svd_YS, c->svd_eslot, c->svd_ekch,
+                                                 c->svd_yidx);
   ExpArgs e;
-  e.tiles = c->tiles;
-  e.tile_src = c->tile_src;
-  e.tile_act = c->tile_act;
   e.tile_nact = c->tile_nact;
-  e.cls_t = c->cls_t;
-  e.t_ry = c->svd_ry;
-  e.yoff = c->svd_yoff;
+  e.eslot = c->svd_eslot;
+  e.ekch = c->svd_ekch;
+  e.yidx = c->svd_yidx;
   e.Y = (const float*)c->svd_Y;
+  e.U = c->svd_Uhi;
   e.partial = c->tc_partial;
   e.err = c->tc_err;
   e.YS = c->svd_YS;
@@ -696,8 +842,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
   const int ue = c->ntiles * e.nh * EX_GROUPS;
-  k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(
-      *(const CUtensorMap*)c->tm_uhi, *(const CUtensorMap*)c->tm_ulo, e, c->lv);
+  k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
   FMM_CUDA(c, cudaGetLastError());
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
   return launch_m2l_tc_reduce(c, s, c->tc_partial, EX_GT);

@@ -67,6 +67,43 @@ __device__ inline void tma_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
       : "memory");
 }
 
+// Linear copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on an mbarrier's transaction count.
+__device__ inline void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Position of element e (0..15) of row r in a K-major slab of 64-byte rows
+// under the 64-byte swizzle: 16-byte chunk c of row r sits at chunk
+// c ^ ((r >> 1) & 3) (the pattern repeats every 8 rows), so that data
+// stored this way in global memory lands correctly with a linear copy into
+// a 512-byte-aligned shared-memory slab.
+__host__ __device__ inline int sw64_pos(int r, int e) { return ((((e >> 2) ^ (r >> 1)) & 3) << 2) | (e & 3); }
+
+// Interleaved hi/lo slabs: row G of a stack of 64-byte rows keeps its TF32 hi
+// row and lo row in the same 1 KB block of its 8-row group (hi in the first
+// 512 B, lo in the second), each in the 64-byte swizzled order; so one linear
+// copy brings both halves of a slab, and the two halves are read with
+// descriptors 512 B apart whose 8-row groups are 1024 B apart.
+// Index (in floats) of element e (0..15) of row G, half lo (0 hi, 1 lo).
+__host__ __device__ inline int64_t il_idx(int64_t G, int lo, int e) {
+  return ((((G >> 3) << 4) + (lo << 3) + (G & 7)) << 4) + sw64_pos((int)(G & 7), e);
+}
+
+// Shared-memory matrix descriptor, K-major, 64-byte swizzle: rows of 64 B,
+// 8-row groups `sbo` bytes apart (512: dense; 1024: interleaved hi/lo slabs).
+__device__ inline uint64_t sdesc_sw64s(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(sbo >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // Shared-memory matrix descriptor, K-major, 64-byte swizzle: rows of 64 B,
 // 8-row groups 512 B apart.
 __device__ inline uint64_t sdesc_sw64(uint32_t saddr) {
