@@ -91,44 +91,69 @@ struct ProjArgs {
 };
 
 // Greedy grouping of each tile's active source transfer vectors into units
-// (one thread per tile; every record of the tile is written, n = 0 past the
-// last group).
-__global__ void k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs lv, McBase mb,
-                             const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
-                             const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
-                             const int32_t* __restrict__ yoff, ProjRec* __restrict__ recs,
-                             int32_t* __restrict__ err) {
-  const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tile >= ntiles) return;
+// (every record of the tile is written, n = 0 past the last group).  One
+// block per tile: the threads fetch the ranks and offsets, one thread draws
+// the group boundaries, the threads write the records.
+__global__ void __launch_bounds__(256)
+k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs lv, McBase mb,
+             const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
+             const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
+             const int32_t* __restrict__ yoff, ProjRec* __restrict__ recs, int32_t* __restrict__ err) {
+  __shared__ int16_t s_slot[FMM_NT_CLASS];
+  __shared__ int16_t s_yo16[FMM_NT_CLASS];
+  __shared__ uint8_t s_ry16[FMM_NT_CLASS];
+  __shared__ int16_t s_gs[FMM_NT_CLASS + 2];
+  __shared__ int s_ng;
+  const int tile = blockIdx.x;
   const Tile tl = tiles[tile];
   const int nact = src_nact[tile];
-  ProjRec r;
-  r.crow = (int32_t)lv.row_off[tl.level];
-  r.first = tl.first;
-  r.arow = mb.base[tl.level][tl.cls] + (tl.first - mb.clsoff[tl.level][tl.cls]);
-  r.count = (int16_t)tl.count;
-  r.cls = (int8_t)tl.cls;
-  r.level = (int8_t)tl.level;
-  int gi = 0, ai = 0;
-  while (gi < ngroups) {
-    int n = 0, cols = 0;
-    while (ai < nact && n < SP_MAXG) {
-      const int slot = src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)tile * FMM_NT_CLASS + ai]];
-      const int ry = t_ry[slot];
-      if (cols + ry > SP_ACC) break;
-      r.slot[n] = (int16_t)slot;
-      r.ry16[n] = (uint8_t)(ry / 16);
-      r.yo16[n] = (int16_t)(yoff[tl.cls * FMM_NT + slot] / 16);
+  for (int a = threadIdx.x; a < nact; a += blockDim.x) {
+    const int slot = src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)tile * FMM_NT_CLASS + a]];
+    s_slot[a] = (int16_t)slot;
+    s_ry16[a] = (uint8_t)(t_ry[slot] / 16);
+    s_yo16[a] = (int16_t)(yoff[tl.cls * FMM_NT + slot] / 16);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0, cols = 0, members = 0;
+    for (int a = 0; a < nact; ++a) {
+      const int ry = 16 * s_ry16[a];
+      if (a == 0 || cols + ry > SP_ACC || members == SP_MAXG) {
+        s_gs[n++] = (int16_t)a;
+        cols = 0;
+        members = 0;
+      }
       cols += ry;
-      ++n;
-      ++ai;
+      ++members;
+    }
+    s_gs[n] = (int16_t)nact;
+    s_ng = n;
+    if (n > ngroups) atomicOr(err, 2);  // more groups than the bound (cannot happen with ranks >= 16)
+  }
+  __syncthreads();
+  const int ng = min(s_ng, ngroups);
+  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+    ProjRec r;
+    r.crow = (int32_t)lv.row_off[tl.level];
+    r.first = tl.first;
+    r.arow = mb.base[tl.level][tl.cls] + (tl.first - mb.clsoff[tl.level][tl.cls]);
+    r.count = (int16_t)tl.count;
+    r.cls = (int8_t)tl.cls;
+    r.level = (int8_t)tl.level;
+    int n = 0, cols = 0;
+    if (gi < ng) {
+      const int a0 = s_gs[gi], a1 = s_gs[gi + 1];
+      for (int a = a0; a < a1; ++a, ++n) {
+        r.slot[n] = s_slot[a];
+        r.ry16[n] = s_ry16[a];
+        r.yo16[n] = s_yo16[a];
+        cols += 16 * s_ry16[a];
+      }
     }
     r.n = (int8_t)n;
     r.cols16 = (uint8_t)(cols / 16);
     recs[(int64_t)tile * ngroups + gi] = r;
-    ++gi;
   }
-  if (ai < nact) atomicOr(err, 2);  // more groups than the bound (cannot happen with ranks >= 16)
 }
 
 // The multipoles of each level in class order (the order of lv.cls), each
@@ -390,10 +415,12 @@ struct ExpArgs {
   uint32_t acol, tmem_cols;
 };
 
+constexpr int EXS_CHUNK = 8;  // active transfer vectors per setup block
+
 // Per (tile, active transfer vector): the operator slot, its pipeline stages
 // (rank / 16), and per target row the first Y value of its source for t (-1:
 // no source), so that the expansion's roles read flat tables.  One block per
-// tile, one thread per row.
+// (tile, chunk of EXS_CHUNK transfer vectors), one thread per row.
 __global__ void __launch_bounds__(FMM_TILE)
 k_svd_exp_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
                 const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
@@ -403,7 +430,8 @@ k_svd_exp_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile
   const Tile tl = tiles[tile];
   const int l = tl.level, zero = lv.ncell[l], nact = tile_nact[tile];
   const int64_t rbase = lv.row_off[l];
-  for (int ai = 0; ai < nact; ++ai) {
+  const int a_end = min(nact, (int)(blockIdx.y + 1) * EXS_CHUNK);
+  for (int ai = blockIdx.y * EXS_CHUNK; ai < a_end; ++ai) {
     const int k = tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
     const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
     if (r == 0) {
@@ -814,13 +842,13 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.Mc = c->svd_Mcls;
   p.VT = c->svd_VThi;
   p.nst = sp_nst();
-  k_svd_groups<<<ceil_div(c->ntiles, 128), 128, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
+  k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
                                                        c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
                                                        (ProjRec*)c->svd_recs, c->tc_err);
   const int up = p.ntiles * p.ngroups;
   k_svd_proj_tc<<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
   FMM_CUDA(c, cudaGetLastError());
-  k_svd_exp_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
+  k_svd_exp_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
                                                  c->svd_ry, c->svd_yoff, c->svd_YS, c->svd_eslot, c->svd_ekch,
                                                  c->svd_yidx);
   ExpArgs e;

@@ -314,8 +314,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
-// L_T[m] = (1/a) * sum over the tile's groups of the partial sums (FP64).
-// Block (tile, slice): rows 16*slice .. 16*slice+15 of the tile.
+// L_T[m] = (1/a) * sum over the tile's groups of the partial sums: at most
+// three FP32 slices, added in FP32.  Block (tile, slice): rows 16*slice ..
+// 16*slice+15 of the tile, four coefficients per thread.
 __global__ void __launch_bounds__(256)
 k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_nact, LevelPtrs lv, int ntiles,
                 int gt, int cpad, int ncol, const float* __restrict__ partial, float* __restrict__ L,
@@ -325,14 +326,21 @@ k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile
   if (r0 >= tl.count) return;
   const int nrow = min(16, tl.count - r0);
   const int ng = (tile_nact[tile] + gt - 1) / gt;
-  const double inv_a = ldexp(1.0, tl.level + 1) / box[3];
+  const float inv_a = (float)(ldexp(1.0, tl.level + 1) / box[3]);
   const int64_t rbase = lv.row_off[tl.level];
-  for (int idx = threadIdx.x; idx < nrow * ncol; idx += blockDim.x) {
-    const int row = r0 + idx / ncol, col = idx % ncol;
-    double s = 0.0;
-    for (int g = 0; g < ng; ++g) s += (double)partial[(((int64_t)g * ntiles + tile) * FMM_TILE + row) * cpad + col];
+  const int nq = (ncol + 3) / 4;  // float4 columns (cpad is a multiple of 32)
+  for (int idx = threadIdx.x; idx < nrow * nq; idx += blockDim.x) {
+    const int row = r0 + idx / nq, c4 = 4 * (idx % nq);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int g = 0; g < ng; ++g) {
+      const float4 v = *(const float4*)&partial[(((int64_t)g * ntiles + tile) * FMM_TILE + row) * cpad + c4];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
     const int cell = lv.cls[tl.level][tl.first + row];
-    L[(rbase + cell) * cpad + col] = (float)(s * inv_a);
+    *(float4*)&L[(rbase + cell) * cpad + c4] = make_float4(s.x * inv_a, s.y * inv_a, s.z * inv_a, s.w * inv_a);
   }
 }
 
