@@ -273,7 +273,7 @@ k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lb
 // ---------------------------------------------------------------- L2P + output
 
 template <int P, typename T, bool MIXED>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
 k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const T* __restrict__ cheb,
           int cpad, const T* __restrict__ L, int has_far, const double4* __restrict__ pos64,
           const float4* __restrict__ pos32, const float4* __restrict__ near32,
@@ -317,7 +317,9 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
       interp_weights<P, T, true>(sC, xi[1], Sy, dSy);
       interp_weights<P, T, true>(sC, xi[2], Sz, dSz);
       T f = T(0), ax = T(0), ay = T(0), az = T(0);
-#pragma unroll
+      // the x loop stays rolled: unrolling all P^3 terms needs more registers
+      // than occupancy allows
+#pragma unroll 1
       for (int mx = 0; mx < P; ++mx) {
 #pragma unroll
         for (int my = 0; my < P; ++my) {
