@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--m2l", choices=["full", "svd"], default="full",
+    ap.add_argument("--m2l", choices=["full", "svd"], default="svd",
                     help="M2L operators: full-rank K_t, or the SVD-compressed canonical operators (eps = 10^-p)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -288,6 +288,8 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage = []
+    ktimes = []
+    tc_timed = int(stats[4]) in (2, 5)
     clocks = Clocks(local)
     if ws > 1:
         torch.distributed.barrier()
@@ -301,6 +303,8 @@ def run_ours(args):
         step()
         ends[k].record(stream)
         stage.append(fmm.fmm_get_stage_times(f.h).tolist())
+        if tc_timed:
+            ktimes.append(fmm.fmm_get_m2l_kernel_times(f.h).tolist())
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     if ws > 1:
@@ -349,10 +353,9 @@ def run_ours(args):
     else:
         m2l_flop = 2.0 * C * C * m2l_pairs
         m2l_alg = f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per evaluation"
-    # the tensor-core kernel covers every level in one launch (stage [2]; the
-    # FP64 reduction of its partial sums is stage [3]); the CUDA-core kernels
-    # are timed over all levels (stage [1])
-    m2l_ms = m2l_leaf_ms if m2l_kind in (2, 5) else float(np.mean(stage[:, 1]))
+    # the tensor-core kernels cover every level in one launch each and are
+    # timed by their own events; the CUDA-core kernels over all levels (stage [1])
+    kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
     p2p_pairs = int(work[0])
     tc_path = m2l_kind in (2, 5)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
@@ -362,20 +365,51 @@ def run_ours(args):
         bound, peak, peak_note = "alu", fp32_peak, "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock"
     else:
         bound, peak, peak_note = "alu", fp32_peak / 64.0, "FP64 FMA: FP32 rate / 64 (nominal ratio)"
-    achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
     p2p_gflop = 20.0 * p2p_pairs / 1e9
     tensor_pipe = None
-    if tc_path:
-        cpad = ((C + 1 + 31) // 32) * 32
-        if m2l_kind == 2:
-            # MMAs actually issued: every (tile, active transfer vector) runs a
-            # full 128-row x cpad-column x cpad-deep product three times (3xTF32)
-            hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
-        else:
-            # projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, 3xTF32
-            hw_flop = 3 * 2.0 * 128 * cpad * (int(work[14]) + int(work[15]))
-        tensor_pipe = {"mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_leaf_ms / 1e3) / 1e12,
-                       "frac_of_tf32_peak": hw_flop / (m2l_leaf_ms / 1e3) / 1e12 / peak}
+    roofline_proj = None
+    cpad = ((C + 1 + 31) // 32) * 32
+    if m2l_kind == 5:
+        # the dominant kernel is the expansion; each half carries 2 C r flop per pair
+        kernel_name = "k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, 3xTF32), all levels"
+        half_flop = m2l_flop / 2.0
+        m2l_ms = float(kt[1])
+        achieved = half_flop / (m2l_ms / 1e3) / 1e12
+        m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
+                   f"(the projection carries as much)")
+        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
+                                    "// groups per tile at most")
+                   if args.workload == WORKLOAD else None)
+        # MMAs issued: projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, 3xTF32
+        hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
+        hw_e = 3 * 2.0 * 128 * cpad * int(work[15])
+        tensor_pipe = {"expansion": {"mma_flop_per_launch": hw_e, "tflops": hw_e / (kt[1] / 1e3) / 1e12,
+                                     "frac_of_tf32_peak": hw_e / (kt[1] / 1e3) / 1e12 / peak},
+                       "projection": {"mma_flop_per_launch": hw_p, "tflops": hw_p / (kt[0] / 1e3) / 1e12,
+                                      "frac_of_tf32_peak": hw_p / (kt[0] / 1e3) / 1e12 / peak}}
+        ach_p = half_flop / (kt[0] / 1e3) / 1e12
+        roofline_proj = {"kernel": "k_svd_proj_tc (compressed M2L projection y = V^T M, tcgen05, 3xTF32)",
+                         "bound": "tensor", "achieved": ach_p, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach_p / peak, "ms": float(kt[0]), "peak_source": peak_note}
+    elif m2l_kind == 2:
+        kernel_name = "k_m2l_tc (full-rank M2L, tcgen05, 3xTF32), all levels"
+        m2l_ms = float(kt[1])
+        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
+        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu", "profiles/m2l_tc_cube_n1m_h6_p7.md",
+                                    "// L_T[m] = (1/a) * sum over the tile's groups")
+                   if args.workload == WORKLOAD else None)
+        # every (tile, active transfer vector) runs a 128-row x cpad x cpad product three times
+        hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
+        tensor_pipe = {"mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_ms / 1e3) / 1e12,
+                       "frac_of_tf32_peak": hw_flop / (m2l_ms / 1e3) / 1e12 / peak}
+    else:
+        kernel_name = ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
+                       "k_m2l_simt<float> (FP32 CUDA cores), all levels", "",
+                       "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
+                       "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels"][m2l_kind]
+        m2l_ms = float(np.mean(stage[:, 1]))
+        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
+        traffic = None
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -394,20 +428,10 @@ def run_ours(args):
                      "evaluate": float(np.mean(stage[:, 7]))},
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
-        "roofline": {"kernel": ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
-                                "k_m2l_simt<float> (FP32 CUDA cores), all levels",
-                                "k_m2l_tc (tcgen05, 3xTF32), all levels",
-                                "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
-                                "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels",
-                                "k_svd_proj_tc + k_svd_expand_tc (compressed, tcgen05, 3xTF32), all levels",
-                                ][m2l_kind], "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu",
-                                                 "profiles/m2l_tc_cube_n1m_h6_p7.md",
-                                                 "// L_T[m] = (1/a) * sum over the tile's groups")
-                     if m2l_kind == 2 and args.workload == WORKLOAD else None,
-                     "algorithmic": m2l_alg,
-                     "peak_source": peak_note},
+        "roofline": {"kernel": kernel_name, "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "ms": m2l_ms,
+                     "algorithmic": m2l_alg, "peak_source": peak_note},
+        "roofline_m2l_projection": roofline_proj,
         "tensor_pipe": tensor_pipe,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)",
                          "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),

@@ -198,6 +198,16 @@ fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 fmm_status fmm_set_timing(fmm_handle h, int mode);
 fmm_status fmm_get_stage_times(fmm_handle h, float* out);
 
+/* Device times in milliseconds of the tensor-core M2L kernels of the last
+ * timed fmm_evaluate (Sec. 2.1.2's M2L; CUDA events recorded around each
+ * launch inside the evaluation graph while fmm_set_timing is on):
+ * out[0] = the compressed projection y = V^T M (k_svd_proj_tc; 0 on the
+ * full-rank path), out[1] = the compressed expansion L += U y
+ * (k_svd_expand_tc) or the full-rank product (k_m2l_tc).  Synchronises the
+ * stream.  Errors: FMM_ERR_STATE (timing off, no timed evaluation, or an M2L
+ * path that does not run on the tensor cores).  out: 2 floats, host. */
+fmm_status fmm_get_m2l_kernel_times(fmm_handle h, float* out);
+
 /* Allocation-free Morton ordering (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they
  * run -- processes whose HBM is owned by a pool reserved at start-up, such as

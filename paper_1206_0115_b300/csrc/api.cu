@@ -249,7 +249,7 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
     cuda_err(c, cudaGetLastError(), "fmm_create: stream/event creation");
     return fail(FMM_ERR_CUDA);
   }
-  for (int k = 0; k < 10; ++k)
+  for (int k = 0; k < 14; ++k)
     if (cudaEventCreate(&c->tev[k]) != cudaSuccess) {
       cuda_err(c, cudaGetLastError(), "fmm_create: event creation");
       return fail(FMM_ERR_CUDA);
@@ -312,7 +312,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  for (int k = 0; k < 10; ++k)
+  for (int k = 0; k < 14; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   delete c;
   return FMM_OK;
@@ -540,6 +540,26 @@ fmm_status fmm_get_stage_times(fmm_handle h, float* out) {
   out[5] = el(5, 6);  // P2P
   out[6] = el(7, 8);  // L2P + output
   out[7] = el(0, 8);  // whole evaluation (from the branch start)
+  return FMM_OK;
+}
+
+fmm_status fmm_get_m2l_kernel_times(fmm_handle h, float* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  Ctx* c = h;
+  const int kind = m2l_kind(c);
+  if (!c->tev_recorded || (kind != 2 && kind != 5) || c->ntiles == 0)
+    return set_err(c, FMM_ERR_STATE, "fmm_get_m2l_kernel_times: no timed evaluation on the tensor-core M2L path");
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  auto el = [&](int a, int b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->tev[a], c->tev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    return ms;
+  };
+  out[0] = kind == 5 ? el(9, 10) : 0.f;
+  out[1] = el(11, 12);
   return FMM_OK;
 }
 

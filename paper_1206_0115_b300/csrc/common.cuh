@@ -139,7 +139,7 @@ struct fmm_ctx {
   int graph_precision = -1;
   bool use_graph = true;
   int timing = 0;  // 0 off, 1 events in the overlapped schedule, 2 events with P2P run alone
-  cudaEvent_t tev[10] = {nullptr};
+  cudaEvent_t tev[14] = {nullptr};  // [9..12]: around the tensor-core M2L kernels
   bool tev_recorded = false;
 
   // tensor-core M2L

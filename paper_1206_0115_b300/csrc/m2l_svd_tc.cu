@@ -846,8 +846,10 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
                                                        c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
                                                        (ProjRec*)c->svd_recs, c->tc_err);
   const int up = p.ntiles * p.ngroups;
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[9], s, cudaEventRecordExternal));
   k_svd_proj_tc<<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
   FMM_CUDA(c, cudaGetLastError());
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[10], s, cudaEventRecordExternal));
   k_svd_exp_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
                                                  c->svd_ry, c->svd_yoff, c->svd_YS, c->svd_eslot, c->svd_ekch,
                                                  c->svd_yidx);
@@ -870,8 +872,10 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
   const int ue = c->ntiles * e.nh * EX_GROUPS;
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
   k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
   FMM_CUDA(c, cudaGetLastError());
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
   return launch_m2l_tc_reduce(c, s, c->tc_partial, EX_GT);
 }

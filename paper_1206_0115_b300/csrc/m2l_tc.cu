@@ -438,9 +438,11 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   const int smem = c->tc_nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
   const int nunits = c->ntiles * nh * TC_GROUPS;
   const int grid = nunits < c->num_sms ? nunits : c->num_sms;
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
   k_m2l_tc<<<grid, TC_THREADS, smem, s>>>(*(const CUtensorMap*)c->tm_khi, *(const CUtensorMap*)c->tm_klo, a,
                                           c->lv, c->Mhi, c->Mlo);
   FMM_CUDA(c, cudaGetLastError());
+  if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
   k_m2l_tc_reduce<<<dim3(c->ntiles, FMM_TILE / 16), 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, TC_GT, cp, c->ncoef + 1,
                                             c->tc_partial, c->L32, c->box);

@@ -50,6 +50,7 @@ _SIGS = {
     "fmm_get_work": [_vp, _vp],
     "fmm_set_timing": [_vp, C.c_int],
     "fmm_get_stage_times": [_vp, _vp],
+    "fmm_get_m2l_kernel_times": [_vp, _vp],
     "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
@@ -175,6 +176,12 @@ def fmm_set_timing(h, mode) -> int:
 def fmm_get_stage_times(h) -> np.ndarray:
     out = np.zeros(8, dtype=np.float32)
     _check(h, lib.fmm_get_stage_times(h, _ptr(out)))
+    return out
+
+
+def fmm_get_m2l_kernel_times(h) -> np.ndarray:
+    out = np.zeros(2, dtype=np.float32)
+    _check(h, lib.fmm_get_m2l_kernel_times(h, _ptr(out)))
     return out
 
 
