@@ -143,7 +143,7 @@ def profiled_traffic(kernel_file: str, profile: str, marker: str):
     cut = src.find(marker)
     h = hashlib.sha256((src[:cut] if cut >= 0 else src).encode()).hexdigest()
     m = re.search(r"kernel-source-sha256: ([0-9a-f]{64})", text)
-    t = re.search(r"dram-traffic-bytes-per-launch \| (\d+)", text)
+    t = re.search(r"dram-traffic-bytes-per-launch[^|\n]*\|[ |]*(\d+)", text)
     if not m or not t or m.group(1) != h:
         return None
     return int(t.group(1))
@@ -378,7 +378,7 @@ def run_ours(args):
         m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
                    f"(the projection carries as much)")
         traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
-                                    "// groups per tile at most")
+                                    "int sp_ngroups(int Rp)")
                    if args.workload == WORKLOAD else None)
         # MMAs issued: projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, 3xTF32
         hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
@@ -454,10 +454,184 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+BATCH_WORKLOAD = "batched_256_p5"
+
+
+def run_batched(args):
+    """256 independent problems of uneven size (1e3 .. 2e5 particles, heights
+    3..6 by size, cube or ellipsoid by seed, p = 5) solved as one batch: a step
+    is fmm_set_batch + fmm_evaluate over all of them (one launch per stage)."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0115_b300 import build, inputs
+    build.build()
+    from paper_1206_0115_b300 import fmm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = 5
+    counts, heights, xyz_np, q_np = inputs.batch_workload(seed=999 + 1000 * rank)
+    n = int(counts.sum())
+    prec = fmm.FMM_MIXED if args.precision == "mixed" else fmm.FMM_FP64
+    stream = torch.cuda.Stream(device=dev)
+    method = fmm.FMM_M2L_SVD if args.m2l == "svd" else fmm.FMM_M2L_FULL
+    f = fmm.FMM(3, p, prec, stream=stream, m2l=method)
+    xyz = torch.from_numpy(xyz_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        f.set_batch(counts, heights, xyz, q)
+        f.evaluate(phi, F)
+
+    fmm.fmm_set_timing(f.h, 1)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    work = fmm.fmm_get_work(f.h)
+    stats = f.stats()
+    fmm.fmm_set_timing(f.h, 2)
+    iso = []
+    for _ in range(3):
+        step()
+        iso.append(fmm.fmm_get_stage_times(f.h).tolist())
+    iso = np.median(np.array(iso), axis=0)
+    fmm.fmm_set_timing(f.h, 1)
+    step()
+    torch.cuda.synchronize()
+    tc_timed = int(stats[4]) in (2, 5)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ktimes = []
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        f.set_batch(counts, heights, xyz, q)
+        mids[k].record(stream)
+        f.evaluate(phi, F)
+        ends[k].record(stream)
+        if tc_timed:
+            ktimes.append(fmm.fmm_get_m2l_kernel_times(f.h).tolist())
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    build_ms = [a.elapsed_time(b) for a, b in zip(starts, mids)]
+    value, total_ms = replica_throughput(n, args.steps, sum(ms), device=dev)
+
+    xyz_h = torch.from_numpy(xyz_np).pin_memory()
+    q_h = torch.from_numpy(q_np).pin_memory()
+    phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.set_batch(counts, heights, xyz_h, q_h)
+        f.evaluate(phi_h, F_h)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e_ms.append(a.elapsed_time(b))
+    e2e_value = replica_throughput(n, len(e_ms), sum(e_ms), device=dev)[0] if e_ms else None
+    if rank != 0:
+        f.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    pk = peaks()
+    C = p ** 3
+    cpad = ((C + 1 + 31) // 32) * 32
+    peak = pk["bf16"] * TF32_OVER_BF16
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
+    half_flop = 2.0 * C * int(work[13])
+    p2p_pairs = int(work[0])
+    p2p_ms = float(iso[5])
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "problems": int(len(counts)), "n_total": n,
+                   "n_min": int(counts.min()), "n_max": int(counts.max()),
+                   "heights": {str(hh): int((heights == hh).sum()) for hh in sorted(set(heights.tolist()))},
+                   "order": p, "precision": args.precision, "m2l": args.m2l,
+                   "distribution": "cube (even seed) / ellipsoid surface (odd seed)", "charges": "pos",
+                   "batch_tree_leaf_level": int(f.batch_info(0)[0][4]),
+                   "l2": "flushed between steps (512 MB rewrite outside the timed events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "set_batch_ms": float(np.mean(build_ms)),
+        "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
+                              "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
+        "roofline": None if kt is None else {
+            "kernel": "k_svd_expand_tc (compressed M2L expansion, tcgen05, 3xTF32), all problems and levels",
+            "bound": "tensor", "achieved": half_flop / (kt[1] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": half_flop / (kt[1] / 1e3) / 1e12 / peak, "traffic": None, "ms": float(kt[1]),
+            "algorithmic": f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch",
+            "peak_source": f"TF32 = {pk['src']} bf16 x 1.1/2.25"},
+        "roofline_m2l_projection": None if kt is None else {
+            "kernel": "k_svd_proj_tc", "achieved": half_flop / (kt[0] / 1e3) / 1e12, "peak": peak,
+            "unit": "TFLOP/s", "frac": half_flop / (kt[0] / 1e3) / 1e12 / peak, "ms": float(kt[0])},
+        "tensor_pipe": None if kt is None else {
+            "expansion_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
+            "projection_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
+        "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)", "interactions": p2p_pairs,
+                         "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
+                         "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2)},
+        "gpu_launches": int((stats[0] + stats[1]) * args.steps),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
+                "d2h_bytes_per_step": int(32 * n), "steps": len(e_ms)},
+        "clocks": clk,
+    }
+    f.close()
+    if ws == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: the first 8 problems, one after another
+        import oracle
+        from paper_1206_0115_b300 import inputs as _inp
+        st = np.concatenate([[0], np.cumsum(counts)])
+        ops = oracle_operators({"order": p}, args.m2l)
+        t0 = time.perf_counter()
+        m = 0
+        for k in range(8):
+            a, b = st[k], st[k + 1]
+            with oracle.OracleFMM(xyz_np[a:b], q_np[a:b], int(heights[k]), p, svd_from=ops) as o:
+                o.evaluate()
+            m += b - a
+        t = time.perf_counter() - t0
+        result["cpu_baseline"] = {"value": m / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                  "sample": f"problems 0..7 of the batch ({m} particles) one after another, FP64 "
+                                            f"oracle FMM ({args.m2l} M2L operators, computed beforehand), {t:.2f} s"}
+    print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batched(args)
     else:
         run_ours(args)
 

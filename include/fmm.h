@@ -115,9 +115,52 @@ fmm_status fmm_get_svd_ranks(fmm_handle h, int32_t* ranks);
  * coordinate or charge -- detected on the device), FMM_ERR_OOM, FMM_ERR_CUDA. */
 fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const double* q);
 
-/* Runs one FMM pass over the particles of the last fmm_set_particles:
- * P2M, M2M, M2L, L2L, L2P on one branch and P2P on another (Sec. 3.2), and
- * writes phi [n] and F [n][3] (FP64) in the caller's input order.
+/* Loads a batch of nprob independent problems (1 .. 4096) and builds one
+ * tree over all of them, so that every later fmm_evaluate runs each stage of
+ * the method for the whole batch in one launch.  Problem k has counts[k]
+ * particles (0 allowed) and its own tree of heights[k] levels (1..10), and is
+ * solved exactly as fmm_set_particles + fmm_evaluate would solve it alone on
+ * a handle of that height and the handle's order: its own root cube,
+ * Morton keys and cells (Sec. 3.2, Sec. 4.2), no interaction with any other
+ * problem.
+ *   xyz: [sum counts][3] FP64 and q: [sum counts] FP64 (device or host), the
+ *   problems' particles one after another in problem order.
+ * Layout: problem k occupies an aligned slot of the batch tree -- one cell of
+ * level Lf - (heights[k] - 1), where Lf is the batch tree's leaf level -- and
+ * its particles are mapped into that cell (coordinates scaled by
+ * lambda_k = slot width / W_k); cells of different problems are never
+ * neighbours; fmm_evaluate rescales phi by lambda_k and F by lambda_k^2, so the
+ * outputs are in each problem's own units, in the concatenated input order.
+ * The slots' leaf cells, sum over problems of 8^(heights[k]-1), must fit in
+ * 8^9.  The handle's own height is not used (fmm_set_particles restores it);
+ * the introspection calls (fmm_get_order, fmm_get_level_*, fmm_get_box,
+ * fmm_get_work, fmm_get_expansion) describe the batch tree.  Synchronises the
+ * stream.
+ * Errors: FMM_ERR_ARG (nprob, a count or a height out of range, too many
+ * leaf cells, NULL with particles, a non-finite input), FMM_ERR_OOM,
+ * FMM_ERR_CUDA. */
+fmm_status fmm_set_batch(fmm_handle h, int32_t nprob, const int64_t* counts, const int32_t* heights,
+                         const double* xyz, const double* q);
+
+/* Problem k of the last fmm_set_batch:
+ *   info[0] = Morton rank of its first particle in the batch tree (its
+ *             particles hold ranks info[0] .. info[0] + info[1] - 1, in the
+ *             problem's own Morton order),
+ *   info[1] = particle count, info[2] = level of its slot cell in the batch
+ *   tree (-1 if it has no particles), info[3] = first leaf key of the slot
+ *   (the problem's own leaf key of a particle is its batch leaf key minus
+ *   info[3]), info[4] = leaf level of the batch tree, info[5] = the problem's
+ *   height, info[6] = index of its first particle in the input, info[7] = 0;
+ *   box[0..3] = the problem's root cube (lower corner, side), as
+ *   fmm_get_box would report it for the problem alone.
+ * Either pointer may be NULL.  Host memory.  Errors: FMM_ERR_STATE (no batch
+ * loaded), FMM_ERR_ARG (k out of range). */
+fmm_status fmm_get_batch_info(fmm_handle h, int32_t k, int64_t* info, double* box);
+
+/* Runs one FMM pass over the particles of the last fmm_set_particles (or
+ * fmm_set_batch): P2M, M2M, M2L, L2L, L2P on one branch and P2P on another
+ * (Sec. 3.2), and writes phi [n] and F [n][3] (FP64) in the caller's input
+ * order.
  * Device outputs: the call returns after enqueueing (stream-ordered).
  * Host outputs: the call returns after the results are in host memory.
  * Errors: FMM_ERR_STATE (no particles loaded), FMM_ERR_ARG (NULL with

@@ -125,13 +125,15 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 // Everything the captured evaluation graph bakes into its kernel arguments.
 std::vector<int64_t> graph_signature(const Ctx* c) {
   std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
-                            c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items};
+                            c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
+                            (int64_t)(uintptr_t)c->fb_scale};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
     for (int k = 0; k < 9; ++k) s.push_back(c->cls_off[l][k]);  // baked into the compressed M2L's launches
     for (const void* p : {(const void*)c->lv.key[l], (const void*)c->lv.first[l], (const void*)c->lv.count[l],
-                          (const void*)c->lv.parent[l], (const void*)c->lv.grid[l], (const void*)c->lv.cls[l]})
+                          (const void*)c->lv.parent[l], (const void*)c->lv.grid[l], (const void*)c->lv.cls[l],
+                          (const void*)c->lv.slot[l]})
       s.push_back((int64_t)(uintptr_t)p);
   }
   for (const void* p : {(const void*)c->pos32, (const void*)c->pos32lo, (const void*)c->pos64, (const void*)c->near32,
@@ -297,11 +299,13 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
-                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx};
+                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx,
+                  c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_sstart, c->fb_sprob, c->fb_bstart};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
-    void* lb[] = {c->lv.key[l], c->lv.first[l], c->lv.count[l], c->lv.parent[l], c->lv.grid[l], c->lv.cls[l]};
+    void* lb[] = {c->lv.key[l], c->lv.first[l], c->lv.count[l], c->lv.parent[l], c->lv.grid[l], c->lv.cls[l],
+                  c->slot_buf[l]};
     for (void* b : lb)
       if (b) cudaFree(b);
   }
@@ -376,7 +380,70 @@ fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const d
     dxyz = c->stage_in;
     dq = c->stage_in + 3 * n;
   }
+  c->forest = false;
+  c->nprob = 0;
+  c->leaf = c->height - 1;
   FMM_TRY(tree_build(c, n, dxyz, dq));
+  return FMM_OK;
+}
+
+fmm_status fmm_set_batch(fmm_handle h, int32_t nprob, const int64_t* counts, const int32_t* heights,
+                         const double* xyz, const double* q) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  c->loaded = false;
+  if (nprob < 1 || nprob > FMM_MAX_BATCH)
+    return set_err(c, FMM_ERR_ARG, "fmm_set_batch: nprob = %d outside 1..%d", nprob, FMM_MAX_BATCH);
+  if (!counts || !heights) return set_err(c, FMM_ERR_ARG, "fmm_set_batch: NULL counts or heights");
+  int64_t n = 0;
+  for (int k = 0; k < nprob; ++k) {
+    if (counts[k] < 0 || counts[k] > ((int64_t)1 << 30))
+      return set_err(c, FMM_ERR_ARG, "fmm_set_batch: count[%d] = %lld outside 0..2^30", k, (long long)counts[k]);
+    if (heights[k] < 1 || heights[k] > FMM_MAX_FOREST_LEAF + 1)
+      return set_err(c, FMM_ERR_ARG, "fmm_set_batch: height[%d] = %d outside 1..%d", k, heights[k],
+                     FMM_MAX_FOREST_LEAF + 1);
+    n += counts[k];
+  }
+  if (n > ((int64_t)1 << 30)) return set_err(c, FMM_ERR_ARG, "fmm_set_batch: %lld particles > 2^30", (long long)n);
+  if (n > 0 && (!xyz || !q)) return set_err(c, FMM_ERR_ARG, "fmm_set_batch: NULL input with particles");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  const double* dxyz = xyz;
+  const double* dq = q;
+  if (n > 0 && !(is_device_ptr(xyz) && is_device_ptr(q))) {
+    FMM_TRY(ensure_stage(c, &c->stage_in, &c->stage_in_cap, 4 * n));
+    FMM_CUDA(c, cudaMemcpyAsync(c->stage_in, xyz, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->stage_in + 3 * n, q, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+    dxyz = c->stage_in;
+    dq = c->stage_in + 3 * n;
+  }
+  int64_t total = 0;
+  FMM_TRY(batch_layout(c, nprob, counts, heights, &total));
+  FMM_TRY(tree_build(c, total, dxyz, dq));
+  return FMM_OK;
+}
+
+fmm_status fmm_get_batch_info(fmm_handle h, int32_t k, int64_t* info, double* box) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  if (!c->loaded || !c->forest) return set_err(c, FMM_ERR_STATE, "fmm_get_batch_info: no batch loaded");
+  if (k < 0 || k >= c->nprob) return set_err(c, FMM_ERR_ARG, "fmm_get_batch_info: problem %d outside 0..%d", k,
+                                             c->nprob - 1);
+  const int64_t cnt = c->fb_start_h[k + 1] - c->fb_start_h[k];
+  if (info) {
+    info[0] = c->fb_first_h[k];
+    info[1] = cnt;
+    info[2] = cnt > 0 ? c->fb_prob_h[k].S : -1;
+    info[3] = cnt > 0 ? (int64_t)c->fb_prob_h[k].slot_key : -1;
+    info[4] = c->leaf;
+    info[5] = c->fb_prob_h[k].L + 1;
+    info[6] = c->fb_start_h[k];
+    info[7] = 0;
+  }
+  if (box) {
+    const bool has = cnt > 0 && c->fb_box_h.size() >= 4 * (size_t)(k + 1);
+    for (int d = 0; d < 4; ++d) box[d] = has ? c->fb_box_h[4 * k + d] : (d == 3 ? 1.0 : 0.0);
+  }
   return FMM_OK;
 }
 

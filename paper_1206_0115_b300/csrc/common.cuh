@@ -16,6 +16,14 @@
 //     (the source row of a missing M2L neighbour).
 //   M2L operators: 316 transfer vectors t (|t|_inf in {2,3}) in lexicographic
 //     order; K_t[m][n] = 1 / |2t + xbar_n - xbar_m| for unit half-width.
+//   batched problems (fmm_set_batch): one octree over a unit "forest" cube in
+//     which problem k owns an aligned slot, the cell of level S_k = Lf - L_k
+//     (L_k its own leaf level) whose leaf keys are [slot_k, slot_k + 8^L_k);
+//     its particles are mapped into the slot by x' = o_k + (x - lo_k) 2^-S_k / W_k,
+//     cells carry the problem of their slot (slot[l][cell], -1 above the
+//     slots), and cells of different problems are never neighbours, so every
+//     stage runs over all problems in one launch; results are rescaled by
+//     lambda_k = 2^-S_k / W_k (phi * lambda, F * lambda^2) on output.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -50,9 +58,30 @@ struct LevelPtrs {
   int32_t* parent[FMM_MAX_LEVELS];
   int32_t* grid[FMM_MAX_LEVELS];
   int32_t* cls[FMM_MAX_LEVELS];
+  int32_t* slot[FMM_MAX_LEVELS];  // batched trees: problem of each cell (-1: none); nullptr for one problem
   int64_t row_off[FMM_MAX_LEVELS];
   int32_t ncell[FMM_MAX_LEVELS];  // host-known sizes (valid after the readback)
 };
+
+// Batched trees: whether cell g at level l may interact with a cell whose
+// problem is `mine` (the problem of the asking cell; -1 above the slots).
+__host__ __device__ inline bool same_problem(const LevelPtrs& lv, int l, int mine, int g) {
+  return !lv.slot[l] || (mine >= 0 && lv.slot[l][g] == mine);
+}
+__host__ __device__ inline int problem_of(const LevelPtrs& lv, int l, int cell) {
+  return lv.slot[l] ? lv.slot[l][cell] : 0;
+}
+
+// One problem of a batch (device copy, input order).
+struct BatchProb {
+  uint32_t slot_key;  // first forest leaf key of the problem's slot
+  int32_t L;          // the problem's own leaf level (height - 1)
+  int32_t S;          // level of its slot cell in the forest (Lf - L)
+  int32_t pad;
+};
+
+#define FMM_MAX_FOREST_LEAF 9  // leaf level of a batched tree at most (dense grid 8^9 x 4 bytes)
+#define FMM_MAX_BATCH 4096     // problems per batch at most
 
 }  // namespace fmm
 
@@ -97,10 +126,29 @@ struct fmm_ctx {
   // tree
   LevelPtrs lv;
   int64_t lcap[FMM_MAX_LEVELS] = {0};  // capacity (cells) of the per-level arrays
+  int32_t* slot_buf[FMM_MAX_LEVELS] = {nullptr};  // storage of lv.slot (set only for batched trees)
+  int prev_leaf = -1;                  // leaf level of the previous tree (its grid entries get cleared)
   int32_t cls_off[FMM_MAX_LEVELS][9] = {{0}};
   int prev_ncell[FMM_MAX_LEVELS] = {0};
   bool have_prev = false;
   double box_host[4] = {0, 0, 0, 1};
+
+  // batched problems (fmm_set_batch)
+  bool forest = false;             // the current tree holds a batch
+  int nprob = 0, fb_cap = 0, fb_bcap = 0;
+  std::vector<int64_t> fb_start_h;   // [nprob + 1] input offsets
+  std::vector<fmm::BatchProb> fb_prob_h;
+  std::vector<int64_t> fb_first_h;   // [nprob] first Morton rank of each problem
+  std::vector<double> fb_box_h;      // [nprob][4] after the build
+  int64_t* fb_pstart = nullptr;      // [nprob + 1]
+  fmm::BatchProb* fb_prob = nullptr; // [nprob]
+  double* fb_box = nullptr;          // [nprob][4]: lo, W
+  double* fb_scale = nullptr;        // [nprob]: lambda_k (output scale)
+  uint32_t* fb_sstart = nullptr;     // [nslot]: slot start keys, ascending
+  int32_t* fb_sprob = nullptr;       // [nslot]: problem of each slot
+  int32_t* fb_bstart = nullptr;      // [nprob + 1]: bounding-box blocks per problem (prefix)
+  int fb_nslot = 0;
+  int fb_nblocks = 0;                // bounding-box blocks of the batch
 
   // expansions
   int64_t rows = 0, rows_cap = 0;
@@ -223,6 +271,8 @@ void dfree(Ctx* c, void* p, size_t bytes);
 
 // ---- stages (host launchers) -------------------------------------------------
 fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q);
+// slots of a batch (sets c->forest, c->leaf and the device tables); *n_total = sum of counts
+fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total);
 fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);

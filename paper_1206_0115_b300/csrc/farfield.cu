@@ -278,7 +278,7 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
           int cpad, const T* __restrict__ L, int has_far, const double4* __restrict__ pos64,
           const float4* __restrict__ pos32, const float4* __restrict__ near32,
           const double4* __restrict__ near64, const int32_t* __restrict__ perm, double* __restrict__ phi,
-          double* __restrict__ F) {
+          double* __restrict__ F, const double* __restrict__ fscale) {
   constexpr int C = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sL = (T*)smem_raw;
@@ -297,6 +297,9 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
   const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
   double ctr[3], a;
   cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  // batched trees: back from the forest cube to the problem's own units
+  const int prob = fscale ? lv.slot[leaf][cell] : -1;
+  const double lam = prob >= 0 ? fscale[prob] : 1.0, lam2 = lam * lam;
   for (int r = first + lane; r < first + cnt; r += 32) {
     double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
     if (has_far) {
@@ -357,10 +360,10 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
       nz = nr.w;
     }
     const int64_t i = perm[r];
-    phi[i] = pf + nphi;
-    F[3 * i] = gx + nx;
-    F[3 * i + 1] = gy + ny;
-    F[3 * i + 2] = gz + nz;
+    phi[i] = (pf + nphi) * lam;
+    F[3 * i] = (gx + nx) * lam2;
+    F[3 * i + 1] = (gy + ny) * lam2;
+    F[3 * i + 2] = (gz + nz) * lam2;
   }
 }
 
@@ -527,11 +530,11 @@ fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
   if (c->precision == FMM_MIXED)
     k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
         c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
-        c->perm, phi, F);
+        c->perm, phi, F, c->forest ? c->fb_scale : nullptr);
   else
     k_l2p_out<P, double, false><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(double), s>>>(
         c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32, c->near64,
-        c->perm, phi, F);
+        c->perm, phi, F, c->forest ? c->fb_scale : nullptr);
   return cuda_err(c, cudaGetLastError(), "L2P launch");
 }
 

@@ -84,7 +84,7 @@ __global__ void k_count_p2p_pairs(LevelPtrs lv, int leaf, int nleaf, unsigned lo
     const int sx = ix + k / 9 - 1, sy = iy + (k / 3) % 3 - 1, sz = iz + k % 3 - 1;
     if (sx < 0 || sy < 0 || sz < 0 || sx > top || sy > top || sz > top) continue;
     const int g = lv.grid[leaf][morton3(sx, sy, sz)];
-    if (g >= 0) src += lv.count[leaf][g];
+    if (g >= 0 && same_problem(lv, leaf, problem_of(lv, leaf, T), g)) src += lv.count[leaf][g];
   }
   const unsigned long long nt = lv.count[leaf][T];
   atomicAdd(&out[0], nt * src - nt);

@@ -110,6 +110,7 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
   int ix, iy, iz;
   demorton3(lv.key[leaf][T], ix, iy, iz);
   const int top = (1 << leaf) - 1;
+  const int mine = problem_of(lv, leaf, T);
   // neighbour j of lane j: lane 0 is the target leaf itself, lanes 1..26 the others
   int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
   if (lane < 27) {
@@ -120,7 +121,7 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
     const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
     if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
       const int g = lv.grid[leaf][morton3(sx, sy, sz)];
-      if (g >= 0) {
+      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
         nf = lv.first[leaf][g];
         ncnt = lv.count[leaf][g];
       }
@@ -232,12 +233,13 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
   int ix, iy, iz;
   demorton3(lv.key[leaf][T], ix, iy, iz);
   const int top = (1 << leaf) - 1;
+  const int mine = problem_of(lv, leaf, T);
   int nf = 0, ncnt = 0;
   if (lane < 27) {
     const int sx = ix + lane / 9 - 1, sy = iy + (lane / 3) % 3 - 1, sz = iz + lane % 3 - 1;
     if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
       const int g = lv.grid[leaf][morton3(sx, sy, sz)];
-      if (g >= 0) {
+      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
         nf = lv.first[leaf][g];
         ncnt = lv.count[leaf][g];
       }

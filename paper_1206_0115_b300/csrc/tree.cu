@@ -8,6 +8,7 @@
 // cells grouped by child class -> M2L tiles and their source lists.
 // Every step is integer or exact, so the tree is bit-identical to any other
 // implementation of the same rules.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -254,6 +255,182 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uin
   pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
 }
 
+// ---- batched problems (one tree over all problems' slots) ----------------------
+
+constexpr int FB_CHUNK = BB_THREADS * 8;  // particles per bounding-box block
+
+// last k in [0, cnt) with a[k] <= v (a ascending, a[0] <= v)
+template <typename A, typename V>
+__device__ inline int last_le(const A* __restrict__ a, int cnt, V v) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((V)a[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-block min/max of one problem's chunk (blocks of a problem are
+// consecutive: bstart[k] .. bstart[k+1]); raises the flag on non-finite input.
+__global__ void __launch_bounds__(BB_THREADS)
+k_fbox_partial(int nprob, const int32_t* __restrict__ bstart, const int64_t* __restrict__ pstart,
+               const double* __restrict__ xyz, const double* __restrict__ q, double* __restrict__ part,
+               int32_t* __restrict__ counters) {
+  const int k = last_le(bstart, nprob, (int32_t)blockIdx.x);
+  const int64_t beg = pstart[k] + (int64_t)(blockIdx.x - bstart[k]) * FB_CHUNK;
+  const int64_t end = min(pstart[k + 1], beg + FB_CHUNK);
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int bad = 0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += BB_THREADS) {
+    for (int d = 0; d < 3; ++d) {
+      const double v = xyz[3 * i + d];
+      bad |= !isfinite(v);
+      mn[d] = fmin(mn[d], v);
+      mx[d] = fmax(mx[d], v);
+    }
+    bad |= !isfinite(q[i]);
+  }
+  __shared__ double sm[2][3][BB_THREADS / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = 0; d < 3; ++d) {
+    const double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    if (lane == 0) {
+      sm[0][d][w] = a;
+      sm[1][d][w] = b;
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 3; ++d) {
+      double a = sm[0][d][0], b = sm[1][d][0];
+      for (int j = 1; j < BB_THREADS / 32; ++j) {
+        a = fmin(a, sm[0][d][j]);
+        b = fmax(b, sm[1][d][j]);
+      }
+      part[6 * blockIdx.x + d] = a;
+      part[6 * blockIdx.x + 3 + d] = b;
+    }
+    if (bad) atomicOr(&counters[CNT_BAD], 1);
+  }
+}
+
+// Root cube of each problem (one block per problem; the rule of k_bbox_final)
+// and its output scale lambda_k = 2^-S_k / W_k.
+__global__ void __launch_bounds__(256)
+k_fbox_final(const int32_t* __restrict__ bstart, const double* __restrict__ part,
+             const BatchProb* __restrict__ prob, double* __restrict__ fbox, double* __restrict__ fscale) {
+  const int k = blockIdx.x;
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int b = bstart[k] + threadIdx.x; b < bstart[k + 1]; b += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      mn[d] = fmin(mn[d], part[6 * b + d]);
+      mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
+    }
+  __shared__ double sm[2][3][8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = 0; d < 3; ++d) {
+    const double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    if (lane == 0) {
+      sm[0][d][w] = a;
+      sm[1][d][w] = b;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const bool empty = bstart[k + 1] == bstart[k];
+  double w3 = 0.0, lo[3];
+  for (int d = 0; d < 3; ++d) {
+    double a = sm[0][d][0], b = sm[1][d][0];
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+      a = fmin(a, sm[0][d][j]);
+      b = fmax(b, sm[1][d][j]);
+    }
+    lo[d] = empty ? 0.0 : a;
+    w3 = empty ? 0.0 : fmax(w3, __dsub_rn(b, a));
+  }
+  const double W = (w3 > 0.0) ? w3 : 1.0;
+  for (int d = 0; d < 3; ++d) fbox[4 * k + d] = lo[d];
+  fbox[4 * k + 3] = W;
+  fscale[k] = __ddiv_rn(ldexp(1.0, -prob[k].S), W);
+}
+
+// Forest leaf key of every particle: the slot's first key + the key the
+// single-problem rule (k_morton) gives in the problem's own cube.
+__global__ void k_fmorton(int64_t n, int nprob, const int64_t* __restrict__ pstart,
+                          const BatchProb* __restrict__ prob, const double* __restrict__ fbox,
+                          const double* __restrict__ xyz, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = last_le(pstart, nprob, i);
+  const double* box = fbox + 4 * k;
+  const int L = prob[k].L;
+  const double W = box[3];
+  const double scale = (double)(1u << L);
+  const int top = (1 << L) - 1;
+  uint32_t c[3];
+  for (int d = 0; d < 3; ++d) {
+    const double t = __ddiv_rn(__dsub_rn(xyz[3 * i + d], box[d]), W);
+    const double u = floor(__dmul_rn(t, scale));
+    const int v = (u >= 0.0) ? (u <= (double)top ? (int)u : top) : 0;
+    c[d] = (uint32_t)v;
+  }
+  key[i] = prob[k].slot_key + morton3(c[0], c[1], c[2]);
+  idx[i] = (uint32_t)i;
+}
+
+// Morton-ordered copies of a batch: FP64 positions mapped into the forest
+// cube (x' = o_k + t 2^-S_k, t = (x - lo_k) / W_k), FP32 leaf-local
+// coordinates from the problem's own cube exactly as k_gather computes them.
+__global__ void k_fgather(int64_t n, int nprob, const int64_t* __restrict__ pstart,
+                          const BatchProb* __restrict__ prob, const double* __restrict__ fbox,
+                          const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
+                          const double* __restrict__ xyz, const double* __restrict__ q, int32_t* __restrict__ perm,
+                          double4* __restrict__ pos64, float4* __restrict__ pos32, float4* __restrict__ pos32lo) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t i = sidx[r];
+  perm[r] = (int32_t)i;
+  const int k = last_le(pstart, nprob, (int64_t)i);
+  const BatchProb pb = prob[k];
+  const double* box = fbox + 4 * k;
+  const double x = xyz[3 * (int64_t)i], y = xyz[3 * (int64_t)i + 1], z = xyz[3 * (int64_t)i + 2];
+  const double qq = q[i];
+  int ox, oy, oz;
+  demorton3(pb.slot_key >> (3 * pb.L), ox, oy, oz);
+  const double W = box[3], ws = ldexp(1.0, -pb.S);
+  const double tx = __ddiv_rn(__dsub_rn(x, box[0]), W), ty = __ddiv_rn(__dsub_rn(y, box[1]), W),
+               tz = __ddiv_rn(__dsub_rn(z, box[2]), W);
+  pos64[r] = make_double4(__dadd_rn((double)ox * ws, __dmul_rn(tx, ws)), __dadd_rn((double)oy * ws, __dmul_rn(ty, ws)),
+                          __dadd_rn((double)oz * ws, __dmul_rn(tz, ws)), qq);
+  int ix, iy, iz;
+  demorton3(skey[r] - pb.slot_key, ix, iy, iz);
+  const double w = ldexp(W, -pb.L);
+  const double cx = box[0] + ((double)ix + 0.5) * w;
+  const double cy = box[1] + ((double)iy + 0.5) * w;
+  const double cz = box[2] + ((double)iz + 0.5) * w;
+  const double vx = (x - cx) / w, vy = (y - cy) / w, vz = (z - cz) / w;
+  const double Q = 8388608.0, iQ = 1.0 / 8388608.0;
+  const double hx = rint(vx * Q) * iQ, hy = rint(vy * Q) * iQ, hz = rint(vz * Q) * iQ;
+  pos32[r] = make_float4((float)hx, (float)hy, (float)hz, (float)qq);
+  pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
+}
+
+// Problem of every cell of level l: the slot containing the cell's first
+// leaf key, if the cell lies inside it (l >= S_k); -1 for cells above the slots.
+__global__ void k_cell_slot(const int32_t* __restrict__ n_ptr, const uint32_t* __restrict__ key, int l, int Lf,
+                            int nslot, const uint32_t* __restrict__ sstart, const int32_t* __restrict__ sprob,
+                            const BatchProb* __restrict__ prob, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n_ptr) return;
+  const uint64_t kk = (uint64_t)key[i] << (3 * (Lf - l));
+  const int j = last_le(sstart, nslot, kk);
+  const int k = sprob[j];
+  const BatchProb pb = prob[k];
+  const bool inside = (uint64_t)sstart[j] <= kk && l >= pb.S && kk < (uint64_t)pb.slot_key + (1ull << (3 * pb.L));
+  out[i] = inside ? k : -1;
+}
+
 // ---- unique prefixes of a sorted key list --------------------------------------
 
 __device__ inline int64_t load_n(const int32_t* p, int64_t s) { return p ? (int64_t)*p : s; }
@@ -416,10 +593,11 @@ k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restr
   const int l = tl.level, row = threadIdx.x;
   const bool valid = row < tl.count;
   const int zero_row = lv.ncell[l];
-  int ix = 0, iy = 0, iz = 0;
+  int ix = 0, iy = 0, iz = 0, mine = 0;
   if (valid) {
     int cell = lv.cls[l][tl.first + row];
     demorton3(lv.key[l][cell], ix, iy, iz);
+    mine = problem_of(lv, l, cell);
   }
   const int top = (1 << l) - 1;
   __shared__ int16_t act[FMM_NT_CLASS];
@@ -432,7 +610,7 @@ k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restr
     int src = zero_row;
     if (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
       int g = lv.grid[l][morton3(sx, sy, sz)];
-      if (g >= 0) src = g;
+      if (g >= 0 && same_problem(lv, l, mine, g)) src = g;
     }
     tile_src[((int64_t)blockIdx.x * FMM_NT_CLASS + k) * FMM_TILE + row] = src;
     if (__syncthreads_or(src != zero_row) && row == 0) act[nact++] = (int16_t)k;
@@ -451,8 +629,12 @@ k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __r
   const Tile tl = tiles[blockIdx.x];
   const int l = tl.level, row = threadIdx.x;
   const bool valid = row < tl.count;
-  int ix = 0, iy = 0, iz = 0;
-  if (valid) demorton3(lv.key[l][lv.cls[l][tl.first + row]], ix, iy, iz);
+  int ix = 0, iy = 0, iz = 0, mine = 0;
+  if (valid) {
+    const int cell = lv.cls[l][tl.first + row];
+    demorton3(lv.key[l][cell], ix, iy, iz);
+    mine = problem_of(lv, l, cell);
+  }
   const int top = (1 << l) - 1;
   __shared__ int16_t act[FMM_NT_CLASS];
   __shared__ int nact;
@@ -462,8 +644,10 @@ k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __r
     const int slot = src_t[tl.cls * FMM_NT_CLASS + k];
     const int tx = ix - tvec[3 * slot], ty = iy - tvec[3 * slot + 1], tz = iz - tvec[3 * slot + 2];
     bool has = false;
-    if (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top)
-      has = lv.grid[l][morton3(tx, ty, tz)] >= 0;
+    if (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top) {
+      const int g = lv.grid[l][morton3(tx, ty, tz)];
+      has = g >= 0 && same_problem(lv, l, mine, g);
+    }
     if (__syncthreads_or(has) && row == 0) act[nact++] = (int16_t)k;
   }
   __syncthreads();
@@ -529,8 +713,10 @@ fmm_status ensure_level(Ctx* c, int l, int64_t cells) {
   dfree(c, c->lv.count[l], 4 * (size_t)old);
   dfree(c, c->lv.parent[l], 4 * (size_t)old);
   dfree(c, c->lv.cls[l], 4 * (size_t)old);
+  dfree(c, c->slot_buf[l], 4 * (size_t)old);
   c->lv.key[l] = nullptr;
   c->lv.first[l] = c->lv.count[l] = c->lv.parent[l] = c->lv.cls[l] = nullptr;
+  c->slot_buf[l] = c->lv.slot[l] = nullptr;
   FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
   c->lv.key[l] = (uint32_t*)p;
   FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
@@ -541,7 +727,22 @@ fmm_status ensure_level(Ctx* c, int l, int64_t cells) {
   c->lv.parent[l] = (int32_t*)p;
   FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
   c->lv.cls[l] = (int32_t*)p;
+  FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+  c->slot_buf[l] = (int32_t*)p;
   c->lcap[l] = cap;
+  return FMM_OK;
+}
+
+// dense key -> cell grids of levels 0 .. Lf (all -1 when allocated)
+fmm_status ensure_grids(Ctx* c, int Lf) {
+  for (int l = 0; l <= Lf; ++l) {
+    if (c->lv.grid[l]) continue;
+    void* p;
+    const size_t bytes = sizeof(int32_t) * ((size_t)1 << (3 * l));
+    FMM_TRY(dalloc(c, &p, bytes));
+    c->lv.grid[l] = (int32_t*)p;
+    FMM_CUDA(c, cudaMemsetAsync(p, 0xFF, bytes, c->stream));
+  }
   return FMM_OK;
 }
 
@@ -692,6 +893,104 @@ extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int
 
 namespace fmm {
 
+// Slots of a batch: problems with particles, largest slot first (ties in input
+// order), take consecutive ranges of forest leaf keys; a slot of 8^L keys then
+// starts at a multiple of 8^L, i.e. it is one cell of level Lf - L.  The forest
+// leaf level Lf is the smallest that holds every slot.
+fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total) {
+  std::vector<int64_t> start(nprob + 1, 0);
+  std::vector<BatchProb> prob(nprob);
+  std::vector<int> order;
+  int maxL = 0;
+  for (int k = 0; k < nprob; ++k) {
+    start[k + 1] = start[k] + counts[k];
+    prob[k] = BatchProb{0u, heights[k] - 1, 0, 0};
+    if (counts[k] > 0) {
+      order.push_back(k);
+      maxL = std::max(maxL, heights[k] - 1);
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return prob[a].L > prob[b].L; });
+  uint64_t off = 0;
+  for (int k : order) {
+    prob[k].slot_key = (uint32_t)off;
+    off += (uint64_t)1 << (3 * prob[k].L);
+    if (off > ((uint64_t)1 << (3 * FMM_MAX_FOREST_LEAF)))
+      return set_err(c, FMM_ERR_ARG,
+                     "fmm_set_batch: the problems' leaf cells (sum of 8^(height-1)) exceed 8^%d; split the batch",
+                     FMM_MAX_FOREST_LEAF);
+  }
+  int Lf = maxL;
+  while (((uint64_t)1 << (3 * Lf)) < off) ++Lf;
+  std::vector<uint32_t> sstart;
+  std::vector<int32_t> sprob;
+  std::vector<int64_t> first(nprob, 0);
+  int64_t rank = 0;
+  for (int k : order) {
+    prob[k].S = Lf - prob[k].L;
+    sstart.push_back(prob[k].slot_key);
+    sprob.push_back(k);
+    first[k] = rank;
+    rank += counts[k];
+  }
+  for (int k = 0; k < nprob; ++k)
+    if (counts[k] == 0) first[k] = rank;
+  std::vector<int32_t> bstart(nprob + 1, 0);
+  for (int k = 0; k < nprob; ++k)
+    bstart[k + 1] = bstart[k] + (int32_t)((counts[k] + FB_CHUNK - 1) / FB_CHUNK);
+  if (nprob + 1 > c->fb_cap) {
+    dfree(c, c->fb_pstart, 8 * (size_t)c->fb_cap);
+    dfree(c, c->fb_prob, sizeof(BatchProb) * (size_t)c->fb_cap);
+    dfree(c, c->fb_box, 32 * (size_t)c->fb_cap);
+    dfree(c, c->fb_scale, 8 * (size_t)c->fb_cap);
+    dfree(c, c->fb_sstart, 4 * (size_t)c->fb_cap);
+    dfree(c, c->fb_sprob, 4 * (size_t)c->fb_cap);
+    dfree(c, c->fb_bstart, 4 * (size_t)c->fb_cap);
+    c->fb_pstart = nullptr;
+    c->fb_prob = nullptr;
+    c->fb_box = c->fb_scale = nullptr;
+    c->fb_sstart = nullptr;
+    c->fb_sprob = c->fb_bstart = nullptr;
+    c->fb_cap = 0;
+    const int cap = nprob + 1 + 64;
+    void* p;
+    FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
+    c->fb_pstart = (int64_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(BatchProb) * (size_t)cap));
+    c->fb_prob = (BatchProb*)p;
+    FMM_TRY(dalloc(c, &p, 32 * (size_t)cap));
+    c->fb_box = (double*)p;
+    FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
+    c->fb_scale = (double*)p;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+    c->fb_sstart = (uint32_t*)p;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+    c->fb_sprob = (int32_t*)p;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+    c->fb_bstart = (int32_t*)p;
+    c->fb_cap = cap;
+  }
+  // the tables are small; synchronous copies keep the host vectors' lifetime simple
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  FMM_CUDA(c, cudaMemcpy(c->fb_pstart, start.data(), 8 * (size_t)(nprob + 1), cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->fb_prob, prob.data(), sizeof(BatchProb) * (size_t)nprob, cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpy(c->fb_bstart, bstart.data(), 4 * (size_t)(nprob + 1), cudaMemcpyHostToDevice));
+  if (!sstart.empty()) {
+    FMM_CUDA(c, cudaMemcpy(c->fb_sstart, sstart.data(), 4 * sstart.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpy(c->fb_sprob, sprob.data(), 4 * sprob.size(), cudaMemcpyHostToDevice));
+  }
+  c->forest = true;
+  c->nprob = nprob;
+  c->leaf = Lf;
+  c->fb_nslot = (int)sstart.size();
+  c->fb_nblocks = bstart[nprob];
+  c->fb_start_h = start;
+  c->fb_prob_h = prob;
+  c->fb_first_h = first;
+  *n_total = start[nprob];
+  return FMM_OK;
+}
+
 fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   cudaStream_t s = c->stream;
   const int Lf = c->leaf;
@@ -701,7 +1000,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
 
   // forget the previous tree in the dense grids
   if (c->have_prev) {
-    for (int l = 0; l <= Lf; ++l)
+    for (int l = 0; l <= c->prev_leaf; ++l)
       if (c->prev_ncell[l] > 0) {
         k_grid_set<<<ceil_div(c->prev_ncell[l], 256), 256, 0, s>>>(nullptr, c->prev_ncell[l], c->lv.key[l],
                                                                    c->lv.grid[l], 1);
@@ -709,6 +1008,9 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       }
     c->have_prev = false;
   }
+  c->prev_leaf = Lf;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) c->prev_ncell[l] = 0;
+  FMM_TRY(ensure_grids(c, Lf));
   FMM_CUDA(c, cudaMemsetAsync(c->counters, 0, 128 * sizeof(int32_t), s));
 
   // per-level capacities from upper bounds
@@ -729,7 +1031,20 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     c->p2p_items_cap = cap;
   }
 
-  if (n > 0) {
+  if (n > 0 && c->forest) {
+    // bounding cube of every problem, then forest keys
+    const int nbb = c->fb_nblocks;
+    double* part = (double*)c->scratch;
+    k_fbox_partial<<<nbb, BB_THREADS, 0, s>>>(c->nprob, c->fb_bstart, c->fb_pstart, xyz, q, part, c->counters);
+    k_fbox_final<<<c->nprob, 256, 0, s>>>(c->fb_bstart, part, c->fb_prob, c->fb_box, c->fb_scale);
+    k_fmorton<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_box, xyz, c->key_a,
+                                               c->idx_a);
+    // the forest cube itself is the unit cube at the origin
+    c->box_h[0] = c->box_h[1] = c->box_h[2] = 0.0;
+    c->box_h[3] = 1.0;
+    FMM_CUDA(c, cudaMemcpyAsync(c->box, c->box_h, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+    c->launches_set += 3;
+  } else if (n > 0) {
     // bounding cube
     int nbb = ceil_div(n, BB_THREADS * 8);
     if (nbb > 1184) nbb = 1184;
@@ -739,6 +1054,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     // keys
     k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, c->box, Lf, c->key_a, c->idx_a);
     c->launches_set += 3;
+  }
+  if (n > 0) {
     // sort
     uint32_t *ka = c->key_a, *kb = c->key_b, *va = c->idx_a, *vb = c->idx_b;
     int bits = 3 * Lf;
@@ -757,8 +1074,12 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       vb = t;
     }
     c->skey = ka;
-    k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, Lf, c->perm, c->pos64, c->pos32,
-                                              c->pos32lo);
+    if (c->forest)
+      k_fgather<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_box, ka, va, xyz, q,
+                                                 c->perm, c->pos64, c->pos32, c->pos32lo);
+    else
+      k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, Lf, c->perm, c->pos64, c->pos32,
+                                                c->pos32lo);
     c->launches_set++;
     // levels
     FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, nullptr));
@@ -768,6 +1089,12 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       k_grid_set<<<ceil_div(ub[l], 256), 256, 0, s>>>(c->counters + l, ub[l], c->lv.key[l], c->lv.grid[l], 0);
       c->launches_set++;
     }
+    if (c->forest)
+      for (int l = 0; l <= Lf; ++l) {
+        k_cell_slot<<<ceil_div(ub[l], 256), 256, 0, s>>>(c->counters + l, c->lv.key[l], l, Lf, c->fb_nslot,
+                                                         c->fb_sstart, c->fb_sprob, c->fb_prob, c->slot_buf[l]);
+        c->launches_set++;
+      }
     // P2P items: exclusive offsets per leaf, total in counters[CNT_ITEMS]
     k_p2p_items<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items);
     k_scan1<int32_t><<<1, 1024, 0, s>>>(c->p2p_items, ub[Lf], c->counters + CNT_ITEMS);
@@ -786,7 +1113,13 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
 
   FMM_CUDA(c, cudaMemcpyAsync(c->counters_h, c->counters, 128 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA(c, cudaMemcpyAsync(c->box_h, c->box, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (c->forest && n > 0) {
+    c->fb_box_h.assign(4 * (size_t)c->nprob, 0.0);
+    FMM_CUDA(c, cudaMemcpyAsync(c->fb_box_h.data(), c->fb_box, 4 * sizeof(double) * c->nprob,
+                                cudaMemcpyDeviceToHost, s));
+  }
   FMM_CUDA(c, cudaStreamSynchronize(s));
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) c->lv.slot[l] = (c->forest && l <= Lf) ? c->slot_buf[l] : nullptr;
   if (c->counters_h[CNT_BAD]) {
     for (int l = 0; l <= Lf; ++l) c->prev_ncell[l] = n > 0 ? c->counters_h[l] : 0;
     c->have_prev = n > 0;

@@ -39,6 +39,8 @@ _SIGS = {
     "fmm_set_m2l": [_vp, C.c_int, C.c_double],
     "fmm_get_svd_ranks": [_vp, _vp],
     "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
+    "fmm_set_batch": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
+    "fmm_get_batch_info": [_vp, C.c_int32, _vp, _vp],
     "fmm_evaluate": [_vp, _vp, _vp],
     "fmm_get_order": [_vp, _vp],
     "fmm_get_box": [_vp, _vp],
@@ -122,6 +124,21 @@ def fmm_get_svd_ranks(h) -> np.ndarray:
 
 def fmm_set_particles(h, n: int, xyz, q) -> int:
     return _check(h, lib.fmm_set_particles(h, n, _ptr(xyz), _ptr(q)))
+
+
+def fmm_set_batch(h, counts, heights, xyz, q) -> int:
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    heights = np.ascontiguousarray(heights, dtype=np.int32)
+    if counts.shape != heights.shape or counts.ndim != 1:
+        raise ValueError("counts and heights must be 1-D arrays of the same length")
+    return _check(h, lib.fmm_set_batch(h, len(counts), _ptr(counts), _ptr(heights), _ptr(xyz), _ptr(q)))
+
+
+def fmm_get_batch_info(h, k: int):
+    info = np.zeros(8, dtype=np.int64)
+    box = np.zeros(4, dtype=np.float64)
+    _check(h, lib.fmm_get_batch_info(h, k, _ptr(info), _ptr(box)))
+    return info, box
 
 
 def fmm_evaluate(h, phi, F) -> int:
@@ -241,6 +258,14 @@ class FMM:
         n = int(xyz.shape[0])
         fmm_set_particles(self.h, n, xyz, q)
         self.n = n
+
+    def set_batch(self, counts, heights, xyz, q):
+        """Independent problems, particles concatenated in problem order."""
+        fmm_set_batch(self.h, counts, heights, xyz, q)
+        self.n = int(np.sum(counts))
+
+    def batch_info(self, k: int):
+        return fmm_get_batch_info(self.h, k)
 
     def evaluate(self, phi, F):
         fmm_evaluate(self.h, phi, F)

@@ -112,3 +112,36 @@ def workload(name: str):
     w = WORKLOADS[name]
     xyz, q = particles(w["n"], w["seed"], w["dist"], w["qkind"])
     return xyz, q, w["height"], w["order"]
+
+
+def batch_height(n: int, hmin: int = 3, hmax: int = 6) -> int:
+    """Tree height of a batched problem: the smallest leaf level L with
+    32 * 8^L >= n (about 32 particles per leaf in the cube), plus one,
+    clamped to [hmin, hmax]."""
+    L = 0
+    while 32 * 8 ** L < n:
+        L += 1
+    return min(max(1 + L, hmin), hmax)
+
+
+def batch_workload(nprob: int = 256, seed: int = 999, nmin: float = 1e3, nmax: float = 2e5,
+                   hmin: int = 3, hmax: int = 6):
+    """Independent problems of uneven size for the batched path.
+
+    Sizes are log-uniform in [nmin, nmax] (draw k of stream `seed` gives
+    problem k); problem k uses seed 1000 + k, points uniform in the unit cube
+    if that seed is even and on the ellipsoid surface if it is odd, charges in
+    (0, 1].  Returns (counts, heights, xyz, q) with the problems' particles
+    concatenated in problem order.
+    """
+    u = uniform01(seed, nprob)
+    lo, hi = np.log10(nmin), np.log10(nmax)
+    counts = np.floor(10.0 ** (lo + u * (hi - lo))).astype(np.int64)
+    heights = np.array([batch_height(int(n), hmin, hmax) for n in counts], dtype=np.int32)
+    xs, qs = [], []
+    for k, n in enumerate(counts):
+        s = 1000 + k
+        xyz, q = particles(int(n), s, "cube" if s % 2 == 0 else "ellipsoid", "pos")
+        xs.append(xyz)
+        qs.append(q)
+    return counts, heights, np.ascontiguousarray(np.concatenate(xs)), np.ascontiguousarray(np.concatenate(qs))
