@@ -61,7 +61,13 @@ def parse():
                     help="M2L operators: full-rank K_t, or the SVD-compressed canonical operators (eps = 10^-p)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default P2P kernel shape")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the request stream")
+    ap.add_argument("--lanes", type=int, default=3, help="serving: concurrent batches")
+    ap.add_argument("--ring-gb", type=int, default=8, help="serving: pinned result ring (GB)")
+    ap.add_argument("--max-batch-particles", type=int, default=8_000_000, help="serving: particles per batch")
     return ap.parse_args()
 
 
@@ -271,6 +277,13 @@ def run_ours(args):
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
+    tuned = None
+    if not args.no_autotune:
+        choice, ttimes = fmm.fmm_autotune(f.h)
+        tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
+                 "variant_ms": [round(float(t), 4) for t in ttimes]}
+        step()
+        torch.cuda.synchronize()
     work = fmm.fmm_get_work(f.h)
     stats = f.stats()
     # stage times with every stage run alone (P2P normally overlaps M2L), for
@@ -433,6 +446,7 @@ def run_ours(args):
                      "algorithmic": m2l_alg, "peak_source": peak_note},
         "roofline_m2l_projection": roofline_proj,
         "tensor_pipe": tensor_pipe,
+        "autotune": tuned,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)",
                          "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
                          "interactions": p2p_pairs,
@@ -496,6 +510,13 @@ def run_batched(args):
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
+    tuned = None
+    if not args.no_autotune:
+        choice, ttimes = fmm.fmm_autotune(f.h)
+        tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
+                 "variant_ms": [round(float(t), 4) for t in ttimes]}
+        step()
+        torch.cuda.synchronize()
     work = fmm.fmm_get_work(f.h)
     stats = f.stats()
     fmm.fmm_set_timing(f.h, 2)
@@ -595,6 +616,7 @@ def run_batched(args):
         "tensor_pipe": None if kt is None else {
             "expansion_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
             "projection_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
+        "autotune": tuned,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)", "interactions": p2p_pairs,
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
                          "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2)},
@@ -626,12 +648,205 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+SERVE_WORKLOAD = "serving_poisson200"
+
+
+class Ring:
+    """Pinned host arena handed out in arrival order and returned in the same
+    order (a FIFO ring); take() blocks while the ring is full."""
+
+    def __init__(self, nbytes: int):
+        import threading
+
+        import torch
+        self.buf = torch.empty(nbytes // 8, dtype=torch.float64).pin_memory().numpy()
+        self.cap = len(self.buf)
+        self.head = 0          # next free slot (float64 units)
+        self.used = 0
+        self.spans = []        # (start, length incl. the padding skipped at the end), FIFO
+        self.cv = threading.Condition()
+
+    def take(self, nbytes: int):
+        n = nbytes // 8
+        if n > self.cap:
+            raise ValueError("request larger than the result ring")
+        with self.cv:
+            while True:
+                pad = self.cap - self.head if self.head + n > self.cap else 0
+                if self.used + pad + n <= self.cap:
+                    break
+                self.cv.wait()
+            start = 0 if pad else self.head
+            self.spans.append(pad + n)
+            self.used += pad + n
+            self.head = (start + n) % self.cap
+            return self.buf[start:start + n]
+
+    def give(self, nbytes: int):
+        with self.cv:
+            self.used -= self.spans.pop(0)
+            self.cv.notify_all()
+
+
+def run_serving(args):
+    """Poisson stream of solve requests (mean 200 per second; sizes
+    log-uniform in [1e4, 5e6] particles, uniform cube, order 5 or 7 by coin
+    flip, height from the size as in the batched workload, capped at 8)
+    through the solve server: 3 lanes, 150 GB admission budget.  Requests
+    carry host buffers (inputs pinned, outputs pageable); latency is submit
+    to results in host memory."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1206_0115_b300 import build, inputs
+    build.build()
+    from paper_1206_0115_b300 import fmm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rate, seconds = args.rate, args.serve_seconds
+    nreq = max(1, int(rate * seconds))
+    seed = 2_000_000 + 1000 * rank
+    u = inputs.uniform01(seed, 3 * nreq)
+    gaps = -np.log1p(-u[:nreq]) / rate
+    arrivals = np.cumsum(gaps)
+    sizes = np.floor(10.0 ** (4.0 + u[nreq:2 * nreq] * (np.log10(5e6) - 4.0))).astype(np.int64)
+    orders = np.where(u[2 * nreq:] < 0.5, 5, 7)
+    heights = np.array([inputs.batch_height(int(n), 3, 8) for n in sizes])
+    # request payloads: prefixes of four base sets of 5e6 points uniform in the
+    # unit cube (a prefix of a uniform sample is a uniform sample), charges in (0, 1]
+    bases = []
+    for b in range(4):
+        xyz, q = inputs.particles(5_000_000, seed + 1 + b, "cube", "pos")
+        bases.append((torch.from_numpy(xyz).pin_memory(), torch.from_numpy(q).pin_memory()))
+
+    lanes = args.lanes
+    budget = 150 << 30
+    prec = fmm.FMM_MIXED if args.precision == "mixed" else fmm.FMM_FP64
+    s = fmm.fmm_server_create(lanes, prec, budget, args.max_batch_particles, 64)
+    try:
+        for p in (5, 7):
+            fmm.fmm_server_warmup(s, p)
+
+        # result buffers: a pinned ring (requests finish about in arrival order
+        # and are collected in that order); a request waits for room
+        ring = Ring(args.ring_gb << 30)
+
+        def make(k):
+            n = int(sizes[k])
+            xyz, q = bases[k % 4]
+            out = ring.take(32 * n)
+            return dict(n=n, h=int(heights[k]), p=int(orders[k]), xyz=xyz[:n], q=q[:n],
+                        phi=out[:n], F=out[n:].reshape(n, 3), ring=32 * n)
+
+        # untimed warm-up traffic: grows the lanes' resident buffers
+        warm = [make(k) for k in range(min(nreq, 3 * lanes))]
+        for r in warm:
+            r["t"] = fmm.fmm_server_submit(s, r["n"], r["h"], r["p"], r["xyz"], r["q"], r["phi"], r["F"])
+        for r in warm:
+            fmm.fmm_server_wait(s, r["t"])
+            ring.give(r["ring"])
+        st0 = fmm.fmm_server_stats(s)
+
+        reqs = [None] * nreq
+        tickets = [None] * nreq
+        submit_err = []
+        clocks = Clocks(local)
+        clocks.start()
+        t0 = time.perf_counter()
+
+        def producer():
+            try:
+                for k in range(nreq):
+                    dt = t0 + arrivals[k] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    r = reqs[k] = make(k)
+                    tickets[k] = fmm.fmm_server_submit(s, r["n"], r["h"], r["p"], r["xyz"], r["q"], r["phi"], r["F"])
+            except Exception as e:  # surfaced below
+                submit_err.append(e)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        times = []
+        for k in range(nreq):
+            while tickets[k] is None and not submit_err:
+                time.sleep(0.0005)
+            if submit_err:
+                break
+            times.append(fmm.fmm_server_wait(s, tickets[k]))
+            if k < nreq - 8:
+                ring.give(reqs[k]["ring"])  # the last few stay readable for the check below
+        th.join()
+        t_end = time.perf_counter()
+        clk = clocks.stop()
+        if submit_err:
+            raise submit_err[0]
+        st = fmm.fmm_server_stats(s) - st0
+        st[3:8] = fmm.fmm_server_stats(s)[3:8]
+    finally:
+        fmm.fmm_server_destroy(s)
+    times = np.array(times)
+    done_at = arrivals + times[:, 2] / 1e3          # completion, seconds after t0
+    span = float(done_at.max())
+    parts = int(sizes.sum())
+    lat = times[:, 2]
+    # correctness spot check: the last request of each order against a lone solve
+    check = {}
+    for p in (5, 7):
+        ks = np.nonzero(orders[nreq - 8:] == p)[0] + nreq - 8
+        if len(ks) == 0:
+            continue
+        k = int(ks[-1])
+        r = reqs[k]
+        with fmm.FMM(r["h"], r["p"], prec) as f:
+            f.set_particles(r["xyz"].numpy(), r["q"].numpy())
+            phi = np.empty(r["n"])
+            Fo = np.empty((r["n"], 3))
+            f.evaluate(phi, Fo)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        check[str(p)] = {"request": k, "n": r["n"], "rel_l2_phi_vs_alone": rel(r["phi"], phi),
+                         "rel_l2_F_vs_alone": rel(r["F"], Fo)}
+    result = {
+        "metric": METRIC, "value": parts / span, "unit": UNIT, "n_gpus": 1, "steps": nreq,
+        "warmup": len(warm), "ms_per_step": 1e3 * span / nreq, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "rate_rps": rate, "duration_s": seconds, "requests": nreq,
+                   "n_range": [10_000, 5_000_000], "orders": [5, 7], "heights": "3..8 by size",
+                   "distribution": "cube", "lanes": lanes, "hbm_budget_bytes": budget,
+                   "max_batch_particles": args.max_batch_particles, "max_batch_requests": 64,
+                   "payload": "prefixes of 4 seeded 5e6-point cube sets (pinned host); outputs in a pinned host ring",
+                   "precision": args.precision, "m2l": "svd"},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                       "queue_p50": float(np.percentile(times[:, 0], 50)),
+                       "queue_p99": float(np.percentile(times[:, 0], 99)),
+                       "service_p50": float(np.percentile(times[:, 1], 50))},
+        "offered": {"requests_per_s": nreq / float(arrivals[-1]), "particles_per_s": parts / float(arrivals[-1])},
+        "sustained": {"requests_per_s": nreq / span, "particles_per_s": parts / span, "span_s": span,
+                      "wall_s": t_end - t0},
+        "server": {"batches": int(st[1]), "mean_batch_requests": float(nreq / max(1, st[1])),
+                   "largest_batch": int(st[5]), "peak_batches_at_once": int(st[4]),
+                   "peak_inflight_estimate_bytes": int(st[3]), "device_bytes_held": int(st[7])},
+        "check_vs_alone": check,
+        "e2e": {"value": parts / span, "unit": UNIT, "h2d_bytes_per_step": int(32 * parts / nreq),
+                "d2h_bytes_per_step": int(32 * parts / nreq)},
+        "clocks": clk,
+    }
+    print(json.dumps(result))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == BATCH_WORKLOAD:
         run_batched(args)
+    elif args.workload == SERVE_WORKLOAD:
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -39,6 +39,8 @@ extern "C" {
 
 typedef struct fmm_ctx* fmm_handle;
 
+#define FMM_P2P_VARIANTS 6  /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+
 typedef enum {
   FMM_OK = 0,
   FMM_ERR_ARG = -1,     /* invalid argument (range, null pointer, non-finite input) */
@@ -170,6 +172,31 @@ fmm_status fmm_get_batch_info(fmm_handle h, int32_t k, int64_t* info, double* bo
  * call on the handle). */
 fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
 
+/* Picks the shape of the mixed-precision P2P kernel (the near field of
+ * Sec. 2.1, the largest kernel on surface distributions and batches) for the
+ * current tree by timing each variant -- (warps per block, sources staged per
+ * chunk) = (4,256), (2,128), (2,256), (4,128), (8,128), (8,256), index 0..5 --
+ * three times on the handle's stream with CUDA events, and keeps the fastest
+ * for later evaluations (the evaluation graph is rebuilt).  The variants give
+ * the same sums up to the grouping of FP32 partial sums.  choice (may be
+ * NULL): [0] index, [1] warps per block, [2] sources per chunk; times_ms
+ * (may be NULL): FMM_P2P_VARIANTS mean launch times.  Synchronises the
+ * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
+fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
+
+/* Sets the P2P variant directly (0 .. FMM_P2P_VARIANTS-1; 0 is the default),
+ * e.g. to reuse a choice fmm_autotune made on another handle. */
+fmm_status fmm_set_p2p_variant(fmm_handle h, int variant);
+
+/* Releases every device buffer that belongs to the current tree (particles,
+ * cells, expansions, M2L work tables and projections, staging) and keeps the
+ * translation operators and the compressed factors, so that a later
+ * fmm_set_particles / fmm_set_batch rebuilds without recomputing them.  Until
+ * then evaluate and the tree getters report FMM_ERR_STATE.  Synchronises the
+ * handle's streams.  (A long-lived process -- the solve server below -- uses
+ * it to keep idle handles small.) */
+fmm_status fmm_trim(fmm_handle h);
+
 /* Morton permutation of the last fmm_set_particles: perm[r] = input index of
  * the particle with Morton rank r.  perm: [n] int64, device or host. */
 fmm_status fmm_get_order(fmm_handle h, int64_t* perm);
@@ -275,6 +302,84 @@ fmm_status fmm_get_m2l_kernel_times(fmm_handle h, float* out);
  * FMM_ERR_ARG (range, NULL, non-finite coordinate), FMM_ERR_CUDA. */
 fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int height, uint64_t* keys, int64_t* perm,
                                     void* stream);
+
+/* ---- Solve server: continuous batching of independent requests ------------
+ *
+ * A server owns `lanes` worker threads on the current device, each with its
+ * own CUDA stream and one resident FMM handle per interpolation order (trees,
+ * expansions and operators stay on the device between batches).  A free lane
+ * takes the oldest queued request and every later queued request of the same
+ * order that still fits -- at most max_batch_particles particles and
+ * max_batch_requests requests per batch, the batch tree's leaf cells within
+ * fmm_set_batch's limit, and the device-memory estimate of all batches in
+ * flight within hbm_budget_bytes -- and solves them as one fmm_set_batch +
+ * fmm_evaluate.  Requests that arrive while lanes are busy wait in the queue
+ * and are admitted as lanes and memory free up; batches on different lanes
+ * overlap on the device.  Each request is solved exactly as it would be alone
+ * (fmm_set_batch's guarantee); only the rounding of the tensor-core partial
+ * sums may differ.  The paper has no counterpart (its runtime schedules the
+ * tasks of one FMM). */
+typedef struct fmm_server* fmm_server_handle;
+
+typedef struct {
+  int32_t lanes;               /* concurrent batches (1..16) */
+  int32_t precision;           /* FMM_MIXED or FMM_FP64 */
+  int64_t hbm_budget_bytes;    /* device-memory estimate of all batches in flight at most */
+  int64_t max_batch_particles; /* particles per batch at most (a larger single request runs alone) */
+  int32_t max_batch_requests;  /* requests per batch at most (1..4096) */
+  int32_t reserved;
+} fmm_server_config;
+
+/* Device memory a request is charged for admission: 256 bytes per particle
+ * plus, per cell (1.15 x min(n, 8^(height-1)) cells), its expansions
+ * (28 bytes x order^3 rounded up to 32) and its share of the compressed M2L's
+ * projections (4 bytes x 189 x 16 at order <= 5, x 32 above) and tables
+ * (1 KB).  A request above hbm_budget_bytes is refused. */
+int64_t fmm_server_request_bytes(int64_t n, int height, int order);
+
+/* Creates a server (threads start at once, idle).  Errors: FMM_ERR_ARG (a
+ * config field out of range), FMM_ERR_CUDA (no device, stream creation). */
+fmm_status fmm_server_create(const fmm_server_config* cfg, fmm_server_handle* out);
+
+/* Creates every lane's handle for `order` and its compressed M2L operators
+ * (the FP64 SVDs, seconds at order 7) before traffic; blocks until done. */
+fmm_status fmm_server_warmup(fmm_server_handle s, int order);
+
+/* Queues one request: n particles (xyz [n][3], q [n], FP64) for a tree of
+ * `height` levels (1..10) and interpolation order `order` (2..10); results
+ * phi [n] and F [n][3] (FP64, input order) are written by the lane.  All four
+ * pointers may be host (pageable or pinned) or device memory and must stay
+ * valid until fmm_server_wait returns for the ticket.  Returns at once;
+ * *ticket identifies the request.  Errors: FMM_ERR_ARG (range, NULL),
+ * FMM_ERR_OOM (the request alone exceeds the budget), FMM_ERR_STATE (server
+ * stopping). */
+fmm_status fmm_server_submit(fmm_server_handle s, int64_t n, int height, int order, const double* xyz,
+                             const double* q, double* phi, double* F, int64_t* ticket);
+
+/* Waits up to timeout_s seconds (< 0: forever) for a request.  On completion
+ * the ticket is released and the request's own status is returned (FMM_OK or
+ * the failing call's status, message in fmm_server_last_error); times (may be
+ * NULL) receives, in ms of the host's steady clock: [0] submit -> batch start
+ * (queueing), [1] batch start -> results in the caller's memory (service),
+ * [2] submit -> results (latency), [3] requests in the request's batch.
+ * Errors: FMM_ERR_ARG (unknown ticket), FMM_ERR_TIMEOUT (still pending; the
+ * ticket stays valid). */
+fmm_status fmm_server_wait(fmm_server_handle s, int64_t ticket, double timeout_s, double* times);
+
+/* Counters: out[0] requests completed, [1] batches run, [2] particles
+ * completed, [3] peak memory estimate in flight (bytes), [4] peak number of
+ * batches running at once, [5] largest batch (requests), [6] requests queued
+ * now, [7] device bytes held by the lanes (handles and staging buffers).
+ * out: 8 int64, host. */
+fmm_status fmm_server_stats(fmm_server_handle s, int64_t* out);
+
+/* Stops the lanes after their current batch, fails the requests still
+ * queued, joins the threads and releases the server and its device memory.
+ * No other call on the server may be in progress or follow.  NULL accepted. */
+fmm_status fmm_server_destroy(fmm_server_handle s);
+
+/* Message of the last failure of a server call or of a request it ran. */
+const char* fmm_server_last_error(fmm_server_handle s);
 
 /* Message of the last failed call on this handle ("" if none).  With
  * h == NULL: the message of the last failed fmm_create in this thread. */

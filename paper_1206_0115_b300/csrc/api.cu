@@ -12,6 +12,8 @@
 // pointers, which change from call to call).
 #include <cstdarg>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -34,24 +36,82 @@ fmm_status cuda_err(Ctx* c, cudaError_t e, const char* what) {
   return set_err(c, FMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Device memory of every handle comes from one stream-ordered pool per device
+// that keeps freed blocks cached (release threshold: never): buffers that
+// grow, shrink (fmm_trim) or move between handles are recycled without
+// cudaMalloc / cudaFree, whose device-wide synchronisation would serialise
+// handles that run on different streams.  The pool reuses a block freed on
+// another stream only once that free has completed (no implicit cross-stream
+// dependencies).
+cudaMemPool_t device_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = UINT64_MAX;
+  int no = 0;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  pools[dev] = pool;
+  return pool;
+}
+
+cudaError_t pool_alloc(int dev, cudaStream_t s, void** p, size_t bytes) {
+  cudaMemPool_t pool = device_pool(dev);
+  if (!pool) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+// Allocates on the handle's stream and waits for that stream, so that the
+// block is ready for any stream (a block reused from a free on the same
+// stream is only free in that stream's order).
 fmm_status dalloc(Ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = pool_alloc(c->dev, c->stream, p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return set_err(c, e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA,
-                   "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+                   "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   c->bytes += (int64_t)bytes;
   return FMM_OK;
 }
 
+// Returns a block to the pool in the handle's stream order (after the work
+// already enqueued there, which includes the joined P2P branch).
 void dfree(Ctx* c, void* p, size_t bytes) {
   if (!p) return;
-  cudaFree(p);
+  if (cudaFreeAsync(p, c->stream) != cudaSuccess) cudaGetLastError();
   c->bytes -= (int64_t)(bytes ? bytes : 16);
+}
+
+// A kernel's dynamic shared-memory limit belongs to the function in the
+// device's context, not to a handle: handles of different orders need
+// different sizes, so the limit is only ever raised (one record per device
+// and function, under a lock shared by every thread).
+fmm_status raise_smem_limit(Ctx* c, const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> set;
+  std::lock_guard<std::mutex> lk(mu);
+  int& cur = set[{c->dev, func}];
+  if (bytes <= cur) return FMM_OK;
+  FMM_CUDA(c, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
+  return FMM_OK;
 }
 
 namespace {
@@ -126,7 +186,7 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 std::vector<int64_t> graph_signature(const Ctx* c) {
   std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
-                            (int64_t)(uintptr_t)c->fb_scale};
+                            (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -301,14 +361,17 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
                   c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx,
                   c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_sstart, c->fb_sprob, c->fb_bstart};
+  // back to the pool on the handle's own side stream (both streams are idle)
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) cudaFreeAsync(b, c->side);
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
     void* lb[] = {c->lv.key[l], c->lv.first[l], c->lv.count[l], c->lv.parent[l], c->lv.grid[l], c->lv.cls[l],
                   c->slot_buf[l]};
     for (void* b : lb)
-      if (b) cudaFree(b);
+      if (b) cudaFreeAsync(b, c->side);
   }
+  if (c->side) cudaStreamSynchronize(c->side);
+  cudaGetLastError();
   if (c->counters_h) cudaFreeHost(c->counters_h);
   if (c->tc_err_h) cudaFreeHost(c->tc_err_h);
   if (c->box_h) cudaFreeHost(c->box_h);
@@ -324,6 +387,8 @@ fmm_status fmm_destroy(fmm_handle h) {
 
 fmm_status fmm_set_stream(fmm_handle h, void* stream) {
   if (!h) return FMM_ERR_ARG;
+  // buffers are freed in the handle's stream order: finish the old stream first
+  if (h->stream != (cudaStream_t)stream) FMM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->stream = (cudaStream_t)stream;
   return FMM_OK;
 }
@@ -457,6 +522,7 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   if (!phi || !F) return set_err(c, FMM_ERR_ARG, "fmm_evaluate: NULL output");
   FMM_CUDA(c, cudaSetDevice(c->dev));
   FMM_TRY(check_device_error(c));
+  FMM_TRY(ensure_expansions(c, c->precision));
   if (c->m2l_method == FMM_M2L_SVD) {
     if (c->leaf >= 2) FMM_TRY(m2l_svd_prepare(c));
     if (c->leaf >= 2 && m2l_kind(c) == 5) FMM_TRY(m2l_svd_tc_prepare(c));
@@ -488,6 +554,70 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
     FMM_CUDA(c, cudaMemcpyAsync(F, dF, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
     FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   }
+  return FMM_OK;
+}
+
+fmm_status fmm_set_p2p_variant(fmm_handle h, int variant) {
+  if (!h) return FMM_ERR_ARG;
+  if (variant < 0 || variant >= FMM_P2P_VARIANTS)
+    return set_err(h, FMM_ERR_ARG, "fmm_set_p2p_variant: %d outside 0..%d", variant, FMM_P2P_VARIANTS - 1);
+  if (variant != h->p2p_variant) {
+    h->p2p_variant = variant;
+    h->graph_ok = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_autotune: no particles loaded");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  const int keep_prec = c->precision, keep_var = c->p2p_variant;
+  c->precision = FMM_MIXED;  // the variants are shapes of the mixed kernel
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = -1.f;
+  int best_v = keep_var;
+  fmm_status st = FMM_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "fmm_autotune: events");
+  for (int v = 0; v < FMM_P2P_VARIANTS && st == FMM_OK; ++v) {
+    c->p2p_variant = v;
+    float ms = 0.f;
+    st = launch_p2p(c, c->stream);  // warm-up
+    if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
+    for (int k = 0; k < 3 && st == FMM_OK; ++k) st = launch_p2p(c, c->stream);
+    if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
+    ms /= 3.f;
+    if (times_ms) times_ms[v] = ms;
+    if (st == FMM_OK && (best < 0.f || ms < best)) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->precision = keep_prec;
+  c->p2p_variant = st == FMM_OK ? best_v : keep_var;
+  c->graph_ok = false;
+  if (st != FMM_OK) return st;
+  if (choice) {
+    choice[0] = best_v;
+    choice[1] = kP2PVariants[best_v][0];
+    choice[2] = kP2PVariants[best_v][1];
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_trim(fmm_handle h) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  drop_graph(c);
+  release_tree(c);
   return FMM_OK;
 }
 

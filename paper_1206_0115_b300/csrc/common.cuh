@@ -111,6 +111,7 @@ struct fmm_ctx {
   int32_t* p2p_items = nullptr;  // per leaf: first P2P work item (batches of 32 targets)
   int64_t p2p_items_cap = 0;
   int p2p_nitems = 0;
+  int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants)
   double4* near64 = nullptr;
   double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
   int64_t stage_in_cap = 0, stage_out_cap = 0;
@@ -151,7 +152,7 @@ struct fmm_ctx {
   int fb_nblocks = 0;                // bounding-box blocks of the batch
 
   // expansions
-  int64_t rows = 0, rows_cap = 0;
+  int64_t rows = 0, rows_cap32 = 0, rows_cap64 = 0;  // buffers of one precision exist once it is used
   float *Mhi = nullptr, *Mlo = nullptr, *L32 = nullptr;
   double *M64 = nullptr, *L64 = nullptr;
 
@@ -200,12 +201,10 @@ struct fmm_ctx {
   int64_t tm_rows = -1;
   alignas(64) unsigned char tm_vthi[128], tm_vtlo[128], tm_uhi[128], tm_ulo[128];  // compressed banks
   const void* tm_svd_ptr = nullptr;
-  int svd_tc_smem_set[2] = {0, 0}, svd_tc_nst = 0;
+  int svd_tc_nst = 0;
   float* svd_Mcls = nullptr;       // multipoles in class order, interleaved hi/lo slabs
   int svd_mcbase[FMM_MAX_LEVELS][8] = {{0}};  // first row of each (level, class) segment
   int64_t svd_mcls_rows = 0;
-  alignas(64) unsigned char tm_mchi[128], tm_mclo[128];
-  const void* tm_mcls_ptr = nullptr;
   void* svd_recs = nullptr;      // projection work units (records of k_svd_groups)
   int16_t* svd_eslot = nullptr;  // expansion tables (k_svd_exp_setup)
   int8_t* svd_ekch = nullptr;
@@ -213,7 +212,7 @@ struct fmm_ctx {
   int64_t svd_ecap = 0;
   int64_t svd_gcap = 0;
   const void* tm_khi_ptr = nullptr;
-  int tc_smem_set = 0, tc_nst = 0, num_sms = 0;
+  int tc_nst = 0, num_sms = 0;
 
   // SVD-compressed M2L (m2l_svd.cu)
   int m2l_method = FMM_M2L_SVD;
@@ -267,15 +266,23 @@ fmm_status cuda_err(Ctx* c, cudaError_t e, const char* what);
   } while (0)
 
 fmm_status dalloc(Ctx* c, void** p, size_t bytes);
+// a block of the library's device pool, ready for any stream when it returns
+cudaError_t pool_alloc(int dev, cudaStream_t s, void** p, size_t bytes);
+fmm_status raise_smem_limit(Ctx* c, const void* func, int bytes);
 void dfree(Ctx* c, void* p, size_t bytes);
 
 // ---- stages (host launchers) -------------------------------------------------
 fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q);
+// expansion buffers of one precision for the current tree's rows (new buffers start at zero)
+fmm_status ensure_expansions(Ctx* c, int precision);
+// releases every buffer that depends on the tree (the operators stay)
+void release_tree(Ctx* c);
 // slots of a batch (sets c->forest, c->leaf and the device tables); *n_total = sum of counts
 fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total);
 fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
+extern const int kP2PVariants[FMM_P2P_VARIANTS][2];
 fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
 fmm_status svd_prepare(Ctx* c);        // SVD of the canonical operators (ranks to the host)

@@ -614,6 +614,8 @@ fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
 fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out) {
   const int64_t nrows = c->lv.ncell[level];
   if (nrows == 0) return FMM_OK;
+  if (c->precision == FMM_MIXED ? !c->Mhi : !c->M64)
+    return set_err(c, FMM_ERR_STATE, "fmm_get_expansion: no evaluation in the current precision on this tree");
   const int64_t row0 = c->lv.row_off[level];
   const int64_t total = nrows * c->ncoef;
   const int grid = ceil_div(total, 256);

@@ -743,7 +743,7 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     void* p;
     FMM_TRY(dalloc(c, &p, 64));
     c->tc_err = (int32_t*)p;
-    FMM_CUDA(c, cudaMemset(c->tc_err, 0, 64));
+    FMM_CUDA(c, cudaMemsetAsync(c->tc_err, 0, 64, c->stream));
   }
   if (!c->tc_err_h) return set_err(c, FMM_ERR_STATE, "internal: no host error word");
   const int64_t gneed = (int64_t)c->ntiles * sp_ngroups(Rp);
@@ -790,7 +790,7 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     const int64_t cap = (mrows + mrows / 8 + FMM_TILE - 1) / FMM_TILE * FMM_TILE;  // chunks start on 8-row groups
     void* p;
     FMM_TRY(dalloc(c, &p, 8 * (size_t)cap * cp));
-    FMM_CUDA(c, cudaMemset(p, 0, 8 * (size_t)cap * cp));
+    FMM_CUDA(c, cudaMemsetAsync(p, 0, 8 * (size_t)cap * cp, c->stream));
     c->svd_Mcls = (float*)p;
     c->svd_mcls_rows = cap;
   }
@@ -801,15 +801,8 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   const int nst_p = sp_nst();
   if (nst < 2 || nst_p < 2) return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: no room for 2 stages");
   c->svd_tc_nst = nst;
-  if (sp_smem(nst_p) > c->svd_tc_smem_set[0]) {
-    FMM_CUDA(c, cudaFuncSetAttribute(k_svd_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sp_smem(nst_p)));
-    c->svd_tc_smem_set[0] = sp_smem(nst_p);
-  }
-  if (ex_smem(cp, nst) > c->svd_tc_smem_set[1]) {
-    FMM_CUDA(c, cudaFuncSetAttribute(k_svd_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     ex_smem(cp, nst)));
-    c->svd_tc_smem_set[1] = ex_smem(cp, nst);
-  }
+  FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc, sp_smem(nst_p)));
+  FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc, ex_smem(cp, nst)));
   if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
   return FMM_OK;
 }

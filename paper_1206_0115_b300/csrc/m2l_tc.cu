@@ -380,7 +380,7 @@ fmm_status m2l_tc_prepare(Ctx* c) {
     void* p;
     FMM_TRY(dalloc(c, &p, 64));
     c->tc_err = (int32_t*)p;
-    FMM_CUDA(c, cudaMemset(c->tc_err, 0, 64));
+    FMM_CUDA(c, cudaMemsetAsync(c->tc_err, 0, 64, c->stream));
   }
   if (c->tm_khi_ptr != c->Khi) {
     bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, cp, (uint64_t)FMM_NT * cp, TC_KC, nhalf) &&
@@ -395,10 +395,7 @@ fmm_status m2l_tc_prepare(Ctx* c) {
   if (nst < 2) return set_err(c, FMM_ERR_ARG, "M2L tensor path: stage too large for cpad %d", cp);
   c->tc_nst = nst;
   const int smem = nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
-  if (smem > c->tc_smem_set) {
-    FMM_CUDA(c, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    c->tc_smem_set = smem;
-  }
+  FMM_TRY(raise_smem_limit(c, (const void*)k_m2l_tc, smem));
   if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
   return FMM_OK;
 }

@@ -36,6 +36,8 @@ namespace fmm {
 
 namespace {
 
+// FP64 kernel shape; the mixed kernel's shape (warps per block, sources per
+// staged chunk) is one of the variants below, chosen per handle (fmm_autotune)
 constexpr int P2P_WARPS = 4;
 constexpr int P2P_CH = 256;
 
@@ -83,17 +85,18 @@ __device__ __forceinline__ void p2p_chunk(const float4* shi, const float4* slo, 
   p2p_span<G, false>(shi, slo, k0, cn, th, tl, fphi, fx, fy, fz);
 }
 
-__global__ void __launch_bounds__(P2P_WARPS * 32)
+template <int W, int CH>
+__global__ void __launch_bounds__(W * 32)
 k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
         const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
         float4* __restrict__ out) {
-  __shared__ float4 shi[P2P_WARPS][P2P_CH];
-  __shared__ float4 slo[P2P_WARPS][P2P_CH];
-  __shared__ int nb_first[P2P_WARPS][27];
-  __shared__ int nb_pre[P2P_WARPS][28];
-  __shared__ int8_t nb_off[P2P_WARPS][27][3];
+  __shared__ float4 shi[W][CH];
+  __shared__ float4 slo[W][CH];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * P2P_WARPS + warp;
+  const int item = blockIdx.x * W + warp;
   if (item >= nitems) return;
   int T;  // the leaf holding this item: last leaf with items[T] <= item
   {
@@ -156,8 +159,8 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
       tl = pos32lo[tf + tb + ti];
     }
     Kahan kp, kx, ky, kz;
-    for (int c0 = 0; c0 < total; c0 += P2P_CH) {
-      const int cn = min(P2P_CH, total - c0);
+    for (int c0 = 0; c0 < total; c0 += CH) {
+      const int cn = min(CH, total - c0);
       __syncwarp();
       for (int k = lane; k < cn; k += 32) {
         const int s = c0 + k;
@@ -305,14 +308,27 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
 
 }  // namespace
 
+// (warps per block, sources per staged chunk) of the mixed P2P variants, in
+// the order of fmm_autotune's index
+const int kP2PVariants[FMM_P2P_VARIANTS][2] = {{4, 256}, {2, 128}, {2, 256}, {4, 128}, {8, 128}, {8, 256}};
+
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
-  if (c->precision == FMM_MIXED)
-    k_p2p32<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
-                                                                          c->p2p_nitems, c->pos32, c->pos32lo,
-                                                                          c->box, c->near32);
-  else
+  if (c->precision == FMM_MIXED) {
+#define P2P_LAUNCH(W, CH)                                                                              \
+  k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_nitems, \
+                                                             c->pos32, c->pos32lo, c->box, c->near32)
+    switch (c->p2p_variant) {
+      case 1: P2P_LAUNCH(2, 128); break;
+      case 2: P2P_LAUNCH(2, 256); break;
+      case 3: P2P_LAUNCH(4, 128); break;
+      case 4: P2P_LAUNCH(8, 128); break;
+      case 5: P2P_LAUNCH(8, 256); break;
+      default: P2P_LAUNCH(4, 256); break;
+    }
+#undef P2P_LAUNCH
+  } else
     k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
                                                                           c->p2p_nitems, c->pos64, c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");

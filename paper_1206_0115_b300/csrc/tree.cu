@@ -991,6 +991,128 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
   return FMM_OK;
 }
 
+fmm_status ensure_expansions(Ctx* c, int precision) {
+  const int64_t rows = c->rows;
+  const size_t cp = (size_t)c->cpad;
+  void* p;
+  if (precision == FMM_MIXED && rows > c->rows_cap32) {
+    dfree(c, c->Mhi, 4 * cp * c->rows_cap32);
+    dfree(c, c->Mlo, 4 * cp * c->rows_cap32);
+    dfree(c, c->L32, 4 * cp * c->rows_cap32);
+    c->Mhi = c->Mlo = c->L32 = nullptr;
+    c->rows_cap32 = 0;
+    const int64_t cap = rows + rows / 8 + 16;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->Mhi = (float*)p;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->Mlo = (float*)p;
+    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
+    c->L32 = (float*)p;
+    FMM_CUDA(c, cudaMemsetAsync(c->Mhi, 0, 4 * cp * cap, c->stream));
+    FMM_CUDA(c, cudaMemsetAsync(c->Mlo, 0, 4 * cp * cap, c->stream));
+    FMM_CUDA(c, cudaMemsetAsync(c->L32, 0, 4 * cp * cap, c->stream));
+    c->rows_cap32 = cap;
+  }
+  if (precision == FMM_FP64 && rows > c->rows_cap64) {
+    dfree(c, c->M64, 8 * cp * c->rows_cap64);
+    dfree(c, c->L64, 8 * cp * c->rows_cap64);
+    c->M64 = c->L64 = nullptr;
+    c->rows_cap64 = 0;
+    const int64_t cap = rows + rows / 8 + 16;
+    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
+    c->M64 = (double*)p;
+    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
+    c->L64 = (double*)p;
+    FMM_CUDA(c, cudaMemsetAsync(c->M64, 0, 8 * cp * cap, c->stream));
+    FMM_CUDA(c, cudaMemsetAsync(c->L64, 0, 8 * cp * cap, c->stream));
+    c->rows_cap64 = cap;
+  }
+  return FMM_OK;
+}
+
+void release_tree(Ctx* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
+  auto rel = [&](auto*& ptr, size_t bytes) {
+    dfree(c, (void*)ptr, bytes);
+    ptr = nullptr;
+  };
+  const size_t nc = (size_t)c->ncap;
+  rel(c->key_a, 4 * nc);
+  rel(c->key_b, 4 * nc);
+  rel(c->idx_a, 4 * nc);
+  rel(c->idx_b, 4 * nc);
+  rel(c->perm, 4 * nc);
+  rel(c->pos64, 32 * nc);
+  rel(c->pos32, 16 * nc);
+  rel(c->pos32lo, 16 * nc);
+  rel(c->near32, 16 * nc);
+  rel(c->near64, 32 * nc);
+  c->skey = nullptr;
+  c->ncap = 0;
+  rel(c->scratch, 4 * (size_t)c->scratch_cap);
+  c->scratch_cap = 0;
+  rel(c->p2p_items, 4 * (size_t)c->p2p_items_cap);
+  c->p2p_items_cap = 0;
+  c->p2p_nitems = 0;
+  rel(c->stage_in, 8 * (size_t)c->stage_in_cap);
+  rel(c->stage_out, 8 * (size_t)c->stage_out_cap);
+  c->stage_in_cap = c->stage_out_cap = 0;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
+    const size_t lc = 4 * (size_t)c->lcap[l];
+    rel(c->lv.key[l], lc);
+    rel(c->lv.first[l], lc);
+    rel(c->lv.count[l], lc);
+    rel(c->lv.parent[l], lc);
+    rel(c->lv.cls[l], lc);
+    rel(c->slot_buf[l], lc);
+    c->lv.slot[l] = nullptr;
+    c->lcap[l] = 0;
+    rel(c->lv.grid[l], sizeof(int32_t) * ((size_t)1 << (3 * l)));
+    c->lv.ncell[l] = 0;
+    c->prev_ncell[l] = 0;
+  }
+  c->have_prev = false;
+  c->prev_leaf = -1;
+  const size_t cp = (size_t)c->cpad;
+  rel(c->Mhi, 4 * cp * c->rows_cap32);
+  rel(c->Mlo, 4 * cp * c->rows_cap32);
+  rel(c->L32, 4 * cp * c->rows_cap32);
+  rel(c->M64, 8 * cp * c->rows_cap64);
+  rel(c->L64, 8 * cp * c->rows_cap64);
+  c->rows_cap32 = c->rows_cap64 = 0;
+  c->rows = 0;
+  const size_t tc = (size_t)c->tiles_cap;
+  rel(c->tiles, sizeof(Tile) * tc);
+  rel(c->tile_src, sizeof(int32_t) * tc * FMM_NT_CLASS * FMM_TILE);
+  rel(c->tile_act, sizeof(int16_t) * tc * FMM_NT_CLASS);
+  rel(c->tile_nact, sizeof(int32_t) * tc);
+  rel(c->src_act, sizeof(int16_t) * tc * FMM_NT_CLASS);
+  rel(c->src_nact, sizeof(int32_t) * tc);
+  c->tiles_cap = 0;
+  c->ntiles = c->leaf_tiles = 0;
+  c->tiles_h.clear();
+  rel(c->tc_partial, 4 * (size_t)c->tc_partial_cap);
+  c->tc_partial_cap = 0;
+  dfree(c, c->svd_Y, c->svd_Y_cap);
+  c->svd_Y = nullptr;
+  c->svd_Y_cap = 0;
+  dfree(c, c->svd_recs, 128 * (size_t)c->svd_gcap);
+  c->svd_recs = nullptr;
+  c->svd_gcap = 0;
+  const size_t ec = (size_t)c->svd_ecap;
+  rel(c->svd_eslot, sizeof(int16_t) * ec * FMM_NT_CLASS);
+  rel(c->svd_ekch, sizeof(int8_t) * ec * FMM_NT_CLASS);
+  rel(c->svd_yidx, sizeof(int64_t) * ec * FMM_NT_CLASS * FMM_TILE);
+  c->svd_ecap = 0;
+  rel(c->svd_Mcls, 8 * (size_t)c->svd_mcls_rows * cp);
+  c->svd_mcls_rows = 0;
+  c->loaded = false;
+  c->forest = false;
+  c->n = 0;
+  c->tree_gen++;
+}
+
 fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   cudaStream_t s = c->stream;
   const int Lf = c->leaf;
@@ -1150,35 +1272,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     rows += c->lv.ncell[l] + 1;
   }
   c->rows = rows;
-  if (rows > c->rows_cap) {
-    int64_t cap = rows + rows / 8 + 16;
-    size_t cp = (size_t)c->cpad;
-    dfree(c, c->Mhi, 4 * cp * c->rows_cap);
-    dfree(c, c->Mlo, 4 * cp * c->rows_cap);
-    dfree(c, c->L32, 4 * cp * c->rows_cap);
-    dfree(c, c->M64, 8 * cp * c->rows_cap);
-    dfree(c, c->L64, 8 * cp * c->rows_cap);
-    c->Mhi = c->Mlo = c->L32 = nullptr;
-    c->M64 = c->L64 = nullptr;
-    c->rows_cap = 0;
-    void* p;
-    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
-    c->Mhi = (float*)p;
-    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
-    c->Mlo = (float*)p;
-    FMM_TRY(dalloc(c, &p, 4 * cp * cap));
-    c->L32 = (float*)p;
-    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
-    c->M64 = (double*)p;
-    FMM_TRY(dalloc(c, &p, 8 * cp * cap));
-    c->L64 = (double*)p;
-    FMM_CUDA(c, cudaMemsetAsync(c->Mhi, 0, 4 * cp * cap, s));
-    FMM_CUDA(c, cudaMemsetAsync(c->Mlo, 0, 4 * cp * cap, s));
-    FMM_CUDA(c, cudaMemsetAsync(c->L32, 0, 4 * cp * cap, s));
-    FMM_CUDA(c, cudaMemsetAsync(c->M64, 0, 8 * cp * cap, s));
-    FMM_CUDA(c, cudaMemsetAsync(c->L64, 0, 8 * cp * cap, s));
-    c->rows_cap = cap;
-  }
+  FMM_TRY(ensure_expansions(c, c->precision));
 
   // M2L tiles, leaf level first (largest first for the combined launch)
   std::vector<Tile> tiles;

@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
 FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FMM_FP64, FMM_MIXED = 0, 1
 FMM_M2L_FULL, FMM_M2L_SVD = 0, 1
+FMM_P2P_VARIANTS = 6
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
                 -5: "FMM_ERR_TIMEOUT"}
 
@@ -43,6 +44,9 @@ _SIGS = {
     "fmm_get_batch_info": [_vp, C.c_int32, _vp, _vp],
     "fmm_evaluate": [_vp, _vp, _vp],
     "fmm_get_order": [_vp, _vp],
+    "fmm_trim": [_vp],
+    "fmm_autotune": [_vp, _vp, _vp],
+    "fmm_set_p2p_variant": [_vp, C.c_int],
     "fmm_get_box": [_vp, _vp],
     "fmm_get_level_size": [_vp, C.c_int, _vp],
     "fmm_get_level_keys": [_vp, C.c_int, _vp],
@@ -55,12 +59,29 @@ _SIGS = {
     "fmm_get_m2l_kernel_times": [_vp, _vp],
     "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
 }
+_SIGS.update({
+    "fmm_server_create": [_vp, C.POINTER(_vp)],
+    "fmm_server_warmup": [_vp, C.c_int],
+    "fmm_server_submit": [_vp, C.c_int64, C.c_int, C.c_int, _vp, _vp, _vp, _vp, C.POINTER(C.c_int64)],
+    "fmm_server_wait": [_vp, C.c_int64, C.c_double, _vp],
+    "fmm_server_stats": [_vp, _vp],
+    "fmm_server_destroy": [_vp],
+})
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
     _f.restype = C.c_int
 lib.fmm_last_error.argtypes = [_vp]
 lib.fmm_last_error.restype = C.c_char_p
+lib.fmm_server_last_error.argtypes = [_vp]
+lib.fmm_server_last_error.restype = C.c_char_p
+lib.fmm_server_request_bytes.argtypes = [C.c_int64, C.c_int, C.c_int]
+lib.fmm_server_request_bytes.restype = C.c_int64
+
+
+class fmm_server_config(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("max_batch_particles", C.c_int64), ("max_batch_requests", C.c_int32), ("reserved", C.c_int32)]
 
 
 class FMMError(RuntimeError):
@@ -145,6 +166,22 @@ def fmm_evaluate(h, phi, F) -> int:
     return _check(h, lib.fmm_evaluate(h, _ptr(phi), _ptr(F)))
 
 
+def fmm_autotune(h):
+    """Returns (choice [index, warps, chunk], mean ms of each P2P variant)."""
+    choice = np.zeros(3, dtype=np.int32)
+    times = np.zeros(FMM_P2P_VARIANTS, dtype=np.float32)
+    _check(h, lib.fmm_autotune(h, _ptr(choice), _ptr(times)))
+    return choice, times
+
+
+def fmm_set_p2p_variant(h, variant: int) -> int:
+    return _check(h, lib.fmm_set_p2p_variant(h, variant))
+
+
+def fmm_trim(h) -> int:
+    return _check(h, lib.fmm_trim(h))
+
+
 def fmm_get_order(h, perm) -> int:
     return _check(h, lib.fmm_get_order(h, _ptr(perm)))
 
@@ -205,6 +242,59 @@ def fmm_get_m2l_kernel_times(h) -> np.ndarray:
 def fmm_morton_order_noalloc(n: int, xyz, height: int, keys, perm, stream=None) -> int:
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     return _check(None, lib.fmm_morton_order_noalloc(n, _ptr(xyz), height, _ptr(keys), _ptr(perm), handle))
+
+
+def _check_server(s, status: int):
+    if status != FMM_OK:
+        msg = lib.fmm_server_last_error(s) if s else b""
+        raise FMMError(status, msg.decode() if msg else "")
+    return status
+
+
+def fmm_server_request_bytes(n: int, height: int, order: int) -> int:
+    return int(lib.fmm_server_request_bytes(n, height, order))
+
+
+def fmm_server_create(lanes: int, precision: int, hbm_budget_bytes: int, max_batch_particles: int,
+                      max_batch_requests: int) -> int:
+    cfg = fmm_server_config(lanes, precision, hbm_budget_bytes, max_batch_particles, max_batch_requests, 0)
+    s = _vp()
+    _check_server(None, lib.fmm_server_create(C.byref(cfg), C.byref(s)))
+    return s.value
+
+
+def fmm_server_warmup(s, order: int) -> int:
+    return _check_server(s, lib.fmm_server_warmup(s, order))
+
+
+def fmm_server_submit(s, n: int, height: int, order: int, xyz, q, phi, F) -> int:
+    t = C.c_int64(0)
+    _check_server(s, lib.fmm_server_submit(s, n, height, order, _ptr(xyz), _ptr(q), _ptr(phi), _ptr(F),
+                                           C.byref(t)))
+    return t.value
+
+
+def fmm_server_wait(s, ticket: int, timeout_s: float = -1.0) -> np.ndarray:
+    """Blocks (without the GIL) until the request is done; returns its times
+    [queue ms, service ms, latency ms, batch size]."""
+    times = np.zeros(4, dtype=np.float64)
+    _check_server(s, lib.fmm_server_wait(s, ticket, timeout_s, _ptr(times)))
+    return times
+
+
+def fmm_server_stats(s) -> np.ndarray:
+    out = np.zeros(8, dtype=np.int64)
+    _check_server(s, lib.fmm_server_stats(s, _ptr(out)))
+    return out
+
+
+def fmm_server_destroy(s) -> int:
+    return lib.fmm_server_destroy(s)
+
+
+def fmm_server_last_error(s) -> str:
+    m = lib.fmm_server_last_error(s)
+    return m.decode() if m else ""
 
 
 def fmm_last_error(h) -> str:

@@ -53,3 +53,27 @@ def test_create_without_device_reports_cuda_error(F):
     assert F.lib.fmm_create(4, 5, ctypes.byref(h)) == F.FMM_ERR_CUDA
     assert h.value is None
     assert b"device" in F.lib.fmm_last_error(None)
+
+
+def test_server_request_bytes_formula(F):
+    """The admission estimate the header documents: 256 B per particle plus,
+    per cell (1.15 x min(n, 8^(h-1)) + 1), 28 x cpad + 4 x 189 x (16 | 32) + 1024."""
+    for n, h, p in [(0, 3, 5), (1000, 3, 5), (10**6, 6, 7), (5 * 10**6, 7, 5), (12345, 1, 2)]:
+        cpad = (p ** 3 + 1 + 31) // 32 * 32
+        cells = int(1.15 * min(n, 8 ** (h - 1))) + 1
+        want = 256 * n + cells * (28 * cpad + 4 * 189 * (16 if p <= 5 else 32) + 1024)
+        assert F.fmm_server_request_bytes(n, h, p) == want
+    assert F.fmm_server_request_bytes(-1, 3, 5) == -1
+    assert F.fmm_server_request_bytes(10, 3, 11) == -1
+
+
+def test_server_config_rejected_before_device_use(F):
+    cfg = F.fmm_server_config(0, 1, 1 << 30, 1000, 4, 0)
+    s = ctypes.c_void_p()
+    assert F.lib.fmm_server_create(ctypes.byref(cfg), ctypes.byref(s)) == F.FMM_ERR_ARG
+    for bad in [(2, 7, 1 << 30, 1000, 4, 0), (2, 1, 0, 1000, 4, 0), (2, 1, 1 << 30, 0, 4, 0),
+                (2, 1, 1 << 30, 1000, 0, 0), (2, 1, 1 << 30, 1000, 5000, 0), (17, 1, 1 << 30, 1000, 4, 0)]:
+        cfg = F.fmm_server_config(*bad)
+        assert F.lib.fmm_server_create(ctypes.byref(cfg), ctypes.byref(s)) == F.FMM_ERR_ARG, bad
+    assert F.lib.fmm_server_destroy(None) == F.FMM_OK
+    assert F.lib.fmm_server_submit(None, 1, 3, 5, None, None, None, None, None) == F.FMM_ERR_ARG

@@ -248,3 +248,33 @@ def test_batched_workload_sampled(F):
             rphi, rF = o.evaluate()
         assert oracle.rel_l2(phi[a:b], rphi) <= TOL_MIXED, k
         assert oracle.rel_l2(Fo[a:b], rF) <= TOL_MIXED, k
+
+
+def test_p2p_variants_agree_and_autotune_picks_one(F):
+    """Every shape of the mixed P2P kernel gives the same result up to the
+    grouping of FP32 partial sums; the autotuner keeps one of them."""
+    import torch
+    probs = _mixed_batch()
+    counts, heights, xyz, q = _concat(probs)
+    n = len(q)
+    out = {}
+    with F.FMM(3, 5, F.FMM_MIXED) as f:
+        f.set_batch(counts, heights, torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        for v in range(F.FMM_P2P_VARIANTS):
+            F.fmm_set_p2p_variant(f.h, v)
+            f.evaluate(phi, Fo)
+            torch.cuda.synchronize()
+            out[v] = (phi.cpu().numpy().copy(), Fo.cpu().numpy().copy())
+        choice, times = F.fmm_autotune(f.h)
+        assert 0 <= choice[0] < F.FMM_P2P_VARIANTS and np.all(times > 0)
+        assert times[choice[0]] == times.min()
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        assert np.array_equal(phi.cpu().numpy(), out[int(choice[0])][0])
+        with pytest.raises(F.FMMError):
+            F.fmm_set_p2p_variant(f.h, F.FMM_P2P_VARIANTS)
+    for v in range(1, F.FMM_P2P_VARIANTS):
+        assert oracle.rel_l2(out[v][0], out[0][0]) <= TOL_ALONE, v
+        assert oracle.rel_l2(out[v][1], out[0][1]) <= TOL_ALONE, v

@@ -377,3 +377,53 @@ def test_ellipsoid_n10m_h8_p7_full_size(F):
     assert oracle.rel_l2(Fo[idx], Fr) <= TOL_MIXED
     pd, Fd = oracle.direct_sampled(xyz, q, idx)
     print("ellipsoid mixed vs direct: phi %.3e F %.3e" % (oracle.rel_l2(phi[idx], pd), oracle.rel_l2(Fo[idx], Fd)))
+
+
+def test_handles_of_different_orders_interleave(F):
+    """Kernel launch limits are shared by all handles: a handle of a larger
+    order keeps working after a smaller one ran (and the other way round)."""
+    import torch
+    xyz, q = inputs.particles(6000, 31, "cube", "sym")
+    dx, dq = torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda()
+    outs = {}
+    with F.FMM(4, 7, F.FMM_MIXED) as f7, F.FMM(4, 4, F.FMM_MIXED) as f4:
+        for rnd in range(2):
+            for p, f in ((7, f7), (4, f4)):
+                f.set_particles(dx, dq)
+                phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
+                Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
+                f.evaluate(phi, Fo)
+                torch.cuda.synchronize()
+                outs[(rnd, p)] = (phi.cpu().numpy(), Fo.cpu().numpy())
+    for p in (7, 4):
+        assert np.array_equal(outs[(0, p)][0], outs[(1, p)][0]) and np.array_equal(outs[(0, p)][1], outs[(1, p)][1])
+    with _oracle(xyz, q, 4, 7) as o:
+        rphi, rF = o.evaluate()
+    assert oracle.rel_l2(outs[(1, 7)][0], rphi) <= TOL_MIXED and oracle.rel_l2(outs[(1, 7)][1], rF) <= TOL_MIXED
+
+
+def test_trim_releases_the_tree_and_keeps_the_operators(F):
+    import torch
+    xyz, q = inputs.particles(20000, 32, "cube", "sym")
+    dx, dq = torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda()
+    phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
+    Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
+    with F.FMM(5, 5, F.FMM_MIXED) as f:
+        f.set_particles(dx, dq)
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        a = (phi.cpu().numpy().copy(), Fo.cpu().numpy().copy())
+        held = int(f.stats()[3])
+        F.fmm_trim(f.h)
+        assert int(f.stats()[3]) < held // 2
+        with pytest.raises(F.FMMError) as e:
+            f.evaluate(phi, Fo)
+        assert e.value.status == F.FMM_ERR_STATE
+        f.set_particles(dx, dq)
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        assert np.array_equal(phi.cpu().numpy(), a[0]) and np.array_equal(Fo.cpu().numpy(), a[1])
+        # a precision never used on this tree has no expansions to read
+        F.fmm_set_precision(f.h, F.FMM_FP64)
+        with pytest.raises(F.FMMError):
+            F.fmm_get_expansion(f.h, 3, 0, np.zeros((F.fmm_get_level_size(f.h, 3), 125)))
