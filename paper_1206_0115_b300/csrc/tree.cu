@@ -178,6 +178,91 @@ __global__ void __launch_bounds__(1024) k_scan1(W* __restrict__ data, int64_t co
   if (t == 1023 && total) *total = part[1023];
 }
 
+// Exclusive scan of long arrays in three passes: per-block sums of
+// SC_CHUNK-entry chunks (coalesced), k_scan1 over the block sums, and a
+// per-block scan of each chunk staged through shared memory (coalesced loads
+// and stores; each thread scans SC_ITEMS consecutive entries).
+constexpr int SC_THREADS = 512;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_CHUNK = SC_THREADS * SC_ITEMS;
+
+template <typename W>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_sums(const W* __restrict__ data, int64_t count,
+                                                         W* __restrict__ bsum) {
+  const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+  W v = 0;
+  for (int k = threadIdx.x; k < SC_CHUNK; k += SC_THREADS) {
+    const int64_t i = base + k;
+    if (i < count) v += data[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ W ws[SC_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    W t = 0;
+    for (int w = 0; w < SC_THREADS / 32; ++w) t += ws[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_chunks(W* __restrict__ data, int64_t count,
+                                                           const W* __restrict__ boff) {
+  __shared__ W sm[SC_CHUNK];
+  __shared__ W ws[SC_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * SC_CHUNK;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < SC_CHUNK; k += SC_THREADS) {
+    const int64_t i = base + k;
+    sm[k] = i < count ? data[i] : W(0);
+  }
+  __syncthreads();
+  W loc[SC_ITEMS];
+  W sum = 0;
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) {
+    loc[j] = sm[tid * SC_ITEMS + j];
+    sum += loc[j];
+  }
+  W incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const W v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  W woff = 0;
+  for (int w = 0; w < warp; ++w) woff += ws[w];
+  W run = boff[blockIdx.x] + woff + incl - sum;
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) {
+    sm[tid * SC_ITEMS + j] = run;
+    run += loc[j];
+  }
+  __syncthreads();
+  for (int k = tid; k < SC_CHUNK; k += SC_THREADS) {
+    const int64_t i = base + k;
+    if (i < count) data[i] = sm[k];
+  }
+}
+
+// Exclusive scan of data[0..count) in place; the total goes to *total (if
+// not NULL).  work: ceil(count / SC_CHUNK) words of scratch.
+template <typename W>
+void scan_excl(cudaStream_t s, W* data, int64_t count, W* total, W* work, int64_t* launches) {
+  if (count <= 4 * SC_CHUNK) {
+    k_scan1<W><<<1, 1024, 0, s>>>(data, count, total);
+    *launches += 1;
+    return;
+  }
+  const int nb = ceil_div(count, SC_CHUNK);
+  k_scan_sums<W><<<nb, SC_THREADS, 0, s>>>(data, count, work);
+  k_scan1<W><<<1, 1024, 0, s>>>(work, nb, total);
+  k_scan_chunks<W><<<nb, SC_THREADS, 0, s>>>(data, count, work);
+  *launches += 3;
+}
+
 // Scatter of one digit pass.  The tile is walked in order, 256 keys at a time;
 // within a round a key's rank among equal digits is (earlier rounds) +
 // (earlier warps of this round) + (lower lanes of its warp), so equal keys
@@ -1185,9 +1270,10 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     uint32_t* hist = c->scratch;
     for (int sh = 0; sh < bits; sh += 8) {
       k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(n, ka, sh, hist, ntiles);
-      k_scan1<uint32_t><<<1, 1024, 0, s>>>(hist, (int64_t)256 * ntiles, nullptr);
+      scan_excl<uint32_t>(s, hist, (int64_t)256 * ntiles, nullptr, hist + (int64_t)256 * ntiles,
+                          &c->launches_set);
       k_radix_scatter<<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, kb, vb, sh, hist, ntiles);
-      c->launches_set += 3;
+      c->launches_set += 2;
       uint32_t* t = ka;
       ka = kb;
       kb = t;
@@ -1219,8 +1305,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       }
     // P2P items: exclusive offsets per leaf, total in counters[CNT_ITEMS]
     k_p2p_items<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items);
-    k_scan1<int32_t><<<1, 1024, 0, s>>>(c->p2p_items, ub[Lf], c->counters + CNT_ITEMS);
-    c->launches_set += 2;
+    scan_excl<int32_t>(s, c->p2p_items, ub[Lf], c->counters + CNT_ITEMS, (int32_t*)c->scratch, &c->launches_set);
+    c->launches_set += 1;
     if (Lf >= 2) {
       ClassArgs ca;
       for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
