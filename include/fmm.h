@@ -39,7 +39,7 @@ extern "C" {
 
 typedef struct fmm_ctx* fmm_handle;
 
-#define FMM_P2P_VARIANTS 6  /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+#define FMM_P2P_VARIANTS 10 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
 
 typedef enum {
   FMM_OK = 0,
@@ -174,14 +174,16 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
 
 /* Picks the shape of the mixed-precision P2P kernel (the near field of
  * Sec. 2.1, the largest kernel on surface distributions and batches) for the
- * current tree by timing each variant -- (warps per block, sources staged per
- * chunk) = (4,256), (2,128), (2,256), (4,128), (8,128), (8,256), index 0..5 --
- * three times on the handle's stream with CUDA events, and keeps the fastest
- * for later evaluations (the evaluation graph is rebuilt).  The variants give
- * the same sums up to the grouping of FP32 partial sums.  choice (may be
- * NULL): [0] index, [1] warps per block, [2] sources per chunk; times_ms
- * (may be NULL): FMM_P2P_VARIANTS mean launch times.  Synchronises the
- * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
+ * current tree by timing each variant three times on the handle's stream
+ * with CUDA events, and keeps the fastest for later evaluations (the
+ * evaluation graph is rebuilt).  Variants 0..5: one source per instruction,
+ * (warps per block, sources staged per chunk) = (4,256), (2,128), (2,256),
+ * (4,128), (8,128), (8,256); variants 6..9: two sources per instruction
+ * (packed FP32 pairs) in the shapes (4,256), (4,128), (8,128), (8,256).
+ * They give the same sums up to the grouping of FP32 partial sums.  choice
+ * (may be NULL): [0] index, [1] warps per block, [2] sources per chunk;
+ * times_ms (may be NULL): FMM_P2P_VARIANTS mean launch times.  Synchronises
+ * the stream.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
 
 /* Sets the P2P variant directly (0 .. FMM_P2P_VARIANTS-1; 0 is the default),

@@ -211,6 +211,241 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
   }
 }
 
+// ---- packed-pair variant --------------------------------------------------
+// The same sums with two sources per instruction: sm_100-class SMs execute
+// FP32 add / mul / fma on register pairs (add/sub/mul/fma.rn.f32x2), one
+// issue slot for two operations.  The near-field loop is issue-bound (one
+// interaction is 19 FP32 operations, a reciprocal square root and shared
+// loads), so halving its FP32 issue count lets the FP32 pipe, not the issue
+// port, set the pace.  Sources are staged as pairs in a structure-of-pairs
+// layout: for pair j (sources 2j, 2j+1) the words (x0,x1 | y0,y1),
+// (z0,z1 | q0,q1), (xl0,xl1 | yl0,yl1), (zl0,zl1), so every operand is a
+// register pair loaded by one 128- or 64-bit shared load.  An odd chunk is
+// padded with a zero charge 64 leaf widths away.  The arithmetic of each
+// pair is that of p2p_span: d = (hi_t - hi_s) + (lo_t - lo_s) per component.
+
+typedef unsigned long long f2_t;  // two FP32 values (low word = first)
+
+__device__ __forceinline__ f2_t f2pack(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(f2_t r) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ f2_t f2add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+struct PairAcc {
+  f2_t phi, fx, fy, fz;
+};
+
+template <int G, bool SELF>
+__device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, const ulonglong2* __restrict__ sB,
+                                          const ulonglong2* __restrict__ sC, const f2_t* __restrict__ sD, int j0,
+                                          int j1, f2_t TX, f2_t TY, f2_t TZ, f2_t LX, f2_t LY, f2_t LZ,
+                                          PairAcc& acc) {
+#pragma unroll 2
+  for (int j = j0; j < j1; j += G) {
+    const ulonglong2 a = sA[j], b = sB[j], c = sC[j];
+    const f2_t dlz = sD[j];
+    const f2_t dx = f2add(f2sub(TX, a.x), f2sub(LX, c.x));
+    const f2_t dy = f2add(f2sub(TY, a.y), f2sub(LY, c.y));
+    const f2_t dz = f2add(f2sub(TZ, b.x), f2sub(LZ, dlz));
+    const f2_t r2 = f2fma(dx, dx, f2fma(dy, dy, f2mul(dz, dz)));
+    const float2 rr = f2unpack(r2);
+    float i0 = rsqrtf(rr.x), i1 = rsqrtf(rr.y);
+    if (SELF) {
+      i0 = rr.x > 0.f ? i0 : 0.f;
+      i1 = rr.y > 0.f ? i1 : 0.f;
+    }
+    const f2_t inv = f2pack(i0, i1);
+    const f2_t qi = f2mul(b.y, inv);
+    const f2_t qi3 = f2mul(f2mul(qi, inv), inv);
+    acc.phi = f2add(acc.phi, qi);
+    acc.fx = f2fma(qi3, dx, acc.fx);
+    acc.fy = f2fma(qi3, dy, acc.fy);
+    acc.fz = f2fma(qi3, dz, acc.fz);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void p2p_pair_chunk(const ulonglong2* sA, const ulonglong2* sB, const ulonglong2* sC,
+                                               const f2_t* sD, int sub, int jown, int np, f2_t TX, f2_t TY, f2_t TZ,
+                                               f2_t LX, f2_t LY, f2_t LZ, PairAcc& acc) {
+  p2p_pairs<G, true>(sA, sB, sC, sD, sub, jown, TX, TY, TZ, LX, LY, LZ, acc);
+  const int j0 = jown + ((sub - jown) % G + G) % G;
+  p2p_pairs<G, false>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, acc);
+}
+
+template <int W, int CH>
+__global__ void __launch_bounds__(W * 32)
+k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+          const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
+          float4* __restrict__ out) {
+  constexpr int NP = CH / 2;
+  __shared__ ulonglong2 sA[W][NP];
+  __shared__ ulonglong2 sB[W][NP];
+  __shared__ ulonglong2 sC[W][NP];
+  __shared__ f2_t sD[W][NP];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * W + warp;
+  if (item >= nitems) return;
+  int T;  // the leaf holding this item: last leaf with items[T] <= item
+  {
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    T = lo;
+  }
+  const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int tb = (item - items[T]) * 32;
+  int ix, iy, iz;
+  demorton3(lv.key[leaf][T], ix, iy, iz);
+  const int top = (1 << leaf) - 1;
+  const int mine = problem_of(lv, leaf, T);
+  int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
+  if (lane < 27) {
+    const int k = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+    ox = k / 9 - 1;
+    oy = (k / 3) % 3 - 1;
+    oz = k % 3 - 1;
+    const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
+    if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
+      const int g = lv.grid[leaf][morton3(sx, sy, sz)];
+      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
+        nf = lv.first[leaf][g];
+        ncnt = lv.count[leaf][g];
+      }
+    }
+  }
+  int incl = ncnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane < 27) {
+    nb_first[warp][lane] = nf;
+    nb_pre[warp][lane] = incl - ncnt;
+    nb_off[warp][lane][0] = (int8_t)ox;
+    nb_off[warp][lane][1] = (int8_t)oy;
+    nb_off[warp][lane][2] = (int8_t)oz;
+  }
+  if (lane == 0) nb_pre[warp][27] = total;
+  __syncwarp();
+  const int own = tc;  // sources [0, own) are the target leaf's particles
+
+  const int nt = min(32, tc - tb);
+  int lg = 0;
+  while ((nt << (lg + 1)) <= 32) ++lg;
+  const int g = 1 << lg, ti = lane >> lg, sub = lane & (g - 1);
+  const bool tvalid = ti < nt;
+  float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+  if (tvalid) {
+    th = pos32[tf + tb + ti];
+    tl = pos32lo[tf + tb + ti];
+  }
+  const f2_t TX = f2pack(th.x, th.x), TY = f2pack(th.y, th.y), TZ = f2pack(th.z, th.z);
+  const f2_t LX = f2pack(tl.x, tl.x), LY = f2pack(tl.y, tl.y), LZ = f2pack(tl.z, tl.z);
+  Kahan kp, kx, ky, kz;
+  // staged source s of the chunk starting at c0: position (hi with the
+  // neighbour shift, lo) and charge
+  auto fetch = [&](int s, float4& ph, float4& pl) {
+    int lo = 0, hi = 26;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (nb_pre[warp][mid] <= s) lo = mid;
+      else hi = mid - 1;
+    }
+    const int j = nb_first[warp][lo] + (s - nb_pre[warp][lo]);
+    ph = pos32[j];
+    ph.x += (float)nb_off[warp][lo][0];
+    ph.y += (float)nb_off[warp][lo][1];
+    ph.z += (float)nb_off[warp][lo][2];
+    pl = pos32lo[j];
+  };
+  for (int c0 = 0; c0 < total; c0 += CH) {
+    const int cn = min(CH, total - c0);
+    const int np = (cn + 1) >> 1;
+    __syncwarp();
+    for (int m = lane; m < np; m += 32) {
+      float4 h0, l0, h1, l1;
+      fetch(c0 + 2 * m, h0, l0);
+      if (2 * m + 1 < cn) {
+        fetch(c0 + 2 * m + 1, h1, l1);
+      } else {  // padding: no charge, far from every target
+        h1 = make_float4(64.f, 64.f, 64.f, 0.f);
+        l1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      sA[warp][m] = make_ulonglong2(f2pack(h0.x, h1.x), f2pack(h0.y, h1.y));
+      sB[warp][m] = make_ulonglong2(f2pack(h0.z, h1.z), f2pack(h0.w, h1.w));
+      sC[warp][m] = make_ulonglong2(f2pack(l0.x, l1.x), f2pack(l0.y, l1.y));
+      sD[warp][m] = f2pack(l0.z, l1.z);
+    }
+    __syncwarp();
+    PairAcc acc{0ull, 0ull, 0ull, 0ull};
+    // pairs [0, jown) may hold the target's own leaf (r = 0 pairs skipped)
+    const int kown = min(cn, max(0, own - c0));
+    const int jown = (kown + 1) >> 1;
+    const ulonglong2* A = &sA[warp][0];
+    const ulonglong2* B = &sB[warp][0];
+    const ulonglong2* Cc = &sC[warp][0];
+    const f2_t* D = &sD[warp][0];
+    switch (g) {
+      case 1: p2p_pair_chunk<1>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 2: p2p_pair_chunk<2>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 4: p2p_pair_chunk<4>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 8: p2p_pair_chunk<8>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 16: p2p_pair_chunk<16>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      default: p2p_pair_chunk<32>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+    }
+    const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
+    kp.add(ph.x + ph.y);
+    kx.add(px.x + px.y);
+    ky.add(py.x + py.y);
+    kz.add(pz.x + pz.y);
+  }
+  float aphi = kp.s, ax = kx.s, ay = ky.s, az = kz.s;
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+  if (tvalid && sub == 0) {
+    const float s1 = (float)(1.0 / ldexp(box[3], -leaf)), s2 = s1 * s1;
+    out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
+  }
+}
+
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
 k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
@@ -310,7 +545,9 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
 
 // (warps per block, sources per staged chunk) of the mixed P2P variants, in
 // the order of fmm_autotune's index
-const int kP2PVariants[FMM_P2P_VARIANTS][2] = {{4, 256}, {2, 128}, {2, 256}, {4, 128}, {8, 128}, {8, 256}};
+// variants 6.. are the packed-pair kernel (k_p2p32x2) in the same shapes
+const int kP2PVariants[FMM_P2P_VARIANTS][2] = {{4, 256}, {2, 128}, {2, 256}, {4, 128}, {8, 128}, {8, 256},
+                                               {4, 256}, {4, 128}, {8, 128}, {8, 256}};
 
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
@@ -319,15 +556,23 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
 #define P2P_LAUNCH(W, CH)                                                                              \
   k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_nitems, \
                                                              c->pos32, c->pos32lo, c->box, c->near32)
+#define P2P_LAUNCH2(W, CH)                                                                                \
+  k_p2p32x2<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_nitems, \
+                                                               c->pos32, c->pos32lo, c->box, c->near32)
     switch (c->p2p_variant) {
       case 1: P2P_LAUNCH(2, 128); break;
       case 2: P2P_LAUNCH(2, 256); break;
       case 3: P2P_LAUNCH(4, 128); break;
       case 4: P2P_LAUNCH(8, 128); break;
       case 5: P2P_LAUNCH(8, 256); break;
+      case 6: P2P_LAUNCH2(4, 256); break;
+      case 7: P2P_LAUNCH2(4, 128); break;
+      case 8: P2P_LAUNCH2(8, 128); break;
+      case 9: P2P_LAUNCH2(8, 256); break;
       default: P2P_LAUNCH(4, 256); break;
     }
 #undef P2P_LAUNCH
+#undef P2P_LAUNCH2
   } else
     k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
                                                                           c->p2p_nitems, c->pos64, c->near64);
