@@ -44,10 +44,13 @@ REFERENCE_STEP_SAMPLE = dict(n=15_625, height=4, order=7, dist="cube", qkind="sy
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates
-# FP32-pipe operations of one P2P interaction in k_p2p: 3 subtractions, the
-# squared distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential
-# sum (1) and the field sums (3 FMA); 1/sqrt runs on the MUFU pipe
-P2P_FP32_OPS = 13
+# FP32 operations of one P2P interaction as the mixed kernel issues them: the
+# exact difference (hi_t - hi_s) + (lo_t - lo_s) per axis (9), the squared
+# distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential sum (1)
+# and the field sums (3 FMA) = 19; 1/sqrt runs on the MUFU pipe.  A plain
+# single-word FP32 difference would need 13.
+P2P_FP32_OPS = 19
+P2P_FP32_OPS_PLAIN = 13
 
 
 def parse():
@@ -171,6 +174,36 @@ def replica_throughput(n_local: int, steps: int, local_ms: float, device="cpu"):
     return n_local * ws * steps / (max_ms / 1e3), max_ms
 
 
+def stage_rooflines(n, h, p, ncell, iso, build_ms, pk, precision):
+    """HBM rooflines of the stages around M2L and P2P (each timed alone):
+    algorithmic bytes per evaluation / stage time against the measured copy
+    bandwidth.  Mixed precision: a multipole row is C TF32 hi/lo pairs (8 B
+    per coefficient), a local row C + 1 FP32 values."""
+    if precision != "mixed" or h < 3:
+        return None
+    C = p ** 3
+    Lf = h - 1
+    leaves = ncell[Lf]
+    parents = sum(ncell[2:Lf])  # cells of levels 2 .. Lf-1 (M2M outputs, L2L inputs)
+    bw = pk["hbm"]
+    stages = {
+        # P2M: pos32 in, leaf multipoles out; M2M: 8 children in, parent out
+        "upward": (16 * n + 8 * C * leaves + 9 * 8 * C * parents, iso[0]),
+        # L2L: parent in, 8 children read and written
+        "l2l": (4 * (C + 1) * parents + 2 * 8 * 4 * (C + 1) * parents, iso[4]),
+        # L2P + output: pos32, near field and permutation in, phi and F (FP64) out, leaf locals in
+        "l2p_out": (n * (16 + 16 + 4 + 32) + 4 * (C + 1) * leaves, iso[6]),
+        # tree build: coordinates and charges in (twice: cube, keys), 4 radix passes of key + index,
+        # gather in Morton order (32 B in, 32 + 16 + 16 + 4 B out), cells
+        "set_particles": (n * (32 + 24 + 4 * 16 + 32 + 68) + 20 * sum(ncell), build_ms),
+    }
+    out = {}
+    for k, (b, ms) in stages.items():
+        out[k] = {"ms": float(ms), "bytes": int(b), "gbs": b / (ms / 1e3) / 1e9,
+                  "frac_of_hbm": b / (ms / 1e3) / 1e9 / bw}
+    return out
+
+
 def oracle_operators(s: dict, m2l: str):
     """An oracle tree whose compressed M2L operators later trees reuse (the
     operators depend on the order only, as the GPU path's are computed once
@@ -281,6 +314,7 @@ def run_ours(args):
     if not args.no_autotune:
         choice, ttimes = fmm.fmm_autotune(f.h)
         tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
+                 "sources_per_instruction": int(choice[3]), "unroll": int(choice[4]),
                  "variant_ms": [round(float(t), 4) for t in ttimes]}
         step()
         torch.cuda.synchronize()
@@ -309,11 +343,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     t_wall = time.perf_counter()
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))
         starts[k].record(stream)
-        step()
+        f.set_particles(xyz, q)
+        mids[k].record(stream)
+        f.evaluate(phi, F)
         ends[k].record(stream)
         stage.append(fmm.fmm_get_stage_times(f.h).tolist())
         if tc_timed:
@@ -324,7 +361,9 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    build_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, mids)]))
     value, total_ms = replica_throughput(n, args.steps, sum(ms), device=dev)
+    ncell = [fmm.fmm_get_level_size(f.h, l) for l in range(h)]
 
     # end to end through the same calls with pinned host buffers
     xyz_h = torch.from_numpy(xyz_np).pin_memory()
@@ -453,7 +492,10 @@ def run_ours(args):
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
                          "fp32_ops_per_interaction": P2P_FP32_OPS,
                          "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2),
+                         "fp32_pipe_frac_plain_13": P2P_FP32_OPS_PLAIN * p2p_pairs / (p2p_ms / 1e3)
+                         / (fp32_peak * 1e12 / 2),
                          "peak_fp32_tflops": fp32_peak},
+        "roofline_stages": stage_rooflines(n, h, p, ncell, iso, build_ms, pk, args.precision),
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
                 "d2h_bytes_per_step": int(32 * n), "steps": len(e_ms)},
@@ -514,6 +556,7 @@ def run_batched(args):
     if not args.no_autotune:
         choice, ttimes = fmm.fmm_autotune(f.h)
         tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
+                 "sources_per_instruction": int(choice[3]), "unroll": int(choice[4]),
                  "variant_ms": [round(float(t), 4) for t in ttimes]}
         step()
         torch.cuda.synchronize()
@@ -619,6 +662,7 @@ def run_batched(args):
         "autotune": tuned,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)", "interactions": p2p_pairs,
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
+                         "fp32_ops_per_interaction": P2P_FP32_OPS,
                          "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2)},
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
@@ -786,6 +830,7 @@ def run_serving(args):
             raise submit_err[0]
         st = fmm.fmm_server_stats(s) - st0
         st[3:8] = fmm.fmm_server_stats(s)[3:8]
+        span_lanes = lanes * (time.perf_counter() - t0)
     finally:
         fmm.fmm_server_destroy(s)
     times = np.array(times)
@@ -830,7 +875,11 @@ def run_serving(args):
                       "wall_s": t_end - t0},
         "server": {"batches": int(st[1]), "mean_batch_requests": float(nreq / max(1, st[1])),
                    "largest_batch": int(st[5]), "peak_batches_at_once": int(st[4]),
-                   "peak_inflight_estimate_bytes": int(st[3]), "device_bytes_held": int(st[7])},
+                   "peak_inflight_estimate_bytes": int(st[3]), "device_bytes_held": int(st[7]),
+                   "lane_time_s": {"copy_in": st[8] / 1e6, "set_batch": st[9] / 1e6,
+                                   "evaluate_and_copy_out": st[10] / 1e6},
+                   "lane_busy_frac": float((st[8] + st[9] + st[10]) / 1e6 / span_lanes),
+                   "trims": int(st[11])},
         "check_vs_alone": check,
         "e2e": {"value": parts / span, "unit": UNIT, "h2d_bytes_per_step": int(32 * parts / nreq),
                 "d2h_bytes_per_step": int(32 * parts / nreq)},

@@ -39,7 +39,7 @@ extern "C" {
 
 typedef struct fmm_ctx* fmm_handle;
 
-#define FMM_P2P_VARIANTS 10 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+#define FMM_P2P_VARIANTS 12 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
 
 typedef enum {
   FMM_OK = 0,
@@ -176,14 +176,16 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * Sec. 2.1, the largest kernel on surface distributions and batches) for the
  * current tree by timing each variant three times on the handle's stream
  * with CUDA events, and keeps the fastest for later evaluations (the
- * evaluation graph is rebuilt).  Variants 0..5: one source per instruction,
- * (warps per block, sources staged per chunk) = (4,256), (2,128), (2,256),
- * (4,128), (8,128), (8,256); variants 6..9: two sources per instruction
- * (packed FP32 pairs) in the shapes (4,256), (4,128), (8,128), (8,256).
- * They give the same sums up to the grouping of FP32 partial sums.  choice
- * (may be NULL): [0] index, [1] warps per block, [2] sources per chunk;
- * times_ms (may be NULL): FMM_P2P_VARIANTS mean launch times.  Synchronises
- * the stream.  Errors: FMM_ERR_STATE (no particles loaded). */
+ * evaluation graph is rebuilt).  Variants 0..5: two sources per
+ * instruction (packed FP32 pairs), (warps per block, sources staged per
+ * chunk, unroll of the pair loop) = (8,128,4) -- the default --, (4,128,4),
+ * (4,256,2), (4,128,2), (8,128,2), (8,256,2); variants 6..11: one source per
+ * instruction, (warps, chunk) = (4,256), (2,128), (2,256), (4,128), (8,128),
+ * (8,256).  They give the same sums up to the grouping of FP32 partial sums.
+ * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
+ * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
+ * FMM_P2P_VARIANTS mean launch times.  Synchronises the
+ * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
 
 /* Sets the P2P variant directly (0 .. FMM_P2P_VARIANTS-1; 0 is the default),
@@ -369,10 +371,12 @@ fmm_status fmm_server_submit(fmm_server_handle s, int64_t n, int height, int ord
 fmm_status fmm_server_wait(fmm_server_handle s, int64_t ticket, double timeout_s, double* times);
 
 /* Counters: out[0] requests completed, [1] batches run, [2] particles
- * completed, [3] peak memory estimate in flight (bytes), [4] peak number of
- * batches running at once, [5] largest batch (requests), [6] requests queued
- * now, [7] device bytes held by the lanes (handles and staging buffers).
- * out: 8 int64, host. */
+ * completed, [3] peak memory charge at an admission (bytes), [4] peak number
+ * of batches running at once, [5] largest batch (requests), [6] requests
+ * queued now, [7] device bytes held by the lanes (handles and staging),
+ * [8] [9] [10] lane time summed over batches, in microseconds: copying the
+ * inputs, fmm_set_batch, fmm_evaluate + copying the results, [11] trims of
+ * idle handles.  out: 12 int64, host. */
 fmm_status fmm_server_stats(fmm_server_handle s, int64_t* out);
 
 /* Stops the lanes after their current batch, fails the requests still

@@ -186,7 +186,7 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 std::vector<int64_t> graph_signature(const Ctx* c) {
   std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
-                            (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant};
+                            (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -352,6 +352,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
   void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pos64, c->pos32, c->pos32lo, c->p2p_items,
+                  c->p2p_leaf,
                   c->near32,
                   c->near64,
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
@@ -605,8 +606,7 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
   if (st != FMM_OK) return st;
   if (choice) {
     choice[0] = best_v;
-    choice[1] = kP2PVariants[best_v][0];
-    choice[2] = kP2PVariants[best_v][1];
+    for (int k = 0; k < 4; ++k) choice[1 + k] = kP2PVariants[best_v][k];
   }
   return FMM_OK;
 }

@@ -110,6 +110,8 @@ struct fmm_ctx {
   float4* near32 = nullptr;
   int32_t* p2p_items = nullptr;  // per leaf: first P2P work item (batches of 32 targets)
   int64_t p2p_items_cap = 0;
+  int32_t* p2p_leaf = nullptr;   // per work item: its leaf
+  int64_t p2p_leaf_cap = 0;
   int p2p_nitems = 0;
   int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants)
   double4* near64 = nullptr;
@@ -282,7 +284,7 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
 fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
-extern const int kP2PVariants[FMM_P2P_VARIANTS][2];
+extern const int kP2PVariants[FMM_P2P_VARIANTS][4];
 fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
 fmm_status svd_prepare(Ctx* c);        // SVD of the canonical operators (ranks to the host)

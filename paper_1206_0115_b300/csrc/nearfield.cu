@@ -87,7 +87,8 @@ __device__ __forceinline__ void p2p_chunk(const float4* shi, const float4* slo, 
 
 template <int W, int CH>
 __global__ void __launch_bounds__(W * 32)
-k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+        int nitems,
         const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
         float4* __restrict__ out) {
   __shared__ float4 shi[W][CH];
@@ -98,16 +99,7 @@ k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * W + warp;
   if (item >= nitems) return;
-  int T;  // the leaf holding this item: last leaf with items[T] <= item
-  {
-    int lo = 0, hi = nleaf - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (items[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    T = lo;
-  }
+  const int T = leaf_of[item];  // the leaf holding this item
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
   const int tb = (item - items[T]) * 32;
   int ix, iy, iz;
@@ -261,12 +253,12 @@ struct PairAcc {
   f2_t phi, fx, fy, fz;
 };
 
-template <int G, bool SELF>
+template <int G, bool SELF, int U>
 __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, const ulonglong2* __restrict__ sB,
                                           const ulonglong2* __restrict__ sC, const f2_t* __restrict__ sD, int j0,
                                           int j1, f2_t TX, f2_t TY, f2_t TZ, f2_t LX, f2_t LY, f2_t LZ,
                                           PairAcc& acc) {
-#pragma unroll 2
+#pragma unroll U
   for (int j = j0; j < j1; j += G) {
     const ulonglong2 a = sA[j], b = sB[j], c = sC[j];
     const f2_t dlz = sD[j];
@@ -290,18 +282,19 @@ __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, con
   }
 }
 
-template <int G>
+template <int G, int U>
 __device__ __forceinline__ void p2p_pair_chunk(const ulonglong2* sA, const ulonglong2* sB, const ulonglong2* sC,
                                                const f2_t* sD, int sub, int jown, int np, f2_t TX, f2_t TY, f2_t TZ,
                                                f2_t LX, f2_t LY, f2_t LZ, PairAcc& acc) {
-  p2p_pairs<G, true>(sA, sB, sC, sD, sub, jown, TX, TY, TZ, LX, LY, LZ, acc);
+  p2p_pairs<G, true, 1>(sA, sB, sC, sD, sub, jown, TX, TY, TZ, LX, LY, LZ, acc);
   const int j0 = jown + ((sub - jown) % G + G) % G;
-  p2p_pairs<G, false>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, acc);
+  p2p_pairs<G, false, U>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, acc);
 }
 
-template <int W, int CH>
+template <int W, int CH, int U>
 __global__ void __launch_bounds__(W * 32)
-k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+          int nitems,
           const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
           float4* __restrict__ out) {
   constexpr int NP = CH / 2;
@@ -315,16 +308,7 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * W + warp;
   if (item >= nitems) return;
-  int T;  // the leaf holding this item: last leaf with items[T] <= item
-  {
-    int lo = 0, hi = nleaf - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (items[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    T = lo;
-  }
+  const int T = leaf_of[item];  // the leaf holding this item
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
   const int tb = (item - items[T]) * 32;
   int ix, iy, iz;
@@ -420,12 +404,12 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     const ulonglong2* Cc = &sC[warp][0];
     const f2_t* D = &sD[warp][0];
     switch (g) {
-      case 1: p2p_pair_chunk<1>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 2: p2p_pair_chunk<2>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 4: p2p_pair_chunk<4>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 8: p2p_pair_chunk<8>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 16: p2p_pair_chunk<16>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      default: p2p_pair_chunk<32>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 1: p2p_pair_chunk<1, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 2: p2p_pair_chunk<2, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 4: p2p_pair_chunk<4, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 8: p2p_pair_chunk<8, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 16: p2p_pair_chunk<16, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      default: p2p_pair_chunk<32, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
     }
     const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
     kp.add(ph.x + ph.y);
@@ -448,7 +432,8 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
 
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
-k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, int nitems,
+k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+        int nitems,
         const double4* __restrict__ pos64, double4* __restrict__ out) {
   __shared__ double4 src[P2P_WARPS][P2P_CH];
   __shared__ int nb_first[P2P_WARPS][27];
@@ -456,16 +441,7 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * P2P_WARPS + warp;
   if (item >= nitems) return;
-  int T;  // the leaf holding this item: last leaf with items[T] <= item
-  {
-    int lo = 0, hi = nleaf - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (items[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    T = lo;
-  }
+  const int T = leaf_of[item];  // the leaf holding this item
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
   const int tb = (item - items[T]) * 32;
   int ix, iy, iz;
@@ -546,35 +522,41 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, in
 // (warps per block, sources per staged chunk) of the mixed P2P variants, in
 // the order of fmm_autotune's index
 // variants 6.. are the packed-pair kernel (k_p2p32x2) in the same shapes
-const int kP2PVariants[FMM_P2P_VARIANTS][2] = {{4, 256}, {2, 128}, {2, 256}, {4, 128}, {8, 128}, {8, 256},
-                                               {4, 256}, {4, 128}, {8, 128}, {8, 256}};
+// (warps, chunk, sources per instruction, unroll of the pair loop); index 0
+// is the default (the packed kernel, fastest on every workload measured)
+const int kP2PVariants[FMM_P2P_VARIANTS][4] = {{8, 128, 2, 4}, {4, 128, 2, 4}, {4, 256, 2, 2}, {4, 128, 2, 2},
+                                               {8, 128, 2, 2}, {8, 256, 2, 2}, {4, 256, 1, 4}, {2, 128, 1, 4},
+                                               {2, 256, 1, 4}, {4, 128, 1, 4}, {8, 128, 1, 4}, {8, 256, 1, 4}};
 
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
   if (c->precision == FMM_MIXED) {
 #define P2P_LAUNCH(W, CH)                                                                              \
-  k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_nitems, \
-                                                             c->pos32, c->pos32lo, c->box, c->near32)
-#define P2P_LAUNCH2(W, CH)                                                                                \
-  k_p2p32x2<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_nitems, \
-                                                               c->pos32, c->pos32lo, c->box, c->near32)
+  k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,   \
+                                                             c->p2p_nitems, c->pos32, c->pos32lo, c->box, c->near32)
+#define P2P_LAUNCH2(W, CH, U)                                                                          \
+  k_p2p32x2<W, CH, U><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,         \
+                                                                  c->p2p_leaf, c->p2p_nitems, c->pos32,        \
+                                                                  c->pos32lo, c->box, c->near32)
     switch (c->p2p_variant) {
-      case 1: P2P_LAUNCH(2, 128); break;
-      case 2: P2P_LAUNCH(2, 256); break;
-      case 3: P2P_LAUNCH(4, 128); break;
-      case 4: P2P_LAUNCH(8, 128); break;
-      case 5: P2P_LAUNCH(8, 256); break;
-      case 6: P2P_LAUNCH2(4, 256); break;
-      case 7: P2P_LAUNCH2(4, 128); break;
-      case 8: P2P_LAUNCH2(8, 128); break;
-      case 9: P2P_LAUNCH2(8, 256); break;
-      default: P2P_LAUNCH(4, 256); break;
+      case 1: P2P_LAUNCH2(4, 128, 4); break;
+      case 2: P2P_LAUNCH2(4, 256, 2); break;
+      case 3: P2P_LAUNCH2(4, 128, 2); break;
+      case 4: P2P_LAUNCH2(8, 128, 2); break;
+      case 5: P2P_LAUNCH2(8, 256, 2); break;
+      case 6: P2P_LAUNCH(4, 256); break;
+      case 7: P2P_LAUNCH(2, 128); break;
+      case 8: P2P_LAUNCH(2, 256); break;
+      case 9: P2P_LAUNCH(4, 128); break;
+      case 10: P2P_LAUNCH(8, 128); break;
+      case 11: P2P_LAUNCH(8, 256); break;
+      default: P2P_LAUNCH2(8, 128, 4); break;
     }
 #undef P2P_LAUNCH
 #undef P2P_LAUNCH2
   } else
-    k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,
+    k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
                                                                           c->p2p_nitems, c->pos64, c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");
 }

@@ -75,6 +75,7 @@ struct fmm_server {
   int64_t inflight = 0, peak_inflight = 0;
   int busy = 0, peak_busy = 0;
   int64_t peak_held = 0;  // peak device bytes held by all lanes after a batch
+  int64_t us_copy_in = 0, us_build = 0, us_eval = 0, trims = 0;  // lane time per phase (microseconds), trims
   int64_t n_done = 0, n_batches = 0, particles_done = 0, largest_batch = 0;
   bool stop = false;
   std::vector<Lane*> lanes;
@@ -160,7 +161,8 @@ int64_t lane_held(Lane* L) {
 // Releases the lane's per-tree memory (its handles keep their operators):
 // first the handles of orders other than `keep`, then, if `all`, every handle
 // and the staging buffers.  Called with the lock held, by the lane itself.
-void lane_trim(Lane* L, int keep, bool all) {
+void lane_trim(fmm_server* s, Lane* L, int keep, bool all) {
+  s->trims++;
   for (auto& kv : L->h)
     if (all || kv.first != keep) fmm_trim(kv.second);
   if (all) {
@@ -213,7 +215,8 @@ fmm_status stage_capacity(fmm_server* s, Lane* L, int64_t n) {
   return FMM_OK;
 }
 
-fmm_status run_batch(fmm_server* s, Lane* L, const std::vector<Req*>& b) {
+fmm_status run_batch(fmm_server* s, Lane* L, const std::vector<Req*>& b, int64_t* us) {
+  const Clock::time_point t0 = Clock::now();
   fmm_handle h = nullptr;
   FMM_TRY(lane_handle(s, L, b[0]->order, &h));
   int64_t n = 0;
@@ -240,7 +243,13 @@ fmm_status run_batch(fmm_server* s, Lane* L, const std::vector<Req*>& b) {
     }
     off += r->n;
   }
+  if (cudaStreamSynchronize(L->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return server_err(s, FMM_ERR_CUDA, "batch of %zu requests: input copies failed", b.size());
+  }
+  const Clock::time_point t1 = Clock::now();
   fmm_status st = fmm_set_batch(h, (int32_t)b.size(), counts.data(), heights.data(), xyz, q);
+  const Clock::time_point t2 = Clock::now();
   if (st == FMM_OK && n > 0) st = fmm_evaluate(h, phi, F);
   if (st != FMM_OK) return server_err(s, st, "batch of %zu requests: %s", b.size(), fmm_last_error(h));
   off = 0;
@@ -258,6 +267,10 @@ fmm_status run_batch(fmm_server* s, Lane* L, const std::vector<Req*>& b) {
     cudaGetLastError();
     return server_err(s, FMM_ERR_CUDA, "batch of %zu requests: stream synchronisation failed", b.size());
   }
+  const Clock::time_point t3 = Clock::now();
+  us[0] = std::chrono::duration_cast<std::chrono::microseconds>(t1 - t0).count();
+  us[1] = std::chrono::duration_cast<std::chrono::microseconds>(t2 - t1).count();
+  us[2] = std::chrono::duration_cast<std::chrono::microseconds>(t3 - t2).count();
   return FMM_OK;
 }
 
@@ -275,10 +288,10 @@ void lane_main(fmm_server* s, Lane* L) {
         // the head does not fit: give back what this lane holds (handles of
         // other orders first) and wake the other idle lanes to do the same
         if (!L->trimmed) {
-          lane_trim(L, s->queue.front()->order, false);
+          lane_trim(s, L, s->queue.front()->order, false);
           b = pick(s, L);
           if (b.empty()) {
-            lane_trim(L, 0, true);
+            lane_trim(s, L, 0, true);
             b = pick(s, L);
           }
           s->cv_work.notify_all();
@@ -293,12 +306,16 @@ void lane_main(fmm_server* s, Lane* L) {
     }
     const Clock::time_point t0 = Clock::now();
     for (Req* r : b) r->t_start = t0;
-    const fmm_status st = run_batch(s, L, b);
+    int64_t us[3] = {0, 0, 0};
+    const fmm_status st = run_batch(s, L, b, us);
     const Clock::time_point t1 = Clock::now();
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->busy--;
       s->n_batches++;
+      s->us_copy_in += us[0];
+      s->us_build += us[1];
+      s->us_eval += us[2];
       s->largest_batch = std::max<int64_t>(s->largest_batch, (int64_t)b.size());
       for (Req* r : b) {
         s->inflight -= r->bytes;
@@ -315,8 +332,8 @@ void lane_main(fmm_server* s, Lane* L) {
       // per-tree memory above the budget: this lane gives back what it holds
       int64_t total = tree_bytes(L) + others_charge(s, L);
       s->peak_held = std::max(s->peak_held, total);
-      if (total > s->cfg.hbm_budget_bytes) lane_trim(L, b[0]->order, false);
-      if (tree_bytes(L) + others_charge(s, L) > s->cfg.hbm_budget_bytes) lane_trim(L, 0, true);
+      if (total > s->cfg.hbm_budget_bytes) lane_trim(s, L, b[0]->order, false);
+      if (tree_bytes(L) + others_charge(s, L) > s->cfg.hbm_budget_bytes) lane_trim(s, L, 0, true);
     }
     s->cv_work.notify_all();
     s->cv_done.notify_all();
@@ -460,6 +477,10 @@ fmm_status fmm_server_stats(fmm_server_handle s, int64_t* out) {
   int64_t held = 0;
   for (Lane* L : s->lanes) held += L->held;
   out[7] = held;
+  out[8] = s->us_copy_in;
+  out[9] = s->us_build;
+  out[10] = s->us_eval;
+  out[11] = s->trims;
   return FMM_OK;
 }
 

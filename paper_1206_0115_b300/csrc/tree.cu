@@ -605,6 +605,16 @@ __global__ void k_p2p_items(const int32_t* __restrict__ nleaf_ptr, int64_t cap, 
   items[j] = j < *nleaf_ptr ? (count[j] + 31) >> 5 : 0;
 }
 
+// Leaf of every P2P work item (items[T] .. items[T] + ceil(count/32) - 1
+// belong to leaf T), so that a warp finds its leaf with one load.
+__global__ void k_item_leaf(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
+                            const int32_t* __restrict__ items, int32_t* __restrict__ leaf_of) {
+  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= cap || T >= *nleaf_ptr) return;
+  const int b = items[T], e = b + ((count[T] + 31) >> 5);
+  for (int i = b; i < e; ++i) leaf_of[i] = (int32_t)T;
+}
+
 __global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
                            int32_t* __restrict__ grid, int clear) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1139,6 +1149,8 @@ void release_tree(Ctx* c) {
   c->scratch_cap = 0;
   rel(c->p2p_items, 4 * (size_t)c->p2p_items_cap);
   c->p2p_items_cap = 0;
+  rel(c->p2p_leaf, 4 * (size_t)c->p2p_leaf_cap);
+  c->p2p_leaf_cap = 0;
   c->p2p_nitems = 0;
   rel(c->stage_in, 8 * (size_t)c->stage_in_cap);
   rel(c->stage_out, 8 * (size_t)c->stage_out_cap);
@@ -1237,6 +1249,20 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     c->p2p_items = (int32_t*)p;
     c->p2p_items_cap = cap;
   }
+  {
+    // items: at most one per leaf plus one per 32 particles
+    const int64_t need = ub[Lf] + n / 32 + 2;
+    if (need > c->p2p_leaf_cap) {
+      dfree(c, c->p2p_leaf, 4 * (size_t)c->p2p_leaf_cap);
+      c->p2p_leaf = nullptr;
+      c->p2p_leaf_cap = 0;
+      void* p;
+      const int64_t cap = need + need / 8 + 64;
+      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+      c->p2p_leaf = (int32_t*)p;
+      c->p2p_leaf_cap = cap;
+    }
+  }
 
   if (n > 0 && c->forest) {
     // bounding cube of every problem, then forest keys
@@ -1306,7 +1332,9 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     // P2P items: exclusive offsets per leaf, total in counters[CNT_ITEMS]
     k_p2p_items<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items);
     scan_excl<int32_t>(s, c->p2p_items, ub[Lf], c->counters + CNT_ITEMS, (int32_t*)c->scratch, &c->launches_set);
-    c->launches_set += 1;
+    k_item_leaf<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
+                                                     c->p2p_leaf);
+    c->launches_set += 2;
     if (Lf >= 2) {
       ClassArgs ca;
       for (int l = 0; l < FMM_MAX_LEVELS; ++l) {

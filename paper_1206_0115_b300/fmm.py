@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
 FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FMM_FP64, FMM_MIXED = 0, 1
 FMM_M2L_FULL, FMM_M2L_SVD = 0, 1
-FMM_P2P_VARIANTS = 10
+FMM_P2P_VARIANTS = 12
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
                 -5: "FMM_ERR_TIMEOUT"}
 
@@ -167,8 +167,9 @@ def fmm_evaluate(h, phi, F) -> int:
 
 
 def fmm_autotune(h):
-    """Returns (choice [index, warps, chunk], mean ms of each P2P variant)."""
-    choice = np.zeros(3, dtype=np.int32)
+    """Returns (choice [index, warps, chunk, sources per instruction, unroll],
+    mean ms of each P2P variant)."""
+    choice = np.zeros(5, dtype=np.int32)
     times = np.zeros(FMM_P2P_VARIANTS, dtype=np.float32)
     _check(h, lib.fmm_autotune(h, _ptr(choice), _ptr(times)))
     return choice, times
@@ -283,7 +284,7 @@ def fmm_server_wait(s, ticket: int, timeout_s: float = -1.0) -> np.ndarray:
 
 
 def fmm_server_stats(s) -> np.ndarray:
-    out = np.zeros(8, dtype=np.int64)
+    out = np.zeros(12, dtype=np.int64)
     _check_server(s, lib.fmm_server_stats(s, _ptr(out)))
     return out
 
