@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the request stream")
-    ap.add_argument("--lanes", type=int, default=3, help="serving: concurrent batches")
+    ap.add_argument("--lanes", type=int, default=2, help="serving: concurrent batches")
     ap.add_argument("--ring-gb", type=int, default=8, help="serving: pinned result ring (GB)")
     ap.add_argument("--max-batch-particles", type=int, default=8_000_000, help="serving: particles per batch")
     return ap.parse_args()
@@ -736,7 +736,7 @@ def run_serving(args):
     """Poisson stream of solve requests (mean 200 per second; sizes
     log-uniform in [1e4, 5e6] particles, uniform cube, order 5 or 7 by coin
     flip, height from the size as in the batched workload, capped at 8)
-    through the solve server: 3 lanes, 150 GB admission budget.  Requests
+    through the solve server: 2 lanes, 150 GB admission budget.  Requests
     carry host buffers (inputs pinned, outputs pageable); latency is submit
     to results in host memory."""
     import threading

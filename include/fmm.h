@@ -312,7 +312,9 @@ fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int height, ui
  * A server owns `lanes` worker threads on the current device, each with its
  * own CUDA stream and one resident FMM handle per interpolation order (trees,
  * expansions and operators stay on the device between batches).  A free lane
- * takes the oldest queued request and every later queued request of the same
+ * takes the oldest queued request (or, while that one has waited less than
+ * 50 ms, the oldest request of the order the lane ran last, whose tree it
+ * holds) and every later queued request of the same
  * order that still fits -- at most max_batch_particles particles and
  * max_batch_requests requests per batch, the batch tree's leaf cells within
  * fmm_set_batch's limit, and the device-memory estimate of all batches in

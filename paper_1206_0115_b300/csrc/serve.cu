@@ -53,6 +53,7 @@ struct Lane {
   int64_t held = 0;             // device bytes of the handles + staging (as of the last update)
   int64_t floor = 0;            // what the handles hold with no tree (operators), as of the last full trim
   int64_t est = 0;              // memory estimate of the batch it runs (0 when idle)
+  int last_order = 0;           // order of its last batch (its resident tree)
   bool busy = false;
   bool trimmed = true;          // nothing but operators held since the last full trim
 };
@@ -111,26 +112,43 @@ int64_t others_charge(fmm_server* s, const Lane* self) {
   return c;
 }
 
+// Order affinity: a lane keeps taking requests of the order whose tree it
+// holds (its handle's buffers are already sized, and it does not have to hold
+// trees of two orders) unless the oldest request of another order has waited
+// longer than this.
+constexpr double AFFINITY_MS = 50.0;
+
 // Requests lane L may take now (called with the lock held): the oldest queued
-// request, then later ones of the same order while they fit (particles,
-// requests, leaf cells, and the memory rule: the other lanes' charge plus
-// max(what L holds, the batch's estimate) within the budget).  Returns an
-// empty list when the head does not fit yet.
+// request -- or, by affinity, the oldest of the lane's own order --, then
+// later ones of the same order while they fit (particles, requests, leaf
+// cells, and the memory rule: the other lanes' charge plus max(what L holds,
+// the batch's estimate) within the budget).  Returns an empty list when the
+// chosen head does not fit yet.
 std::vector<Req*> pick(fmm_server* s, Lane* L) {
   std::vector<Req*> b;
   if (s->queue.empty()) return b;
   Req* head = s->queue.front();
+  if (L->last_order != 0 && head->order != L->last_order &&
+      ms_between(head->t_submit, Clock::now()) < AFFINITY_MS) {
+    for (Req* r : s->queue)
+      if (r->order == L->last_order) {
+        head = r;
+        break;
+      }
+  }
   const int64_t others = others_charge(s, L);
   if (others + std::max(tree_bytes(L), head->bytes) > s->cfg.hbm_budget_bytes) return b;
   int64_t parts = 0, bytes = 0, cells = 0;
   const int64_t max_cells = (int64_t)1 << (3 * FMM_MAX_FOREST_LEAF);
+  bool seen_head = false;
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     Req* r = *it;
-    const bool first = b.empty();
-    if (r->order != head->order) {
+    seen_head = seen_head || r == head;
+    if (!seen_head || r->order != head->order) {
       ++it;
       continue;
     }
+    const bool first = b.empty();
     if (!first && ((int)b.size() >= s->cfg.max_batch_requests || parts + r->n > s->cfg.max_batch_particles ||
                    cells + r->cells > max_cells ||
                    others + std::max(tree_bytes(L), bytes + r->bytes) > s->cfg.hbm_budget_bytes)) {
@@ -144,6 +162,7 @@ std::vector<Req*> pick(fmm_server* s, Lane* L) {
     it = s->queue.erase(it);
   }
   L->est = bytes;
+  L->last_order = head->order;
   s->inflight += bytes;
   s->peak_inflight = std::max(s->peak_inflight, others + std::max(tree_bytes(L), bytes));
   return b;

@@ -329,7 +329,11 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uin
   double cx = box[0] + ((double)ix + 0.5) * w;
   double cy = box[1] + ((double)iy + 0.5) * w;
   double cz = box[2] + ((double)iz + 0.5) * w;
-  const double vx = (x - cx) / w, vy = (y - cy) / w, vz = (z - cz) / w;
+  // one FP64 division per particle (FP64 runs at 1/64 of the FP32 rate on
+  // this part); the leaf-frame offsets need ~2^-48 of a leaf width, not the
+  // correctly rounded quotient
+  const double iw = 1.0 / w;
+  const double vx = (x - cx) * iw, vy = (y - cy) * iw, vz = (z - cz) * iw;
   // hi on the grid of multiples of 2^-23 leaf widths: with |hi| <= 1/2, hi
   // plus a neighbour shift of +-1 and the difference of two such values
   // (|.| <= 2) are exact in FP32, which the near field relies on; lo = the
@@ -483,18 +487,17 @@ __global__ void k_fgather(int64_t n, int nprob, const int64_t* __restrict__ psta
   const double qq = q[i];
   int ox, oy, oz;
   demorton3(pb.slot_key >> (3 * pb.L), ox, oy, oz);
-  const double W = box[3], ws = ldexp(1.0, -pb.S);
-  const double tx = __ddiv_rn(__dsub_rn(x, box[0]), W), ty = __ddiv_rn(__dsub_rn(y, box[1]), W),
-               tz = __ddiv_rn(__dsub_rn(z, box[2]), W);
+  const double W = box[3], ws = ldexp(1.0, -pb.S), iW = 1.0 / W;
+  const double tx = (x - box[0]) * iW, ty = (y - box[1]) * iW, tz = (z - box[2]) * iW;
   pos64[r] = make_double4(__dadd_rn((double)ox * ws, __dmul_rn(tx, ws)), __dadd_rn((double)oy * ws, __dmul_rn(ty, ws)),
                           __dadd_rn((double)oz * ws, __dmul_rn(tz, ws)), qq);
   int ix, iy, iz;
   demorton3(skey[r] - pb.slot_key, ix, iy, iz);
-  const double w = ldexp(W, -pb.L);
+  const double w = ldexp(W, -pb.L), iw = ldexp(iW, pb.L);
   const double cx = box[0] + ((double)ix + 0.5) * w;
   const double cy = box[1] + ((double)iy + 0.5) * w;
   const double cz = box[2] + ((double)iz + 0.5) * w;
-  const double vx = (x - cx) / w, vy = (y - cy) / w, vz = (z - cz) / w;
+  const double vx = (x - cx) * iw, vy = (y - cy) * iw, vz = (z - cz) * iw;
   const double Q = 8388608.0, iQ = 1.0 / 8388608.0;
   const double hx = rint(vx * Q) * iQ, hy = rint(vy * Q) * iQ, hz = rint(vz * Q) * iQ;
   pos32[r] = make_float4((float)hx, (float)hy, (float)hz, (float)qq);
