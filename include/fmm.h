@@ -144,6 +144,19 @@ fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const d
 fmm_status fmm_set_batch(fmm_handle h, int32_t nprob, const int64_t* counts, const int32_t* heights,
                          const double* xyz, const double* q);
 
+/* The slot layout fmm_set_batch uses, computed on the host only (no device
+ * needed): problems with particles, sorted by decreasing height (ties in
+ * input order), take consecutive ranges of 8^(height-1) leaf keys of the
+ * batch tree, so every range starts at a multiple of its size and is one
+ * cell of level *leaf_level - (height - 1); *leaf_level is the smallest
+ * level that holds every range and every problem's own leaf level.
+ * slot_key[k] = first leaf key of problem k's slot, slot_level[k] = the
+ * slot cell's level (both -1 for a problem without particles); host arrays
+ * of nprob.  Errors (message from fmm_last_error(NULL)): FMM_ERR_ARG (ranges
+ * as in fmm_set_batch, or more than 8^9 leaf keys in all). */
+fmm_status fmm_batch_plan(int32_t nprob, const int64_t* counts, const int32_t* heights, int64_t* slot_key,
+                          int64_t* slot_level, int32_t* leaf_level);
+
 /* Problem k of the last fmm_set_batch:
  *   info[0] = Morton rank of its first particle in the batch tree (its
  *             particles hold ranks info[0] .. info[0] + info[1] - 1, in the

@@ -489,6 +489,20 @@ fmm_status fmm_set_batch(fmm_handle h, int32_t nprob, const int64_t* counts, con
   return FMM_OK;
 }
 
+fmm_status fmm_batch_plan(int32_t nprob, const int64_t* counts, const int32_t* heights, int64_t* slot_key,
+                          int64_t* slot_level, int32_t* leaf_level) {
+  if (nprob < 1 || nprob > FMM_MAX_BATCH || !counts || !heights || !slot_key || !slot_level || !leaf_level)
+    return set_err(nullptr, FMM_ERR_ARG, "fmm_batch_plan: bad arguments");
+  for (int k = 0; k < nprob; ++k)
+    if (counts[k] < 0 || heights[k] < 1 || heights[k] > FMM_MAX_FOREST_LEAF + 1)
+      return set_err(nullptr, FMM_ERR_ARG, "fmm_batch_plan: count or height of problem %d out of range", k);
+  int Lf = 0;
+  if (batch_plan(nprob, counts, heights, slot_key, slot_level, &Lf) != 0)
+    return set_err(nullptr, FMM_ERR_ARG, "fmm_batch_plan: the leaf cells exceed 8^%d", FMM_MAX_FOREST_LEAF);
+  *leaf_level = Lf;
+  return FMM_OK;
+}
+
 fmm_status fmm_get_batch_info(fmm_handle h, int32_t k, int64_t* info, double* box) {
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;

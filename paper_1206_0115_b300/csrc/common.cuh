@@ -279,6 +279,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q);
 fmm_status ensure_expansions(Ctx* c, int precision);
 // releases every buffer that depends on the tree (the operators stay)
 void release_tree(Ctx* c);
+// slot of every problem of a batch (host only): first leaf key, slot level, batch leaf level; -1 if too big
+int batch_plan(int nprob, const int64_t* counts, const int32_t* heights, int64_t* slot, int64_t* level, int* leaf);
 // slots of a batch (sets c->forest, c->leaf and the device tables); *n_total = sum of counts
 fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total);
 fmm_status operators_init(Ctx* c);

@@ -994,32 +994,55 @@ namespace fmm {
 // Slots of a batch: problems with particles, largest slot first (ties in input
 // order), take consecutive ranges of forest leaf keys; a slot of 8^L keys then
 // starts at a multiple of 8^L, i.e. it is one cell of level Lf - L.  The forest
-// leaf level Lf is the smallest that holds every slot.
-fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total) {
-  std::vector<int64_t> start(nprob + 1, 0);
-  std::vector<BatchProb> prob(nprob);
+// leaf level Lf is the smallest that holds every slot (and at least every
+// problem's own leaf level).  Host only; returns -1 if the slots do not fit
+// in 8^FMM_MAX_FOREST_LEAF keys.
+int batch_plan(int nprob, const int64_t* counts, const int32_t* heights, int64_t* slot, int64_t* level, int* leaf) {
   std::vector<int> order;
   int maxL = 0;
   for (int k = 0; k < nprob; ++k) {
-    start[k + 1] = start[k] + counts[k];
-    prob[k] = BatchProb{0u, heights[k] - 1, 0, 0};
+    slot[k] = -1;
+    level[k] = -1;
     if (counts[k] > 0) {
       order.push_back(k);
       maxL = std::max(maxL, heights[k] - 1);
     }
   }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return prob[a].L > prob[b].L; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return heights[a] > heights[b]; });
   uint64_t off = 0;
   for (int k : order) {
-    prob[k].slot_key = (uint32_t)off;
-    off += (uint64_t)1 << (3 * prob[k].L);
-    if (off > ((uint64_t)1 << (3 * FMM_MAX_FOREST_LEAF)))
-      return set_err(c, FMM_ERR_ARG,
-                     "fmm_set_batch: the problems' leaf cells (sum of 8^(height-1)) exceed 8^%d; split the batch",
-                     FMM_MAX_FOREST_LEAF);
+    slot[k] = (int64_t)off;
+    off += (uint64_t)1 << (3 * (heights[k] - 1));
+    if (off > ((uint64_t)1 << (3 * FMM_MAX_FOREST_LEAF))) return -1;
   }
   int Lf = maxL;
   while (((uint64_t)1 << (3 * Lf)) < off) ++Lf;
+  for (int k : order) level[k] = Lf - (heights[k] - 1);
+  *leaf = Lf;
+  return 0;
+}
+fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t* heights, int64_t* n_total) {
+  std::vector<int64_t> start(nprob + 1, 0);
+  std::vector<BatchProb> prob(nprob);
+  std::vector<int> order;
+  for (int k = 0; k < nprob; ++k) {
+    start[k + 1] = start[k] + counts[k];
+    prob[k] = BatchProb{0u, heights[k] - 1, 0, 0};
+  }
+  int Lf = 0;
+  {
+    std::vector<int64_t> slot(nprob), lev(nprob);
+    if (batch_plan(nprob, counts, heights, slot.data(), lev.data(), &Lf) != 0)
+      return set_err(c, FMM_ERR_ARG,
+                     "fmm_set_batch: the problems' leaf cells (sum of 8^(height-1)) exceed 8^%d; split the batch",
+                     FMM_MAX_FOREST_LEAF);
+    for (int k = 0; k < nprob; ++k)
+      if (counts[k] > 0) {
+        prob[k].slot_key = (uint32_t)slot[k];
+        order.push_back(k);
+      }
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return prob[a].slot_key < prob[b].slot_key; });
+  }
   std::vector<uint32_t> sstart;
   std::vector<int32_t> sprob;
   std::vector<int64_t> first(nprob, 0);

@@ -42,6 +42,7 @@ _SIGS = {
     "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
     "fmm_set_batch": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
     "fmm_get_batch_info": [_vp, C.c_int32, _vp, _vp],
+    "fmm_batch_plan": [C.c_int32, _vp, _vp, _vp, _vp, _vp],
     "fmm_evaluate": [_vp, _vp, _vp],
     "fmm_get_order": [_vp, _vp],
     "fmm_trim": [_vp],
@@ -153,6 +154,17 @@ def fmm_set_batch(h, counts, heights, xyz, q) -> int:
     if counts.shape != heights.shape or counts.ndim != 1:
         raise ValueError("counts and heights must be 1-D arrays of the same length")
     return _check(h, lib.fmm_set_batch(h, len(counts), _ptr(counts), _ptr(heights), _ptr(xyz), _ptr(q)))
+
+
+def fmm_batch_plan(counts, heights):
+    """Host-only slot layout of a batch: (slot_key[k], slot_level[k], leaf level)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    heights = np.ascontiguousarray(heights, dtype=np.int32)
+    key = np.zeros(len(counts), dtype=np.int64)
+    lev = np.zeros(len(counts), dtype=np.int64)
+    leaf = np.zeros(1, dtype=np.int32)
+    _check(None, lib.fmm_batch_plan(len(counts), _ptr(counts), _ptr(heights), _ptr(key), _ptr(lev), _ptr(leaf)))
+    return key, lev, int(leaf[0])
 
 
 def fmm_get_batch_info(h, k: int):

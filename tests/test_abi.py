@@ -4,6 +4,7 @@ touches the device."""
 import ctypes
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1206_0115_b300 import build
@@ -77,3 +78,40 @@ def test_server_config_rejected_before_device_use(F):
         assert F.lib.fmm_server_create(ctypes.byref(cfg), ctypes.byref(s)) == F.FMM_ERR_ARG, bad
     assert F.lib.fmm_server_destroy(None) == F.FMM_OK
     assert F.lib.fmm_server_submit(None, 1, 3, 5, None, None, None, None, None) == F.FMM_ERR_ARG
+
+
+def test_batch_plan_slots_are_aligned_disjoint_cells(F):
+    """The batch layout (host only): every problem with particles owns an
+    aligned, disjoint range of 8^(h-1) leaf keys -- one cell of the batch
+    tree -- larger slots first, the leaf level minimal."""
+    from paper_1206_0115_b300 import inputs
+    rng_counts, rng_heights, _, _ = inputs.batch_workload(nprob=64, nmax=5e4)
+    cases = [
+        (rng_counts, rng_heights),
+        ([5, 0, 7, 1, 9], [3, 4, 1, 6, 3]),
+        ([1], [1]),
+        ([10] * 9, [2] * 9),            # 9 slots of 8 keys: needs a leaf level of 2
+        ([3, 3], [9, 1]),
+        ([3], [10]),                    # one slot of the largest size
+    ]
+    for counts, heights in cases:
+        counts = np.asarray(counts, dtype=np.int64)
+        heights = np.asarray(heights, dtype=np.int32)
+        key, lev, Lf = F.fmm_batch_plan(counts, heights)
+        used = counts > 0
+        assert np.all(key[~used] == -1) and np.all(lev[~used] == -1)
+        size = 8 ** (heights.astype(np.int64) - 1)
+        assert np.all(key[used] % size[used] == 0)                  # aligned: one cell
+        assert np.all(lev[used] == Lf - (heights[used] - 1))
+        spans = sorted((int(key[k]), int(key[k] + size[k])) for k in np.nonzero(used)[0])
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert a1 <= b0                                            # disjoint
+        assert spans[-1][1] <= 8 ** Lf
+        need = max(int(size[used].sum()), int(size[used].max()))
+        assert Lf == 0 or 8 ** (Lf - 1) < need or Lf == int(heights[used].max()) - 1  # minimal
+        order = np.argsort(key[used], kind="stable")
+        assert np.all(np.diff(heights[used][order]) <= 0)             # larger slots first
+    with pytest.raises(F.FMMError):
+        F.fmm_batch_plan([1, 1], [10, 10])                             # 2 x 8^9 keys
+    with pytest.raises(F.FMMError):
+        F.fmm_batch_plan([1], [0])
