@@ -351,7 +351,8 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
-  void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pos64, c->pos32, c->pos32lo, c->p2p_items,
+  void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pleaf, c->pos64, c->pos32, c->pos32lo,
+                  c->p2p_items,
                   c->p2p_leaf,
                   c->near32,
                   c->near64,

@@ -104,6 +104,7 @@ struct fmm_ctx {
   uint32_t *key_a = nullptr, *key_b = nullptr, *idx_a = nullptr, *idx_b = nullptr;
   uint32_t* skey = nullptr;  // sorted keys (points at key_a or key_b)
   int32_t* perm = nullptr;
+  int32_t* pleaf = nullptr;  // leaf of every particle (Morton order)
   double4* pos64 = nullptr;
   float4* pos32 = nullptr;
   float4* pos32lo = nullptr;  // rounding residuals of pos32's coordinates (x = hi + lo to ~2^-48)

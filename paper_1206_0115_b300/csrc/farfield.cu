@@ -272,6 +272,91 @@ k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lb
 
 // ---------------------------------------------------------------- L2P + output
 
+// Far-field potential and field of one particle from its leaf's local
+// expansion Lr (C values; the mixed path's cell mean in Lr[C]) at xi, the
+// particle's position in the leaf's frame; a = the leaf's half-width.
+template <int P, typename T, bool MIXED>
+__device__ __forceinline__ void l2p_eval(const T* __restrict__ Lrow, const T* __restrict__ sC, const T xi[3],
+                                         double a, double& pf, double& gx, double& gy, double& gz) {
+  constexpr int C = P * P * P;
+  T Sx[P], Sy[P], Sz[P], dSx[P], dSy[P], dSz[P];
+  interp_weights<P, T, true>(sC, xi[0], Sx, dSx);
+  interp_weights<P, T, true>(sC, xi[1], Sy, dSy);
+  interp_weights<P, T, true>(sC, xi[2], Sz, dSz);
+  T f = T(0), ax = T(0), ay = T(0), az = T(0);
+  // the x loop stays rolled: unrolling all P^3 terms needs more registers
+  // than occupancy allows
+#pragma unroll 1
+  for (int mx = 0; mx < P; ++mx) {
+#pragma unroll
+    for (int my = 0; my < P; ++my) {
+      const T* Lr = Lrow + (mx * P + my) * P;
+      T sz = T(0), dz = T(0);
+#pragma unroll
+      for (int mz = 0; mz < P; ++mz) {
+        sz += Lr[mz] * Sz[mz];
+        dz += Lr[mz] * dSz[mz];
+      }
+      const T sxy = Sx[mx] * Sy[my];
+      f += sxy * sz;
+      ax += dSx[mx] * Sy[my] * sz;
+      ay += Sx[mx] * dSy[my] * sz;
+      az += sxy * dz;
+    }
+  }
+  pf = (double)f + (MIXED ? (double)Lrow[C] : 0.0);  // mixed: cell mean + deviations
+  gx = -(double)ax / a;
+  gy = -(double)ay / a;
+  gz = -(double)az / a;
+}
+
+// xi of particle r in its leaf's frame
+template <typename T, bool MIXED>
+__device__ __forceinline__ void leaf_xi(int64_t r, const double4* __restrict__ pos64, const float4* __restrict__ pos32,
+                                        const double* ctr, double a, T* xi) {
+  if (MIXED) {
+    const float4 pp = pos32[r];
+    xi[0] = T(2) * pp.x;
+    xi[1] = T(2) * pp.y;
+    xi[2] = T(2) * pp.z;
+  } else {
+    const double4 pp = pos64[r];
+    xi[0] = (T)((pp.x - ctr[0]) / a);
+    xi[1] = (T)((pp.y - ctr[1]) / a);
+    xi[2] = (T)((pp.z - ctr[2]) / a);
+  }
+}
+
+// far + near, scaled to the problem's units, scattered to the caller's order
+template <bool MIXED>
+__device__ __forceinline__ void l2p_store(int64_t r, double pf, double gx, double gy, double gz, double lam,
+                                          const float4* __restrict__ near32, const double4* __restrict__ near64,
+                                          const int32_t* __restrict__ perm, double* __restrict__ phi,
+                                          double* __restrict__ F) {
+  double nphi, nx, ny, nz;
+  if (MIXED) {
+    const float4 nr = near32[r];
+    nphi = nr.x;
+    nx = nr.y;
+    ny = nr.z;
+    nz = nr.w;
+  } else {
+    const double4 nr = near64[r];
+    nphi = nr.x;
+    nx = nr.y;
+    ny = nr.z;
+    nz = nr.w;
+  }
+  const double lam2 = lam * lam;
+  const int64_t i = perm[r];
+  phi[i] = (pf + nphi) * lam;
+  F[3 * i] = (gx + nx) * lam2;
+  F[3 * i + 1] = (gy + ny) * lam2;
+  F[3 * i + 2] = (gz + nz) * lam2;
+}
+
+// One warp per leaf: the leaf's local expansion is staged in shared memory
+// and the lanes take its particles (leaves with many particles).
 template <int P, typename T, bool MIXED>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
 k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const T* __restrict__ cheb,
@@ -299,72 +384,46 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
   cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
   // batched trees: back from the forest cube to the problem's own units
   const int prob = fscale ? lv.slot[leaf][cell] : -1;
-  const double lam = prob >= 0 ? fscale[prob] : 1.0, lam2 = lam * lam;
+  const double lam = prob >= 0 ? fscale[prob] : 1.0;
   for (int r = first + lane; r < first + cnt; r += 32) {
     double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
     if (has_far) {
       T xi[3];
-      if (MIXED) {
-        float4 pp = pos32[r];
-        xi[0] = T(2) * pp.x;
-        xi[1] = T(2) * pp.y;
-        xi[2] = T(2) * pp.z;
-      } else {
-        double4 pp = pos64[r];
-        xi[0] = (T)((pp.x - ctr[0]) / a);
-        xi[1] = (T)((pp.y - ctr[1]) / a);
-        xi[2] = (T)((pp.z - ctr[2]) / a);
-      }
-      T Sx[P], Sy[P], Sz[P], dSx[P], dSy[P], dSz[P];
-      interp_weights<P, T, true>(sC, xi[0], Sx, dSx);
-      interp_weights<P, T, true>(sC, xi[1], Sy, dSy);
-      interp_weights<P, T, true>(sC, xi[2], Sz, dSz);
-      T f = T(0), ax = T(0), ay = T(0), az = T(0);
-      // the x loop stays rolled: unrolling all P^3 terms needs more registers
-      // than occupancy allows
-#pragma unroll 1
-      for (int mx = 0; mx < P; ++mx) {
-#pragma unroll
-        for (int my = 0; my < P; ++my) {
-          const T* Lr = myL + (mx * P + my) * P;
-          T sz = T(0), dz = T(0);
-#pragma unroll
-          for (int mz = 0; mz < P; ++mz) {
-            sz += Lr[mz] * Sz[mz];
-            dz += Lr[mz] * dSz[mz];
-          }
-          const T sxy = Sx[mx] * Sy[my];
-          f += sxy * sz;
-          ax += dSx[mx] * Sy[my] * sz;
-          ay += Sx[mx] * dSy[my] * sz;
-          az += sxy * dz;
-        }
-      }
-      pf = (double)f + (MIXED ? (double)myL[C] : 0.0);  // mixed: cell mean + deviations
-      gx = -(double)ax / a;
-      gy = -(double)ay / a;
-      gz = -(double)az / a;
+      leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
+      l2p_eval<P, T, MIXED>(myL, sC, xi, a, pf, gx, gy, gz);
     }
-    double nphi, nx, ny, nz;
-    if (MIXED) {
-      float4 nr = near32[r];
-      nphi = nr.x;
-      nx = nr.y;
-      ny = nr.z;
-      nz = nr.w;
-    } else {
-      double4 nr = near64[r];
-      nphi = nr.x;
-      nx = nr.y;
-      ny = nr.z;
-      nz = nr.w;
-    }
-    const int64_t i = perm[r];
-    phi[i] = (pf + nphi) * lam;
-    F[3 * i] = (gx + nx) * lam2;
-    F[3 * i + 1] = (gy + ny) * lam2;
-    F[3 * i + 2] = (gz + nz) * lam2;
+    l2p_store<MIXED>(r, pf, gx, gy, gz, lam, near32, near64, perm, phi, F);
   }
+}
+
+// One thread per particle (leaves with few particles, where a warp per leaf
+// would leave most lanes idle): the particle's leaf comes from the per-
+// particle leaf index and its local expansion is read through the L1 cache
+// (neighbouring threads share leaves, so the loads are mostly broadcasts).
+template <int P, typename T, bool MIXED>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+k_l2p_pp(LevelPtrs lv, int leaf, int64_t n, const int32_t* __restrict__ pleaf, const double* __restrict__ box,
+         const T* __restrict__ cheb, int cpad, const T* __restrict__ L, int has_far,
+         const double4* __restrict__ pos64, const float4* __restrict__ pos32, const float4* __restrict__ near32,
+         const double4* __restrict__ near64, const int32_t* __restrict__ perm, double* __restrict__ phi,
+         double* __restrict__ F, const double* __restrict__ fscale) {
+  __shared__ T sC[P * P];
+  for (int i = threadIdx.x; i < P * P; i += 128) sC[i] = cheb[i];
+  __syncthreads();
+  const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (r >= n) return;
+  const int cell = pleaf[r];
+  double ctr[3], a;
+  cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  const int prob = fscale ? lv.slot[leaf][cell] : -1;
+  const double lam = prob >= 0 ? fscale[prob] : 1.0;
+  double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  if (has_far) {
+    T xi[3];
+    leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
+    l2p_eval<P, T, MIXED>(L + (lv.row_off[leaf] + cell) * (int64_t)cpad, sC, xi, a, pf, gx, gy, gz);
+  }
+  l2p_store<MIXED>(r, pf, gx, gy, gz, lam, near32, near64, perm, phi, F);
 }
 
 // ---------------------------------------------------------------- M2L (SIMT)
@@ -527,14 +586,30 @@ fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   const int has_far = Lf >= 2;
   if (nleaf == 0) return FMM_OK;
-  if (c->precision == FMM_MIXED)
-    k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
-        c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
-        c->perm, phi, F, c->forest ? c->fb_scale : nullptr);
-  else
-    k_l2p_out<P, double, false><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(double), s>>>(
-        c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32, c->near64,
-        c->perm, phi, F, c->forest ? c->fb_scale : nullptr);
+  const double* fs = c->forest ? c->fb_scale : nullptr;
+  // a warp per leaf keeps n / (32 x warps) of its lanes busy (one warp per
+  // 32-particle batch of a leaf, as the P2P work items count them); below 60 %
+  // one thread per particle wins
+  const bool pp = c->pleaf && 10 * c->n < 6 * 32 * (int64_t)c->p2p_nitems;
+  if (c->precision == FMM_MIXED) {
+    if (pp)
+      k_l2p_pp<P, float, true><<<ceil_div(c->n, 128), 128, 0, s>>>(
+          c->lv, Lf, c->n, c->pleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32,
+          c->near64, c->perm, phi, F, fs);
+    else
+      k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
+          c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
+          c->perm, phi, F, fs);
+  } else {
+    if (pp)
+      k_l2p_pp<P, double, false><<<ceil_div(c->n, 128), 128, 0, s>>>(
+          c->lv, Lf, c->n, c->pleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32,
+          c->near64, c->perm, phi, F, fs);
+    else
+      k_l2p_out<P, double, false><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(double), s>>>(
+          c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32, c->near64,
+          c->perm, phi, F, fs);
+  }
   return cuda_err(c, cudaGetLastError(), "L2P launch");
 }
 

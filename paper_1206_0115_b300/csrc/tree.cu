@@ -630,53 +630,112 @@ struct ClassArgs {
   int32_t* out[FMM_MAX_LEVELS];
 };
 
-// Groups the cells of levels lmin.. by child class (key & 7), keeping Morton
-// order inside each class; one block per level.
-__global__ void __launch_bounds__(1024)
-k_class_partition(int lmin, int32_t* __restrict__ counters, ClassArgs a) {
-  const int l = lmin + blockIdx.x;
+// Groups the cells of every level l >= 2 by child class (key & 7), keeping
+// Morton order inside each class (the M2L tiles are runs of one class).  The
+// cells of each level go in chunks of CP_CHUNK; (1) per chunk the count
+// of each class, laid out per level as [class][chunk] behind the previous
+// levels; (2) one exclusive scan over all of it; (3) per chunk a stable
+// scatter: a cell's position is its level's class offset + the counts of
+// its class in earlier chunks + its rank among the chunk's cells of its class.
+constexpr int CP_THREADS = 256;
+constexpr int CP_ITEMS = 8;
+constexpr int CP_CHUNK = CP_THREADS * CP_ITEMS;
+
+struct ClassChunks {
+  int lmin, nlev;
+  int blk0[FMM_MAX_LEVELS + 1];  // first block of each level (from lmin), and the total
+  int seg0[FMM_MAX_LEVELS + 1];  // first count of each level in the scanned array, and its length
+};
+
+__device__ inline int cp_level(const ClassChunks& a, int b) {
+  int k = 0;
+  while (k + 1 < a.nlev && a.blk0[k + 1] <= b) ++k;
+  return k;
+}
+
+__global__ void __launch_bounds__(CP_THREADS)
+k_cls_count(ClassChunks a, const int32_t* __restrict__ counters, ClassArgs ca, int32_t* __restrict__ cnt) {
+  const int k = cp_level(a, blockIdx.x), l = a.lmin + k;
+  const int nb = a.blk0[k + 1] - a.blk0[k], bl = blockIdx.x - a.blk0[k];
   const int n = counters[l];
-  const uint32_t* key = a.key[l];
-  const int tid = threadIdx.x;
-  const int per = (n + 1023) / 1024;
-  const int b = min(n, tid * per), e = min(n, b + per);
-  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = b; i < e; ++i) cnt[key[i] & 7]++;
-  __shared__ int s[8][1024];
-  __shared__ int tot[8];
-  __shared__ int cbase[9];
-  for (int c = 0; c < 8; ++c) s[c][tid] = cnt[c];
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  if (warp < 8) {
-    int* row = s[warp];
-    int sum = 0;
-    for (int k = 0; k < 32; ++k) sum += row[lane * 32 + k];
-    int incl = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-      int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    int run = incl - sum;
-    for (int k = 0; k < 32; ++k) {
-      int v = row[lane * 32 + k];
-      row[lane * 32 + k] = run;
-      run += v;
-    }
-    if (lane == 31) tot[warp] = incl;
+  const uint32_t* key = ca.key[l];
+  int c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = threadIdx.x; j < CP_CHUNK; j += CP_THREADS) {
+    const int i = bl * CP_CHUNK + j;
+    if (i < n) c8[key[i] & 7]++;
+  }
+  __shared__ int ws[8][CP_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < 8; ++c) {
+    int v = c8[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) ws[c][w] = v;
   }
   __syncthreads();
-  if (tid == 0) {
-    cbase[0] = 0;
-    for (int c = 0; c < 8; ++c) {
-      cbase[c + 1] = cbase[c] + tot[c];
-      counters[CNT_CLS + 8 * l + c] = tot[c];
+  if (threadIdx.x < 8) {
+    int t = 0;
+    for (int j = 0; j < CP_THREADS / 32; ++j) t += ws[threadIdx.x][j];
+    cnt[a.seg0[k] + threadIdx.x * nb + bl] = t;
+  }
+}
+
+__global__ void __launch_bounds__(CP_THREADS)
+k_cls_scatter(ClassChunks a, int32_t* __restrict__ counters, ClassArgs ca, const int32_t* __restrict__ off) {
+  const int k = cp_level(a, blockIdx.x), l = a.lmin + k;
+  const int nb = a.blk0[k + 1] - a.blk0[k], bl = blockIdx.x - a.blk0[k];
+  const int n = counters[l];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  __shared__ uint8_t scls[CP_CHUNK];
+  __shared__ int pre[8][CP_THREADS];
+  __shared__ int base[8];
+  const uint32_t* key = ca.key[l];
+  for (int j = tid; j < CP_CHUNK; j += CP_THREADS) {
+    const int i = bl * CP_CHUNK + j;
+    scls[j] = i < n ? (uint8_t)(key[i] & 7) : (uint8_t)8;
+  }
+  if (tid < 8) {
+    const int level0 = off[a.seg0[k]];  // the scanned array restarts per level at this value
+    base[tid] = off[a.seg0[k] + tid * nb + bl] - level0;
+    if (bl == 0) {
+      const int end = tid < 7 ? off[a.seg0[k] + (tid + 1) * nb] : off[a.seg0[k + 1]];
+      counters[CNT_CLS + 8 * l + tid] = end - off[a.seg0[k] + tid * nb];
+    }
+  }
+  __syncthreads();
+  int c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < CP_ITEMS; ++j) {
+    const int c = scls[tid * CP_ITEMS + j];
+    if (c < 8) c8[c]++;
+  }
+  for (int c = 0; c < 8; ++c) pre[c][tid] = c8[c];
+  __syncthreads();
+  // warp c scans class c over the threads (8 values per lane)
+  if (w < 8) {
+    int* row = pre[w];
+    int v[CP_THREADS / 32], sum = 0;
+    for (int j = 0; j < CP_THREADS / 32; ++j) {
+      v[j] = row[lane * (CP_THREADS / 32) + j];
+      sum += v[j];
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    int run = incl - sum;
+    for (int j = 0; j < CP_THREADS / 32; ++j) {
+      row[lane * (CP_THREADS / 32) + j] = run;
+      run += v[j];
     }
   }
   __syncthreads();
   int pos[8];
-  for (int c = 0; c < 8; ++c) pos[c] = cbase[c] + s[c][tid];
-  for (int i = b; i < e; ++i) a.out[l][pos[key[i] & 7]++] = i;
+  for (int c = 0; c < 8; ++c) pos[c] = base[c] + pre[c][tid];
+  int32_t* out = ca.out[l];
+  for (int j = 0; j < CP_ITEMS; ++j) {
+    const int c = scls[tid * CP_ITEMS + j];
+    if (c < 8) out[pos[c]++] = bl * CP_CHUNK + tid * CP_ITEMS + j;
+  }
 }
 
 // Per M2L tile: for each of the class's 189 transfer vectors the source cell
@@ -783,6 +842,7 @@ fmm_status ensure_particles(Ctx* c, int64_t n) {
   REALLOC(idx_a, uint32_t, 1)
   REALLOC(idx_b, uint32_t, 1)
   REALLOC(perm, int32_t, 1)
+  REALLOC(pleaf, int32_t, 1)
   REALLOC(pos64, double4, 1)
   REALLOC(pos32, float4, 1)
   REALLOC(pos32lo, float4, 1)
@@ -1164,6 +1224,7 @@ void release_tree(Ctx* c) {
   rel(c->idx_a, 4 * nc);
   rel(c->idx_b, 4 * nc);
   rel(c->perm, 4 * nc);
+  rel(c->pleaf, 4 * nc);
   rel(c->pos64, 32 * nc);
   rel(c->pos32, 16 * nc);
   rel(c->pos32lo, 16 * nc);
@@ -1342,7 +1403,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
                                                 c->pos32lo);
     c->launches_set++;
     // levels
-    FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, nullptr));
+    FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, c->pleaf));
     for (int l = Lf - 1; l >= 0; --l)
       FMM_TRY(unique_level(c, s, c->counters + l + 1, ub[l + 1], c->lv.key[l + 1], 3, l, c->lv.parent[l + 1]));
     for (int l = 0; l <= Lf; ++l) {
@@ -1367,8 +1428,26 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
         ca.key[l] = c->lv.key[l];
         ca.out[l] = c->lv.cls[l];
       }
-      k_class_partition<<<Lf - 1, 1024, 0, s>>>(2, c->counters, ca);
-      c->launches_set++;
+      // chunked partition (levels 2 .. Lf; sized by the cells' upper bounds)
+      ClassChunks cc;
+      cc.lmin = 2;
+      cc.nlev = Lf - 1;
+      cc.blk0[0] = 0;
+      cc.seg0[0] = 0;
+      for (int k = 0; k < cc.nlev; ++k) {
+        const int nb = ceil_div(ub[2 + k] > 0 ? ub[2 + k] : 1, CP_CHUNK);
+        cc.blk0[k + 1] = cc.blk0[k] + nb;
+        cc.seg0[k + 1] = cc.seg0[k] + 8 * nb;
+      }
+      const int64_t nseg = cc.seg0[cc.nlev];
+      // counts + 1 trailing zero (its exclusive prefix is the grand total), then the scan's block sums
+      int32_t* cnt = (int32_t*)c->scratch + 64;
+      int32_t* work = cnt + nseg + 1;
+      FMM_CUDA(c, cudaMemsetAsync(cnt + nseg, 0, sizeof(int32_t), s));
+      k_cls_count<<<cc.blk0[cc.nlev], CP_THREADS, 0, s>>>(cc, c->counters, ca, cnt);
+      scan_excl<int32_t>(s, cnt, nseg + 1, nullptr, work, &c->launches_set);
+      k_cls_scatter<<<cc.blk0[cc.nlev], CP_THREADS, 0, s>>>(cc, c->counters, ca, cnt);
+      c->launches_set += 2;
     }
     FMM_CUDA(c, cudaGetLastError());
   }
