@@ -169,8 +169,12 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   FMM_TRY(launch_upward(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
   FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
+  c->p2p_after_proj = false;
   FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
-  FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  // the P2P branch starts with the persistent expansion kernel, so that its
+  // blocks fill the room beside the expansion's CTAs instead of holding the
+  // SMs the persistent kernels need (see launch_m2l_svd_tc)
+  FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->p2p_after_proj ? c->ev_p2p : c->ev_fork, 0));
   if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], ps, cudaEventRecordExternal));
   if (c->timing != 2) FMM_TRY(launch_p2p(c, ps));
   if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], ps, cudaEventRecordExternal));
@@ -249,16 +253,31 @@ fmm_status build_graph(Ctx* c) {
   }
   FMM_CUDA(c, e);
   c->graph = g;
-  FMM_CUDA(c, cudaGraphInstantiate(&c->gexec, g, 0));
   size_t nn = 0;
   FMM_CUDA(c, cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
   FMM_CUDA(c, cudaGraphGetNodes(g, nodes.data(), &nn));
+  // Launch priorities: the near field (P2P, FP32 pipe) gets the lowest, every
+  // other kernel the highest, so that the persistent tensor-core M2L kernels
+  // take their one CTA per SM as soon as the P2P branch (started first)
+  // frees room, and P2P blocks then run in the room left beside them.
+  int prio_low = 0, prio_high = 0;
+  FMM_CUDA(c, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   int64_t kernels = 0;
   for (auto nd : nodes) {
     cudaGraphNodeType t;
-    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    ++kernels;
+    cudaKernelNodeParams kp;
+    if (c->p2p_priority && cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess) {
+      cudaKernelNodeAttrValue v;
+      memset(&v, 0, sizeof(v));
+      v.priority = is_p2p_kernel(kp.func) ? prio_low : prio_high;
+      FMM_CUDA(c, cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
+    }
   }
+  cudaGetLastError();
+  FMM_CUDA(c, cudaGraphInstantiate(&c->gexec, g, 0));
   c->launches_eval = kernels + 1;  // + the L2P/output launch
   c->graph_sig = graph_signature(c);
   c->graph_ok = true;
@@ -297,6 +316,9 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   {
     const char* e = getenv("FMM_M2L_KERNEL");  // "simt": CUDA-core M2L in mixed precision too
     c->use_tc = !(e && strcmp(e, "simt") == 0);
+    const char* pr = getenv("FMM_P2P_PRIORITY");  // "0": every graph node at the default priority
+    c->p2p_priority = !(pr && strcmp(pr, "0") == 0);
+    if (c->p2p_priority) p2p_carveout();
   }
   fmm_status st = FMM_OK;
   auto fail = [&](fmm_status s) {
@@ -307,7 +329,8 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_p2p, cudaEventDisableTiming) != cudaSuccess) {
     cuda_err(c, cudaGetLastError(), "fmm_create: stream/event creation");
     return fail(FMM_ERR_CUDA);
   }
@@ -381,6 +404,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_p2p) cudaEventDestroy(c->ev_p2p);
   for (int k = 0; k < 14; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   delete c;

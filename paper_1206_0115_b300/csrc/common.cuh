@@ -96,6 +96,8 @@ struct fmm_ctx {
   cudaStream_t side = nullptr;    // P2P branch
   cudaStream_t cap = nullptr;     // graph capture
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_p2p = nullptr;  // where the P2P branch starts (after the compressed M2L projection)
+  bool p2p_after_proj = false;   // ev_p2p was recorded by the M2L launch
   char err[512] = {0};
 
   // particles
@@ -190,6 +192,7 @@ struct fmm_ctx {
   bool graph_ok = false;
   int graph_precision = -1;
   bool use_graph = true;
+  bool p2p_priority = true;  // P2P graph nodes at the low launch priority (the rest high)
   int timing = 0;  // 0 off, 1 events in the overlapped schedule, 2 events with P2P run alone
   cudaEvent_t tev[14] = {nullptr};  // [9..12]: around the tensor-core M2L kernels
   bool tev_recorded = false;
@@ -287,6 +290,8 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
 fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
+bool is_p2p_kernel(const void* func);
+void p2p_carveout();
 extern const int kP2PVariants[FMM_P2P_VARIANTS][4];
 fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);

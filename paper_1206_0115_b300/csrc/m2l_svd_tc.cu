@@ -866,6 +866,13 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
   const int ue = c->ntiles * e.nh * EX_GROUPS;
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
+  // the P2P branch is released here: its blocks and the expansion's CTAs
+  // become ready together and the expansion's (higher launch priority) are
+  // placed first, one per SM, with P2P blocks in the room beside them
+  if (c->timing != 2 && c->p2p_priority) {
+    FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
+    c->p2p_after_proj = true;
+  }
   k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));

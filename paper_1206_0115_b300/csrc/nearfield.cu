@@ -30,6 +30,8 @@
 // the particle itself (or a coincident one), so only they need the r > 0
 // test; a pair at distance 0 contributes nothing.
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fmm {
@@ -527,6 +529,37 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, co
 const int kP2PVariants[FMM_P2P_VARIANTS][4] = {{8, 128, 2, 4}, {4, 128, 2, 4}, {4, 256, 2, 2}, {4, 128, 2, 2},
                                                {8, 128, 2, 2}, {8, 256, 2, 2}, {4, 256, 1, 4}, {2, 128, 1, 4},
                                                {2, 256, 1, 4}, {4, 128, 1, 4}, {8, 128, 1, 4}, {8, 256, 1, 4}};
+
+// Whether a kernel is one of the P2P kernels (graph nodes of the near field
+// get the low launch priority, see build_graph).
+bool is_p2p_kernel(const void* f) {
+  const void* ks[] = {(const void*)k_p2p32<4, 256>,      (const void*)k_p2p32<2, 128>,
+                      (const void*)k_p2p32<2, 256>,      (const void*)k_p2p32<4, 128>,
+                      (const void*)k_p2p32<8, 128>,      (const void*)k_p2p32<8, 256>,
+                      (const void*)k_p2p32x2<8, 128, 4>, (const void*)k_p2p32x2<4, 128, 4>,
+                      (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
+                      (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
+                      (const void*)k_p2p64};
+  for (const void* k : ks)
+    if (k == f) return true;
+  return false;
+}
+
+// The P2P kernels prefer the largest shared-memory carveout, so that their
+// blocks can join an SM configured for a persistent tensor-core M2L CTA.
+void p2p_carveout() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const void* ks[] = {(const void*)k_p2p32<4, 256>,      (const void*)k_p2p32<2, 128>,
+                        (const void*)k_p2p32<2, 256>,      (const void*)k_p2p32<4, 128>,
+                        (const void*)k_p2p32<8, 128>,      (const void*)k_p2p32<8, 256>,
+                        (const void*)k_p2p32x2<8, 128, 4>, (const void*)k_p2p32x2<4, 128, 4>,
+                        (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
+                        (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>};
+    for (const void* k : ks) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaGetLastError();
+  });
+}
 
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
