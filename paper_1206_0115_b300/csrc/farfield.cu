@@ -142,6 +142,85 @@ k_p2m(LevelPtrs lv, int leaf, const double* __restrict__ box, const T* __restric
   }
 }
 
+// Four leaves per block, a warp each (trees whose leaves hold a few
+// particles, where a block per leaf would be mostly idle): the lanes compute
+// the interpolation weights of up to 32 particles at a time, then each lane
+// accumulates the coefficients m = lane, lane + 32, ...
+template <int P, typename T, bool MIXED>
+__global__ void __launch_bounds__(128)
+k_p2m_warp(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const T* __restrict__ cheb, int cpad,
+           const double4* __restrict__ pos64, const float4* __restrict__ pos32, T* __restrict__ Mout,
+           T* __restrict__ Mlo) {
+  constexpr int C = P * P * P, NPER = (C + 31) / 32;
+  __shared__ T sS[4][32][3][P];
+  __shared__ T sq[4][32];
+  __shared__ T sC[P * P];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < P * P; i += 128) sC[i] = cheb[i];
+  __syncthreads();
+  const int cell = blockIdx.x * 4 + warp;
+  if (cell >= nleaf) return;
+  const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
+  double ctr[3], a = 1.0;
+  if (!MIXED) cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  T acc[NPER];
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) acc[k] = T(0);
+  for (int b0 = 0; b0 < cnt; b0 += 32) {
+    const int nb = min(32, cnt - b0);
+    if (lane < nb) {
+      T xi[3], qq;
+      if (MIXED) {
+        const float4 pp = pos32[first + b0 + lane];
+        xi[0] = T(2) * pp.x;
+        xi[1] = T(2) * pp.y;
+        xi[2] = T(2) * pp.z;
+        qq = pp.w;
+      } else {
+        const double4 pp = pos64[first + b0 + lane];
+        xi[0] = (T)((pp.x - ctr[0]) / a);
+        xi[1] = (T)((pp.y - ctr[1]) / a);
+        xi[2] = (T)((pp.z - ctr[2]) / a);
+        qq = (T)pp.w;
+      }
+      for (int d = 0; d < 3; ++d) {
+        T S[P];
+        interp_weights<P, T, false>(sC, xi[d], S, nullptr);
+#pragma unroll
+        for (int m = 0; m < P; ++m) sS[warp][lane][d][m] = S[m];
+      }
+      sq[warp][lane] = qq;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < NPER; ++k) {
+      const int m = lane + 32 * k;
+      if (m < C) {
+        const int mx = m / (P * P), my = (m / P) % P, mz = m % P;
+        T s = acc[k];
+        for (int j = 0; j < nb; ++j)
+          s += sq[warp][j] * sS[warp][j][0][mx] * sS[warp][j][1][my] * sS[warp][j][2][mz];
+        acc[k] = s;
+      }
+    }
+    __syncwarp();
+  }
+  const int64_t row = lv.row_off[leaf] + cell;
+#pragma unroll
+  for (int k = 0; k < NPER; ++k) {
+    const int m = lane + 32 * k;
+    if (m < C) {
+      if (MIXED) {
+        const float hi = tf32_rna((float)acc[k]);
+        Mout[row * cpad + m] = hi;
+        Mlo[row * cpad + m] = tf32_rna((float)acc[k] - hi);
+      } else {
+        Mout[row * cpad + m] = acc[k];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- M2M
 
 template <int P, typename T, bool MIXED>
@@ -554,15 +633,26 @@ __global__ void k_rows_to_f64(int64_t nrows, int64_t row0, int C, int cpad, cons
 template <int P>
 fmm_status upward_p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf;
+  // leaves of a few particles (the same lane-utilisation rule as L2P): a warp per leaf
+  const int nleaf = c->lv.ncell[Lf];
+  const bool small = 10 * c->n < 6 * 32 * (int64_t)c->p2p_nitems;
   if (c->precision == FMM_MIXED) {
-    k_p2m<P, float, true><<<c->lv.ncell[Lf], 128, 0, s>>>(c->lv, Lf, c->box, c->cheb32, c->cpad, c->pos64,
-                                                          c->pos32, c->Mhi, c->Mlo);
+    if (small)
+      k_p2m_warp<P, float, true><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad,
+                                                                    c->pos64, c->pos32, c->Mhi, c->Mlo);
+    else
+      k_p2m<P, float, true><<<nleaf, 128, 0, s>>>(c->lv, Lf, c->box, c->cheb32, c->cpad, c->pos64, c->pos32, c->Mhi,
+                                                  c->Mlo);
     for (int l = Lf - 1; l >= 2; --l)
       k_m2m<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo, c->Mhi,
                                                            c->Mlo);
   } else {
-    k_p2m<P, double, false><<<c->lv.ncell[Lf], 128, 0, s>>>(c->lv, Lf, c->box, c->cheb64, c->cpad, c->pos64,
-                                                            c->pos32, c->M64, nullptr);
+    if (small)
+      k_p2m_warp<P, double, false><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad,
+                                                                      c->pos64, c->pos32, c->M64, nullptr);
+    else
+      k_p2m<P, double, false><<<nleaf, 128, 0, s>>>(c->lv, Lf, c->box, c->cheb64, c->cpad, c->pos64, c->pos32,
+                                                    c->M64, nullptr);
     for (int l = Lf - 1; l >= 2; --l)
       k_m2m<P, double, false><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m64, c->cpad, c->M64, nullptr,
                                                              c->M64, nullptr);
