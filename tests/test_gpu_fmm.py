@@ -110,8 +110,27 @@ def _dup_faces():
     return xyz, q
 
 
+def _near_faces():
+    """Coordinates a few ulps either side of leaf faces of a box that is not a
+    power of two wide (lo = -0.3, W = 1.7): the quotient (x - lo) / W and its
+    product with the reciprocal can round to opposite sides of a face."""
+    rng = np.random.default_rng(41)
+    lo, W, L = -0.3, 1.7, 6
+    faces = lo + np.arange(1, 2 ** L) * (W / 2 ** L)
+    pick = faces[rng.integers(0, len(faces), size=(6000, 3))]
+    steps = rng.integers(-6, 7, size=pick.shape)
+    xyz = np.nextafter(pick, np.where(steps >= 0, np.inf, -np.inf))
+    for _ in range(6):                      # up to six ulps away
+        more = np.abs(steps) > 1
+        xyz = np.where(more, np.nextafter(xyz, np.where(steps >= 0, np.inf, -np.inf)), xyz)
+        steps = np.where(more, steps - np.sign(steps), steps)
+    xyz = np.vstack([xyz, [[lo, lo, lo], [lo + W, lo, lo]]])   # fixes the root cube
+    return np.ascontiguousarray(xyz), np.ones(len(xyz))
+
+
 @pytest.mark.parametrize("name,make,h", TREE_CASES + [("golden_faces", _golden_points, 4),
                                                      ("duplicates_faces", _dup_faces, 4),
+                                                     ("near_faces_h7", _near_faces, 7),
                                                      ("h1", lambda: inputs.particles(300, 5, "cube", "pos"), 1),
                                                      ("h2", lambda: inputs.particles(300, 5, "cube", "pos"), 2)])
 def test_tree_bit_exact(F, name, make, h):
