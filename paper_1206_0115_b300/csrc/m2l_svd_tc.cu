@@ -23,7 +23,7 @@
 //   by linear bulk copies of pre-swizzled slabs, ry_t / 16 pipeline stages
 //   per t.  The tensor cores' FP32
 //   accumulation does not round to nearest, so an accumulator takes at most
-//   EX_TPA transfer vectors (a chain no longer than that of one full-rank
+//   tpa transfer vectors (a chain no longer than that of one full-rank
 //   operator) before the epilogue adds it into FP32 running sums in shared
 //   memory; k_m2l_tc_reduce adds a tile's group slices in FP64 and scales by
 //   1/a.
@@ -399,7 +399,9 @@ constexpr int EX_MMA = EX_EPI + 4;
 constexpr int EX_THREADS = 32 * (EX_MMA + 1);
 constexpr int EX_GT = 64;    // transfer vectors per work unit
 constexpr int EX_GROUPS = (FMM_NT_CLASS + EX_GT - 1) / EX_GT;
-constexpr int EX_TPA = 4;    // transfer vectors per accumulator before it is drained
+// transfer vectors per accumulator before it is drained (ExpArgs::tpa): as
+// many as keep the accumulation chain within one full-rank operator's
+// (order^3 products), at least 4, at most 16
 
 struct ExpArgs {
   const int32_t* tile_nact;
@@ -411,7 +413,7 @@ struct ExpArgs {
   float* partial;  // [group][tile][128][cpad]
   int32_t* err;
   int64_t YS;
-  int ntiles, cpad, nh, nhalf, nst;
+  int ntiles, cpad, nh, nhalf, nst, tpa;
   uint32_t acol, tmem_cols;
 };
 
@@ -597,8 +599,8 @@ k_svd_expand_tc(ExpArgs a) {
       const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
       const int kA = a0 + lane < a1 ? a.ekch[tb + a0 + lane] : 0;
       const int kB = a0 + 32 + lane < a1 ? a.ekch[tb + a0 + 32 + lane] : 0;
-      for (int ag = a0; ag < a1 && ok; ag += EX_TPA, ++tt) {
-        const int ae = min(a1, ag + EX_TPA);
+      for (int ag = a0; ag < a1 && ok; ag += a.tpa, ++tt) {
+        const int ae = min(a1, ag + a.tpa);
         const int b = (int)(tt & 1u);
         if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag)) {
           ok = false;
@@ -661,7 +663,7 @@ k_svd_expand_tc(ExpArgs a) {
       const int nact = a.tile_nact[tile];
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
-      for (int ag = a0; ag < a1; ag += EX_TPA, ++tt) {
+      for (int ag = a0; ag < a1; ag += a.tpa, ++tt) {
         const int b = (int)(tt & 1u);
         if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag)) {
           ok = false;
@@ -861,6 +863,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.nhalf = ex_nhalf(cp);
   e.nh = cp / e.nhalf;
   e.nst = c->svd_tc_nst;
+  e.tpa = std::max(4, std::min(16, c->ncoef / std::max(16, Rp)));
   e.acol = (uint32_t)(2 * e.nhalf);
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
