@@ -39,7 +39,7 @@ extern "C" {
 
 typedef struct fmm_ctx* fmm_handle;
 
-#define FMM_P2P_VARIANTS 12 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+#define FMM_P2P_VARIANTS 14 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
 
 typedef enum {
   FMM_OK = 0,
@@ -194,7 +194,10 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * chunk, unroll of the pair loop) = (8,128,4) -- the default --, (4,128,4),
  * (4,256,2), (4,128,2), (8,128,2), (8,256,2); variants 6..11: one source per
  * instruction, (warps, chunk) = (4,256), (2,128), (2,256), (4,128), (8,128),
- * (8,256).  They give the same sums up to the grouping of FP32 partial sums.
+ * (8,256); variants 12, 13: packed, leaf-cooperative (a block of 8 warps
+ * takes up to 8 work items of one leaf and stages each chunk of their common
+ * sources once), chunks of 512 and 1024 sources.  They give the same sums up
+ * to the grouping of FP32 partial sums.
  * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
  * FMM_P2P_VARIANTS mean launch times.  Synchronises the

@@ -190,7 +190,8 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
 std::vector<int64_t> graph_signature(const Ctx* c) {
   std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
-                            (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf};
+                            (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
+                            (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -376,7 +377,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   drop_graph(c);
   void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pleaf, c->pos64, c->pos32, c->pos32lo,
                   c->p2p_items,
-                  c->p2p_leaf,
+                  c->p2p_leaf, c->p2p_units, c->p2p_uoff,
                   c->near32,
                   c->near64,
                   c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,

@@ -115,6 +115,10 @@ struct fmm_ctx {
   int64_t p2p_items_cap = 0;
   int32_t* p2p_leaf = nullptr;   // per work item: its leaf
   int64_t p2p_leaf_cap = 0;
+  int32_t* p2p_units = nullptr;  // cooperative P2P units: first item of each (up to 8 items of a leaf)
+  int32_t* p2p_uoff = nullptr;   // per leaf: its first unit
+  int64_t p2p_units_cap = 0;
+  int p2p_nunits = 0;
   int p2p_nitems = 0;
   int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants)
   double4* near64 = nullptr;

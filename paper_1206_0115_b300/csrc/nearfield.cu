@@ -432,6 +432,150 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
   }
 }
 
+// Leaf-cooperative packed kernel, for leaves of many particles: a block of
+// 8 warps takes a unit of up to 8 consecutive work items of one leaf (their
+// targets share the 27-leaf source list), stages each chunk of sources once
+// for all of them, and every warp sums its own 32 targets against it.  A
+// leaf's sources are staged once per unit instead of once per item.
+constexpr int CW = 8;  // warps per block = items per unit
+
+template <int CH, int U>
+__global__ void __launch_bounds__(CW * 32)
+k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+           const int32_t* __restrict__ units, int nunits, const float4* __restrict__ pos32,
+           const float4* __restrict__ pos32lo, const double* __restrict__ box, float4* __restrict__ out) {
+  constexpr int NP = CH / 2;
+  __shared__ ulonglong2 sA[NP];
+  __shared__ ulonglong2 sB[NP];
+  __shared__ ulonglong2 sC[NP];
+  __shared__ f2_t sD[NP];
+  __shared__ int nb_first[27];
+  __shared__ int nb_pre[28];
+  __shared__ int8_t nb_off[27][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  if ((int)blockIdx.x >= nunits) return;
+  const int item0 = units[blockIdx.x];
+  const int T = leaf_of[item0];
+  const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int nit = (tc + 31) >> 5;                        // the leaf's items
+  const int item = item0 + warp;
+  const bool active = item - items[T] < nit;             // this warp has an item
+  const int tb = (item - items[T]) * 32;
+  if (warp == 0) {
+    int ix, iy, iz;
+    demorton3(lv.key[leaf][T], ix, iy, iz);
+    const int top = (1 << leaf) - 1;
+    const int mine = problem_of(lv, leaf, T);
+    int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
+    if (lane < 27) {
+      const int k = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+      ox = k / 9 - 1;
+      oy = (k / 3) % 3 - 1;
+      oz = k % 3 - 1;
+      const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
+      if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
+        const int g = lv.grid[leaf][morton3(sx, sy, sz)];
+        if (g >= 0 && same_problem(lv, leaf, mine, g)) {
+          nf = lv.first[leaf][g];
+          ncnt = lv.count[leaf][g];
+        }
+      }
+    }
+    int incl = ncnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane < 27) {
+      nb_first[lane] = nf;
+      nb_pre[lane] = incl - ncnt;
+      nb_off[lane][0] = (int8_t)ox;
+      nb_off[lane][1] = (int8_t)oy;
+      nb_off[lane][2] = (int8_t)oz;
+    }
+    if (lane == 31) nb_pre[27] = incl;
+  }
+  __syncthreads();
+  const int total = nb_pre[27];
+  const int own = tc;
+  const int nt = active ? min(32, tc - tb) : 1;
+  int lg = 0;
+  while ((nt << (lg + 1)) <= 32) ++lg;
+  const int g = 1 << lg, ti = lane >> lg, sub = lane & (g - 1);
+  const bool tvalid = active && ti < nt;
+  float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+  if (tvalid) {
+    th = pos32[tf + tb + ti];
+    tl = pos32lo[tf + tb + ti];
+  }
+  const f2_t TX = f2pack(th.x, th.x), TY = f2pack(th.y, th.y), TZ = f2pack(th.z, th.z);
+  const f2_t LX = f2pack(tl.x, tl.x), LY = f2pack(tl.y, tl.y), LZ = f2pack(tl.z, tl.z);
+  Kahan kp, kx, ky, kz;
+  auto fetch = [&](int s, float4& ph, float4& pl) {
+    int lo = 0, hi = 26;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (nb_pre[mid] <= s) lo = mid;
+      else hi = mid - 1;
+    }
+    const int j = nb_first[lo] + (s - nb_pre[lo]);
+    ph = pos32[j];
+    ph.x += (float)nb_off[lo][0];
+    ph.y += (float)nb_off[lo][1];
+    ph.z += (float)nb_off[lo][2];
+    pl = pos32lo[j];
+  };
+  for (int c0 = 0; c0 < total; c0 += CH) {
+    const int cn = min(CH, total - c0);
+    const int np = (cn + 1) >> 1;
+    __syncthreads();  // the previous chunk is no longer read
+    for (int m = tid; m < np; m += CW * 32) {
+      float4 h0, l0, h1, l1;
+      fetch(c0 + 2 * m, h0, l0);
+      if (2 * m + 1 < cn) {
+        fetch(c0 + 2 * m + 1, h1, l1);
+      } else {  // padding: no charge, far from every target
+        h1 = make_float4(64.f, 64.f, 64.f, 0.f);
+        l1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      sA[m] = make_ulonglong2(f2pack(h0.x, h1.x), f2pack(h0.y, h1.y));
+      sB[m] = make_ulonglong2(f2pack(h0.z, h1.z), f2pack(h0.w, h1.w));
+      sC[m] = make_ulonglong2(f2pack(l0.x, l1.x), f2pack(l0.y, l1.y));
+      sD[m] = f2pack(l0.z, l1.z);
+    }
+    __syncthreads();
+    if (!active) continue;
+    PairAcc acc{0ull, 0ull, 0ull, 0ull};
+    const int kown = min(cn, max(0, own - c0));
+    const int jown = (kown + 1) >> 1;
+    switch (g) {
+      case 1: p2p_pair_chunk<1, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 2: p2p_pair_chunk<2, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 4: p2p_pair_chunk<4, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 8: p2p_pair_chunk<8, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 16: p2p_pair_chunk<16, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      default: p2p_pair_chunk<32, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+    }
+    const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
+    kp.add(ph.x + ph.y);
+    kx.add(px.x + px.y);
+    ky.add(py.x + py.y);
+    kz.add(pz.x + pz.y);
+  }
+  if (!active) return;
+  float aphi = kp.s, ax = kx.s, ay = ky.s, az = kz.s;
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+  if (tvalid && sub == 0) {
+    const float s1 = (float)(1.0 / ldexp(box[3], -leaf)), s2 = s1 * s1;
+    out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
+  }
+}
+
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
 k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
@@ -526,9 +670,11 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, co
 // variants 6.. are the packed-pair kernel (k_p2p32x2) in the same shapes
 // (warps, chunk, sources per instruction, unroll of the pair loop); index 0
 // is the default (the packed kernel, fastest on every workload measured)
+// 12, 13: the leaf-cooperative packed kernel (8 warps share each staged chunk)
 const int kP2PVariants[FMM_P2P_VARIANTS][4] = {{8, 128, 2, 4}, {4, 128, 2, 4}, {4, 256, 2, 2}, {4, 128, 2, 2},
                                                {8, 128, 2, 2}, {8, 256, 2, 2}, {4, 256, 1, 4}, {2, 128, 1, 4},
-                                               {2, 256, 1, 4}, {4, 128, 1, 4}, {8, 128, 1, 4}, {8, 256, 1, 4}};
+                                               {2, 256, 1, 4}, {4, 128, 1, 4}, {8, 128, 1, 4}, {8, 256, 1, 4},
+                                               {8, 512, 2, 4}, {8, 1024, 2, 4}};
 
 // Whether a kernel is one of the P2P kernels (graph nodes of the near field
 // get the low launch priority, see build_graph).
@@ -539,6 +685,7 @@ bool is_p2p_kernel(const void* f) {
                       (const void*)k_p2p32x2<8, 128, 4>, (const void*)k_p2p32x2<4, 128, 4>,
                       (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                       (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
+                      (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
                       (const void*)k_p2p64};
   for (const void* k : ks)
     if (k == f) return true;
@@ -555,7 +702,8 @@ void p2p_carveout() {
                         (const void*)k_p2p32<8, 128>,      (const void*)k_p2p32<8, 256>,
                         (const void*)k_p2p32x2<8, 128, 4>, (const void*)k_p2p32x2<4, 128, 4>,
                         (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
-                        (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>};
+                        (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
+                        (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>};
     for (const void* k : ks) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaGetLastError();
   });
@@ -584,6 +732,16 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
       case 9: P2P_LAUNCH(4, 128); break;
       case 10: P2P_LAUNCH(8, 128); break;
       case 11: P2P_LAUNCH(8, 256); break;
+      case 12:
+        if (c->p2p_nunits > 0)
+          k_p2p32x2c<512, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+                                                              c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
+        break;
+      case 13:
+        if (c->p2p_nunits > 0)
+          k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+                                                               c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
+        break;
       default: P2P_LAUNCH2(8, 128, 4); break;
     }
 #undef P2P_LAUNCH

@@ -29,6 +29,7 @@ constexpr int U_CHUNK = U_THREADS * U_ITEMS;
 constexpr int CNT_BAD = 127;  // counters[] slot of the non-finite-input flag
 constexpr int CNT_CLS = 16;   // counters[16 + 8 l + c] = cells of class c at level l
 constexpr int CNT_ITEMS = 120;  // counters[120] = P2P work items (leaf, 32-target batch)
+constexpr int CNT_UNITS = 121;  // counters[121] = cooperative P2P units (up to 8 items of one leaf)
 
 __device__ inline double warp_min(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -616,6 +617,25 @@ __global__ void k_item_leaf(const int32_t* __restrict__ nleaf_ptr, int64_t cap, 
   if (T >= cap || T >= *nleaf_ptr) return;
   const int b = items[T], e = b + ((count[T] + 31) >> 5);
   for (int i = b; i < e; ++i) leaf_of[i] = (int32_t)T;
+}
+
+// Cooperative P2P units: up to P2P_UNIT consecutive work items of one leaf.
+// uoff[T] = units of leaf T (scanned afterwards); units[u] = first item of u.
+constexpr int P2P_UNIT = 8;
+__global__ void k_unit_count(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
+                             int32_t* __restrict__ uoff) {
+  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= cap) return;
+  const int ni = T < *nleaf_ptr ? (count[T] + 31) >> 5 : 0;
+  uoff[T] = (ni + P2P_UNIT - 1) / P2P_UNIT;
+}
+__global__ void k_unit_write(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
+                             const int32_t* __restrict__ items, const int32_t* __restrict__ uoff,
+                             int32_t* __restrict__ units) {
+  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= cap || T >= *nleaf_ptr) return;
+  const int ni = (count[T] + 31) >> 5;
+  for (int k = 0; k * P2P_UNIT < ni; ++k) units[uoff[T] + k] = items[T] + k * P2P_UNIT;
 }
 
 __global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
@@ -1238,6 +1258,10 @@ void release_tree(Ctx* c) {
   c->p2p_items_cap = 0;
   rel(c->p2p_leaf, 4 * (size_t)c->p2p_leaf_cap);
   c->p2p_leaf_cap = 0;
+  rel(c->p2p_units, 4 * (size_t)c->p2p_units_cap);
+  rel(c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
+  c->p2p_units_cap = 0;
+  c->p2p_nunits = 0;
   c->p2p_nitems = 0;
   rel(c->stage_in, 8 * (size_t)c->stage_in_cap);
   rel(c->stage_out, 8 * (size_t)c->stage_out_cap);
@@ -1349,6 +1373,20 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       c->p2p_leaf = (int32_t*)p;
       c->p2p_leaf_cap = cap;
     }
+    // units: at most one per leaf plus one per 8 items; offsets: one per leaf
+    if (need > c->p2p_units_cap) {
+      dfree(c, c->p2p_units, 4 * (size_t)c->p2p_units_cap);
+      dfree(c, c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
+      c->p2p_units = c->p2p_uoff = nullptr;
+      c->p2p_units_cap = 0;
+      void* p;
+      const int64_t cap = need + need / 8 + 64;
+      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+      c->p2p_units = (int32_t*)p;
+      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+      c->p2p_uoff = (int32_t*)p;
+      c->p2p_units_cap = cap;
+    }
   }
 
   if (n > 0 && c->forest) {
@@ -1421,7 +1459,11 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     scan_excl<int32_t>(s, c->p2p_items, ub[Lf], c->counters + CNT_ITEMS, (int32_t*)c->scratch, &c->launches_set);
     k_item_leaf<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
                                                      c->p2p_leaf);
-    c->launches_set += 2;
+    k_unit_count<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_uoff);
+    scan_excl<int32_t>(s, c->p2p_uoff, ub[Lf], c->counters + CNT_UNITS, (int32_t*)c->scratch, &c->launches_set);
+    k_unit_write<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
+                                                      c->p2p_uoff, c->p2p_units);
+    c->launches_set += 4;
     if (Lf >= 2) {
       ClassArgs ca;
       for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
@@ -1468,6 +1510,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   }
   c->n = n;
   c->p2p_nitems = n > 0 ? c->counters_h[CNT_ITEMS] : 0;
+  c->p2p_nunits = n > 0 ? c->counters_h[CNT_UNITS] : 0;
   if (n > 0) {
     for (int d = 0; d < 4; ++d) c->box_host[d] = c->box_h[d];
   } else {
