@@ -58,6 +58,9 @@ def lib():
             "ofmm_m2l_pair_count": (C.c_int64, [C.c_void_p, C.c_int]),
             "ofmm_coverage": (None, [C.c_void_p, _i32]),
             "ofmm_direct": (None, [C.c_int64, _d, _d, _d, _d]),
+            "ofmm_direct_kernel": (None, [C.c_int64, _d, _d, C.c_double, _d, _d]),
+            "ofmm_direct_sampled_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_int64, _i64, _d, _d]),
+            "ofmm_set_kernel": (C.c_int, [C.c_void_p, C.c_double]),
             "ofmm_direct_sampled": (None, [C.c_int64, _d, _d, C.c_int64, _i64, _d, _d]),
         }
         for name, (res, args) in sig.items():
@@ -106,25 +109,26 @@ def morton_keys(xyz, lo, width: float, leaf: int) -> np.ndarray:
     return keys
 
 
-def direct(xyz, q):
-    """Exact potentials and fields by O(N^2) summation (eq. 1, 2)."""
+def direct(xyz, q, kernel_s: float = 1.0):
+    """Exact potentials and fields by O(N^2) summation (eq. 1, 2; with
+    kernel_s != 1 the kernel |x - y|^-s and F = -grad phi)."""
     xyz = _f64(xyz).reshape(-1, 3)
     q = _f64(q)
     n = xyz.shape[0]
     phi = np.zeros(n)
     F = np.zeros((n, 3))
-    lib().ofmm_direct(n, _p(xyz, _d), _p(q, _d), _p(phi, _d), _p(F, _d))
+    lib().ofmm_direct_kernel(n, _p(xyz, _d), _p(q, _d), float(kernel_s), _p(phi, _d), _p(F, _d))
     return phi, F
 
 
-def direct_sampled(xyz, q, idx):
+def direct_sampled(xyz, q, idx, kernel_s: float = 1.0):
     xyz = _f64(xyz).reshape(-1, 3)
     q = _f64(q)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     phi = np.zeros(idx.shape[0])
     F = np.zeros((idx.shape[0], 3))
-    lib().ofmm_direct_sampled(xyz.shape[0], _p(xyz, _d), _p(q, _d), idx.shape[0], _p(idx, _i64),
-                              _p(phi, _d), _p(F, _d))
+    lib().ofmm_direct_sampled_kernel(xyz.shape[0], _p(xyz, _d), _p(q, _d), float(kernel_s), idx.shape[0],
+                                     _p(idx, _i64), _p(phi, _d), _p(F, _d))
     return phi, F
 
 
@@ -178,7 +182,7 @@ class OracleFMM:
     (the paper's pairing is svd_eps = 10^-order).
     """
 
-    def __init__(self, xyz, q, height: int, order: int, svd_eps=None, svd_from=None):
+    def __init__(self, xyz, q, height: int, order: int, svd_eps=None, svd_from=None, kernel_s: float = 1.0):
         self.xyz = _f64(xyz).reshape(-1, 3)
         self.q = _f64(q)
         self.n = self.xyz.shape[0]
@@ -187,6 +191,9 @@ class OracleFMM:
         self._h = lib().ofmm_create(self.n, _p(self.xyz, _d), _p(self.q, _d), height, order)
         if not self._h:
             raise ValueError("oracle rejected the arguments")
+        self.kernel_s = kernel_s
+        if kernel_s != 1.0 and lib().ofmm_set_kernel(self._h, float(kernel_s)) != 0:
+            raise ValueError("oracle: kernel exponent outside (0, 4]")
         self.svd_eps = svd_eps
         if svd_from is not None:
             # reuse another tree's compressed operators (they depend on order and eps only)

@@ -50,6 +50,7 @@ struct ofmm {
   double* M[MAXH];       /* multipole expansions [ncell][ncoef] */
   double* L[MAXH];       /* local expansions [ncell][ncoef] */
   double xbar[MAXP];     /* Chebyshev roots */
+  double ks;             /* kernel exponent: P(x, y) = |x - y|^-ks (1: Laplace) */
   double* K;             /* M2L operators for unit half-width, see m2l_operators() */
   /* SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator"); svd_eps > 0
    * selects it.  For the 16 canonical transfer vectors: rank, U_k Sigma_k
@@ -221,6 +222,13 @@ static void cell_geometry(const ofmm* c, int level, int64_t cell, double* centre
  * c_S + a xbar_n and c_S - c_T = 2 a t. */
 static int tslot(int tx, int ty, int tz) { return ((tx + 3) * 7 + (ty + 3)) * 7 + (tz + 3); }
 
+/* |r|^-s from r^2 (s = 1: the Laplace kernel, kept as 1 / sqrt). */
+static double kernel_of_r2(double r2, double s) { return s == 1.0 ? 1.0 / sqrt(r2) : pow(r2, -0.5 * s); }
+
+/* The factor a^-s that scales the unit-half-width operators to half-width a
+ * (P is homogeneous of degree -s); s = 1 divides by a as before. */
+static double scale_a(double x, double a, double s) { return s == 1.0 ? x / a : x * pow(a, -s); }
+
 static void m2l_operators(ofmm* c) {
   int p = c->order, C = c->ncoef;
   c->K = (double*)calloc((size_t)343 * C * C, sizeof(double));
@@ -239,7 +247,7 @@ static void m2l_operators(ofmm* c) {
           double r = 2.0 * t[d] + c->xbar[ni[d]] - c->xbar[mi[d]];
           r2 += r * r;
         }
-        K[(size_t)m * C + nn] = 1.0 / sqrt(r2);
+        K[(size_t)m * C + nn] = kernel_of_r2(r2, c->ks);
       }
     }
   }
@@ -255,6 +263,7 @@ ofmm* ofmm_create(int64_t n, const double* xyz, const double* q, int height, int
   ofmm* c = (ofmm*)calloc(1, sizeof(ofmm));
   c->height = height;
   c->order = order;
+  c->ks = 1.0;
   c->leaf = height - 1;
   c->ncoef = order * order * order;
   c->n = n;
@@ -509,7 +518,7 @@ static void m2l_cell(ofmm* c, int l, int64_t T, int64_t* src, int* tv) {
     for (int m = 0; m < C; ++m) {
       double s = 0.0;
       for (int nn = 0; nn < C; ++nn) s += K[(size_t)m * C + nn] * MS[nn];
-      LT[m] += s / a;
+      LT[m] += scale_a(s, a, c->ks);
     }
   }
 }
@@ -654,6 +663,26 @@ int ofmm_jacobi_svd(int n, const double* A, double* U, double* s, double* V) {
   return sweeps;
 }
 
+/* The kernel |x - y|^-s: the operators are rebuilt with it and a compressed
+ * set is dropped (compress again with ofmm_set_m2l_svd).  0 < s <= 4. */
+int ofmm_set_kernel(ofmm* c, double s) {
+  if (!(s > 0.0 && s <= 4.0)) return -1;
+  c->ks = s;
+  if (c->K) {
+    free(c->K);
+    c->K = NULL;
+    m2l_operators(c);
+  }
+  c->svd_eps = 0.0;
+  for (int k = 0; k < 16; ++k) {
+    free(c->svd_US[k]);
+    free(c->svd_V[k]);
+    c->svd_US[k] = c->svd_V[k] = NULL;
+    c->svd_rank[k] = 0;
+  }
+  return 0;
+}
+
 /* The 16 canonical operators K_that (unit half-width, the formula of
  * m2l_operators), each compressed by its own SVD to the rank
  * r = #{ i : s_i >= eps * s_0 } (Sec. 2.1.2 with (l, eps) = (Acc, 10^-Acc)). */
@@ -704,7 +733,7 @@ int ofmm_set_m2l_svd(ofmm* c, double eps) {
  * the order and eps only.  0 on success. */
 int ofmm_copy_m2l_svd(ofmm* dst, const ofmm* src) {
   int C = dst->ncoef;
-  if (src->svd_eps <= 0.0 || src->order != dst->order || dst->leaf < 2) return -1;
+  if (src->svd_eps <= 0.0 || src->order != dst->order || dst->leaf < 2 || src->ks != dst->ks) return -1;
   dst->svd_eps = src->svd_eps;
   for (int k = 0; k < 16; ++k) {
     int r = src->svd_rank[k];
@@ -764,7 +793,7 @@ static void m2l_cell_svd(ofmm* c, int l, int64_t T, int64_t* src, int* tv, doubl
   for (int k = 0; k < nf; ++k) {
     for (int m = 0; m < C; ++m) z[m] = 0.0;
     ofmm_m2l_apply(c, tv + 3 * k, c->M[l] + (size_t)src[k] * C, z);
-    for (int m = 0; m < C; ++m) LT[m] += z[m] / a;
+    for (int m = 0; m < C; ++m) LT[m] += scale_a(z[m], a, c->ks);
   }
 }
 
@@ -859,9 +888,15 @@ static void p2p_particle(const ofmm* c, const int64_t* src, int ns, int64_t r, d
       double d[3] = {xi[0] - c->x[3 * j], xi[1] - c->x[3 * j + 1], xi[2] - c->x[3 * j + 2]};
       double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       if (r2 == 0.0) continue;
-      double rr = sqrt(r2);
-      f += c->q[j] / rr;
-      for (int e = 0; e < 3; ++e) g[e] += c->q[j] * d[e] / (rr * r2);
+      if (c->ks == 1.0) {
+        double rr = sqrt(r2);
+        f += c->q[j] / rr;
+        for (int e = 0; e < 3; ++e) g[e] += c->q[j] * d[e] / (rr * r2);
+      } else { /* F = -grad phi = s q d |d|^-(s+2) */
+        double pk = c->q[j] * pow(r2, -0.5 * c->ks);
+        f += pk;
+        for (int e = 0; e < 3; ++e) g[e] += c->ks * pk * d[e] / r2;
+      }
     }
   *phi = f;
   for (int e = 0; e < 3; ++e) F[e] = g[e];
@@ -1020,7 +1055,7 @@ void ofmm_coverage(const ofmm* c, int32_t* counts) {
 /* Direct summation, eq. 1 with eq. 2                                        */
 /* ------------------------------------------------------------------------ */
 
-static void direct_one(int64_t n, const double* xyz, const double* q, int64_t i, double* phi,
+static void direct_one(int64_t n, const double* xyz, const double* q, double ks, int64_t i, double* phi,
                        double* F) {
   double f = 0.0, g[3] = {0.0, 0.0, 0.0};
   for (int64_t j = 0; j < n; ++j) {
@@ -1029,21 +1064,36 @@ static void direct_one(int64_t n, const double* xyz, const double* q, int64_t i,
                    xyz[3 * i + 2] - xyz[3 * j + 2]};
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 == 0.0) continue;
-    double r = sqrt(r2);
-    f += q[j] / r;
-    for (int e = 0; e < 3; ++e) g[e] += q[j] * d[e] / (r * r2);
+    if (ks == 1.0) {
+      double r = sqrt(r2);
+      f += q[j] / r;
+      for (int e = 0; e < 3; ++e) g[e] += q[j] * d[e] / (r * r2);
+    } else { /* P = |d|^-s, F = -grad phi = s q d |d|^-(s+2) */
+      double pk = q[j] * pow(r2, -0.5 * ks);
+      f += pk;
+      for (int e = 0; e < 3; ++e) g[e] += ks * pk * d[e] / r2;
+    }
   }
   *phi = f;
   for (int e = 0; e < 3; ++e) F[e] = g[e];
 }
 
-void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F) {
+void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double ks, double* phi, double* F) {
 #pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t i = 0; i < n; ++i) direct_one(n, xyz, q, i, &phi[i], &F[3 * i]);
+  for (int64_t i = 0; i < n; ++i) direct_one(n, xyz, q, ks, i, &phi[i], &F[3 * i]);
+}
+
+void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double ks, int64_t ns,
+                                const int64_t* idx, double* phi, double* F) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, ks, idx[s], &phi[s], &F[3 * s]);
+}
+
+void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F) {
+  ofmm_direct_kernel(n, xyz, q, 1.0, phi, F);
 }
 
 void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
                          const int64_t* idx, double* phi, double* F) {
-#pragma omp parallel for schedule(dynamic, 1)
-  for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, idx[s], &phi[s], &F[3 * s]);
+  ofmm_direct_sampled_kernel(n, xyz, q, 1.0, ns, idx, phi, F);
 }

@@ -48,6 +48,11 @@ void ofmm_keys(int64_t n, const double* xyz, const double* lo, double width,
  * (height 1..12, order 2..12, n >= 0, finite inputs). */
 ofmm* ofmm_create(int64_t n, const double* xyz, const double* q, int height, int order);
 void ofmm_destroy(ofmm* c);
+/* Kernel P(x, y) = |x - y|^-s, 0 < s <= 4 (the default s = 1 is the Laplace
+ * kernel of eq. 2; F = -grad phi).  Rebuilds the M2L operators (the kernel is
+ * homogeneous of degree -s: operators of unit half-width scaled by a^-s) and
+ * drops a compressed set.  0 on success, -1 for s out of range. */
+int ofmm_set_kernel(ofmm* c, double s);
 
 void ofmm_box(const ofmm* c, double* lo, double* width);
 int64_t ofmm_level_size(const ofmm* c, int level);
@@ -107,6 +112,11 @@ void ofmm_coverage(const ofmm* c, int32_t* counts);
 
 /* Direct O(N^2) sums of eq. 1 with the kernels of eq. 2. */
 void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F);
+/* The same sums with the kernel |x - y|^-s: phi_i = sum q_j r^-s,
+ * F_i = s sum q_j (x_i - x_j) r^-(s+2). */
+void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double s, double* phi, double* F);
+void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double s, int64_t ns,
+                                const int64_t* idx, double* phi, double* F);
 void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
                          const int64_t* idx, double* phi, double* F);
 

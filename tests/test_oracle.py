@@ -545,3 +545,85 @@ def test_shared_svd_operators_give_the_same_result():
         pb, Fb = b.evaluate()
         assert b.svd_ranks().tolist() == a.svd_ranks().tolist()
     assert np.array_equal(pa, pb) and np.array_equal(Fa, Fb)
+
+
+# ---- the kernel family |x - y|^-s (fmm_set_kernel; the black-box method needs
+# only kernel values).  s = 1 must reproduce the Laplace oracle above exactly;
+# the other pins use the mathematics of the family, not its formula.
+
+KERNELS = (0.5, 2.0, 3.0)
+
+
+def test_kernel_exponent_one_is_the_laplace_oracle():
+    xyz, q = inputs.particles(1500, 61, "cube", "sym")
+    a = oracle.direct(xyz, q)
+    b = oracle.direct(xyz, q, kernel_s=1.0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with oracle.OracleFMM(xyz, q, 4, 5) as o:
+        ra = o.evaluate()
+    with oracle.OracleFMM(xyz, q, 4, 5, kernel_s=1.0) as o:
+        rb = o.evaluate()
+    assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+
+
+@pytest.mark.parametrize("s", KERNELS)
+def test_kernel_field_is_minus_gradient_of_potential(s):
+    """F_i = -d phi_i / d x_i by central differences of the direct sum."""
+    xyz, q = inputs.particles(60, 62, "cube", "sym")
+    _, F = oracle.direct(xyz, q, kernel_s=s)
+    h = 1e-6
+    for i in (0, 17, 59):
+        for d in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            dphi = (oracle.direct(xp, q, kernel_s=s)[0][i] - oracle.direct(xm, q, kernel_s=s)[0][i]) / (2 * h)
+            assert abs(-dphi - F[i, d]) <= 1e-6 * max(1.0, np.abs(F[i]).max()), (i, d)
+
+
+@pytest.mark.parametrize("s", KERNELS)
+def test_kernel_homogeneity_and_newton(s):
+    """x -> 2x scales phi by 2^-s and F by 2^-(s+1); sum_i q_i F_i = 0 for
+    any radial kernel (pairs cancel)."""
+    xyz, q = inputs.particles(800, 63, "cube", "sym")
+    p1, F1 = oracle.direct(xyz, q, kernel_s=s)
+    p2, F2 = oracle.direct(2.0 * xyz, q, kernel_s=s)
+    assert oracle.rel_l2(p2, p1 * 2.0 ** -s) <= 1e-13
+    assert oracle.rel_l2(F2, F1 * 2.0 ** -(s + 1)) <= 1e-13
+    net = (q[:, None] * F1).sum(axis=0)
+    assert np.abs(net).max() <= 1e-12 * np.abs(q[:, None] * F1).sum()
+    with oracle.OracleFMM(xyz, q, 4, 5, kernel_s=s) as o:
+        pa, Fa = o.evaluate()
+    with oracle.OracleFMM(2.0 * xyz, q, 4, 5, kernel_s=s) as o:
+        pb, Fb = o.evaluate()
+    assert oracle.rel_l2(pb, pa * 2.0 ** -s) <= 1e-12
+    assert oracle.rel_l2(Fb, Fa * 2.0 ** -(s + 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("s", KERNELS)
+def test_kernel_fmm_converges_to_the_direct_sum(s):
+    """The FMM error against the direct sum falls as p rises, trees of height
+    <= 2 are the direct sum, and the compressed operators stay within their
+    eps of the full-rank ones."""
+    xyz, q = inputs.particles(3000, 64, "cube", "pos")
+    pd, Fd = oracle.direct(xyz, q, kernel_s=s)
+    errs = []
+    for p in (3, 5, 7):
+        with oracle.OracleFMM(xyz, q, 4, p, kernel_s=s) as o:
+            pf, Ff = o.evaluate()
+        errs.append(max(oracle.rel_l2(pf, pd), oracle.rel_l2(Ff, Fd)))
+        with oracle.OracleFMM(xyz, q, 4, p, kernel_s=s, svd_eps=10.0 ** -p) as o:
+            ps, Fs = o.evaluate()
+        assert oracle.rel_l2(ps, pf) <= 10.0 ** -p and oracle.rel_l2(Fs, Ff) <= 10.0 ** (1 - p)
+    assert errs[0] > 5 * errs[1] > 25 * errs[2], errs
+    assert errs[2] <= 1e-4
+    with oracle.OracleFMM(xyz, q, 2, 4, kernel_s=s) as o:
+        p2, F2 = o.evaluate()
+    assert oracle.rel_l2(p2, pd) <= 1e-14 and oracle.rel_l2(F2, Fd) <= 1e-14
+
+
+def test_kernel_exponent_out_of_range_rejected():
+    xyz, q = inputs.particles(10, 65, "cube", "pos")
+    for bad in (0.0, -1.0, 4.5, float("nan")):
+        with pytest.raises(ValueError):
+            oracle.OracleFMM(xyz, q, 3, 3, kernel_s=bad)
