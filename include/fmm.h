@@ -95,6 +95,20 @@ fmm_status fmm_set_precision(fmm_handle h, int precision);
  * Errors: FMM_ERR_ARG (unknown method, eps >= 1 or NaN). */
 fmm_status fmm_set_m2l(fmm_handle h, int method, double eps);
 
+/* Chooses the kernel of later evaluations from the family
+ * P(x, y) = |x - y|^-s, 0 < s <= 4 (default s = 1, the Laplace kernel of
+ * eq. 2): phi_i = sum_j q_j |x_i - x_j|^-s and F_i = -grad phi_i =
+ * s sum_j q_j (x_i - x_j) |x_i - x_j|^-(s+2).  The black-box method of
+ * Sec. 2.1 needs nothing but kernel values: the M2L operators become
+ * K_t[m][n] = |2t + xbar_n - xbar_m|^-s, scaled per level by a^-s (the kernels
+ * are homogeneous of degree -s), their SVDs are recomputed, and the near
+ * field evaluates the new kernel (with s != 1 in one kernel shape; see
+ * fmm_autotune).  Multiquadrics and the other non-homogeneous kernels of the
+ * method would need operators per level and are not offered.  Drops the
+ * handle's M2L operators (rebuilt by the next evaluation); synchronises the
+ * stream.  Errors: FMM_ERR_ARG (s outside (0, 4]). */
+fmm_status fmm_set_kernel(fmm_handle h, double s);
+
 /* Ranks of the 16 compressed canonical operators, in lexicographic order of
  * their transfer vectors ((0,0,2), (0,0,3), (0,1,2), ..., (3,3,3)), for the
  * handle's order and the eps of fmm_set_m2l; computes the SVDs if they are
@@ -200,7 +214,10 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * to the grouping of FP32 partial sums.
  * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
- * FMM_P2P_VARIANTS mean launch times.  Synchronises the
+ * FMM_P2P_VARIANTS mean launch times.  With a kernel exponent other than 1
+ * (fmm_set_kernel) the near field has one shape (4 warps, 256-source chunks,
+ * one source per instruction): choice = {-1, 4, 256, 1, 4} and every time is
+ * that shape's.  Synchronises the
  * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
 

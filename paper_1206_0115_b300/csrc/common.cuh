@@ -63,6 +63,15 @@ struct LevelPtrs {
   int32_t ncell[FMM_MAX_LEVELS];  // host-known sizes (valid after the readback)
 };
 
+// The kernel family P(x, y) = |x - y|^-s (s = 1: the Laplace kernel of eq. 2;
+// fmm_set_kernel).  A homogeneous kernel: with cell half-width a the M2L
+// operators are K_t / a^s, K_t[m][n] = |2t + xbar_n - xbar_m|^-s.  s = 1 keeps
+// the reciprocal square root exactly as before.
+__host__ __device__ inline double kernel_r2(double r2, double s) {
+  return s == 1.0 ? 1.0 / sqrt(r2) : pow(r2, -0.5 * s);
+}
+__host__ __device__ inline double kernel_scale(double inv_a, double s) { return s == 1.0 ? inv_a : pow(inv_a, s); }
+
 // Batched trees: whether cell g at level l may interact with a cell whose
 // problem is `mine` (the problem of the asking cell; -1 above the slots).
 __host__ __device__ inline bool same_problem(const LevelPtrs& lv, int l, int mine, int g) {
@@ -91,6 +100,7 @@ struct fmm_ctx {
   using LevelPtrs = fmm::LevelPtrs;
   int height = 0, order = 0, leaf = 0, ncoef = 0, cpad = 0;
   int precision = FMM_MIXED;
+  double kernel_s = 1.0;  // P(x, y) = |x - y|^-kernel_s
   int dev = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t side = nullptr;    // P2P branch

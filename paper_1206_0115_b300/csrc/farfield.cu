@@ -409,9 +409,9 @@ __device__ __forceinline__ void leaf_xi(int64_t r, const double4* __restrict__ p
 // far + near, scaled to the problem's units, scattered to the caller's order
 template <bool MIXED>
 __device__ __forceinline__ void l2p_store(int64_t r, double pf, double gx, double gy, double gz, double lam,
-                                          const float4* __restrict__ near32, const double4* __restrict__ near64,
-                                          const int32_t* __restrict__ perm, double* __restrict__ phi,
-                                          double* __restrict__ F) {
+                                          double lam2, const float4* __restrict__ near32,
+                                          const double4* __restrict__ near64, const int32_t* __restrict__ perm,
+                                          double* __restrict__ phi, double* __restrict__ F) {
   double nphi, nx, ny, nz;
   if (MIXED) {
     const float4 nr = near32[r];
@@ -426,7 +426,6 @@ __device__ __forceinline__ void l2p_store(int64_t r, double pf, double gx, doubl
     ny = nr.z;
     nz = nr.w;
   }
-  const double lam2 = lam * lam;
   const int64_t i = perm[r];
   phi[i] = (pf + nphi) * lam;
   F[3 * i] = (gx + nx) * lam2;
@@ -442,7 +441,7 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
           int cpad, const T* __restrict__ L, int has_far, const double4* __restrict__ pos64,
           const float4* __restrict__ pos32, const float4* __restrict__ near32,
           const double4* __restrict__ near64, const int32_t* __restrict__ perm, double* __restrict__ phi,
-          double* __restrict__ F, const double* __restrict__ fscale) {
+          double* __restrict__ F, const double* __restrict__ fscale, double ks) {
   constexpr int C = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sL = (T*)smem_raw;
@@ -462,8 +461,11 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
   double ctr[3], a;
   cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
   // batched trees: back from the forest cube to the problem's own units
+  // (distances there are lambda times the problem's: phi scales by lambda^s,
+  // F by lambda^(s+1))
   const int prob = fscale ? lv.slot[leaf][cell] : -1;
-  const double lam = prob >= 0 ? fscale[prob] : 1.0;
+  const double lam = prob >= 0 ? kernel_scale(fscale[prob], ks) : 1.0;
+  const double lam2 = prob >= 0 ? lam * fscale[prob] : 1.0;
   for (int r = first + lane; r < first + cnt; r += 32) {
     double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
     if (has_far) {
@@ -471,7 +473,7 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
       leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
       l2p_eval<P, T, MIXED>(myL, sC, xi, a, pf, gx, gy, gz);
     }
-    l2p_store<MIXED>(r, pf, gx, gy, gz, lam, near32, near64, perm, phi, F);
+    l2p_store<MIXED>(r, pf, gx, gy, gz, lam, lam2, near32, near64, perm, phi, F);
   }
 }
 
@@ -485,7 +487,7 @@ k_l2p_pp(LevelPtrs lv, int leaf, int64_t n, const int32_t* __restrict__ pleaf, c
          const T* __restrict__ cheb, int cpad, const T* __restrict__ L, int has_far,
          const double4* __restrict__ pos64, const float4* __restrict__ pos32, const float4* __restrict__ near32,
          const double4* __restrict__ near64, const int32_t* __restrict__ perm, double* __restrict__ phi,
-         double* __restrict__ F, const double* __restrict__ fscale) {
+         double* __restrict__ F, const double* __restrict__ fscale, double ks) {
   __shared__ T sC[P * P];
   for (int i = threadIdx.x; i < P * P; i += 128) sC[i] = cheb[i];
   __syncthreads();
@@ -495,14 +497,15 @@ k_l2p_pp(LevelPtrs lv, int leaf, int64_t n, const int32_t* __restrict__ pleaf, c
   double ctr[3], a;
   cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
   const int prob = fscale ? lv.slot[leaf][cell] : -1;
-  const double lam = prob >= 0 ? fscale[prob] : 1.0;
+  const double lam = prob >= 0 ? kernel_scale(fscale[prob], ks) : 1.0;
+  const double lam2 = prob >= 0 ? lam * fscale[prob] : 1.0;
   double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
   if (has_far) {
     T xi[3];
     leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
     l2p_eval<P, T, MIXED>(L + (lv.row_off[leaf] + cell) * (int64_t)cpad, sC, xi, a, pf, gx, gy, gz);
   }
-  l2p_store<MIXED>(r, pf, gx, gy, gz, lam, near32, near64, perm, phi, F);
+  l2p_store<MIXED>(r, pf, gx, gy, gz, lam, lam2, near32, near64, perm, phi, F);
 }
 
 // ---------------------------------------------------------------- M2L (SIMT)
@@ -518,7 +521,7 @@ k_m2l_simt(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
            const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
            const int16_t* __restrict__ cls_t, const T* __restrict__ Khi, const T* __restrict__ Klo,
            int kstride, int C, int cpad, const T* __restrict__ Mhi, const T* __restrict__ Mlo,
-           T* __restrict__ Lout, const double* __restrict__ box) {
+           T* __restrict__ Lout, const double* __restrict__ box, double ks) {
   __shared__ T As[16][64];
   __shared__ T Bs[16][64 + 1];
   __shared__ int srow[64];
@@ -597,7 +600,7 @@ k_m2l_simt(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
         tot[i][j] = s;
       }
   }
-  const double inv_a = ldexp(1.0, l + 1) / box[3];
+  const double inv_a = kernel_scale(ldexp(1.0, l + 1) / box[3], ks);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = half * 64 + ty + 16 * i;
@@ -685,20 +688,20 @@ fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
     if (pp)
       k_l2p_pp<P, float, true><<<ceil_div(c->n, 128), 128, 0, s>>>(
           c->lv, Lf, c->n, c->pleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32,
-          c->near64, c->perm, phi, F, fs);
+          c->near64, c->perm, phi, F, fs, c->kernel_s);
     else
       k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
           c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
-          c->perm, phi, F, fs);
+          c->perm, phi, F, fs, c->kernel_s);
   } else {
     if (pp)
       k_l2p_pp<P, double, false><<<ceil_div(c->n, 128), 128, 0, s>>>(
           c->lv, Lf, c->n, c->pleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32,
-          c->near64, c->perm, phi, F, fs);
+          c->near64, c->perm, phi, F, fs, c->kernel_s);
     else
       k_l2p_out<P, double, false><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(double), s>>>(
           c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad, c->L64, has_far, c->pos64, c->pos32, c->near32, c->near64,
-          c->perm, phi, F, fs);
+          c->perm, phi, F, fs, c->kernel_s);
   }
   return cuda_err(c, cudaGetLastError(), "L2P launch");
 }
@@ -768,11 +771,11 @@ fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
   const int32_t* nact = c->tile_nact + first_tile;
   if (c->precision == FMM_MIXED)
     k_m2l_simt<float, true><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->Khi, c->Klo, c->cpad,
-                                                 c->ncoef, c->cpad, c->Mhi, c->Mlo, c->L32, c->box);
+                                                 c->ncoef, c->cpad, c->Mhi, c->Mlo, c->L32, c->box, c->kernel_s);
   else
     k_m2l_simt<double, false><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->K64, nullptr,
                                                    c->ncoef, c->ncoef, c->cpad, c->M64, nullptr, c->L64,
-                                                   c->box);
+                                                   c->box, c->kernel_s);
   return cuda_err(c, cudaGetLastError(), "M2L launch");
 }
 

@@ -53,9 +53,9 @@ constexpr int SVD_MAX_SWEEPS = 60;
 
 using tc::tf32_rna;
 
-// K_that[m][n] = 1 / |2 that + xbar_n - xbar_m| for the 16 canonical vectors.
+// K_that[m][n] = |2 that + xbar_n - xbar_m|^-s for the 16 canonical vectors.
 __global__ void k_canon_ops64(int p, int C, const double* __restrict__ nodes, const int8_t* __restrict__ canon,
-                              double* __restrict__ K) {
+                              double ks, double* __restrict__ K) {
   const int64_t total = (int64_t)16 * C * C;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / ((int64_t)C * C));
@@ -68,7 +68,7 @@ __global__ void k_canon_ops64(int p, int C, const double* __restrict__ nodes, co
       const double r = 2.0 * canon[3 * k + d] + nodes[ni[d]] - nodes[mi[d]];
       r2 += r * r;
     }
-    K[e] = 1.0 / sqrt(r2);
+    K[e] = kernel_r2(r2, ks);
   }
 }
 
@@ -329,7 +329,7 @@ k_m2l_proj(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict_
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(256)
 k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restrict__ Ub, const T* __restrict__ Ulo,
-             const T* __restrict__ Y, T* __restrict__ Lout, const double* __restrict__ box) {
+             const T* __restrict__ Y, T* __restrict__ Lout, const double* __restrict__ box, double ks) {
   __shared__ T As[16][64];
   __shared__ T Bs[16][64 + 1];
   __shared__ int64_t sy[64];
@@ -405,7 +405,7 @@ k_m2l_expand(SvdArgs a, LevelPtrs lv, int C, int cpad, int R, const T* __restric
         tot[i][j] = s;
       }
   }
-  const double inv_a = ldexp(1.0, l + 1) / box[3];
+  const double inv_a = kernel_scale(ldexp(1.0, l + 1) / box[3], ks);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = half * 64 + ty + 16 * i;
@@ -504,7 +504,7 @@ fmm_status svd_prepare(Ctx* c) {
   double* K;
   FMM_TRY(dalloc(c, &ptr, sizeof(double) * mat));
   K = (double*)ptr;
-  k_canon_ops64<<<ceil_div(mat, 256), 256, 0, s>>>(p, C, c->nodes64, c->svd_canon, K);
+  k_canon_ops64<<<ceil_div(mat, 256), 256, 0, s>>>(p, C, c->nodes64, c->svd_canon, c->kernel_s, K);
   k_svd_jacobi<<<16, SVD_THREADS, 0, s>>>(C, K, c->svd_W, c->svd_Z, c->svd_sweeps_d);
   k_svd_order<<<16, SVD_THREADS, 0, s>>>(C, eps, c->svd_W, c->svd_vals, c->svd_ord, c->svd_rank_d, c->svd_colmean);
   FMM_CUDA(c, cudaGetLastError());
@@ -652,14 +652,14 @@ fmm_status launch_m2l_svd_simt(Ctx* c, cudaStream_t s, int first_tile, int ntile
     k_m2l_proj<float, true><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_VThi, nullptr, c->Mhi,
                                                      c->Mlo, Y);
     k_m2l_expand<float, true><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rp, c->svd_Uhi, nullptr, Y, c->L32,
-                                                 c->box);
+                                                 c->box, c->kernel_s);
   } else {
     dim3 ge(ntiles, 2, ceil_div(C, 64));
     double* Y = (double*)c->svd_Y;
     k_m2l_proj<double, false><<<gp, FMM_TILE, 0, s>>>(a, c->lv, C, cp, c->svd_rmax, c->svd_V64, nullptr, c->M64,
                                                        nullptr, Y);
     k_m2l_expand<double, false><<<ge, 256, 0, s>>>(a, c->lv, C, cp, c->svd_rmax, c->svd_U64, nullptr, Y, c->L64,
-                                                   c->box);
+                                                   c->box, c->kernel_s);
   }
   return cuda_err(c, cudaGetLastError(), "compressed M2L launch");
 }

@@ -713,7 +713,11 @@ int sp_ngroups(int Rp) { return (FMM_NT_CLASS * Rp + (SP_ACC - Rp)) / (SP_ACC - 
 int sp_stage_bytes() { return 2 * SP_A_BYTES + 2 * SP_B_BYTES; }
 int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256) / sp_stage_bytes()); }
 int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256; }
-int ex_nhalf(int cp) { return cp > 256 ? cp / 2 : cp; }
+// Columns per half: cp, or cp / 2 when one accumulator of cp columns is
+// wider than an MMA or the two accumulators would leave TMEM room for fewer A
+// stages than there are producer sets (parity waits need every set to run at
+// most one phase ahead of the MMA; p = 6, cp = 224, would leave two stages).
+int ex_nhalf(int cp) { return (cp > 256 || 2 * cp + 32 * EX_SETS > 512) ? cp / 2 : cp; }
 int ex_stage_bytes(int cp) { return 2 * ex_nhalf(cp) * KC * 4; }
 int ex_smem(int cp, int nst) { return nst * ex_stage_bytes(cp) + ex_nhalf(cp) * FMM_TILE * 4 + 1024 + 256; }
 
@@ -723,7 +727,7 @@ int ex_smem(int cp, int nst) { return nst * ex_stage_bytes(cp) + ex_nhalf(cp) * 
 // that fit two TMEM accumulators beside the A stages: order <= 7.
 bool m2l_svd_tc_supported(const Ctx* c) {
   const int nhalf = ex_nhalf(c->cpad);
-  return c->cpad % 32 == 0 && nhalf <= 256 && nhalf % 16 == 0 && 2 * nhalf + 32 * 2 <= 512 && c->svd_rp <= SP_ACC;
+  return c->cpad % 32 == 0 && nhalf <= 256 && nhalf % 16 == 0 && 2 * nhalf + 32 * EX_SETS <= 512 && c->svd_rp <= SP_ACC;
 }
 
 // Tensor maps of the compressed factor banks, the partial-sum buffer and the
@@ -801,7 +805,8 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   nst = std::min(nst, (512 - 2 * nhalf) / 32);
   nst = std::min(nst, MAXST);
   const int nst_p = sp_nst();
-  if (nst < 2 || nst_p < 2) return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: no room for 2 stages");
+  if (nst < EX_SETS || nst_p < 2)
+    return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: fewer stages than producer sets");
   c->svd_tc_nst = nst;
   FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc, sp_smem(nst_p)));
   FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc, ex_smem(cp, nst)));

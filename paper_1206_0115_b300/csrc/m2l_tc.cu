@@ -320,13 +320,13 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
 __global__ void __launch_bounds__(256)
 k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_nact, LevelPtrs lv, int ntiles,
                 int gt, int cpad, int ncol, const float* __restrict__ partial, float* __restrict__ L,
-                const double* __restrict__ box) {
+                const double* __restrict__ box, double ks) {
   const int tile = blockIdx.x, r0 = blockIdx.y * 16;
   const Tile tl = tiles[tile];
   if (r0 >= tl.count) return;
   const int nrow = min(16, tl.count - r0);
   const int ng = (tile_nact[tile] + gt - 1) / gt;
-  const float inv_a = (float)(ldexp(1.0, tl.level + 1) / box[3]);
+  const float inv_a = (float)kernel_scale(ldexp(1.0, tl.level + 1) / box[3], ks);
   const int64_t rbase = lv.row_off[tl.level];
   const int nq = (ncol + 3) / 4;  // float4 columns (cpad is a multiple of 32)
   for (int idx = threadIdx.x; idx < nrow * nq; idx += blockDim.x) {
@@ -353,7 +353,13 @@ bool m2l_tc_supported(const Ctx* c) { return c->cpad <= 512 && c->cpad % 32 == 0
 namespace {
 constexpr int TC_GT = 64;  // transfer vectors per work unit
 constexpr int TC_GROUPS = (FMM_NT_CLASS + TC_GT - 1) / TC_GT;
-int tc_nh(int cp) { return cp > 256 ? 2 : 1; }
+// Column halves per tile: two when one accumulator of cp columns is wider
+// than an MMA (256) or when the two accumulators would leave TMEM room for
+// fewer A stages than there are producer sets.  A set waits on its stage's
+// barrier by phase parity, which is only unambiguous while it runs at most
+// one phase ahead of the MMA; with fewer stages than sets it could run two
+// ahead (p = 6: cp = 224 leaves room for two stages).
+int tc_nh(int cp) { return (cp > 256 || 2 * cp + 32 * TC_SETS > 512) ? 2 : 1; }
 int tc_stage_bytes(int cp) { return 2 * (cp / tc_nh(cp)) * TC_KC * 4; }
 int tc_fixed_bytes(int cp) { return (cp / tc_nh(cp)) * FMM_TILE * 4 + 1024 + 256; }  // sums, alignment, barriers
 }  // namespace
@@ -364,7 +370,7 @@ int tc_fixed_bytes(int cp) { return (cp / tc_nh(cp)) * FMM_TILE * 4 + 1024 + 256
 fmm_status m2l_tc_prepare(Ctx* c) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad;
-  const int nh = cp > 256 ? 2 : 1, nhalf = cp / nh;
+  const int nh = tc_nh(cp), nhalf = cp / nh;
   if (nhalf % 16 != 0 || nhalf > 256) return set_err(c, FMM_ERR_ARG, "M2L tensor path: unsupported cpad %d", cp);
   const int64_t need = (int64_t)c->ntiles * TC_GROUPS * FMM_TILE * cp;
   if (need > c->tc_partial_cap) {
@@ -392,7 +398,7 @@ fmm_status m2l_tc_prepare(Ctx* c) {
   const int tmem_stages = (512 - 2 * (cp / tc_nh(cp))) / 32;  // A stages beside the two accumulators
   if (nst > tmem_stages) nst = tmem_stages;
   if (nst > TC_MAXST) nst = TC_MAXST;
-  if (nst < 2) return set_err(c, FMM_ERR_ARG, "M2L tensor path: stage too large for cpad %d", cp);
+  if (nst < TC_SETS) return set_err(c, FMM_ERR_ARG, "M2L tensor path: fewer stages than producer sets for cpad %d", cp);
   c->tc_nst = nst;
   const int smem = nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
   FMM_TRY(raise_smem_limit(c, (const void*)k_m2l_tc, smem));
@@ -403,7 +409,7 @@ fmm_status m2l_tc_prepare(Ctx* c) {
 // L_T = (1/a) * (sum of the partial slices) for every tile (see k_m2l_tc_reduce).
 fmm_status launch_m2l_tc_reduce(Ctx* c, cudaStream_t s, const float* partial, int gt) {
   k_m2l_tc_reduce<<<dim3(c->ntiles, FMM_TILE / 16), 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, gt,
-                                                                  c->cpad, c->ncoef + 1, partial, c->L32, c->box);
+                                                                  c->cpad, c->ncoef + 1, partial, c->L32, c->box, c->kernel_s);
   return cuda_err(c, cudaGetLastError(), "M2L reduction launch");
 }
 
@@ -412,7 +418,7 @@ fmm_status launch_m2l_tc_reduce(Ctx* c, cudaStream_t s, const float* partial, in
 fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad;
-  const int nh = cp > 256 ? 2 : 1, nhalf = cp / nh;
+  const int nh = tc_nh(cp), nhalf = cp / nh;
   TcArgs a;
   a.tiles = c->tiles;
   a.tile_src = c->tile_src;
@@ -442,7 +448,7 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
   k_m2l_tc_reduce<<<dim3(c->ntiles, FMM_TILE / 16), 256, 0, s>>>(c->tiles, c->tile_nact, c->lv, c->ntiles, TC_GT, cp, c->ncoef + 1,
-                                            c->tc_partial, c->L32, c->box);
+                                            c->tc_partial, c->L32, c->box, c->kernel_s);
   return cuda_err(c, cudaGetLastError(), "M2L tensor-core launch");
 }
 

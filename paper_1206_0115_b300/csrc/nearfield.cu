@@ -576,11 +576,159 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   }
 }
 
+// ---- the kernel family |x - y|^-s, s != 1 ----------------------------------
+// The same work items, staging and exact hi/lo differences as k_p2p32; per
+// pair phi += q r^-s and F += s q d r^-(s+2) (F = -grad phi), with
+// r^-s = 2^(-s/2 log2 r^2) and 1/r^2 on the MUFU pipe.
+template <int G, bool SELF>
+__device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, const float4* __restrict__ slo, int k0,
+                                             int k1, float4 th, float4 tl, float hs, float sk, float& fphi,
+                                             float& fx, float& fy, float& fz) {
+#pragma unroll 4
+  for (int k = k0; k < k1; k += G) {
+    const float4 sh = shi[k], sl = slo[k];
+    const float dx = (th.x - sh.x) + (tl.x - sl.x);
+    const float dy = (th.y - sh.y) + (tl.y - sl.y);
+    const float dz = (th.z - sh.z) + (tl.z - sl.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float ps = exp2f(-hs * __log2f(r2));
+    float ir2 = __frcp_rn(r2);
+    if (SELF) {
+      ps = r2 > 0.f ? ps : 0.f;
+      ir2 = r2 > 0.f ? ir2 : 0.f;
+    }
+    const float qi = sh.w * ps;
+    const float qi3 = sk * qi * ir2;
+    fphi += qi;
+    fx = fmaf(qi3, dx, fx);
+    fy = fmaf(qi3, dy, fy);
+    fz = fmaf(qi3, dz, fz);
+  }
+}
+
+template <int W, int CH>
+__global__ void __launch_bounds__(W * 32)
+k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of, int nitems,
+         const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
+         double ks, float4* __restrict__ out) {
+  __shared__ float4 shi[W][CH];
+  __shared__ float4 slo[W][CH];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * W + warp;
+  if (item >= nitems) return;
+  const int T = leaf_of[item];
+  const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int tb = (item - items[T]) * 32;
+  int ix, iy, iz;
+  demorton3(lv.key[leaf][T], ix, iy, iz);
+  const int top = (1 << leaf) - 1;
+  const int mine = problem_of(lv, leaf, T);
+  int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
+  if (lane < 27) {
+    const int k = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+    ox = k / 9 - 1;
+    oy = (k / 3) % 3 - 1;
+    oz = k % 3 - 1;
+    const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
+    if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
+      const int g = lv.grid[leaf][morton3(sx, sy, sz)];
+      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
+        nf = lv.first[leaf][g];
+        ncnt = lv.count[leaf][g];
+      }
+    }
+  }
+  int incl = ncnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane < 27) {
+    nb_first[warp][lane] = nf;
+    nb_pre[warp][lane] = incl - ncnt;
+    nb_off[warp][lane][0] = (int8_t)ox;
+    nb_off[warp][lane][1] = (int8_t)oy;
+    nb_off[warp][lane][2] = (int8_t)oz;
+  }
+  if (lane == 0) nb_pre[warp][27] = total;
+  __syncwarp();
+  const int own = tc;
+  const int nt = min(32, tc - tb);
+  int lg = 0;
+  while ((nt << (lg + 1)) <= 32) ++lg;
+  const int g = 1 << lg, ti = lane >> lg, sub = lane & (g - 1);
+  const bool tvalid = ti < nt;
+  float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+  if (tvalid) {
+    th = pos32[tf + tb + ti];
+    tl = pos32lo[tf + tb + ti];
+  }
+  const float hs = (float)(0.5 * ks), sk = (float)ks;
+  Kahan kp, kx, ky, kz;
+  for (int c0 = 0; c0 < total; c0 += CH) {
+    const int cn = min(CH, total - c0);
+    __syncwarp();
+    for (int k = lane; k < cn; k += 32) {
+      const int sidx = c0 + k;
+      int lo = 0, hi = 26;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nb_pre[warp][mid] <= sidx) lo = mid;
+        else hi = mid - 1;
+      }
+      const int j = nb_first[warp][lo] + (sidx - nb_pre[warp][lo]);
+      float4 ph = pos32[j];
+      ph.x += (float)nb_off[warp][lo][0];
+      ph.y += (float)nb_off[warp][lo][1];
+      ph.z += (float)nb_off[warp][lo][2];
+      shi[warp][k] = ph;
+      slo[warp][k] = pos32lo[j];
+    }
+    __syncwarp();
+    float fphi = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    const int kown = min(cn, max(0, own - c0));
+    const float4* sh = &shi[warp][0];
+    const float4* sl = &slo[warp][0];
+    // one lane group per target: sources sub, sub + g, ... (own leaf first: r = 0 pairs skipped)
+    switch (g) {
+#define SPAN_POW(G)                                                                               \
+  case G: {                                                                                       \
+    p2p_span_pow<G, true>(sh, sl, sub, kown, th, tl, hs, sk, fphi, fx, fy, fz);                   \
+    const int k0 = kown + ((sub - kown) % G + G) % G;                                             \
+    p2p_span_pow<G, false>(sh, sl, k0, cn, th, tl, hs, sk, fphi, fx, fy, fz);                     \
+  } break;
+      SPAN_POW(1) SPAN_POW(2) SPAN_POW(4) SPAN_POW(8) SPAN_POW(16) SPAN_POW(32)
+#undef SPAN_POW
+    }
+    kp.add(fphi);
+    kx.add(fx);
+    ky.add(fy);
+    kz.add(fz);
+  }
+  float aphi = kp.s, ax = kx.s, ay = ky.s, az = kz.s;
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+  if (tvalid && sub == 0) {
+    // positions are in leaf widths w: phi scales by w^-s, F by w^-(s+1)
+    const double iw = 1.0 / ldexp(box[3], -leaf);
+    const float s1 = (float)pow(iw, ks), s2 = (float)(pow(iw, ks) * iw);
+    out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
+  }
+}
+
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
 k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
         int nitems,
-        const double4* __restrict__ pos64, double4* __restrict__ out) {
+        const double4* __restrict__ pos64, double ks, double4* __restrict__ out) {
   __shared__ double4 src[P2P_WARPS][P2P_CH];
   __shared__ int nb_first[P2P_WARPS][27];
   __shared__ int nb_pre[P2P_WARPS][28];
@@ -644,9 +792,16 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, co
         const double dx = t.x - pp.x, dy = t.y - pp.y, dz = t.z - pp.z;
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 > 0.0) {
-          const double rr = sqrt(r2);
-          aphi += pp.w / rr;
-          const double q3 = pp.w / (rr * r2);
+          double q1, q3;
+          if (ks == 1.0) {
+            const double rr = sqrt(r2);
+            q1 = pp.w / rr;
+            q3 = pp.w / (rr * r2);
+          } else {  // |x - y|^-s: phi += q r^-s, F += s q d r^-(s+2)
+            q1 = pp.w * pow(r2, -0.5 * ks);
+            q3 = ks * q1 / r2;
+          }
+          aphi += q1;
           ax += q3 * dx;
           ay += q3 * dy;
           az += q3 * dz;
@@ -686,7 +841,7 @@ bool is_p2p_kernel(const void* f) {
                       (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                       (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
                       (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
-                      (const void*)k_p2p64};
+                      (const void*)k_p2p32s<4, 256>,     (const void*)k_p2p64};
   for (const void* k : ks)
     if (k == f) return true;
   return false;
@@ -712,7 +867,10 @@ void p2p_carveout() {
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
-  if (c->precision == FMM_MIXED) {
+  if (c->precision == FMM_MIXED && c->kernel_s != 1.0) {
+    k_p2p32s<4, 256><<<ceil_div(c->p2p_nitems, 4), 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems,
+                                                                 c->pos32, c->pos32lo, c->box, c->kernel_s, c->near32);
+  } else if (c->precision == FMM_MIXED) {
 #define P2P_LAUNCH(W, CH)                                                                              \
   k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,   \
                                                              c->p2p_nitems, c->pos32, c->pos32lo, c->box, c->near32)
@@ -748,7 +906,8 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
 #undef P2P_LAUNCH2
   } else
     k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
-                                                                          c->p2p_nitems, c->pos64, c->near64);
+                                                                          c->p2p_nitems, c->pos64, c->kernel_s,
+                                                                          c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");
 }
 

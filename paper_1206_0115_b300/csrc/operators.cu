@@ -28,7 +28,7 @@ __device__ inline float tf32_rna(float x) {
 
 // FP64 bank: K_t[m][n] for m, n < C.
 __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, const int8_t* __restrict__ tvec,
-                            double* __restrict__ K64) {
+                            double ks, double* __restrict__ K64) {
   const int64_t total = (int64_t)FMM_NT * C * C;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -42,7 +42,7 @@ __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, cons
       const double r = 2.0 * tvec[3 * t + d] + nodes[ni[d]] - nodes[mi[d]];
       r2 += r * r;
     }
-    K64[i] = 1.0 / sqrt(r2);
+    K64[i] = kernel_r2(r2, ks);
   }
 }
 
@@ -52,7 +52,7 @@ __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, cons
 // (rows < C) as separate FP32 numbers; every value is split into TF32 hi/lo.
 // One thread per (t, n).
 __global__ void k_m2l_ops_split(int p, int C, int cpad, const double* __restrict__ nodes,
-                                const int8_t* __restrict__ tvec, float* __restrict__ Khi,
+                                const int8_t* __restrict__ tvec, double ks, float* __restrict__ Khi,
                                 float* __restrict__ Klo) {
   const int64_t total = (int64_t)FMM_NT * cpad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -74,7 +74,7 @@ __global__ void k_m2l_ops_split(int p, int C, int cpad, const double* __restrict
         const double r = y[d] - nodes[mi[d]];
         r2 += r * r;
       }
-      return 1.0 / sqrt(r2);
+      return kernel_r2(r2, ks);
     };
     double mean = 0.0;
     for (int m = 0; m < C; ++m) mean += K(m);
@@ -214,9 +214,10 @@ fmm_status operators_m2l(Ctx* c, int precision) {
     FMM_TRY(dalloc(c, &ptr, sizeof(float) * (size_t)FMM_NT * cp * cp));
     c->Klo = (float*)ptr;
   }
-  if (want64) k_m2l_ops64<<<1184, 256, 0, c->stream>>>(p, C, c->nodes64, c->tvec, c->K64);
+  if (want64) k_m2l_ops64<<<1184, 256, 0, c->stream>>>(p, C, c->nodes64, c->tvec, c->kernel_s, c->K64);
   if (want32) k_m2l_ops_split<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(p, C, cp, c->nodes64,
-                                                                                           c->tvec, c->Khi, c->Klo);
+                                                                                           c->tvec, c->kernel_s,
+                                                                                           c->Khi, c->Klo);
   FMM_CUDA(c, cudaGetLastError());
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (want64) c->ops64 = true;

@@ -168,6 +168,8 @@ FP64_CASES = [
     ("cube_n2k_h4_p8", lambda: inputs.particles(2000, 16, "cube", "pos"), 4, 8),
     ("cube_n1k_h3_p10", lambda: inputs.particles(1000, 17, "cube", "pos"), 3, 10),
     ("dups_h4_p3", _dup_faces, 4, 3),
+    ("ellipsoid_n20k_h5_p6", lambda: inputs.particles(20000, 18, "ellipsoid", "sym"), 5, 6),
+    ("cube_n1500_h3_p9", lambda: inputs.particles(1500, 19, "cube", "pos"), 3, 9),
 ]
 
 
@@ -230,6 +232,11 @@ MIXED_CASES = [
     ("cube_n2k_h4_p8", lambda: inputs.particles(2000, 16, "cube", "pos"), 4, 8),
     ("cube_n1k_h3_p10", lambda: inputs.particles(1000, 17, "cube", "pos"), 3, 10),
     ("dups_h4_p4", _dup_faces, 4, 4),
+    # p = 6: the tensor-core M2L splits its 224 columns into two halves (the
+    # two accumulators of 224 would leave room for only two pipeline stages)
+    ("ellipsoid_n40k_h5_p6", lambda: inputs.particles(40000, 34, "ellipsoid", "sym"), 5, 6),
+    ("cube_n20k_h4_p6", lambda: inputs.particles(20000, 35, "cube", "pos"), 4, 6),
+    ("cube_n1500_h3_p9", lambda: inputs.particles(1500, 19, "cube", "pos"), 3, 9),
 ]
 
 

@@ -1,0 +1,221 @@
+"""The kernel family |x - y|^-s (fmm_set_kernel) on the GPU.
+
+The oracle is the FP64 CPU oracle built with the same exponent: M2L operators
+from |x - y|^-s, the per-level a^-s scaling the homogeneity of the kernel
+allows (Sec. 2.2, improved M2L operator), and the same kernel in the near
+field.  Bars:
+  * FP64 path: relative L2 error against the oracle's FMM <= 1e-10, with the
+    full-rank and the compressed M2L;
+  * mixed path: <= 1e-5 against the oracle's FMM;
+  * trees of height <= 2 (near field only) against the direct sum, FP64
+    <= 1e-12 and mixed <= 1e-5;
+  * batches with s != 1, per problem, against the oracle run on each problem;
+  * switching the exponent on a handle rebuilds its operators: s = 1 after
+    s = 2 gives the s = 1 result again.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_0115_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10
+TOL_MIXED = 1e-5
+TOL_ALONE = 1e-6
+EXPONENTS = (0.5, 2.0, 3.0)
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1206_0115_b300 import build
+    build.build()
+    from paper_1206_0115_b300 import fmm
+    return fmm
+
+
+@functools.lru_cache(maxsize=None)
+def _problem(n, seed, dist):
+    return inputs.particles(n, seed, dist, "sym")
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(n, seed, dist, h, p, s, svd):
+    xyz, q = _problem(n, seed, dist)
+    eps = 10.0 ** -p if (svd and h >= 3) else None
+    with oracle.OracleFMM(xyz, q, h, p, svd_eps=eps, kernel_s=s) as o:
+        return o.evaluate()
+
+
+def _gpu(F, xyz, q, h, p, precision, s, m2l=None, f=None):
+    import torch
+    n = len(q)
+    own = f is None
+    if own:
+        f = F.FMM(h, p, precision, m2l=F.FMM_M2L_SVD if m2l is None else m2l, kernel_s=s)
+    try:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        return phi.cpu().numpy(), Fo.cpu().numpy()
+    finally:
+        if own:
+            f.close()
+
+
+@pytest.mark.parametrize("s", EXPONENTS)
+@pytest.mark.parametrize("svd", [True, False], ids=["svd", "full"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kernel_matches_the_oracle(F, s, svd, prec):
+    n, seed, dist, h, p = 20000, 71, "cube", 4, 5
+    xyz, q = _problem(n, seed, dist)
+    precision = F.FMM_FP64 if prec == "fp64" else F.FMM_MIXED
+    phi, Fo = _gpu(F, xyz, q, h, p, precision, s, F.FMM_M2L_SVD if svd else F.FMM_M2L_FULL)
+    rphi, rF = _oracle(n, seed, dist, h, p, s, svd)
+    tol = TOL_FP64 if prec == "fp64" else TOL_MIXED
+    assert oracle.rel_l2(phi, rphi) <= tol
+    assert oracle.rel_l2(Fo, rF) <= tol
+
+
+@pytest.mark.parametrize("s", (0.5, 2.0))
+def test_kernel_ragged_surface_tree(F, s):
+    """Points on an ellipsoid surface, height 5, order 6: leaves from empty to
+    crowded, several tiles of M2L work and a ragged tail."""
+    n, seed, dist, h, p = 40000, 72, "ellipsoid", 5, 6
+    xyz, q = _problem(n, seed, dist)
+    rphi, rF = _oracle(n, seed, dist, h, p, s, True)
+    for precision, tol in ((F.FMM_FP64, TOL_FP64), (F.FMM_MIXED, TOL_MIXED)):
+        phi, Fo = _gpu(F, xyz, q, h, p, precision, s)
+        assert oracle.rel_l2(phi, rphi) <= tol, precision
+        assert oracle.rel_l2(Fo, rF) <= tol, precision
+
+
+@pytest.mark.parametrize("s", EXPONENTS + (4.0,))
+@pytest.mark.parametrize("h", [1, 2])
+def test_kernel_near_field_only_is_the_direct_sum(F, s, h):
+    xyz, q = _problem(3000, 73, "cube")
+    dphi, dF = oracle.direct(xyz, q, kernel_s=s)
+    phi, Fo = _gpu(F, xyz, q, h, 4, F.FMM_FP64, s)
+    assert oracle.rel_l2(phi, dphi) <= 1e-12 and oracle.rel_l2(Fo, dF) <= 1e-12
+    phi, Fo = _gpu(F, xyz, q, h, 4, F.FMM_MIXED, s)
+    assert oracle.rel_l2(phi, dphi) <= TOL_MIXED and oracle.rel_l2(Fo, dF) <= TOL_MIXED
+
+
+def test_kernel_error_against_the_direct_sum_falls_with_order(F):
+    """At s = 2 the mixed path at p = 3, 5, 7 is as close to the direct sum as
+    the oracle's FMM of the same order (within the mixed-precision bar)."""
+    xyz, q = _problem(20000, 74, "cube")
+    dphi, dF = oracle.direct(xyz, q, kernel_s=2.0)
+    errs = []
+    for p in (3, 5, 7):
+        phi, Fo = _gpu(F, xyz, q, 4, p, F.FMM_MIXED, 2.0)
+        rphi, rF = _oracle(20000, 74, "cube", 4, p, 2.0, True)
+        e = max(oracle.rel_l2(phi, dphi), oracle.rel_l2(Fo, dF))
+        eo = max(oracle.rel_l2(rphi, dphi), oracle.rel_l2(rF, dF))
+        assert e <= eo + TOL_MIXED, (p, e, eo)
+        errs.append(e)
+    assert errs[0] > errs[1] > errs[2], errs
+
+
+def test_kernel_switch_on_a_handle_rebuilds_the_operators(F):
+    xyz, q = _problem(20000, 75, "cube")
+    for precision, tol in ((F.FMM_FP64, 1e-13), (F.FMM_MIXED, TOL_ALONE)):
+        with F.FMM(4, 5, precision) as f:
+            a = _gpu(F, xyz, q, 4, 5, precision, 1.0, f=f)
+            f.set_kernel(2.0)
+            b = _gpu(F, xyz, q, 4, 5, precision, 2.0, f=f)
+            f.set_kernel(1.0)
+            c = _gpu(F, xyz, q, 4, 5, precision, 1.0, f=f)
+        ra = _oracle(20000, 75, "cube", 4, 5, 1.0, True)
+        rb = _oracle(20000, 75, "cube", 4, 5, 2.0, True)
+        bar = TOL_FP64 if precision == F.FMM_FP64 else TOL_MIXED
+        assert oracle.rel_l2(a[0], ra[0]) <= bar and oracle.rel_l2(a[1], ra[1]) <= bar
+        assert oracle.rel_l2(b[0], rb[0]) <= bar and oracle.rel_l2(b[1], rb[1]) <= bar
+        assert oracle.rel_l2(c[0], a[0]) <= tol and oracle.rel_l2(c[1], a[1]) <= tol
+
+
+def test_kernel_batch_matches_each_problem_alone(F):
+    import torch
+    s, p = 2.0, 5
+    specs = [(3000, "cube", 4), (9000, "ellipsoid", 5), (0, "cube", 3), (1, "cube", 3), (500, "ellipsoid", 3),
+             (2000, "cube", 2), (6000, "cube", 4)]
+    probs = [(*inputs.particles(n, 760 + k, dist, "pos" if k % 2 else "sym"), h)
+             for k, (n, dist, h) in enumerate(specs)]
+    counts = np.array([len(q) for _, q, _ in probs], dtype=np.int64)
+    heights = np.array([h for _, _, h in probs], dtype=np.int32)
+    xyz = np.ascontiguousarray(np.concatenate([x.reshape(-1, 3) for x, _, _ in probs]))
+    qq = np.ascontiguousarray(np.concatenate([q for _, q, _ in probs]))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for precision, tol in ((F.FMM_FP64, TOL_FP64), (F.FMM_MIXED, TOL_MIXED)):
+        with F.FMM(3, p, precision, kernel_s=s) as f:
+            f.set_batch(counts, heights, torch.from_numpy(xyz).cuda(), torch.from_numpy(qq).cuda())
+            phi = torch.zeros(len(qq), dtype=torch.float64, device="cuda")
+            Fo = torch.zeros((len(qq), 3), dtype=torch.float64, device="cuda")
+            f.evaluate(phi, Fo)
+            torch.cuda.synchronize()
+            phi, Fo = phi.cpu().numpy(), Fo.cpu().numpy()
+        for k, (x, q, h) in enumerate(probs):
+            sl = slice(off[k], off[k + 1])
+            if len(q) <= 1:
+                assert np.all(phi[sl] == 0) and np.all(Fo[sl] == 0), k
+                continue
+            with oracle.OracleFMM(x, q, h, p, svd_eps=10.0 ** -p if h >= 3 else None, kernel_s=s) as o:
+                rphi, rF = o.evaluate()
+            assert oracle.rel_l2(phi[sl], rphi) <= tol, (k, precision)
+            assert oracle.rel_l2(Fo[sl], rF) <= tol, (k, precision)
+
+
+def test_kernel_autotune_reports_the_one_shape(F):
+    import torch
+    xyz, q = _problem(20000, 71, "cube")
+    with F.FMM(4, 5, F.FMM_MIXED, kernel_s=0.5) as f:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        choice, times = F.fmm_autotune(f.h)
+        assert list(choice) == [-1, 4, 256, 1, 4]
+        assert np.all(times > 0) and np.all(times == times[0])
+        phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+    rphi, rF = _oracle(20000, 71, "cube", 4, 5, 0.5, True)
+    assert oracle.rel_l2(phi.cpu().numpy(), rphi) <= TOL_MIXED
+    assert oracle.rel_l2(Fo.cpu().numpy(), rF) <= TOL_MIXED
+
+
+def test_kernel_exponent_checked(F):
+    with F.FMM(3, 4, F.FMM_MIXED) as f:
+        for bad in (0.0, -1.0, 4.5, float("nan")):
+            with pytest.raises(F.FMMError) as e:
+                f.set_kernel(bad)
+            assert e.value.status == F.FMM_ERR_ARG
+        f.set_kernel(4.0)
+
+
+@pytest.mark.slow
+def test_kernel_full_size_sampled(F):
+    """1e6 points in the unit cube, h 6, p 7, s = 2, mixed precision with the
+    autotuned near field: 2000 sampled outputs against the oracle."""
+    n, h, p, s = 1_000_000, 6, 7, 2.0
+    xyz, q = inputs.particles(n, 77, "cube", "sym")
+    idx = np.sort(np.random.default_rng(78).choice(n, size=2000, replace=False))
+    import torch
+    with F.FMM(h, p, F.FMM_MIXED, kernel_s=s) as f:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        F.fmm_autotune(f.h)
+        phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        phi, Fo = phi.cpu().numpy(), Fo.cpu().numpy()
+    with oracle.OracleFMM(xyz, q, h, p, svd_eps=10.0 ** -p, kernel_s=s) as o:
+        rphi, rF = o.evaluate_sampled(idx)
+    assert oracle.rel_l2(phi[idx], rphi) <= TOL_MIXED
+    assert oracle.rel_l2(Fo[idx], rF) <= TOL_MIXED
