@@ -58,9 +58,9 @@ def lib():
             "ofmm_m2l_pair_count": (C.c_int64, [C.c_void_p, C.c_int]),
             "ofmm_coverage": (None, [C.c_void_p, _i32]),
             "ofmm_direct": (None, [C.c_int64, _d, _d, _d, _d]),
-            "ofmm_direct_kernel": (None, [C.c_int64, _d, _d, C.c_double, _d, _d]),
-            "ofmm_direct_sampled_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_int64, _i64, _d, _d]),
-            "ofmm_set_kernel": (C.c_int, [C.c_void_p, C.c_double]),
+            "ofmm_direct_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_double, _d, _d]),
+            "ofmm_direct_sampled_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_double, C.c_int64, _i64, _d, _d]),
+            "ofmm_set_kernel": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
             "ofmm_direct_sampled": (None, [C.c_int64, _d, _d, C.c_int64, _i64, _d, _d]),
         }
         for name, (res, args) in sig.items():
@@ -109,25 +109,25 @@ def morton_keys(xyz, lo, width: float, leaf: int) -> np.ndarray:
     return keys
 
 
-def direct(xyz, q, kernel_s: float = 1.0):
-    """Exact potentials and fields by O(N^2) summation (eq. 1, 2; with
-    kernel_s != 1 the kernel |x - y|^-s and F = -grad phi)."""
+def direct(xyz, q, kernel_s: float = 1.0, kernel_c: float = 0.0):
+    """Exact potentials and fields by O(N^2) summation (eq. 1, 2; otherwise
+    the kernel (|x - y|^2 + c^2)^(-s/2) and F = -grad phi)."""
     xyz = _f64(xyz).reshape(-1, 3)
     q = _f64(q)
     n = xyz.shape[0]
     phi = np.zeros(n)
     F = np.zeros((n, 3))
-    lib().ofmm_direct_kernel(n, _p(xyz, _d), _p(q, _d), float(kernel_s), _p(phi, _d), _p(F, _d))
+    lib().ofmm_direct_kernel(n, _p(xyz, _d), _p(q, _d), float(kernel_s), float(kernel_c), _p(phi, _d), _p(F, _d))
     return phi, F
 
 
-def direct_sampled(xyz, q, idx, kernel_s: float = 1.0):
+def direct_sampled(xyz, q, idx, kernel_s: float = 1.0, kernel_c: float = 0.0):
     xyz = _f64(xyz).reshape(-1, 3)
     q = _f64(q)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     phi = np.zeros(idx.shape[0])
     F = np.zeros((idx.shape[0], 3))
-    lib().ofmm_direct_sampled_kernel(xyz.shape[0], _p(xyz, _d), _p(q, _d), float(kernel_s), idx.shape[0],
+    lib().ofmm_direct_sampled_kernel(xyz.shape[0], _p(xyz, _d), _p(q, _d), float(kernel_s), float(kernel_c), idx.shape[0],
                                      _p(idx, _i64), _p(phi, _d), _p(F, _d))
     return phi, F
 
@@ -182,7 +182,8 @@ class OracleFMM:
     (the paper's pairing is svd_eps = 10^-order).
     """
 
-    def __init__(self, xyz, q, height: int, order: int, svd_eps=None, svd_from=None, kernel_s: float = 1.0):
+    def __init__(self, xyz, q, height: int, order: int, svd_eps=None, svd_from=None, kernel_s: float = 1.0,
+                 kernel_c: float = 0.0):
         self.xyz = _f64(xyz).reshape(-1, 3)
         self.q = _f64(q)
         self.n = self.xyz.shape[0]
@@ -191,9 +192,10 @@ class OracleFMM:
         self._h = lib().ofmm_create(self.n, _p(self.xyz, _d), _p(self.q, _d), height, order)
         if not self._h:
             raise ValueError("oracle rejected the arguments")
-        self.kernel_s = kernel_s
-        if kernel_s != 1.0 and lib().ofmm_set_kernel(self._h, float(kernel_s)) != 0:
-            raise ValueError("oracle: kernel exponent outside (0, 4]")
+        self.kernel_s, self.kernel_c = kernel_s, kernel_c
+        if (kernel_s != 1.0 or kernel_c != 0.0) and lib().ofmm_set_kernel(self._h, float(kernel_s),
+                                                                           float(kernel_c)) != 0:
+            raise ValueError("oracle: kernel outside -2 <= s <= 4, s != 0, c >= 0")
         self.svd_eps = svd_eps
         if svd_from is not None:
             # reuse another tree's compressed operators (they depend on order and eps only)
@@ -201,7 +203,8 @@ class OracleFMM:
             if lib().ofmm_copy_m2l_svd(self._h, svd_from._h) != 0:
                 raise ValueError("oracle: cannot share the compressed operators")
         elif svd_eps is not None and lib().ofmm_set_m2l_svd(self._h, float(svd_eps)) != 0:
-            raise ValueError("oracle: the compression needs height >= 3 and a converged SVD")
+            raise ValueError("oracle: the compression needs height >= 3, a homogeneous kernel (c = 0) "
+                             "and a converged SVD")
 
     def svd_ranks(self) -> np.ndarray:
         return np.array([lib().ofmm_svd_rank(self._h, k) for k in range(16)])

@@ -20,6 +20,9 @@
  *   Sec. 2.1.2  M2L over the children of the parent's neighbours that are not
  *          neighbours themselves (at most 189), 316 distinct transfer
  *          vectors, computed once thanks to the homogeneity of 1/r.
+ *   Sec. 2.2  the method needs kernel values only: ofmm_set_kernel selects
+ *          (|x-y|^2 + kc^2)^(-ks/2); kc = 0 is homogeneous (one operator set,
+ *          scaled per level), kc > 0 (multiquadrics) gets a set per level.
  *   Sec. 3.2  bottom-up P2M, M2M; top-down M2L, L2L, L2P; P2P at the leaves.
  *   Sec. 4.2  cells in Morton order.
  *
@@ -50,8 +53,10 @@ struct ofmm {
   double* M[MAXH];       /* multipole expansions [ncell][ncoef] */
   double* L[MAXH];       /* local expansions [ncell][ncoef] */
   double xbar[MAXP];     /* Chebyshev roots */
-  double ks;             /* kernel exponent: P(x, y) = |x - y|^-ks (1: Laplace) */
+  double ks;             /* kernel exponent: P(x, y) = (|x - y|^2 + kc^2)^(-ks/2) */
+  double kc;             /* kernel offset c (0: |x - y|^-ks; ks = 1, kc = 0: Laplace) */
   double* K;             /* M2L operators for unit half-width, see m2l_operators() */
+  double* Kl[MAXH];      /* kc > 0: the operators of each level, at its half-width */
   /* SVD-compressed M2L (Sec. 2.1.2, "Improved M2L operator"); svd_eps > 0
    * selects it.  For the 16 canonical transfer vectors: rank, U_k Sigma_k
    * [C][rank] and V_k [C][rank]. */
@@ -222,34 +227,62 @@ static void cell_geometry(const ofmm* c, int level, int64_t cell, double* centre
  * c_S + a xbar_n and c_S - c_T = 2 a t. */
 static int tslot(int tx, int ty, int tz) { return ((tx + 3) * 7 + (ty + 3)) * 7 + (tz + 3); }
 
-/* |r|^-s from r^2 (s = 1: the Laplace kernel, kept as 1 / sqrt). */
-static double kernel_of_r2(double r2, double s) { return s == 1.0 ? 1.0 / sqrt(r2) : pow(r2, -0.5 * s); }
+/* (r^2 + kc^2)^(-s/2) from r^2 (s = 1, kc = 0: the Laplace kernel, kept as
+ * 1 / sqrt). */
+static double kernel_of_r2(double r2, double s, double kc) {
+  if (kc == 0.0) return s == 1.0 ? 1.0 / sqrt(r2) : pow(r2, -0.5 * s);
+  return pow(r2 + kc * kc, -0.5 * s);
+}
 
 /* The factor a^-s that scales the unit-half-width operators to half-width a
  * (P is homogeneous of degree -s); s = 1 divides by a as before. */
 static double scale_a(double x, double a, double s) { return s == 1.0 ? x / a : x * pow(a, -s); }
 
-static void m2l_operators(ofmm* c) {
+/* K_t[m][n] = P(xbar_m, 2 a t + a xbar_n) over the 343 slots of t in
+ * [-3, 3]^3 (only the far ones are filled) for half-width a. */
+static double* operators_at(const ofmm* c, double a, double kc) {
   int p = c->order, C = c->ncoef;
-  c->K = (double*)calloc((size_t)343 * C * C, sizeof(double));
+  double* Kall = (double*)calloc((size_t)343 * C * C, sizeof(double));
 #pragma omp parallel for schedule(dynamic)
   for (int s = 0; s < 343; ++s) {
     int t[3] = {s / 49 - 3, (s / 7) % 7 - 3, s % 7 - 3};
     int far = abs(t[0]) >= 2 || abs(t[1]) >= 2 || abs(t[2]) >= 2;
     if (!far) continue;
-    double* K = c->K + (size_t)s * C * C;
+    double* K = Kall + (size_t)s * C * C;
     for (int m = 0; m < C; ++m) {
       int mi[3] = {m / (p * p), (m / p) % p, m % p};
       for (int nn = 0; nn < C; ++nn) {
         int ni[3] = {nn / (p * p), (nn / p) % p, nn % p};
         double r2 = 0.0;
         for (int d = 0; d < 3; ++d) {
-          double r = 2.0 * t[d] + c->xbar[ni[d]] - c->xbar[mi[d]];
+          double r = a * (2.0 * t[d] + c->xbar[ni[d]] - c->xbar[mi[d]]);
           r2 += r * r;
         }
-        K[(size_t)m * C + nn] = kernel_of_r2(r2, c->ks);
+        K[(size_t)m * C + nn] = kernel_of_r2(r2, c->ks, kc);
       }
     }
+  }
+  return Kall;
+}
+
+/* Homogeneous kernels (kc = 0): one set at unit half-width, scaled per level
+ * (Sec. 2.1.2).  kc > 0 is not homogeneous: every level l gets its own set,
+ * the kernel evaluated at the level's own node positions (half-width
+ * a_l = W / 2^(l+1)), which the M2L applies unscaled. */
+static void m2l_operators(ofmm* c) {
+  if (c->kc == 0.0) {
+    c->K = operators_at(c, 1.0, 0.0);
+    return;
+  }
+  for (int l = 2; l <= c->leaf; ++l) c->Kl[l] = operators_at(c, ldexp(c->width, -l - 1), c->kc);
+}
+
+static void free_operators(ofmm* c) {
+  free(c->K);
+  c->K = NULL;
+  for (int l = 0; l < MAXH; ++l) {
+    free(c->Kl[l]);
+    c->Kl[l] = NULL;
   }
 }
 
@@ -354,7 +387,7 @@ void ofmm_destroy(ofmm* c) {
   free(c->perm);
   free(c->x);
   free(c->q);
-  free(c->K);
+  free_operators(c);
   for (int k = 0; k < 16; ++k) {
     free(c->svd_US[k]);
     free(c->svd_V[k]);
@@ -510,15 +543,16 @@ static void m2l_cell(ofmm* c, int l, int64_t T, int64_t* src, int* tv) {
   int C = c->ncoef;
   double a = ldexp(c->width, -l - 1);
   double* LT = c->L[l] + (size_t)T * C;
+  const double* Kset = c->kc == 0.0 ? c->K : c->Kl[l];
   for (int m = 0; m < C; ++m) LT[m] = 0.0;
   int nf = far_list(c, l, T, src, tv);
   for (int k = 0; k < nf; ++k) {
-    const double* K = c->K + (size_t)tslot(tv[3 * k], tv[3 * k + 1], tv[3 * k + 2]) * C * C;
+    const double* K = Kset + (size_t)tslot(tv[3 * k], tv[3 * k + 1], tv[3 * k + 2]) * C * C;
     const double* MS = c->M[l] + (size_t)src[k] * C;
     for (int m = 0; m < C; ++m) {
       double s = 0.0;
       for (int nn = 0; nn < C; ++nn) s += K[(size_t)m * C + nn] * MS[nn];
-      LT[m] += scale_a(s, a, c->ks);
+      LT[m] += c->kc == 0.0 ? scale_a(s, a, c->ks) : s;
     }
   }
 }
@@ -663,16 +697,16 @@ int ofmm_jacobi_svd(int n, const double* A, double* U, double* s, double* V) {
   return sweeps;
 }
 
-/* The kernel |x - y|^-s: the operators are rebuilt with it and a compressed
- * set is dropped (compress again with ofmm_set_m2l_svd).  0 < s <= 4. */
-int ofmm_set_kernel(ofmm* c, double s) {
-  if (!(s > 0.0 && s <= 4.0)) return -1;
+/* The kernel (|x - y|^2 + kc^2)^(-s/2): the operators are rebuilt with it
+ * and a compressed set is dropped (compress again with ofmm_set_m2l_svd;
+ * kc = 0 only).  -2 <= s <= 4, s != 0, kc >= 0. */
+int ofmm_set_kernel(ofmm* c, double s, double kc) {
+  if (!(s >= -2.0 && s <= 4.0 && s != 0.0) || !(kc >= 0.0 && isfinite(kc))) return -1;
+  int had = c->K != NULL || c->Kl[c->leaf] != NULL;
   c->ks = s;
-  if (c->K) {
-    free(c->K);
-    c->K = NULL;
-    m2l_operators(c);
-  }
+  c->kc = kc;
+  free_operators(c);
+  if (had) m2l_operators(c);
   c->svd_eps = 0.0;
   for (int k = 0; k < 16; ++k) {
     free(c->svd_US[k]);
@@ -688,7 +722,7 @@ int ofmm_set_kernel(ofmm* c, double s) {
  * r = #{ i : s_i >= eps * s_0 } (Sec. 2.1.2 with (l, eps) = (Acc, 10^-Acc)). */
 int ofmm_set_m2l_svd(ofmm* c, double eps) {
   int C = c->ncoef, bad = 0;
-  if (c->leaf < 2 || eps <= 0.0) return -1;
+  if (c->leaf < 2 || eps <= 0.0 || c->kc != 0.0) return -1;
   c->svd_eps = eps;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
   for (int k = 0; k < 16; ++k) {
@@ -733,7 +767,8 @@ int ofmm_set_m2l_svd(ofmm* c, double eps) {
  * the order and eps only.  0 on success. */
 int ofmm_copy_m2l_svd(ofmm* dst, const ofmm* src) {
   int C = dst->ncoef;
-  if (src->svd_eps <= 0.0 || src->order != dst->order || dst->leaf < 2 || src->ks != dst->ks) return -1;
+  if (src->svd_eps <= 0.0 || src->order != dst->order || dst->leaf < 2 || src->ks != dst->ks || dst->kc != 0.0)
+    return -1;
   dst->svd_eps = src->svd_eps;
   for (int k = 0; k < 16; ++k) {
     int r = src->svd_rank[k];
@@ -757,6 +792,7 @@ int ofmm_svd_rank(const ofmm* c, int k) { return (k >= 0 && k < 16 && c->svd_eps
  * because sigma is an isometry that maps the nodes onto the nodes). */
 void ofmm_m2l_apply(const ofmm* c, const int* t, const double* M, double* out) {
   int C = c->ncoef;
+  if (c->svd_eps <= 0.0 && !c->K) return; /* kc > 0: no unit-half-width set */
   if (c->svd_eps <= 0.0) {
     const double* K = c->K + (size_t)tslot(t[0], t[1], t[2]) * C * C;
     for (int m = 0; m < C; ++m) {
@@ -888,14 +924,15 @@ static void p2p_particle(const ofmm* c, const int64_t* src, int ns, int64_t r, d
       double d[3] = {xi[0] - c->x[3 * j], xi[1] - c->x[3 * j + 1], xi[2] - c->x[3 * j + 2]};
       double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       if (r2 == 0.0) continue;
-      if (c->ks == 1.0) {
+      if (c->ks == 1.0 && c->kc == 0.0) {
         double rr = sqrt(r2);
         f += c->q[j] / rr;
         for (int e = 0; e < 3; ++e) g[e] += c->q[j] * d[e] / (rr * r2);
-      } else { /* F = -grad phi = s q d |d|^-(s+2) */
-        double pk = c->q[j] * pow(r2, -0.5 * c->ks);
+      } else { /* F = -grad phi = s q d (|d|^2 + kc^2)^-(s+2)/2 */
+        double re = r2 + c->kc * c->kc;
+        double pk = c->q[j] * pow(re, -0.5 * c->ks);
         f += pk;
-        for (int e = 0; e < 3; ++e) g[e] += c->ks * pk * d[e] / r2;
+        for (int e = 0; e < 3; ++e) g[e] += c->ks * pk * d[e] / re;
       }
     }
   *phi = f;
@@ -1055,8 +1092,8 @@ void ofmm_coverage(const ofmm* c, int32_t* counts) {
 /* Direct summation, eq. 1 with eq. 2                                        */
 /* ------------------------------------------------------------------------ */
 
-static void direct_one(int64_t n, const double* xyz, const double* q, double ks, int64_t i, double* phi,
-                       double* F) {
+static void direct_one(int64_t n, const double* xyz, const double* q, double ks, double kc, int64_t i,
+                       double* phi, double* F) {
   double f = 0.0, g[3] = {0.0, 0.0, 0.0};
   for (int64_t j = 0; j < n; ++j) {
     if (j == i) continue;
@@ -1064,36 +1101,38 @@ static void direct_one(int64_t n, const double* xyz, const double* q, double ks,
                    xyz[3 * i + 2] - xyz[3 * j + 2]};
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 == 0.0) continue;
-    if (ks == 1.0) {
+    if (ks == 1.0 && kc == 0.0) {
       double r = sqrt(r2);
       f += q[j] / r;
       for (int e = 0; e < 3; ++e) g[e] += q[j] * d[e] / (r * r2);
-    } else { /* P = |d|^-s, F = -grad phi = s q d |d|^-(s+2) */
-      double pk = q[j] * pow(r2, -0.5 * ks);
+    } else { /* P = (|d|^2 + kc^2)^(-s/2), F = -grad phi = s q d (|d|^2 + kc^2)^-(s+2)/2 */
+      double re = r2 + kc * kc;
+      double pk = q[j] * pow(re, -0.5 * ks);
       f += pk;
-      for (int e = 0; e < 3; ++e) g[e] += ks * pk * d[e] / r2;
+      for (int e = 0; e < 3; ++e) g[e] += ks * pk * d[e] / re;
     }
   }
   *phi = f;
   for (int e = 0; e < 3; ++e) F[e] = g[e];
 }
 
-void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double ks, double* phi, double* F) {
+void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double ks, double kc, double* phi,
+                        double* F) {
 #pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t i = 0; i < n; ++i) direct_one(n, xyz, q, ks, i, &phi[i], &F[3 * i]);
+  for (int64_t i = 0; i < n; ++i) direct_one(n, xyz, q, ks, kc, i, &phi[i], &F[3 * i]);
 }
 
-void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double ks, int64_t ns,
+void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double ks, double kc, int64_t ns,
                                 const int64_t* idx, double* phi, double* F) {
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, ks, idx[s], &phi[s], &F[3 * s]);
+  for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, ks, kc, idx[s], &phi[s], &F[3 * s]);
 }
 
 void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F) {
-  ofmm_direct_kernel(n, xyz, q, 1.0, phi, F);
+  ofmm_direct_kernel(n, xyz, q, 1.0, 0.0, phi, F);
 }
 
 void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
                          const int64_t* idx, double* phi, double* F) {
-  ofmm_direct_sampled_kernel(n, xyz, q, 1.0, ns, idx, phi, F);
+  ofmm_direct_sampled_kernel(n, xyz, q, 1.0, 0.0, ns, idx, phi, F);
 }

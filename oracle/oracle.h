@@ -48,11 +48,14 @@ void ofmm_keys(int64_t n, const double* xyz, const double* lo, double width,
  * (height 1..12, order 2..12, n >= 0, finite inputs). */
 ofmm* ofmm_create(int64_t n, const double* xyz, const double* q, int height, int order);
 void ofmm_destroy(ofmm* c);
-/* Kernel P(x, y) = |x - y|^-s, 0 < s <= 4 (the default s = 1 is the Laplace
- * kernel of eq. 2; F = -grad phi).  Rebuilds the M2L operators (the kernel is
- * homogeneous of degree -s: operators of unit half-width scaled by a^-s) and
- * drops a compressed set.  0 on success, -1 for s out of range. */
-int ofmm_set_kernel(ofmm* c, double s);
+/* Kernel P(x, y) = (|x - y|^2 + kc^2)^(-s/2), -2 <= s <= 4, s != 0, kc >= 0
+ * (the default s = 1, kc = 0 is the Laplace kernel of eq. 2; F = -grad phi;
+ * kc > 0: multiquadric s = -1, inverse multiquadric s = 1).  Rebuilds the M2L
+ * operators and drops a compressed set.  kc = 0 is homogeneous of degree -s:
+ * one set of unit half-width scaled by a^-s; kc > 0 is not: one set per
+ * level, the kernel at the level's own node positions, and no compression.
+ * 0 on success, -1 for arguments out of range. */
+int ofmm_set_kernel(ofmm* c, double s, double kc);
 
 void ofmm_box(const ofmm* c, double* lo, double* width);
 int64_t ofmm_level_size(const ofmm* c, int level);
@@ -100,7 +103,8 @@ int ofmm_set_m2l_svd(ofmm* c, double eps);
 int ofmm_copy_m2l_svd(ofmm* dst, const ofmm* src);
 /* Rank of canonical operator k (0..15), -1 if the compression is off. */
 int ofmm_svd_rank(const ofmm* c, int k);
-/* out[C] += (operator of transfer vector t at unit half-width) M[C]. */
+/* out[C] += (operator of transfer vector t at unit half-width) M[C]
+ * (homogeneous kernels; with kc > 0 out is left unchanged). */
 void ofmm_m2l_apply(const ofmm* c, const int* t, const double* M, double* out);
 
 /* Number of ordered (target, source) cell pairs M2L visits at `level`. */
@@ -112,10 +116,12 @@ void ofmm_coverage(const ofmm* c, int32_t* counts);
 
 /* Direct O(N^2) sums of eq. 1 with the kernels of eq. 2. */
 void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F);
-/* The same sums with the kernel |x - y|^-s: phi_i = sum q_j r^-s,
- * F_i = s sum q_j (x_i - x_j) r^-(s+2). */
-void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double s, double* phi, double* F);
-void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double s, int64_t ns,
+/* The same sums with the kernel (r^2 + kc^2)^(-s/2): phi_i = sum q_j
+ * (r^2 + kc^2)^(-s/2), F_i = s sum q_j (x_i - x_j) (r^2 + kc^2)^(-(s+2)/2);
+ * pairs at distance 0 are skipped. */
+void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double s, double kc, double* phi,
+                        double* F);
+void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double s, double kc, int64_t ns,
                                 const int64_t* idx, double* phi, double* F);
 void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
                          const int64_t* idx, double* phi, double* F);

@@ -622,8 +622,99 @@ def test_kernel_fmm_converges_to_the_direct_sum(s):
     assert oracle.rel_l2(p2, pd) <= 1e-14 and oracle.rel_l2(F2, Fd) <= 1e-14
 
 
-def test_kernel_exponent_out_of_range_rejected():
+def test_kernel_arguments_out_of_range_rejected():
     xyz, q = inputs.particles(10, 65, "cube", "pos")
-    for bad in (0.0, -1.0, 4.5, float("nan")):
+    for bad in (0.0, -2.5, 4.5, float("nan")):
         with pytest.raises(ValueError):
             oracle.OracleFMM(xyz, q, 3, 3, kernel_s=bad)
+    for bad in (-1.0, float("inf"), float("nan")):
+        with pytest.raises(ValueError):
+            oracle.OracleFMM(xyz, q, 3, 3, kernel_s=1.0, kernel_c=bad)
+    # the compression needs one operator set for all levels (c = 0)
+    with pytest.raises(ValueError):
+        oracle.OracleFMM(xyz, q, 3, 3, kernel_s=1.0, kernel_c=0.1, svd_eps=1e-3)
+
+
+# ---- multiquadrics: (|x - y|^2 + c^2)^(-s/2), c > 0 (not homogeneous: one
+# operator set per level).  s = -1 multiquadric, s = 1 inverse multiquadric.
+
+MQ = ((1.0, 0.05), (-1.0, 0.05), (2.0, 0.02))
+
+
+def _quadratic_closed_form(xyz, q, c):
+    """s = -2: P = |x - y|^2 + c^2, so with Q = sum q, S = sum q x, T = sum q |x|^2
+    (self pair excluded): phi_i = Q |x_i|^2 - 2 x_i . S + T + c^2 (Q - q_i),
+    F_i = -grad phi_i = 2 S - 2 Q x_i."""
+    Q = q.sum()
+    S = (q[:, None] * xyz).sum(axis=0)
+    T = (q * (xyz ** 2).sum(axis=1)).sum()
+    phi = Q * (xyz ** 2).sum(axis=1) - 2.0 * xyz @ S + T + c * c * (Q - q)
+    return phi, 2.0 * S[None, :] - 2.0 * Q * xyz
+
+
+@pytest.mark.parametrize("c", [0.0, 0.3])
+def test_quadratic_kernel_is_reproduced_exactly(c):
+    """Chebyshev interpolation of order p >= 3 reproduces quadratics, so the
+    FMM of |x - y|^2 + c^2 equals the closed form to rounding at every height
+    (per-level operators for c > 0, the scaled unit set for c = 0); a wrong
+    level, scale or sign anywhere in the far field breaks this."""
+    xyz, q = inputs.particles(2500, 66, "ellipsoid", "sym")
+    pc, Fc = _quadratic_closed_form(xyz, q, c)
+    pd, Fd = oracle.direct(xyz, q, kernel_s=-2.0, kernel_c=c)
+    assert oracle.rel_l2(pd, pc) <= 1e-13 and oracle.rel_l2(Fd, Fc) <= 1e-13
+    for h, p in ((4, 3), (5, 4)):
+        with oracle.OracleFMM(xyz, q, h, p, kernel_s=-2.0, kernel_c=c) as o:
+            pf, Ff = o.evaluate()
+        assert oracle.rel_l2(pf, pc) <= 1e-12, (h, p)
+        assert oracle.rel_l2(Ff, Fc) <= 1e-12, (h, p)
+
+
+@pytest.mark.parametrize("s,c", MQ)
+def test_multiquadric_field_is_minus_gradient(s, c):
+    xyz, q = inputs.particles(60, 67, "cube", "sym")
+    _, F = oracle.direct(xyz, q, kernel_s=s, kernel_c=c)
+    h = 1e-6
+    for i in (0, 31, 59):
+        for d in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            dphi = (oracle.direct(xp, q, kernel_s=s, kernel_c=c)[0][i]
+                    - oracle.direct(xm, q, kernel_s=s, kernel_c=c)[0][i]) / (2 * h)
+            assert abs(-dphi - F[i, d]) <= 1e-6 * max(1.0, np.abs(F[i]).max()), (i, d)
+
+
+@pytest.mark.parametrize("s,c", MQ)
+def test_multiquadric_joint_scaling_and_newton(s, c):
+    """x -> 2x together with c -> 2c scales phi by 2^-s and F by 2^-(s+1)
+    (direct sum and FMM: the tree is the same, every level's operators are
+    rebuilt at the new widths); sum_i q_i F_i = 0."""
+    xyz, q = inputs.particles(800, 68, "cube", "sym")
+    p1, F1 = oracle.direct(xyz, q, kernel_s=s, kernel_c=c)
+    p2, F2 = oracle.direct(2.0 * xyz, q, kernel_s=s, kernel_c=2.0 * c)
+    assert oracle.rel_l2(p2, p1 * 2.0 ** -s) <= 1e-13
+    assert oracle.rel_l2(F2, F1 * 2.0 ** -(s + 1)) <= 1e-13
+    net = (q[:, None] * F1).sum(axis=0)
+    assert np.abs(net).max() <= 1e-12 * np.abs(q[:, None] * F1).sum()
+    with oracle.OracleFMM(xyz, q, 4, 5, kernel_s=s, kernel_c=c) as o:
+        pa, Fa = o.evaluate()
+    with oracle.OracleFMM(2.0 * xyz, q, 4, 5, kernel_s=s, kernel_c=2.0 * c) as o:
+        pb, Fb = o.evaluate()
+    assert oracle.rel_l2(pb, pa * 2.0 ** -s) <= 1e-12
+    assert oracle.rel_l2(Fb, Fa * 2.0 ** -(s + 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("s,c", MQ)
+def test_multiquadric_fmm_converges_to_the_direct_sum(s, c):
+    xyz, q = inputs.particles(3000, 69, "cube", "pos")
+    pd, Fd = oracle.direct(xyz, q, kernel_s=s, kernel_c=c)
+    errs = []
+    for p in (3, 5, 7):
+        with oracle.OracleFMM(xyz, q, 4, p, kernel_s=s, kernel_c=c) as o:
+            pf, Ff = o.evaluate()
+        errs.append(max(oracle.rel_l2(pf, pd), oracle.rel_l2(Ff, Fd)))
+    assert errs[0] > 5 * errs[1] > 25 * errs[2], errs
+    assert errs[2] <= 1e-4
+    with oracle.OracleFMM(xyz, q, 2, 4, kernel_s=s, kernel_c=c) as o:
+        p2, F2 = o.evaluate()
+    assert oracle.rel_l2(p2, pd) <= 1e-14 and oracle.rel_l2(F2, Fd) <= 1e-14
