@@ -96,18 +96,25 @@ fmm_status fmm_set_precision(fmm_handle h, int precision);
 fmm_status fmm_set_m2l(fmm_handle h, int method, double eps);
 
 /* Chooses the kernel of later evaluations from the family
- * P(x, y) = |x - y|^-s, 0 < s <= 4 (default s = 1, the Laplace kernel of
- * eq. 2): phi_i = sum_j q_j |x_i - x_j|^-s and F_i = -grad phi_i =
- * s sum_j q_j (x_i - x_j) |x_i - x_j|^-(s+2).  The black-box method of
- * Sec. 2.1 needs nothing but kernel values: the M2L operators become
- * K_t[m][n] = |2t + xbar_n - xbar_m|^-s, scaled per level by a^-s (the kernels
- * are homogeneous of degree -s), their SVDs are recomputed, and the near
- * field evaluates the new kernel (with s != 1 in one kernel shape; see
- * fmm_autotune).  Multiquadrics and the other non-homogeneous kernels of the
- * method would need operators per level and are not offered.  Drops the
- * handle's M2L operators (rebuilt by the next evaluation); synchronises the
- * stream.  Errors: FMM_ERR_ARG (s outside (0, 4]). */
-fmm_status fmm_set_kernel(fmm_handle h, double s);
+ * P(x, y) = (|x - y|^2 + c^2)^(-s/2), -2 <= s <= 4, s != 0, c >= 0 (default
+ * s = 1, c = 0, the Laplace kernel of eq. 2; c = 0: |x - y|^-s; c > 0 the
+ * multiquadrics: s = -1 multiquadric, s = 1 inverse multiquadric, s = 2
+ * inverse quadric).  phi_i = sum_j q_j P(x_i, x_j) and F_i = -grad phi_i =
+ * s sum_j q_j (x_i - x_j) (|x_i - x_j|^2 + c^2)^(-(s+2)/2); pairs at distance 0
+ * are skipped (also for c > 0: a caller wanting the diagonal adds q_i P(0)).
+ * The black-box method (Sec. 2.2) needs nothing but kernel values: the M2L
+ * operators become K_t[m][n] = P_(c/a)(2t + xbar_n - xbar_m) scaled by a^-s
+ * at half-width a.  c = 0 is homogeneous: one set serves every level, and the
+ * compressed operators (fmm_set_m2l) are recomputed for it.  c > 0 is not:
+ * one full-rank set per level 2..h-1 (c/a of that level), rebuilt when the
+ * root width changes; the compression and batches (fmm_set_batch) need c = 0
+ * (with c > 0 the full-rank operators are used whatever fmm_set_m2l chose,
+ * and evaluating a batch fails with FMM_ERR_STATE).  The near field
+ * evaluates the kernel (other than 1/r in one kernel shape; see
+ * fmm_autotune).  Drops the handle's M2L operators (rebuilt by the next
+ * evaluation); synchronises the stream.  Errors: FMM_ERR_ARG (s or c out of
+ * range, or not finite). */
+fmm_status fmm_set_kernel(fmm_handle h, double s, double c);
 
 /* Ranks of the 16 compressed canonical operators, in lexicographic order of
  * their transfer vectors ((0,0,2), (0,0,3), (0,1,2), ..., (3,3,3)), for the
@@ -214,7 +221,7 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * to the grouping of FP32 partial sums.
  * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
- * FMM_P2P_VARIANTS mean launch times.  With a kernel exponent other than 1
+ * FMM_P2P_VARIANTS mean launch times.  With a kernel other than 1/r
  * (fmm_set_kernel) the near field has one shape (4 warps, 256-source chunks,
  * one source per instruction): choice = {-1, 4, 256, 1, 4} and every time is
  * that shape's.  Synchronises the

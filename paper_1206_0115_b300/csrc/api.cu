@@ -10,6 +10,7 @@
 // followed by one plain launch of L2P, which adds the near field and scatters
 // phi and F to the caller's order (its arguments are the caller's output
 // pointers, which change from call to call).
+#include <cmath>
 #include <cstdarg>
 #include <cstdlib>
 #include <map>
@@ -192,7 +193,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
                             (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
-                            (int64_t)(c->kernel_s * 1e6)};
+                            (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9)};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -432,22 +433,26 @@ fmm_status fmm_set_precision(fmm_handle h, int precision) {
   return FMM_OK;
 }
 
-fmm_status fmm_set_kernel(fmm_handle h, double s) {
+fmm_status fmm_set_kernel(fmm_handle h, double s, double kc) {
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
-  if (!(s > 0.0 && s <= 4.0)) return set_err(c, FMM_ERR_ARG, "fmm_set_kernel: exponent %g outside (0, 4]", s);
-  if (s == c->kernel_s) return FMM_OK;
+  if (!(s >= -2.0 && s <= 4.0 && s != 0.0))
+    return set_err(c, FMM_ERR_ARG, "fmm_set_kernel: exponent %g outside [-2, 4] or 0", s);
+  if (!(kc >= 0.0 && std::isfinite(kc))) return set_err(c, FMM_ERR_ARG, "fmm_set_kernel: offset %g", kc);
+  if (s == c->kernel_s && kc == c->kernel_c) return FMM_OK;
   FMM_CUDA(c, cudaSetDevice(c->dev));
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->kernel_s = s;
+  c->kernel_c = kc;
   // the M2L operators are values of the kernel: dropped here, rebuilt by the next evaluation
   const size_t C = (size_t)c->ncoef, cp = (size_t)c->cpad;
-  dfree(c, c->K64, sizeof(double) * FMM_NT * C * C);
-  dfree(c, c->Khi, sizeof(float) * FMM_NT * cp * cp);
-  dfree(c, c->Klo, sizeof(float) * FMM_NT * cp * cp);
+  dfree(c, c->K64, sizeof(double) * FMM_NT * C * C * c->ops64_nb);
+  dfree(c, c->Khi, sizeof(float) * FMM_NT * cp * cp * c->ops32_nb);
+  dfree(c, c->Klo, sizeof(float) * FMM_NT * cp * cp * c->ops32_nb);
   c->K64 = nullptr;
   c->Khi = c->Klo = nullptr;
   c->ops64 = c->ops32 = false;
+  c->ops64_nb = c->ops32_nb = 0;
   c->svd_ready = false;
   c->graph_ok = false;
   return FMM_OK;
@@ -471,6 +476,7 @@ fmm_status fmm_get_svd_ranks(fmm_handle h, int32_t* ranks) {
   Ctx* c = h;
   c->err[0] = 0;
   if (c->leaf < 2) return set_err(c, FMM_ERR_STATE, "fmm_get_svd_ranks: height < 3 has no M2L");
+  if (c->kernel_c > 0.0) return set_err(c, FMM_ERR_STATE, "fmm_get_svd_ranks: no compression with c > 0");
   FMM_CUDA(c, cudaSetDevice(c->dev));
   FMM_TRY(svd_prepare(c));
   for (int k = 0; k < 16; ++k) ranks[k] = c->svd_rank[k];
@@ -586,7 +592,9 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   FMM_CUDA(c, cudaSetDevice(c->dev));
   FMM_TRY(check_device_error(c));
   FMM_TRY(ensure_expansions(c, c->precision));
-  if (c->m2l_method == FMM_M2L_SVD) {
+  if (c->forest && c->kernel_c > 0.0)
+    return set_err(c, FMM_ERR_STATE, "fmm_evaluate: batches need a homogeneous kernel (c = 0)");
+  if (uses_svd(c)) {
     if (c->leaf >= 2) FMM_TRY(m2l_svd_prepare(c));
     if (c->leaf >= 2 && m2l_kind(c) == 5) FMM_TRY(m2l_svd_tc_prepare(c));
   } else {
@@ -637,7 +645,7 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
   c->err[0] = 0;
   if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_autotune: no particles loaded");
   FMM_CUDA(c, cudaSetDevice(c->dev));
-  if (c->kernel_s != 1.0) {
+  if (c->kernel_s != 1.0 || c->kernel_c != 0.0) {
     // one shape of the general-kernel P2P: report its time only
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = -1.f;

@@ -63,12 +63,14 @@ struct LevelPtrs {
   int32_t ncell[FMM_MAX_LEVELS];  // host-known sizes (valid after the readback)
 };
 
-// The kernel family P(x, y) = |x - y|^-s (s = 1: the Laplace kernel of eq. 2;
-// fmm_set_kernel).  A homogeneous kernel: with cell half-width a the M2L
-// operators are K_t / a^s, K_t[m][n] = |2t + xbar_n - xbar_m|^-s.  s = 1 keeps
-// the reciprocal square root exactly as before.
-__host__ __device__ inline double kernel_r2(double r2, double s) {
-  return s == 1.0 ? 1.0 / sqrt(r2) : pow(r2, -0.5 * s);
+// The kernel family P(x, y) = (|x - y|^2 + c^2)^(-s/2) (s = 1, c = 0: the
+// Laplace kernel of eq. 2; fmm_set_kernel).  P(a rho) = a^-s (|rho|^2 +
+// (c/a)^2)^(-s/2): with cell half-width a the M2L operators are a^-s K_t,
+// K_t[m][n] = P_(c/a)(2t + xbar_n - xbar_m), one set for every level when
+// c = 0 (homogeneous), one set per level (c2 = (c/a)^2) when c > 0.  s = 1,
+// c = 0 keeps the reciprocal square root exactly as before.
+__host__ __device__ inline double kernel_r2(double r2, double s, double c2 = 0.0) {
+  return (s == 1.0 && c2 == 0.0) ? 1.0 / sqrt(r2) : pow(r2 + c2, -0.5 * s);
 }
 __host__ __device__ inline double kernel_scale(double inv_a, double s) { return s == 1.0 ? inv_a : pow(inv_a, s); }
 
@@ -100,7 +102,8 @@ struct fmm_ctx {
   using LevelPtrs = fmm::LevelPtrs;
   int height = 0, order = 0, leaf = 0, ncoef = 0, cpad = 0;
   int precision = FMM_MIXED;
-  double kernel_s = 1.0;  // P(x, y) = |x - y|^-kernel_s
+  double kernel_s = 1.0;  // P(x, y) = (|x - y|^2 + kernel_c^2)^(-kernel_s / 2)
+  double kernel_c = 0.0;
   int dev = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t side = nullptr;    // P2P branch
@@ -195,9 +198,13 @@ struct fmm_ctx {
   int8_t* tvec = nullptr;      // [316][3]
   int16_t* cls_t = nullptr;    // [8][189] -> transfer vector index
   int16_t* src_t = nullptr;    // [8][189]: transfer vectors with which a source of the class serves a target
-  double* K64 = nullptr;       // [316][C][C]
-  float *Khi = nullptr, *Klo = nullptr;  // [316][cpad][cpad], TF32 split
+  double* K64 = nullptr;       // [banks][316][C][C]
+  float *Khi = nullptr, *Klo = nullptr;  // [banks][316][cpad][cpad], TF32 split
   bool ops64 = false, ops32 = false;
+  // banks: 1 (homogeneous kernel), or one per level 2..leaf (c > 0), built for
+  // root width ops*_W (c > 0 only)
+  int ops64_nb = 0, ops32_nb = 0;
+  double ops64_W = 0.0, ops32_W = 0.0;
 
   // evaluation schedule
   std::vector<int64_t> graph_sig;  // what the captured graph depends on
@@ -232,6 +239,7 @@ struct fmm_ctx {
   int64_t svd_ecap = 0;
   int64_t svd_gcap = 0;
   const void* tm_khi_ptr = nullptr;
+  int tm_khi_nb = 0;
   int tc_nst = 0, num_sms = 0;
 
   // SVD-compressed M2L (m2l_svd.cu)
@@ -329,6 +337,10 @@ fmm_status work_counts(Ctx* c, int64_t* out);
 // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank operators); 3 FP64 SIMT, 4 FP32 SIMT,
 // 5 tcgen05 (SVD-compressed)
 int m2l_kind(const Ctx* c);
+// The compressed operators need one operator set for every level: c = 0.
+inline bool uses_svd(const Ctx* c) { return c->m2l_method == FMM_M2L_SVD && c->kernel_c == 0.0; }
+// Full-rank operator banks: one, or one per level 2..leaf when c > 0.
+inline int op_banks(const Ctx* c) { return c->kernel_c > 0.0 && c->leaf > 2 ? c->leaf - 1 : 1; }
 
 // ---- device helpers ----------------------------------------------------------
 // Spreads the low 10 bits of v so that bit b lands at bit 3b.

@@ -521,7 +521,7 @@ k_m2l_simt(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
            const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
            const int16_t* __restrict__ cls_t, const T* __restrict__ Khi, const T* __restrict__ Klo,
            int kstride, int C, int cpad, const T* __restrict__ Mhi, const T* __restrict__ Mlo,
-           T* __restrict__ Lout, const double* __restrict__ box, double ks) {
+           T* __restrict__ Lout, const double* __restrict__ box, double ks, int lev_ops) {
   __shared__ T As[16][64];
   __shared__ T Bs[16][64 + 1];
   __shared__ int srow[64];
@@ -548,7 +548,8 @@ k_m2l_simt(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src,
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     const int k = tile_act[(int64_t)tile * FMM_NT_CLASS + a];
-    const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
+    // lev_ops: one operator bank per level 2.. (kernels with c > 0)
+    const int slot = cls_t[tl.cls * FMM_NT_CLASS + k] + (lev_ops ? (l - 2) * FMM_NT : 0);
     __syncthreads();
     if (tid < 64) srow[tid] = tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + half * 64 + tid];
     const T* Kh = Khi + (int64_t)slot * kstride * kstride;
@@ -771,11 +772,12 @@ fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles) {
   const int32_t* nact = c->tile_nact + first_tile;
   if (c->precision == FMM_MIXED)
     k_m2l_simt<float, true><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->Khi, c->Klo, c->cpad,
-                                                 c->ncoef, c->cpad, c->Mhi, c->Mlo, c->L32, c->box, c->kernel_s);
+                                                 c->ncoef, c->cpad, c->Mhi, c->Mlo, c->L32, c->box, c->kernel_s,
+                                                 op_banks(c) > 1);
   else
     k_m2l_simt<double, false><<<grid, 256, 0, s>>>(tiles, src, act, nact, c->lv, c->cls_t, c->K64, nullptr,
                                                    c->ncoef, c->ncoef, c->cpad, c->M64, nullptr, c->L64,
-                                                   c->box, c->kernel_s);
+                                                   c->box, c->kernel_s, op_banks(c) > 1);
   return cuda_err(c, cudaGetLastError(), "M2L launch");
 }
 

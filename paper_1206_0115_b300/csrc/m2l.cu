@@ -7,7 +7,7 @@
 namespace fmm {
 
 int m2l_kind(const Ctx* c) {
-  if (c->m2l_method == FMM_M2L_SVD) {
+  if (uses_svd(c)) {
     if (c->precision == FMM_FP64) return 3;
     return (c->use_tc && m2l_svd_tc_supported(c)) ? 5 : 4;
   }

@@ -59,6 +59,7 @@ struct TcArgs {
   float* partial;  // [group][tile][128][cpad]
   int32_t* err;    // nonzero after a timed-out wait
   int ntiles, groups, gt, cpad, nh, nhalf, kchunks, nst;
+  int lev_ops;         // one operator bank per level 2.. (kernels with c > 0)
   uint32_t acol;       // first TMEM column of the A stages (after the two accumulators)
   uint32_t tmem_cols;  // power of two >= 2 * nhalf + 32 * nst
 };
@@ -150,7 +151,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
           continue;
         }
         const int k = a.tile_act[(int64_t)tile * FMM_NT_CLASS + ai];
-        const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k];
+        const int slot = a.cls_t[tl.cls * FMM_NT_CLASS + k] + (a.lev_ops ? (tl.level - 2) * FMM_NT : 0);
         const int64_t src = rbase + a.tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
         const float* ghi = Mhi + src * a.cpad;
         const float* glo = Mlo + src * a.cpad;
@@ -388,11 +389,14 @@ fmm_status m2l_tc_prepare(Ctx* c) {
     c->tc_err = (int32_t*)p;
     FMM_CUDA(c, cudaMemsetAsync(c->tc_err, 0, 64, c->stream));
   }
-  if (c->tm_khi_ptr != c->Khi) {
-    bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, cp, (uint64_t)FMM_NT * cp, TC_KC, nhalf) &&
-              encode_2d((CUtensorMap*)c->tm_klo, c->Klo, cp, (uint64_t)FMM_NT * cp, TC_KC, nhalf);
+  const int nb = op_banks(c);
+  if (c->tm_khi_ptr != c->Khi || c->tm_khi_nb != nb) {
+    const uint64_t rows = (uint64_t)FMM_NT * cp * nb;
+    bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, cp, rows, TC_KC, nhalf) &&
+              encode_2d((CUtensorMap*)c->tm_klo, c->Klo, cp, rows, TC_KC, nhalf);
     if (!ok) return set_err(c, FMM_ERR_CUDA, "M2L tensor path: cuTensorMapEncodeTiled failed");
     c->tm_khi_ptr = c->Khi;
+    c->tm_khi_nb = nb;
   }
   int nst = (227 * 1024 - tc_fixed_bytes(cp)) / tc_stage_bytes(cp);
   const int tmem_stages = (512 - 2 * (cp / tc_nh(cp))) / 32;  // A stages beside the two accumulators
@@ -435,6 +439,7 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   a.nhalf = nhalf;
   a.kchunks = cp / TC_KC;
   a.nst = c->tc_nst;
+  a.lev_ops = op_banks(c) > 1;
   a.acol = (uint32_t)(2 * nhalf);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < 2 * nhalf + 32 * c->tc_nst) a.tmem_cols <<= 1;

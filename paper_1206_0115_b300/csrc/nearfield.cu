@@ -576,14 +576,15 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   }
 }
 
-// ---- the kernel family |x - y|^-s, s != 1 ----------------------------------
+// ---- the kernel family (|x - y|^2 + c^2)^(-s/2), other than 1/r -----------
 // The same work items, staging and exact hi/lo differences as k_p2p32; per
-// pair phi += q r^-s and F += s q d r^-(s+2) (F = -grad phi), with
-// r^-s = 2^(-s/2 log2 r^2) and 1/r^2 on the MUFU pipe.
+// pair, with e = r^2 + c^2 (c in leaf widths), phi += q e^(-s/2) and
+// F += s q d e^(-(s+2)/2) (F = -grad phi), e^(-s/2) = 2^(-s/2 log2 e) and 1/e
+// on the MUFU pipe.  Pairs at distance 0 are skipped, also when c > 0.
 template <int G, bool SELF>
 __device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, const float4* __restrict__ slo, int k0,
-                                             int k1, float4 th, float4 tl, float hs, float sk, float& fphi,
-                                             float& fx, float& fy, float& fz) {
+                                             int k1, float4 th, float4 tl, float hs, float sk, float cw2,
+                                             float& fphi, float& fx, float& fy, float& fz) {
 #pragma unroll 4
   for (int k = k0; k < k1; k += G) {
     const float4 sh = shi[k], sl = slo[k];
@@ -591,8 +592,9 @@ __device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, con
     const float dy = (th.y - sh.y) + (tl.y - sl.y);
     const float dz = (th.z - sh.z) + (tl.z - sl.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float ps = exp2f(-hs * __log2f(r2));
-    float ir2 = __frcp_rn(r2);
+    const float e = r2 + cw2;
+    float ps = exp2f(-hs * __log2f(e));
+    float ir2 = __frcp_rn(e);
     if (SELF) {
       ps = r2 > 0.f ? ps : 0.f;
       ir2 = r2 > 0.f ? ir2 : 0.f;
@@ -610,7 +612,7 @@ template <int W, int CH>
 __global__ void __launch_bounds__(W * 32)
 k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of, int nitems,
          const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-         double ks, float4* __restrict__ out) {
+         double ks, double kc, float4* __restrict__ out) {
   __shared__ float4 shi[W][CH];
   __shared__ float4 slo[W][CH];
   __shared__ int nb_first[W][27];
@@ -668,6 +670,8 @@ k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_
     tl = pos32lo[tf + tb + ti];
   }
   const float hs = (float)(0.5 * ks), sk = (float)ks;
+  const double ckw = kc / ldexp(box[3], -leaf);  // c in leaf widths
+  const float cw2 = (float)(ckw * ckw);
   Kahan kp, kx, ky, kz;
   for (int c0 = 0; c0 < total; c0 += CH) {
     const int cn = min(CH, total - c0);
@@ -697,9 +701,9 @@ k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_
     switch (g) {
 #define SPAN_POW(G)                                                                               \
   case G: {                                                                                       \
-    p2p_span_pow<G, true>(sh, sl, sub, kown, th, tl, hs, sk, fphi, fx, fy, fz);                   \
+    p2p_span_pow<G, true>(sh, sl, sub, kown, th, tl, hs, sk, cw2, fphi, fx, fy, fz);              \
     const int k0 = kown + ((sub - kown) % G + G) % G;                                             \
-    p2p_span_pow<G, false>(sh, sl, k0, cn, th, tl, hs, sk, fphi, fx, fy, fz);                     \
+    p2p_span_pow<G, false>(sh, sl, k0, cn, th, tl, hs, sk, cw2, fphi, fx, fy, fz);                \
   } break;
       SPAN_POW(1) SPAN_POW(2) SPAN_POW(4) SPAN_POW(8) SPAN_POW(16) SPAN_POW(32)
 #undef SPAN_POW
@@ -728,7 +732,7 @@ k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_
 __global__ void __launch_bounds__(P2P_WARPS * 32)
 k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
         int nitems,
-        const double4* __restrict__ pos64, double ks, double4* __restrict__ out) {
+        const double4* __restrict__ pos64, double ks, double kc2, double4* __restrict__ out) {
   __shared__ double4 src[P2P_WARPS][P2P_CH];
   __shared__ int nb_first[P2P_WARPS][27];
   __shared__ int nb_pre[P2P_WARPS][28];
@@ -793,13 +797,14 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, co
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 > 0.0) {
           double q1, q3;
-          if (ks == 1.0) {
+          if (ks == 1.0 && kc2 == 0.0) {
             const double rr = sqrt(r2);
             q1 = pp.w / rr;
             q3 = pp.w / (rr * r2);
-          } else {  // |x - y|^-s: phi += q r^-s, F += s q d r^-(s+2)
-            q1 = pp.w * pow(r2, -0.5 * ks);
-            q3 = ks * q1 / r2;
+          } else {  // e = r^2 + c^2: phi += q e^(-s/2), F += s q d e^(-(s+2)/2)
+            const double e = r2 + kc2;
+            q1 = pp.w * pow(e, -0.5 * ks);
+            q3 = ks * q1 / e;
           }
           aphi += q1;
           ax += q3 * dx;
@@ -867,9 +872,10 @@ void p2p_carveout() {
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
-  if (c->precision == FMM_MIXED && c->kernel_s != 1.0) {
+  if (c->precision == FMM_MIXED && (c->kernel_s != 1.0 || c->kernel_c != 0.0)) {
     k_p2p32s<4, 256><<<ceil_div(c->p2p_nitems, 4), 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems,
-                                                                 c->pos32, c->pos32lo, c->box, c->kernel_s, c->near32);
+                                                                 c->pos32, c->pos32lo, c->box, c->kernel_s,
+                                                                 c->kernel_c, c->near32);
   } else if (c->precision == FMM_MIXED) {
 #define P2P_LAUNCH(W, CH)                                                                              \
   k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,   \
@@ -907,7 +913,7 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   } else
     k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
                                                                           c->p2p_nitems, c->pos64, c->kernel_s,
-                                                                          c->near64);
+                                                                          c->kernel_c * c->kernel_c, c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");
 }
 

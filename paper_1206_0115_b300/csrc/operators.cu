@@ -10,7 +10,9 @@
 //    K_t[m][n] = 1 / |2t + xbar_n - xbar_m| (3-vectors, multi-index z
 //    fastest), computed on the GPU in FP64 and kept as FP64 and, for the
 //    mixed path, in mean-split form (see k_m2l_ops_split) as TF32 hi/lo pairs
-//    (hi = tf32(v), lo = tf32(v - hi)).
+//    (hi = tf32(v), lo = tf32(v - hi)).  Other kernels (fmm_set_kernel): the
+//    same formula with P = (r^2 + c2)^(-s/2), scaled by a^-s; with c > 0 one
+//    bank per level, c2 = (c / a_l)^2 for that level's half-width a_l.
 #include <cmath>
 #include <vector>
 
@@ -28,7 +30,7 @@ __device__ inline float tf32_rna(float x) {
 
 // FP64 bank: K_t[m][n] for m, n < C.
 __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, const int8_t* __restrict__ tvec,
-                            double ks, double* __restrict__ K64) {
+                            double ks, double c2, double* __restrict__ K64) {
   const int64_t total = (int64_t)FMM_NT * C * C;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -42,7 +44,7 @@ __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, cons
       const double r = 2.0 * tvec[3 * t + d] + nodes[ni[d]] - nodes[mi[d]];
       r2 += r * r;
     }
-    K64[i] = kernel_r2(r2, ks);
+    K64[i] = kernel_r2(r2, ks, c2);
   }
 }
 
@@ -52,7 +54,7 @@ __global__ void k_m2l_ops64(int p, int C, const double* __restrict__ nodes, cons
 // (rows < C) as separate FP32 numbers; every value is split into TF32 hi/lo.
 // One thread per (t, n).
 __global__ void k_m2l_ops_split(int p, int C, int cpad, const double* __restrict__ nodes,
-                                const int8_t* __restrict__ tvec, double ks, float* __restrict__ Khi,
+                                const int8_t* __restrict__ tvec, double ks, double c2, float* __restrict__ Khi,
                                 float* __restrict__ Klo) {
   const int64_t total = (int64_t)FMM_NT * cpad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -74,7 +76,7 @@ __global__ void k_m2l_ops_split(int p, int C, int cpad, const double* __restrict
         const double r = y[d] - nodes[mi[d]];
         r2 += r * r;
       }
-      return kernel_r2(r2, ks);
+      return kernel_r2(r2, ks, c2);
     };
     double mean = 0.0;
     for (int m = 0; m < C; ++m) mean += K(m);
@@ -196,32 +198,58 @@ fmm_status operators_init(Ctx* c) {
   return FMM_OK;
 }
 
-// M2L operator banks for one precision, built on first use.
+// M2L operator banks for one precision, built on first use.  With c > 0 the
+// banks depend on the root width: they are regenerated in place (same
+// buffers, so captured graphs stay valid) when the width changes, and
+// reallocated when the number of levels does.
 fmm_status operators_m2l(Ctx* c, int precision) {
   const int p = c->order, C = c->ncoef, cp = c->cpad;
   if (c->leaf < 2) return FMM_OK;
-  const bool want64 = precision == FMM_FP64 && !c->ops64;
-  const bool want32 = precision == FMM_MIXED && !c->ops32;
-  if (!want64 && !want32) return FMM_OK;
+  const int nb = op_banks(c);
+  const double W = c->kernel_c > 0.0 ? c->box_host[3] : 0.0;
+  const bool mixed = precision == FMM_MIXED;
+  bool& built = mixed ? c->ops32 : c->ops64;
+  int& bnb = mixed ? c->ops32_nb : c->ops64_nb;
+  double& bW = mixed ? c->ops32_W : c->ops64_W;
+  if (built && bnb == nb && bW == W) return FMM_OK;
+  const size_t bank64 = (size_t)FMM_NT * C * C, bank32 = (size_t)FMM_NT * cp * cp;
   void* ptr;
-  if (want64) {
-    FMM_TRY(dalloc(c, &ptr, sizeof(double) * (size_t)FMM_NT * C * C));
-    c->K64 = (double*)ptr;
+  if (built && bnb != nb) {  // a tree with another number of levels
+    if (mixed) {
+      dfree(c, c->Khi, sizeof(float) * bank32 * bnb);
+      dfree(c, c->Klo, sizeof(float) * bank32 * bnb);
+      c->Khi = c->Klo = nullptr;
+    } else {
+      dfree(c, c->K64, sizeof(double) * bank64 * bnb);
+      c->K64 = nullptr;
+    }
+    built = false;
+    c->graph_ok = false;
   }
-  if (want32) {
-    FMM_TRY(dalloc(c, &ptr, sizeof(float) * (size_t)FMM_NT * cp * cp));
+  if (mixed && !c->Khi) {
+    FMM_TRY(dalloc(c, &ptr, sizeof(float) * bank32 * nb));
     c->Khi = (float*)ptr;
-    FMM_TRY(dalloc(c, &ptr, sizeof(float) * (size_t)FMM_NT * cp * cp));
+    FMM_TRY(dalloc(c, &ptr, sizeof(float) * bank32 * nb));
     c->Klo = (float*)ptr;
   }
-  if (want64) k_m2l_ops64<<<1184, 256, 0, c->stream>>>(p, C, c->nodes64, c->tvec, c->kernel_s, c->K64);
-  if (want32) k_m2l_ops_split<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(p, C, cp, c->nodes64,
-                                                                                           c->tvec, c->kernel_s,
-                                                                                           c->Khi, c->Klo);
+  if (!mixed && !c->K64) {
+    FMM_TRY(dalloc(c, &ptr, sizeof(double) * bank64 * nb));
+    c->K64 = (double*)ptr;
+  }
+  for (int b = 0; b < nb; ++b) {
+    // bank b serves level 2 + b (c > 0): c / a_l = c 2^(l+1) / W
+    const double ca = c->kernel_c > 0.0 ? c->kernel_c * std::ldexp(1.0, 2 + b + 1) / W : 0.0;
+    if (mixed)
+      k_m2l_ops_split<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(
+          p, C, cp, c->nodes64, c->tvec, c->kernel_s, ca * ca, c->Khi + bank32 * b, c->Klo + bank32 * b);
+    else
+      k_m2l_ops64<<<1184, 256, 0, c->stream>>>(p, C, c->nodes64, c->tvec, c->kernel_s, ca * ca, c->K64 + bank64 * b);
+  }
   FMM_CUDA(c, cudaGetLastError());
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (want64) c->ops64 = true;
-  if (want32) c->ops32 = true;
+  built = true;
+  bnb = nb;
+  bW = W;
   return FMM_OK;
 }
 

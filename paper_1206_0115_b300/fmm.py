@@ -38,7 +38,7 @@ _SIGS = {
     "fmm_set_stream": [_vp, _vp],
     "fmm_set_precision": [_vp, C.c_int],
     "fmm_set_m2l": [_vp, C.c_int, C.c_double],
-    "fmm_set_kernel": [_vp, C.c_double],
+    "fmm_set_kernel": [_vp, C.c_double, C.c_double],
     "fmm_get_svd_ranks": [_vp, _vp],
     "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
     "fmm_set_batch": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
@@ -135,8 +135,8 @@ def fmm_set_precision(h, precision: int) -> int:
     return _check(h, lib.fmm_set_precision(h, precision))
 
 
-def fmm_set_kernel(h, s: float) -> int:
-    return _check(h, lib.fmm_set_kernel(h, float(s)))
+def fmm_set_kernel(h, s: float, c: float = 0.0) -> int:
+    return _check(h, lib.fmm_set_kernel(h, float(s), float(c)))
 
 
 def fmm_set_m2l(h, method: int, eps: float = 0.0) -> int:
@@ -327,13 +327,14 @@ class FMM:
     arrays; every step runs in the CUDA library."""
 
     def __init__(self, height: int, order: int, precision: int = FMM_MIXED, stream=None,
-                 m2l: int = FMM_M2L_SVD, svd_eps: float = 0.0, kernel_s: float = 1.0):
+                 m2l: int = FMM_M2L_SVD, svd_eps: float = 0.0, kernel_s: float = 1.0,
+                 kernel_c: float = 0.0):
         self.h = fmm_create(height, order)
         self.height, self.order = height, order
         fmm_set_precision(self.h, precision)
         fmm_set_m2l(self.h, m2l, svd_eps)
-        if kernel_s != 1.0:
-            fmm_set_kernel(self.h, kernel_s)
+        if kernel_s != 1.0 or kernel_c != 0.0:
+            fmm_set_kernel(self.h, kernel_s, kernel_c)
         if stream is not None:
             fmm_set_stream(self.h, stream)
         self.n = 0
@@ -361,9 +362,10 @@ class FMM:
     def set_m2l(self, method: int, eps: float = 0.0):
         fmm_set_m2l(self.h, method, eps)
 
-    def set_kernel(self, s: float):
-        """Kernel |x - y|^-s of later evaluations (s = 1: Laplace)."""
-        fmm_set_kernel(self.h, s)
+    def set_kernel(self, s: float, c: float = 0.0):
+        """Kernel (|x - y|^2 + c^2)^(-s/2) of later evaluations (s = 1, c = 0:
+        Laplace)."""
+        fmm_set_kernel(self.h, s, c)
 
     def svd_ranks(self) -> np.ndarray:
         return fmm_get_svd_ranks(self.h)
