@@ -61,6 +61,7 @@ def lib():
             "ofmm_direct_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_double, _d, _d]),
             "ofmm_direct_sampled_kernel": (None, [C.c_int64, _d, _d, C.c_double, C.c_double, C.c_int64, _i64, _d, _d]),
             "ofmm_set_kernel": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+            "ofmm_stokes_direct": (None, [C.c_int64, _d, _d, _d]),
             "ofmm_direct_sampled": (None, [C.c_int64, _d, _d, C.c_int64, _i64, _d, _d]),
         }
         for name, (res, args) in sig.items():
@@ -130,6 +131,41 @@ def direct_sampled(xyz, q, idx, kernel_s: float = 1.0, kernel_c: float = 0.0):
     lib().ofmm_direct_sampled_kernel(xyz.shape[0], _p(xyz, _d), _p(q, _d), float(kernel_s), float(kernel_c), idx.shape[0],
                                      _p(idx, _i64), _p(phi, _d), _p(F, _d))
     return phi, F
+
+
+def stokes_direct(xyz, f):
+    """Stokeslet sums u_i = sum_{k != i} [f_k / r + d (d . f_k) / r^3],
+    d = x_i - x_k (the Stokes kernel, unit viscosity factor), by O(N^2)
+    summation."""
+    xyz = _f64(xyz).reshape(-1, 3)
+    f = _f64(f).reshape(-1, 3)
+    u = np.zeros_like(xyz)
+    lib().ofmm_stokes_direct(xyz.shape[0], _p(xyz, _d), _p(f, _d), _p(u, _d))
+    return u
+
+
+def stokes_fmm(xyz, f, height: int, order: int, svd_eps=None):
+    """The Stokeslet sums from four 1/r FMM passes on one tree.  With
+    phi^j, F^j = -grad phi^j the 1/r potentials and fields of the charges
+    f_j (j = 0, 1, 2) and phi^3, F^3 those of the charges y . f,
+
+        u_i = phi^i + sum_j x_j F^j_i - F^3_i,
+
+    because d (d . f) / r^3 = -grad_x(1/r) ((x . f) - (y . f)).  The identity
+    holds for any origin; positions are used as given."""
+    xyz = _f64(xyz).reshape(-1, 3)
+    f = _f64(f).reshape(-1, 3)
+    charges = [f[:, 0], f[:, 1], f[:, 2], (xyz * f).sum(axis=1)]
+    phis, Fs = [], []
+    for q in charges:
+        with OracleFMM(xyz, np.ascontiguousarray(q), height, order, svd_eps=svd_eps) as o:
+            ph, F = o.evaluate()
+        phis.append(ph)
+        Fs.append(F)
+    u = np.zeros_like(xyz)
+    for i in range(3):
+        u[:, i] = phis[i] + sum(xyz[:, j] * Fs[j][:, i] for j in range(3)) - Fs[3][:, i]
+    return u
 
 
 # SVD-compressed M2L (Sec. 2.1.2): cube symmetries, canonical vectors, Jacobi SVD

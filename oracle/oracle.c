@@ -1128,6 +1128,26 @@ void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, d
   for (int64_t s = 0; s < ns; ++s) direct_one(n, xyz, q, ks, kc, idx[s], &phi[s], &F[3 * s]);
 }
 
+/* Stokeslet sums (the Stokes kernel of the black-box method, unit viscosity
+ * factor): u_i = sum_{k != i, r > 0} [ f_k / r + d (d . f_k) / r^3 ],
+ * d = x_i - x_k, r = |d|; xyz [n][3], f [n][3], u [n][3]. */
+void ofmm_stokes_direct(int64_t n, const double* xyz, const double* f, double* u) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < n; ++k) {
+      if (k == i) continue;
+      double d[3] = {xyz[3 * i] - xyz[3 * k], xyz[3 * i + 1] - xyz[3 * k + 1], xyz[3 * i + 2] - xyz[3 * k + 2]};
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (r2 == 0.0) continue;
+      double r = sqrt(r2);
+      double df = d[0] * f[3 * k] + d[1] * f[3 * k + 1] + d[2] * f[3 * k + 2];
+      for (int e = 0; e < 3; ++e) acc[e] += f[3 * k + e] / r + d[e] * df / (r * r2);
+    }
+    for (int e = 0; e < 3; ++e) u[3 * i + e] = acc[e];
+  }
+}
+
 void ofmm_direct(int64_t n, const double* xyz, const double* q, double* phi, double* F) {
   ofmm_direct_kernel(n, xyz, q, 1.0, 0.0, phi, F);
 }

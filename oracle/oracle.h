@@ -123,6 +123,9 @@ void ofmm_direct_kernel(int64_t n, const double* xyz, const double* q, double s,
                         double* F);
 void ofmm_direct_sampled_kernel(int64_t n, const double* xyz, const double* q, double s, double kc, int64_t ns,
                                 const int64_t* idx, double* phi, double* F);
+/* Stokeslet sums u_i = sum_{k != i} [ f_k / r + d (d . f_k) / r^3 ], d = x_i - x_k
+ * (pairs at distance 0 skipped); f, u [n][3]. */
+void ofmm_stokes_direct(int64_t n, const double* xyz, const double* f, double* u);
 void ofmm_direct_sampled(int64_t n, const double* xyz, const double* q, int64_t ns,
                          const int64_t* idx, double* phi, double* F);
 

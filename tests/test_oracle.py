@@ -718,3 +718,64 @@ def test_multiquadric_fmm_converges_to_the_direct_sum(s, c):
     with oracle.OracleFMM(xyz, q, 2, 4, kernel_s=s, kernel_c=c) as o:
         p2, F2 = o.evaluate()
     assert oracle.rel_l2(p2, pd) <= 1e-14 and oracle.rel_l2(F2, Fd) <= 1e-14
+
+
+# ---- the Stokes kernel (Stokeslet, unit viscosity factor):
+# u_i = sum_k [f_k / r + d (d . f_k) / r^3], d = x_i - x_k.
+
+def _forces(n, seed):
+    return np.stack([inputs.charges(n, seed + k, "sym", 0) for k in range(3)], axis=1)
+
+
+def test_stokeslet_hand_values():
+    # x1 = 0, x2 = (1, 0, 0), f1 = 0, f2 = (1, 2, 3): d = (-1, 0, 0), r = 1,
+    # u1 = f2 + d (d . f2) = (1, 2, 3) + (-1, 0, 0)(-1) = (2, 2, 3); u2 = 0
+    u = oracle.stokes_direct(np.array([[0.0, 0, 0], [1.0, 0, 0]]), np.array([[0.0, 0, 0], [1.0, 2, 3]]))
+    assert np.array_equal(u, np.array([[2.0, 2, 3], [0, 0, 0]]))
+    # x2 = (0, 2, 0), f1 = (-1, 0, 2), f2 = (1, 1, 1): r = 2;
+    # u1 = f2 / 2 + (0, -2, 0)(-2) / 8 = (0.5, 1.0, 0.5); u2 = f1 / 2 (d . f1 = 0)
+    u = oracle.stokes_direct(np.array([[0.0, 0, 0], [0.0, 2, 0]]), np.array([[-1.0, 0, 2], [1.0, 1, 1]]))
+    assert np.allclose(u, np.array([[0.5, 1.0, 0.5], [-0.5, 0.0, 1.0]]), rtol=0, atol=1e-15)
+
+
+def test_stokeslet_field_is_divergence_free_and_reciprocal():
+    """Away from the sources the Stokeslet field has zero divergence (probe:
+    a particle with zero force, moved by central differences); the kernel is
+    symmetric and even, so <f, U g> = <g, U f>."""
+    xyz, _ = inputs.particles(50, 94, "cube", "pos")
+    f = _forces(50, 95)
+    probe = np.array([0.37, 0.52, 0.61])
+    h = 1e-4
+    div, scale = 0.0, 0.0
+    for d in range(3):
+        vals = []
+        for sgn in (1.0, -1.0):
+            x = np.vstack([xyz, probe + sgn * h * np.eye(3)[d]])
+            ff = np.vstack([f, np.zeros((1, 3))])
+            vals.append(oracle.stokes_direct(x, ff)[-1])
+        g = (vals[0] - vals[1]) / (2 * h)
+        div += g[d]
+        scale += np.abs(g).sum()
+    assert abs(div) <= 1e-6 * scale
+    g2 = _forces(50, 98)
+    a = (f * oracle.stokes_direct(xyz, g2)).sum()
+    b = (g2 * oracle.stokes_direct(xyz, f)).sum()
+    assert abs(a - b) <= 1e-13 * abs(a)
+
+
+def test_stokes_from_four_laplace_passes():
+    """Trees of height <= 2 make every 1/r pass a direct sum, so the identity
+    u_i = phi^i + sum_j x_j F^j_i - F^3_i must give the Stokeslet sum to
+    rounding, for any origin (points shifted far from it too); with a far
+    field the error falls with the order."""
+    xyz, _ = inputs.particles(1500, 96, "cube", "sym")
+    f = _forces(1500, 97)
+    ud = oracle.stokes_direct(xyz, f)
+    for h in (1, 2):
+        assert oracle.rel_l2(oracle.stokes_fmm(xyz, f, h, 4), ud) <= 1e-13
+    shifted = xyz + np.array([5.0, -3.0, 2.0])
+    assert oracle.rel_l2(oracle.stokes_direct(shifted, f), ud) <= 1e-13
+    assert oracle.rel_l2(oracle.stokes_fmm(shifted, f, 2, 4), ud) <= 1e-12
+    errs = [oracle.rel_l2(oracle.stokes_fmm(xyz, f, 4, p), ud) for p in (3, 5, 7)]
+    assert errs[0] > 5 * errs[1] > 25 * errs[2], errs
+    assert errs[2] <= 3e-5
