@@ -116,6 +116,22 @@ fmm_status fmm_set_m2l(fmm_handle h, int method, double eps);
  * range, or not finite). */
 fmm_status fmm_set_kernel(fmm_handle h, double s, double c);
 
+/* Stokes kernel (Sec. 2.2 names it with Laplace among the kernels of the
+ * black-box method): velocities u_i = sum_k [f_k / r + d (d . f_k) / r^3],
+ * d = x_i - x_k, r = |d| (the Stokeslet with unit viscosity factor: multiply
+ * by 1/(8 pi mu) for a fluid of viscosity mu), at the handle's particles
+ * (fmm_set_particles; their charges are not used) for forces f [n][3]
+ * (caller order, host or device); u [n][3] (host or device).  Computed from
+ * four 1/r passes on the handle's tree, with the charges f_x, f_y, f_z and
+ * (y - o) . f (o = the root cube's centre):
+ *     u_i = phi^i + sum_j (x_i - o)_j F^j_i - F^3_i,
+ * since d (d . f) / r^3 = -grad_x(1/r) ((x - o) . f - (y - o) . f); the
+ * handle's precision, M2L form and P2P variant apply to each pass.  The
+ * handle's charges are restored afterwards.  Pairs at distance 0 are
+ * skipped.  Synchronises the stream for host output.  Errors: FMM_ERR_STATE
+ * (no particles, a batch, or a kernel other than 1/r), FMM_ERR_ARG. */
+fmm_status fmm_evaluate_stokes(fmm_handle h, const double* f, double* u);
+
 /* Ranks of the 16 compressed canonical operators, in lexicographic order of
  * their transfer vectors ((0,0,2), (0,0,3), (0,1,2), ..., (3,3,3)), for the
  * handle's order and the eps of fmm_set_m2l; computes the SVDs if they are

@@ -193,7 +193,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
                             (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
-                            (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9)};
+                            (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -382,7 +382,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->p2p_leaf, c->p2p_units, c->p2p_uoff,
                   c->near32,
                   c->near64,
-                  c->stage_in, c->stage_out, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
+                  c->stage_in, c->stage_out, c->stokes_buf, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
@@ -623,6 +623,59 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   if (!dev_out) {
     FMM_CUDA(c, cudaMemcpyAsync(phi, dphi, sizeof(double) * n, cudaMemcpyDefault, c->stream));
     FMM_CUDA(c, cudaMemcpyAsync(F, dF, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+    FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_evaluate_stokes(fmm_handle h, const double* f, double* u) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_evaluate_stokes: no particles loaded");
+  if (c->forest) return set_err(c, FMM_ERR_STATE, "fmm_evaluate_stokes: single problems only");
+  if (c->kernel_s != 1.0 || c->kernel_c != 0.0)
+    return set_err(c, FMM_ERR_STATE, "fmm_evaluate_stokes: needs the 1/r kernel");
+  const int64_t n = c->n;
+  if (n == 0) return FMM_OK;
+  if (!f || !u) return set_err(c, FMM_ERR_ARG, "fmm_evaluate_stokes: NULL argument");
+  FMM_CUDA(c, cudaSetDevice(c->dev));
+  FMM_TRY(ensure_stage(c, &c->stokes_buf, &c->stokes_cap, 27 * n));
+  float4* f32 = (float4*)c->stokes_buf;    // [n] forces, Morton order (mixed)
+  float4* unear = f32 + n;                 // [n] Stokeslet near field, Morton order (mixed)
+  double* phi4 = c->stokes_buf + 4 * n;    // [4][n]
+  double* F4 = phi4 + 4 * n;               // [4][n][3]
+  double* q0 = F4 + 12 * n;                // [n] the loaded charges, Morton order
+  double* df = q0 + n;                     // [n][3] forces on the device
+  double* du = df + 3 * n;                 // [n][3] result on the device
+  const double* fd = f;
+  if (!is_device_ptr(f)) {
+    FMM_CUDA(c, cudaMemcpyAsync(df, f, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+    fd = df;
+  }
+  const bool dev_out = is_device_ptr(u);
+  // Mixed precision: the four 1/r passes give the far field only and the
+  // near field is the Stokeslet summed directly (the identity's terms are
+  // |x - o| / r times the result there, too much for FP32 on close pairs);
+  // FP64 takes all of u from the four passes.
+  const bool mixed = c->precision == FMM_MIXED;
+  FMM_TRY(launch_stokes_save(c, q0));
+  fmm_status st = FMM_OK;
+  c->skip_p2p = mixed;
+  for (int j = 0; j < 4 && st == FMM_OK; ++j) {
+    st = launch_stokes_charges(c, fd, q0, j);
+    if (st == FMM_OK) st = fmm_evaluate(h, phi4 + j * n, F4 + 3 * j * n);
+  }
+  c->skip_p2p = false;
+  if (st == FMM_OK && mixed) st = launch_stokes_forces(c, fd, f32);
+  if (st == FMM_OK && mixed) st = launch_p2p_stokes(c, c->stream, f32, unear);
+  if (st == FMM_OK) st = launch_stokes_combine(c, phi4, F4, mixed ? unear : nullptr, dev_out ? u : du);
+  // the handle's own charges come back whatever happened above
+  const fmm_status rs = launch_stokes_charges(c, nullptr, q0, -1);
+  if (st != FMM_OK) return st;
+  if (rs != FMM_OK) return rs;
+  if (!dev_out) {
+    FMM_CUDA(c, cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
     FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return FMM_OK;

@@ -137,6 +137,9 @@ struct fmm_ctx {
   double4* near64 = nullptr;
   double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
   int64_t stage_in_cap = 0, stage_out_cap = 0;
+  double* stokes_buf = nullptr;  // fmm_evaluate_stokes: 4 passes' outputs, saved charges, forces, result
+  int64_t stokes_cap = 0;
+  bool skip_p2p = false;         // evaluations without the near field (the Stokes far-field passes)
 
   // scratch
   uint32_t* scratch = nullptr;
@@ -337,6 +340,12 @@ fmm_status work_counts(Ctx* c, int64_t* out);
 // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank operators); 3 FP64 SIMT, 4 FP32 SIMT,
 // 5 tcgen05 (SVD-compressed)
 int m2l_kind(const Ctx* c);
+// Stokes from four 1/r passes (stokes.cu)
+fmm_status launch_stokes_save(Ctx* c, double* q0);
+fmm_status launch_stokes_charges(Ctx* c, const double* f, const double* q0, int j);
+fmm_status launch_stokes_combine(Ctx* c, const double* phi4, const double* F4, const float4* unear, double* u);
+fmm_status launch_stokes_forces(Ctx* c, const double* f, float4* f32);
+fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* out);
 // The compressed operators need one operator set for every level: c = 0.
 inline bool uses_svd(const Ctx* c) { return c->m2l_method == FMM_M2L_SVD && c->kernel_c == 0.0; }
 // Full-rank operator banks: one, or one per level 2..leaf when c > 0.

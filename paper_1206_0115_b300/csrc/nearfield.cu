@@ -728,6 +728,148 @@ k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_
   }
 }
 
+// ---- the Stokeslet near field (fmm_evaluate_stokes, mixed precision) ------
+// Work items, staging and exact hi/lo differences of k_p2p32, with each
+// source's force staged beside its position: per pair u += f / r +
+// d (d . f) / r^3 directly, in leaf widths (u scales by 1/w).  The four 1/r
+// passes that give the far field would give the near field only as a
+// difference of terms |x - o| / r times larger than it, which FP32 cannot
+// carry for close pairs.
+template <int G, bool SELF>
+__device__ __forceinline__ void p2p_span_stokes(const float4* __restrict__ shi, const float4* __restrict__ slo,
+                                                const float4* __restrict__ sfo, int k0, int k1, float4 th, float4 tl,
+                                                float& ux, float& uy, float& uz) {
+#pragma unroll 4
+  for (int k = k0; k < k1; k += G) {
+    const float4 sh = shi[k], sl = slo[k], sf = sfo[k];
+    const float dx = (th.x - sh.x) + (tl.x - sl.x);
+    const float dy = (th.y - sh.y) + (tl.y - sl.y);
+    const float dz = (th.z - sh.z) + (tl.z - sl.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float inv = rsqrtf(r2);
+    if (SELF) inv = r2 > 0.f ? inv : 0.f;
+    const float t = fmaf(dx, sf.x, fmaf(dy, sf.y, dz * sf.z)) * (inv * inv * inv);
+    ux = fmaf(sf.x, inv, fmaf(dx, t, ux));
+    uy = fmaf(sf.y, inv, fmaf(dy, t, uy));
+    uz = fmaf(sf.z, inv, fmaf(dz, t, uz));
+  }
+}
+
+template <int W, int CH>
+__global__ void __launch_bounds__(W * 32)
+k_p2p_stokes32(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+               int nitems, const float4* __restrict__ pos32, const float4* __restrict__ pos32lo,
+               const float4* __restrict__ f32, const double* __restrict__ box, float4* __restrict__ out) {
+  __shared__ float4 shi[W][CH];
+  __shared__ float4 slo[W][CH];
+  __shared__ float4 sfo[W][CH];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * W + warp;
+  if (item >= nitems) return;
+  const int T = leaf_of[item];
+  const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
+  const int tb = (item - items[T]) * 32;
+  int ix, iy, iz;
+  demorton3(lv.key[leaf][T], ix, iy, iz);
+  const int top = (1 << leaf) - 1;
+  const int mine = problem_of(lv, leaf, T);
+  int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
+  if (lane < 27) {
+    const int k = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+    ox = k / 9 - 1;
+    oy = (k / 3) % 3 - 1;
+    oz = k % 3 - 1;
+    const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
+    if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
+      const int g = lv.grid[leaf][morton3(sx, sy, sz)];
+      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
+        nf = lv.first[leaf][g];
+        ncnt = lv.count[leaf][g];
+      }
+    }
+  }
+  int incl = ncnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane < 27) {
+    nb_first[warp][lane] = nf;
+    nb_pre[warp][lane] = incl - ncnt;
+    nb_off[warp][lane][0] = (int8_t)ox;
+    nb_off[warp][lane][1] = (int8_t)oy;
+    nb_off[warp][lane][2] = (int8_t)oz;
+  }
+  if (lane == 0) nb_pre[warp][27] = total;
+  __syncwarp();
+  const int own = tc;
+  const int nt = min(32, tc - tb);
+  int lg = 0;
+  while ((nt << (lg + 1)) <= 32) ++lg;
+  const int g = 1 << lg, ti = lane >> lg, sub = lane & (g - 1);
+  const bool tvalid = ti < nt;
+  float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+  if (tvalid) {
+    th = pos32[tf + tb + ti];
+    tl = pos32lo[tf + tb + ti];
+  }
+  Kahan kx, ky, kz;
+  for (int c0 = 0; c0 < total; c0 += CH) {
+    const int cn = min(CH, total - c0);
+    __syncwarp();
+    for (int k = lane; k < cn; k += 32) {
+      const int sidx = c0 + k;
+      int lo = 0, hi = 26;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nb_pre[warp][mid] <= sidx) lo = mid;
+        else hi = mid - 1;
+      }
+      const int j = nb_first[warp][lo] + (sidx - nb_pre[warp][lo]);
+      float4 ph = pos32[j];
+      ph.x += (float)nb_off[warp][lo][0];
+      ph.y += (float)nb_off[warp][lo][1];
+      ph.z += (float)nb_off[warp][lo][2];
+      shi[warp][k] = ph;
+      slo[warp][k] = pos32lo[j];
+      sfo[warp][k] = f32[j];
+    }
+    __syncwarp();
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    const int kown = min(cn, max(0, own - c0));
+    const float4* sh = &shi[warp][0];
+    const float4* sl = &slo[warp][0];
+    const float4* sf = &sfo[warp][0];
+    switch (g) {
+#define SPAN_ST(G)                                                                                \
+  case G: {                                                                                       \
+    p2p_span_stokes<G, true>(sh, sl, sf, sub, kown, th, tl, ux, uy, uz);                          \
+    const int k0 = kown + ((sub - kown) % G + G) % G;                                             \
+    p2p_span_stokes<G, false>(sh, sl, sf, k0, cn, th, tl, ux, uy, uz);                            \
+  } break;
+      SPAN_ST(1) SPAN_ST(2) SPAN_ST(4) SPAN_ST(8) SPAN_ST(16) SPAN_ST(32)
+#undef SPAN_ST
+    }
+    kx.add(ux);
+    ky.add(uy);
+    kz.add(uz);
+  }
+  float ax = kx.s, ay = ky.s, az = kz.s;
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+  if (tvalid && sub == 0) {
+    const float iw = (float)(1.0 / ldexp(box[3], -leaf));
+    out[tf + tb + ti] = make_float4(ax * iw, ay * iw, az * iw, 0.f);
+  }
+}
+
 // FP64: positions as given, exact skip of r = 0.
 __global__ void __launch_bounds__(P2P_WARPS * 32)
 k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
@@ -846,7 +988,8 @@ bool is_p2p_kernel(const void* f) {
                       (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                       (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
                       (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
-                      (const void*)k_p2p32s<4, 256>,     (const void*)k_p2p64};
+                      (const void*)k_p2p32s<4, 256>,     (const void*)k_p2p_stokes32<4, 128>,
+                      (const void*)k_p2p64};
   for (const void* k : ks)
     if (k == f) return true;
   return false;
@@ -872,6 +1015,11 @@ void p2p_carveout() {
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
+  if (c->skip_p2p) {  // far field only (fmm_evaluate_stokes): no near part
+    void* nb = c->precision == FMM_MIXED ? (void*)c->near32 : (void*)c->near64;
+    const size_t bytes = (c->precision == FMM_MIXED ? sizeof(float4) : sizeof(double4)) * (size_t)c->n;
+    return cuda_err(c, cudaMemsetAsync(nb, 0, bytes, s), "P2P skip");
+  }
   if (c->precision == FMM_MIXED && (c->kernel_s != 1.0 || c->kernel_c != 0.0)) {
     k_p2p32s<4, 256><<<ceil_div(c->p2p_nitems, 4), 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems,
                                                                  c->pos32, c->pos32lo, c->box, c->kernel_s,
@@ -915,6 +1063,17 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
                                                                           c->p2p_nitems, c->pos64, c->kernel_s,
                                                                           c->kernel_c * c->kernel_c, c->near64);
   return cuda_err(c, cudaGetLastError(), "P2P launch");
+}
+
+// Stokeslet near field of the loaded tree for forces f32 (Morton order,
+// float4 (f, 0)); out [n] float4 (u, 0) in Morton order.
+fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* out) {
+  const int Lf = c->leaf;
+  if (c->lv.ncell[Lf] == 0 || c->p2p_nitems == 0) return FMM_OK;
+  k_p2p_stokes32<4, 128><<<ceil_div(c->p2p_nitems, 4), 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf,
+                                                                    c->p2p_nitems, c->pos32, c->pos32lo, f32, c->box,
+                                                                    out);
+  return cuda_err(c, cudaGetLastError(), "Stokes P2P launch");
 }
 
 }  // namespace fmm

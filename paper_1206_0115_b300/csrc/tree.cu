@@ -1266,6 +1266,8 @@ void release_tree(Ctx* c) {
   rel(c->stage_in, 8 * (size_t)c->stage_in_cap);
   rel(c->stage_out, 8 * (size_t)c->stage_out_cap);
   c->stage_in_cap = c->stage_out_cap = 0;
+  rel(c->stokes_buf, 8 * (size_t)c->stokes_cap);
+  c->stokes_cap = 0;
   for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
     const size_t lc = 4 * (size_t)c->lcap[l];
     rel(c->lv.key[l], lc);

@@ -39,6 +39,7 @@ _SIGS = {
     "fmm_set_precision": [_vp, C.c_int],
     "fmm_set_m2l": [_vp, C.c_int, C.c_double],
     "fmm_set_kernel": [_vp, C.c_double, C.c_double],
+    "fmm_evaluate_stokes": [_vp, _vp, _vp],
     "fmm_get_svd_ranks": [_vp, _vp],
     "fmm_set_particles": [_vp, C.c_int64, _vp, _vp],
     "fmm_set_batch": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
@@ -137,6 +138,10 @@ def fmm_set_precision(h, precision: int) -> int:
 
 def fmm_set_kernel(h, s: float, c: float = 0.0) -> int:
     return _check(h, lib.fmm_set_kernel(h, float(s), float(c)))
+
+
+def fmm_evaluate_stokes(h, f, u) -> int:
+    return _check(h, lib.fmm_evaluate_stokes(h, _ptr(f), _ptr(u)))
 
 
 def fmm_set_m2l(h, method: int, eps: float = 0.0) -> int:
@@ -385,6 +390,10 @@ class FMM:
 
     def evaluate(self, phi, F):
         fmm_evaluate(self.h, phi, F)
+
+    def evaluate_stokes(self, f, u):
+        """Stokeslet velocities u [n][3] of forces f [n][3] at the particles."""
+        fmm_evaluate_stokes(self.h, f, u)
 
     def order_perm(self, out):
         fmm_get_order(self.h, out)
