@@ -33,6 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "cube_n1m_h6_p7"
+# the same cube under every kernel of fmm_set_kernel and the Stokes path
+KERNELS_WORKLOAD = "kernels_cube_n1m_h6_p7"
 METRIC = "FMM particles/s at rel.err<=1e-5 vs FP64 direct; P2P/M2L % roofline; p50/p99 ms"
 UNIT = "particles/s"
 # the CPU oracle is timed once on the full workload (about 30 s on 16 cores);
@@ -888,10 +890,90 @@ def run_serving(args):
     print(json.dumps(result))
 
 
+def run_kernels(args):
+    """One step (fmm_set_particles + evaluation) of the 1e6-point cube (h 6,
+    p 7, mixed) for each kernel: 1/r (the reference line), |x - y|^-s
+    (compressed M2L), multiquadrics (c > 0: full-rank operators per level)
+    and Stokes (fmm_evaluate_stokes: four 1/r passes + the direct Stokeslet
+    near field).  Each: CUDA events on the library's stream, L2 flushed
+    between steps, operators and SVDs built during the warm-up."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0115_b300 import build, inputs
+    build.build()
+    from paper_1206_0115_b300 import fmm
+
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = dict(inputs.WORKLOADS[WORKLOAD])
+    xyz_np, q_np = inputs.particles(w["n"], w["seed"], w["dist"], w["qkind"])
+    n, h, p = w["n"], w["height"], w["order"]
+    f_np = np.ascontiguousarray(np.stack([inputs.charges(n, 7 + k, "sym", 0) for k in range(3)], axis=1))
+    xyz = torch.from_numpy(xyz_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    fo = torch.from_numpy(f_np).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    u = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    cases = [("laplace 1/r", 1.0, 0.0, fmm.FMM_M2L_SVD, False),
+             ("|x-y|^-2", 2.0, 0.0, fmm.FMM_M2L_SVD, False),
+             ("|x-y|^-0.5", 0.5, 0.0, fmm.FMM_M2L_SVD, False),
+             ("|x-y| (s = -1)", -1.0, 0.0, fmm.FMM_M2L_SVD, False),
+             ("inverse multiquadric c = 0.01", 1.0, 0.01, fmm.FMM_M2L_FULL, False),
+             ("multiquadric c = 0.01", -1.0, 0.01, fmm.FMM_M2L_FULL, False),
+             ("stokes", 1.0, 0.0, fmm.FMM_M2L_SVD, True)]
+    out = {}
+    clocks = Clocks(local)
+    clocks.start()
+    for name, ks, kc, m2l, stokes in cases:
+        with fmm.FMM(h, p, fmm.FMM_MIXED, stream=stream, m2l=m2l, kernel_s=ks, kernel_c=kc) as hd:
+            def step():
+                hd.set_particles(xyz, q)
+                if stokes:
+                    hd.evaluate_stokes(fo, u)
+                else:
+                    hd.evaluate(phi, F)
+            for _ in range(max(args.warmup, 1)):
+                step()
+            torch.cuda.synchronize()
+            ms = []
+            for k in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(k))
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = statistics.median(ms)
+            out[name] = {"ms_per_step": round(t, 4), "value": round(n / (t * 1e-3), 1),
+                         "m2l": "compressed" if m2l == fmm.FMM_M2L_SVD else "full-rank per level"}
+    clk = clocks.stop()
+    base = out["laplace 1/r"]["ms_per_step"]
+    for v in out.values():
+        v["relative_to_laplace"] = round(v["ms_per_step"] / base, 3)
+    print(json.dumps({"metric": "particles/s per kernel (one step: tree build + evaluation)", "unit": UNIT,
+                      "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32 (mixed: FP32 near field, 3xTF32 M2L, FP64 accumulation of outputs)",
+                      "data": "synthetic", "config": {"workload": KERNELS_WORKLOAD, "n": n, "height": h,
+                                                      "order": p, "precision": "mixed", "l2": "flushed"},
+                      "kernels": out, "clocks": clk}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == KERNELS_WORKLOAD:
+        run_kernels(args)
     elif args.workload == BATCH_WORKLOAD:
         run_batched(args)
     elif args.workload == SERVE_WORKLOAD:

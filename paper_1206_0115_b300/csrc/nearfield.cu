@@ -580,7 +580,8 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
 // The same work items, staging and exact hi/lo differences as k_p2p32; per
 // pair, with e = r^2 + c^2 (c in leaf widths), phi += q e^(-s/2) and
 // F += s q d e^(-(s+2)/2) (F = -grad phi), e^(-s/2) = 2^(-s/2 log2 e) and 1/e
-// on the MUFU pipe.  Pairs at distance 0 are skipped, also when c > 0.
+// on the MUFU pipe (three MUFU operations per pair against one rsqrt for
+// 1/r).  Pairs at distance 0 are skipped, also when c > 0.
 template <int G, bool SELF>
 __device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, const float4* __restrict__ slo, int k0,
                                              int k1, float4 th, float4 tl, float hs, float sk, float cw2,
@@ -594,7 +595,7 @@ __device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, con
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float e = r2 + cw2;
     float ps = exp2f(-hs * __log2f(e));
-    float ir2 = __frcp_rn(e);
+    float ir2 = __fdividef(1.f, e);  // approximate reciprocal (one MUFU op, ~1 ulp)
     if (SELF) {
       ps = r2 > 0.f ? ps : 0.f;
       ir2 = r2 > 0.f ? ir2 : 0.f;
