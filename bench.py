@@ -45,7 +45,19 @@ REFERENCE_STEP_SAMPLE = dict(n=15_625, height=4, order=7, dist="cube", qkind="sy
 
 FP32_LANES_PER_SM = 128
 NUM_SMS = 148
-TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates
+TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (FP16 runs at the BF16 rate)
+
+
+def m2l_math(stats) -> str:
+    """Operand form of the tensor-core M2L: FP16 hi/lo pairs (compressed
+    operators, the default) or TF32 hi/lo pairs."""
+    return "f16x3" if int(stats[4]) == 5 and int(stats[5]) == 1 else "tf32x3"
+
+
+def tensor_peak(pk, math: str):
+    if math == "f16x3":
+        return pk["bf16"], f"FP16 = {pk['src']} bf16 (the same dense rate)"
+    return pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
 # FP32 operations of one P2P interaction as the mixed kernel issues them: the
 # exact difference (hi_t - hi_s) + (lo_t - lo_s) per axis (9), the squared
 # distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential sum (1)
@@ -399,6 +411,8 @@ def run_ours(args):
     p2p_ms = float(iso[5])  # P2P alone
     # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank K_t); 3 FP64 SIMT, 4 FP32 SIMT (compressed)
     m2l_kind = int(stats[4])
+    math = m2l_math(stats)
+    mlabel = "3xFP16" if math == "f16x3" else "3xTF32"
     m2l_pairs = int(work[1:12].sum())
     if m2l_kind >= 3:
         # compressed: y = V^T M (2 C r flop) and L += U y (2 C r flop) per pair
@@ -414,7 +428,8 @@ def run_ours(args):
     tc_path = m2l_kind in (2, 5)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if tc_path:
-        bound, peak, peak_note = "tensor", pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
+        peak, peak_note = tensor_peak(pk, math)
+        bound = "tensor"
     elif m2l_kind in (1, 4):
         bound, peak, peak_note = "alu", fp32_peak, "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock"
     else:
@@ -425,7 +440,7 @@ def run_ours(args):
     cpad = ((C + 1 + 31) // 32) * 32
     if m2l_kind == 5:
         # the dominant kernel is the expansion; each half carries 2 C r flop per pair
-        kernel_name = "k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, 3xTF32), all levels"
+        kernel_name = f"k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels"
         half_flop = m2l_flop / 2.0
         m2l_ms = float(kt[1])
         achieved = half_flop / (m2l_ms / 1e3) / 1e12
@@ -434,15 +449,17 @@ def run_ours(args):
         traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
                                     "int sp_ngroups(int Rp)")
                    if args.workload == WORKLOAD else None)
-        # MMAs issued: projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, 3xTF32
+        # MMAs issued: projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, three
+        # products per multiply (hi hi, hi lo, lo hi)
         hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
         hw_e = 3 * 2.0 * 128 * cpad * int(work[15])
-        tensor_pipe = {"expansion": {"mma_flop_per_launch": hw_e, "tflops": hw_e / (kt[1] / 1e3) / 1e12,
-                                     "frac_of_tf32_peak": hw_e / (kt[1] / 1e3) / 1e12 / peak},
+        tensor_pipe = {"operands": math,
+                       "expansion": {"mma_flop_per_launch": hw_e, "tflops": hw_e / (kt[1] / 1e3) / 1e12,
+                                     "frac_of_peak": hw_e / (kt[1] / 1e3) / 1e12 / peak},
                        "projection": {"mma_flop_per_launch": hw_p, "tflops": hw_p / (kt[0] / 1e3) / 1e12,
-                                      "frac_of_tf32_peak": hw_p / (kt[0] / 1e3) / 1e12 / peak}}
+                                      "frac_of_peak": hw_p / (kt[0] / 1e3) / 1e12 / peak}}
         ach_p = half_flop / (kt[0] / 1e3) / 1e12
-        roofline_proj = {"kernel": "k_svd_proj_tc (compressed M2L projection y = V^T M, tcgen05, 3xTF32)",
+        roofline_proj = {"kernel": f"k_svd_proj_tc (compressed M2L projection y = V^T M, tcgen05, {mlabel})",
                          "bound": "tensor", "achieved": ach_p, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach_p / peak, "ms": float(kt[0]), "peak_source": peak_note}
     elif m2l_kind == 2:
@@ -468,7 +485,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64",
+        "dtype": f"f32+{math}" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "height": h, "order": p, "precision": args.precision,
                    "m2l": args.m2l,
@@ -626,7 +643,9 @@ def run_batched(args):
     pk = peaks()
     C = p ** 3
     cpad = ((C + 1 + 31) // 32) * 32
-    peak = pk["bf16"] * TF32_OVER_BF16
+    math = m2l_math(stats)
+    mlabel = "3xFP16" if math == "f16x3" else "3xTF32"
+    peak, peak_note = tensor_peak(pk, math)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
     half_flop = 2.0 * C * int(work[13])
@@ -636,7 +655,7 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "dtype": f"f32+{math}" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "problems": int(len(counts)), "n_total": n,
                    "n_min": int(counts.min()), "n_max": int(counts.max()),
                    "heights": {str(hh): int((heights == hh).sum()) for hh in sorted(set(heights.tolist()))},
@@ -650,17 +669,18 @@ def run_batched(args):
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
         "roofline": None if kt is None else {
-            "kernel": "k_svd_expand_tc (compressed M2L expansion, tcgen05, 3xTF32), all problems and levels",
+            "kernel": f"k_svd_expand_tc (compressed M2L expansion, tcgen05, {mlabel}), all problems and levels",
             "bound": "tensor", "achieved": half_flop / (kt[1] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": half_flop / (kt[1] / 1e3) / 1e12 / peak, "traffic": None, "ms": float(kt[1]),
             "algorithmic": f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch",
-            "peak_source": f"TF32 = {pk['src']} bf16 x 1.1/2.25"},
+            "peak_source": peak_note},
         "roofline_m2l_projection": None if kt is None else {
             "kernel": "k_svd_proj_tc", "achieved": half_flop / (kt[0] / 1e3) / 1e12, "peak": peak,
             "unit": "TFLOP/s", "frac": half_flop / (kt[0] / 1e3) / 1e12 / peak, "ms": float(kt[0])},
         "tensor_pipe": None if kt is None else {
-            "expansion_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
-            "projection_frac_of_tf32_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
+            "operands": math,
+            "expansion_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
+            "projection_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
         "autotune": tuned,
         "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)", "interactions": p2p_pairs,
                          "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
@@ -859,7 +879,10 @@ def run_serving(args):
     result = {
         "metric": METRIC, "value": parts / span, "unit": UNIT, "n_gpus": 1, "steps": nreq,
         "warmup": len(warm), "ms_per_step": 1e3 * span / nreq, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None,
+        # the server's handles take the library's default operand form unless FMM_M2L_MATH=tf32
+        "dtype": ("f32+" + ("tf32x3" if os.environ.get("FMM_M2L_MATH") == "tf32" else "f16x3"))
+                 if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": SERVE_WORKLOAD, "rate_rps": rate, "duration_s": seconds, "requests": nreq,
                    "n_range": [10_000, 5_000_000], "orders": [5, 7], "heights": "3..8 by size",
                    "distribution": "cube", "lanes": lanes, "hbm_budget_bytes": budget,
@@ -962,7 +985,8 @@ def run_kernels(args):
         v["relative_to_laplace"] = round(v["ms_per_step"] / base, 3)
     print(json.dumps({"metric": "particles/s per kernel (one step: tree build + evaluation)", "unit": UNIT,
                       "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "dtype": "f32 (mixed: FP32 near field, 3xTF32 M2L, FP64 accumulation of outputs)",
+                      "dtype": "f32 (mixed: FP32 near field, tensor-core M2L on FP16 hi/lo operands (TF32 for the "
+                               "full-rank banks), FP64 accumulation of outputs)",
                       "data": "synthetic", "config": {"workload": KERNELS_WORKLOAD, "n": n, "height": h,
                                                       "order": p, "precision": "mixed", "l2": "flushed"},
                       "kernels": out, "clocks": clk}))

@@ -193,7 +193,8 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
                             (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
-                            (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p};
+                            (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p,
+                            c->m2l_f16};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -319,6 +320,10 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   {
     const char* e = getenv("FMM_M2L_KERNEL");  // "simt": CUDA-core M2L in mixed precision too
     c->use_tc = !(e && strcmp(e, "simt") == 0);
+    // compressed tensor-core M2L operands: FP16 hi/lo pairs (default, twice the
+    // TF32 MMA rate) or "tf32": TF32 hi/lo pairs
+    const char* mm = getenv("FMM_M2L_MATH");
+    c->m2l_f16 = !(mm && strcmp(mm, "tf32") == 0);
     const char* pr = getenv("FMM_P2P_PRIORITY");  // "0": every graph node at the default priority
     c->p2p_priority = !(pr && strcmp(pr, "0") == 0);
     if (c->p2p_priority) p2p_carveout();
@@ -387,7 +392,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
-                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx,
+                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax,
                   c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_sstart, c->fb_sprob, c->fb_bstart};
   // back to the pool on the handle's own side stream (both streams are idle)
   for (void* b : bufs)
@@ -847,7 +852,8 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out) {
   out[2] = h->use_graph ? 1 : 0;
   out[3] = h->bytes;
   out[4] = m2l_kind(h);
-  out[5] = out[6] = out[7] = 0;
+  out[5] = h->m2l_f16 ? 1 : 0;
+  out[6] = out[7] = 0;
   return FMM_OK;
 }
 

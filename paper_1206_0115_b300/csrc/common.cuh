@@ -263,6 +263,11 @@ struct fmm_ctx {
   float* svd_VThi = nullptr;  // mixed projection factors, interleaved hi/lo slabs per class (m2l_svd.cu)
   float* svd_Uhi = nullptr;   // mixed expansion factors, interleaved hi/lo slabs, mean-split
   size_t svd_vt_bytes = 0, svd_u_bytes = 0;
+  // compressed tensor-core M2L with FP16 hi/lo operands (m2l_f16): the mixed
+  // banks' format, their scales, and per-level max |M| and |Y| (device words)
+  bool m2l_f16 = false, svd_bank_f16 = false;
+  float svd_vscale = 1.f, svd_uscale = 1.f;
+  uint32_t* svd_umax = nullptr;  // [2][FMM_MAX_LEVELS]
   std::vector<int32_t> svd_yoff_h;
   int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_yoff = nullptr;  // [316], [316], [8][316]
   int64_t svd_YS = 0;            // Y values per cell row
@@ -348,6 +353,9 @@ fmm_status launch_stokes_forces(Ctx* c, const double* f, float4* f32);
 fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* out);
 // The compressed operators need one operator set for every level: c = 0.
 inline bool uses_svd(const Ctx* c) { return c->m2l_method == FMM_M2L_SVD && c->kernel_c == 0.0; }
+// The mixed compressed factor banks are FP16 hi/lo pairs (the tensor-core
+// kernels' FP16 form) or TF32 hi/lo pairs.
+bool svd_wants_f16(const Ctx* c);
 // Full-rank operator banks: one, or one per level 2..leaf when c > 0.
 inline int op_banks(const Ctx* c) { return c->kernel_c > 0.0 && c->leaf > 2 ? c->leaf - 1 : 1; }
 

@@ -248,6 +248,46 @@ __global__ void k_svd_banks32(int C, int cpad, int64_t YS, const int8_t* __restr
   }
 }
 
+// The same banks with FP16 hi/lo operands for the tensor-core kernels' FP16
+// form: 32 values of the contracted index per 64-byte row (two per 32-bit
+// word, the even one in the low half), V scaled by vscale and U by uscale
+// (powers of two that keep them below 2^13):
+//   VT row G = (cls * (cpad / 32) + n / 32) * YS + yoff[cls][t] + i,
+//   U row  G = ((i / 32) * 316 + t) * cpad + sigma.m (mean row C).
+// Halves are stored one by one (threads of different n share a word).
+__device__ inline void put_h(uint16_t* b, int64_t G, int e, double x) {
+  const __half h = __float2half_rn((float)x);
+  const __half l = __float2half_rn((float)(x - (double)__half2float(h)));
+  b[2 * tc::il_idx(G, 0, e >> 1) + (e & 1)] = __half_as_ushort(h);
+  b[2 * tc::il_idx(G, 1, e >> 1) + (e & 1)] = __half_as_ushort(l);
+}
+
+__global__ void k_svd_banks16(int C, int cpad, int64_t YS, const int8_t* __restrict__ t_canon,
+                              const int16_t* __restrict__ sm, const int32_t* __restrict__ ord,
+                              const int32_t* __restrict__ rank, const double* __restrict__ W,
+                              const double* __restrict__ Z, const double* __restrict__ colmean,
+                              const int32_t* __restrict__ yoff, double vscale, double uscale,
+                              uint16_t* __restrict__ VT, uint16_t* __restrict__ U) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)FMM_NT * C) return;
+  const int t = (int)(e / C), n = (int)(e - (int64_t)t * C);
+  const int k = t_canon[t], r = rank[k];
+  const int np = sm[e];
+  const int kch = cpad / 32;
+  for (int i = 0; i < r; ++i) {
+    const int j = ord[k * C + i];
+    const double v = Z[((size_t)k * C + j) * C + n] * vscale;
+    const double u = (W[((size_t)k * C + j) * C + n] - colmean[k * C + j]) * uscale;
+    for (int cls = 0; cls < 8; ++cls) {
+      const int yo = yoff[cls * FMM_NT + t];
+      if (yo < 0) continue;
+      put_h(VT, ((int64_t)cls * kch + (np >> 5)) * YS + yo + i, np & 31, v);
+    }
+    put_h(U, ((int64_t)(i >> 5) * FMM_NT + t) * cpad + np, i & 31, u);
+    if (n == 0) put_h(U, ((int64_t)(i >> 5) * FMM_NT + t) * cpad + C, i & 31, colmean[k * C + j] * uscale);
+  }
+}
+
 // ---------------------------------------------------------------- evaluation
 
 struct SvdArgs {
@@ -552,11 +592,14 @@ fmm_status svd_banks(Ctx* c) {
     FMM_CUDA(c, cudaStreamSynchronize(s));
     c->svd64 = true;
   }
-  if (c->precision == FMM_MIXED && !c->svd32) {
-    // VT: 8 classes x cpad/16 chunks x YS rows; U: Rp/16 chunks x 316 x cpad rows; 2 halves x 16 floats per row
+  const bool f16 = c->precision == FMM_MIXED && svd_wants_f16(c);
+  if (c->precision == FMM_MIXED && (!c->svd32 || c->svd_bank_f16 != f16)) {
+    // TF32: VT 8 classes x cpad/16 chunks x YS rows, U Rp/16 chunks x 316 x cpad rows, 2 halves x 16 floats
+    // per row; FP16: chunks of 32 (cpad/32, ceil(Rp/32)), 2 halves x 32 FP16 per row (the same 128 bytes)
     const int Rp = c->svd_rp;
-    const size_t vbytes = sizeof(float) * 32 * (size_t)8 * (cp / 16) * c->svd_YS;
-    const size_t ubytes = sizeof(float) * 32 * (size_t)(Rp / 16) * FMM_NT * cp;
+    const int kw = f16 ? 32 : 16;
+    const size_t vbytes = sizeof(float) * 32 * (size_t)8 * (cp / kw) * c->svd_YS;
+    const size_t ubytes = sizeof(float) * 32 * (size_t)((Rp + kw - 1) / kw) * FMM_NT * cp;
     dfree(c, c->svd_VThi, c->svd_vt_bytes);
     dfree(c, c->svd_Uhi, c->svd_u_bytes);
     c->svd_VThi = c->svd_Uhi = nullptr;
@@ -568,11 +611,25 @@ fmm_status svd_banks(Ctx* c) {
     FMM_CUDA(c, cudaMemsetAsync(ptr, 0, ubytes, s));
     c->svd_vt_bytes = vbytes;
     c->svd_u_bytes = ubytes;
-    k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
-                                       c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, c->svd_VThi, c->svd_Uhi);
+    if (f16) {
+      // |U entries| <= 2 s_max (columns of U Sigma and their means), |V entries| <= 1
+      std::vector<double> sv((size_t)16 * C);
+      FMM_CUDA(c, cudaMemcpy(sv.data(), c->svd_vals, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost));
+      double smax = 0.0;
+      for (double v : sv) smax = std::max(smax, std::fabs(v));
+      c->svd_vscale = tc::pow2_scale(1.0f);
+      c->svd_uscale = tc::pow2_scale((float)(2.0 * smax));
+      k_svd_banks16<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
+                                         c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, (double)c->svd_vscale,
+                                         (double)c->svd_uscale, (uint16_t*)c->svd_VThi, (uint16_t*)c->svd_Uhi);
+    } else {
+      k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
+                                         c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, c->svd_VThi, c->svd_Uhi);
+    }
     FMM_CUDA(c, cudaGetLastError());
     FMM_CUDA(c, cudaStreamSynchronize(s));
     c->svd32 = true;
+    c->svd_bank_f16 = f16;
   }
   return FMM_OK;
 }

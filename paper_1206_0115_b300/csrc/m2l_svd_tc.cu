@@ -85,9 +85,14 @@ struct ProjArgs {
   float* Y;
   int32_t* err;
   int64_t YS;
-  int64_t mrows;         // rows of the class-ordered multipole copy per chunk of 16 coefficients
+  int64_t mrows;         // rows of the class-ordered multipole copy per chunk of coefficients
   const float *Mc, *VT;  // interleaved hi/lo slabs (il_idx)
   int ntiles, ngroups, kchunks, nst;
+  // FP16 operands: per-level max |M| (float bits; M scaled by pow2_scale of it),
+  // the VT bank's scale, and per-level max |Y| written here for the expansion
+  const uint32_t* mmax;
+  uint32_t* ymax;
+  float vscale;
 };
 
 // Greedy grouping of each tile's active source transfer vectors into units
@@ -175,6 +180,45 @@ __global__ void k_gather_cls(int l, LevelPtrs lv, McBase mb, int cpad, int64_t r
   }
 }
 
+// FP16 operands: the largest |M| of each level 2.. (float bits, atomicMax;
+// non-negative floats order like their bits).  Grid over the levels' rows;
+// a level's zero row adds nothing.
+__global__ void __launch_bounds__(256)
+k_m_absmax(LevelPtrs lv, int lmin, int lmax, int cpad, const float* __restrict__ Mhi,
+           const float* __restrict__ Mlo, uint32_t* __restrict__ mmax) {
+  const int64_t r0 = lv.row_off[lmin], r1 = lv.row_off[lmax] + lv.ncell[lmax] + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t r = r0 + (int64_t)blockIdx.x * 8 + warp; r < r1; r += (int64_t)gridDim.x * 8) {
+    int l = lmin;
+    while (l < lmax && r >= lv.row_off[l + 1]) ++l;
+    float m = 0.f;
+    for (int k = lane; k < cpad; k += 32) m = fmaxf(m, fabsf(Mhi[r * cpad + k] + Mlo[r * cpad + k]));
+    const uint32_t mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if (lane == 0 && mb) atomicMax(mmax + l, mb);
+  }
+}
+
+// k_gather_cls with FP16 operands: the same rows, 32 coefficients per row
+// (chunk kc = k / 32), two per 32-bit word, scaled by the level's
+// pow2_scale(max |M|).  One block per cell, a thread per pair of coefficients.
+__global__ void k_gather_cls16(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
+                               const float* __restrict__ Mlo, const uint32_t* __restrict__ mmax,
+                               uint32_t* __restrict__ Mc) {
+  const int j = blockIdx.x;
+  const int cell = lv.cls[l][j];
+  const int c = lv.key[l][cell] & 7;
+  const int64_t row = mb.base[l][c] + (j - mb.clsoff[l][c]), src = (lv.row_off[l] + cell) * cpad;
+  const float sc = pow2_scale(__uint_as_float(mmax[l]));
+  for (int k = 2 * threadIdx.x; k < cpad; k += 2 * blockDim.x) {
+    const int64_t G = (int64_t)(k >> 5) * rows + row;
+    uint32_t hi, lo;
+    split_h2((Mhi[src + k] + Mlo[src + k]) * sc, (Mhi[src + k + 1] + Mlo[src + k + 1]) * sc, hi, lo);
+    const int w = (k & 31) >> 1;
+    Mc[il_idx(G, 0, w)] = hi;
+    Mc[il_idx(G, 1, w)] = lo;
+  }
+}
+
 __device__ inline ProjRec load_rec(const ProjRec* p) {
   ProjRec r;
   const int4* s = (const int4*)p;
@@ -188,6 +232,10 @@ __device__ inline void st_cs_v4(float* p, float a, float b, float c, float d) {
   asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
+// F16: operands are FP16 hi/lo pairs (32 coefficients per 64-byte row, one
+// MMA of K = 16 per half row, at twice the TF32 rate; M scaled per level, VT
+// by vscale, both undone exactly in the epilogue); otherwise TF32 hi/lo.
+template <bool F16>
 __global__ void __launch_bounds__(SP_THREADS, 1)
 k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
   extern __shared__ unsigned char smem_raw[];
@@ -305,7 +353,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       const uint32_t d0 = tmem + (uint32_t)(b * SP_ACC);
       // the group's factors are stacked in the stage, so one MMA of
       // N = sum of the ranks covers every transfer vector of the group
-      const uint32_t idesc = idesc_tf32(FMM_TILE, cols);
+      const uint32_t idesc = F16 ? idesc_f16(FMM_TILE, cols) : idesc_tf32(FMM_TILE, cols);
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
         const int s = (int)(it % a.nst);
         const uint32_t ph = (it / a.nst) & 1u;
@@ -321,9 +369,15 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
           for (int ks = 0; ks < 2; ++ks) {
             const uint64_t ahi = sdesc_sw64s(st + ks * 32u, 1024), alo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
             const uint64_t bhi = sdesc_sw64s(sb + ks * 32u, 1024), blo = sdesc_sw64s(sb + 512u + ks * 32u, 1024);
-            mma_tf32(d0, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(d0, ahi, blo, idesc, 1u);
-            mma_tf32(d0, alo, bhi, idesc, 1u);
+            if (F16) {
+              mma_f16(d0, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+              mma_f16(d0, ahi, blo, idesc, 1u);
+              mma_f16(d0, alo, bhi, idesc, 1u);
+            } else {
+              mma_tf32(d0, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+              mma_tf32(d0, ahi, blo, idesc, 1u);
+              mma_tf32(d0, alo, bhi, idesc, 1u);
+            }
           }
           mma_commit(empty(s));
         }
@@ -361,12 +415,22 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       }
       tc_fence_after();
       const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * SP_ACC);
+      // F16: back from the operands' scales (powers of two: exact)
+      const float inv = F16 ? 1.f / (pow2_scale(__uint_as_float(a.mmax[g.level])) * a.vscale) : 1.f;
+      float vmax = 0.f;
       int off = 0;
       for (int q = 0; q < g.n; ++q) {
         float* y = a.Y + cellrow * a.YS + 16 * g.yo16[q];
         for (int c16 = 0; c16 < 16 * g.ry16[q]; c16 += 16) {
           float v[16];
           tmem_ld16(tb + (uint32_t)(off + c16), v);
+          if (F16) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              v[i] *= inv;
+              vmax = fmaxf(vmax, fabsf(v[i]));
+            }
+          }
           if (valid) {
             st_cs_v4(y + c16, v[0], v[1], v[2], v[3]);
             st_cs_v4(y + c16 + 4, v[4], v[5], v[6], v[7]);
@@ -375,6 +439,10 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
           }
         }
         off += 16 * g.ry16[q];
+      }
+      if (F16) {  // the level's largest |Y| (non-negative floats order like their bits)
+        const uint32_t m = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(vmax) : 0u);
+        if (lane == 0 && m) atomicMax(a.ymax + g.level, m);
       }
       tc_fence_before();
       mbar_arrive(acc_empty(b));
@@ -406,7 +474,7 @@ constexpr int EX_GROUPS = (FMM_NT_CLASS + EX_GT - 1) / EX_GT;
 struct ExpArgs {
   const int32_t* tile_nact;
   const int16_t* eslot;   // [tile][189] operator slot of active transfer vector ai
-  const int8_t* ekch;     // [tile][189] its pipeline stages
+  const int8_t* ekch;     // [tile][189] its padded rank / 16 (TF32: its pipeline stages)
   const int64_t* yidx;    // [tile][189][128] first Y value of the row's source, -1 if none
   const float* Y;
   const float* U;  // interleaved hi/lo slabs (il_idx)
@@ -415,6 +483,11 @@ struct ExpArgs {
   int64_t YS;
   int ntiles, cpad, nh, nhalf, nst, tpa;
   uint32_t acol, tmem_cols;
+  // FP16 operands: per-level max |Y| (float bits; Y scaled by pow2_scale of
+  // it) and the U bank's scale, undone in the epilogue
+  const uint32_t* ymax;
+  const Tile* tiles;
+  float uscale;
 };
 
 constexpr int EXS_CHUNK = 8;  // active transfer vectors per setup block
@@ -456,6 +529,10 @@ __device__ inline void exp_unit(const ExpArgs& a, int u, int& g, int& h, int& ti
   h = rem - tile * a.nh;
 }
 
+// F16: operands FP16 hi/lo pairs, 32 ranks per stage (the last stage of a
+// rank = 16 mod 32 holds 16 and issues one MMA of K = 16 instead of two),
+// Y scaled per level and U by uscale, undone in the epilogue.
+template <bool F16>
 __global__ void __launch_bounds__(EX_THREADS, 1)
 k_svd_expand_tc(ExpArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -505,9 +582,10 @@ k_svd_expand_tc(ExpArgs a) {
 
   if (warp < EX_EPI) {
     // ---------------------------------------------------------- producers
-    // thread r loads 16 Y values of its target's source for the stage, splits
-    // them into TF32 hi/lo and writes them into its TMEM lane; one thread
-    // issues the B slab (U_t rows of this column half x 16 rank columns).
+    // thread r loads 16 Y values (F16: 32) of its target's source for the
+    // stage, splits them into hi/lo and writes them into its TMEM lane; one
+    // thread issues the B slab (U_t rows of this column half x the stage's
+    // rank columns).
     const int set = warp >> 2;
     const int r = threadIdx.x & (FMM_TILE - 1);
     uint32_t it = 0, last = 0;
@@ -519,12 +597,14 @@ k_svd_expand_tc(ExpArgs a) {
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
       const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
+      const float ysc = F16 ? pow2_scale(__uint_as_float(a.ymax[a.tiles[tile].level])) : 1.f;
       // the next transfer vector's slot, stages and source offset are loaded
       // while the current one is being copied
       int nslot = a.eslot[tb + a0], nkch = a.ekch[tb + a0];
       int64_t nyi = a.yidx[(tb + a0) * FMM_TILE + r];
       for (int ai = a0; ai < a1 && ok; ++ai) {
-        const int slot = nslot, kch = nkch;
+        const int slot = nslot, e16 = nkch;
+        const int kch = F16 ? (e16 + 1) >> 1 : e16;
         const int64_t yi = nyi;
         if (ai + 1 < a1) {
           nslot = a.eslot[tb + ai + 1];
@@ -537,7 +617,24 @@ k_svd_expand_tc(ExpArgs a) {
           for (int kc = kc0; kc < kch; kc += EX_SETS) {
             const uint32_t j = it + (uint32_t)kc;
             uint32_t vh[16], vl[16];
-            if (yr) {
+            if (yr && F16) {
+              // 32 ranks (16 in a half stage: the upper words are zeros, never read)
+              const bool half = (e16 & 1) && kc == kch - 1;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                uint32_t w[8];
+                if (q < 2 || !half) {
+                  ld_v8(yr + kc * 32 + 8 * q, w);
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 8; ++i) w[i] = 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  split_h2(__uint_as_float(w[2 * i]) * ysc, __uint_as_float(w[2 * i + 1]) * ysc, vh[4 * q + i],
+                           vl[4 * q + i]);
+              }
+            } else if (yr) {
               ld_v8(yr + kc * KC, vh);
               ld_v8(yr + kc * KC + 8, vh + 8);
 #pragma unroll
@@ -588,7 +685,7 @@ k_svd_expand_tc(ExpArgs a) {
     // ---------------------------------------------------------- MMA issuer
     uint32_t it = 0, tt = 0;
     bool ok = true;
-    const uint32_t idesc = idesc_tf32(FMM_TILE, a.nhalf);
+    const uint32_t idesc = F16 ? idesc_f16(FMM_TILE, a.nhalf) : idesc_tf32(FMM_TILE, a.nhalf);
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
       int g, h, tile;
       exp_unit(a, unit, g, h, tile);
@@ -611,7 +708,8 @@ k_svd_expand_tc(ExpArgs a) {
         bool first = true;
         for (int ai = ag; ai < ae && ok; ++ai) {
           const int u = ai - a0;
-          const int kch = __shfl_sync(0xffffffffu, u < 32 ? kA : kB, u & 31);
+          const int e16 = __shfl_sync(0xffffffffu, u < 32 ? kA : kB, u & 31);
+          const int kch = F16 ? (e16 + 1) >> 1 : e16;
           for (int kc = 0; kc < kch; ++kc, ++it) {
             const int s = (int)(it % a.nst);
             const uint32_t ph = (it / a.nst) & 1u;
@@ -623,14 +721,23 @@ k_svd_expand_tc(ExpArgs a) {
             if (lane == 0) {
               const uint32_t st = base + (uint32_t)s * stage_bytes;
               const uint32_t ahi0 = tmem + a.acol + (uint32_t)s * 32u;
+              // F16: a half stage (rank = 16 mod 32, its last stage) holds K = 16
+              const int nks = (F16 && (e16 & 1) && kc == kch - 1) ? 1 : 2;
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
+                if (ks >= nks) break;
                 const uint32_t ahi = ahi0 + ks * 8u, alo = ahi0 + 16u + ks * 8u;
                 const uint64_t bhi = sdesc_sw64s(st + ks * 32u, 1024);
                 const uint64_t blo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
-                mma_tf32_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
-                mma_tf32_ta(d, ahi, blo, idesc, 1u);
-                mma_tf32_ta(d, alo, bhi, idesc, 1u);
+                if (F16) {
+                  mma_f16_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
+                  mma_f16_ta(d, ahi, blo, idesc, 1u);
+                  mma_f16_ta(d, alo, bhi, idesc, 1u);
+                } else {
+                  mma_tf32_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
+                  mma_tf32_ta(d, ahi, blo, idesc, 1u);
+                  mma_tf32_ta(d, alo, bhi, idesc, 1u);
+                }
               }
               mma_commit(empty(s));
             }
@@ -692,9 +799,11 @@ k_svd_expand_tc(ExpArgs a) {
       }
       if (!ok) break;
       float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
+      // F16: back from the operands' scales (powers of two: exact)
+      const float inv = F16 ? 1.f / (pow2_scale(__uint_as_float(a.ymax[a.tiles[tile].level])) * a.uscale) : 1.f;
       for (int c = 0; c < a.nhalf; c += 4)
-        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row], S[(c + 1) * FMM_TILE + row],
-                                          S[(c + 2) * FMM_TILE + row], S[(c + 3) * FMM_TILE + row]);
+        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row] * inv, S[(c + 1) * FMM_TILE + row] * inv,
+                                          S[(c + 2) * FMM_TILE + row] * inv, S[(c + 3) * FMM_TILE + row] * inv);
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
@@ -808,17 +917,33 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   if (nst < EX_SETS || nst_p < 2)
     return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: fewer stages than producer sets");
   c->svd_tc_nst = nst;
-  FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc, sp_smem(nst_p)));
-  FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc, ex_smem(cp, nst)));
+  if (c->m2l_f16) {
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<true>, sp_smem(nst_p)));
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<true>, ex_smem(cp, nst)));
+    if (!c->svd_umax) {
+      void* p;
+      FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * 2 * FMM_MAX_LEVELS));
+      c->svd_umax = (uint32_t*)p;
+    }
+  } else {
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<false>, sp_smem(nst_p)));
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<false>, ex_smem(cp, nst)));
+  }
   if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
   return FMM_OK;
 }
 
 // Projection of every tile, then the expansion and (after `mid`) the FP64
 // reduction of its partial sums.
+bool svd_wants_f16(const Ctx* c) { return c->m2l_f16 && c->use_tc && m2l_svd_tc_supported(c); }
+
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp;
+  const bool f16 = c->m2l_f16;
+  if (f16 != c->svd_bank_f16) return set_err(c, FMM_ERR_STATE, "internal: compressed M2L banks in the other format");
+  uint32_t* mmax = c->svd_umax;
+  uint32_t* ymax = f16 ? c->svd_umax + FMM_MAX_LEVELS : nullptr;
   // multipoles in class order, every level with far field
   const int64_t mrows = c->svd_mcls_rows;
   McBase mb;
@@ -827,9 +952,21 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
       mb.base[l][k] = l >= 2 && l <= c->leaf ? c->svd_mcbase[l][k] : 0;
       mb.clsoff[l][k] = c->cls_off[l][k];
     }
-  for (int l = 2; l <= c->leaf; ++l)
-    if (c->lv.ncell[l] > 0)
-      k_gather_cls<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo, c->svd_Mcls);
+  if (f16) {
+    // per-level largest |M| first: the FP16 copy is scaled by it
+    FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * 2 * FMM_MAX_LEVELS, s));
+    const int64_t mrows_all = c->lv.row_off[c->leaf] + c->lv.ncell[c->leaf] + 1 - c->lv.row_off[2];
+    k_m_absmax<<<(int)std::min<int64_t>(ceil_div(mrows_all, 8), 8 * 1184), 256, 0, s>>>(c->lv, 2, c->leaf, cp, c->Mhi,
+                                                                                         c->Mlo, mmax);
+    for (int l = 2; l <= c->leaf; ++l)
+      if (c->lv.ncell[l] > 0)
+        k_gather_cls16<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo, mmax,
+                                                       (uint32_t*)c->svd_Mcls);
+  } else {
+    for (int l = 2; l <= c->leaf; ++l)
+      if (c->lv.ncell[l] > 0)
+        k_gather_cls<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo, c->svd_Mcls);
+  }
   ProjArgs p;
   p.Y = (float*)c->svd_Y;
   p.err = c->tc_err;
@@ -837,17 +974,23 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.ntiles = c->ntiles;
   p.ngroups = sp_ngroups(Rp);
   p.recs = (const ProjRec*)c->svd_recs;
-  p.kchunks = cp / KC;
+  p.kchunks = cp / (f16 ? 32 : KC);
   p.mrows = mrows;
   p.Mc = c->svd_Mcls;
   p.VT = c->svd_VThi;
   p.nst = sp_nst();
+  p.mmax = mmax;
+  p.ymax = ymax;
+  p.vscale = c->svd_vscale;
   k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
                                                        c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
                                                        (ProjRec*)c->svd_recs, c->tc_err);
   const int up = p.ntiles * p.ngroups;
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[9], s, cudaEventRecordExternal));
-  k_svd_proj_tc<<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
+  if (f16)
+    k_svd_proj_tc<true><<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
+  else
+    k_svd_proj_tc<false><<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[10], s, cudaEventRecordExternal));
   k_svd_exp_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
@@ -870,6 +1013,9 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.nst = c->svd_tc_nst;
   e.tpa = std::max(4, std::min(16, c->ncoef / std::max(16, Rp)));
   e.acol = (uint32_t)(2 * e.nhalf);
+  e.ymax = ymax;
+  e.tiles = c->tiles;
+  e.uscale = c->svd_uscale;
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
   const int ue = c->ntiles * e.nh * EX_GROUPS;
@@ -881,7 +1027,10 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
     c->p2p_after_proj = true;
   }
-  k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
+  if (f16)
+    k_svd_expand_tc<true><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
+  else
+    k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));

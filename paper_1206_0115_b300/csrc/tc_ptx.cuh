@@ -1,10 +1,12 @@
 // tc_ptx.cuh -- inline-PTX helpers of the sm_103a tensor-core kernels:
 // mbarriers with time-bounded waits, 2-D tiled TMA loads, shared-memory
-// matrix descriptors (K-major, 64-byte swizzle), tcgen05 MMA (kind::tf32,
-// A from tensor memory), tcgen05 loads/stores and the tensor-map encoder.
+// matrix descriptors (K-major, 64-byte swizzle), tcgen05 MMA (kind::tf32 and
+// kind::f16, A from shared or tensor memory), FP16 hi/lo splitting, tcgen05
+// loads/stores and the tensor-map encoder.
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -137,6 +139,51 @@ __device__ inline void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdes
       "r"(atmem), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
+// Instruction descriptor of kind::f16 with FP16 A and B (both K-major; the
+// two operands always share the type) and FP32 accumulate, M x N.  One MMA
+// covers K = 16 (32 bytes of a 64-byte swizzled row, like K = 8 of TF32).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ inline void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// D (+)= A * B with A in tensor memory (two FP16 per column).
+__device__ inline void mma_f16_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// FP16 hi/lo split of two values (already scaled into the FP16 range): hi =
+// fp16(x), lo = fp16(x - hi) (x - hi is exact in FP32), so hi + lo keeps 22
+// bits like a TF32 pair; lo may be subnormal, which costs at most 2^-25 in
+// absolute terms.  Packed two per 32-bit word, the first value in the low half
+// (K-major order of 16-bit operands).
+__device__ inline void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+  const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
+  hi = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+  lo = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+}
+
+// The power of two that brings magnitudes up to mx below 2^13 (1 for mx = 0
+// or not finite): scaling by it is exact, and 2^13 leaves room below the FP16
+// maximum (65504) for the rounding of hi.
+__host__ __device__ inline float pow2_scale(float mx) {
+  if (!(mx > 0.f) || !(mx < 3.0e38f)) return 1.f;
+  int e = 0;
+  frexpf(mx, &e);  // mx < 2^e
+  e = e < -100 ? -100 : e;
+  return ldexpf(1.f, 13 - e);
+}
+
 // 32 bytes from global memory (read-only path); the address must be 32-byte aligned.
 __device__ inline void ld_v8(const float* p, uint32_t* v) {
   asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"

@@ -250,6 +250,35 @@ def test_mixed_matches_oracle_fmm(F, name, make, h, p, m2l):
     assert oracle.rel_l2(Fo, Fr) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("name,make,h,p", [
+    ("cube_sym_n20k_h4_p7", lambda: inputs.particles(20000, 31, "cube", "sym"), 4, 7),
+    ("ellipsoid_n40k_h5_p6", lambda: inputs.particles(40000, 34, "ellipsoid", "sym"), 5, 6),
+    ("cube_n20k_h4_p5", lambda: inputs.particles(20000, 1, "cube", "pos"), 4, 5),
+])
+def test_m2l_operand_forms_agree(F, monkeypatch, name, make, h, p):
+    """The compressed tensor-core M2L on FP16 hi/lo operands (the default,
+    scaled per level by powers of two) and on TF32 hi/lo operands
+    (FMM_M2L_MATH=tf32 when the handle is created): both within the mixed bar
+    of the oracle, within 1e-5 of each other, and fmm_get_stats says which
+    form ran."""
+    xyz, q = make()
+    out = {}
+    for math in ("f16", "tf32"):
+        monkeypatch.setenv("FMM_M2L_MATH", math)
+        with F.FMM(h, p, F.FMM_MIXED) as f:
+            st = f.stats()
+            assert int(st[5]) == (1 if math == "f16" else 0)
+        out[math] = _run(F, xyz, q, h, p, F.FMM_MIXED)
+    monkeypatch.delenv("FMM_M2L_MATH")
+    with _oracle(xyz, q, h, p) as o:
+        pr, Fr = o.evaluate()
+    for math in ("f16", "tf32"):
+        assert oracle.rel_l2(out[math][0], pr) <= TOL_MIXED, math
+        assert oracle.rel_l2(out[math][1], Fr) <= TOL_MIXED, math
+    assert oracle.rel_l2(out["f16"][0], out["tf32"][0]) <= TOL_MIXED
+    assert oracle.rel_l2(out["f16"][1], out["tf32"][1]) <= TOL_MIXED
+
+
 def test_mixed_p7_matches_direct_sum(F):
     xyz, q = inputs.particles(20000, 41, "cube", "sym")
     phi, Fo = _run(F, xyz, q, 4, 7, F.FMM_MIXED)
