@@ -353,6 +353,10 @@ fmm_status launch_stokes_forces(Ctx* c, const double* f, float4* f32);
 fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* out);
 // The compressed operators need one operator set for every level: c = 0.
 inline bool uses_svd(const Ctx* c) { return c->m2l_method == FMM_M2L_SVD && c->kernel_c == 0.0; }
+// The compressed tensor-core M2L takes FP16 hi/lo operands (m2l_f16) for
+// single-problem trees; a batch's forest keeps TF32 operands, since one FP16
+// scale per level would be shared by problems of any relative magnitude.
+inline bool m2l_uses_f16(const Ctx* c) { return c->m2l_f16 && !c->forest; }
 // The mixed compressed factor banks are FP16 hi/lo pairs (the tensor-core
 // kernels' FP16 form) or TF32 hi/lo pairs.
 bool svd_wants_f16(const Ctx* c);

@@ -917,7 +917,7 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   if (nst < EX_SETS || nst_p < 2)
     return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: fewer stages than producer sets");
   c->svd_tc_nst = nst;
-  if (c->m2l_f16) {
+  if (m2l_uses_f16(c)) {
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<true>, sp_smem(nst_p)));
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<true>, ex_smem(cp, nst)));
     if (!c->svd_umax) {
@@ -935,12 +935,12 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
 
 // Projection of every tile, then the expansion and (after `mid`) the FP64
 // reduction of its partial sums.
-bool svd_wants_f16(const Ctx* c) { return c->m2l_f16 && c->use_tc && m2l_svd_tc_supported(c); }
+bool svd_wants_f16(const Ctx* c) { return m2l_uses_f16(c) && c->use_tc && m2l_svd_tc_supported(c); }
 
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp;
-  const bool f16 = c->m2l_f16;
+  const bool f16 = m2l_uses_f16(c);
   if (f16 != c->svd_bank_f16) return set_err(c, FMM_ERR_STATE, "internal: compressed M2L banks in the other format");
   uint32_t* mmax = c->svd_umax;
   uint32_t* ymax = f16 ? c->svd_umax + FMM_MAX_LEVELS : nullptr;

@@ -278,3 +278,27 @@ def test_p2p_variants_agree_and_autotune_picks_one(F):
     for v in range(1, F.FMM_P2P_VARIANTS):
         assert oracle.rel_l2(out[v][0], out[0][0]) <= TOL_ALONE, v
         assert oracle.rel_l2(out[v][1], out[0][1]) <= TOL_ALONE, v
+
+
+def test_batch_problems_of_very_different_magnitude(F):
+    """Two problems whose charges differ by a factor of 1e8 in one batch: each
+    matches its own oracle within the mixed bar (the batch's M2L keeps TF32
+    operands, relative precision per value, where a per-level FP16 scale
+    would be shared by both), and the handle reports the TF32 form."""
+    a = inputs.particles(8000, 801, "cube", "sym")
+    b = inputs.particles(12000, 802, "ellipsoid", "pos")
+    probs = [(a[0], a[1], 4), (b[0], 1e-8 * b[1], 5)]
+    phi, Fo, _ = _run_batch(F, probs, 5, F.FMM_MIXED)
+    with F.FMM(3, 5, F.FMM_MIXED) as f:
+        import torch
+        counts, heights, xyz, q = _concat(probs)
+        f.set_batch(counts, heights, torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        assert int(f.stats()[5]) == 0
+    off = 0
+    for x, q, h in probs:
+        sl = slice(off, off + len(q))
+        off += len(q)
+        with oracle.OracleFMM(x, q, h, 5, svd_eps=1e-5) as o:
+            rphi, rF = o.evaluate()
+        assert oracle.rel_l2(phi[sl], rphi) <= TOL_MIXED
+        assert oracle.rel_l2(Fo[sl], rF) <= TOL_MIXED
