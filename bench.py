@@ -880,8 +880,9 @@ def run_serving(args):
         "metric": METRIC, "value": parts / span, "unit": UNIT, "n_gpus": 1, "steps": nreq,
         "warmup": len(warm), "ms_per_step": 1e3 * span / nreq, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        # the server evaluates batches (fmm_set_batch), whose M2L keeps TF32 operands
-        "dtype": "f32+tf32x3" if args.precision == "mixed" else "f64", "data": "synthetic",
+        # the server's handles take the library's default operand form unless FMM_M2L_MATH=tf32
+        "dtype": ("f32+" + ("tf32x3" if os.environ.get("FMM_M2L_MATH") == "tf32" else "f16x3"))
+                 if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": SERVE_WORKLOAD, "rate_rps": rate, "duration_s": seconds, "requests": nreq,
                    "n_range": [10_000, 5_000_000], "orders": [5, 7], "heights": "3..8 by size",
                    "distribution": "cube", "lanes": lanes, "hbm_budget_bytes": budget,

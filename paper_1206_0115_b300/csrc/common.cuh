@@ -267,7 +267,8 @@ struct fmm_ctx {
   // banks' format, their scales, and per-level max |M| and |Y| (device words)
   bool m2l_f16 = false, svd_bank_f16 = false;
   float svd_vscale = 1.f, svd_uscale = 1.f;
-  uint32_t* svd_umax = nullptr;  // [2][FMM_MAX_LEVELS]
+  uint32_t* svd_umax = nullptr;  // max |Y| per (problem + 1, level): [FMM_MAX_BATCH + 1][FMM_MAX_LEVELS]
+  float* svd_mscale = nullptr;   // scale of each class-ordered multipole row (FP16 operands)
   std::vector<int32_t> svd_yoff_h;
   int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_yoff = nullptr;  // [316], [316], [8][316]
   int64_t svd_YS = 0;            // Y values per cell row
@@ -353,10 +354,10 @@ fmm_status launch_stokes_forces(Ctx* c, const double* f, float4* f32);
 fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* out);
 // The compressed operators need one operator set for every level: c = 0.
 inline bool uses_svd(const Ctx* c) { return c->m2l_method == FMM_M2L_SVD && c->kernel_c == 0.0; }
-// The compressed tensor-core M2L takes FP16 hi/lo operands (m2l_f16) for
-// single-problem trees; a batch's forest keeps TF32 operands, since one FP16
-// scale per level would be shared by problems of any relative magnitude.
-inline bool m2l_uses_f16(const Ctx* c) { return c->m2l_f16 && !c->forest; }
+// The compressed tensor-core M2L takes FP16 hi/lo operands (m2l_f16), scaled
+// per multipole row and per (problem, level), for single problems and
+// batches alike.
+inline bool m2l_uses_f16(const Ctx* c) { return c->m2l_f16; }
 // The mixed compressed factor banks are FP16 hi/lo pairs (the tensor-core
 // kernels' FP16 form) or TF32 hi/lo pairs.
 bool svd_wants_f16(const Ctx* c);

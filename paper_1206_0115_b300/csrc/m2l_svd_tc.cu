@@ -88,12 +88,17 @@ struct ProjArgs {
   int64_t mrows;         // rows of the class-ordered multipole copy per chunk of coefficients
   const float *Mc, *VT;  // interleaved hi/lo slabs (il_idx)
   int ntiles, ngroups, kchunks, nst;
-  // FP16 operands: per-level max |M| (float bits; M scaled by pow2_scale of it),
-  // the VT bank's scale, and per-level max |Y| written here for the expansion
-  const uint32_t* mmax;
+  // FP16 operands: each class-ordered multipole row's scale (pow2_scale of
+  // the cell's max |M|), the VT bank's scale, and the max |Y| per (problem,
+  // level) written here for the expansion (ymax_index)
+  const float* mscale;
   uint32_t* ymax;
   float vscale;
 };
+
+// Slot of the max |Y| of (problem, level): problem -1 (cells above a batch's
+// problem slots) first.
+__host__ __device__ inline int ymax_index(int prob, int level) { return (prob + 1) * FMM_MAX_LEVELS + level; }
 
 // Greedy grouping of each tile's active source transfer vectors into units
 // (every record of the tile is written, n = 0 past the last group).  One
@@ -180,35 +185,25 @@ __global__ void k_gather_cls(int l, LevelPtrs lv, McBase mb, int cpad, int64_t r
   }
 }
 
-// FP16 operands: the largest |M| of each level 2.. (float bits, atomicMax;
-// non-negative floats order like their bits).  Grid over the levels' rows;
-// a level's zero row adds nothing.
-__global__ void __launch_bounds__(256)
-k_m_absmax(LevelPtrs lv, int lmin, int lmax, int cpad, const float* __restrict__ Mhi,
-           const float* __restrict__ Mlo, uint32_t* __restrict__ mmax) {
-  const int64_t r0 = lv.row_off[lmin], r1 = lv.row_off[lmax] + lv.ncell[lmax] + 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t r = r0 + (int64_t)blockIdx.x * 8 + warp; r < r1; r += (int64_t)gridDim.x * 8) {
-    int l = lmin;
-    while (l < lmax && r >= lv.row_off[l + 1]) ++l;
-    float m = 0.f;
-    for (int k = lane; k < cpad; k += 32) m = fmaxf(m, fabsf(Mhi[r * cpad + k] + Mlo[r * cpad + k]));
-    const uint32_t mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-    if (lane == 0 && mb) atomicMax(mmax + l, mb);
-  }
-}
-
 // k_gather_cls with FP16 operands: the same rows, 32 coefficients per row
-// (chunk kc = k / 32), two per 32-bit word, scaled by the level's
-// pow2_scale(max |M|).  One block per cell, a thread per pair of coefficients.
-__global__ void k_gather_cls16(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
-                               const float* __restrict__ Mlo, const uint32_t* __restrict__ mmax,
-                               uint32_t* __restrict__ Mc) {
+// (chunk kc = k / 32), two per 32-bit word, scaled by pow2_scale of the
+// cell's own max |M| (recorded per row for the projection's epilogue).  One
+// block of 128 threads per cell, a thread per pair of coefficients.
+__global__ void __launch_bounds__(128)
+k_gather_cls16(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
+               const float* __restrict__ Mlo, uint32_t* __restrict__ Mc, float* __restrict__ mscale) {
+  __shared__ uint32_t s_max[4];
   const int j = blockIdx.x;
   const int cell = lv.cls[l][j];
   const int c = lv.key[l][cell] & 7;
   const int64_t row = mb.base[l][c] + (j - mb.clsoff[l][c]), src = (lv.row_off[l] + cell) * cpad;
-  const float sc = pow2_scale(__uint_as_float(mmax[l]));
+  float m = 0.f;
+  for (int k = threadIdx.x; k < cpad; k += blockDim.x) m = fmaxf(m, fabsf(Mhi[src + k] + Mlo[src + k]));
+  const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // non-negative floats order like bits
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = wm;
+  __syncthreads();
+  const float sc = pow2_scale(__uint_as_float(max(max(s_max[0], s_max[1]), max(s_max[2], s_max[3]))));
+  if (threadIdx.x == 0) mscale[row] = sc;
   for (int k = 2 * threadIdx.x; k < cpad; k += 2 * blockDim.x) {
     const int64_t G = (int64_t)(k >> 5) * rows + row;
     uint32_t hi, lo;
@@ -416,7 +411,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       tc_fence_after();
       const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * SP_ACC);
       // F16: back from the operands' scales (powers of two: exact)
-      const float inv = F16 ? 1.f / (pow2_scale(__uint_as_float(a.mmax[g.level])) * a.vscale) : 1.f;
+      const float inv = F16 && valid ? 1.f / (a.mscale[g.arow + row] * a.vscale) : 1.f;
       float vmax = 0.f;
       int off = 0;
       for (int q = 0; q < g.n; ++q) {
@@ -440,9 +435,16 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
         }
         off += 16 * g.ry16[q];
       }
-      if (F16) {  // the level's largest |Y| (non-negative floats order like their bits)
-        const uint32_t m = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(vmax) : 0u);
-        if (lane == 0 && m) atomicMax(a.ymax + g.level, m);
+      if (F16) {  // largest |Y| per (problem, level); non-negative floats order like their bits
+        const int prob = valid ? problem_of(lv, g.level, lv.cls[g.level][g.first + row]) : -2;
+        const uint32_t mine = valid ? __float_as_uint(vmax) : 0u;
+        const int p0 = __shfl_sync(0xffffffffu, prob, 0);
+        if (__all_sync(0xffffffffu, prob == p0 || prob == -2)) {
+          const uint32_t m = __reduce_max_sync(0xffffffffu, mine);
+          if (lane == 0 && m && p0 != -2) atomicMax(a.ymax + ymax_index(p0, g.level), m);
+        } else if (valid && mine) {
+          atomicMax(a.ymax + ymax_index(prob, g.level), mine);
+        }
       }
       tc_fence_before();
       mbar_arrive(acc_empty(b));
@@ -483,12 +485,20 @@ struct ExpArgs {
   int64_t YS;
   int ntiles, cpad, nh, nhalf, nst, tpa;
   uint32_t acol, tmem_cols;
-  // FP16 operands: per-level max |Y| (float bits; Y scaled by pow2_scale of
-  // it) and the U bank's scale, undone in the epilogue
+  // FP16 operands: the max |Y| per (problem, level) (float bits, ymax_index;
+  // a target row's Y values, all of its own problem, are scaled by
+  // pow2_scale of it) and the U bank's scale, undone per row in the epilogue
   const uint32_t* ymax;
   const Tile* tiles;
   float uscale;
 };
+
+// pow2_scale of the max |Y| of the problem of target row r of a tile.
+__device__ inline float row_yscale(const ExpArgs& a, const LevelPtrs& lv, const Tile& tl, int r) {
+  if (r >= tl.count) return 1.f;
+  const int prob = problem_of(lv, tl.level, lv.cls[tl.level][tl.first + r]);
+  return pow2_scale(__uint_as_float(a.ymax[ymax_index(prob, tl.level)]));
+}
 
 constexpr int EXS_CHUNK = 8;  // active transfer vectors per setup block
 
@@ -534,7 +544,7 @@ __device__ inline void exp_unit(const ExpArgs& a, int u, int& g, int& h, int& ti
 // Y scaled per level and U by uscale, undone in the epilogue.
 template <bool F16>
 __global__ void __launch_bounds__(EX_THREADS, 1)
-k_svd_expand_tc(ExpArgs a) {
+k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -597,7 +607,7 @@ k_svd_expand_tc(ExpArgs a) {
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
       const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
-      const float ysc = F16 ? pow2_scale(__uint_as_float(a.ymax[a.tiles[tile].level])) : 1.f;
+      const float ysc = F16 ? row_yscale(a, lv, a.tiles[tile], r) : 1.f;
       // the next transfer vector's slot, stages and source offset are loaded
       // while the current one is being copied
       int nslot = a.eslot[tb + a0], nkch = a.ekch[tb + a0];
@@ -800,7 +810,7 @@ k_svd_expand_tc(ExpArgs a) {
       if (!ok) break;
       float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
       // F16: back from the operands' scales (powers of two: exact)
-      const float inv = F16 ? 1.f / (pow2_scale(__uint_as_float(a.ymax[a.tiles[tile].level])) * a.uscale) : 1.f;
+      const float inv = F16 ? 1.f / (row_yscale(a, lv, a.tiles[tile], row) * a.uscale) : 1.f;
       for (int c = 0; c < a.nhalf; c += 4)
         *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row] * inv, S[(c + 1) * FMM_TILE + row] * inv,
                                           S[(c + 2) * FMM_TILE + row] * inv, S[(c + 3) * FMM_TILE + row] * inv);
@@ -900,13 +910,17 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   mrows += FMM_TILE;
   if (mrows > c->svd_mcls_rows) {
     dfree(c, c->svd_Mcls, 8 * (size_t)c->svd_mcls_rows * cp);
+    dfree(c, c->svd_mscale, 4 * (size_t)c->svd_mcls_rows);
     c->svd_Mcls = nullptr;
+    c->svd_mscale = nullptr;
     c->svd_mcls_rows = 0;
     const int64_t cap = (mrows + mrows / 8 + FMM_TILE - 1) / FMM_TILE * FMM_TILE;  // chunks start on 8-row groups
     void* p;
     FMM_TRY(dalloc(c, &p, 8 * (size_t)cap * cp));
     FMM_CUDA(c, cudaMemsetAsync(p, 0, 8 * (size_t)cap * cp, c->stream));
     c->svd_Mcls = (float*)p;
+    FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));  // FP16 operands: each row's scale
+    c->svd_mscale = (float*)p;
     c->svd_mcls_rows = cap;
   }
   // stages: shared memory and the TMEM columns beside the accumulators
@@ -920,9 +934,9 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   if (m2l_uses_f16(c)) {
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<true>, sp_smem(nst_p)));
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<true>, ex_smem(cp, nst)));
-    if (!c->svd_umax) {
+    if (!c->svd_umax) {  // max |Y| per (problem + 1, level): every batch size
       void* p;
-      FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * 2 * FMM_MAX_LEVELS));
+      FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * (FMM_MAX_BATCH + 1) * FMM_MAX_LEVELS));
       c->svd_umax = (uint32_t*)p;
     }
   } else {
@@ -942,8 +956,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   const int cp = c->cpad, Rp = c->svd_rp;
   const bool f16 = m2l_uses_f16(c);
   if (f16 != c->svd_bank_f16) return set_err(c, FMM_ERR_STATE, "internal: compressed M2L banks in the other format");
-  uint32_t* mmax = c->svd_umax;
-  uint32_t* ymax = f16 ? c->svd_umax + FMM_MAX_LEVELS : nullptr;
+  uint32_t* ymax = f16 ? c->svd_umax : nullptr;
   // multipoles in class order, every level with far field
   const int64_t mrows = c->svd_mcls_rows;
   McBase mb;
@@ -953,15 +966,13 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
       mb.clsoff[l][k] = c->cls_off[l][k];
     }
   if (f16) {
-    // per-level largest |M| first: the FP16 copy is scaled by it
-    FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * 2 * FMM_MAX_LEVELS, s));
-    const int64_t mrows_all = c->lv.row_off[c->leaf] + c->lv.ncell[c->leaf] + 1 - c->lv.row_off[2];
-    k_m_absmax<<<(int)std::min<int64_t>(ceil_div(mrows_all, 8), 8 * 1184), 256, 0, s>>>(c->lv, 2, c->leaf, cp, c->Mhi,
-                                                                                         c->Mlo, mmax);
+    // the projection's epilogue records the max |Y| per (problem, level) afresh
+    const int nslots = (c->forest ? c->nprob : 1) + 1;
+    FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * nslots * FMM_MAX_LEVELS, s));
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
-        k_gather_cls16<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo, mmax,
-                                                       (uint32_t*)c->svd_Mcls);
+        k_gather_cls16<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo,
+                                                       (uint32_t*)c->svd_Mcls, c->svd_mscale);
   } else {
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
@@ -979,7 +990,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.Mc = c->svd_Mcls;
   p.VT = c->svd_VThi;
   p.nst = sp_nst();
-  p.mmax = mmax;
+  p.mscale = c->svd_mscale;
   p.ymax = ymax;
   p.vscale = c->svd_vscale;
   k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
@@ -1028,9 +1039,9 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     c->p2p_after_proj = true;
   }
   if (f16)
-    k_svd_expand_tc<true><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
+    k_svd_expand_tc<true><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
   else
-    k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e);
+    k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
