@@ -49,9 +49,9 @@ TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (FP16 runs at the B
 
 
 def m2l_math(stats) -> str:
-    """Operand form of the tensor-core M2L: FP16 hi/lo pairs (compressed
-    operators, the default) or TF32 hi/lo pairs."""
-    return "f16x3" if int(stats[4]) == 5 and int(stats[5]) == 1 else "tf32x3"
+    """Operand form of the tensor-core M2L (compressed or full-rank
+    operators): FP16 hi/lo pairs (the default) or TF32 hi/lo pairs."""
+    return "f16x3" if int(stats[4]) in (2, 5) and int(stats[5]) == 1 else "tf32x3"
 
 
 def tensor_peak(pk, math: str):
@@ -463,7 +463,7 @@ def run_ours(args):
                          "bound": "tensor", "achieved": ach_p, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach_p / peak, "ms": float(kt[0]), "peak_source": peak_note}
     elif m2l_kind == 2:
-        kernel_name = "k_m2l_tc (full-rank M2L, tcgen05, 3xTF32), all levels"
+        kernel_name = f"k_m2l_tc (full-rank M2L, tcgen05, {mlabel}), all levels"
         m2l_ms = float(kt[1])
         achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
         traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu", "profiles/m2l_tc_cube_n1m_h6_p7.md",
@@ -471,8 +471,8 @@ def run_ours(args):
                    if args.workload == WORKLOAD else None)
         # every (tile, active transfer vector) runs a 128-row x cpad x cpad product three times
         hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
-        tensor_pipe = {"mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_ms / 1e3) / 1e12,
-                       "frac_of_tf32_peak": hw_flop / (m2l_ms / 1e3) / 1e12 / peak}
+        tensor_pipe = {"operands": math, "mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_ms / 1e3) / 1e12,
+                       "frac_of_peak": hw_flop / (m2l_ms / 1e3) / 1e12 / peak}
     else:
         kernel_name = ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
                        "k_m2l_simt<float> (FP32 CUDA cores), all levels", "",

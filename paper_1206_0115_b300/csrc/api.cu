@@ -392,7 +392,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
-                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax, c->svd_mscale,
+                  c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax, c->svd_mscale, c->tc_mmax,
                   c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_sstart, c->fb_sprob, c->fb_bstart};
   // back to the pool on the handle's own side stream (both streams are idle)
   for (void* b : bufs)

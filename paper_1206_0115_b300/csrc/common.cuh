@@ -204,6 +204,9 @@ struct fmm_ctx {
   double* K64 = nullptr;       // [banks][316][C][C]
   float *Khi = nullptr, *Klo = nullptr;  // [banks][316][cpad][cpad], TF32 split
   bool ops64 = false, ops32 = false;
+  bool ops32_f16 = false;   // the mixed banks hold FP16 hi/lo pairs (tensor-core FP16 form), scaled by ops_kscale
+  float ops_kscale = 1.f;
+  uint32_t* tc_mmax = nullptr;  // full-rank FP16 form: max |M| per (problem + 1, level)
   // banks: 1 (homogeneous kernel), or one per level 2..leaf (c > 0), built for
   // root width ops*_W (c > 0 only)
   int ops64_nb = 0, ops32_nb = 0;
@@ -243,6 +246,7 @@ struct fmm_ctx {
   int64_t svd_gcap = 0;
   const void* tm_khi_ptr = nullptr;
   int tm_khi_nb = 0;
+  bool tm_khi_f16 = false;
   int tc_nst = 0, num_sms = 0;
 
   // SVD-compressed M2L (m2l_svd.cu)

@@ -116,7 +116,7 @@ int64_t count_launches_eval(const Ctx* c) {
   if (Lf >= 2 && c->n > 0) {
     k += 1 + (Lf - 2);                                      // P2M, M2M
     const int kind = m2l_kind(c), per = kind >= 3 ? 2 : 1;
-    k += kind == 2 ? 2 * (c->ntiles > 0)
+    k += kind == 2 ? (2 + (c->ops32_f16 ? 1 : 0)) * (c->ntiles > 0)
                    : kind == 5 ? (5 + (Lf - 1)) * (c->ntiles > 0)
                                : per * ((c->leaf_tiles > 0) + (c->ntiles > c->leaf_tiles));
     k += (Lf - 2);                                          // L2L

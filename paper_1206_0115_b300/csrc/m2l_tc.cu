@@ -60,6 +60,11 @@ struct TcArgs {
   int32_t* err;    // nonzero after a timed-out wait
   int ntiles, groups, gt, cpad, nh, nhalf, kchunks, nst;
   int lev_ops;         // one operator bank per level 2.. (kernels with c > 0)
+  // FP16 operands: max |M| per (problem + 1, level) (float bits; a target
+  // row's gathered multipoles, all of its own problem, are scaled by
+  // pow2_scale of it) and the operator banks' scale, undone per row
+  const uint32_t* mmax;
+  float kscale;
   uint32_t acol;       // first TMEM column of the A stages (after the two accumulators)
   uint32_t tmem_cols;  // power of two >= 2 * nhalf + 32 * nst
 };
@@ -75,6 +80,38 @@ __device__ inline void unit_coords(const TcArgs& a, int u, int& g, int& h, int& 
   tile = rem - h * a.ntiles;
 }
 
+// pow2_scale of the max |M| of the problem of target row r of a tile.
+__device__ inline float row_mscale(const TcArgs& a, const LevelPtrs& lv, const Tile& tl, int r) {
+  if (r >= tl.count) return 1.f;
+  const int prob = problem_of(lv, tl.level, lv.cls[tl.level][tl.first + r]);
+  return pow2_scale(__uint_as_float(a.mmax[(prob + 1) * FMM_MAX_LEVELS + tl.level]));
+}
+
+// FP16 form: the max |M| of each (problem, level 2..), over the multipole
+// rows of the levels (one warp per row; a level's zero row is skipped).
+__global__ void __launch_bounds__(256)
+k_m_absmax(LevelPtrs lv, int lmin, int lmax, int cpad, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+           uint32_t* __restrict__ mmax) {
+  const int64_t r0 = lv.row_off[lmin], r1 = lv.row_off[lmax] + lv.ncell[lmax] + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t r = r0 + (int64_t)blockIdx.x * 8 + warp; r < r1; r += (int64_t)gridDim.x * 8) {
+    int l = lmin;
+    while (l < lmax && r >= lv.row_off[l + 1]) ++l;
+    const int64_t cell = r - lv.row_off[l];
+    if (cell >= lv.ncell[l]) continue;  // the level's zero row (warp-uniform)
+    float m = 0.f;
+    for (int k = lane; k < cpad; k += 32) m = fmaxf(m, fabsf(Mhi[r * cpad + k] + Mlo[r * cpad + k]));
+    const uint32_t mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // non-negative floats order like bits
+    const int prob = problem_of(lv, l, (int)cell);
+    if (lane == 0 && mb) atomicMax(mmax + (prob + 1) * FMM_MAX_LEVELS + l, mb);
+  }
+}
+
+// F16: operands FP16 hi/lo pairs (32 coefficients per stage, two MMAs of
+// K = 16, at twice the TF32 rate; operator banks as rows of packed FP16
+// pairs, copied by the same float32 tensor maps as 32-bit words); otherwise
+// TF32 hi/lo pairs.
+template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUtensorMap tm_klo, TcArgs a,
          LevelPtrs lv, const float* __restrict__ Mhi, const float* __restrict__ Mlo) {
@@ -143,6 +180,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       if (a0 >= a1) continue;
       const Tile tl = a.tiles[tile];
       const int64_t rbase = lv.row_off[tl.level];
+      const float msc = F16 ? row_mscale(a, lv, tl, r) : 1.f;
       for (int ai = a0; ai < a1 && ok; ++ai) {
         // stages of this transfer vector owned by the set
         const uint32_t kc0 = (uint32_t)((set - (int)(it % TC_SETS) + TC_SETS) % TC_SETS);
@@ -158,10 +196,25 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
         for (int kc = (int)kc0; kc < a.kchunks; kc += TC_SETS) {
           const uint32_t j = it + (uint32_t)kc;
           uint32_t vh[16], vl[16];
-          ld_v8((const float*)ghi + kc * TC_KC, vh);
-          ld_v8((const float*)ghi + kc * TC_KC + 8, vh + 8);
-          ld_v8((const float*)glo + kc * TC_KC, vl);
-          ld_v8((const float*)glo + kc * TC_KC + 8, vl + 8);
+          if (F16) {
+            // 32 coefficients: M = hi + lo, scaled, split into FP16 pairs
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint32_t wh[8], wl[8];
+              ld_v8((const float*)ghi + kc * 32 + 8 * q, wh);
+              ld_v8((const float*)glo + kc * 32 + 8 * q, wl);
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                split_h2((__uint_as_float(wh[2 * i]) + __uint_as_float(wl[2 * i])) * msc,
+                         (__uint_as_float(wh[2 * i + 1]) + __uint_as_float(wl[2 * i + 1])) * msc, vh[4 * q + i],
+                         vl[4 * q + i]);
+            }
+          } else {
+            ld_v8((const float*)ghi + kc * TC_KC, vh);
+            ld_v8((const float*)ghi + kc * TC_KC + 8, vh + 8);
+            ld_v8((const float*)glo + kc * TC_KC, vl);
+            ld_v8((const float*)glo + kc * TC_KC + 8, vl + 8);
+          }
           const int s = (int)(j % a.nst);
           const uint32_t ph = (j / a.nst) & 1u;
           if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
@@ -172,8 +225,9 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
           if (r == 0) {
             mbar_expect_tx(full(s), 2u * b_bytes);
             const int y = slot * a.cpad + h * a.nhalf;
-            tma_2d(st, &tm_khi, kc * TC_KC, y, full(s));
-            tma_2d(st + b_bytes, &tm_klo, kc * TC_KC, y, full(s));
+            // x in 32-bit words: 16 per stage (TF32: 16 values; FP16: 32 values)
+            tma_2d(st, &tm_khi, kc * 16, y, full(s));
+            tma_2d(st + b_bytes, &tm_klo, kc * 16, y, full(s));
           }
           // A row r -> TMEM lane r: hi in columns [0, 16), lo in [16, 32) of the stage's slot
           const uint32_t ta = tmem + ((uint32_t)(r & ~31) << 16) + a.acol + (uint32_t)s * 32u;
@@ -203,7 +257,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
     // buffers so that the epilogue drains t while t+1 accumulates
     uint32_t it = 0, tt = 0;
     bool ok = true;
-    const uint32_t idesc = idesc_tf32(FMM_TILE, a.nhalf);
+    const uint32_t idesc = F16 ? idesc_f16(FMM_TILE, a.nhalf) : idesc_tf32(FMM_TILE, a.nhalf);
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
       int g, h, tile;
       unit_coords(a, unit, g, h, tile);
@@ -234,9 +288,15 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
               const uint32_t ahi = ahi0 + ks * 8u, alo = ahi0 + 16u + ks * 8u;
               const uint64_t bhi = sdesc_sw64(st + ks * 32u);
               const uint64_t blo = sdesc_sw64(st + b_bytes + ks * 32u);
-              mma_tf32_ta(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-              mma_tf32_ta(d, ahi, blo, idesc, 1u);
-              mma_tf32_ta(d, alo, bhi, idesc, 1u);
+              if (F16) {
+                mma_f16_ta(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                mma_f16_ta(d, ahi, blo, idesc, 1u);
+                mma_f16_ta(d, alo, bhi, idesc, 1u);
+              } else {
+                mma_tf32_ta(d, ahi, bhi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                mma_tf32_ta(d, ahi, blo, idesc, 1u);
+                mma_tf32_ta(d, alo, bhi, idesc, 1u);
+              }
             }
             mma_commit(empty(s));
           }
@@ -299,9 +359,11 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       }
       if (!ok) break;
       float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
+      // F16: back from the operands' scales (powers of two: exact)
+      const float inv = F16 ? 1.f / (row_mscale(a, lv, a.tiles[tile], row) * a.kscale) : 1.f;
       for (int c = 0; c < a.nhalf; c += 4)
-        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row], S[(c + 1) * FMM_TILE + row],
-                                          S[(c + 2) * FMM_TILE + row], S[(c + 3) * FMM_TILE + row]);
+        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row] * inv, S[(c + 1) * FMM_TILE + row] * inv,
+                                          S[(c + 2) * FMM_TILE + row] * inv, S[(c + 3) * FMM_TILE + row] * inv);
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
@@ -390,13 +452,21 @@ fmm_status m2l_tc_prepare(Ctx* c) {
     FMM_CUDA(c, cudaMemsetAsync(c->tc_err, 0, 64, c->stream));
   }
   const int nb = op_banks(c);
-  if (c->tm_khi_ptr != c->Khi || c->tm_khi_nb != nb) {
-    const uint64_t rows = (uint64_t)FMM_NT * cp * nb;
-    bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, cp, rows, TC_KC, nhalf) &&
-              encode_2d((CUtensorMap*)c->tm_klo, c->Klo, cp, rows, TC_KC, nhalf);
+  const bool f16 = c->ops32_f16;
+  if (c->tm_khi_ptr != c->Khi || c->tm_khi_nb != nb || c->tm_khi_f16 != f16) {
+    // rows of cpad values: TF32 (cpad words) or packed FP16 pairs (cpad / 2 words), 16 words per box row
+    const uint64_t rows = (uint64_t)FMM_NT * cp * nb, words = f16 ? cp / 2 : cp;
+    bool ok = encode_2d((CUtensorMap*)c->tm_khi, c->Khi, words, rows, 16, nhalf) &&
+              encode_2d((CUtensorMap*)c->tm_klo, c->Klo, words, rows, 16, nhalf);
     if (!ok) return set_err(c, FMM_ERR_CUDA, "M2L tensor path: cuTensorMapEncodeTiled failed");
     c->tm_khi_ptr = c->Khi;
     c->tm_khi_nb = nb;
+    c->tm_khi_f16 = f16;
+  }
+  if (f16 && !c->tc_mmax) {  // max |M| per (problem + 1, level): every batch size
+    void* p;
+    FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * (FMM_MAX_BATCH + 1) * FMM_MAX_LEVELS));
+    c->tc_mmax = (uint32_t*)p;
   }
   int nst = (227 * 1024 - tc_fixed_bytes(cp)) / tc_stage_bytes(cp);
   const int tmem_stages = (512 - 2 * (cp / tc_nh(cp))) / 32;  // A stages beside the two accumulators
@@ -405,7 +475,7 @@ fmm_status m2l_tc_prepare(Ctx* c) {
   if (nst < TC_SETS) return set_err(c, FMM_ERR_ARG, "M2L tensor path: fewer stages than producer sets for cpad %d", cp);
   c->tc_nst = nst;
   const int smem = nst * tc_stage_bytes(cp) + tc_fixed_bytes(cp);
-  FMM_TRY(raise_smem_limit(c, (const void*)k_m2l_tc, smem));
+  FMM_TRY(raise_smem_limit(c, f16 ? (const void*)k_m2l_tc<true> : (const void*)k_m2l_tc<false>, smem));
   if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
   return FMM_OK;
 }
@@ -437,9 +507,12 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   a.cpad = cp;
   a.nh = nh;
   a.nhalf = nhalf;
-  a.kchunks = cp / TC_KC;
+  const bool f16 = c->ops32_f16;
+  a.kchunks = cp / (f16 ? 32 : TC_KC);
   a.nst = c->tc_nst;
   a.lev_ops = op_banks(c) > 1;
+  a.mmax = c->tc_mmax;
+  a.kscale = c->ops_kscale;
   a.acol = (uint32_t)(2 * nhalf);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < 2 * nhalf + 32 * c->tc_nst) a.tmem_cols <<= 1;
@@ -447,8 +520,29 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   const int nunits = c->ntiles * nh * TC_GROUPS;
   const int grid = nunits < c->num_sms ? nunits : c->num_sms;
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
-  k_m2l_tc<<<grid, TC_THREADS, smem, s>>>(*(const CUtensorMap*)c->tm_khi, *(const CUtensorMap*)c->tm_klo, a,
-                                          c->lv, c->Mhi, c->Mlo);
+  if (f16) {
+    // the largest |M| per (problem, level) sets each target row's scale
+    FMM_CUDA(c, cudaMemsetAsync(c->tc_mmax, 0,
+                                sizeof(uint32_t) * ((c->forest ? c->nprob : 1) + 1) * FMM_MAX_LEVELS, s));
+    const int64_t mrows = c->lv.row_off[c->leaf] + c->lv.ncell[c->leaf] + 1 - c->lv.row_off[2];
+    k_m_absmax<<<(int)std::min<int64_t>(ceil_div(mrows, 8), 8 * 1184), 256, 0, s>>>(c->lv, 2, c->leaf, cp, c->Mhi,
+                                                                                     c->Mlo, c->tc_mmax);
+  }
+  // the P2P branch is released here: its blocks and this kernel's CTAs become
+  // ready together and the CTAs (higher launch priority) are placed first,
+  // one per SM; released earlier, P2P blocks would hold the registers a CTA
+  // needs and delay the CTA's statically assigned units
+  if (c->timing != 2 && c->p2p_priority) {
+    FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
+    c->p2p_after_proj = true;
+  }
+  if (f16) {
+    k_m2l_tc<true><<<grid, TC_THREADS, smem, s>>>(*(const CUtensorMap*)c->tm_khi, *(const CUtensorMap*)c->tm_klo, a,
+                                                  c->lv, c->Mhi, c->Mlo);
+  } else {
+    k_m2l_tc<false><<<grid, TC_THREADS, smem, s>>>(*(const CUtensorMap*)c->tm_khi, *(const CUtensorMap*)c->tm_klo, a,
+                                                   c->lv, c->Mhi, c->Mlo);
+  }
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));

@@ -14,9 +14,11 @@
 //    same formula with P = (r^2 + c2)^(-s/2), scaled by a^-s; with c > 0 one
 //    bank per level, c2 = (c / a_l)^2 for that level's half-width a_l.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmm {
 
@@ -87,6 +89,56 @@ __global__ void k_m2l_ops_split(int p, int C, int cpad, const double* __restrict
       hi[(int64_t)m * cpad + nn] = h;
       lo[(int64_t)m * cpad + nn] = tf32_rna((float)(v - (double)h));
     }
+  }
+}
+
+// The same mean-split values as FP16 hi/lo pairs for the tensor-core
+// kernel's FP16 form (rows of cpad halves; the kernel's tensor maps copy them
+// as 32-bit words), scaled by `scale`.  mode 0: only the largest magnitude
+// (float bits, atomic max into *vmax); mode 1: the banks.  One thread per
+// (t, n).
+__global__ void k_m2l_ops_split16(int p, int C, int cpad, const double* __restrict__ nodes,
+                                  const int8_t* __restrict__ tvec, double ks, double c2, int mode, float scale,
+                                  uint32_t* __restrict__ vmax, __half* __restrict__ Khi, __half* __restrict__ Klo) {
+  const int64_t total = (int64_t)FMM_NT * cpad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i / cpad), nn = (int)(i - (int64_t)t * cpad);
+    __half* hi = Khi + (int64_t)t * cpad * cpad;
+    __half* lo = Klo + (int64_t)t * cpad * cpad;
+    if (nn >= C) {
+      if (mode == 1)
+        for (int m = 0; m < cpad; ++m) hi[(int64_t)m * cpad + nn] = lo[(int64_t)m * cpad + nn] = __float2half(0.f);
+      continue;
+    }
+    const int ni[3] = {nn / (p * p), (nn / p) % p, nn % p};
+    double y[3];
+    for (int d = 0; d < 3; ++d) y[d] = 2.0 * tvec[3 * t + d] + nodes[ni[d]];
+    auto K = [&](int m) {
+      double r2 = 0.0;
+      const int mi[3] = {m / (p * p), (m / p) % p, m % p};
+      for (int d = 0; d < 3; ++d) {
+        const double r = y[d] - nodes[mi[d]];
+        r2 += r * r;
+      }
+      return kernel_r2(r2, ks, c2);
+    };
+    double mean = 0.0;
+    for (int m = 0; m < C; ++m) mean += K(m);
+    mean /= C;
+    float mx = 0.f;
+    for (int m = 0; m < cpad; ++m) {
+      const double v = m < C ? K(m) - mean : (m == C ? mean : 0.0);
+      if (mode == 0) {
+        mx = fmaxf(mx, (float)fabs(v));
+      } else {
+        const double x = v * scale;
+        const __half h = __float2half_rn((float)x);
+        hi[(int64_t)m * cpad + nn] = h;
+        lo[(int64_t)m * cpad + nn] = __float2half_rn((float)(x - (double)__half2float(h)));
+      }
+    }
+    if (mode == 0) atomicMax(vmax, __float_as_uint(mx));
   }
 }
 
@@ -208,9 +260,12 @@ fmm_status operators_m2l(Ctx* c, int precision) {
   const int nb = op_banks(c);
   const double W = c->kernel_c > 0.0 ? c->box_host[3] : 0.0;
   const bool mixed = precision == FMM_MIXED;
+  // the tensor-core kernel's FP16 form takes FP16 banks; the CUDA-core kernel TF32 ones
+  const bool f16 = mixed && m2l_uses_f16(c) && m2l_kind(c) == 2;
   bool& built = mixed ? c->ops32 : c->ops64;
   int& bnb = mixed ? c->ops32_nb : c->ops64_nb;
   double& bW = mixed ? c->ops32_W : c->ops64_W;
+  if (mixed && built && c->ops32_f16 != f16) built = false;
   if (built && bnb == nb && bW == W) return FMM_OK;
   const size_t bank64 = (size_t)FMM_NT * C * C, bank32 = (size_t)FMM_NT * cp * cp;
   void* ptr;
@@ -236,10 +291,30 @@ fmm_status operators_m2l(Ctx* c, int precision) {
     FMM_TRY(dalloc(c, &ptr, sizeof(double) * bank64 * nb));
     c->K64 = (double*)ptr;
   }
+  if (f16) {
+    // one scale for every bank: the largest magnitude first
+    uint32_t* vmax = (uint32_t*)c->scratch;
+    FMM_CUDA(c, cudaMemsetAsync(vmax, 0, sizeof(uint32_t), c->stream));
+    for (int b = 0; b < nb; ++b) {
+      const double ca = c->kernel_c > 0.0 ? c->kernel_c * std::ldexp(1.0, 2 + b + 1) / W : 0.0;
+      k_m2l_ops_split16<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(
+          p, C, cp, c->nodes64, c->tvec, c->kernel_s, ca * ca, 0, 1.f, vmax, nullptr, nullptr);
+    }
+    uint32_t vb = 0;
+    FMM_CUDA(c, cudaMemcpyAsync(&vb, vmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    FMM_CUDA(c, cudaStreamSynchronize(c->stream));
+    float vf;
+    std::memcpy(&vf, &vb, sizeof(vf));
+    c->ops_kscale = tc::pow2_scale(vf);
+  }
   for (int b = 0; b < nb; ++b) {
     // bank b serves level 2 + b (c > 0): c / a_l = c 2^(l+1) / W
     const double ca = c->kernel_c > 0.0 ? c->kernel_c * std::ldexp(1.0, 2 + b + 1) / W : 0.0;
-    if (mixed)
+    if (f16)
+      k_m2l_ops_split16<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(
+          p, C, cp, c->nodes64, c->tvec, c->kernel_s, ca * ca, 1, c->ops_kscale, nullptr,
+          (__half*)c->Khi + bank32 * b, (__half*)c->Klo + bank32 * b);
+    else if (mixed)
       k_m2l_ops_split<<<ceil_div((int64_t)FMM_NT * cp, 128), 128, 0, c->stream>>>(
           p, C, cp, c->nodes64, c->tvec, c->kernel_s, ca * ca, c->Khi + bank32 * b, c->Klo + bank32 * b);
     else
@@ -250,6 +325,10 @@ fmm_status operators_m2l(Ctx* c, int precision) {
   built = true;
   bnb = nb;
   bW = W;
+  if (mixed) {
+    c->ops32_f16 = f16;
+    c->graph_ok = false;  // the tensor maps and the kernel's form follow the banks' format
+  }
   return FMM_OK;
 }
 

@@ -255,12 +255,13 @@ def test_mixed_matches_oracle_fmm(F, name, make, h, p, m2l):
     ("ellipsoid_n40k_h5_p6", lambda: inputs.particles(40000, 34, "ellipsoid", "sym"), 5, 6),
     ("cube_n20k_h4_p5", lambda: inputs.particles(20000, 1, "cube", "pos"), 4, 5),
 ])
-def test_m2l_operand_forms_agree(F, monkeypatch, name, make, h, p):
-    """The compressed tensor-core M2L on FP16 hi/lo operands (the default,
-    scaled per level by powers of two) and on TF32 hi/lo operands
-    (FMM_M2L_MATH=tf32 when the handle is created): both within the mixed bar
-    of the oracle, within 1e-5 of each other, and fmm_get_stats says which
-    form ran."""
+@pytest.mark.parametrize("m2l", [SVD, FULL], ids=["svd", "full"])
+def test_m2l_operand_forms_agree(F, monkeypatch, name, make, h, p, m2l):
+    """The tensor-core M2L (compressed or full-rank operators) on FP16 hi/lo
+    operands (the default, scaled by powers of two) and on TF32 hi/lo
+    operands (FMM_M2L_MATH=tf32 when the handle is created): both within the
+    mixed bar of the oracle, within 1e-5 of each other, and fmm_get_stats
+    says which form ran."""
     xyz, q = make()
     out = {}
     for math in ("f16", "tf32"):
@@ -268,9 +269,9 @@ def test_m2l_operand_forms_agree(F, monkeypatch, name, make, h, p):
         with F.FMM(h, p, F.FMM_MIXED) as f:
             st = f.stats()
             assert int(st[5]) == (1 if math == "f16" else 0)
-        out[math] = _run(F, xyz, q, h, p, F.FMM_MIXED)
+        out[math] = _run(F, xyz, q, h, p, F.FMM_MIXED, m2l=m2l)
     monkeypatch.delenv("FMM_M2L_MATH")
-    with _oracle(xyz, q, h, p) as o:
+    with _oracle(xyz, q, h, p, m2l) as o:
         pr, Fr = o.evaluate()
     for math in ("f16", "tf32"):
         assert oracle.rel_l2(out[math][0], pr) <= TOL_MIXED, math
