@@ -758,16 +758,36 @@ k_cls_scatter(ClassChunks a, int32_t* __restrict__ counters, ClassArgs ca, const
   }
 }
 
+// The ordered list of the set bits of a 189-bit mask (transfer vectors with
+// at least one pair): thread k < 189 writes k at its rank among the set bits.
+__device__ inline void mask_to_list(const uint32_t* mask, int k, int16_t* out, int32_t* count) {
+  if (k < FMM_NT_CLASS && ((mask[k >> 5] >> (k & 31)) & 1u)) {
+    int pos = __popc(mask[k >> 5] & ((1u << (k & 31)) - 1u));
+    for (int w = 0; w < (k >> 5); ++w) pos += __popc(mask[w]);
+    out[pos] = (int16_t)k;
+  }
+  if (k == 0) {
+    int n = 0;
+    for (int w = 0; w < (FMM_NT_CLASS + 31) / 32; ++w) n += __popc(mask[w]);
+    *count = n;
+  }
+}
+
+constexpr int SETUP_BATCH = 7;  // 189 = 27 x 7 independent grid lookups in flight per thread
+static_assert(FMM_NT_CLASS % SETUP_BATCH == 0, "setup batches cover the transfer vectors");
+
 // Per M2L tile: for each of the class's 189 transfer vectors the source cell
 // of every target row (the level's zero row when the source is absent or
 // outside the cube) and the list of transfer vectors with at least one
-// source.  One block of 128 threads (one per target row) per tile.
+// source.  One block of 128 threads (one per target row) per tile; each
+// thread looks its sources up in batches of independent loads, and a warp
+// ballot per transfer vector sets the tile's bit mask.
 __global__ void __launch_bounds__(FMM_TILE)
 k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ cls_t,
             const int8_t* __restrict__ tvec, int32_t* __restrict__ tile_src,
             int16_t* __restrict__ tile_act, int32_t* __restrict__ tile_nact) {
   const Tile tl = tiles[blockIdx.x];
-  const int l = tl.level, row = threadIdx.x;
+  const int l = tl.level, row = threadIdx.x, lane = row & 31;
   const bool valid = row < tl.count;
   const int zero_row = lv.ncell[l];
   int ix = 0, iy = 0, iz = 0, mine = 0;
@@ -777,24 +797,31 @@ k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restr
     mine = problem_of(lv, l, cell);
   }
   const int top = (1 << l) - 1;
-  __shared__ int16_t act[FMM_NT_CLASS];
-  __shared__ int nact;
-  if (row == 0) nact = 0;
+  __shared__ uint32_t mask[(FMM_NT_CLASS + 31) / 32];
+  if (row < (FMM_NT_CLASS + 31) / 32) mask[row] = 0u;
   __syncthreads();
-  for (int k = 0; k < FMM_NT_CLASS; ++k) {
-    int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
-    int sx = ix + tvec[3 * slot], sy = iy + tvec[3 * slot + 1], sz = iz + tvec[3 * slot + 2];
-    int src = zero_row;
-    if (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
-      int g = lv.grid[l][morton3(sx, sy, sz)];
-      if (g >= 0 && same_problem(lv, l, mine, g)) src = g;
+  int32_t* out = tile_src + (int64_t)blockIdx.x * FMM_NT_CLASS * FMM_TILE + row;
+  for (int k0 = 0; k0 < FMM_NT_CLASS; k0 += SETUP_BATCH) {
+    int g[SETUP_BATCH];
+#pragma unroll
+    for (int j = 0; j < SETUP_BATCH; ++j) {
+      const int slot = cls_t[tl.cls * FMM_NT_CLASS + k0 + j];
+      const int sx = ix + tvec[3 * slot], sy = iy + tvec[3 * slot + 1], sz = iz + tvec[3 * slot + 2];
+      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top)
+                 ? lv.grid[l][morton3(sx, sy, sz)]
+                 : -1;
     }
-    tile_src[((int64_t)blockIdx.x * FMM_NT_CLASS + k) * FMM_TILE + row] = src;
-    if (__syncthreads_or(src != zero_row) && row == 0) act[nact++] = (int16_t)k;
+#pragma unroll
+    for (int j = 0; j < SETUP_BATCH; ++j) {
+      const int src = (g[j] >= 0 && same_problem(lv, l, mine, g[j])) ? g[j] : zero_row;
+      out[(int64_t)(k0 + j) * FMM_TILE] = src;
+      const uint32_t any = __ballot_sync(0xffffffffu, src != zero_row);
+      if (lane == 0 && any) atomicOr(&mask[(k0 + j) >> 5], 1u << ((k0 + j) & 31));
+    }
   }
   __syncthreads();
-  for (int k = row; k < nact; k += FMM_TILE) tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + k] = act[k];
-  if (row == 0) tile_nact[blockIdx.x] = nact;
+  for (int k = row; k < FMM_TILE * 2; k += FMM_TILE)
+    mask_to_list(mask, k, tile_act + (int64_t)blockIdx.x * FMM_NT_CLASS, tile_nact + blockIdx.x);
 }
 
 // The same for the tile's cells as sources: the transfer vectors of the
@@ -804,7 +831,7 @@ __global__ void __launch_bounds__(FMM_TILE)
 k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ src_t,
                 const int8_t* __restrict__ tvec, int16_t* __restrict__ src_act, int32_t* __restrict__ src_nact) {
   const Tile tl = tiles[blockIdx.x];
-  const int l = tl.level, row = threadIdx.x;
+  const int l = tl.level, row = threadIdx.x, lane = row & 31;
   const bool valid = row < tl.count;
   int ix = 0, iy = 0, iz = 0, mine = 0;
   if (valid) {
@@ -813,23 +840,29 @@ k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __r
     mine = problem_of(lv, l, cell);
   }
   const int top = (1 << l) - 1;
-  __shared__ int16_t act[FMM_NT_CLASS];
-  __shared__ int nact;
-  if (row == 0) nact = 0;
+  __shared__ uint32_t mask[(FMM_NT_CLASS + 31) / 32];
+  if (row < (FMM_NT_CLASS + 31) / 32) mask[row] = 0u;
   __syncthreads();
-  for (int k = 0; k < FMM_NT_CLASS; ++k) {
-    const int slot = src_t[tl.cls * FMM_NT_CLASS + k];
-    const int tx = ix - tvec[3 * slot], ty = iy - tvec[3 * slot + 1], tz = iz - tvec[3 * slot + 2];
-    bool has = false;
-    if (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top) {
-      const int g = lv.grid[l][morton3(tx, ty, tz)];
-      has = g >= 0 && same_problem(lv, l, mine, g);
+  for (int k0 = 0; k0 < FMM_NT_CLASS; k0 += SETUP_BATCH) {
+    int g[SETUP_BATCH];
+#pragma unroll
+    for (int j = 0; j < SETUP_BATCH; ++j) {
+      const int slot = src_t[tl.cls * FMM_NT_CLASS + k0 + j];
+      const int tx = ix - tvec[3 * slot], ty = iy - tvec[3 * slot + 1], tz = iz - tvec[3 * slot + 2];
+      g[j] = (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top)
+                 ? lv.grid[l][morton3(tx, ty, tz)]
+                 : -1;
     }
-    if (__syncthreads_or(has) && row == 0) act[nact++] = (int16_t)k;
+#pragma unroll
+    for (int j = 0; j < SETUP_BATCH; ++j) {
+      const bool has = g[j] >= 0 && same_problem(lv, l, mine, g[j]);
+      const uint32_t any = __ballot_sync(0xffffffffu, has);
+      if (lane == 0 && any) atomicOr(&mask[(k0 + j) >> 5], 1u << ((k0 + j) & 31));
+    }
   }
   __syncthreads();
-  for (int k = row; k < nact; k += FMM_TILE) src_act[(int64_t)blockIdx.x * FMM_NT_CLASS + k] = act[k];
-  if (row == 0) src_nact[blockIdx.x] = nact;
+  for (int k = row; k < FMM_TILE * 2; k += FMM_TILE)
+    mask_to_list(mask, k, src_act + (int64_t)blockIdx.x * FMM_NT_CLASS, src_nact + blockIdx.x);
 }
 
 __global__ void k_zero_rows(int nrows, const int64_t* __restrict__ rows, int cpad, float* a, float* b,
