@@ -238,8 +238,8 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
  * FMM_P2P_VARIANTS mean launch times.  With a kernel other than 1/r
- * (fmm_set_kernel) the near field has one shape (4 warps, 256-source chunks,
- * one source per instruction): choice = {-1, 4, 256, 1, 4} and every time is
+ * (fmm_set_kernel) the near field has one shape (8 warps, 128-source chunks,
+ * two sources per instruction): choice = {-1, 8, 128, 2, 4} and every time is
  * that shape's.  Synchronises the
  * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);

@@ -724,7 +724,7 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
     c->precision = keep;
     if (st != FMM_OK) return st;
     if (choice) {
-      const int32_t v[5] = {-1, 4, 256, 1, 4};
+      const int32_t v[5] = {-1, 8, 128, 2, 4};
       for (int k = 0; k < 5; ++k) choice[k] = v[k];
     }
     if (times_ms)

@@ -255,11 +255,19 @@ struct PairAcc {
   f2_t phi, fx, fy, fz;
 };
 
-template <int G, bool SELF, int U>
+// General kernels (GEN, fmm_set_kernel): e = r^2 + c^2 in leaf widths,
+// phi += q e^(-s/2) = q 2^(-s/2 log2 e), F += s q d / e (three MUFU
+// operations per source, the rest in pairs).
+struct GenK {
+  float hs;         // s / 2
+  f2_t sk, cw2;     // (s, s), (c^2, c^2) in leaf widths
+};
+
+template <int G, bool SELF, int U, bool GEN>
 __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, const ulonglong2* __restrict__ sB,
                                           const ulonglong2* __restrict__ sC, const f2_t* __restrict__ sD, int j0,
                                           int j1, f2_t TX, f2_t TY, f2_t TZ, f2_t LX, f2_t LY, f2_t LZ,
-                                          PairAcc& acc) {
+                                          const GenK& gk, PairAcc& acc) {
 #pragma unroll U
   for (int j = j0; j < j1; j += G) {
     const ulonglong2 a = sA[j], b = sB[j], c = sC[j];
@@ -269,14 +277,29 @@ __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, con
     const f2_t dz = f2add(f2sub(TZ, b.x), f2sub(LZ, dlz));
     const f2_t r2 = f2fma(dx, dx, f2fma(dy, dy, f2mul(dz, dz)));
     const float2 rr = f2unpack(r2);
-    float i0 = rsqrtf(rr.x), i1 = rsqrtf(rr.y);
-    if (SELF) {
-      i0 = rr.x > 0.f ? i0 : 0.f;
-      i1 = rr.y > 0.f ? i1 : 0.f;
+    f2_t qi, qi3;
+    if (GEN) {
+      const float2 ee = f2unpack(f2add(r2, gk.cw2));
+      float p0 = exp2f(-gk.hs * __log2f(ee.x)), p1 = exp2f(-gk.hs * __log2f(ee.y));
+      float e0 = __fdividef(1.f, ee.x), e1 = __fdividef(1.f, ee.y);
+      if (SELF) {  // pairs at distance 0 contribute nothing, also when c > 0
+        p0 = rr.x > 0.f ? p0 : 0.f;
+        p1 = rr.y > 0.f ? p1 : 0.f;
+        e0 = rr.x > 0.f ? e0 : 0.f;
+        e1 = rr.y > 0.f ? e1 : 0.f;
+      }
+      qi = f2mul(b.y, f2pack(p0, p1));
+      qi3 = f2mul(f2mul(qi, gk.sk), f2pack(e0, e1));
+    } else {
+      float i0 = rsqrtf(rr.x), i1 = rsqrtf(rr.y);
+      if (SELF) {
+        i0 = rr.x > 0.f ? i0 : 0.f;
+        i1 = rr.y > 0.f ? i1 : 0.f;
+      }
+      const f2_t inv = f2pack(i0, i1);
+      qi = f2mul(b.y, inv);
+      qi3 = f2mul(f2mul(qi, inv), inv);
     }
-    const f2_t inv = f2pack(i0, i1);
-    const f2_t qi = f2mul(b.y, inv);
-    const f2_t qi3 = f2mul(f2mul(qi, inv), inv);
     acc.phi = f2add(acc.phi, qi);
     acc.fx = f2fma(qi3, dx, acc.fx);
     acc.fy = f2fma(qi3, dy, acc.fy);
@@ -284,21 +307,23 @@ __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, con
   }
 }
 
-template <int G, int U>
+template <int G, int U, bool GEN = false>
 __device__ __forceinline__ void p2p_pair_chunk(const ulonglong2* sA, const ulonglong2* sB, const ulonglong2* sC,
                                                const f2_t* sD, int sub, int jown, int np, f2_t TX, f2_t TY, f2_t TZ,
-                                               f2_t LX, f2_t LY, f2_t LZ, PairAcc& acc) {
-  p2p_pairs<G, true, 1>(sA, sB, sC, sD, sub, jown, TX, TY, TZ, LX, LY, LZ, acc);
+                                               f2_t LX, f2_t LY, f2_t LZ, PairAcc& acc, const GenK& gk = GenK{}) {
+  p2p_pairs<G, true, 1, GEN>(sA, sB, sC, sD, sub, jown, TX, TY, TZ, LX, LY, LZ, gk, acc);
   const int j0 = jown + ((sub - jown) % G + G) % G;
-  p2p_pairs<G, false, U>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, acc);
+  p2p_pairs<G, false, U, GEN>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, gk, acc);
 }
 
-template <int W, int CH, int U>
+// GEN: the kernels of fmm_set_kernel other than 1/r (ks, kc); outputs scaled
+// by w^-s and w^-(s+1).
+template <int W, int CH, int U, bool GEN = false>
 __global__ void __launch_bounds__(W * 32)
 k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
           int nitems,
           const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-          float4* __restrict__ out) {
+          float4* __restrict__ out, double ks = 1.0, double kc = 0.0) {
   constexpr int NP = CH / 2;
   __shared__ ulonglong2 sA[W][NP];
   __shared__ ulonglong2 sB[W][NP];
@@ -361,6 +386,13 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
   }
   const f2_t TX = f2pack(th.x, th.x), TY = f2pack(th.y, th.y), TZ = f2pack(th.z, th.z);
   const f2_t LX = f2pack(tl.x, tl.x), LY = f2pack(tl.y, tl.y), LZ = f2pack(tl.z, tl.z);
+  GenK gk{};
+  if (GEN) {
+    const double ckw = kc / ldexp(box[3], -leaf);  // c in leaf widths
+    gk.hs = (float)(0.5 * ks);
+    gk.sk = f2pack((float)ks, (float)ks);
+    gk.cw2 = f2pack((float)(ckw * ckw), (float)(ckw * ckw));
+  }
   Kahan kp, kx, ky, kz;
   // staged source s of the chunk starting at c0: position (hi with the
   // neighbour shift, lo) and charge
@@ -406,12 +438,12 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     const ulonglong2* Cc = &sC[warp][0];
     const f2_t* D = &sD[warp][0];
     switch (g) {
-      case 1: p2p_pair_chunk<1, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 2: p2p_pair_chunk<2, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 4: p2p_pair_chunk<4, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 8: p2p_pair_chunk<8, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 16: p2p_pair_chunk<16, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      default: p2p_pair_chunk<32, U>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      case 1: p2p_pair_chunk<1, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 2: p2p_pair_chunk<2, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 4: p2p_pair_chunk<4, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 8: p2p_pair_chunk<8, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 16: p2p_pair_chunk<16, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      default: p2p_pair_chunk<32, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
     }
     const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
     kp.add(ph.x + ph.y);
@@ -427,7 +459,9 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     az += __shfl_xor_sync(0xffffffffu, az, o);
   }
   if (tvalid && sub == 0) {
-    const float s1 = (float)(1.0 / ldexp(box[3], -leaf)), s2 = s1 * s1;
+    const double iw = 1.0 / ldexp(box[3], -leaf);
+    const float s1 = GEN ? (float)pow(iw, ks) : (float)iw;
+    const float s2 = GEN ? (float)(pow(iw, ks) * iw) : s1 * s1;
     out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
   }
 }
@@ -572,159 +606,6 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   }
   if (tvalid && sub == 0) {
     const float s1 = (float)(1.0 / ldexp(box[3], -leaf)), s2 = s1 * s1;
-    out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
-  }
-}
-
-// ---- the kernel family (|x - y|^2 + c^2)^(-s/2), other than 1/r -----------
-// The same work items, staging and exact hi/lo differences as k_p2p32; per
-// pair, with e = r^2 + c^2 (c in leaf widths), phi += q e^(-s/2) and
-// F += s q d e^(-(s+2)/2) (F = -grad phi), e^(-s/2) = 2^(-s/2 log2 e) and 1/e
-// on the MUFU pipe (three MUFU operations per pair against one rsqrt for
-// 1/r).  Pairs at distance 0 are skipped, also when c > 0.
-template <int G, bool SELF>
-__device__ __forceinline__ void p2p_span_pow(const float4* __restrict__ shi, const float4* __restrict__ slo, int k0,
-                                             int k1, float4 th, float4 tl, float hs, float sk, float cw2,
-                                             float& fphi, float& fx, float& fy, float& fz) {
-#pragma unroll 4
-  for (int k = k0; k < k1; k += G) {
-    const float4 sh = shi[k], sl = slo[k];
-    const float dx = (th.x - sh.x) + (tl.x - sl.x);
-    const float dy = (th.y - sh.y) + (tl.y - sl.y);
-    const float dz = (th.z - sh.z) + (tl.z - sl.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float e = r2 + cw2;
-    float ps = exp2f(-hs * __log2f(e));
-    float ir2 = __fdividef(1.f, e);  // approximate reciprocal (one MUFU op, ~1 ulp)
-    if (SELF) {
-      ps = r2 > 0.f ? ps : 0.f;
-      ir2 = r2 > 0.f ? ir2 : 0.f;
-    }
-    const float qi = sh.w * ps;
-    const float qi3 = sk * qi * ir2;
-    fphi += qi;
-    fx = fmaf(qi3, dx, fx);
-    fy = fmaf(qi3, dy, fy);
-    fz = fmaf(qi3, dz, fz);
-  }
-}
-
-template <int W, int CH>
-__global__ void __launch_bounds__(W * 32)
-k_p2p32s(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of, int nitems,
-         const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-         double ks, double kc, float4* __restrict__ out) {
-  __shared__ float4 shi[W][CH];
-  __shared__ float4 slo[W][CH];
-  __shared__ int nb_first[W][27];
-  __shared__ int nb_pre[W][28];
-  __shared__ int8_t nb_off[W][27][3];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * W + warp;
-  if (item >= nitems) return;
-  const int T = leaf_of[item];
-  const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
-  const int tb = (item - items[T]) * 32;
-  int ix, iy, iz;
-  demorton3(lv.key[leaf][T], ix, iy, iz);
-  const int top = (1 << leaf) - 1;
-  const int mine = problem_of(lv, leaf, T);
-  int nf = 0, ncnt = 0, ox = 0, oy = 0, oz = 0;
-  if (lane < 27) {
-    const int k = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
-    ox = k / 9 - 1;
-    oy = (k / 3) % 3 - 1;
-    oz = k % 3 - 1;
-    const int sx = ix + ox, sy = iy + oy, sz = iz + oz;
-    if (sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) {
-      const int g = lv.grid[leaf][morton3(sx, sy, sz)];
-      if (g >= 0 && same_problem(lv, leaf, mine, g)) {
-        nf = lv.first[leaf][g];
-        ncnt = lv.count[leaf][g];
-      }
-    }
-  }
-  int incl = ncnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  if (lane < 27) {
-    nb_first[warp][lane] = nf;
-    nb_pre[warp][lane] = incl - ncnt;
-    nb_off[warp][lane][0] = (int8_t)ox;
-    nb_off[warp][lane][1] = (int8_t)oy;
-    nb_off[warp][lane][2] = (int8_t)oz;
-  }
-  if (lane == 0) nb_pre[warp][27] = total;
-  __syncwarp();
-  const int own = tc;
-  const int nt = min(32, tc - tb);
-  int lg = 0;
-  while ((nt << (lg + 1)) <= 32) ++lg;
-  const int g = 1 << lg, ti = lane >> lg, sub = lane & (g - 1);
-  const bool tvalid = ti < nt;
-  float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
-  if (tvalid) {
-    th = pos32[tf + tb + ti];
-    tl = pos32lo[tf + tb + ti];
-  }
-  const float hs = (float)(0.5 * ks), sk = (float)ks;
-  const double ckw = kc / ldexp(box[3], -leaf);  // c in leaf widths
-  const float cw2 = (float)(ckw * ckw);
-  Kahan kp, kx, ky, kz;
-  for (int c0 = 0; c0 < total; c0 += CH) {
-    const int cn = min(CH, total - c0);
-    __syncwarp();
-    for (int k = lane; k < cn; k += 32) {
-      const int sidx = c0 + k;
-      int lo = 0, hi = 26;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (nb_pre[warp][mid] <= sidx) lo = mid;
-        else hi = mid - 1;
-      }
-      const int j = nb_first[warp][lo] + (sidx - nb_pre[warp][lo]);
-      float4 ph = pos32[j];
-      ph.x += (float)nb_off[warp][lo][0];
-      ph.y += (float)nb_off[warp][lo][1];
-      ph.z += (float)nb_off[warp][lo][2];
-      shi[warp][k] = ph;
-      slo[warp][k] = pos32lo[j];
-    }
-    __syncwarp();
-    float fphi = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    const int kown = min(cn, max(0, own - c0));
-    const float4* sh = &shi[warp][0];
-    const float4* sl = &slo[warp][0];
-    // one lane group per target: sources sub, sub + g, ... (own leaf first: r = 0 pairs skipped)
-    switch (g) {
-#define SPAN_POW(G)                                                                               \
-  case G: {                                                                                       \
-    p2p_span_pow<G, true>(sh, sl, sub, kown, th, tl, hs, sk, cw2, fphi, fx, fy, fz);              \
-    const int k0 = kown + ((sub - kown) % G + G) % G;                                             \
-    p2p_span_pow<G, false>(sh, sl, k0, cn, th, tl, hs, sk, cw2, fphi, fx, fy, fz);                \
-  } break;
-      SPAN_POW(1) SPAN_POW(2) SPAN_POW(4) SPAN_POW(8) SPAN_POW(16) SPAN_POW(32)
-#undef SPAN_POW
-    }
-    kp.add(fphi);
-    kx.add(fx);
-    ky.add(fy);
-    kz.add(fz);
-  }
-  float aphi = kp.s, ax = kx.s, ay = ky.s, az = kz.s;
-  for (int o = g >> 1; o > 0; o >>= 1) {
-    aphi += __shfl_xor_sync(0xffffffffu, aphi, o);
-    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-    ay += __shfl_xor_sync(0xffffffffu, ay, o);
-    az += __shfl_xor_sync(0xffffffffu, az, o);
-  }
-  if (tvalid && sub == 0) {
-    // positions are in leaf widths w: phi scales by w^-s, F by w^-(s+1)
-    const double iw = 1.0 / ldexp(box[3], -leaf);
-    const float s1 = (float)pow(iw, ks), s2 = (float)(pow(iw, ks) * iw);
     out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
   }
 }
@@ -989,7 +870,7 @@ bool is_p2p_kernel(const void* f) {
                       (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                       (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
                       (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
-                      (const void*)k_p2p32s<4, 256>,     (const void*)k_p2p_stokes32<4, 128>,
+                      (const void*)k_p2p32x2<8, 128, 4, true>, (const void*)k_p2p_stokes32<4, 128>,
                       (const void*)k_p2p64};
   for (const void* k : ks)
     if (k == f) return true;
@@ -1007,7 +888,8 @@ void p2p_carveout() {
                         (const void*)k_p2p32x2<8, 128, 4>, (const void*)k_p2p32x2<4, 128, 4>,
                         (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                         (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
-                        (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>};
+                        (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
+                        (const void*)k_p2p32x2<8, 128, 4, true>};
     for (const void* k : ks) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaGetLastError();
   });
@@ -1022,9 +904,9 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
     return cuda_err(c, cudaMemsetAsync(nb, 0, bytes, s), "P2P skip");
   }
   if (c->precision == FMM_MIXED && (c->kernel_s != 1.0 || c->kernel_c != 0.0)) {
-    k_p2p32s<4, 256><<<ceil_div(c->p2p_nitems, 4), 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems,
-                                                                 c->pos32, c->pos32lo, c->box, c->kernel_s,
-                                                                 c->kernel_c, c->near32);
+    k_p2p32x2<8, 128, 4, true><<<ceil_div(c->p2p_nitems, 8), 256, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
+                                                                           c->p2p_nitems, c->pos32, c->pos32lo, c->box,
+                                                                           c->near32, c->kernel_s, c->kernel_c);
   } else if (c->precision == FMM_MIXED) {
 #define P2P_LAUNCH(W, CH)                                                                              \
   k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,   \

@@ -280,6 +280,20 @@ def test_m2l_operand_forms_agree(F, monkeypatch, name, make, h, p, m2l):
     assert oracle.rel_l2(out["f16"][1], out["tf32"][1]) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("m2l", [SVD, FULL], ids=["svd", "full"])
+def test_mixed_charges_scaled_by_powers_of_two(F, m2l):
+    """phi and F are linear in the charges: charges times 2^60 or 2^-60 give
+    results times the same power of two.  The FP16 operands' power-of-two
+    scales absorb the factor (and FP32 stays in range), so the results agree
+    to rounding; a lost or doubled scale anywhere would break this."""
+    xyz, q = inputs.particles(20000, 31, "cube", "sym")
+    phi0, F0 = _run(F, xyz, q, 4, 7, F.FMM_MIXED, m2l=m2l)
+    for e in (60, -60):
+        phi, Fo = _run(F, xyz, np.ldexp(q, e), 4, 7, F.FMM_MIXED, m2l=m2l)
+        assert oracle.rel_l2(np.ldexp(phi, -e), phi0) <= 1e-12, e
+        assert oracle.rel_l2(np.ldexp(Fo, -e), F0) <= 1e-12, e
+
+
 def test_mixed_p7_matches_direct_sum(F):
     xyz, q = inputs.particles(20000, 41, "cube", "sym")
     phi, Fo = _run(F, xyz, q, 4, 7, F.FMM_MIXED)

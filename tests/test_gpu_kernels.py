@@ -184,7 +184,7 @@ def test_kernel_autotune_reports_the_one_shape(F):
     with F.FMM(4, 5, F.FMM_MIXED, kernel_s=0.5) as f:
         f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
         choice, times = F.fmm_autotune(f.h)
-        assert list(choice) == [-1, 4, 256, 1, 4]
+        assert list(choice) == [-1, 8, 128, 2, 4]
         assert np.all(times > 0) and np.all(times == times[0])
         phi = torch.zeros(len(q), dtype=torch.float64, device="cuda")
         Fo = torch.zeros((len(q), 3), dtype=torch.float64, device="cuda")
