@@ -292,9 +292,9 @@ fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
  * operators: 0 = FP64 CUDA cores, 1 = FP32 CUDA cores on split operands,
  * 2 = tcgen05 tensor cores; compressed operators: 3 = FP64 CUDA cores,
  * 4 = FP32 CUDA cores, 5 = tcgen05 tensor cores), out[5] = 1 if the
- * compressed tensor-core M2L takes FP16 hi/lo operands (the default; 0:
- * TF32 hi/lo, chosen at fmm_create by the environment variable
- * FMM_M2L_MATH=tf32),
+ * tensor-core M2L (out[4] = 2 or 5) takes FP16 hi/lo operands (the default;
+ * 0: TF32 hi/lo, chosen at fmm_create by the environment variable
+ * FMM_M2L_MATH=tf32, or a CUDA-core M2L),
  * out[6..7] = 0 (reserved).  out: 8 int64, host. */
 fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
 

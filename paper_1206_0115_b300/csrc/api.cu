@@ -852,7 +852,7 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out) {
   out[2] = h->use_graph ? 1 : 0;
   out[3] = h->bytes;
   out[4] = m2l_kind(h);
-  out[5] = m2l_uses_f16(h) ? 1 : 0;
+  out[5] = (m2l_uses_f16(h) && (out[4] == 2 || out[4] == 5)) ? 1 : 0;  // the tensor-core kernels' operand form
   out[6] = out[7] = 0;
   return FMM_OK;
 }

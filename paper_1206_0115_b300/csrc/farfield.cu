@@ -74,23 +74,34 @@ __device__ inline void cell_centre(const double* box, int level, uint32_t key, d
 
 // ---------------------------------------------------------------- P2M
 
+// One block per leaf (leaves of many particles).  The multipole is a sum of
+// tensor products, M[mx][my][mz] = sum_j q_j Sx_j[mx] Sy_j[my] Sz_j[mz]: the
+// weights of 32 particles at a time are staged in shared memory, thread
+// (my, mz) forms w = q Sy Sz once per particle and adds w Sx[mx] for every mx
+// (one staged load per multiply, the Sx row a broadcast), and 128 / P^2
+// particle subsets run side by side and are added at the end.
 template <int P, typename T, bool MIXED>
 __global__ void __launch_bounds__(128)
 k_p2m(LevelPtrs lv, int leaf, const double* __restrict__ box, const T* __restrict__ cheb, int cpad,
       const double4* __restrict__ pos64, const float4* __restrict__ pos32, T* __restrict__ Mout,
       T* __restrict__ Mlo) {
-  constexpr int C = P * P * P, NB = 32, NPER = (C + 127) / 128;
+  constexpr int C = P * P * P, NB = 32, PP = P * P;
+  constexpr int PARTS = PP <= 128 ? 128 / PP : 1;  // particle subsets summed side by side
+  static_assert(PP <= 128, "one thread per (my, mz) pair");
   __shared__ T sS[NB][3][P];
   __shared__ T sq[NB];
   __shared__ T sC[P * P];
+  __shared__ T red[PARTS > 1 ? PARTS - 1 : 1][C];
   const int cell = blockIdx.x, tid = threadIdx.x;
+  const int pair = tid % PP, part = tid / PP, my = pair / P, mz = pair % P;
+  const bool active = part < PARTS;
   for (int i = tid; i < P * P; i += 128) sC[i] = cheb[i];
   const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
   double ctr[3], a = 1.0;
   if (!MIXED) cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
-  T acc[NPER];
+  T acc[P];
 #pragma unroll
-  for (int k = 0; k < NPER; ++k) acc[k] = T(0);
+  for (int k = 0; k < P; ++k) acc[k] = T(0);
   __syncthreads();
   for (int b0 = 0; b0 < cnt; b0 += NB) {
     const int nb = min(NB, cnt - b0);
@@ -114,29 +125,31 @@ k_p2m(LevelPtrs lv, int leaf, const double* __restrict__ box, const T* __restric
       if (d == 0) sq[j] = qq;
     }
     __syncthreads();
+    if (active)
+      for (int j = part; j < nb; j += PARTS) {
+        const T w = sq[j] * sS[j][1][my] * sS[j][2][mz];
 #pragma unroll
-    for (int k = 0; k < NPER; ++k) {
-      const int m = tid + 128 * k;
-      if (m < C) {
-        const int mx = m / (P * P), my = (m / P) % P, mz = m % P;
-        T s = acc[k];
-        for (int j = 0; j < nb; ++j) s += sq[j] * sS[j][0][mx] * sS[j][1][my] * sS[j][2][mz];
-        acc[k] = s;
+        for (int mx = 0; mx < P; ++mx) acc[mx] += w * sS[j][0][mx];
       }
-    }
     __syncthreads();
   }
-  const int64_t row = lv.row_off[leaf] + cell;
+  if (active && part > 0)
 #pragma unroll
-  for (int k = 0; k < NPER; ++k) {
-    const int m = tid + 128 * k;
-    if (m < C) {
+    for (int mx = 0; mx < P; ++mx) red[part - 1][mx * PP + pair] = acc[mx];
+  __syncthreads();
+  if (part == 0) {
+    const int64_t row = lv.row_off[leaf] + cell;
+#pragma unroll
+    for (int mx = 0; mx < P; ++mx) {
+      T v = acc[mx];
+      for (int q = 0; q + 1 < PARTS; ++q) v += red[q][mx * PP + pair];
+      const int m = mx * PP + pair;  // (mx * P + my) * P + mz
       if (MIXED) {
-        float hi = tf32_rna((float)acc[k]);
+        const float hi = tf32_rna((float)v);
         Mout[row * cpad + m] = hi;
-        Mlo[row * cpad + m] = tf32_rna((float)acc[k] - hi);
+        Mlo[row * cpad + m] = tf32_rna((float)v - hi);
       } else {
-        Mout[row * cpad + m] = acc[k];
+        Mout[row * cpad + m] = v;
       }
     }
   }
