@@ -449,7 +449,7 @@ __device__ __forceinline__ void l2p_store(int64_t r, double pf, double gx, doubl
 // One warp per leaf: the leaf's local expansion is staged in shared memory
 // and the lanes take its particles (leaves with many particles).
 template <int P, typename T, bool MIXED>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 2)
 k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const T* __restrict__ cheb,
           int cpad, const T* __restrict__ L, int has_far, const double4* __restrict__ pos64,
           const float4* __restrict__ pos32, const float4* __restrict__ near32,
@@ -495,7 +495,7 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
 // particle leaf index and its local expansion is read through the L1 cache
 // (neighbouring threads share leaves, so the loads are mostly broadcasts).
 template <int P, typename T, bool MIXED>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 2)
 k_l2p_pp(LevelPtrs lv, int leaf, int64_t n, const int32_t* __restrict__ pleaf, const double* __restrict__ box,
          const T* __restrict__ cheb, int cpad, const T* __restrict__ L, int has_far,
          const double4* __restrict__ pos64, const float4* __restrict__ pos32, const float4* __restrict__ near32,
