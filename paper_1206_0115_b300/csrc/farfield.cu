@@ -236,60 +236,74 @@ k_p2m_warp(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, co
 
 // ---------------------------------------------------------------- M2M
 
+// Children rows staged together (up to 8, within 16 KB of shared memory, so
+// that every order stays inside the 48 KB of static shared memory): one
+// global-load round trip per batch of children instead of one per child.
+template <int C, typename T>
+constexpr int child_batch() {
+  return (16384 / (C * (int)sizeof(T))) >= 8 ? 8 : ((16384 / (C * (int)sizeof(T))) < 1 ? 1 : 16384 / (C * (int)sizeof(T)));
+}
+
 template <int P, typename T, bool MIXED>
 __global__ void __launch_bounds__(256)
 k_m2m(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, const T* __restrict__ Mhi,
       const T* __restrict__ Mlo, T* __restrict__ Mout_hi, T* __restrict__ Mout_lo) {
-  constexpr int C = P * P * P, NPER = (C + 255) / 256;
+  constexpr int C = P * P * P, NPER = (C + 255) / 256, CB = child_batch<C, T>();
   __shared__ T sA[2 * P * P];
-  __shared__ T sin_[C], su[C], sv[C];
+  __shared__ T sin_[CB][C];
+  __shared__ T su[C], sv[C];
   const int cell = blockIdx.x, tid = threadIdx.x;
   for (int i = tid; i < 2 * P * P; i += 256) sA[i] = A[i];
   T acc[NPER];
 #pragma unroll
   for (int k = 0; k < NPER; ++k) acc[k] = T(0);
   const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
-  for (int ch = c0; ch < c0 + nc; ++ch) {
-    const uint32_t b = lv.key[l + 1][ch] & 7u;
-    const T* Ax = sA + ((b >> 2) & 1) * P * P;
-    const T* Ay = sA + ((b >> 1) & 1) * P * P;
-    const T* Az = sA + (b & 1) * P * P;
-    const int64_t row = lv.row_off[l + 1] + ch;
+  for (int cb = c0; cb < c0 + nc; cb += CB) {
+    const int nb = min(CB, c0 + nc - cb);
     __syncthreads();
-    for (int m = tid; m < C; m += 256) {
+    for (int e = tid; e < nb * C; e += 256) {
+      const int k = e / C, m = e - k * C;
+      const int64_t row = lv.row_off[l + 1] + cb + k;
       T v = Mhi[row * cpad + m];
       if (MIXED) v += Mlo[row * cpad + m];
-      sin_[m] = v;
+      sin_[k][m] = v;
     }
-    __syncthreads();
-    // z: u[x][y][mz] = sum_k Az[mz][k] in[x][y][k]
-    for (int m = tid; m < C; m += 256) {
-      const int xy = m / P, mz = m % P;
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < P; ++k) s += Az[mz * P + k] * sin_[xy * P + k];
-      su[m] = s;
-    }
-    __syncthreads();
-    // y: v[x][my][z] = sum_k Ay[my][k] u[x][k][z]
-    for (int m = tid; m < C; m += 256) {
-      const int x = m / (P * P), my = (m / P) % P, z = m % P;
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < P; ++k) s += Ay[my * P + k] * su[(x * P + k) * P + z];
-      sv[m] = s;
-    }
-    __syncthreads();
-    // x: acc[mx][y][z] += sum_k Ax[mx][k] v[k][y][z]
-#pragma unroll
-    for (int kk = 0; kk < NPER; ++kk) {
-      const int m = tid + 256 * kk;
-      if (m < C) {
-        const int mx = m / (P * P), yz = m % (P * P);
+    for (int k = 0; k < nb; ++k) {
+      const uint32_t b = lv.key[l + 1][cb + k] & 7u;
+      const T* Ax = sA + ((b >> 2) & 1) * P * P;
+      const T* Ay = sA + ((b >> 1) & 1) * P * P;
+      const T* Az = sA + (b & 1) * P * P;
+      const T* in = sin_[k];
+      __syncthreads();
+      // z: u[x][y][mz] = sum_k Az[mz][k] in[x][y][k]
+      for (int m = tid; m < C; m += 256) {
+        const int xy = m / P, mz = m % P;
         T s = T(0);
 #pragma unroll
-        for (int k = 0; k < P; ++k) s += Ax[mx * P + k] * sv[k * P * P + yz];
-        acc[kk] += s;
+        for (int q = 0; q < P; ++q) s += Az[mz * P + q] * in[xy * P + q];
+        su[m] = s;
+      }
+      __syncthreads();
+      // y: v[x][my][z] = sum_k Ay[my][k] u[x][k][z]
+      for (int m = tid; m < C; m += 256) {
+        const int x = m / (P * P), my = (m / P) % P, z = m % P;
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < P; ++q) s += Ay[my * P + q] * su[(x * P + q) * P + z];
+        sv[m] = s;
+      }
+      __syncthreads();
+      // x: acc[mx][y][z] += sum_k Ax[mx][k] v[k][y][z]
+#pragma unroll
+      for (int kk = 0; kk < NPER; ++kk) {
+        const int m = tid + 256 * kk;
+        if (m < C) {
+          const int mx = m / (P * P), yz = m % (P * P);
+          T s = T(0);
+#pragma unroll
+          for (int q = 0; q < P; ++q) s += Ax[mx * P + q] * sv[q * P * P + yz];
+          acc[kk] += s;
+        }
       }
     }
   }
@@ -314,9 +328,10 @@ k_m2m(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, const T* __restric
 template <int P, typename T, bool MEAN>
 __global__ void __launch_bounds__(256)
 k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lbuf) {
-  constexpr int C = P * P * P;
+  constexpr int C = P * P * P, CB = child_batch<C + 1, T>();
   __shared__ T sA[2 * P * P];
   __shared__ T sin_[C], su[C], sv[C];
+  __shared__ T sch[CB][C + 1];  // the children's own rows (from M2L), staged per batch
   const int cell = blockIdx.x, tid = threadIdx.x;
   for (int i = tid; i < 2 * P * P; i += 256) sA[i] = A[i];
   const int64_t prow = lv.row_off[l] + cell;
@@ -325,40 +340,49 @@ k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lb
   // child unchanged and only the deviations go through the L2L matrices
   const T mean = MEAN ? Lbuf[prow * cpad + C] : T(0);
   const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
-  for (int ch = c0; ch < c0 + nc; ++ch) {
-    const uint32_t b = lv.key[l + 1][ch] & 7u;
-    const T* Ax = sA + ((b >> 2) & 1) * P * P;
-    const T* Ay = sA + ((b >> 1) & 1) * P * P;
-    const T* Az = sA + (b & 1) * P * P;
+  for (int cb = c0; cb < c0 + nc; cb += CB) {
+    const int nb = min(CB, c0 + nc - cb);
     __syncthreads();
-    // z: u[mx][my][z'] = sum_k Az[k][z'] in[mx][my][k]
-    for (int m = tid; m < C; m += 256) {
-      const int xy = m / P, zp = m % P;
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < P; ++k) s += Az[k * P + zp] * sin_[xy * P + k];
-      su[m] = s;
+    for (int e = tid; e < nb * (C + 1); e += 256) {
+      const int k = e / (C + 1), m = e - k * (C + 1);
+      sch[k][m] = (MEAN || m < C) ? Lbuf[(lv.row_off[l + 1] + cb + k) * cpad + m] : T(0);
     }
-    __syncthreads();
-    // y: v[mx][y'][z'] = sum_k Ay[k][y'] u[mx][k][z']
-    for (int m = tid; m < C; m += 256) {
-      const int x = m / (P * P), yp = (m / P) % P, z = m % P;
-      T s = T(0);
+    for (int k = 0; k < nb; ++k) {
+      const int ch = cb + k;
+      const uint32_t b = lv.key[l + 1][ch] & 7u;
+      const T* Ax = sA + ((b >> 2) & 1) * P * P;
+      const T* Ay = sA + ((b >> 1) & 1) * P * P;
+      const T* Az = sA + (b & 1) * P * P;
+      __syncthreads();
+      // z: u[mx][my][z'] = sum_k Az[k][z'] in[mx][my][k]
+      for (int m = tid; m < C; m += 256) {
+        const int xy = m / P, zp = m % P;
+        T s = T(0);
 #pragma unroll
-      for (int k = 0; k < P; ++k) s += Ay[k * P + yp] * su[(x * P + k) * P + z];
-      sv[m] = s;
-    }
-    __syncthreads();
-    // x: L_C[x'][y'][z'] += sum_k Ax[k][x'] v[k][y'][z']
-    const int64_t crow = lv.row_off[l + 1] + ch;
-    for (int m = tid; m < C; m += 256) {
-      const int xp = m / (P * P), yz = m % (P * P);
-      T s = T(0);
+        for (int q = 0; q < P; ++q) s += Az[q * P + zp] * sin_[xy * P + q];
+        su[m] = s;
+      }
+      __syncthreads();
+      // y: v[mx][y'][z'] = sum_k Ay[k][y'] u[mx][k][z']
+      for (int m = tid; m < C; m += 256) {
+        const int x = m / (P * P), yp = (m / P) % P, z = m % P;
+        T s = T(0);
 #pragma unroll
-      for (int k = 0; k < P; ++k) s += Ax[k * P + xp] * sv[k * P * P + yz];
-      Lbuf[crow * cpad + m] += s;
+        for (int q = 0; q < P; ++q) s += Ay[q * P + yp] * su[(x * P + q) * P + z];
+        sv[m] = s;
+      }
+      __syncthreads();
+      // x: L_C[x'][y'][z'] += sum_k Ax[k][x'] v[k][y'][z']
+      const int64_t crow = lv.row_off[l + 1] + ch;
+      for (int m = tid; m < C; m += 256) {
+        const int xp = m / (P * P), yz = m % (P * P);
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < P; ++q) s += Ax[q * P + xp] * sv[q * P * P + yz];
+        Lbuf[crow * cpad + m] = sch[k][m] + s;
+      }
+      if (MEAN && tid == 0) Lbuf[crow * cpad + C] = sch[k][C] + mean;
     }
-    if (MEAN && tid == 0) Lbuf[crow * cpad + C] += mean;
   }
 }
 
