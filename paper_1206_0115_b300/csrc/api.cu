@@ -348,7 +348,8 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
       return fail(FMM_ERR_CUDA);
     }
   void* p;
-  if ((st = dalloc(c, &p, 4 * sizeof(double))) != FMM_OK) return fail(st);
+  // corner, side, and the leaf frame of the FP32 coordinates (tree.cu, k_bbox_final)
+  if ((st = dalloc(c, &p, 8 * sizeof(double))) != FMM_OK) return fail(st);
   c->box = (double*)p;
   if ((st = dalloc(c, &p, 128 * sizeof(int32_t))) != FMM_OK) return fail(st);
   c->counters = (int32_t*)p;
@@ -393,7 +394,8 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
                   c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax, c->svd_mscale, c->tc_mmax,
-                  c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_sstart, c->fb_sprob, c->fb_bstart};
+                  c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_frame, c->fb_thr, c->fb_sstart, c->fb_sprob,
+                  c->fb_bstart};
   // back to the pool on the handle's own side stream (both streams are idle)
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, c->side);

@@ -88,7 +88,7 @@ struct BatchProb {
   uint32_t slot_key;  // first forest leaf key of the problem's slot
   int32_t L;          // the problem's own leaf level (height - 1)
   int32_t S;          // level of its slot cell in the forest (Lf - L)
-  int32_t pad;
+  int32_t thr;        // offset of its leaf-level cell thresholds in the batch's table
 };
 
 #define FMM_MAX_FOREST_LEAF 9  // leaf level of a batched tree at most (dense grid 8^9 x 4 bytes)
@@ -170,6 +170,9 @@ struct fmm_ctx {
   fmm::BatchProb* fb_prob = nullptr; // [nprob]
   double* fb_box = nullptr;          // [nprob][4]: lo, W
   double* fb_scale = nullptr;        // [nprob]: lambda_k (output scale)
+  double* fb_frame = nullptr;        // [nprob][4]: 2^-e, FP32 pair 2^L / (W 2^-e), 1 / W (W = m 2^e)
+  int64_t* fb_thr = nullptr;         // cell thresholds, 3 << L per problem (BatchProb::thr)
+  int64_t fb_thr_cap = 0;
   uint32_t* fb_sstart = nullptr;     // [nslot]: slot start keys, ascending
   int32_t* fb_sprob = nullptr;       // [nslot]: problem of each slot
   int32_t* fb_bstart = nullptr;      // [nprob + 1]: bounding-box blocks per problem (prefix)

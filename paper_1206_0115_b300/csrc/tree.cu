@@ -9,6 +9,7 @@
 // Every step is integer or exact, so the tree is bit-identical to any other
 // implementation of the same rules.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -40,26 +41,48 @@ __device__ inline double warp_max(double v) {
   return v;
 }
 
-// Per-block min/max of each coordinate; raises the flag on non-finite input.
+// Order key of a double: an int64 that orders as the double does (-0 just
+// below +0), so min / max / comparisons run on the integer pipes (FP64
+// arithmetic runs at 1/64 of the FP32 rate on this part).
+__device__ inline int64_t dkey(double x) {
+  const int64_t b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & INT64_MAX);
+}
+__device__ inline double dkey_inv(int64_t k) { return __longlong_as_double(k ^ ((k >> 63) & INT64_MAX)); }
+__device__ inline int bits_nonfinite(int64_t b) { return ((b >> 52) & 0x7ff) == 0x7ff; }
+constexpr int64_t KEY_PINF = 0x7ff0000000000000LL;             // dkey(+inf)
+constexpr int64_t KEY_NINF = (int64_t)0x800fffffffffffffULL;   // dkey(-inf)
+__device__ inline int64_t warp_min64(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, o));
+  return v;
+}
+__device__ inline int64_t warp_max64(int64_t v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, o));
+  return v;
+}
+
+// Per-block min/max of each coordinate (on order keys: exact, the same
+// values as FP64 min/max); raises the flag on non-finite input.
 __global__ void __launch_bounds__(BB_THREADS)
 k_bbox_partial(int64_t n, const double* __restrict__ xyz, const double* __restrict__ q,
                double* __restrict__ part, int32_t* __restrict__ counters) {
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int64_t mn[3] = {KEY_PINF, KEY_PINF, KEY_PINF}, mx[3] = {KEY_NINF, KEY_NINF, KEY_NINF};
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int d = 0; d < 3; ++d) {
-      double v = xyz[3 * i + d];
-      bad |= !isfinite(v);
-      mn[d] = fmin(mn[d], v);
-      mx[d] = fmax(mx[d], v);
+      const int64_t b = __double_as_longlong(xyz[3 * i + d]);
+      bad |= bits_nonfinite(b);
+      const int64_t k = b ^ ((b >> 63) & INT64_MAX);
+      mn[d] = min(mn[d], k);
+      mx[d] = max(mx[d], k);
     }
-    bad |= !isfinite(q[i]);
+    bad |= bits_nonfinite(__double_as_longlong(q[i]));
   }
-  __shared__ double s[2][3][BB_THREADS / 32];
+  __shared__ int64_t s[2][3][BB_THREADS / 32];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int d = 0; d < 3; ++d) {
-    double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    int64_t a = warp_min64(mn[d]), b = warp_max64(mx[d]);
     if (lane == 0) {
       s[0][d][w] = a;
       s[1][d][w] = b;
@@ -68,22 +91,67 @@ k_bbox_partial(int64_t n, const double* __restrict__ xyz, const double* __restri
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     for (int d = 0; d < 3; ++d) {
-      double a = s[0][d][0], b = s[1][d][0];
+      int64_t a = s[0][d][0], b = s[1][d][0];
       for (int k = 1; k < BB_THREADS / 32; ++k) {
-        a = fmin(a, s[0][d][k]);
-        b = fmax(b, s[1][d][k]);
+        a = min(a, s[0][d][k]);
+        b = max(b, s[1][d][k]);
       }
-      part[6 * blockIdx.x + d] = a;
-      part[6 * blockIdx.x + 3 + d] = b;
+      part[6 * blockIdx.x + d] = dkey_inv(a);
+      part[6 * blockIdx.x + 3 + d] = dkey_inv(b);
     }
     if (bad) atomicOr(&counters[CNT_BAD], 1);
   }
 }
 
+// Leaf cell of coordinate x along one axis: floor(((x - lo) / W) * 2^leaf)
+// clamped to the cube.  Multiplying by 2^leaf is exact; the subtraction and
+// the division are the IEEE round-to-nearest operations, written out so
+// nothing is contracted.  Each step rounds monotonically, so the cell is a
+// nondecreasing function of x.
+__device__ inline int cell_of(double x, double lo, double W, int leaf) {
+  const double t = __ddiv_rn(__dsub_rn(x, lo), W);
+  const double u = floor(__dmul_rn(t, (double)(1u << leaf)));
+  const int top = (1 << leaf) - 1;
+  return (u >= 0.0) ? (u <= (double)top ? (int)u : top) : 0;
+}
+
+// Order key of the smallest double x with cell_of(x) >= k (1 <= k <= top):
+// bracketed around lo + k W 2^-leaf, then bisected over order keys.  The
+// bracket holds cell_of(a) < k <= cell_of(b); cell_of(lo) = 0 and
+// cell_of(DBL_MAX) = top bound it, and every key in [dkey(lo), dkey(DBL_MAX)]
+// is a finite double.
+__device__ int64_t cell_threshold(double lo, double W, int leaf, int k) {
+  const int64_t kmin = dkey(lo), kmax = dkey(DBL_MAX);
+  int64_t m = dkey(lo + W * ((double)k / (double)(1 << leaf)));
+  m = min(max(m, kmin), kmax);
+  int64_t a = m, b = m;
+  uint64_t step = 16;
+  while (a > kmin && cell_of(dkey_inv(a), lo, W, leaf) >= k) {
+    a = ((uint64_t)a - (uint64_t)kmin > step) ? (int64_t)((uint64_t)a - step) : kmin;
+    step = min(step << 1, (uint64_t)1 << 62);  // every pass moves; at most ~64 passes
+  }
+  step = 16;
+  while (b < kmax && cell_of(dkey_inv(b), lo, W, leaf) < k) {
+    b = ((uint64_t)kmax - (uint64_t)b > step) ? (int64_t)((uint64_t)b + step) : kmax;
+    step = min(step << 1, (uint64_t)1 << 62);
+  }
+  while ((uint64_t)b - (uint64_t)a > 1) {
+    const int64_t mid = (int64_t)((uint64_t)a + (((uint64_t)b - (uint64_t)a) >> 1));
+    if (cell_of(dkey_inv(mid), lo, W, leaf) >= k) b = mid;
+    else a = mid;
+  }
+  return b;
+}
+
 // Root cube: corner = minimum per axis, side = largest extent (1 if zero).
-// One block reduces the per-block partials (min and max are exact in any order).
+// Every block reduces the per-block partials (min and max are exact in any
+// order); block 0 writes box[0..3] and the leaf frame of k_gather:
+// box[4] = 2^-e (W = m 2^e, 1 <= m < 2) and box[5] holding the FP32 pair
+// Rh + Rl = 2^leaf / m.  With thr given, the blocks then fill the cell
+// thresholds of the leaf level, thr[d 2^leaf + k] = cell_threshold(k) for
+// k = 1 .. 2^leaf - 1 (the cell of x along axis d is the number of them <= x).
 __global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* __restrict__ part,
-                                                    double* __restrict__ box) {
+                                                    double* __restrict__ box, int leaf, int64_t* __restrict__ thr) {
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
     for (int d = 0; d < 3; ++d) {
@@ -91,6 +159,7 @@ __global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* _
       mx[d] = fmax(mx[d], part[6 * b + 3 + d]);
     }
   __shared__ double s[2][3][8];
+  __shared__ double cube[4];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int d = 0; d < 3; ++d) {
     const double a = warp_min(mn[d]), b = warp_max(mx[d]);
@@ -100,40 +169,64 @@ __global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* _
     }
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double w3 = 0.0, lo[3];
-  for (int d = 0; d < 3; ++d) {
-    double a = s[0][d][0], b = s[1][d][0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-      a = fmin(a, s[0][d][k]);
-      b = fmax(b, s[1][d][k]);
+  if (threadIdx.x == 0) {
+    double w3 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double a = s[0][d][0], b = s[1][d][0];
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+        a = fmin(a, s[0][d][k]);
+        b = fmax(b, s[1][d][k]);
+      }
+      cube[d] = a;
+      w3 = fmax(w3, __dsub_rn(b, a));
     }
-    lo[d] = a;
-    w3 = fmax(w3, __dsub_rn(b, a));
+    cube[3] = (w3 > 0.0) ? w3 : 1.0;
+    if (blockIdx.x == 0) {
+      for (int d = 0; d < 4; ++d) box[d] = cube[d];
+      int e = 0;
+      frexp(cube[3], &e);  // W = m 2^(e - 1), 1 <= m < 2
+      e = min(max(e - 1, -1021), 1021);
+      const double scl = ldexp(1.0, -e);
+      const double R = __ddiv_rn((double)(1u << leaf), __dmul_rn(cube[3], scl));
+      const float Rh = __double2float_rn(R);
+      box[4] = scl;
+      float* f = (float*)(box + 5);
+      f[0] = Rh;
+      f[1] = __double2float_rn(__dsub_rn(R, (double)Rh));
+      if (thr)
+        for (int d = 0; d < 3; ++d) thr[d << leaf] = INT64_MIN;  // never read by the search
+    }
   }
-  for (int d = 0; d < 3; ++d) box[d] = lo[d];
-  box[3] = (w3 > 0.0) ? w3 : 1.0;
+  if (!thr) return;
+  __syncthreads();
+  const int top = (1 << leaf) - 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * top; t += gridDim.x * blockDim.x) {
+    const int d = t / top, k = t - d * top + 1;
+    thr[(d << leaf) + k] = cell_threshold(cube[d], cube[3], leaf, k);
+  }
 }
 
-// Leaf-level key: per axis floor(((x - lo) / W) * 2^leaf) clamped to the cube.
-// Multiplying by 2^leaf is exact; the subtraction and the division are the
-// IEEE round-to-nearest operations, written out so nothing is contracted.
-__global__ void k_morton(int64_t n, const double* __restrict__ xyz, const double* __restrict__ box,
-                         int leaf, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double W = box[3];
-  const double scale = (double)(1u << leaf);
-  const int top = (1 << leaf) - 1;
-  uint32_t c[3];
-  for (int d = 0; d < 3; ++d) {
-    double t = __ddiv_rn(__dsub_rn(xyz[3 * i + d], box[d]), W);
-    double u = floor(__dmul_rn(t, scale));
-    int v = (u >= 0.0) ? (u <= (double)top ? (int)u : top) : 0;
-    c[d] = (uint32_t)v;
+// Leaf-level key: per axis the number of cell thresholds <= x (the rule of
+// cell_of, exactly), found by binary search over the table in shared memory.
+__global__ void __launch_bounds__(256) k_morton(int64_t n, const double* __restrict__ xyz,
+                                                const int64_t* __restrict__ thr, int leaf,
+                                                uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+  extern __shared__ int64_t sthr[];
+  for (int t = threadIdx.x; t < (3 << leaf); t += blockDim.x) sthr[t] = thr[t];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[3];
+    for (int d = 0; d < 3; ++d) {
+      const int64_t kx = dkey(xyz[3 * i + d]);
+      const int64_t* T = sthr + (d << leaf);
+      int pos = 0;
+      for (int step = 1 << leaf >> 1; step > 0; step >>= 1)
+        if (T[pos + step] <= kx) pos += step;
+      c[d] = (uint32_t)pos;
+    }
+    key[i] = morton3(c[0], c[1], c[2]);
+    idx[i] = (uint32_t)i;
   }
-  key[i] = morton3(c[0], c[1], c[2]);
-  idx[i] = (uint32_t)i;
 }
 
 // ---- stable LSD radix sort (8-bit digits) -------------------------------------
@@ -310,12 +403,48 @@ k_radix_scatter(int64_t n, const uint32_t* __restrict__ kin, const uint32_t* __r
   }
 }
 
-// Morton-ordered particle copies: FP64 (x, y, z, q) and FP32 leaf-local
-// coordinates ((x - c) / w, ..., q) computed in FP64 and rounded once, plus
-// the rounding residual of each coordinate.
+// Root cube, leaf frame and cell thresholds (k_bbox_final), then the keys
+// (k_morton); part holds the per-block partials of k_bbox_partial.
+void launch_cube_keys(cudaStream_t s, int64_t n, const double* xyz, int nbb, const double* part, double* box,
+                      int64_t* thr, int leaf, uint32_t* key, uint32_t* idx) {
+  const int top = (1 << leaf) - 1;
+  k_bbox_final<<<std::max(1, ceil_div(3 * top, 256)), 256, 0, s>>>(nbb, part, box, leaf, thr);
+  const int64_t nb = std::min<int64_t>(ceil_div(n, 256), 148 * 8);
+  k_morton<<<(int)nb, 256, (size_t)(3 << leaf) * sizeof(int64_t), s>>>(n, xyz, thr, leaf, key, idx);
+}
+
+// Leaf-frame coordinate along one axis, v = (x - lo) / w - (i + 1/2) with w
+// the leaf width and i the leaf's cell, split as hi + lo: hi on the grid of
+// multiples of 2^-23 (|hi| <= 1/2 + 2^-23: hi plus a neighbour shift of +-1
+// and the difference of two such values are exact in FP32, which the near
+// field relies on) and lo the remainder.  One FP64 subtraction and an exact
+// power-of-two scaling give d = (x - lo) 2^-e; d is cut into two FP32 words
+// (the upper 24 significand bits and the rounded rest) and multiplied by
+// 2^leaf / (W 2^-e), held as two FP32 words, in double-float arithmetic:
+// Dekker's product with an FMA for the leading term, Knuth's two-sum for the
+// offset from the cell centre.  v carries ~2^-46 relative error of
+// (x - lo) / w, i.e. about 2^(leaf - 46) leaf widths.
+__device__ inline void leaf_frame(double x, double lo, double scl, float Rh, float Rl, int i, float& hi,
+                                  float& rest) {
+  const double d = __dmul_rn(__dsub_rn(x, lo), scl);
+  const double d1 = __longlong_as_double(__double_as_longlong(d) & ~0x1fffffffLL);
+  const float dh = __double2float_rn(d1), dl = __double2float_rn(__dsub_rn(d, d1));
+  const float p = __fmul_rn(dh, Rh);
+  const float e = __fmaf_rn(dh, Rl, __fmaf_rn(dl, Rh, __fmaf_rn(dh, Rh, -p)));
+  const float c = __fadd_rn((float)i, 0.5f);
+  const float s = __fsub_rn(p, c);
+  const float bv = __fsub_rn(s, p);
+  const float t = __fadd_rn(__fadd_rn(__fsub_rn(p, __fsub_rn(s, bv)), __fsub_rn(-c, bv)), e);  // v = s + t
+  hi = __fsub_rn(__fadd_rn(__fadd_rn(s, t), 1.5f), 1.5f);
+  rest = __fadd_rn(__fsub_rn(s, hi), t);
+}
+
+// Morton-ordered particle copies: FP64 (x, y, z, q), FP32 leaf-frame
+// coordinates (hi, with q) and their remainders (leaf_frame; the frame
+// constants are box[4] and box[5], written by k_bbox_final).
 __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
                          const double* __restrict__ xyz, const double* __restrict__ q,
-                         const double* __restrict__ box, int leaf, int32_t* __restrict__ perm,
+                         const double* __restrict__ box, int32_t* __restrict__ perm,
                          double4* __restrict__ pos64, float4* __restrict__ pos32, float4* __restrict__ pos32lo) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -326,23 +455,14 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uin
   pos64[r] = make_double4(x, y, z, qq);
   int ix, iy, iz;
   demorton3(skey[r], ix, iy, iz);
-  double w = ldexp(box[3], -leaf);
-  double cx = box[0] + ((double)ix + 0.5) * w;
-  double cy = box[1] + ((double)iy + 0.5) * w;
-  double cz = box[2] + ((double)iz + 0.5) * w;
-  // one FP64 division per particle (FP64 runs at 1/64 of the FP32 rate on
-  // this part); the leaf-frame offsets need ~2^-48 of a leaf width, not the
-  // correctly rounded quotient
-  const double iw = 1.0 / w;
-  const double vx = (x - cx) * iw, vy = (y - cy) * iw, vz = (z - cz) * iw;
-  // hi on the grid of multiples of 2^-23 leaf widths: with |hi| <= 1/2, hi
-  // plus a neighbour shift of +-1 and the difference of two such values
-  // (|.| <= 2) are exact in FP32, which the near field relies on; lo = the
-  // remainder (|lo| <= 2^-24) rounded to FP32.
-  const double Q = 8388608.0, iQ = 1.0 / 8388608.0;
-  const double hx = rint(vx * Q) * iQ, hy = rint(vy * Q) * iQ, hz = rint(vz * Q) * iQ;
-  pos32[r] = make_float4((float)hx, (float)hy, (float)hz, (float)qq);
-  pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
+  const double scl = box[4];
+  const float2 R = *(const float2*)(box + 5);
+  float hx, hy, hz, lx, ly, lz;
+  leaf_frame(x, box[0], scl, R.x, R.y, ix, hx, lx);
+  leaf_frame(y, box[1], scl, R.x, R.y, iy, hy, ly);
+  leaf_frame(z, box[2], scl, R.x, R.y, iz, hz, lz);
+  pos32[r] = make_float4(hx, hy, hz, (float)qq);
+  pos32lo[r] = make_float4(lx, ly, lz, 0.f);
 }
 
 // ---- batched problems (one tree over all problems' slots) ----------------------
@@ -362,7 +482,8 @@ __device__ inline int last_le(const A* __restrict__ a, int cnt, V v) {
 }
 
 // Per-block min/max of one problem's chunk (blocks of a problem are
-// consecutive: bstart[k] .. bstart[k+1]); raises the flag on non-finite input.
+// consecutive: bstart[k] .. bstart[k+1]; order keys as in k_bbox_partial);
+// raises the flag on non-finite input.
 __global__ void __launch_bounds__(BB_THREADS)
 k_fbox_partial(int nprob, const int32_t* __restrict__ bstart, const int64_t* __restrict__ pstart,
                const double* __restrict__ xyz, const double* __restrict__ q, double* __restrict__ part,
@@ -370,21 +491,22 @@ k_fbox_partial(int nprob, const int32_t* __restrict__ bstart, const int64_t* __r
   const int k = last_le(bstart, nprob, (int32_t)blockIdx.x);
   const int64_t beg = pstart[k] + (int64_t)(blockIdx.x - bstart[k]) * FB_CHUNK;
   const int64_t end = min(pstart[k + 1], beg + FB_CHUNK);
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int64_t mn[3] = {KEY_PINF, KEY_PINF, KEY_PINF}, mx[3] = {KEY_NINF, KEY_NINF, KEY_NINF};
   int bad = 0;
   for (int64_t i = beg + threadIdx.x; i < end; i += BB_THREADS) {
     for (int d = 0; d < 3; ++d) {
-      const double v = xyz[3 * i + d];
-      bad |= !isfinite(v);
-      mn[d] = fmin(mn[d], v);
-      mx[d] = fmax(mx[d], v);
+      const int64_t b = __double_as_longlong(xyz[3 * i + d]);
+      bad |= bits_nonfinite(b);
+      const int64_t kk = b ^ ((b >> 63) & INT64_MAX);
+      mn[d] = min(mn[d], kk);
+      mx[d] = max(mx[d], kk);
     }
-    bad |= !isfinite(q[i]);
+    bad |= bits_nonfinite(__double_as_longlong(q[i]));
   }
-  __shared__ double sm[2][3][BB_THREADS / 32];
+  __shared__ int64_t sm[2][3][BB_THREADS / 32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int d = 0; d < 3; ++d) {
-    const double a = warp_min(mn[d]), b = warp_max(mx[d]);
+    const int64_t a = warp_min64(mn[d]), b = warp_max64(mx[d]);
     if (lane == 0) {
       sm[0][d][w] = a;
       sm[1][d][w] = b;
@@ -393,23 +515,26 @@ k_fbox_partial(int nprob, const int32_t* __restrict__ bstart, const int64_t* __r
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     for (int d = 0; d < 3; ++d) {
-      double a = sm[0][d][0], b = sm[1][d][0];
+      int64_t a = sm[0][d][0], b = sm[1][d][0];
       for (int j = 1; j < BB_THREADS / 32; ++j) {
-        a = fmin(a, sm[0][d][j]);
-        b = fmax(b, sm[1][d][j]);
+        a = min(a, sm[0][d][j]);
+        b = max(b, sm[1][d][j]);
       }
-      part[6 * blockIdx.x + d] = a;
-      part[6 * blockIdx.x + 3 + d] = b;
+      part[6 * blockIdx.x + d] = dkey_inv(a);
+      part[6 * blockIdx.x + 3 + d] = dkey_inv(b);
     }
     if (bad) atomicOr(&counters[CNT_BAD], 1);
   }
 }
 
-// Root cube of each problem (one block per problem; the rule of k_bbox_final)
-// and its output scale lambda_k = 2^-S_k / W_k.
+// Root cube of each problem (one block per problem; the rule of k_bbox_final),
+// its output scale lambda_k = 2^-S_k / W_k, its leaf frame (frame[4k]: 2^-e,
+// the FP32 pair 2^L / (W 2^-e), 1 / W) and its cell thresholds (thr +
+// prob[k].thr, laid out as in k_bbox_final).
 __global__ void __launch_bounds__(256)
 k_fbox_final(const int32_t* __restrict__ bstart, const double* __restrict__ part,
-             const BatchProb* __restrict__ prob, double* __restrict__ fbox, double* __restrict__ fscale) {
+             const BatchProb* __restrict__ prob, double* __restrict__ fbox, double* __restrict__ fscale,
+             double* __restrict__ frame, int64_t* __restrict__ thr) {
   const int k = blockIdx.x;
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int b = bstart[k] + threadIdx.x; b < bstart[k + 1]; b += blockDim.x)
@@ -427,56 +552,78 @@ k_fbox_final(const int32_t* __restrict__ bstart, const double* __restrict__ part
     }
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const bool empty = bstart[k + 1] == bstart[k];
-  double w3 = 0.0, lo[3];
-  for (int d = 0; d < 3; ++d) {
-    double a = sm[0][d][0], b = sm[1][d][0];
-    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
-      a = fmin(a, sm[0][d][j]);
-      b = fmax(b, sm[1][d][j]);
+  __shared__ double cube[4];
+  const BatchProb pb = prob[k];
+  if (threadIdx.x == 0) {
+    const bool empty = bstart[k + 1] == bstart[k];
+    double w3 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double a = sm[0][d][0], b = sm[1][d][0];
+      for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+        a = fmin(a, sm[0][d][j]);
+        b = fmax(b, sm[1][d][j]);
+      }
+      cube[d] = empty ? 0.0 : a;
+      w3 = empty ? 0.0 : fmax(w3, __dsub_rn(b, a));
     }
-    lo[d] = empty ? 0.0 : a;
-    w3 = empty ? 0.0 : fmax(w3, __dsub_rn(b, a));
+    const double W = (w3 > 0.0) ? w3 : 1.0;
+    cube[3] = W;
+    for (int d = 0; d < 4; ++d) fbox[4 * k + d] = cube[d];
+    fscale[k] = __ddiv_rn(ldexp(1.0, -pb.S), W);
+    int e = 0;
+    frexp(W, &e);
+    e = min(max(e - 1, -1021), 1021);
+    const double scl = ldexp(1.0, -e);
+    const double R = __ddiv_rn((double)(1u << pb.L), __dmul_rn(W, scl));
+    const float Rh = __double2float_rn(R);
+    frame[4 * k] = scl;
+    float* f = (float*)(frame + 4 * k + 1);
+    f[0] = Rh;
+    f[1] = __double2float_rn(__dsub_rn(R, (double)Rh));
+    frame[4 * k + 2] = 1.0 / W;
+    for (int d = 0; d < 3; ++d) thr[pb.thr + (d << pb.L)] = INT64_MIN;  // never read by the search
   }
-  const double W = (w3 > 0.0) ? w3 : 1.0;
-  for (int d = 0; d < 3; ++d) fbox[4 * k + d] = lo[d];
-  fbox[4 * k + 3] = W;
-  fscale[k] = __ddiv_rn(ldexp(1.0, -prob[k].S), W);
+  __syncthreads();
+  const int top = (1 << pb.L) - 1;
+  for (int t = threadIdx.x; t < 3 * top; t += blockDim.x) {
+    const int d = t / top, kk = t - d * top + 1;
+    thr[pb.thr + (d << pb.L) + kk] = cell_threshold(cube[d], cube[3], pb.L, kk);
+  }
 }
 
 // Forest leaf key of every particle: the slot's first key + the key the
-// single-problem rule (k_morton) gives in the problem's own cube.
+// single-problem rule (cell_of) gives in the problem's own cube, read off the
+// problem's cell thresholds by binary search.
 __global__ void k_fmorton(int64_t n, int nprob, const int64_t* __restrict__ pstart,
-                          const BatchProb* __restrict__ prob, const double* __restrict__ fbox,
+                          const BatchProb* __restrict__ prob, const int64_t* __restrict__ thr,
                           const double* __restrict__ xyz, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int k = last_le(pstart, nprob, i);
-  const double* box = fbox + 4 * k;
-  const int L = prob[k].L;
-  const double W = box[3];
-  const double scale = (double)(1u << L);
-  const int top = (1 << L) - 1;
+  const BatchProb pb = prob[k];
   uint32_t c[3];
   for (int d = 0; d < 3; ++d) {
-    const double t = __ddiv_rn(__dsub_rn(xyz[3 * i + d], box[d]), W);
-    const double u = floor(__dmul_rn(t, scale));
-    const int v = (u >= 0.0) ? (u <= (double)top ? (int)u : top) : 0;
-    c[d] = (uint32_t)v;
+    const int64_t kx = dkey(xyz[3 * i + d]);
+    const int64_t* T = thr + pb.thr + (d << pb.L);
+    int pos = 0;
+    for (int step = 1 << pb.L >> 1; step > 0; step >>= 1)
+      if (__ldg(T + pos + step) <= kx) pos += step;
+    c[d] = (uint32_t)pos;
   }
-  key[i] = prob[k].slot_key + morton3(c[0], c[1], c[2]);
+  key[i] = pb.slot_key + morton3(c[0], c[1], c[2]);
   idx[i] = (uint32_t)i;
 }
 
 // Morton-ordered copies of a batch: FP64 positions mapped into the forest
-// cube (x' = o_k + t 2^-S_k, t = (x - lo_k) / W_k), FP32 leaf-local
-// coordinates from the problem's own cube exactly as k_gather computes them.
+// cube (x' = o_k + t 2^-S_k, t = (x - lo_k) / W_k with the correctly rounded
+// 1 / W_k), FP32 leaf-frame coordinates from the problem's own cube
+// (leaf_frame with the problem's frame).
 __global__ void k_fgather(int64_t n, int nprob, const int64_t* __restrict__ pstart,
                           const BatchProb* __restrict__ prob, const double* __restrict__ fbox,
-                          const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
-                          const double* __restrict__ xyz, const double* __restrict__ q, int32_t* __restrict__ perm,
-                          double4* __restrict__ pos64, float4* __restrict__ pos32, float4* __restrict__ pos32lo) {
+                          const double* __restrict__ frame, const uint32_t* __restrict__ skey,
+                          const uint32_t* __restrict__ sidx, const double* __restrict__ xyz,
+                          const double* __restrict__ q, int32_t* __restrict__ perm, double4* __restrict__ pos64,
+                          float4* __restrict__ pos32, float4* __restrict__ pos32lo) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint32_t i = sidx[r];
@@ -488,21 +635,20 @@ __global__ void k_fgather(int64_t n, int nprob, const int64_t* __restrict__ psta
   const double qq = q[i];
   int ox, oy, oz;
   demorton3(pb.slot_key >> (3 * pb.L), ox, oy, oz);
-  const double W = box[3], ws = ldexp(1.0, -pb.S), iW = 1.0 / W;
+  const double ws = ldexp(1.0, -pb.S), iW = frame[4 * k + 2];
   const double tx = (x - box[0]) * iW, ty = (y - box[1]) * iW, tz = (z - box[2]) * iW;
   pos64[r] = make_double4(__dadd_rn((double)ox * ws, __dmul_rn(tx, ws)), __dadd_rn((double)oy * ws, __dmul_rn(ty, ws)),
                           __dadd_rn((double)oz * ws, __dmul_rn(tz, ws)), qq);
   int ix, iy, iz;
   demorton3(skey[r] - pb.slot_key, ix, iy, iz);
-  const double w = ldexp(W, -pb.L), iw = ldexp(iW, pb.L);
-  const double cx = box[0] + ((double)ix + 0.5) * w;
-  const double cy = box[1] + ((double)iy + 0.5) * w;
-  const double cz = box[2] + ((double)iz + 0.5) * w;
-  const double vx = (x - cx) * iw, vy = (y - cy) * iw, vz = (z - cz) * iw;
-  const double Q = 8388608.0, iQ = 1.0 / 8388608.0;
-  const double hx = rint(vx * Q) * iQ, hy = rint(vy * Q) * iQ, hz = rint(vz * Q) * iQ;
-  pos32[r] = make_float4((float)hx, (float)hy, (float)hz, (float)qq);
-  pos32lo[r] = make_float4((float)(vx - hx), (float)(vy - hy), (float)(vz - hz), 0.f);
+  const double scl = frame[4 * k];
+  const float2 R = *(const float2*)(frame + 4 * k + 1);
+  float hx, hy, hz, lx, ly, lz;
+  leaf_frame(x, box[0], scl, R.x, R.y, ix, hx, lx);
+  leaf_frame(y, box[1], scl, R.x, R.y, iy, hy, ly);
+  leaf_frame(z, box[2], scl, R.x, R.y, iz, hz, lz);
+  pos32[r] = make_float4(hx, hy, hz, (float)qq);
+  pos32lo[r] = make_float4(lx, ly, lz, 0.f);
 }
 
 // Problem of every cell of level l: the slot containing the cell's first
@@ -1008,8 +1154,9 @@ constexpr int64_t NA_IDX_A = NA_KEY_B + NOALLOC_MAX_N;
 constexpr int64_t NA_IDX_B = NA_IDX_A + NOALLOC_MAX_N;
 constexpr int64_t NA_HIST = NA_IDX_B + NOALLOC_MAX_N;
 constexpr int64_t NA_PART = NA_HIST + 256 * NOALLOC_TILES;          // doubles: 8-byte aligned
-constexpr int64_t NA_BOX = NA_PART + 2 * 6 * NOALLOC_BBOX_BLOCKS;   // 4 doubles
-constexpr int64_t NA_COUNTERS = NA_BOX + 2 * 4;                     // 128 int32
+constexpr int64_t NA_BOX = NA_PART + 2 * 6 * NOALLOC_BBOX_BLOCKS;   // 8 doubles
+constexpr int64_t NA_THR = NA_BOX + 2 * 8;                          // 3 << (FMM_MAX_LEVELS - 1) int64
+constexpr int64_t NA_COUNTERS = NA_THR + 2 * (3 << (FMM_MAX_LEVELS - 1));  // 128 int32
 constexpr int64_t NA_WORDS = NA_COUNTERS + 128;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
@@ -1065,6 +1212,7 @@ extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int
   uint32_t* hist = base + NA_HIST;
   double* part = (double*)(base + NA_PART);
   double* box = (double*)(base + NA_BOX);
+  int64_t* thr = (int64_t*)(base + NA_THR);
   int32_t* counters = (int32_t*)(base + NA_COUNTERS);
   const int Lf = height - 1;
   // the array keeps the previous call's contents: clear the input-error flag
@@ -1074,8 +1222,7 @@ extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int
   // positions only: the charge check of the cube kernel re-reads coordinates
   if (e == cudaSuccess) {
     k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, xyz, part, counters);
-    k_bbox_final<<<1, 256, 0, s>>>(nbb, part, box);
-    k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, box, Lf, ka, va);
+    launch_cube_keys(s, n, xyz, nbb, part, box, thr, Lf, ka, va);
     const int ntiles = ceil_div(n, RS_TILE);
     for (int sh = 0; sh < 3 * Lf; sh += 8) {
       k_radix_hist<<<ntiles, RS_THREADS, 0, s>>>(n, ka, sh, hist, ntiles);
@@ -1142,6 +1289,12 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
     start[k + 1] = start[k] + counts[k];
     prob[k] = BatchProb{0u, heights[k] - 1, 0, 0};
   }
+  int64_t nthr = 0;  // cell thresholds: 3 << L per problem
+  for (int k = 0; k < nprob; ++k) {
+    prob[k].thr = (int32_t)nthr;
+    nthr += (int64_t)3 << prob[k].L;
+  }
+  if (nthr > INT32_MAX) return set_err(c, FMM_ERR_ARG, "fmm_set_batch: too many problems in one batch");
   int Lf = 0;
   {
     std::vector<int64_t> slot(nprob), lev(nprob);
@@ -1177,12 +1330,13 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
     dfree(c, c->fb_prob, sizeof(BatchProb) * (size_t)c->fb_cap);
     dfree(c, c->fb_box, 32 * (size_t)c->fb_cap);
     dfree(c, c->fb_scale, 8 * (size_t)c->fb_cap);
+    dfree(c, c->fb_frame, 32 * (size_t)c->fb_cap);
     dfree(c, c->fb_sstart, 4 * (size_t)c->fb_cap);
     dfree(c, c->fb_sprob, 4 * (size_t)c->fb_cap);
     dfree(c, c->fb_bstart, 4 * (size_t)c->fb_cap);
     c->fb_pstart = nullptr;
     c->fb_prob = nullptr;
-    c->fb_box = c->fb_scale = nullptr;
+    c->fb_box = c->fb_scale = c->fb_frame = nullptr;
     c->fb_sstart = nullptr;
     c->fb_sprob = c->fb_bstart = nullptr;
     c->fb_cap = 0;
@@ -1196,6 +1350,8 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
     c->fb_box = (double*)p;
     FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
     c->fb_scale = (double*)p;
+    FMM_TRY(dalloc(c, &p, 32 * (size_t)cap));
+    c->fb_frame = (double*)p;
     FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
     c->fb_sstart = (uint32_t*)p;
     FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
@@ -1203,6 +1359,16 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
     FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
     c->fb_bstart = (int32_t*)p;
     c->fb_cap = cap;
+  }
+  if (nthr > c->fb_thr_cap) {
+    dfree(c, c->fb_thr, 8 * (size_t)c->fb_thr_cap);
+    c->fb_thr = nullptr;
+    c->fb_thr_cap = 0;
+    void* p;
+    const int64_t cap = nthr + nthr / 4 + 64;
+    FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
+    c->fb_thr = (int64_t*)p;
+    c->fb_thr_cap = cap;
   }
   // the tables are small; synchronous copies keep the host vectors' lifetime simple
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1429,8 +1595,9 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     const int nbb = c->fb_nblocks;
     double* part = (double*)c->scratch;
     k_fbox_partial<<<nbb, BB_THREADS, 0, s>>>(c->nprob, c->fb_bstart, c->fb_pstart, xyz, q, part, c->counters);
-    k_fbox_final<<<c->nprob, 256, 0, s>>>(c->fb_bstart, part, c->fb_prob, c->fb_box, c->fb_scale);
-    k_fmorton<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_box, xyz, c->key_a,
+    k_fbox_final<<<c->nprob, 256, 0, s>>>(c->fb_bstart, part, c->fb_prob, c->fb_box, c->fb_scale, c->fb_frame,
+                                          c->fb_thr);
+    k_fmorton<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_thr, xyz, c->key_a,
                                                c->idx_a);
     // the forest cube itself is the unit cube at the origin
     c->box_h[0] = c->box_h[1] = c->box_h[2] = 0.0;
@@ -1443,9 +1610,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     if (nbb > 1184) nbb = 1184;
     double* part = (double*)c->scratch;
     k_bbox_partial<<<nbb, BB_THREADS, 0, s>>>(n, xyz, q, part, c->counters);
-    k_bbox_final<<<1, 256, 0, s>>>(nbb, part, c->box);
-    // keys
-    k_morton<<<ceil_div(n, 256), 256, 0, s>>>(n, xyz, c->box, Lf, c->key_a, c->idx_a);
+    // cube, leaf frame, cell thresholds (scratch words 32768.., past the partials) and keys
+    launch_cube_keys(s, n, xyz, nbb, part, c->box, (int64_t*)(c->scratch + 32768), Lf, c->key_a, c->idx_a);
     c->launches_set += 3;
   }
   if (n > 0) {
@@ -1469,10 +1635,11 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     }
     c->skey = ka;
     if (c->forest)
-      k_fgather<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_box, ka, va, xyz, q,
+      k_fgather<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_box, c->fb_frame, ka,
+                                                 va, xyz, q,
                                                  c->perm, c->pos64, c->pos32, c->pos32lo);
     else
-      k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, Lf, c->perm, c->pos64, c->pos32,
+      k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, c->perm, c->pos64, c->pos32,
                                                 c->pos32lo);
     c->launches_set++;
     // levels
