@@ -985,8 +985,8 @@ def run_kernels(args):
         v["relative_to_laplace"] = round(v["ms_per_step"] / base, 3)
     print(json.dumps({"metric": "particles/s per kernel (one step: tree build + evaluation)", "unit": UNIT,
                       "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "dtype": "f32 (mixed: FP32 near field, tensor-core M2L on FP16 hi/lo operands, FP64 "
-                               "accumulation of outputs)",
+                      "dtype": "f32 (mixed: FP32 near field, tensor-core M2L on FP16 hi/lo operands, "
+                               "outputs written as FP64)",
                       "data": "synthetic", "config": {"workload": KERNELS_WORKLOAD, "n": n, "height": h,
                                                       "order": p, "precision": "mixed", "l2": "flushed"},
                       "kernels": out, "clocks": clk}))

@@ -295,7 +295,9 @@ fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
  * tensor-core M2L (out[4] = 2 or 5) takes FP16 hi/lo operands (the default;
  * 0: TF32 hi/lo, chosen at fmm_create by the environment variable
  * FMM_M2L_MATH=tf32, or a CUDA-core M2L),
- * out[6..7] = 0 (reserved).  out: 8 int64, host. */
+ * out[6] = evaluations that ran their launches without a CUDA graph because
+ * capturing the graph failed with a CUDA error (the same kernels, launched
+ * one by one), out[7] = 0 (reserved).  out: 8 int64, host. */
 fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
 
 /* Algorithmic work of one evaluation on the current tree (Sec. 4.3 counts

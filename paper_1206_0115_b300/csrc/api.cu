@@ -354,7 +354,7 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   if ((st = dalloc(c, &p, 128 * sizeof(int32_t))) != FMM_OK) return fail(st);
   c->counters = (int32_t*)p;
   if (cudaMallocHost((void**)&c->counters_h, 128 * sizeof(int32_t)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->box_h, 4 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->box_h, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->tc_err_h, sizeof(int32_t)) != cudaSuccess) {
     cuda_err(c, cudaGetLastError(), "fmm_create: pinned host buffers");
     return fail(FMM_ERR_OOM);
@@ -615,12 +615,22 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
     dphi = c->stage_out;
     dF = c->stage_out + n;
   }
-  if (c->use_graph) {
-    if (!c->graph_ok || c->graph_sig != graph_signature(c)) FMM_TRY(build_graph(c));
-    FMM_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
-  } else {
-    FMM_TRY(enqueue_eval(c, c->stream));
+  bool eager = !c->use_graph;
+  if (c->use_graph && (!c->graph_ok || c->graph_sig != graph_signature(c))) {
+    const fmm_status gs = build_graph(c);
+    if (gs != FMM_OK && gs != FMM_ERR_CUDA) return gs;
+    if (gs == FMM_ERR_CUDA) {
+      // the capture failed (a capture error is not sticky): the same launches
+      // run without a graph; a device fault fails them again and is returned
+      cudaGetLastError();
+      drop_graph(c);
+      c->graph_fallbacks++;
+      c->err[0] = 0;
+      eager = true;
+    }
   }
+  if (eager) FMM_TRY(enqueue_eval(c, c->stream));
+  else FMM_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
   if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[7], c->stream));
   FMM_TRY(launch_l2p_out(c, c->stream, dphi, dF));
   if (c->timing) FMM_CUDA(c, cudaEventRecord(c->tev[8], c->stream));
@@ -855,7 +865,8 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out) {
   out[3] = h->bytes;
   out[4] = m2l_kind(h);
   out[5] = (m2l_uses_f16(h) && (out[4] == 2 || out[4] == 5)) ? 1 : 0;  // the tensor-core kernels' operand form
-  out[6] = out[7] = 0;
+  out[6] = h->graph_fallbacks;  // evaluations run without a graph after a failed capture
+  out[7] = 0;
   return FMM_OK;
 }
 

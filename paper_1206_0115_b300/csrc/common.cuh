@@ -219,6 +219,7 @@ struct fmm_ctx {
   std::vector<int64_t> graph_sig;  // what the captured graph depends on
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  int64_t graph_fallbacks = 0;  // evaluations run without a graph after a failed capture
   bool graph_ok = false;
   int graph_precision = -1;
   bool use_graph = true;

@@ -388,18 +388,20 @@ k_l2l(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, T* __restrict__ Lb
 
 // ---------------------------------------------------------------- L2P + output
 
-// Far-field potential and field of one particle from its leaf's local
-// expansion Lr (C values; the mixed path's cell mean in Lr[C]) at xi, the
-// particle's position in the leaf's frame; a = the leaf's half-width.
+// Far-field potential of one particle from its leaf's local expansion Lr (C
+// values; the mixed path's cell mean in Lr[C]) at xi, the particle's position
+// in the leaf's frame, and the potential's derivatives with respect to xi
+// (the field is -1/a times them, a = the leaf's half-width).
 template <int P, typename T, bool MIXED>
 __device__ __forceinline__ void l2p_eval(const T* __restrict__ Lrow, const T* __restrict__ sC, const T xi[3],
-                                         double a, double& pf, double& gx, double& gy, double& gz) {
+                                         T& pf, T& ax, T& ay, T& az) {
   constexpr int C = P * P * P;
   T Sx[P], Sy[P], Sz[P], dSx[P], dSy[P], dSz[P];
   interp_weights<P, T, true>(sC, xi[0], Sx, dSx);
   interp_weights<P, T, true>(sC, xi[1], Sy, dSy);
   interp_weights<P, T, true>(sC, xi[2], Sz, dSz);
-  T f = T(0), ax = T(0), ay = T(0), az = T(0);
+  T f = T(0);
+  ax = ay = az = T(0);
   // the x loop stays rolled: unrolling all P^3 terms needs more registers
   // than occupancy allows
 #pragma unroll 1
@@ -420,10 +422,7 @@ __device__ __forceinline__ void l2p_eval(const T* __restrict__ Lrow, const T* __
       az += sxy * dz;
     }
   }
-  pf = (double)f + (MIXED ? (double)Lrow[C] : 0.0);  // mixed: cell mean + deviations
-  gx = -(double)ax / a;
-  gy = -(double)ay / a;
-  gz = -(double)az / a;
+  pf = MIXED ? f + Lrow[C] : f;  // mixed: cell mean + deviations
 }
 
 // xi of particle r in its leaf's frame
@@ -443,31 +442,41 @@ __device__ __forceinline__ void leaf_xi(int64_t r, const double4* __restrict__ p
   }
 }
 
-// far + near, scaled to the problem's units, scattered to the caller's order
-template <bool MIXED>
-__device__ __forceinline__ void l2p_store(int64_t r, double pf, double gx, double gy, double gz, double lam,
-                                          double lam2, const float4* __restrict__ near32,
+// far + near, scaled to the problem's units (scaled: a batched tree, lam and
+// lam2 the factors of phi and F), scattered to the caller's order.  Mixed:
+// the far field (FP32, field = -ia times the xi derivatives, ia = 1 / a) and
+// the FP32 near field are added in FP32 and widened to FP64 for the output;
+// FP64: everything in FP64.
+template <typename T, bool MIXED>
+__device__ __forceinline__ void l2p_store(int64_t r, T pf, T ax, T ay, T az, double a, float ia, bool scaled,
+                                          double lam, double lam2, const float4* __restrict__ near32,
                                           const double4* __restrict__ near64, const int32_t* __restrict__ perm,
                                           double* __restrict__ phi, double* __restrict__ F) {
-  double nphi, nx, ny, nz;
+  const int64_t i = perm[r];
+  double v[4];
   if (MIXED) {
     const float4 nr = near32[r];
-    nphi = nr.x;
-    nx = nr.y;
-    ny = nr.z;
-    nz = nr.w;
+    v[0] = (double)((float)pf + nr.x);
+    v[1] = (double)fmaf(-(float)ax, ia, nr.y);
+    v[2] = (double)fmaf(-(float)ay, ia, nr.z);
+    v[3] = (double)fmaf(-(float)az, ia, nr.w);
   } else {
     const double4 nr = near64[r];
-    nphi = nr.x;
-    nx = nr.y;
-    ny = nr.z;
-    nz = nr.w;
+    v[0] = (double)pf + nr.x;
+    v[1] = -(double)ax / a + nr.y;
+    v[2] = -(double)ay / a + nr.z;
+    v[3] = -(double)az / a + nr.w;
   }
-  const int64_t i = perm[r];
-  phi[i] = (pf + nphi) * lam;
-  F[3 * i] = (gx + nx) * lam2;
-  F[3 * i + 1] = (gy + ny) * lam2;
-  F[3 * i + 2] = (gz + nz) * lam2;
+  if (scaled) {
+    v[0] *= lam;
+    v[1] *= lam2;
+    v[2] *= lam2;
+    v[3] *= lam2;
+  }
+  phi[i] = v[0];
+  F[3 * i] = v[1];
+  F[3 * i + 1] = v[2];
+  F[3 * i + 2] = v[3];
 }
 
 // One warp per leaf: the leaf's local expansion is staged in shared memory
@@ -495,8 +504,9 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
   }
   __syncwarp();
   const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
-  double ctr[3], a;
-  cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  double ctr[3] = {0.0, 0.0, 0.0}, a = 1.0;
+  if (!MIXED) cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  const float ia = MIXED ? __double2float_rn(box[6]) : 1.f;
   // batched trees: back from the forest cube to the problem's own units
   // (distances there are lambda times the problem's: phi scales by lambda^s,
   // F by lambda^(s+1))
@@ -504,13 +514,13 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
   const double lam = prob >= 0 ? kernel_scale(fscale[prob], ks) : 1.0;
   const double lam2 = prob >= 0 ? lam * fscale[prob] : 1.0;
   for (int r = first + lane; r < first + cnt; r += 32) {
-    double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    T pf = T(0), ax = T(0), ay = T(0), az = T(0);
     if (has_far) {
       T xi[3];
       leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
-      l2p_eval<P, T, MIXED>(myL, sC, xi, a, pf, gx, gy, gz);
+      l2p_eval<P, T, MIXED>(myL, sC, xi, pf, ax, ay, az);
     }
-    l2p_store<MIXED>(r, pf, gx, gy, gz, lam, lam2, near32, near64, perm, phi, F);
+    l2p_store<T, MIXED>(r, pf, ax, ay, az, a, ia, prob >= 0, lam, lam2, near32, near64, perm, phi, F);
   }
 }
 
@@ -531,18 +541,19 @@ k_l2p_pp(LevelPtrs lv, int leaf, int64_t n, const int32_t* __restrict__ pleaf, c
   const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
   if (r >= n) return;
   const int cell = pleaf[r];
-  double ctr[3], a;
-  cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  double ctr[3] = {0.0, 0.0, 0.0}, a = 1.0;
+  if (!MIXED) cell_centre(box, leaf, lv.key[leaf][cell], ctr, a);
+  const float ia = MIXED ? __double2float_rn(box[6]) : 1.f;
   const int prob = fscale ? lv.slot[leaf][cell] : -1;
   const double lam = prob >= 0 ? kernel_scale(fscale[prob], ks) : 1.0;
   const double lam2 = prob >= 0 ? lam * fscale[prob] : 1.0;
-  double pf = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  T pf = T(0), ax = T(0), ay = T(0), az = T(0);
   if (has_far) {
     T xi[3];
     leaf_xi<T, MIXED>(r, pos64, pos32, ctr, a, xi);
-    l2p_eval<P, T, MIXED>(L + (lv.row_off[leaf] + cell) * (int64_t)cpad, sC, xi, a, pf, gx, gy, gz);
+    l2p_eval<P, T, MIXED>(L + (lv.row_off[leaf] + cell) * (int64_t)cpad, sC, xi, pf, ax, ay, az);
   }
-  l2p_store<MIXED>(r, pf, gx, gy, gz, lam, lam2, near32, near64, perm, phi, F);
+  l2p_store<T, MIXED>(r, pf, ax, ay, az, a, ia, prob >= 0, lam, lam2, near32, near64, perm, phi, F);
 }
 
 // ---------------------------------------------------------------- M2L (SIMT)

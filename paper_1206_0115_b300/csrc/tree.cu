@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -145,9 +146,10 @@ __device__ int64_t cell_threshold(double lo, double W, int leaf, int k) {
 
 // Root cube: corner = minimum per axis, side = largest extent (1 if zero).
 // Every block reduces the per-block partials (min and max are exact in any
-// order); block 0 writes box[0..3] and the leaf frame of k_gather:
-// box[4] = 2^-e (W = m 2^e, 1 <= m < 2) and box[5] holding the FP32 pair
-// Rh + Rl = 2^leaf / m.  With thr given, the blocks then fill the cell
+// order); block 0 writes box[0..3], the leaf frame of k_gather, box[4] =
+// 2^-e (W = m 2^e, 1 <= m < 2) and box[5] holding the FP32 pair
+// Rh + Rl = 2^leaf / m, and box[6] = 2^(leaf + 1) / W, the reciprocal of a
+// leaf's half-width.  With thr given, the blocks then fill the cell
 // thresholds of the leaf level, thr[d 2^leaf + k] = cell_threshold(k) for
 // k = 1 .. 2^leaf - 1 (the cell of x along axis d is the number of them <= x).
 __global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* __restrict__ part,
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(256) k_bbox_final(int nblocks, const double* _
       const double R = __ddiv_rn((double)(1u << leaf), __dmul_rn(cube[3], scl));
       const float Rh = __double2float_rn(R);
       box[4] = scl;
+      box[6] = __ddiv_rn((double)(2u << leaf), cube[3]);  // 1 / (half-width of a leaf)
       float* f = (float*)(box + 5);
       f[0] = Rh;
       f[1] = __double2float_rn(__dsub_rn(R, (double)Rh));
@@ -1600,9 +1603,16 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     k_fmorton<<<ceil_div(n, 256), 256, 0, s>>>(n, c->nprob, c->fb_pstart, c->fb_prob, c->fb_thr, xyz, c->key_a,
                                                c->idx_a);
     // the forest cube itself is the unit cube at the origin
+    // (and its leaf constants as k_bbox_final writes them: 2^-e = 1,
+    // 2^Lf / m = 2^Lf exactly, 1 / half-width = 2^(Lf + 1))
     c->box_h[0] = c->box_h[1] = c->box_h[2] = 0.0;
     c->box_h[3] = 1.0;
-    FMM_CUDA(c, cudaMemcpyAsync(c->box, c->box_h, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+    c->box_h[4] = 1.0;
+    const float R2[2] = {(float)(1u << Lf), 0.f};
+    memcpy(c->box_h + 5, R2, sizeof(R2));
+    c->box_h[6] = (double)(2u << Lf);
+    c->box_h[7] = 0.0;
+    FMM_CUDA(c, cudaMemcpyAsync(c->box, c->box_h, 8 * sizeof(double), cudaMemcpyHostToDevice, s));
     c->launches_set += 3;
   } else if (n > 0) {
     // bounding cube

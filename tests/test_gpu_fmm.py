@@ -59,6 +59,9 @@ def _run(F, xyz, q, h, p, precision, host=False, m2l=SVD):
             f.evaluate(phi_t, F_t)
             torch.cuda.synchronize()
             phi, Fo = phi_t.cpu().numpy(), F_t.cpu().numpy()
+        # the evaluation replayed its CUDA graph (no launch-by-launch fallback)
+        st = f.stats()
+        assert int(st[2]) == 1 and int(st[6]) == 0, list(st)
     return phi, Fo
 
 
