@@ -113,12 +113,12 @@ def _dup_faces():
     return xyz, q
 
 
-def _near_faces():
+def _near_faces(lo=-0.3, W=1.7, L=6, seed=41):
     """Coordinates a few ulps either side of leaf faces of a box that is not a
-    power of two wide (lo = -0.3, W = 1.7): the quotient (x - lo) / W and its
-    product with the reciprocal can round to opposite sides of a face."""
-    rng = np.random.default_rng(41)
-    lo, W, L = -0.3, 1.7, 6
+    power of two wide (by default lo = -0.3, W = 1.7): the quotient
+    (x - lo) / W and its product with the reciprocal can round to opposite
+    sides of a face."""
+    rng = np.random.default_rng(seed)
     faces = lo + np.arange(1, 2 ** L) * (W / 2 ** L)
     pick = faces[rng.integers(0, len(faces), size=(6000, 3))]
     steps = rng.integers(-6, 7, size=pick.shape)
@@ -131,9 +131,25 @@ def _near_faces():
     return np.ascontiguousarray(xyz), np.ones(len(xyz))
 
 
+def _coarse_doubles():
+    """A cube at 3e15 where one ulp (0.5) spans 8 of the 1024 leaf cells per
+    axis: consecutive doubles skip cells, so several cell faces share one
+    smallest double."""
+    rng = np.random.default_rng(45)
+    xyz = 3.0e15 + 0.5 * rng.integers(0, 129, size=(5000, 3)).astype(np.float64)
+    xyz[0] = 3.0e15
+    xyz[1] = 3.0e15 + 64.0
+    return xyz, np.ones(len(xyz))
+
+
 @pytest.mark.parametrize("name,make,h", TREE_CASES + [("golden_faces", _golden_points, 4),
                                                      ("duplicates_faces", _dup_faces, 4),
                                                      ("near_faces_h7", _near_faces, 7),
+                                                     ("near_faces_offset_h11",
+                                                      lambda: _near_faces(1.0e7, 1e-3, 10, 43), 11),
+                                                     ("near_faces_zero_h5",
+                                                      lambda: _near_faces(-0.5, 1.0, 4, 44), 5),
+                                                     ("coarse_doubles_h11", _coarse_doubles, 11),
                                                      ("h1", lambda: inputs.particles(300, 5, "cube", "pos"), 1),
                                                      ("h2", lambda: inputs.particles(300, 5, "cube", "pos"), 2)])
 def test_tree_bit_exact(F, name, make, h):
