@@ -1,9 +1,9 @@
 #!/usr/bin/env python
 """Throughput of the black-box FMM on B300: particles per second for one full
-pass (tree build + evaluation of potentials and forces) over 1e6 points
-uniform in the unit cube, height 6, order 7, mixed precision.
+pass (tree build + evaluation of potentials and forces), mixed precision.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--only-main]
 
 One JSON line on stdout (rank 0).  A step is fmm_set_particles + fmm_evaluate
 on device-resident inputs (all hot-path stages: box, Morton keys, sort, tree,
@@ -11,9 +11,22 @@ P2M, M2M, M2L, L2L, L2P, P2P, output).  Each step is bracketed by CUDA events
 on the library's stream; between steps a 512 MB buffer is rewritten to flush
 the 126 MB L2 (outside the events).  `e2e` repeats the step through the same
 C calls with pinned host buffers, host<->device copies inside the timed
-region.  With N > 1 (torchrun) every rank solves its own independent problem
-(replicas: the FMM itself is not sharded), and value = all particles / the
-slowest rank's time.
+region.
+
+The line's `value` is the 1e6-point unit cube (h 6, p 7).  With one GPU the
+same line also carries, each measured in this run:
+  c3        1e7 points on an ellipsoid surface (h 8, p 7), timed the same way;
+  c4        256 uneven problems solved as one batch (p 5);
+  c5        a Poisson stream of solve requests through the solve server;
+  fp64_gpu  the FP64 GPU path on the cube, and speedup_vs_fp64_gpu;
+  err_vs_direct (cube and c3)  relative L2 error of the last timed step's
+            phi and F against the FP64 direct sum on 2000 seeded targets
+            (the CPU oracle, outside the timed region);
+  fp32_peak the FP32 FMA rate of this GPU, measured by a throughput kernel
+            of the library (the P2P roofline's denominator).
+With N > 1 (torchrun) every rank solves its own independent cube (replicas:
+the FMM itself is not sharded), value = all particles / the slowest rank's
+time, and the line carries the cube only.
 
 --impl reference times the FP64 CPU oracle (the test oracle, as it stands) on
 a density-matched bounded sample of the same workload on the host cores.
@@ -33,19 +46,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "cube_n1m_h6_p7"
+C3_WORKLOAD = "ellipsoid_n10m_h8_p7"
 # the same cube under every kernel of fmm_set_kernel and the Stokes path
 KERNELS_WORKLOAD = "kernels_cube_n1m_h6_p7"
 METRIC = "FMM particles/s at rel.err<=1e-5 vs FP64 direct; P2P/M2L % roofline; p50/p99 ms"
 UNIT = "particles/s"
-# the CPU oracle is timed once on the full workload (about 30 s on 16 cores);
-# the reference arm's steps use a density-matched sample (same particles per
-# leaf: N / 8^k with height - k) so that K steps stay within minutes
-CPU_BASELINE_SAMPLE = dict(n=1_000_000, height=6, order=7, dist="cube", qkind="sym", seed=2)
+ERR_BAR = 1e-5
+ERR_TARGETS = 2000
+# Oracle samples.  The cube is timed on the full workload (about 10 s on 16
+# cores).  The 1e7-point ellipsoid is timed on a density-matched sample: a
+# surface's occupied leaves grow about 4.1x per level, so 600,000 points of
+# the same ellipsoid at h = 6 hold the same ~450 particles per occupied leaf
+# as 1e7 points at h = 8.  The reference arm's steps use a density-matched
+# sample of the cube (N / 8^k at height - k) so that K steps stay within minutes.
+CPU_BASELINE_SAMPLES = {
+    WORKLOAD: dict(n=1_000_000, height=6, order=7, dist="cube", qkind="sym", seed=2,
+                   note="the timed workload itself"),
+    C3_WORKLOAD: dict(n=600_000, height=6, order=7, dist="ellipsoid", qkind="pos", seed=3,
+                      note="density-matched sample of the 1e7-point ellipsoid: the same ellipsoid and charges, "
+                           "~450 particles per occupied leaf as at N=1e7, h=8"),
+}
 REFERENCE_STEP_SAMPLE = dict(n=15_625, height=4, order=7, dist="cube", qkind="sym", seed=2)
 
-FP32_LANES_PER_SM = 128
-NUM_SMS = 148
 TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense tensor rates (FP16 runs at the BF16 rate)
+# FP32 operations of one P2P interaction as the mixed kernel issues them: the
+# exact difference (hi_t - hi_s) + (lo_t - lo_s) per axis (9), the squared
+# distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential sum (1)
+# and the field sums (3 FMA) = 19; 1/sqrt runs on the MUFU pipe.  A plain
+# single-word FP32 difference would need 13.
+P2P_FP32_OPS = 19
+P2P_FP32_OPS_PLAIN = 13
 
 
 def m2l_math(stats) -> str:
@@ -58,13 +88,6 @@ def tensor_peak(pk, math: str):
     if math == "f16x3":
         return pk["bf16"], f"FP16 = {pk['src']} bf16 (the same dense rate)"
     return pk["bf16"] * TF32_OVER_BF16, f"TF32 = {pk['src']} bf16 x 1.1/2.25"
-# FP32 operations of one P2P interaction as the mixed kernel issues them: the
-# exact difference (hi_t - hi_s) + (lo_t - lo_s) per axis (9), the squared
-# distance (1 multiply + 2 FMA), q/r (1), q/r^3 (2), the potential sum (1)
-# and the field sums (3 FMA) = 19; 1/sqrt runs on the MUFU pipe.  A plain
-# single-word FP32 difference would need 13.
-P2P_FP32_OPS = 19
-P2P_FP32_OPS_PLAIN = 13
 
 
 def parse():
@@ -77,9 +100,12 @@ def parse():
     ap.add_argument("--m2l", choices=["full", "svd"], default="svd",
                     help="M2L operators: full-rank K_t, or the SVD-compressed canonical operators (eps = 10^-p)")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-main", action="store_true", help="the named workload alone (no c3/c4/c5/fp64 legs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle legs (CPU baseline timing and the error check against the direct sum)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default P2P kernel shape")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: length of the request stream")
     ap.add_argument("--lanes", type=int, default=2, help="serving: concurrent batches")
@@ -96,6 +122,18 @@ def peaks():
         return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d.get("bf16_tflops_sustained"),
                     sm_max_mhz=d.get("sm_max_mhz", 2032.0), src="measured")
     return dict(hbm=6400.0, bf16=1800.0, bf16_sus=1400.0, sm_max_mhz=2032.0, src="fallback")
+
+
+def fp32_peak(fmm):
+    """The FP32 FMA rate of this GPU, measured in this run by the library's
+    throughput kernel (independent FMA chains on every SM, best of three
+    launches), scalar and packed (fma.rn.f32x2); the larger is the peak."""
+    r = fmm.fmm_measure_fp32_rate()
+    flops = float(max(r[0], r[1]))
+    return {"tflops": flops / 1e12, "scalar_tflops": float(r[0]) / 1e12, "packed_tflops": float(r[1]) / 1e12,
+            "sms": int(r[2]), "ops_per_s": flops / 2.0,
+            "source": "measured in this run: fmm_measure_fp32_rate (FMA chains, 8 x 256 threads per SM, "
+                      "best of 3 launches); an FMA is 2 flop and 1 FP32 operation"}
 
 
 class Clocks:
@@ -176,9 +214,9 @@ def replica_throughput(n_local: int, steps: int, local_ms: float, device="cpu"):
     """Whole-job throughput of independent replicas: every rank solved `steps`
     problems of n_local particles in local_ms; the job took as long as the
     slowest rank.  Returns (particles per second, max ms over ranks)."""
-    ws = 1
     max_ms = float(local_ms)
     import torch.distributed as dist
+    ws = 1
     if dist.is_available() and dist.is_initialized():
         import torch
         ws = dist.get_world_size()
@@ -191,7 +229,7 @@ def replica_throughput(n_local: int, steps: int, local_ms: float, device="cpu"):
 def stage_rooflines(n, h, p, ncell, iso, build_ms, pk, precision):
     """HBM rooflines of the stages around M2L and P2P (each timed alone):
     algorithmic bytes per evaluation / stage time against the measured copy
-    bandwidth.  Mixed precision: a multipole row is C TF32 hi/lo pairs (8 B
+    bandwidth.  Mixed precision: a multipole row is C FP32 hi/lo pairs (8 B
     per coefficient), a local row C + 1 FP32 values."""
     if precision != "mixed" or h < 3:
         return None
@@ -218,7 +256,99 @@ def stage_rooflines(n, h, p, ncell, iso, build_ms, pk, precision):
     return out
 
 
-def oracle_operators(s: dict, m2l: str):
+def m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main: bool):
+    """(roofline of the dominant M2L kernel, the projection's, tensor-pipe
+    counts) from the algorithmic work of fmm_get_work and the kernels' own
+    CUDA-event times inside the timed steps."""
+    C = p ** 3
+    m2l_kind = int(stats[4])
+    math = m2l_math(stats)
+    mlabel = "3xFP16" if math == "f16x3" else "3xTF32"
+    m2l_pairs = int(work[1:12].sum())
+    cpad = ((C + 1 + 31) // 32) * 32
+    if m2l_kind >= 3:
+        # compressed: y = V^T M (2 C r flop) and L += U y (2 C r flop) per pair
+        m2l_flop = 4.0 * C * int(work[13])
+        m2l_alg = f"4 x {C} x sum of pair ranks {int(work[13])} = {m2l_flop:.4g} flop per evaluation"
+    else:
+        m2l_flop = 2.0 * C * C * m2l_pairs
+        m2l_alg = f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per evaluation"
+    fp32_tf = pk["fp32"]["tflops"]
+    if m2l_kind in (2, 5):
+        peak, peak_note = tensor_peak(pk, math)
+        bound = "tensor"
+    elif m2l_kind in (1, 4):
+        bound, peak, peak_note = "alu", fp32_tf, "FP32 FMA, measured (fmm_measure_fp32_rate)"
+    else:
+        bound, peak, peak_note = "alu", fp32_tf / 64.0, "FP64 FMA: measured FP32 rate / 64 (nominal ratio)"
+    tensor_pipe = None
+    roofline_proj = None
+    if m2l_kind == 5:
+        kernel_name = f"k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels"
+        half_flop = m2l_flop / 2.0
+        m2l_ms = float(kt[1])
+        achieved = half_flop / (m2l_ms / 1e3) / 1e12
+        m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
+                   f"(the projection carries as much)")
+        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
+                                    "int sp_ngroups(int Rp)") if main else None)
+        # MMA flop issued (three products per multiply, the padded shapes)
+        hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
+        hw_e = 3 * 2.0 * 128 * cpad * int(work[15])
+        tensor_pipe = {"operands": math,
+                       "expansion": {"mma_flop_per_launch": hw_e, "tflops": hw_e / (kt[1] / 1e3) / 1e12,
+                                     "frac_of_peak": hw_e / (kt[1] / 1e3) / 1e12 / peak},
+                       "projection": {"mma_flop_per_launch": hw_p, "tflops": hw_p / (kt[0] / 1e3) / 1e12,
+                                      "frac_of_peak": hw_p / (kt[0] / 1e3) / 1e12 / peak}}
+        ach_p = half_flop / (kt[0] / 1e3) / 1e12
+        roofline_proj = {"kernel": f"k_svd_proj_tc (compressed M2L projection y = V^T M, tcgen05, {mlabel})",
+                         "bound": "tensor", "achieved": ach_p, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach_p / peak, "ms": float(kt[0]), "peak_source": peak_note}
+    elif m2l_kind == 2:
+        kernel_name = f"k_m2l_tc (full-rank M2L, tcgen05, {mlabel}), all levels"
+        m2l_ms = float(kt[1])
+        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
+        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu", "profiles/m2l_tc_cube_n1m_h6_p7.md",
+                                    "// L_T[m] = (1/a) * sum over the tile's groups") if main else None)
+        hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
+        tensor_pipe = {"operands": math, "mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_ms / 1e3) / 1e12,
+                       "frac_of_peak": hw_flop / (m2l_ms / 1e3) / 1e12 / peak}
+    else:
+        kernel_name = ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
+                       "k_m2l_simt<float> (FP32 CUDA cores), all levels", "",
+                       "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
+                       "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels"][m2l_kind]
+        m2l_ms = float(np.mean(stage[:, 1]))
+        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
+        traffic = None
+    roof = {"kernel": kernel_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "ms": m2l_ms, "algorithmic": m2l_alg,
+            "peak_source": peak_note}
+    return roof, roofline_proj, tensor_pipe
+
+
+def p2p_roofline(p2p_pairs: int, p2p_ms: float, pk, kernel: str):
+    fp = pk["fp32"]
+    ips = p2p_pairs / (p2p_ms / 1e3)
+    return {"bound": "alu", "kernel": kernel, "ms": p2p_ms, "interactions": p2p_pairs, "interactions_per_s": ips,
+            "achieved_gflops_20": 20.0 * ips / 1e9, "frac_20flop": 20.0 * ips / (fp["tflops"] * 1e12),
+            "fp32_ops_per_interaction": P2P_FP32_OPS,
+            "fp32_pipe_frac": P2P_FP32_OPS * ips / fp["ops_per_s"],
+            "fp32_pipe_frac_plain_13": P2P_FP32_OPS_PLAIN * ips / fp["ops_per_s"],
+            "peak_fp32_tflops": fp["tflops"], "peak_source": "measured in this run (fp32_peak)"}
+
+
+def sample_targets(n: int, k: int = ERR_TARGETS, seed: int = 5):
+    import numpy as np
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
+
+
+# ---- the oracle legs ---------------------------------------------------------
+# The CPU oracle serves two purposes here, both outside the timed region: the
+# CPU baseline (its FMM timed on the host cores) and the accuracy check of
+# the timed run's own output against the exact sum on sampled targets.
+
+def oracle_operators(order: int, m2l: str):
     """An oracle tree whose compressed M2L operators later trees reuse (the
     operators depend on the order only, as the GPU path's are computed once
     per handle); None for the full-rank operators."""
@@ -227,27 +357,40 @@ def oracle_operators(s: dict, m2l: str):
     import oracle
     from paper_1206_0115_b300 import inputs
     xyz, q = inputs.particles(64, 1, "cube", "pos")
-    return oracle.OracleFMM(xyz, q, 3, s["order"], svd_eps=10.0 ** -s["order"])
+    return oracle.OracleFMM(xyz, q, 3, order, svd_eps=10.0 ** -order)
 
 
-def cpu_baseline(sample: dict, m2l: str, reps: int = 1):
-    """The FP64 oracle's FMM on the timed workload (same M2L operators)."""
+def oracle_error_check(xyz, q, outputs: dict, idx):
+    """Relative L2 error of each (phi, F) in `outputs` on the targets idx
+    against the FP64 direct sum (the oracle's O(N) per target sum)."""
+    import oracle
+    t0 = time.perf_counter()
+    pd, Fd = oracle.direct_sampled(xyz, q, idx)
+    t = time.perf_counter() - t0
+    res = {}
+    for name, (phi, F) in outputs.items():
+        ep, eF = oracle.rel_l2(phi[idx], pd), oracle.rel_l2(F[idx], Fd)
+        res[name] = {"phi": ep, "F": eF, "targets": int(len(idx)), "bar": ERR_BAR,
+                     "within_bar": bool(ep <= ERR_BAR and eF <= ERR_BAR),
+                     "reference": f"FP64 direct sum (oracle) over all {len(q)} sources, {t:.1f} s on the host"}
+    return res
+
+
+def cpu_baseline(sample: dict, m2l: str):
+    """The FP64 oracle's FMM on `sample` (the timed workload or a stated
+    density-matched sample of it), with the same M2L operators."""
     import oracle
     from paper_1206_0115_b300 import inputs
     xyz, q = inputs.particles(sample["n"], sample["seed"], sample["dist"], sample["qkind"])
-    ops = oracle_operators(sample, m2l)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        with oracle.OracleFMM(xyz, q, sample["height"], sample["order"], svd_from=ops) as o:
-            o.evaluate()
-        times.append(time.perf_counter() - t0)
-    t = statistics.median(times)
+    ops = oracle_operators(sample["order"], m2l)
+    t0 = time.perf_counter()
+    with oracle.OracleFMM(xyz, q, sample["height"], sample["order"], svd_from=ops) as o:
+        o.evaluate()
+    t = time.perf_counter() - t0
     return {"value": sample["n"] / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"N={sample['n']} uniform cube, h={sample['height']}, p={sample['order']} "
-                       f"(the timed workload itself), FP64 oracle FMM ({m2l} M2L operators, computed "
-                       f"beforehand) incl. tree build, {reps} run(s), "
-                       f"{t:.2f} s")}
+            "sample": (f"N={sample['n']} {sample['dist']}, h={sample['height']}, p={sample['order']} "
+                       f"({sample['note']}), FP64 oracle FMM ({m2l} M2L operators, computed beforehand) "
+                       f"incl. tree build, 1 run, {t:.2f} s")}
 
 
 def run_reference(args):
@@ -259,7 +402,7 @@ def run_reference(args):
     from paper_1206_0115_b300 import inputs
     xyz, q = inputs.particles(s["n"], s["seed"], s["dist"], s["qkind"])
 
-    ops = oracle_operators(s, args.m2l)
+    ops = oracle_operators(s["order"], args.m2l)
 
     def step():
         with oracle.OracleFMM(xyz, q, s["height"], s["order"], svd_from=ops) as o:
@@ -275,34 +418,30 @@ def run_reference(args):
     tot = sum(times)
     value = s["n"] * args.steps / tot
     sample = (f"each step: N={s['n']} uniform cube, h={s['height']}, p={s['order']} (same particles per "
-              f"leaf as {args.workload}), FP64 oracle FMM ({args.m2l} M2L operators, computed beforehand) "
+              f"leaf as {WORKLOAD}), FP64 oracle FMM ({args.m2l} M2L operators, computed beforehand) "
               f"incl. tree build")
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": args.workload, "sample": sample},
+        "config": {"workload": WORKLOAD, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def run_ours(args):
+# ---- one problem ---------------------------------------------------------------
+
+def measure_single(args, fmm, dev, workload: str, pk, rank: int = 0, main: bool = True):
+    """Times `workload` (fmm_set_particles + fmm_evaluate per step) and
+    returns (result dict, host inputs, host outputs of the last timed step)."""
     import numpy as np
     import torch
 
-    from paper_1206_0115_b300 import build, inputs
-    build.build()
-    from paper_1206_0115_b300 import fmm
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    w = dict(inputs.WORKLOADS[args.workload])
+    from paper_1206_0115_b300 import inputs
+    ws, _, local = dist_env()
+    w = dict(inputs.WORKLOADS[workload])
     xyz_np, q_np = inputs.particles(w["n"], w["seed"] + 1000 * rank, w["dist"], w["qkind"])
     n, h, p = w["n"], w["height"], w["order"]
     prec = fmm.FMM_MIXED if args.precision == "mixed" else fmm.FMM_FP64
@@ -347,6 +486,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage = []
     ktimes = []
@@ -357,7 +497,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     t_wall = time.perf_counter()
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))
@@ -378,6 +517,8 @@ def run_ours(args):
     build_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, mids)]))
     value, total_ms = replica_throughput(n, args.steps, sum(ms), device=dev)
     ncell = [fmm.fmm_get_level_size(f.h, l) for l in range(h)]
+    out_phi, out_F = phi.cpu().numpy(), F.cpu().numpy()  # the last timed step's results
+    stats = f.stats()
 
     # end to end through the same calls with pinned host buffers
     xyz_h = torch.from_numpy(xyz_np).pin_memory()
@@ -397,158 +538,98 @@ def run_ours(args):
         if k > 0:
             e_ms.append(a.elapsed_time(b))
     e2e_value = replica_throughput(n, len(e_ms), sum(e_ms), device=dev)[0] if e_ms else None
+    f.close()
+    del flush
 
-    if rank != 0:
-        f.close()
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return
-
-    pk = peaks()
-    C = p ** 3
     stage = np.array(stage)
-    m2l_leaf_ms = float(np.mean(stage[:, 2]))
-    p2p_ms = float(iso[5])  # P2P alone
-    # 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 (full-rank K_t); 3 FP64 SIMT, 4 FP32 SIMT (compressed)
-    m2l_kind = int(stats[4])
-    math = m2l_math(stats)
-    mlabel = "3xFP16" if math == "f16x3" else "3xTF32"
-    m2l_pairs = int(work[1:12].sum())
-    if m2l_kind >= 3:
-        # compressed: y = V^T M (2 C r flop) and L += U y (2 C r flop) per pair
-        m2l_flop = 4.0 * C * int(work[13])
-        m2l_alg = f"4 x {C} x sum of pair ranks {int(work[13])} = {m2l_flop:.4g} flop per evaluation"
-    else:
-        m2l_flop = 2.0 * C * C * m2l_pairs
-        m2l_alg = f"2 x {C}^2 flop x {m2l_pairs} pairs = {m2l_flop:.4g} flop per evaluation"
-    # the tensor-core kernels cover every level in one launch each and are
-    # timed by their own events; the CUDA-core kernels over all levels (stage [1])
     kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
-    p2p_pairs = int(work[0])
-    tc_path = m2l_kind in (2, 5)
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    if tc_path:
-        peak, peak_note = tensor_peak(pk, math)
-        bound = "tensor"
-    elif m2l_kind in (1, 4):
-        bound, peak, peak_note = "alu", fp32_peak, "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock"
-    else:
-        bound, peak, peak_note = "alu", fp32_peak / 64.0, "FP64 FMA: FP32 rate / 64 (nominal ratio)"
-    p2p_gflop = 20.0 * p2p_pairs / 1e9
-    tensor_pipe = None
-    roofline_proj = None
-    cpad = ((C + 1 + 31) // 32) * 32
-    if m2l_kind == 5:
-        # the dominant kernel is the expansion; each half carries 2 C r flop per pair
-        kernel_name = f"k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels"
-        half_flop = m2l_flop / 2.0
-        m2l_ms = float(kt[1])
-        achieved = half_flop / (m2l_ms / 1e3) / 1e12
-        m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
-                   f"(the projection carries as much)")
-        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
-                                    "int sp_ngroups(int Rp)")
-                   if args.workload == WORKLOAD else None)
-        # MMAs issued: projection 128 x cpad x (Y columns), expansion 128 x (Y columns) x cpad, three
-        # products per multiply (hi hi, hi lo, lo hi)
-        hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
-        hw_e = 3 * 2.0 * 128 * cpad * int(work[15])
-        tensor_pipe = {"operands": math,
-                       "expansion": {"mma_flop_per_launch": hw_e, "tflops": hw_e / (kt[1] / 1e3) / 1e12,
-                                     "frac_of_peak": hw_e / (kt[1] / 1e3) / 1e12 / peak},
-                       "projection": {"mma_flop_per_launch": hw_p, "tflops": hw_p / (kt[0] / 1e3) / 1e12,
-                                      "frac_of_peak": hw_p / (kt[0] / 1e3) / 1e12 / peak}}
-        ach_p = half_flop / (kt[0] / 1e3) / 1e12
-        roofline_proj = {"kernel": f"k_svd_proj_tc (compressed M2L projection y = V^T M, tcgen05, {mlabel})",
-                         "bound": "tensor", "achieved": ach_p, "peak": peak, "unit": "TFLOP/s",
-                         "frac": ach_p / peak, "ms": float(kt[0]), "peak_source": peak_note}
-    elif m2l_kind == 2:
-        kernel_name = f"k_m2l_tc (full-rank M2L, tcgen05, {mlabel}), all levels"
-        m2l_ms = float(kt[1])
-        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
-        traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_tc.cu", "profiles/m2l_tc_cube_n1m_h6_p7.md",
-                                    "// L_T[m] = (1/a) * sum over the tile's groups")
-                   if args.workload == WORKLOAD else None)
-        # every (tile, active transfer vector) runs a 128-row x cpad x cpad product three times
-        hw_flop = 3 * 2.0 * 128 * cpad * cpad * int(work[12])
-        tensor_pipe = {"operands": math, "mma_flop_per_launch": hw_flop, "tflops": hw_flop / (m2l_ms / 1e3) / 1e12,
-                       "frac_of_peak": hw_flop / (m2l_ms / 1e3) / 1e12 / peak}
-    else:
-        kernel_name = ["k_m2l_simt<double> (FP64 CUDA cores), all levels",
-                       "k_m2l_simt<float> (FP32 CUDA cores), all levels", "",
-                       "k_m2l_proj + k_m2l_expand <double> (compressed, FP64 CUDA cores), all levels",
-                       "k_m2l_proj + k_m2l_expand <float> (compressed, FP32 CUDA cores), all levels"][m2l_kind]
-        m2l_ms = float(np.mean(stage[:, 1]))
-        achieved = m2l_flop / (m2l_ms / 1e3) / 1e12
-        traffic = None
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+    roof, roof_proj, tensor_pipe = m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main)
+    math = m2l_math(stats)
+    res = {
+        "value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
         "dtype": f"f32+{math}" if args.precision == "mixed" else "f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "height": h, "order": p, "precision": args.precision,
-                   "m2l": args.m2l,
-                   "distribution": w["dist"], "charges": w["qkind"], "seed": w["seed"],
+        "config": {"workload": workload, "n": n, "height": h, "order": p, "precision": args.precision,
+                   "m2l": args.m2l, "distribution": w["dist"], "charges": w["qkind"], "seed": w["seed"],
                    "l2": "flushed between steps (512 MB rewrite outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "set_particles_ms": build_ms,
         "stage_ms": {"upward": float(np.mean(stage[:, 0])), "m2l_all": float(np.mean(stage[:, 1])),
-                     "m2l_leaf": m2l_leaf_ms, "m2l_coarse": float(np.mean(stage[:, 3])),
-                     "l2l": float(np.mean(stage[:, 4])), "p2p": p2p_ms, "l2p_out": float(np.mean(stage[:, 6])),
-                     "evaluate": float(np.mean(stage[:, 7]))},
+                     "m2l_main": float(np.mean(stage[:, 2])), "m2l_rest": float(np.mean(stage[:, 3])),
+                     "l2l": float(np.mean(stage[:, 4])), "p2p": float(np.mean(stage[:, 5])),
+                     "l2p_out": float(np.mean(stage[:, 6])), "evaluate": float(np.mean(stage[:, 7]))},
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
-        "roofline": {"kernel": kernel_name, "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "ms": m2l_ms,
-                     "algorithmic": m2l_alg, "peak_source": peak_note},
-        "roofline_m2l_projection": roofline_proj,
+        "roofline": roof,
+        "roofline_m2l_projection": roof_proj,
         "tensor_pipe": tensor_pipe,
         "autotune": tuned,
-        "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)",
-                         "achieved_gflops_20": p2p_gflop / (p2p_ms / 1e3),
-                         "interactions": p2p_pairs,
-                         "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
-                         "fp32_ops_per_interaction": P2P_FP32_OPS,
-                         "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2),
-                         "fp32_pipe_frac_plain_13": P2P_FP32_OPS_PLAIN * p2p_pairs / (p2p_ms / 1e3)
-                         / (fp32_peak * 1e12 / 2),
-                         "peak_fp32_tflops": fp32_peak},
+        "roofline_p2p": p2p_roofline(int(work[0]), float(iso[5]), pk, "k_p2p (the chosen shape, run alone)"),
         "roofline_stages": stage_rooflines(n, h, p, ncell, iso, build_ms, pk, args.precision),
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
+        # evaluations that ran launch by launch after a failed graph capture (0 expected)
+        "graph_fallbacks": int(stats[6]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
                 "d2h_bytes_per_step": int(32 * n), "steps": len(e_ms)},
         "clocks": clk,
         "wall_s": t_wall,
     }
-    f.close()
-    if ws == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLE, args.m2l)
-    print(json.dumps(result))
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    return res, (xyz_np, q_np), (out_phi, out_F)
+
+
+def measure_fp64(args, fmm, dev, workload: str):
+    """The FP64 GPU path (every stage in FP64 on the GPU, the same M2L
+    operators) on `workload`: a few steps after one warm-up (which computes
+    the FP64 operators), timed like the mixed path."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0115_b300 import inputs
+    w = dict(inputs.WORKLOADS[workload])
+    xyz_np, q_np = inputs.particles(w["n"], w["seed"], w["dist"], w["qkind"])
+    n, h, p = w["n"], w["height"], w["order"]
+    stream = torch.cuda.Stream(device=dev)
+    method = fmm.FMM_M2L_SVD if args.m2l == "svd" else fmm.FMM_M2L_FULL
+    xyz = torch.from_numpy(xyz_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ms = []
+    with fmm.FMM(h, p, fmm.FMM_FP64, stream=stream, m2l=method) as f:
+        f.set_particles(xyz, q)
+        f.evaluate(phi, F)
+        torch.cuda.synchronize()
+        for k in range(max(1, args.fp64_steps)):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.set_particles(xyz, q)
+            f.evaluate(phi, F)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms))
+    return {"value": n / (t / 1e3), "unit": UNIT, "ms_per_step": t, "steps": len(ms), "dtype": "f64",
+            "config": {"workload": workload, "precision": "fp64", "m2l": args.m2l}}, (phi.cpu().numpy(),
+                                                                                      F.cpu().numpy())
 
 
 BATCH_WORKLOAD = "batched_256_p5"
 
 
-def run_batched(args):
+def measure_batched(args, fmm, dev, pk, rank: int = 0):
     """256 independent problems of uneven size (1e3 .. 2e5 particles, heights
     3..6 by size, cube or ellipsoid by seed, p = 5) solved as one batch: a step
     is fmm_set_batch + fmm_evaluate over all of them (one launch per stage)."""
     import numpy as np
     import torch
 
-    from paper_1206_0115_b300 import build, inputs
-    build.build()
-    from paper_1206_0115_b300 import fmm
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    from paper_1206_0115_b300 import inputs
+    ws, _, local = dist_env()
     p = 5
     counts, heights, xyz_np, q_np = inputs.batch_workload(seed=999 + 1000 * rank)
     n = int(counts.sum())
@@ -617,7 +698,6 @@ def run_batched(args):
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     build_ms = [a.elapsed_time(b) for a, b in zip(starts, mids)]
     value, total_ms = replica_throughput(n, args.steps, sum(ms), device=dev)
-
     xyz_h = torch.from_numpy(xyz_np).pin_memory()
     q_h = torch.from_numpy(q_np).pin_memory()
     phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -635,33 +715,27 @@ def run_batched(args):
         if k > 0:
             e_ms.append(a.elapsed_time(b))
     e2e_value = replica_throughput(n, len(e_ms), sum(e_ms), device=dev)[0] if e_ms else None
-    if rank != 0:
-        f.close()
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return
-    pk = peaks()
+    leaf_level = int(f.batch_info(0)[0][4])
+    stats = f.stats()
+    f.close()
+    del flush
     C = p ** 3
     cpad = ((C + 1 + 31) // 32) * 32
     math = m2l_math(stats)
     mlabel = "3xFP16" if math == "f16x3" else "3xTF32"
     peak, peak_note = tensor_peak(pk, math)
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
     half_flop = 2.0 * C * int(work[13])
-    p2p_pairs = int(work[0])
-    p2p_ms = float(iso[5])
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": f"f32+{math}" if args.precision == "mixed" else "f64", "data": "synthetic",
+    res = {
+        "value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "dtype": f"f32+{math}" if args.precision == "mixed" else "f64",
         "config": {"workload": BATCH_WORKLOAD, "problems": int(len(counts)), "n_total": n,
                    "n_min": int(counts.min()), "n_max": int(counts.max()),
                    "heights": {str(hh): int((heights == hh).sum()) for hh in sorted(set(heights.tolist()))},
                    "order": p, "precision": args.precision, "m2l": args.m2l,
                    "distribution": "cube (even seed) / ellipsoid surface (odd seed)", "charges": "pos",
-                   "batch_tree_leaf_level": int(f.batch_info(0)[0][4]),
+                   "batch_tree_leaf_level": leaf_level,
                    "l2": "flushed between steps (512 MB rewrite outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
@@ -682,34 +756,118 @@ def run_batched(args):
             "expansion_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
             "projection_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
         "autotune": tuned,
-        "roofline_p2p": {"bound": "alu", "kernel": "k_p2p (run alone)", "interactions": p2p_pairs,
-                         "interactions_per_s": p2p_pairs / (p2p_ms / 1e3),
-                         "fp32_ops_per_interaction": P2P_FP32_OPS,
-                         "fp32_pipe_frac": P2P_FP32_OPS * p2p_pairs / (p2p_ms / 1e3) / (fp32_peak * 1e12 / 2)},
+        "roofline_p2p": p2p_roofline(int(work[0]), float(iso[5]), pk, "k_p2p (the chosen shape, run alone)"),
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
+        "graph_fallbacks": int(stats[6]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
                 "d2h_bytes_per_step": int(32 * n), "steps": len(e_ms)},
         "clocks": clk,
     }
-    f.close()
-    if ws == 1 and not args.no_cpu_baseline:
-        # the oracle on a bounded sample: the first 8 problems, one after another
-        import oracle
-        from paper_1206_0115_b300 import inputs as _inp
-        st = np.concatenate([[0], np.cumsum(counts)])
-        ops = oracle_operators({"order": p}, args.m2l)
-        t0 = time.perf_counter()
-        m = 0
-        for k in range(8):
-            a, b = st[k], st[k + 1]
-            with oracle.OracleFMM(xyz_np[a:b], q_np[a:b], int(heights[k]), p, svd_from=ops) as o:
-                o.evaluate()
-            m += b - a
-        t = time.perf_counter() - t0
-        result["cpu_baseline"] = {"value": m / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                                  "sample": f"problems 0..7 of the batch ({m} particles) one after another, FP64 "
-                                            f"oracle FMM ({args.m2l} M2L operators, computed beforehand), {t:.2f} s"}
-    print(json.dumps(result))
+    return res, (counts, heights, xyz_np, q_np)
+
+
+def batch_cpu_baseline(args, counts, heights, xyz_np, q_np, p: int = 5):
+    """The oracle on a bounded sample of the batch: its first 8 problems, one
+    after another."""
+    import numpy as np
+    import oracle
+    st = np.concatenate([[0], np.cumsum(counts)])
+    ops = oracle_operators(p, args.m2l)
+    t0 = time.perf_counter()
+    m = 0
+    for k in range(8):
+        a, b = st[k], st[k + 1]
+        with oracle.OracleFMM(xyz_np[a:b], q_np[a:b], int(heights[k]), p, svd_from=ops) as o:
+            o.evaluate()
+        m += b - a
+    t = time.perf_counter() - t0
+    return {"value": m / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"problems 0..7 of the batch ({m} particles) one after another, FP64 "
+                      f"oracle FMM ({args.m2l} M2L operators, computed beforehand), {t:.2f} s"}
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1206_0115_b300 import build
+    build.build()
+    from paper_1206_0115_b300 import fmm
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pk = peaks()
+    pk["fp32"] = fp32_peak(fmm)
+    res, data = measure_batched(args, fmm, dev, pk, rank)
+    if rank == 0:
+        line = {"metric": METRIC, "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "data": "synthetic"}
+        line.update(res)
+        line["fp32_peak"] = pk["fp32"]
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = batch_cpu_baseline(args, *data)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1206_0115_b300 import build
+    build.build()
+    from paper_1206_0115_b300 import fmm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pk = peaks()
+    pk["fp32"] = fp32_peak(fmm)
+    main, (xyz, q), outs = measure_single(args, fmm, dev, args.workload, pk, rank, main=True)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {"metric": METRIC, "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    line.update(main)
+    line["fp32_peak"] = pk["fp32"]
+    extras = ws == 1 and not args.only_main and args.workload == WORKLOAD and args.precision == "mixed"
+    fp64_out = None
+    if extras:
+        fp64, fp64_out = measure_fp64(args, fmm, dev, WORKLOAD)
+        line["fp64_gpu"] = fp64
+        line["speedup_vs_fp64_gpu"] = main["value"] / fp64["value"]
+    oracle_ok = ws == 1 and not args.no_cpu_baseline
+    if oracle_ok:
+        outputs = {"mixed": outs}
+        if fp64_out is not None:
+            outputs["fp64_gpu"] = fp64_out
+        errs = oracle_error_check(xyz, q, outputs, sample_targets(len(q)))
+        line["err_vs_direct"] = errs["mixed"]
+        if "fp64_gpu" in errs:
+            line["fp64_gpu"]["err_vs_direct"] = errs["fp64_gpu"]
+    del xyz, q, outs, fp64_out
+    if extras:
+        c3, (x3, q3), o3 = measure_single(args, fmm, dev, C3_WORKLOAD, pk, rank, main=False)
+        if oracle_ok:
+            c3["err_vs_direct"] = oracle_error_check(x3, q3, {"mixed": o3}, sample_targets(len(q3)))["mixed"]
+            c3["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLES[C3_WORKLOAD], args.m2l)
+        del x3, q3, o3
+        line["c3"] = c3
+        c4, data4 = measure_batched(args, fmm, dev, pk, rank)
+        if oracle_ok:
+            c4["cpu_baseline"] = batch_cpu_baseline(args, *data4)
+        line["c4"] = c4
+        line["c5"] = measure_serving(args, fmm)
+    if oracle_ok and args.workload in CPU_BASELINE_SAMPLES:
+        line["cpu_baseline"] = cpu_baseline(CPU_BASELINE_SAMPLES[args.workload], args.m2l)
+    print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -754,24 +912,21 @@ class Ring:
             self.cv.notify_all()
 
 
-def run_serving(args):
+def measure_serving(args, fmm):
     """Poisson stream of solve requests (mean 200 per second; sizes
     log-uniform in [1e4, 5e6] particles, uniform cube, order 5 or 7 by coin
     flip, height from the size as in the batched workload, capped at 8)
     through the solve server: 2 lanes, 150 GB admission budget.  Requests
-    carry host buffers (inputs pinned, outputs pageable); latency is submit
-    to results in host memory."""
+    carry host buffers (inputs pinned, outputs in a pinned ring); latency is
+    submit to results in host memory."""
     import threading
 
     import numpy as np
     import torch
 
-    from paper_1206_0115_b300 import build, inputs
-    build.build()
-    from paper_1206_0115_b300 import fmm
+    from paper_1206_0115_b300 import inputs
 
     ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
     rate, seconds = args.rate, args.serve_seconds
     nreq = max(1, int(rate * seconds))
     seed = 2_000_000 + 1000 * rank
@@ -910,7 +1065,18 @@ def run_serving(args):
                 "d2h_bytes_per_step": int(32 * parts / nreq)},
         "clocks": clk,
     }
-    print(json.dumps(result))
+    return result
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1206_0115_b300 import build
+    build.build()
+    from paper_1206_0115_b300 import fmm
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    print(json.dumps(measure_serving(args, fmm)))
 
 
 def run_kernels(args):

@@ -343,6 +343,18 @@ fmm_status fmm_get_stage_times(fmm_handle h, float* out);
  * path that does not run on the tensor cores).  out: 2 floats, host. */
 fmm_status fmm_get_m2l_kernel_times(fmm_handle h, float* out);
 
+/* FP32 arithmetic rate of the current device, measured (the paper has no
+ * counterpart: it gives the roofline that the near field, Sec. 2.1's P2P, is
+ * judged against).  A throughput kernel runs independent FMA chains on 8
+ * blocks of 256 threads per SM for about 10 ms per launch (one warm-up launch,
+ * then the best of three): out[0] = scalar fma.rn.f32 rate in flop/s (2 flop
+ * per FMA and lane), out[1] = packed fma.rn.f32x2 rate in flop/s (4 flop per
+ * instruction and lane), out[2] = the SM count the kernel ran on
+ * (cudaDevAttrMultiProcessorCount), out[3] = 0.  Uses its own stream and
+ * synchronises it; no handle needed.  out: 4 doubles, host.
+ * Errors: FMM_ERR_ARG (out NULL), FMM_ERR_CUDA. */
+fmm_status fmm_measure_fp32_rate(double* out);
+
 /* Allocation-free Morton ordering (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they
  * run -- processes whose HBM is owned by a pool reserved at start-up, such as

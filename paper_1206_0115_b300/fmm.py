@@ -61,6 +61,7 @@ _SIGS = {
     "fmm_get_stage_times": [_vp, _vp],
     "fmm_get_m2l_kernel_times": [_vp, _vp],
     "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
+    "fmm_measure_fp32_rate": [_vp],
 }
 _SIGS.update({
     "fmm_server_create": [_vp, C.POINTER(_vp)],
@@ -259,6 +260,13 @@ def fmm_get_stage_times(h) -> np.ndarray:
 def fmm_get_m2l_kernel_times(h) -> np.ndarray:
     out = np.zeros(2, dtype=np.float32)
     _check(h, lib.fmm_get_m2l_kernel_times(h, _ptr(out)))
+    return out
+
+
+def fmm_measure_fp32_rate() -> np.ndarray:
+    """[scalar FMA flop/s, packed f32x2 FMA flop/s, SM count, 0] of the current device."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(None, lib.fmm_measure_fp32_rate(_ptr(out)))
     return out
 
 

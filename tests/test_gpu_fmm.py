@@ -456,7 +456,8 @@ def test_cube_n1m_h6_p7_full_size(F):
 @pytest.mark.slow
 def test_ellipsoid_n10m_h8_p7_full_size(F):
     """1e7 points on the ellipsoid surface, h = 8, p = 7, mixed path: against
-    the oracle's FMM (same h, p) and the exact sum on sampled targets."""
+    the oracle's FMM (same h, p) and the exact sum on sampled targets, both
+    within 1e-5."""
     xyz, q, h, p = inputs.workload("ellipsoid_n10m_h8_p7")
     idx = _sample_idx(len(q), 256, 6)
     phi, Fo = _run(F, xyz, q, h, p, F.FMM_MIXED)
@@ -464,8 +465,10 @@ def test_ellipsoid_n10m_h8_p7_full_size(F):
         pr, Fr = o.evaluate_sampled(idx)
     assert oracle.rel_l2(phi[idx], pr) <= TOL_MIXED
     assert oracle.rel_l2(Fo[idx], Fr) <= TOL_MIXED
+    # the metric's own condition on the largest single-GPU workload: rel. err <= 1e-5 vs the FP64 direct sum
     pd, Fd = oracle.direct_sampled(xyz, q, idx)
-    print("ellipsoid mixed vs direct: phi %.3e F %.3e" % (oracle.rel_l2(phi[idx], pd), oracle.rel_l2(Fo[idx], Fd)))
+    assert oracle.rel_l2(phi[idx], pd) <= TOL_MIXED
+    assert oracle.rel_l2(Fo[idx], Fd) <= TOL_MIXED
 
 
 def test_handles_of_different_orders_interleave(F):
