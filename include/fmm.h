@@ -52,7 +52,10 @@ typedef enum {
 
 typedef enum {
   FMM_FP64 = 0,   /* every stage in FP64 on the GPU */
-  FMM_MIXED = 1   /* FP32 P2P and expansions, split-TF32 tensor-core M2L, FP32 accumulate */
+  FMM_MIXED = 1   /* FP32 P2P and expansions; M2L on the tensor cores for order <= 7 as three
+                     products of FP16 hi/lo operand pairs (TF32 hi/lo pairs when the environment
+                     sets FMM_M2L_MATH=tf32 at fmm_create), FP32 accumulate; M2L on the CUDA cores
+                     in FP32 for order >= 8 */
 } fmm_precision;
 
 typedef enum {
@@ -244,6 +247,16 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * stream.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
 
+/* Time limit of each bounded wait inside the tensor-core M2L kernels (the
+ * pipeline waits of Sec. 2.1.2's M2L between the copies, the MMAs and the
+ * epilogue; default 2 s, far beyond any real stage): a wait that runs out
+ * makes the kernel raise its error word, wait for the copies and MMAs it has
+ * already issued (always with the 2 s limit), free its tensor memory and
+ * return, and the next call on the handle reports FMM_ERR_TIMEOUT.  The
+ * paper has no counterpart; this is failure detection without a fault.
+ * 0 < seconds <= 60.  The evaluation graph is rebuilt.  Errors: FMM_ERR_ARG. */
+fmm_status fmm_set_wait_limit(fmm_handle h, double seconds);
+
 /* Sets the P2P variant directly (0 .. FMM_P2P_VARIANTS-1; 0 is the default),
  * e.g. to reuse a choice fmm_autotune made on another handle. */
 fmm_status fmm_set_p2p_variant(fmm_handle h, int variant);
@@ -296,8 +309,10 @@ fmm_status fmm_get_expansion(fmm_handle h, int level, int which, double* out);
  * 0: TF32 hi/lo, chosen at fmm_create by the environment variable
  * FMM_M2L_MATH=tf32, or a CUDA-core M2L),
  * out[6] = evaluations that ran their launches without a CUDA graph because
- * capturing the graph failed with a CUDA error (the same kernels, launched
- * one by one), out[7] = 0 (reserved).  out: 8 int64, host. */
+ * the stream capture of the graph failed with a capture error (the same
+ * kernels, launched one by one; the capture's message stays available from
+ * fmm_last_error; any other CUDA error fails the evaluation), out[7] = 0
+ * (reserved).  out: 8 int64, host. */
 fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
 
 /* Algorithmic work of one evaluation on the current tree (Sec. 4.3 counts
@@ -372,10 +387,11 @@ fmm_status fmm_measure_fp32_rate(double* out);
  * 4.3 MB compiled into the library, which each GPU that loads the library
  * holds until the process exits.  All calls on a GPU share that array, so
  * calls whose work overlaps on the GPU race and must be serialised by the
- * caller.  The first call on each device looks the array's address up (with
- * that device current) and caches it; make that first call before any stream
- * capture.  The call synchronises `stream` before it returns (it reads back
- * the input check).  Errors (message from fmm_last_error(NULL)):
+ * caller.  Every call looks the array's address up on the current device (a
+ * host-side query, so a device reset between calls is harmless) and
+ * synchronises `stream` before it returns (it reads back the input check into
+ * host memory): it cannot be called while the calling thread captures a
+ * stream into a CUDA graph.  Errors (message from fmm_last_error(NULL)):
  * FMM_ERR_ARG (range, NULL, non-finite coordinate), FMM_ERR_CUDA. */
 fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int height, uint64_t* keys, int64_t* perm,
                                     void* stream);
@@ -451,7 +467,9 @@ fmm_status fmm_server_wait(fmm_server_handle s, int64_t ticket, double timeout_s
  * queued now, [7] device bytes held by the lanes (handles and staging),
  * [8] [9] [10] lane time summed over batches, in microseconds: copying the
  * inputs, fmm_set_batch, fmm_evaluate + copying the results, [11] trims of
- * idle handles.  out: 12 int64, host. */
+ * idle handles, [12] evaluations on the lanes' handles that ran without a
+ * CUDA graph because capturing it failed (fmm_get_stats out[6], summed; 0
+ * expected).  out: 13 int64, host. */
 fmm_status fmm_server_stats(fmm_server_handle s, int64_t* out);
 
 /* Stops the lanes after their current batch, fails the requests still

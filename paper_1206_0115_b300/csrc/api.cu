@@ -33,6 +33,7 @@ fmm_status set_err(Ctx* c, fmm_status s, const char* fmt, ...) {
 
 fmm_status cuda_err(Ctx* c, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return FMM_OK;
+  if (c) c->last_cuda = e;
   if (e == cudaErrorMemoryAllocation) return set_err(c, FMM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return set_err(c, FMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -115,7 +116,65 @@ fmm_status raise_smem_limit(Ctx* c, const void* func, int bytes) {
   return FMM_OK;
 }
 
+// Small pinned host words of the handles (the readback of cell counts, the
+// root cube and the tensor-core error word), 1 KB per handle, carved from
+// pinned slabs that the process keeps: cudaFreeHost synchronises the device,
+// which a handle destroyed on one thread must not do to work (or a graph
+// capture) running on another thread's stream.
+constexpr size_t PINNED_SLOT = 1024, PINNED_SLAB_SLOTS = 256;
+
+struct PinnedSlots {
+  std::mutex mu;
+  std::vector<void*> free_slots;
+};
+PinnedSlots& pinned_slots() {
+  static PinnedSlots* p = new PinnedSlots();  // outlives every handle (never destroyed)
+  return *p;
+}
+
+void* pinned_slot() {
+  PinnedSlots& ps = pinned_slots();
+  std::lock_guard<std::mutex> lk(ps.mu);
+  if (ps.free_slots.empty()) {
+    void* slab = nullptr;
+    if (cudaMallocHost(&slab, PINNED_SLOT * PINNED_SLAB_SLOTS) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (size_t k = 0; k < PINNED_SLAB_SLOTS; ++k) ps.free_slots.push_back((char*)slab + k * PINNED_SLOT);
+  }
+  void* p = ps.free_slots.back();
+  ps.free_slots.pop_back();
+  return p;
+}
+
+void pinned_release(void* p) {
+  if (!p) return;
+  PinnedSlots& ps = pinned_slots();
+  std::lock_guard<std::mutex> lk(ps.mu);
+  ps.free_slots.push_back(p);
+}
+
 namespace {
+
+// Errors that a stream capture raises when the capture itself cannot
+// proceed (the launches it records would run fine one by one).
+bool is_capture_error(cudaError_t e) {
+  switch (e) {
+    case cudaErrorStreamCaptureUnsupported:
+    case cudaErrorStreamCaptureInvalidated:
+    case cudaErrorStreamCaptureMerge:
+    case cudaErrorStreamCaptureUnmatched:
+    case cudaErrorStreamCaptureUnjoined:
+    case cudaErrorStreamCaptureIsolation:
+    case cudaErrorStreamCaptureImplicit:
+    case cudaErrorCapturedEvent:
+    case cudaErrorStreamCaptureWrongThread:
+      return true;
+    default:
+      return false;
+  }
+}
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -194,7 +253,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                             (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
                             (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p,
-                            c->m2l_f16};
+                            c->m2l_f16, (int64_t)c->wait_ns};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -246,6 +305,7 @@ fmm_status check_device_error(Ctx* c) {
 
 fmm_status build_graph(Ctx* c) {
   drop_graph(c);
+  c->last_cuda = cudaSuccess;
   cudaStream_t cap = c->cap;
   FMM_CUDA(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   fmm_status st = enqueue_eval(c, cap);
@@ -347,32 +407,42 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
       cuda_err(c, cudaGetLastError(), "fmm_create: event creation");
       return fail(FMM_ERR_CUDA);
     }
+  // Creation is ordered on the handle's own non-blocking side stream (the
+  // caller's stream is not known yet): no legacy-stream operation and no
+  // device-wide synchronisation, so that handles created on one thread leave
+  // graph captures running on other threads' streams undisturbed.
+  c->stream = c->side;
   void* p;
   // corner, side, and the leaf frame of the FP32 coordinates (tree.cu, k_bbox_final)
   if ((st = dalloc(c, &p, 8 * sizeof(double))) != FMM_OK) return fail(st);
   c->box = (double*)p;
   if ((st = dalloc(c, &p, 128 * sizeof(int32_t))) != FMM_OK) return fail(st);
   c->counters = (int32_t*)p;
-  if (cudaMallocHost((void**)&c->counters_h, 128 * sizeof(int32_t)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->box_h, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->tc_err_h, sizeof(int32_t)) != cudaSuccess) {
-    cuda_err(c, cudaGetLastError(), "fmm_create: pinned host buffers");
+  c->pinned = pinned_slot();
+  if (!c->pinned) {
+    set_err(c, FMM_ERR_OOM, "fmm_create: pinned host memory");
     return fail(FMM_ERR_OOM);
   }
+  // 512 B of counters, 64 B of cube, the error word
+  c->counters_h = (int32_t*)c->pinned;
+  c->box_h = (double*)((char*)c->pinned + 512);
+  c->tc_err_h = (int32_t*)((char*)c->pinned + 576);
+  *c->tc_err_h = 0;
   for (int l = 0; l <= c->leaf; ++l) {
     size_t bytes = sizeof(int32_t) * ((size_t)1 << (3 * l));
     if ((st = dalloc(c, &p, bytes)) != FMM_OK) return fail(st);
     c->lv.grid[l] = (int32_t*)p;
-    if (cudaMemset(p, 0xFF, bytes) != cudaSuccess) {
+    if (cudaMemsetAsync(p, 0xFF, bytes, c->side) != cudaSuccess) {
       cuda_err(c, cudaGetLastError(), "fmm_create: grid memset");
       return fail(FMM_ERR_CUDA);
     }
   }
   if ((st = operators_init(c)) != FMM_OK) return fail(st);
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaStreamSynchronize(c->side) != cudaSuccess) {
     cuda_err(c, cudaGetLastError(), "fmm_create");
     return fail(FMM_ERR_CUDA);
   }
+  c->stream = nullptr;  // the default until fmm_set_stream: the legacy stream
   *out = c;
   return FMM_OK;
 }
@@ -380,7 +450,8 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
 fmm_status fmm_destroy(fmm_handle h) {
   Ctx* c = h;
   if (!c) return FMM_OK;
-  if (c->stream) cudaStreamSynchronize(c->stream);
+  // the handle's stream (NULL: the legacy stream) may still copy into its pinned slot
+  if (c->side) cudaStreamSynchronize(c->stream);
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
   void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pleaf, c->pos64, c->pos32, c->pos32lo,
@@ -407,9 +478,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   }
   if (c->side) cudaStreamSynchronize(c->side);
   cudaGetLastError();
-  if (c->counters_h) cudaFreeHost(c->counters_h);
-  if (c->tc_err_h) cudaFreeHost(c->tc_err_h);
-  if (c->box_h) cudaFreeHost(c->box_h);
+  pinned_release(c->pinned);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -618,14 +687,16 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
   bool eager = !c->use_graph;
   if (c->use_graph && (!c->graph_ok || c->graph_sig != graph_signature(c))) {
     const fmm_status gs = build_graph(c);
-    if (gs != FMM_OK && gs != FMM_ERR_CUDA) return gs;
-    if (gs == FMM_ERR_CUDA) {
-      // the capture failed (a capture error is not sticky): the same launches
-      // run without a graph; a device fault fails them again and is returned
+    if (gs != FMM_OK) {
+      // Only a failed capture falls back (a capture error is not sticky):
+      // the same launches run without a graph, counted in fmm_get_stats
+      // out[6], and the capture's message stays in fmm_last_error.  Any
+      // other failure -- instantiation, a launch error, a device fault -- is
+      // returned.
+      if (gs != FMM_ERR_CUDA || !is_capture_error(c->last_cuda)) return gs;
       cudaGetLastError();
       drop_graph(c);
       c->graph_fallbacks++;
-      c->err[0] = 0;
       eager = true;
     }
   }
@@ -695,6 +766,16 @@ fmm_status fmm_evaluate_stokes(fmm_handle h, const double* f, double* u) {
     FMM_CUDA(c, cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
     FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   }
+  return FMM_OK;
+}
+
+fmm_status fmm_set_wait_limit(fmm_handle h, double seconds) {
+  if (!h) return FMM_ERR_ARG;
+  if (!(seconds > 0.0 && seconds <= 60.0))
+    return set_err(h, FMM_ERR_ARG, "fmm_set_wait_limit: %g s outside (0, 60]", seconds);
+  const double ns = std::ceil(seconds * 1e9);
+  h->wait_ns = (uint64_t)ns;
+  h->graph_ok = false;  // the limit is a kernel argument baked into the graph
   return FMM_OK;
 }
 

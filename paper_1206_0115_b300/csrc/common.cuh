@@ -112,6 +112,7 @@ struct fmm_ctx {
   cudaEvent_t ev_p2p = nullptr;  // where the P2P branch starts (after the compressed M2L projection)
   bool p2p_after_proj = false;   // ev_p2p was recorded by the M2L launch
   char err[512] = {0};
+  cudaError_t last_cuda = cudaSuccess;  // the CUDA error behind the last FMM_ERR_CUDA / FMM_ERR_OOM
 
   // particles
   int64_t n = 0, ncap = 0;
@@ -146,6 +147,7 @@ struct fmm_ctx {
   int64_t scratch_cap = 0;  // in uint32 words
   double* box = nullptr;    // lo[3], W
   int32_t* counters = nullptr;   // device: [0..L) ncell, [16 + 8 l + c] class counts, [127] bad input
+  void* pinned = nullptr;         // the handle's 1 KB slot of pinned host memory (below)
   int32_t* counters_h = nullptr; // pinned host mirror
   double* box_h = nullptr;       // pinned
 
@@ -234,6 +236,7 @@ struct fmm_ctx {
   int64_t tc_partial_cap = 0;
   int32_t* tc_err = nullptr;      // device error word of the tensor-core kernel
   int32_t* tc_err_h = nullptr;    // pinned mirror, copied after every evaluation
+  uint64_t wait_ns = 2000000000ull;  // limit of each pipeline wait of the tensor-core kernels (fmm_set_wait_limit)
   alignas(64) unsigned char tm_khi[128], tm_klo[128];  // CUtensorMap of the operator bank
   int64_t tm_rows = -1;
   alignas(64) unsigned char tm_vthi[128], tm_vtlo[128], tm_uhi[128], tm_ulo[128];  // compressed banks

@@ -1,7 +1,10 @@
 // m2l.cu -- M2L dispatch (Sec. 2.1.2): the FP64 path runs the CUDA-core
-// kernel in FP64; the mixed path runs the tcgen05 kernel (3xTF32) when the
-// order allows it (p <= 7) and otherwise the CUDA-core kernel on FP32 sums of
-// the TF32 pairs.
+// kernels in FP64; the mixed path runs the tcgen05 kernels -- three products
+// of FP16 hi/lo operand pairs by default, of TF32 hi/lo pairs with
+// FMM_M2L_MATH=tf32 -- when the order allows it (p <= 7: the padded rows,
+// order^3 + 1 rounded up to 32, fit the tensor-core kernels' accumulators)
+// and otherwise (p >= 8) the CUDA-core kernels on FP32 sums of the
+// split pairs.
 #include "common.cuh"
 
 namespace fmm {

@@ -537,9 +537,10 @@ fmm_status svd_prepare(Ctx* c) {
     c->svd_sm = (int16_t*)ptr;
     c->svd_canon = (int8_t*)(c->svd_sm + (size_t)FMM_NT * C);
     c->svd_tcanon = c->svd_canon + 48;
-    FMM_CUDA(c, cudaMemcpy(c->svd_sm, sm.data(), sm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-    FMM_CUDA(c, cudaMemcpy(c->svd_canon, canon.data(), canon.size(), cudaMemcpyHostToDevice));
-    FMM_CUDA(c, cudaMemcpy(c->svd_tcanon, t_canon.data(), t_canon.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_sm, sm.data(), sm.size() * sizeof(int16_t), cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_canon, canon.data(), canon.size(), cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_tcanon, t_canon.data(), t_canon.size(), cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaStreamSynchronize(c->stream));  // host tables go out of scope
   }
   double* K;
   FMM_TRY(dalloc(c, &ptr, sizeof(double) * mat));
@@ -614,7 +615,8 @@ fmm_status svd_banks(Ctx* c) {
     if (f16) {
       // |U entries| <= 2 s_max (columns of U Sigma and their means), |V entries| <= 1
       std::vector<double> sv((size_t)16 * C);
-      FMM_CUDA(c, cudaMemcpy(sv.data(), c->svd_vals, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost));
+      FMM_CUDA(c, cudaMemcpyAsync(sv.data(), c->svd_vals, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost, c->stream));
+      FMM_CUDA(c, cudaStreamSynchronize(c->stream));
       double smax = 0.0;
       for (double v : sv) smax = std::max(smax, std::fabs(v));
       c->svd_vscale = tc::pow2_scale(1.0f);
@@ -666,9 +668,10 @@ fmm_status m2l_svd_prepare(Ctx* c) {
       c->svd_trank = c->svd_ry + FMM_NT;
       c->svd_yoff = c->svd_trank + FMM_NT;
     }
-    FMM_CUDA(c, cudaMemcpy(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
-    FMM_CUDA(c, cudaMemcpy(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice));
-    FMM_CUDA(c, cudaMemcpy(c->svd_yoff, yoff.data(), sizeof(int32_t) * yoff.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->svd_yoff, yoff.data(), sizeof(int32_t) * yoff.size(), cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->svd_ysig = sig;
     c->svd_yoff_h = yoff;
   }

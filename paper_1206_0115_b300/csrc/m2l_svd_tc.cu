@@ -94,6 +94,7 @@ struct ProjArgs {
   const float* mscale;
   uint32_t* ymax;
   float vscale;
+  uint64_t wait_ns;      // limit of a pipeline wait (fmm_set_wait_limit)
 };
 
 // Slot of the max |Y| of (problem, level): problem -1 (cells above a batch's
@@ -305,7 +306,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
         const int s = (int)(it % a.nst);
         const uint32_t ph = (it / a.nst) & 1u;
-        if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
+        if (!warp_wait(empty(s), ph ^ 1u, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -340,7 +341,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       const int n = a.recs[unit].n, cols = 16 * a.recs[unit].cols16;
       if (n == 0) continue;
       const int b = (int)(uu & 1u);
-      if (!warp_wait(acc_empty(b), ((uu >> 1) & 1u) ^ 1u, abort_flag)) {
+      if (!warp_wait(acc_empty(b), ((uu >> 1) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
         ok = false;
         break;
       }
@@ -352,7 +353,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
         const int s = (int)(it % a.nst);
         const uint32_t ph = (it / a.nst) & 1u;
-        if (!warp_wait(full(s), ph, abort_flag)) {
+        if (!warp_wait(full(s), ph, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -404,7 +405,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       const bool valid = row < g.count;
       const int64_t cellrow = valid ? (int64_t)g.crow + lv.cls[g.level][g.first + row] : 0;
       const int b = (int)(uu & 1u);
-      if (!warp_wait(acc_full(b), (uu >> 1) & 1u, abort_flag)) {
+      if (!warp_wait(acc_full(b), (uu >> 1) & 1u, abort_flag, a.wait_ns)) {
         ok = false;
         break;
       }
@@ -491,6 +492,7 @@ struct ExpArgs {
   const uint32_t* ymax;
   const Tile* tiles;
   float uscale;
+  uint64_t wait_ns;  // limit of a pipeline wait (fmm_set_wait_limit)
 };
 
 // pow2_scale of the max |Y| of the problem of target row r of a tile.
@@ -660,7 +662,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
             }
             const int s = (int)(j % a.nst);
             const uint32_t ph = (j / a.nst) & 1u;
-            if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
+            if (!warp_wait(empty(s), ph ^ 1u, abort_flag, a.wait_ns)) {
               ok = false;
               break;
             }
@@ -709,7 +711,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
       for (int ag = a0; ag < a1 && ok; ag += a.tpa, ++tt) {
         const int ae = min(a1, ag + a.tpa);
         const int b = (int)(tt & 1u);
-        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag)) {
+        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -723,7 +725,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
           for (int kc = 0; kc < kch; ++kc, ++it) {
             const int s = (int)(it % a.nst);
             const uint32_t ph = (it / a.nst) & 1u;
-            if (!warp_wait(full(s), ph, abort_flag)) {
+            if (!warp_wait(full(s), ph, abort_flag, a.wait_ns)) {
               ok = false;
               break;
             }
@@ -782,7 +784,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
       if (a0 >= a1) continue;
       for (int ag = a0; ag < a1; ag += a.tpa, ++tt) {
         const int b = (int)(tt & 1u);
-        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag)) {
+        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -993,6 +995,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.mscale = c->svd_mscale;
   p.ymax = ymax;
   p.vscale = c->svd_vscale;
+  p.wait_ns = c->wait_ns;
   k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
                                                        c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
                                                        (ProjRec*)c->svd_recs, c->tc_err);
@@ -1027,6 +1030,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.ymax = ymax;
   e.tiles = c->tiles;
   e.uscale = c->svd_uscale;
+  e.wait_ns = c->wait_ns;
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
   const int ue = c->ntiles * e.nh * EX_GROUPS;

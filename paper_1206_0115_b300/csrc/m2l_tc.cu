@@ -67,6 +67,7 @@ struct TcArgs {
   float kscale;
   uint32_t acol;       // first TMEM column of the A stages (after the two accumulators)
   uint32_t tmem_cols;  // power of two >= 2 * nhalf + 32 * nst
+  uint64_t wait_ns;    // limit of a pipeline wait (fmm_set_wait_limit)
 };
 
 // Work unit u -> (group g, column half h, tile): groups outermost so that the
@@ -217,7 +218,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
           }
           const int s = (int)(j % a.nst);
           const uint32_t ph = (j / a.nst) & 1u;
-          if (!warp_wait(empty(s), ph ^ 1u, abort_flag)) {
+          if (!warp_wait(empty(s), ph ^ 1u, abort_flag, a.wait_ns)) {
             ok = false;
             break;
           }
@@ -266,7 +267,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       if (a0 >= a1) continue;
       for (int ai = a0; ai < a1 && ok; ++ai, ++tt) {
         const int b = (int)(tt & 1u);
-        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag)) {
+        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -275,7 +276,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
         for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
           const int s = (int)(it % a.nst);
           const uint32_t ph = (it / a.nst) & 1u;
-          if (!warp_wait(full(s), ph, abort_flag)) {
+          if (!warp_wait(full(s), ph, abort_flag, a.wait_ns)) {
             ok = false;
             break;
           }
@@ -332,7 +333,7 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
       if (a0 >= a1) continue;
       for (int ai = a0; ai < a1; ++ai, ++tt) {
         const int b = (int)(tt & 1u);
-        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag)) {
+        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -501,6 +502,7 @@ fmm_status launch_m2l_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   a.cls_t = c->cls_t;
   a.partial = c->tc_partial;
   a.err = c->tc_err;
+  a.wait_ns = c->wait_ns;
   a.ntiles = c->ntiles;
   a.groups = TC_GROUPS;
   a.gt = TC_GT;

@@ -239,14 +239,15 @@ fmm_status operators_init(Ctx* c) {
   c->cls_t = (int16_t*)ptr;
   FMM_TRY(dalloc(c, &ptr, sizeof(int16_t) * st.size()));
   c->src_t = (int16_t*)ptr;
-  FMM_CUDA(c, cudaMemcpy(c->nodes64, nodes.data(), sizeof(double) * p, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->cheb64, cheb.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->cheb32, cheb32.data(), sizeof(float) * p * p, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->m2m64, A.data(), sizeof(double) * 2 * p * p, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->m2m32, A32.data(), sizeof(float) * 2 * p * p, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->tvec, tv.data(), tv.size(), cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->cls_t, ct.data(), sizeof(int16_t) * ct.size(), cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->src_t, st.data(), sizeof(int16_t) * st.size(), cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpyAsync(c->nodes64, nodes.data(), sizeof(double) * p, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->cheb64, cheb.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->cheb32, cheb32.data(), sizeof(float) * p * p, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->m2m64, A.data(), sizeof(double) * 2 * p * p, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->m2m32, A32.data(), sizeof(float) * 2 * p * p, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->tvec, tv.data(), tv.size(), cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->cls_t, ct.data(), sizeof(int16_t) * ct.size(), cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->src_t, st.data(), sizeof(int16_t) * st.size(), cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
   return FMM_OK;
 }
 

@@ -56,6 +56,7 @@ struct Lane {
   int last_order = 0;           // order of its last batch (its resident tree)
   bool busy = false;
   bool trimmed = true;          // nothing but operators held since the last full trim
+  int64_t graph_fallbacks = 0;  // evaluations of its handles that ran without a graph (fmm_get_stats out[6])
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -271,6 +272,15 @@ fmm_status run_batch(fmm_server* s, Lane* L, const std::vector<Req*>& b, int64_t
   const Clock::time_point t2 = Clock::now();
   if (st == FMM_OK && n > 0) st = fmm_evaluate(h, phi, F);
   if (st != FMM_OK) return server_err(s, st, "batch of %zu requests: %s", b.size(), fmm_last_error(h));
+  {
+    int64_t sum = 0;
+    for (auto& kv : L->h) {
+      int64_t o[8];
+      if (fmm_get_stats(kv.second, o) == FMM_OK) sum += o[6];
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    L->graph_fallbacks = sum;
+  }
   off = 0;
   for (Req* r : b) {
     if (r->n > 0) {
@@ -500,6 +510,9 @@ fmm_status fmm_server_stats(fmm_server_handle s, int64_t* out) {
   out[9] = s->us_build;
   out[10] = s->us_eval;
   out[11] = s->trims;
+  int64_t fb = 0;
+  for (Lane* L : s->lanes) fb += L->graph_fallbacks;
+  out[12] = fb;
   return FMM_OK;
 }
 

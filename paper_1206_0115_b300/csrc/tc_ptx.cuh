@@ -16,7 +16,11 @@
 namespace fmm {
 namespace tc {
 
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;     // 2 s per wait: far beyond any real stage
+// Default limit of a pipeline wait (2 s: far beyond any real stage; a handle
+// may set another, fmm_set_wait_limit).  The waits of the abort path -- for
+// copies and MMAs already issued -- always take this one, so that a kernel
+// that gives up never leaves work in flight into memory it releases.
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -45,19 +49,20 @@ __device__ inline bool mbar_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of parity `parity` to complete; false after TC_WAIT_NS.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the phase of parity `parity` to complete; false after limit_ns.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = TC_WAIT_NS) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = gtime();
   while (!mbar_test(bar, parity))
-    if (gtime() - t0 > TC_WAIT_NS) return false;
+    if (gtime() - t0 > limit_ns) return false;
   return true;
 }
-// Warp-uniform wait: lane 0 waits, the whole warp gets its verdict (and the
-// CTA's abort flag), so warp-collective instructions that follow stay converged.
-__device__ inline bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// Warp-uniform pipeline wait: lane 0 waits (at most limit_ns), the whole warp
+// gets its verdict (and the CTA's abort flag), so warp-collective
+// instructions that follow stay converged.
+__device__ inline bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit_ns) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity) && !*abort_flag;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit_ns) && !*abort_flag;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 

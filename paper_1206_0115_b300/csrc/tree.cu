@@ -1164,9 +1164,6 @@ constexpr int64_t NA_WORDS = NA_COUNTERS + 128;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 
-std::mutex g_noalloc_mutex;
-uint32_t* g_noalloc_addr[64] = {nullptr};
-
 __global__ void k_noalloc_out(int64_t n, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
                               uint64_t* __restrict__ keys, int64_t* __restrict__ perm) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1190,25 +1187,16 @@ extern "C" fmm_status fmm_morton_order_noalloc(int64_t n, const double* xyz, int
                    (long long)n, (long long)NOALLOC_MAX_N, (long long)NOALLOC_MAX_N);
   if (n == 0) return FMM_OK;
   if (!xyz || !keys || !perm) return set_err(nullptr, FMM_ERR_ARG, "fmm_morton_order_noalloc: NULL pointer");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: no current device (%s)", cudaGetErrorString(e));
-  }
+  // The array's device address on the current device, looked up on every
+  // call (a host-side query, no device work): in host code the symbol is a
+  // host-side stand-in, and a cached address would go stale after the
+  // caller resets the device.
   uint32_t* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      e = cudaGetSymbolAddress((void**)&g_noalloc_addr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_noalloc_addr[dev] = nullptr;
-        cudaGetLastError();
-        return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: cudaGetSymbolAddress: %s",
-                       cudaGetErrorString(e));
-      }
-    }
-    base = g_noalloc_addr[dev];
+  cudaError_t e = cudaGetSymbolAddress((void**)&base, g_noalloc_scratch);
+  if (e != cudaSuccess || !base) {
+    cudaGetLastError();
+    return set_err(nullptr, FMM_ERR_CUDA, "fmm_morton_order_noalloc: cudaGetSymbolAddress: %s",
+                   cudaGetErrorString(e));
   }
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t *ka = base + NA_KEY_A, *kb = base + NA_KEY_B, *va = base + NA_IDX_A, *vb = base + NA_IDX_B;
@@ -1373,15 +1361,17 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
     c->fb_thr = (int64_t*)p;
     c->fb_thr_cap = cap;
   }
-  // the tables are small; synchronous copies keep the host vectors' lifetime simple
+  // the tables are small; copies on the handle's stream, waited for, keep the
+  // host vectors' lifetime simple (no legacy-stream operation)
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));
-  FMM_CUDA(c, cudaMemcpy(c->fb_pstart, start.data(), 8 * (size_t)(nprob + 1), cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->fb_prob, prob.data(), sizeof(BatchProb) * (size_t)nprob, cudaMemcpyHostToDevice));
-  FMM_CUDA(c, cudaMemcpy(c->fb_bstart, bstart.data(), 4 * (size_t)(nprob + 1), cudaMemcpyHostToDevice));
+  FMM_CUDA(c, cudaMemcpyAsync(c->fb_pstart, start.data(), 8 * (size_t)(nprob + 1), cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->fb_prob, prob.data(), sizeof(BatchProb) * (size_t)nprob, cudaMemcpyHostToDevice, c->stream));
+  FMM_CUDA(c, cudaMemcpyAsync(c->fb_bstart, bstart.data(), 4 * (size_t)(nprob + 1), cudaMemcpyHostToDevice, c->stream));
   if (!sstart.empty()) {
-    FMM_CUDA(c, cudaMemcpy(c->fb_sstart, sstart.data(), 4 * sstart.size(), cudaMemcpyHostToDevice));
-    FMM_CUDA(c, cudaMemcpy(c->fb_sprob, sprob.data(), 4 * sprob.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(c, cudaMemcpyAsync(c->fb_sstart, sstart.data(), 4 * sstart.size(), cudaMemcpyHostToDevice, c->stream));
+    FMM_CUDA(c, cudaMemcpyAsync(c->fb_sprob, sprob.data(), 4 * sprob.size(), cudaMemcpyHostToDevice, c->stream));
   }
+  FMM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->forest = true;
   c->nprob = nprob;
   c->leaf = Lf;

@@ -62,6 +62,7 @@ _SIGS = {
     "fmm_get_m2l_kernel_times": [_vp, _vp],
     "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
     "fmm_measure_fp32_rate": [_vp],
+    "fmm_set_wait_limit": [_vp, C.c_double],
 }
 _SIGS.update({
     "fmm_server_create": [_vp, C.POINTER(_vp)],
@@ -263,6 +264,10 @@ def fmm_get_m2l_kernel_times(h) -> np.ndarray:
     return out
 
 
+def fmm_set_wait_limit(h, seconds: float) -> int:
+    return _check(h, lib.fmm_set_wait_limit(h, float(seconds)))
+
+
 def fmm_measure_fp32_rate() -> np.ndarray:
     """[scalar FMA flop/s, packed f32x2 FMA flop/s, SM count, 0] of the current device."""
     out = np.zeros(4, dtype=np.float64)
@@ -314,7 +319,7 @@ def fmm_server_wait(s, ticket: int, timeout_s: float = -1.0) -> np.ndarray:
 
 
 def fmm_server_stats(s) -> np.ndarray:
-    out = np.zeros(12, dtype=np.int64)
+    out = np.zeros(13, dtype=np.int64)
     _check_server(s, lib.fmm_server_stats(s, _ptr(out)))
     return out
 

@@ -114,6 +114,7 @@ def test_arrivals_during_work_overlap_on_lanes(F):
         F.fmm_server_destroy(s)
     assert st[0] == len(reqs)
     assert st[4] >= 2, "no two batches ran at once"
+    assert st[12] == 0
     for k in (0, 5, 11, 23):
         aphi, aF = _alone(F, reqs[k])
         assert oracle.rel_l2(reqs[k]["phi"], aphi) <= TOL_ALONE, k
@@ -140,6 +141,7 @@ def test_admission_respects_the_budget(F):
         F.fmm_server_destroy(s)
     assert st[0] == len(reqs)
     assert 0 < st[3] <= budget
+    assert st[12] == 0, "an evaluation graph capture failed on a lane"
     aphi, aF = _alone(F, reqs[3])
     assert oracle.rel_l2(reqs[3]["phi"], aphi) <= TOL_ALONE
 
@@ -176,3 +178,34 @@ def test_device_buffers_and_errors(F):
     aphi, aF = _alone(F, r)
     assert oracle.rel_l2(phi.cpu().numpy(), aphi) <= TOL_ALONE
     assert oracle.rel_l2(r2["phi"], aphi) <= TOL_ALONE
+
+
+def test_lanes_create_handles_while_others_capture(F):
+    """Four lanes with no warm-up: each creates its handles (and computes the
+    compressed operators) on first use while other lanes capture and replay
+    their evaluation graphs.  Handle creation is ordered on the handle's own
+    stream, with no device-wide synchronisation and no legacy-stream copy, so
+    no lane's graph capture fails (a failed capture would fall back to
+    launch-by-launch evaluation and be counted in stats[12])."""
+    reqs = _requests(32, 8000, nmin=3000, nmax=60000, orders=(3, 4, 5, 6))
+    s = F.fmm_server_create(4, F.FMM_MIXED, 64 << 30, 120_000, 4)
+    try:
+        def producer(part):
+            for r in part:
+                _submit(F, s, r)
+        ths = [threading.Thread(target=producer, args=(reqs[k::4],)) for k in range(4)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for r in reqs:
+            F.fmm_server_wait(s, r["ticket"], 300.0)
+        st = F.fmm_server_stats(s)
+    finally:
+        F.fmm_server_destroy(s)
+    assert st[0] == len(reqs)
+    assert st[12] == 0, "an evaluation graph capture failed while another lane created a handle"
+    for k in (0, 9, 18, 31):
+        aphi, aF = _alone(F, reqs[k])
+        assert oracle.rel_l2(reqs[k]["phi"], aphi) <= TOL_ALONE, k
+        assert oracle.rel_l2(reqs[k]["F"], aF) <= TOL_ALONE, k
