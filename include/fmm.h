@@ -325,10 +325,12 @@ fmm_status fmm_get_stats(fmm_handle h, int64_t* out);
  * compressed operators exist; one pair costs 4 * order^3 * rank flop),
  * out[14] / out[15] = sum over the (M2L tile, transfer vector) blocks of the
  * compressed projection / expansion of the Y columns per cell (the rank,
- * rounded up to 16 on the mixed path; 0 until the compressed operators
- * exist): the projection multiplies 128 x order^3 by order^3 x out[14]
- * columns, the expansion 128 x out[15] by out[15] x order^3 (summed over
- * blocks).
+ * rounded up to 16 on the mixed path -- to 8 with the FP16 tensor-core
+ * operands, whose expansion runs each tile over its child class's
+ * concatenated ranks: out[15] = tiles x that K; 0 until the compressed
+ * operators exist): the projection multiplies 128 x order^3 by order^3 x
+ * out[14] columns, the expansion 128 x out[15] by out[15] x order^3 (summed
+ * over blocks).
  * Synchronises the stream.  out: 16 int64, host. */
 fmm_status fmm_get_work(fmm_handle h, int64_t* out);
 

@@ -466,7 +466,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
                   c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax, c->svd_mscale, c->tc_mmax,
                   c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_frame, c->fb_thr, c->fb_sstart, c->fb_sprob,
-                  c->fb_bstart};
+                  c->fb_bstart, c->svd_Yx, c->svd_dst, c->svd_kap8, c->svd_Uc};
   // back to the pool on the handle's own side stream (both streams are idle)
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, c->side);

@@ -280,6 +280,23 @@ struct fmm_ctx {
   float svd_vscale = 1.f, svd_uscale = 1.f;
   uint32_t* svd_umax = nullptr;  // max |Y| per (problem + 1, level): [FMM_MAX_BATCH + 1][FMM_MAX_LEVELS]
   float* svd_mscale = nullptr;   // scale of each class-ordered multipole row (FP16 operands)
+  // FP16 tensor-core form (svd_wants_f16): ranks padded to 8; the projection
+  // writes y straight into the expansion's operand layout Yx ([tile][kc][128
+  // rows], interleaved FP16 hi/lo 64-byte rows), through the destination map
+  // dst[src-list index][expansion row] = tile * 128 + row (-1: no target);
+  // the expansion's factor bank Uc is U per target class along the class's
+  // concatenated ranks (kap8: start of t's ranks / 8 per target class, kt8:
+  // the class's total / 8, kct: 32-value chunks per tile row).
+  void* svd_Yx = nullptr;
+  size_t svd_Yx_cap = 0;
+  int32_t* svd_dst = nullptr;
+  size_t svd_dst_cap = 0;
+  int16_t* svd_kap8 = nullptr;    // [8][316], -1 if t is not in the class's list
+  int16_t* svd_srcidx = nullptr;  // [8][316]: index of t in the source class's list, -1 if none
+  int svd_kt8 = 0, svd_kct = 0;
+  uint32_t* svd_Uc = nullptr;
+  size_t svd_uc_bytes = 0;
+  int svd_x_groups = 0;           // K groups of the last expansion launch (partial slices per tile)
   std::vector<int32_t> svd_yoff_h;
   int32_t *svd_ry = nullptr, *svd_trank = nullptr, *svd_yoff = nullptr;  // [316], [316], [8][316]
   int64_t svd_YS = 0;            // Y values per cell row

@@ -40,7 +40,7 @@ k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ ti
                   const int16_t* __restrict__ tile_act, const int32_t* __restrict__ tile_nact, LevelPtrs lv,
                   const int16_t* __restrict__ cls_t, const int32_t* __restrict__ trank,
                   const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
-                  const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
+                  const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry, int64_t xk,
                   unsigned long long* __restrict__ out) {
   const Tile tl = tiles[blockIdx.x];
   const int row = threadIdx.x, zero = lv.ncell[tl.level];
@@ -71,6 +71,9 @@ k_count_m2l_pairs(const Tile* __restrict__ tiles, const int32_t* __restrict__ ti
       yp += t_ry[src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a]]];
     for (int a = 0; a < nact; ++a)
       ye += t_ry[cls_t[tl.cls * FMM_NT_CLASS + tile_act[(int64_t)blockIdx.x * FMM_NT_CLASS + a]]];
+    // FP16 tensor-core form: the expansion runs every tile over its class's
+    // whole concatenated K (xk values)
+    if (xk > 0) ye = (unsigned long long)xk;
     atomicAdd(&out[14], yp);
     atomicAdd(&out[15], ye);
   }
@@ -106,7 +109,11 @@ fmm_status work_counts(Ctx* c, int64_t* out) {
     k_count_m2l_pairs<<<c->ntiles, FMM_TILE, 0, c->stream>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact,
                                                              c->lv, c->cls_t, c->svd_ready ? c->svd_trank : nullptr,
                                                              c->src_act, c->src_nact, c->src_t,
-                                                             c->svd_ready ? c->svd_ry : nullptr, d);
+                                                             c->svd_ready ? c->svd_ry : nullptr,
+                                                             m2l_kind(c) == 5 && svd_wants_f16(c) && c->svd_kct > 0
+                                                                 ? 32 * (int64_t)c->svd_kct
+                                                                 : 0,
+                                                             d);
   FMM_CUDA(c, cudaGetLastError());
   FMM_CUDA(c, cudaMemcpyAsync(out, d, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   FMM_CUDA(c, cudaStreamSynchronize(c->stream));

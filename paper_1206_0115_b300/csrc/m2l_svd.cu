@@ -283,8 +283,40 @@ __global__ void k_svd_banks16(int C, int cpad, int64_t YS, const int8_t* __restr
       if (yo < 0) continue;
       put_h(VT, ((int64_t)cls * kch + (np >> 5)) * YS + yo + i, np & 31, v);
     }
+    if (!U) continue;
     put_h(U, ((int64_t)(i >> 5) * FMM_NT + t) * cpad + np, i & 31, u);
     if (n == 0) put_h(U, ((int64_t)(i >> 5) * FMM_NT + t) * cpad + C, i & 31, colmean[k * C + j] * uscale);
+  }
+}
+
+// The expansion's factor bank of the FP16 tensor-core form, by target class:
+// the class's transfer vectors in the order of its list (cls_t), each taking
+// its rank rounded up to 8 of the contracted index (kap8 = where its ranks
+// start, / 8), so that one slab of 32 contracted values covers consecutive
+// transfer vectors and the expansion's K runs over all of a target's
+// sources at once.  Row G = (cls * kct + k / 32) * cpad + sigma.m (mean row C),
+// FP16 hi/lo scaled by uscale, element k % 32; padding stays zero.
+__global__ void k_svd_bank_uc16(int C, int cpad, int kct, const int8_t* __restrict__ t_canon,
+                                const int16_t* __restrict__ sm, const int32_t* __restrict__ ord,
+                                const int32_t* __restrict__ rank, const double* __restrict__ W,
+                                const double* __restrict__ colmean, const int16_t* __restrict__ kap8, double uscale,
+                                uint16_t* __restrict__ Uc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)FMM_NT * C) return;
+  const int t = (int)(e / C), n = (int)(e - (int64_t)t * C);
+  const int k = t_canon[t], r = rank[k];
+  const int np = sm[e];
+  for (int i = 0; i < r; ++i) {
+    const int j = ord[k * C + i];
+    const double u = (W[((size_t)k * C + j) * C + n] - colmean[k * C + j]) * uscale;
+    for (int cls = 0; cls < 8; ++cls) {
+      const int kp = kap8[cls * FMM_NT + t];
+      if (kp < 0) continue;
+      const int kk = 8 * kp + i;
+      const int64_t G = ((int64_t)cls * kct + (kk >> 5)) * cpad;
+      put_h(Uc, G + np, kk & 31, u);
+      if (n == 0) put_h(Uc, G + C, kk & 31, colmean[k * C + j] * uscale);
+    }
   }
 }
 
@@ -600,7 +632,8 @@ fmm_status svd_banks(Ctx* c) {
     const int Rp = c->svd_rp;
     const int kw = f16 ? 32 : 16;
     const size_t vbytes = sizeof(float) * 32 * (size_t)8 * (cp / kw) * c->svd_YS;
-    const size_t ubytes = sizeof(float) * 32 * (size_t)((Rp + kw - 1) / kw) * FMM_NT * cp;
+    // FP16: the expansion takes the class-ordered bank Uc instead (below)
+    const size_t ubytes = f16 ? 128 : sizeof(float) * 32 * (size_t)((Rp + kw - 1) / kw) * FMM_NT * cp;
     dfree(c, c->svd_VThi, c->svd_vt_bytes);
     dfree(c, c->svd_Uhi, c->svd_u_bytes);
     c->svd_VThi = c->svd_Uhi = nullptr;
@@ -623,7 +656,19 @@ fmm_status svd_banks(Ctx* c) {
       c->svd_uscale = tc::pow2_scale((float)(2.0 * smax));
       k_svd_banks16<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
                                          c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, (double)c->svd_vscale,
-                                         (double)c->svd_uscale, (uint16_t*)c->svd_VThi, (uint16_t*)c->svd_Uhi);
+                                         (double)c->svd_uscale, (uint16_t*)c->svd_VThi, nullptr);
+      // the expansion's bank by target class, along the class's concatenated ranks
+      const size_t ucb = (size_t)128 * 8 * c->svd_kct * cp;
+      dfree(c, c->svd_Uc, c->svd_uc_bytes);
+      c->svd_Uc = nullptr;
+      c->svd_uc_bytes = 0;
+      FMM_TRY(dalloc(c, &ptr, ucb));
+      c->svd_Uc = (uint32_t*)ptr;
+      c->svd_uc_bytes = ucb;
+      FMM_CUDA(c, cudaMemsetAsync(ptr, 0, ucb, s));
+      k_svd_bank_uc16<<<grid, 128, 0, s>>>(C, cp, c->svd_kct, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
+                                           c->svd_W, c->svd_colmean, c->svd_kap8, (double)c->svd_uscale,
+                                           (uint16_t*)c->svd_Uc);
     } else {
       k_svd_banks32<<<grid, 128, 0, s>>>(C, cp, c->svd_YS, c->svd_tcanon, c->svd_sm, c->svd_ord, c->svd_rank_d,
                                          c->svd_W, c->svd_Z, c->svd_colmean, c->svd_yoff, c->svd_VThi, c->svd_Uhi);
@@ -643,13 +688,18 @@ fmm_status svd_banks(Ctx* c) {
 fmm_status m2l_svd_prepare(Ctx* c) {
   FMM_TRY(svd_prepare(c));
   const bool mixed = c->precision == FMM_MIXED;
-  const std::vector<int64_t> sig = {c->precision, c->svd_gen};
+  // FP16 tensor-core form: ranks padded to 8 (the projection's columns and
+  // the expansion's concatenated K); TF32 forms and the CUDA-core kernels: 16
+  const bool xf16 = mixed && svd_wants_f16(c);
+  const std::vector<int64_t> sig = {c->precision, c->svd_gen, xf16};
   void* ptr;
   if (sig != c->svd_ysig) {
+    c->svd32 = false;  // the mixed banks follow the Y layout
+    const int pad = xf16 ? 8 : 16;
     std::vector<int32_t> ry(FMM_NT), rank(FMM_NT), yoff(8 * FMM_NT, -1);
     for (int t = 0; t < FMM_NT; ++t) {
       rank[t] = c->t_rank_h[t];
-      ry[t] = mixed ? (rank[t] + 15) / 16 * 16 : rank[t];
+      ry[t] = mixed ? (rank[t] + pad - 1) / pad * pad : rank[t];
     }
     int64_t ys = 0;
     for (int cls = 0; cls < 8; ++cls) {
@@ -671,11 +721,38 @@ fmm_status m2l_svd_prepare(Ctx* c) {
     FMM_CUDA(c, cudaMemcpyAsync(c->svd_ry, ry.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice, c->stream));
     FMM_CUDA(c, cudaMemcpyAsync(c->svd_trank, rank.data(), sizeof(int32_t) * FMM_NT, cudaMemcpyHostToDevice, c->stream));
     FMM_CUDA(c, cudaMemcpyAsync(c->svd_yoff, yoff.data(), sizeof(int32_t) * yoff.size(), cudaMemcpyHostToDevice, c->stream));
+    if (xf16) {
+      // per target class: where each t's ranks start in the concatenated K (/ 8);
+      // per source class: the index of each t in the class's source list
+      std::vector<int16_t> tab(2 * 8 * FMM_NT, -1);
+      int kt8 = 0;
+      for (int ct = 0; ct < 8; ++ct) {
+        int o = 0;
+        for (int k = 0; k < FMM_NT_CLASS; ++k) {
+          const int slot = c->cls_t_h[ct * FMM_NT_CLASS + k];
+          tab[ct * FMM_NT + slot] = (int16_t)(o / 8);
+          o += ry[slot];
+        }
+        kt8 = std::max(kt8, o / 8);
+      }
+      for (int cs = 0; cs < 8; ++cs)
+        for (int k = 0; k < FMM_NT_CLASS; ++k) tab[8 * FMM_NT + cs * FMM_NT + c->src_t_h[cs * FMM_NT_CLASS + k]] = (int16_t)k;
+      if (!c->svd_kap8) {
+        FMM_TRY(dalloc(c, &ptr, sizeof(int16_t) * tab.size()));
+        c->svd_kap8 = (int16_t*)ptr;
+        c->svd_srcidx = c->svd_kap8 + 8 * FMM_NT;
+      }
+      FMM_CUDA(c, cudaMemcpyAsync(c->svd_kap8, tab.data(), sizeof(int16_t) * tab.size(), cudaMemcpyHostToDevice,
+                                  c->stream));
+      c->svd_kt8 = kt8;
+      c->svd_kct = (8 * kt8 + 31) / 32;
+    }
     FMM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->svd_ysig = sig;
     c->svd_yoff_h = yoff;
   }
   FMM_TRY(svd_banks(c));  // the mixed factor bank is laid out by the Y offsets
+  if (xf16) return FMM_OK;  // the FP16 tensor-core form keeps no Y rows (m2l_svd_tc_prepare: Yx)
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   const size_t ybytes = (size_t)(c->rows > 0 ? c->rows : 1) * c->svd_YS * esz;
   if (ybytes > c->svd_Y_cap) {

@@ -64,11 +64,12 @@ struct __align__(16) ProjRec {
   int32_t arow;            // the tile's first row in the class-ordered multipole copy
   int16_t count;           // cells in the tile
   int8_t cls, level, n;    // child class, level, transfer vectors in the group (0: no unit)
-  uint8_t cols16;          // sum of ranks / 16
-  int16_t slot[SP_MAXG];   // transfer vectors
-  int16_t yo16[SP_MAXG];   // their Y offsets in the class's rows / 16 (= their factor rows)
-  uint8_t ry16[SP_MAXG];   // their ranks / 16
-  int32_t pad[7];
+  uint8_t cols8;           // sum of the padded ranks / 8 (the MMA's N is this x 8 rounded up to 16)
+  int16_t yo8[SP_MAXG];    // their Y offsets in the class's rows / 8 (= their factor rows)
+  uint8_t ry8[SP_MAXG];    // their padded ranks / 8
+  uint8_t kidx[SP_MAXG];   // their index in the source class's list (src_t)
+  int16_t kap8[SP_MAXG];   // FP16 form: start of their ranks in the target class's concatenated K, / 8
+  uint8_t pad[14];
 };
 static_assert(sizeof(ProjRec) == 128, "one record = 128 bytes");
 
@@ -82,7 +83,16 @@ struct McBase {
 struct ProjArgs {
   const ProjRec* recs;   // [ntiles][ngroups]: unit u = tile * ngroups + group, so that CTAs running
                          // at the same time share a tile's multipoles in L2
-  float* Y;
+  float* Y;              // TF32 form: the sources' Y rows
+  // FP16 form: y goes to the expansion's operand layout Yx through the
+  // destination map dst[src-list index][expansion row] (tile * 128 + row of
+  // the target, -1: none), scaled by pow2_scale of the bound ||M||_2 of its
+  // (problem, level) (ybound)
+  uint32_t* Yx;
+  const int32_t* dst;
+  int64_t drows;
+  int kct;
+  const uint32_t* ybound;
   int32_t* err;
   int64_t YS;
   int64_t mrows;         // rows of the class-ordered multipole copy per chunk of coefficients
@@ -109,26 +119,32 @@ __global__ void __launch_bounds__(256)
 k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs lv, McBase mb,
              const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
              const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
-             const int32_t* __restrict__ yoff, ProjRec* __restrict__ recs, int32_t* __restrict__ err) {
-  __shared__ int16_t s_slot[FMM_NT_CLASS];
-  __shared__ int16_t s_yo16[FMM_NT_CLASS];
-  __shared__ uint8_t s_ry16[FMM_NT_CLASS];
+             const int32_t* __restrict__ yoff, const int8_t* __restrict__ tvec, const int16_t* __restrict__ kap8,
+             ProjRec* __restrict__ recs, int32_t* __restrict__ err) {
+  __shared__ int16_t s_kap8[FMM_NT_CLASS];
+  __shared__ int16_t s_yo8[FMM_NT_CLASS];
+  __shared__ uint8_t s_ry8[FMM_NT_CLASS];
+  __shared__ uint8_t s_kidx[FMM_NT_CLASS];
   __shared__ int16_t s_gs[FMM_NT_CLASS + 2];
   __shared__ int s_ng;
   const int tile = blockIdx.x;
   const Tile tl = tiles[tile];
   const int nact = src_nact[tile];
   for (int a = threadIdx.x; a < nact; a += blockDim.x) {
-    const int slot = src_t[tl.cls * FMM_NT_CLASS + src_act[(int64_t)tile * FMM_NT_CLASS + a]];
-    s_slot[a] = (int16_t)slot;
-    s_ry16[a] = (uint8_t)(t_ry[slot] / 16);
-    s_yo16[a] = (int16_t)(yoff[tl.cls * FMM_NT + slot] / 16);
+    const int k = src_act[(int64_t)tile * FMM_NT_CLASS + a];
+    const int slot = src_t[tl.cls * FMM_NT_CLASS + k];
+    s_kidx[a] = (uint8_t)k;
+    s_ry8[a] = (uint8_t)(t_ry[slot] / 8);
+    s_yo8[a] = (int16_t)(yoff[tl.cls * FMM_NT + slot] / 8);
+    // the targets' class: the source's with the parities of t flipped
+    const int ct = tl.cls ^ (((tvec[3 * slot] & 1) << 2) | ((tvec[3 * slot + 1] & 1) << 1) | (tvec[3 * slot + 2] & 1));
+    s_kap8[a] = kap8 ? kap8[ct * FMM_NT + slot] : (int16_t)-1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int n = 0, cols = 0, members = 0;
     for (int a = 0; a < nact; ++a) {
-      const int ry = 16 * s_ry16[a];
+      const int ry = 8 * s_ry8[a];
       if (a == 0 || cols + ry > SP_ACC || members == SP_MAXG) {
         s_gs[n++] = (int16_t)a;
         cols = 0;
@@ -155,14 +171,15 @@ k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs 
     if (gi < ng) {
       const int a0 = s_gs[gi], a1 = s_gs[gi + 1];
       for (int a = a0; a < a1; ++a, ++n) {
-        r.slot[n] = s_slot[a];
-        r.ry16[n] = s_ry16[a];
-        r.yo16[n] = s_yo16[a];
-        cols += 16 * s_ry16[a];
+        r.ry8[n] = s_ry8[a];
+        r.yo8[n] = s_yo8[a];
+        r.kidx[n] = s_kidx[a];
+        r.kap8[n] = s_kap8[a];
+        cols += 8 * s_ry8[a];
       }
     }
     r.n = (int8_t)n;
-    r.cols16 = (uint8_t)(cols / 16);
+    r.cols8 = (uint8_t)(cols / 8);
     recs[(int64_t)tile * ngroups + gi] = r;
   }
 }
@@ -190,21 +207,41 @@ __global__ void k_gather_cls(int l, LevelPtrs lv, McBase mb, int cpad, int64_t r
 // (chunk kc = k / 32), two per 32-bit word, scaled by pow2_scale of the
 // cell's own max |M| (recorded per row for the projection's epilogue).  One
 // block of 128 threads per cell, a thread per pair of coefficients.
+// ybound (FP16 form, may be NULL): the largest ||M_S||_2 of every (problem,
+// level), by atomic max.  A projection y = V^T M_S has |y_i| <= ||M_S||_2
+// (V has orthonormal columns), so a power of two taken from this bound keeps
+// every projection of the (problem, level) inside the FP16 range before the
+// projection runs.
 __global__ void __launch_bounds__(128)
 k_gather_cls16(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
-               const float* __restrict__ Mlo, uint32_t* __restrict__ Mc, float* __restrict__ mscale) {
+               const float* __restrict__ Mlo, uint32_t* __restrict__ Mc, float* __restrict__ mscale,
+               uint32_t* __restrict__ ybound) {
   __shared__ uint32_t s_max[4];
+  __shared__ float s_sq[4];
   const int j = blockIdx.x;
   const int cell = lv.cls[l][j];
   const int c = lv.key[l][cell] & 7;
   const int64_t row = mb.base[l][c] + (j - mb.clsoff[l][c]), src = (lv.row_off[l] + cell) * cpad;
-  float m = 0.f;
-  for (int k = threadIdx.x; k < cpad; k += blockDim.x) m = fmaxf(m, fabsf(Mhi[src + k] + Mlo[src + k]));
+  float m = 0.f, sq = 0.f;
+  for (int k = threadIdx.x; k < cpad; k += blockDim.x) {
+    const float v = Mhi[src + k] + Mlo[src + k];
+    m = fmaxf(m, fabsf(v));
+    sq = fmaf(v, v, sq);
+  }
   const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // non-negative floats order like bits
-  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = wm;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) {
+    s_max[threadIdx.x >> 5] = wm;
+    s_sq[threadIdx.x >> 5] = sq;
+  }
   __syncthreads();
   const float sc = pow2_scale(__uint_as_float(max(max(s_max[0], s_max[1]), max(s_max[2], s_max[3]))));
   if (threadIdx.x == 0) mscale[row] = sc;
+  if (threadIdx.x == 0 && ybound) {
+    // the norm rounded up a little (FP32 sums of 343 squares): a bound, not an estimate
+    const float nrm = sqrtf(s_sq[0] + s_sq[1] + s_sq[2] + s_sq[3]) * 1.001f;
+    atomicMax(ybound + ymax_index(problem_of(lv, l, cell), l), __float_as_uint(nrm));
+  }
   for (int k = 2 * threadIdx.x; k < cpad; k += 2 * blockDim.x) {
     const int64_t G = (int64_t)(k >> 5) * rows + row;
     uint32_t hi, lo;
@@ -227,6 +264,10 @@ __device__ inline ProjRec load_rec(const ProjRec* p) {
 __device__ inline void st_cs_v4(float* p, float a, float b, float c, float d) {
   asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
+__device__ inline void st_cs_u4(uint32_t* p, const uint32_t* v) {
+  asm volatile("st.global.cs.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
 
 // F16: operands are FP16 hi/lo pairs (32 coefficients per 64-byte row, one
 // MMA of K = 16 per half row, at twice the TF32 rate; M scaled per level, VT
@@ -248,6 +289,8 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
   unsigned char* gbase = smem_raw + (base - raw);
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(gbase + (bars - base) + 8u * (2 * MAXST + 6));
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // FP16 form: per epilogue warp, each lane's destinations for the unit's t [q][lane]
+  int32_t* epi_dst = (int32_t*)(gbase + (bars - base) + 256);
   const uint32_t tmem_cols = 2u * SP_ACC;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -293,14 +336,14 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       int off = 0, run = 0;
       bool starts = false;
       if (lane < g.n) {
-        for (int q = 0; q < lane; ++q) off += 16 * g.ry16[q];
-        starts = lane == 0 || g.yo16[lane] != g.yo16[lane - 1] + g.ry16[lane - 1];
+        for (int q = 0; q < lane; ++q) off += 8 * g.ry8[q];
+        starts = lane == 0 || g.yo8[lane] != g.yo8[lane - 1] + g.ry8[lane - 1];
         if (starts) {
           int q = lane;
           do {
-            run += 16 * g.ry16[q];
+            run += 8 * g.ry8[q];
             ++q;
-          } while (q < g.n && g.yo16[q] == g.yo16[q - 1] + g.ry16[q - 1]);
+          } while (q < g.n && g.yo8[q] == g.yo8[q - 1] + g.ry8[q - 1]);
         }
       }
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
@@ -312,12 +355,12 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
         }
         const uint32_t st = base + (uint32_t)s * stage_bytes;
         const uint32_t sb = st + 2u * SP_A_BYTES;
-        if (lane == 0) mbar_expect_tx(full(s), 2u * SP_A_BYTES + (uint32_t)g.cols16 * 16u * 128u);
+        if (lane == 0) mbar_expect_tx(full(s), 2u * SP_A_BYTES + (uint32_t)g.cols8 * 8u * 128u);
         __syncwarp();
         if (lane == SP_MAXG) {
           bulk_g2s(st, a.Mc + ((int64_t)kc * a.mrows + g.arow) * 32, 2u * SP_A_BYTES, full(s));
         } else if (starts) {
-          const int64_t G = ((int64_t)g.cls * a.kchunks + kc) * a.YS + 16 * g.yo16[lane];
+          const int64_t G = ((int64_t)g.cls * a.kchunks + kc) * a.YS + 8 * g.yo8[lane];
           bulk_g2s(sb + (uint32_t)off * 128u, a.VT + G * 32, (uint32_t)run * 128u, full(s));
         }
         last = it + 1;
@@ -338,7 +381,9 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
     uint32_t it = 0, uu = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
-      const int n = a.recs[unit].n, cols = 16 * a.recs[unit].cols16;
+      // N: the group's columns rounded up to the MMA granule of 16 (the rows past
+      // the group's in the stage are stale; their columns are never read)
+      const int n = a.recs[unit].n, cols = (8 * a.recs[unit].cols8 + 15) / 16 * 16;
       if (n == 0) continue;
       const int b = (int)(uu & 1u);
       if (!warp_wait(acc_empty(b), ((uu >> 1) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
@@ -404,6 +449,10 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       if (g.n == 0) continue;
       const bool valid = row < g.count;
       const int64_t cellrow = valid ? (int64_t)g.crow + lv.cls[g.level][g.first + row] : 0;
+      if (F16) {  // the destinations are read while the unit's MMAs run
+        int32_t* sd = epi_dst + qd * (SP_MAXG * 32);
+        for (int q = 0; q < g.n; ++q) sd[q * 32 + lane] = valid ? a.dst[(int64_t)g.kidx[q] * a.drows + cellrow] : -1;
+      }
       const int b = (int)(uu & 1u);
       if (!warp_wait(acc_full(b), (uu >> 1) & 1u, abort_flag, a.wait_ns)) {
         ok = false;
@@ -411,40 +460,58 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       }
       tc_fence_after();
       const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * SP_ACC);
-      // F16: back from the operands' scales (powers of two: exact)
-      const float inv = F16 && valid ? 1.f / (a.mscale[g.arow + row] * a.vscale) : 1.f;
-      float vmax = 0.f;
-      int off = 0;
-      for (int q = 0; q < g.n; ++q) {
-        float* y = a.Y + cellrow * a.YS + 16 * g.yo16[q];
-        for (int c16 = 0; c16 < 16 * g.ry16[q]; c16 += 16) {
+      if (F16) {
+        // y of this row's cell for each t of the group goes to the target's row
+        // of the expansion operand Yx: back from the operand scales, into the
+        // scale of the (problem, level) bound, split into FP16 hi/lo (all
+        // powers of two: exact)
+        const float f = valid ? pow2_scale(__uint_as_float(a.ybound[ymax_index(
+                                    problem_of(lv, g.level, lv.cls[g.level][g.first + row]), g.level)])) /
+                                    (a.mscale[g.arow + row] * a.vscale)
+                              : 0.f;
+        const int32_t* sd = epi_dst + qd * (SP_MAXG * 32);
+        __syncwarp();
+        int q = 0, j = 0;
+        const int nb16 = (g.cols8 + 1) >> 1;
+        for (int b16 = 0; b16 < nb16; ++b16) {
           float v[16];
-          tmem_ld16(tb + (uint32_t)(off + c16), v);
-          if (F16) {
+          tmem_ld16(tb + (uint32_t)(16 * b16), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              v[i] *= inv;
-              vmax = fmaxf(vmax, fabsf(v[i]));
+          for (int hh = 0; hh < 2; ++hh) {
+            if (q < g.n) {
+              const int d = sd[q * 32 + lane];
+              if (d >= 0) {
+                const int a8 = g.kap8[q] + j;
+                const int64_t G = (((int64_t)(d >> 7) * a.kct + (a8 >> 2)) << 7) + (d & 127);
+                uint32_t h4[4], l4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split_h2(v[8 * hh + 2 * i] * f, v[8 * hh + 2 * i + 1] * f, h4[i], l4[i]);
+                st_cs_u4(a.Yx + il_idx(G, 0, 4 * (a8 & 3)), h4);
+                st_cs_u4(a.Yx + il_idx(G, 1, 4 * (a8 & 3)), l4);
+              }
+              if (++j == g.ry8[q]) {
+                ++q;
+                j = 0;
+              }
             }
           }
-          if (valid) {
-            st_cs_v4(y + c16, v[0], v[1], v[2], v[3]);
-            st_cs_v4(y + c16 + 4, v[4], v[5], v[6], v[7]);
-            st_cs_v4(y + c16 + 8, v[8], v[9], v[10], v[11]);
-            st_cs_v4(y + c16 + 12, v[12], v[13], v[14], v[15]);
-          }
         }
-        off += 16 * g.ry16[q];
-      }
-      if (F16) {  // largest |Y| per (problem, level); non-negative floats order like their bits
-        const int prob = valid ? problem_of(lv, g.level, lv.cls[g.level][g.first + row]) : -2;
-        const uint32_t mine = valid ? __float_as_uint(vmax) : 0u;
-        const int p0 = __shfl_sync(0xffffffffu, prob, 0);
-        if (__all_sync(0xffffffffu, prob == p0 || prob == -2)) {
-          const uint32_t m = __reduce_max_sync(0xffffffffu, mine);
-          if (lane == 0 && m && p0 != -2) atomicMax(a.ymax + ymax_index(p0, g.level), m);
-        } else if (valid && mine) {
-          atomicMax(a.ymax + ymax_index(prob, g.level), mine);
+        __syncwarp();
+      } else {
+        int off = 0;
+        for (int q = 0; q < g.n; ++q) {
+          float* y = a.Y + cellrow * a.YS + 8 * g.yo8[q];
+          for (int c16 = 0; c16 < 8 * g.ry8[q]; c16 += 16) {
+            float v[16];
+            tmem_ld16(tb + (uint32_t)(off + c16), v);
+            if (valid) {
+              st_cs_v4(y + c16, v[0], v[1], v[2], v[3]);
+              st_cs_v4(y + c16 + 4, v[4], v[5], v[6], v[7]);
+              st_cs_v4(y + c16 + 8, v[8], v[9], v[10], v[11]);
+              st_cs_v4(y + c16 + 12, v[12], v[13], v[14], v[15]);
+            }
+          }
+          off += 8 * g.ry8[q];
         }
       }
       tc_fence_before();
@@ -529,6 +596,289 @@ k_svd_exp_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile
     yidx[((int64_t)tile * FMM_NT_CLASS + ai) * FMM_TILE + r] =
         src == zero ? -1 : (rbase + src) * YS + yoff[(lv.key[l][src] & 7) * FMM_NT + slot];
   }
+}
+
+// FP16 form, per evaluation: for every (target tile, transfer vector of the
+// tile's class, row) either the destination of the source's projection --
+// dst[the source class's list index of t][the source's expansion row] =
+// tile * 128 + row -- or, where the target has no source for t, zeros in the
+// target's Yx row over t's ranks; the tail of each Yx row past the class's
+// concatenated ranks is zeroed too (the factor bank is zero there, and the
+// products must be finite).  Rows past the tile's count are left alone:
+// their outputs are never read.  One block per (tile, chunk of EXS_CHUNK
+// transfer vectors), one thread per row.
+__global__ void __launch_bounds__(FMM_TILE)
+k_svd_scatter_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_src, LevelPtrs lv,
+                    const int16_t* __restrict__ cls_t, const int32_t* __restrict__ t_ry,
+                    const int16_t* __restrict__ kap8, const int16_t* __restrict__ srcidx, int kct, int64_t drows,
+                    int32_t* __restrict__ dst, uint32_t* __restrict__ Yx) {
+  const int tile = blockIdx.x, r = threadIdx.x;
+  const Tile tl = tiles[tile];
+  if (r >= tl.count) return;
+  const int l = tl.level, zero = lv.ncell[l];
+  const int64_t rbase = lv.row_off[l];
+  const uint32_t z[4] = {0u, 0u, 0u, 0u};
+  const int k_end = min(FMM_NT_CLASS, (int)(blockIdx.y + 1) * EXS_CHUNK);
+  for (int k = blockIdx.y * EXS_CHUNK; k < k_end; ++k) {
+    const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
+    const int src = tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
+    if (src != zero) {
+      const int cs = lv.key[l][src] & 7;
+      dst[(int64_t)srcidx[cs * FMM_NT + slot] * drows + rbase + src] = tile * FMM_TILE + r;
+    } else {
+      const int k8 = kap8[tl.cls * FMM_NT + slot], n8 = t_ry[slot] / 8;
+      for (int j = 0; j < n8; ++j) {
+        const int a8 = k8 + j;
+        const int64_t G = (((int64_t)tile * kct + (a8 >> 2)) << 7) + r;
+        *(uint4*)(Yx + il_idx(G, 0, 4 * (a8 & 3))) = *(const uint4*)z;
+        *(uint4*)(Yx + il_idx(G, 1, 4 * (a8 & 3))) = *(const uint4*)z;
+      }
+    }
+  }
+  if (blockIdx.y == 0) {
+    // the tail past the class's ranks (kap8 of the class's last t + its ranks)
+    const int last = cls_t[tl.cls * FMM_NT_CLASS + FMM_NT_CLASS - 1];
+    for (int a8 = kap8[tl.cls * FMM_NT + last] + t_ry[last] / 8; a8 < 4 * kct; ++a8) {
+      const int64_t G = (((int64_t)tile * kct + (a8 >> 2)) << 7) + r;
+      *(uint4*)(Yx + il_idx(G, 0, 4 * (a8 & 3))) = *(const uint4*)z;
+      *(uint4*)(Yx + il_idx(G, 1, 4 * (a8 & 3))) = *(const uint4*)z;
+    }
+  }
+}
+
+// ---- expansion, FP16 form ---------------------------------------------------
+// L_T += U y over all of a target's sources at once: A = the tile's Yx rows
+// (written by the projection, K = the target class's transfer vectors with
+// their ranks concatenated), B = the class's factor bank Uc along the same K
+// (one column half); both arrive by one linear bulk copy per 32-value chunk,
+// so no role gathers or converts anything.  Work unit = (K group, tile,
+// column half).  The tensor cores' FP32 accumulation does not round to
+// nearest: an accumulator takes `chain` chunks (about order^3 values of K,
+// the chain of one full-rank operator) before the epilogue adds it into FP32
+// running sums in shared memory; the two accumulators alternate.
+constexpr int X_PROD = 0, X_MMA = 1, X_EPI = 2;
+constexpr int X_THREADS = 32 * (X_EPI + 4);
+constexpr int X_A_BYTES = FMM_TILE * 128;  // 128 rows x (32 FP16 hi + 32 FP16 lo)
+
+struct Exp16Args {
+  const uint32_t* Yx;    // [tile][kct][128 rows] interleaved FP16 hi/lo rows (il_idx)
+  const uint32_t* Uc;    // [class][kct][cpad rows] interleaved FP16 hi/lo rows
+  float* partial;        // [group][tile][128][cpad]
+  int32_t* err;
+  const Tile* tiles;
+  const uint32_t* ybound;  // the rows' scales (the projection's)
+  int ntiles, kct, ngroups, cpg, nh, nhalf, cpad, nst, chain;
+  float uscale;
+  uint64_t wait_ns;
+};
+
+__device__ inline void x_unit(const Exp16Args& a, int u, int& g, int& tile, int& h, int& k0, int& k1) {
+  const int per_g = a.ntiles * a.nh;
+  g = u / per_g;
+  const int rem = u - g * per_g;
+  tile = rem / a.nh;
+  h = rem - tile * a.nh;
+  k0 = g * a.cpg;
+  k1 = min(a.kct, k0 + a.cpg);
+}
+
+__global__ void __launch_bounds__(X_THREADS, 1)
+k_svd_expand16_tc(Exp16Args a, LevelPtrs lv) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t b_bytes = (uint32_t)a.nhalf * 128u;
+  const uint32_t stage_bytes = X_A_BYTES + b_bytes;
+  const uint32_t sum_off = (uint32_t)a.nst * stage_bytes;
+  const uint32_t bars = base + sum_off + (uint32_t)a.nhalf * FMM_TILE * 4u;
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (MAXST + s); };
+  auto acc_full = [&](int b) { return bars + 8u * (2 * MAXST + b); };
+  auto acc_empty = [&](int b) { return bars + 8u * (2 * MAXST + 2 + b); };
+  const uint32_t mma_done = bars + 8u * (2 * MAXST + 4);
+  unsigned char* gbase = smem_raw + (base - raw);
+  float* S = (float*)(gbase + sum_off);
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(gbase + (bars - base) + 8u * (2 * MAXST + 6));
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  uint32_t tmem_cols = 32;
+  while ((int)tmem_cols < 2 * a.nhalf) tmem_cols <<= 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      mbar_init(full(s), 1);  // the producer's expect_tx
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 128);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == X_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nunits = a.ngroups * a.ntiles * a.nh;
+
+  if (warp == X_PROD) {
+    // ---------------------------------------------------------- copy producer
+    uint32_t it = 0, last = 0;
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, tile, h, k0, k1;
+      x_unit(a, unit, g, tile, h, k0, k1);
+      const int cls = a.tiles[tile].cls;
+      for (int kc = k0; kc < k1; ++kc, ++it) {
+        const int s = (int)(it % a.nst);
+        const uint32_t ph = (it / a.nst) & 1u;
+        if (!warp_wait(empty(s), ph ^ 1u, abort_flag, a.wait_ns)) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          const uint32_t st = base + (uint32_t)s * stage_bytes;
+          mbar_expect_tx(full(s), X_A_BYTES + b_bytes);
+          bulk_g2s(st, a.Yx + (((int64_t)tile * a.kct + kc) << 7) * 32, X_A_BYTES, full(s));
+          bulk_g2s(st + X_A_BYTES, a.Uc + (((int64_t)cls * a.kct + kc) * a.cpad + (int64_t)h * a.nhalf) * 32,
+                   b_bytes, full(s));
+        }
+        __syncwarp();
+        last = it + 1;
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+      // let the copies already issued land before the CTA leaves (bounded)
+      for (uint32_t j = last > (uint32_t)a.nst ? last - a.nst : 0; j < last; ++j)
+        mbar_wait(full((int)(j % a.nst)), (j / a.nst) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == X_MMA) {
+    // ---------------------------------------------------------- MMA issuer
+    uint32_t it = 0, tt = 0;
+    bool ok = true;
+    const uint32_t idesc = idesc_f16(FMM_TILE, a.nhalf);
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, tile, h, k0, k1;
+      x_unit(a, unit, g, tile, h, k0, k1);
+      for (int kc0 = k0; kc0 < k1 && ok; kc0 += a.chain, ++tt) {
+        const int kc1 = min(k1, kc0 + a.chain);
+        const int b = (int)(tt & 1u);
+        if (!warp_wait(acc_empty(b), ((tt >> 1) & 1u) ^ 1u, abort_flag, a.wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * a.nhalf);
+        for (int kc = kc0; kc < kc1; ++kc, ++it) {
+          const int s = (int)(it % a.nst);
+          const uint32_t ph = (it / a.nst) & 1u;
+          if (!warp_wait(full(s), ph, abort_flag, a.wait_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t st = base + (uint32_t)s * stage_bytes;
+            const uint32_t sb = st + X_A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t ahi = sdesc_sw64s(st + ks * 32u, 1024), alo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
+              const uint64_t bhi = sdesc_sw64s(sb + ks * 32u, 1024), blo = sdesc_sw64s(sb + 512u + ks * 32u, 1024);
+              mma_f16(d, ahi, bhi, idesc, (kc > kc0 || ks > 0) ? 1u : 0u);
+              mma_f16(d, ahi, blo, idesc, 1u);
+              mma_f16(d, alo, bhi, idesc, 1u);
+            }
+            mma_commit(empty(s));
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit(acc_full(b));
+        __syncwarp();
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+    }
+    // every MMA issued so far has finished before TMEM is freed (bounded)
+    if (lane == 0) {
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------- epilogue
+    // TMEM lane quarter = warp % 4; row = the target's position in the tile
+    const int q = warp & 3, row = q * 32 + lane;
+    uint32_t tt = 0;
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
+      int g, tile, h, k0, k1;
+      x_unit(a, unit, g, tile, h, k0, k1);
+      for (int kc0 = k0; kc0 < k1; kc0 += a.chain, ++tt) {
+        const int b = (int)(tt & 1u);
+        if (!warp_wait(acc_full(b), (tt >> 1) & 1u, abort_flag, a.wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * a.nhalf);
+        const bool first = kc0 == k0;
+        int cb = 0;
+        for (; cb + 32 <= a.nhalf; cb += 32) {
+          float v[32];
+          tmem_ld32(tbase + (uint32_t)cb, v);
+          float* sp = S + cb * FMM_TILE + row;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) sp[i * FMM_TILE] = first ? v[i] : sp[i * FMM_TILE] + v[i];
+        }
+        if (cb < a.nhalf) {  // nhalf is a multiple of 16
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)cb, v);
+          float* sp = S + cb * FMM_TILE + row;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sp[i * FMM_TILE] = first ? v[i] : sp[i * FMM_TILE] + v[i];
+        }
+        tc_fence_before();
+        mbar_arrive(acc_empty(b));
+      }
+      if (!ok) break;
+      const Tile tl = a.tiles[tile];
+      if (k0 < k1 && row < tl.count) {
+        float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
+        // back from the operands' scales (powers of two: exact)
+        const int prob = problem_of(lv, tl.level, lv.cls[tl.level][tl.first + row]);
+        const float inv =
+            1.f / (pow2_scale(__uint_as_float(a.ybound[ymax_index(prob, tl.level)])) * a.uscale);
+        for (int c = 0; c < a.nhalf; c += 4)
+          *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row] * inv, S[(c + 1) * FMM_TILE + row] * inv,
+                                            S[(c + 2) * FMM_TILE + row] * inv, S[(c + 3) * FMM_TILE + row] * inv);
+      }
+    }
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(a.err, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == X_MMA)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 // Unit u -> (group g, tile, column half h), the halves of a tile adjacent so
@@ -829,11 +1179,15 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
-// groups per tile at most: every group but the last holds more than SP_ACC - Rp columns
-int sp_ngroups(int Rp) { return (FMM_NT_CLASS * Rp + (SP_ACC - Rp)) / (SP_ACC - Rp + 1) + 1; }
+// groups per tile at most: every group but the last holds SP_MAXG transfer
+// vectors or more than SP_ACC - Rp columns
+int sp_ngroups(int Rp) {
+  return std::min(FMM_NT_CLASS, (FMM_NT_CLASS * Rp + (SP_ACC - Rp)) / (SP_ACC - Rp + 1) +
+                                    (FMM_NT_CLASS + SP_MAXG - 1) / SP_MAXG + 1);
+}
 int sp_stage_bytes() { return 2 * SP_A_BYTES + 2 * SP_B_BYTES; }
-int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256) / sp_stage_bytes()); }
-int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256; }
+int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256 - 4 * SP_MAXG * 32 * 4) / sp_stage_bytes()); }
+int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256 + 4 * SP_MAXG * 32 * 4; }
 // Columns per half: cp, or cp / 2 when one accumulator of cp columns is
 // wider than an MMA or the two accumulators would leave TMEM room for fewer A
 // stages than there are producer sets (parity waits need every set to run at
@@ -841,6 +1195,25 @@ int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256; }
 int ex_nhalf(int cp) { return (cp > 256 || 2 * cp + 32 * EX_SETS > 512) ? cp / 2 : cp; }
 int ex_stage_bytes(int cp) { return 2 * ex_nhalf(cp) * KC * 4; }
 int ex_smem(int cp, int nst) { return nst * ex_stage_bytes(cp) + ex_nhalf(cp) * FMM_TILE * 4 + 1024 + 256; }
+
+// FP16 expansion: stages of one Yx slab and one factor slab, the running sums
+int x_stage_bytes(int cp) { return X_A_BYTES + ex_nhalf(cp) * 128; }
+int x_fixed_bytes(int cp) { return ex_nhalf(cp) * FMM_TILE * 4 + 1024 + 256; }
+int x_nst(int cp) { return std::min(MAXST, (227 * 1024 - x_fixed_bytes(cp)) / x_stage_bytes(cp)); }
+// chunks of 32 K per accumulator: a chain of about order^3 products
+int x_chain(const Ctx* c) { return std::max(1, (c->ncoef + 31) / 32); }
+// K groups per tile: about 12 units per SM over all tiles and column halves,
+// each group a whole number of chains, no group empty
+void x_groups(const Ctx* c, int* ngroups, int* cpg) {
+  const int kct = c->svd_kct, chain = x_chain(c), nh = c->cpad / ex_nhalf(c->cpad);
+  const int sms = c->num_sms > 0 ? c->num_sms : 148;
+  int ng = (int)std::lround(12.0 * sms / std::max(1, c->ntiles * nh));
+  const int chains = (kct + chain - 1) / chain;
+  ng = std::max(1, std::min(ng, std::min(chains, 8)));
+  int per = (chains + ng - 1) / ng * chain;  // chunks per group
+  *cpg = per;
+  *ngroups = (kct + per - 1) / per;
+}
 
 }  // namespace
 
@@ -856,7 +1229,11 @@ bool m2l_svd_tc_supported(const Ctx* c) {
 fmm_status m2l_svd_tc_prepare(Ctx* c) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp, nhalf = ex_nhalf(cp);
-  const int64_t need = (int64_t)c->ntiles * EX_GROUPS * FMM_TILE * cp;
+  const bool f16 = m2l_uses_f16(c);
+  if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+  int xng = EX_GROUPS, xcpg = 0;
+  if (f16) x_groups(c, &xng, &xcpg);
+  const int64_t need = (int64_t)c->ntiles * xng * FMM_TILE * cp;
   if (need > c->tc_partial_cap) {
     dfree(c, c->tc_partial, 4 * (size_t)c->tc_partial_cap);
     c->tc_partial = nullptr;
@@ -883,8 +1260,33 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     c->svd_recs = p;
     c->svd_gcap = gneed;
   }
+  if (f16) {
+    // the expansion operand Yx and the projection's destination map
+    const size_t yx = (size_t)c->ntiles * c->svd_kct * FMM_TILE * 128;
+    if (yx > c->svd_Yx_cap) {
+      dfree(c, c->svd_Yx, c->svd_Yx_cap);
+      c->svd_Yx = nullptr;
+      c->svd_Yx_cap = 0;
+      const size_t cap = yx + yx / 8;
+      void* p;
+      FMM_TRY(dalloc(c, &p, cap));
+      c->svd_Yx = p;
+      c->svd_Yx_cap = cap;
+    }
+    const size_t db = sizeof(int32_t) * FMM_NT_CLASS * (size_t)c->rows;
+    if (db > c->svd_dst_cap) {
+      dfree(c, c->svd_dst, c->svd_dst_cap);
+      c->svd_dst = nullptr;
+      c->svd_dst_cap = 0;
+      const size_t cap = db + db / 8;
+      void* p;
+      FMM_TRY(dalloc(c, &p, cap));
+      c->svd_dst = (int32_t*)p;
+      c->svd_dst_cap = cap;
+    }
+  }
   // class-ordered copy of the multipoles (rows as M) and its tensor maps
-  if (c->ntiles > c->svd_ecap) {
+  if (!f16 && c->ntiles > c->svd_ecap) {
     dfree(c, c->svd_eslot, sizeof(int16_t) * (size_t)c->svd_ecap * FMM_NT_CLASS);
     dfree(c, c->svd_ekch, sizeof(int8_t) * (size_t)c->svd_ecap * FMM_NT_CLASS);
     dfree(c, c->svd_yidx, sizeof(int64_t) * (size_t)c->svd_ecap * FMM_NT_CLASS * FMM_TILE);
@@ -935,7 +1337,8 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
   c->svd_tc_nst = nst;
   if (m2l_uses_f16(c)) {
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<true>, sp_smem(nst_p)));
-    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<true>, ex_smem(cp, nst)));
+    if (x_nst(cp) < 2) return set_err(c, FMM_ERR_ARG, "compressed M2L tensor path: fewer than two expansion stages");
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand16_tc, x_nst(cp) * x_stage_bytes(cp) + x_fixed_bytes(cp)));
     if (!c->svd_umax) {  // max |Y| per (problem + 1, level): every batch size
       void* p;
       FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * (FMM_MAX_BATCH + 1) * FMM_MAX_LEVELS));
@@ -945,7 +1348,6 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<false>, sp_smem(nst_p)));
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<false>, ex_smem(cp, nst)));
   }
-  if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
   return FMM_OK;
 }
 
@@ -958,7 +1360,6 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   const int cp = c->cpad, Rp = c->svd_rp;
   const bool f16 = m2l_uses_f16(c);
   if (f16 != c->svd_bank_f16) return set_err(c, FMM_ERR_STATE, "internal: compressed M2L banks in the other format");
-  uint32_t* ymax = f16 ? c->svd_umax : nullptr;
   // multipoles in class order, every level with far field
   const int64_t mrows = c->svd_mcls_rows;
   McBase mb;
@@ -968,13 +1369,13 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
       mb.clsoff[l][k] = c->cls_off[l][k];
     }
   if (f16) {
-    // the projection's epilogue records the max |Y| per (problem, level) afresh
+    // the bound ||M||_2 per (problem, level), recorded afresh by the gather
     const int nslots = (c->forest ? c->nprob : 1) + 1;
     FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * nslots * FMM_MAX_LEVELS, s));
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
         k_gather_cls16<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo,
-                                                       (uint32_t*)c->svd_Mcls, c->svd_mscale);
+                                                       (uint32_t*)c->svd_Mcls, c->svd_mscale, c->svd_umax);
   } else {
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
@@ -982,6 +1383,11 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   }
   ProjArgs p;
   p.Y = (float*)c->svd_Y;
+  p.Yx = (uint32_t*)c->svd_Yx;
+  p.dst = c->svd_dst;
+  p.drows = c->rows;
+  p.kct = c->svd_kct;
+  p.ybound = c->svd_umax;
   p.err = c->tc_err;
   p.YS = c->svd_YS;
   p.ntiles = c->ntiles;
@@ -993,12 +1399,19 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.VT = c->svd_VThi;
   p.nst = sp_nst();
   p.mscale = c->svd_mscale;
-  p.ymax = ymax;
+  p.ymax = nullptr;
   p.vscale = c->svd_vscale;
   p.wait_ns = c->wait_ns;
-  k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act,
-                                                       c->src_nact, c->src_t, c->svd_ry, c->svd_yoff,
-                                                       (ProjRec*)c->svd_recs, c->tc_err);
+  k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act, c->src_nact, c->src_t,
+                                         c->svd_ry, c->svd_yoff, c->tvec, f16 ? c->svd_kap8 : nullptr,
+                                         (ProjRec*)c->svd_recs, c->tc_err);
+  if (f16) {
+    // destinations of the projections (and zeros where a target has no source)
+    FMM_CUDA(c, cudaMemsetAsync(c->svd_dst, 0xFF, sizeof(int32_t) * FMM_NT_CLASS * (size_t)c->rows, s));
+    k_svd_scatter_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(
+        c->tiles, c->tile_src, c->lv, c->cls_t, c->svd_ry, c->svd_kap8, c->svd_srcidx, c->svd_kct, c->rows,
+        c->svd_dst, (uint32_t*)c->svd_Yx);
+  }
   const int up = p.ntiles * p.ngroups;
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[9], s, cudaEventRecordExternal));
   if (f16)
@@ -1007,6 +1420,40 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     k_svd_proj_tc<false><<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[10], s, cudaEventRecordExternal));
+  if (f16) {
+    Exp16Args e;
+    e.Yx = (const uint32_t*)c->svd_Yx;
+    e.Uc = c->svd_Uc;
+    e.partial = c->tc_partial;
+    e.err = c->tc_err;
+    e.tiles = c->tiles;
+    e.ybound = c->svd_umax;
+    e.ntiles = c->ntiles;
+    e.kct = c->svd_kct;
+    x_groups(c, &e.ngroups, &e.cpg);
+    e.nhalf = ex_nhalf(cp);
+    e.nh = cp / e.nhalf;
+    e.cpad = cp;
+    e.nst = x_nst(cp);
+    e.chain = x_chain(c);
+    e.uscale = c->svd_uscale;
+    e.wait_ns = c->wait_ns;
+    if ((int64_t)e.ngroups * c->ntiles * FMM_TILE * cp > c->tc_partial_cap)
+      return set_err(c, FMM_ERR_STATE, "internal: M2L partial sums smaller than the expansion's groups");
+    c->svd_x_groups = e.ngroups;
+    const int ue = e.ngroups * c->ntiles * e.nh;
+    if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
+    if (c->timing != 2 && c->p2p_priority) {
+      FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
+      c->p2p_after_proj = true;
+    }
+    k_svd_expand16_tc<<<std::min(ue, c->num_sms), X_THREADS, e.nst * x_stage_bytes(cp) + x_fixed_bytes(cp), s>>>(
+        e, c->lv);
+    FMM_CUDA(c, cudaGetLastError());
+    if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
+    if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
+    return launch_m2l_tc_reduce(c, s, c->tc_partial, -e.ngroups);
+  }
   k_svd_exp_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->lv, c->cls_t,
                                                  c->svd_ry, c->svd_yoff, c->svd_YS, c->svd_eslot, c->svd_ekch,
                                                  c->svd_yidx);
@@ -1027,7 +1474,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.nst = c->svd_tc_nst;
   e.tpa = std::max(4, std::min(16, c->ncoef / std::max(16, Rp)));
   e.acol = (uint32_t)(2 * e.nhalf);
-  e.ymax = ymax;
+  e.ymax = nullptr;
   e.tiles = c->tiles;
   e.uscale = c->svd_uscale;
   e.wait_ns = c->wait_ns;
@@ -1042,10 +1489,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
     c->p2p_after_proj = true;
   }
-  if (f16)
-    k_svd_expand_tc<true><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
-  else
-    k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
+  k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));

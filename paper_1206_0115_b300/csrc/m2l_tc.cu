@@ -389,7 +389,9 @@ k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile
   const Tile tl = tiles[tile];
   if (r0 >= tl.count) return;
   const int nrow = min(16, tl.count - r0);
-  const int ng = (tile_nact[tile] + gt - 1) / gt;
+  // gt > 0: slices of gt transfer vectors each (only as many as the tile has);
+  // gt <= 0: -gt slices for every tile
+  const int ng = gt > 0 ? (tile_nact[tile] + gt - 1) / gt : -gt;
   const float inv_a = (float)kernel_scale(ldexp(1.0, tl.level + 1) / box[3], ks);
   const int64_t rbase = lv.row_off[tl.level];
   const int nq = (ncol + 3) / 4;  // float4 columns (cpad is a multiple of 32)

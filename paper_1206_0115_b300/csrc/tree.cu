@@ -1499,6 +1499,12 @@ void release_tree(Ctx* c) {
   dfree(c, c->svd_Y, c->svd_Y_cap);
   c->svd_Y = nullptr;
   c->svd_Y_cap = 0;
+  dfree(c, c->svd_Yx, c->svd_Yx_cap);
+  c->svd_Yx = nullptr;
+  c->svd_Yx_cap = 0;
+  dfree(c, c->svd_dst, c->svd_dst_cap);
+  c->svd_dst = nullptr;
+  c->svd_dst_cap = 0;
   dfree(c, c->svd_recs, 128 * (size_t)c->svd_gcap);
   c->svd_recs = nullptr;
   c->svd_gcap = 0;
