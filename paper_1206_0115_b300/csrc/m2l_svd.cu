@@ -35,8 +35,11 @@
 //                 Y rows are gathered, not the multipoles)
 // The mixed path stores U in the mean-split form of the local expansions
 // (row C = the mean over m of U_t[m][.], rows m < C the deviations), its
-// factors as TF32 hi/lo pairs, and pads every rank to a multiple of 16 with
-// zero factors (the tensor-core granule) -- the result is that of rank r_t.
+// factors as TF32 hi/lo pairs (FP16 hi/lo pairs for the tensor cores' FP16
+// form, whose expansion bank Uc runs along each child class's concatenated
+// ranks), and pads every rank with zero factors to a multiple of 16 (8 in the
+// FP16 form: one 16-byte group of FP16 values) -- the result is that of
+// rank r_t.
 #include <algorithm>
 #include <array>
 #include <cmath>

@@ -1,38 +1,44 @@
 // m2l_svd_tc.cu -- the SVD-compressed M2L (Sec. 2.1.2, "Improved M2L
-// operator"; the factors and the Y layout are those of m2l_svd.cu) on the
-// sm_103a tensor cores, mixed precision, 3xTF32 (hi*hi + hi*lo + lo*hi).
+// operator"; the factors are those of m2l_svd.cu) on the sm_103a tensor
+// cores, mixed precision: three products hi*hi + hi*lo + lo*hi of split
+// operands, FP16 hi/lo pairs (the default, kind::f16) or TF32 hi/lo pairs
+// (FMM_M2L_MATH=tf32, kind::tf32).
 //
 // k_svd_proj_tc -- projection from the sources.  Work unit = (tile of 128
 //   cells of one level and class, group of consecutive active source
-//   transfer vectors whose ranks add up to at most SP_ACC columns).  The A
-//   operand is the tile's multipoles, K = the cpad coefficients, copied from
-//   a class-ordered, pre-swizzled copy of M (k_gather_cls: a tile's slab of
-//   16 coefficients is one contiguous block); B is the group's V_t factors
-//   stacked (VT bank rows, also pre-swizzled); every slab arrives by one
-//   linear bulk copy, so the copy engine is not limited by per-row requests;
-//   so one MMA of N = sum of the ranks computes every product of the group
-//   and each A chunk is loaded once for all of them.  Each t owns a column
-//   range of the TMEM accumulator (two buffers of SP_ACC columns alternate
-//   between units); the epilogue writes the ranges to the cells' Y rows with
-//   streaming stores (Y is read once more, by the expansion).
-// k_svd_expand_tc -- expansion at the targets, the layout of k_m2l_tc
-//   (m2l_tc.cu): work unit = (target tile, half of the output columns, group
-//   of EX_GT active transfer vectors); the A operand is gathered from the
-//   sources' Y rows (ry_t values per t, split into TF32 hi/lo on the way into
-//   tensor memory; an absent source gives zeros), B = U_t (mean-split rows)
-//   by linear bulk copies of pre-swizzled slabs, ry_t / 16 pipeline stages
-//   per t.  The tensor cores' FP32
-//   accumulation does not round to nearest, so an accumulator takes at most
-//   tpa transfer vectors (a chain no longer than that of one full-rank
-//   operator) before the epilogue adds it into FP32 running sums in shared
-//   memory; k_m2l_tc_reduce adds a tile's group slices in FP64 and scales by
-//   1/a.
-// Roles per CTA (one CTA per SM, persistent): producers (the projection: one
-// TMA thread; the expansion: warps in sets of four, one thread per row), four
-// epilogue warps (one per TMEM lane quarter), one MMA warp (one elected
-// thread issues).  Every mbarrier wait is bounded in
-// time; on expiry the CTA raises the error word, drains what it has in
-// flight (bounded), frees TMEM and returns.
+//   transfer vectors whose padded ranks add up to at most SP_ACC columns).
+//   A = the tile's multipoles (K = the cpad coefficients) from a
+//   class-ordered, pre-swizzled copy of M; B = the group's V_t factors
+//   stacked (VT bank rows, pre-swizzled); every slab arrives by one linear
+//   bulk copy, and one MMA of N = the group's columns computes every product
+//   of the group.  Each t owns a column range of the TMEM accumulator (two
+//   buffers of SP_ACC columns alternate between units).  The epilogue:
+//     FP16 form: each y_(S,t) goes straight into the expansion's operand
+//       layout Yx -- the target T = S - t's tile row, at t's place in T's
+//       class's concatenated ranks -- scaled by the power of two of the
+//       (problem, level) bound ||M||_2 and split into FP16 hi/lo; the
+//       destination comes from a map built per evaluation
+//       (k_svd_scatter_setup), which also zeroes the rows of targets
+//       without a source for t;
+//     TF32 form: the cells' FP32 Y rows.
+// k_svd_expand16_tc -- FP16 expansion at the targets: work unit = (K group,
+//   target tile, column half); A = the tile's Yx slab, B = the class's factor
+//   bank Uc along the same concatenated K, one bulk copy each per 32 values
+//   of K.
+// k_svd_expand_tc -- TF32 expansion: work unit = (target tile, column half,
+//   group of EX_GT active transfer vectors); A gathered from the sources' Y
+//   rows and split into TF32 hi/lo on the way into tensor memory, B = U_t.
+// Both expansions: the tensor cores' FP32 accumulation does not round to
+// nearest, so an accumulator takes a chain of about order^3 values of K (the
+// chain of one full-rank operator) before the epilogue adds it into FP32
+// running sums in shared memory; k_m2l_tc_reduce adds a tile's group slices
+// and scales by 1/a.
+// Roles per CTA (one CTA per SM, persistent): producers (one bulk-copy
+// thread; the TF32 expansion: warps in sets of four, one thread per row),
+// four epilogue warps (one per TMEM lane quarter), one MMA warp (one elected
+// thread issues).  Every mbarrier wait is bounded in time (fmm_set_wait_limit);
+// on expiry the CTA raises the error word, drains what it has in flight
+// (bounded), frees TMEM and returns.
 #include "tc_ptx.cuh"
 
 namespace fmm {
@@ -47,8 +53,9 @@ constexpr int MAXST = 4;        // pipeline stages at most
 // ---- projection -------------------------------------------------------------
 constexpr int SP_PROD = 0;                    // TMA producer warp (one thread issues)
 constexpr int SP_MMA = 1;                     // the MMA warp
-constexpr int SP_EPI = 2;                     // first of the four epilogue warps
-constexpr int SP_THREADS = 32 * (SP_EPI + 4);
+constexpr int SP_EPI = 2;                     // first of the eight epilogue warps (two per TMEM lane quarter)
+constexpr int SP_NEPI = 8;
+constexpr int SP_THREADS = 32 * (SP_EPI + SP_NEPI);
 constexpr int SP_ACC = 256;                   // accumulator columns per buffer (two buffers: all of TMEM)
 constexpr int SP_MAXG = SP_ACC / 16;          // transfer vectors per group at most (ranks >= 16)
 constexpr int SP_A_BYTES = FMM_TILE * KC * 4; // one half (hi or lo) of a stage's A: 8 KB
@@ -99,16 +106,14 @@ struct ProjArgs {
   const float *Mc, *VT;  // interleaved hi/lo slabs (il_idx)
   int ntiles, ngroups, kchunks, nst;
   // FP16 operands: each class-ordered multipole row's scale (pow2_scale of
-  // the cell's max |M|), the VT bank's scale, and the max |Y| per (problem,
-  // level) written here for the expansion (ymax_index)
+  // the cell's max |M|) and the VT bank's scale, undone in the epilogue
   const float* mscale;
-  uint32_t* ymax;
   float vscale;
   uint64_t wait_ns;      // limit of a pipeline wait (fmm_set_wait_limit)
 };
 
-// Slot of the max |Y| of (problem, level): problem -1 (cells above a batch's
-// problem slots) first.
+// Slot of a per-(problem, level) value (the FP16 form's bound of |y|):
+// problem -1 (cells above a batch's problem slots) first.
 __host__ __device__ inline int ymax_index(int prob, int level) { return (prob + 1) * FMM_MAX_LEVELS + level; }
 
 // Greedy grouping of each tile's active source transfer vectors into units
@@ -289,11 +294,11 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
   unsigned char* gbase = smem_raw + (base - raw);
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(gbase + (bars - base) + 8u * (2 * MAXST + 6));
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  // FP16 form: per epilogue warp, each lane's destinations for the unit's t [q][lane]
-  int32_t* epi_dst = (int32_t*)(gbase + (bars - base) + 256);
   const uint32_t tmem_cols = 2u * SP_ACC;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // FP16 form: per epilogue warp, each lane's destinations for the unit's t [q][lane]
+  int32_t* epi_dst = (int32_t*)(gbase + (bars - base) + 256) + (warp - SP_EPI) * (SP_MAXG * 32);
   if (threadIdx.x == 0) {
     for (int s = 0; s < MAXST; ++s) {
       mbar_init(full(s), 1);  // the producer's expect_tx
@@ -301,7 +306,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), 128);
+      mbar_init(acc_empty(b), 32 * SP_NEPI);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -440,18 +445,28 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
     __syncwarp();
   } else {
     // ---------------------------------------------------------- epilogue
-    // TMEM lane quarter = warp % 4; row = the cell's position in the tile
-    const int qd = warp & 3, row = qd * 32 + lane;
+    // TMEM lane quarter = warp % 4; row = the cell's position in the tile; the
+    // two warps of a quarter take the group's transfer vectors in turn (half)
+    const int qd = warp & 3, row = qd * 32 + lane, half = (warp - SP_EPI) >> 2;
     uint32_t uu = 0;
     bool ok = true;
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
       const ProjRec g = load_rec(a.recs + unit);
       if (g.n == 0) continue;
       const bool valid = row < g.count;
-      const int64_t cellrow = valid ? (int64_t)g.crow + lv.cls[g.level][g.first + row] : 0;
-      if (F16) {  // the destinations are read while the unit's MMAs run
-        int32_t* sd = epi_dst + qd * (SP_MAXG * 32);
-        for (int q = 0; q < g.n; ++q) sd[q * 32 + lane] = valid ? a.dst[(int64_t)g.kidx[q] * a.drows + cellrow] : -1;
+      const int cell = valid ? lv.cls[g.level][g.first + row] : 0;
+      const int64_t cellrow = (int64_t)g.crow + cell;
+      float f = 0.f;
+      if (F16) {
+        // read while the unit's MMAs run: the destinations of this row's
+        // projections (the target's tile row per t) and the factor that takes
+        // y back from the operand scales into the scale of the (problem,
+        // level) bound (powers of two: exact)
+        for (int q = half; q < g.n; q += 2)
+          epi_dst[q * 32 + lane] = valid ? a.dst[(int64_t)g.kidx[q] * a.drows + cellrow] : -1;
+        if (valid)
+          f = pow2_scale(__uint_as_float(a.ybound[ymax_index(problem_of(lv, g.level, cell), g.level)])) /
+              (a.mscale[g.arow + row] * a.vscale);
       }
       const int b = (int)(uu & 1u);
       if (!warp_wait(acc_full(b), (uu >> 1) & 1u, abort_flag, a.wait_ns)) {
@@ -460,28 +475,25 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
       }
       tc_fence_after();
       const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * SP_ACC);
-      if (F16) {
-        // y of this row's cell for each t of the group goes to the target's row
-        // of the expansion operand Yx: back from the operand scales, into the
-        // scale of the (problem, level) bound, split into FP16 hi/lo (all
-        // powers of two: exact)
-        const float f = valid ? pow2_scale(__uint_as_float(a.ybound[ymax_index(
-                                    problem_of(lv, g.level, lv.cls[g.level][g.first + row]), g.level)])) /
-                                    (a.mscale[g.arow + row] * a.vscale)
-                              : 0.f;
-        const int32_t* sd = epi_dst + qd * (SP_MAXG * 32);
-        __syncwarp();
-        int q = 0, j = 0;
-        const int nb16 = (g.cols8 + 1) >> 1;
-        for (int b16 = 0; b16 < nb16; ++b16) {
-          float v[16];
-          tmem_ld16(tb + (uint32_t)(16 * b16), v);
+      __syncwarp();
+      int off = 0;  // the group's columns before t
+      for (int q = 0; q < g.n; ++q) {
+        const int c0 = off, c1 = off + 8 * g.ry8[q];
+        off = c1;
+        if ((q & 1) != half) continue;
+        if (F16) {
+          // y of t goes to the target's row of the expansion operand Yx, at
+          // t's place in the target class's concatenated ranks, split into
+          // FP16 hi/lo; 8 values (one 16-byte group) at a time
+          const int d = epi_dst[q * 32 + lane];
+          for (int c = c0 & ~15; c < c1; c += 16) {
+            float v[16];
+            tmem_ld16(tb + (uint32_t)c, v);
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            if (q < g.n) {
-              const int d = sd[q * 32 + lane];
-              if (d >= 0) {
-                const int a8 = g.kap8[q] + j;
+            for (int hh = 0; hh < 2; ++hh) {
+              const int col = c + 8 * hh;
+              if (col >= c0 && col < c1 && d >= 0) {
+                const int a8 = g.kap8[q] + ((col - c0) >> 3);
                 const int64_t G = (((int64_t)(d >> 7) * a.kct + (a8 >> 2)) << 7) + (d & 127);
                 uint32_t h4[4], l4[4];
 #pragma unroll
@@ -489,31 +501,24 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
                 st_cs_u4(a.Yx + il_idx(G, 0, 4 * (a8 & 3)), h4);
                 st_cs_u4(a.Yx + il_idx(G, 1, 4 * (a8 & 3)), l4);
               }
-              if (++j == g.ry8[q]) {
-                ++q;
-                j = 0;
-              }
             }
           }
-        }
-        __syncwarp();
-      } else {
-        int off = 0;
-        for (int q = 0; q < g.n; ++q) {
+        } else {
+          // TF32 form: the ranks are multiples of 16, so are the offsets
           float* y = a.Y + cellrow * a.YS + 8 * g.yo8[q];
-          for (int c16 = 0; c16 < 8 * g.ry8[q]; c16 += 16) {
+          for (int c = c0; c < c1; c += 16) {
             float v[16];
-            tmem_ld16(tb + (uint32_t)(off + c16), v);
+            tmem_ld16(tb + (uint32_t)c, v);
             if (valid) {
-              st_cs_v4(y + c16, v[0], v[1], v[2], v[3]);
-              st_cs_v4(y + c16 + 4, v[4], v[5], v[6], v[7]);
-              st_cs_v4(y + c16 + 8, v[8], v[9], v[10], v[11]);
-              st_cs_v4(y + c16 + 12, v[12], v[13], v[14], v[15]);
+              st_cs_v4(y + (c - c0), v[0], v[1], v[2], v[3]);
+              st_cs_v4(y + (c - c0) + 4, v[4], v[5], v[6], v[7]);
+              st_cs_v4(y + (c - c0) + 8, v[8], v[9], v[10], v[11]);
+              st_cs_v4(y + (c - c0) + 12, v[12], v[13], v[14], v[15]);
             }
           }
-          off += 8 * g.ry8[q];
         }
       }
+      __syncwarp();
       tc_fence_before();
       mbar_arrive(acc_empty(b));
       ++uu;
@@ -553,21 +558,8 @@ struct ExpArgs {
   int64_t YS;
   int ntiles, cpad, nh, nhalf, nst, tpa;
   uint32_t acol, tmem_cols;
-  // FP16 operands: the max |Y| per (problem, level) (float bits, ymax_index;
-  // a target row's Y values, all of its own problem, are scaled by
-  // pow2_scale of it) and the U bank's scale, undone per row in the epilogue
-  const uint32_t* ymax;
-  const Tile* tiles;
-  float uscale;
   uint64_t wait_ns;  // limit of a pipeline wait (fmm_set_wait_limit)
 };
-
-// pow2_scale of the max |Y| of the problem of target row r of a tile.
-__device__ inline float row_yscale(const ExpArgs& a, const LevelPtrs& lv, const Tile& tl, int r) {
-  if (r >= tl.count) return 1.f;
-  const int prob = problem_of(lv, tl.level, lv.cls[tl.level][tl.first + r]);
-  return pow2_scale(__uint_as_float(a.ymax[ymax_index(prob, tl.level)]));
-}
 
 constexpr int EXS_CHUNK = 8;  // active transfer vectors per setup block
 
@@ -891,10 +883,7 @@ __device__ inline void exp_unit(const ExpArgs& a, int u, int& g, int& h, int& ti
   h = rem - tile * a.nh;
 }
 
-// F16: operands FP16 hi/lo pairs, 32 ranks per stage (the last stage of a
-// rank = 16 mod 32 holds 16 and issues one MMA of K = 16 instead of two),
-// Y scaled per level and U by uscale, undone in the epilogue.
-template <bool F16>
+// TF32 hi/lo operands (FMM_M2L_MATH=tf32); the FP16 form is k_svd_expand16_tc.
 __global__ void __launch_bounds__(EX_THREADS, 1)
 k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
   extern __shared__ unsigned char smem_raw[];
@@ -944,8 +933,8 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
 
   if (warp < EX_EPI) {
     // ---------------------------------------------------------- producers
-    // thread r loads 16 Y values (F16: 32) of its target's source for the
-    // stage, splits them into hi/lo and writes them into its TMEM lane; one
+    // thread r loads 16 Y values of its target's source for the stage, splits
+    // them into TF32 hi/lo and writes them into its TMEM lane; one
     // thread issues the B slab (U_t rows of this column half x the stage's
     // rank columns).
     const int set = warp >> 2;
@@ -959,14 +948,12 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
       const int a0 = g * EX_GT, a1 = min(nact, a0 + EX_GT);
       if (a0 >= a1) continue;
       const int64_t tb = (int64_t)tile * FMM_NT_CLASS;
-      const float ysc = F16 ? row_yscale(a, lv, a.tiles[tile], r) : 1.f;
       // the next transfer vector's slot, stages and source offset are loaded
       // while the current one is being copied
       int nslot = a.eslot[tb + a0], nkch = a.ekch[tb + a0];
       int64_t nyi = a.yidx[(tb + a0) * FMM_TILE + r];
       for (int ai = a0; ai < a1 && ok; ++ai) {
-        const int slot = nslot, e16 = nkch;
-        const int kch = F16 ? (e16 + 1) >> 1 : e16;
+        const int slot = nslot, kch = nkch;
         const int64_t yi = nyi;
         if (ai + 1 < a1) {
           nslot = a.eslot[tb + ai + 1];
@@ -979,24 +966,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
           for (int kc = kc0; kc < kch; kc += EX_SETS) {
             const uint32_t j = it + (uint32_t)kc;
             uint32_t vh[16], vl[16];
-            if (yr && F16) {
-              // 32 ranks (16 in a half stage: the upper words are zeros, never read)
-              const bool half = (e16 & 1) && kc == kch - 1;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                uint32_t w[8];
-                if (q < 2 || !half) {
-                  ld_v8(yr + kc * 32 + 8 * q, w);
-                } else {
-#pragma unroll
-                  for (int i = 0; i < 8; ++i) w[i] = 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                  split_h2(__uint_as_float(w[2 * i]) * ysc, __uint_as_float(w[2 * i + 1]) * ysc, vh[4 * q + i],
-                           vl[4 * q + i]);
-              }
-            } else if (yr) {
+            if (yr) {
               ld_v8(yr + kc * KC, vh);
               ld_v8(yr + kc * KC + 8, vh + 8);
 #pragma unroll
@@ -1047,7 +1017,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
     // ---------------------------------------------------------- MMA issuer
     uint32_t it = 0, tt = 0;
     bool ok = true;
-    const uint32_t idesc = F16 ? idesc_f16(FMM_TILE, a.nhalf) : idesc_tf32(FMM_TILE, a.nhalf);
+    const uint32_t idesc = idesc_tf32(FMM_TILE, a.nhalf);
     for (int unit = blockIdx.x; unit < nunits && ok; unit += gridDim.x) {
       int g, h, tile;
       exp_unit(a, unit, g, h, tile);
@@ -1070,8 +1040,7 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
         bool first = true;
         for (int ai = ag; ai < ae && ok; ++ai) {
           const int u = ai - a0;
-          const int e16 = __shfl_sync(0xffffffffu, u < 32 ? kA : kB, u & 31);
-          const int kch = F16 ? (e16 + 1) >> 1 : e16;
+          const int kch = __shfl_sync(0xffffffffu, u < 32 ? kA : kB, u & 31);
           for (int kc = 0; kc < kch; ++kc, ++it) {
             const int s = (int)(it % a.nst);
             const uint32_t ph = (it / a.nst) & 1u;
@@ -1083,23 +1052,14 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
             if (lane == 0) {
               const uint32_t st = base + (uint32_t)s * stage_bytes;
               const uint32_t ahi0 = tmem + a.acol + (uint32_t)s * 32u;
-              // F16: a half stage (rank = 16 mod 32, its last stage) holds K = 16
-              const int nks = (F16 && (e16 & 1) && kc == kch - 1) ? 1 : 2;
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
-                if (ks >= nks) break;
                 const uint32_t ahi = ahi0 + ks * 8u, alo = ahi0 + 16u + ks * 8u;
                 const uint64_t bhi = sdesc_sw64s(st + ks * 32u, 1024);
                 const uint64_t blo = sdesc_sw64s(st + 512u + ks * 32u, 1024);
-                if (F16) {
-                  mma_f16_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
-                  mma_f16_ta(d, ahi, blo, idesc, 1u);
-                  mma_f16_ta(d, alo, bhi, idesc, 1u);
-                } else {
-                  mma_tf32_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
-                  mma_tf32_ta(d, ahi, blo, idesc, 1u);
-                  mma_tf32_ta(d, alo, bhi, idesc, 1u);
-                }
+                mma_tf32_ta(d, ahi, bhi, idesc, (first && ks == 0) ? 0u : 1u);
+                mma_tf32_ta(d, ahi, blo, idesc, 1u);
+                mma_tf32_ta(d, alo, bhi, idesc, 1u);
               }
               mma_commit(empty(s));
             }
@@ -1161,11 +1121,10 @@ k_svd_expand_tc(ExpArgs a, LevelPtrs lv) {
       }
       if (!ok) break;
       float* out = a.partial + (((int64_t)g * a.ntiles + tile) * FMM_TILE + row) * a.cpad + h * a.nhalf;
-      // F16: back from the operands' scales (powers of two: exact)
-      const float inv = F16 ? 1.f / (row_yscale(a, lv, a.tiles[tile], row) * a.uscale) : 1.f;
       for (int c = 0; c < a.nhalf; c += 4)
-        *(float4*)(out + c) = make_float4(S[c * FMM_TILE + row] * inv, S[(c + 1) * FMM_TILE + row] * inv,
-                                          S[(c + 2) * FMM_TILE + row] * inv, S[(c + 3) * FMM_TILE + row] * inv);
+        *(float4*)(out + c) =
+            make_float4(S[c * FMM_TILE + row], S[(c + 1) * FMM_TILE + row], S[(c + 2) * FMM_TILE + row],
+                        S[(c + 3) * FMM_TILE + row]);
     }
     if (!ok && lane == 0) {
       *abort_flag = 1;
@@ -1186,8 +1145,8 @@ int sp_ngroups(int Rp) {
                                     (FMM_NT_CLASS + SP_MAXG - 1) / SP_MAXG + 1);
 }
 int sp_stage_bytes() { return 2 * SP_A_BYTES + 2 * SP_B_BYTES; }
-int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256 - 4 * SP_MAXG * 32 * 4) / sp_stage_bytes()); }
-int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256 + 4 * SP_MAXG * 32 * 4; }
+int sp_nst() { return std::min(MAXST, (227 * 1024 - 1024 - 256 - SP_NEPI * SP_MAXG * 32 * 4) / sp_stage_bytes()); }
+int sp_smem(int nst) { return nst * sp_stage_bytes() + 1024 + 256 + SP_NEPI * SP_MAXG * 32 * 4; }
 // Columns per half: cp, or cp / 2 when one accumulator of cp columns is
 // wider than an MMA or the two accumulators would leave TMEM room for fewer A
 // stages than there are producer sets (parity waits need every set to run at
@@ -1346,7 +1305,7 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
     }
   } else {
     FMM_TRY(raise_smem_limit(c, (const void*)k_svd_proj_tc<false>, sp_smem(nst_p)));
-    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc<false>, ex_smem(cp, nst)));
+    FMM_TRY(raise_smem_limit(c, (const void*)k_svd_expand_tc, ex_smem(cp, nst)));
   }
   return FMM_OK;
 }
@@ -1399,7 +1358,6 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.VT = c->svd_VThi;
   p.nst = sp_nst();
   p.mscale = c->svd_mscale;
-  p.ymax = nullptr;
   p.vscale = c->svd_vscale;
   p.wait_ns = c->wait_ns;
   k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act, c->src_nact, c->src_t,
@@ -1474,9 +1432,6 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   e.nst = c->svd_tc_nst;
   e.tpa = std::max(4, std::min(16, c->ncoef / std::max(16, Rp)));
   e.acol = (uint32_t)(2 * e.nhalf);
-  e.ymax = nullptr;
-  e.tiles = c->tiles;
-  e.uscale = c->svd_uscale;
   e.wait_ns = c->wait_ns;
   e.tmem_cols = 32;
   while ((int)e.tmem_cols < 2 * e.nhalf + 32 * e.nst) e.tmem_cols <<= 1;
@@ -1489,7 +1444,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
     c->p2p_after_proj = true;
   }
-  k_svd_expand_tc<false><<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
+  k_svd_expand_tc<<<std::min(ue, c->num_sms), EX_THREADS, ex_smem(cp, e.nst), s>>>(e, c->lv);
   FMM_CUDA(c, cudaGetLastError());
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[12], s, cudaEventRecordExternal));
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
