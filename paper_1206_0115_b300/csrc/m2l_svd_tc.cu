@@ -269,6 +269,13 @@ __device__ inline ProjRec load_rec(const ProjRec* p) {
 __device__ inline void st_cs_v4(float* p, float a, float b, float c, float d) {
   asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
+// 32 / 16 bytes, streaming (the projection's Yx rows are read once, by the
+// expansion); the address must be 32 / 16-byte aligned.
+__device__ inline void st_cs_u8(uint32_t* p, const uint32_t* v) {
+  asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
 __device__ inline void st_cs_u4(uint32_t* p, const uint32_t* v) {
   asm volatile("st.global.cs.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
                : "memory");
@@ -485,21 +492,49 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
           // y of t goes to the target's row of the expansion operand Yx, at
           // t's place in the target class's concatenated ranks, split into
           // FP16 hi/lo; 8 values (one 16-byte group) at a time
+          // Two groups of 8 that fill the same 32-byte sector of a Yx row (an
+          // even and the next odd group of 8 in the row; the 64-byte swizzle
+          // keeps such a pair together) leave in one 32-byte store.
           const int d = epi_dst[q * 32 + lane];
+          const int k8 = g.kap8[q];
           for (int c = c0 & ~15; c < c1; c += 16) {
             float v[16];
             tmem_ld16(tb + (uint32_t)c, v);
+            uint32_t h8[8], l8[8];
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const int col = c + 8 * hh;
-              if (col >= c0 && col < c1 && d >= 0) {
-                const int a8 = g.kap8[q] + ((col - c0) >> 3);
+            for (int i = 0; i < 8; ++i) split_h2(v[2 * i] * f, v[2 * i + 1] * f, h8[i], l8[i]);
+            if (d < 0) continue;
+            // the 16 columns hold groups j0 = (c - c0) / 8 (may be -1) and j0 + 1
+            const int j0 = (c - c0) >> 3;
+            const int a0 = k8 + j0;  // K group of the first half
+            const bool has0 = c >= c0, has1 = c + 8 < c1;
+            if (has0 && has1 && !(a0 & 1)) {
+              // the pair's 16-byte chunks sit at p0 = (a0 & 3) ^ sw and p0 ^ 1 of
+              // the swizzled row: one aligned 32-byte sector, the second group
+              // first when p0 is odd
+              const int64_t G = (((int64_t)(d >> 7) * a.kct + (a0 >> 2)) << 7) + (d & 127);
+              const int sw = (int)((G >> 1) & 3), p0 = (a0 & 3) ^ sw;
+              const int64_t off = 4 * (p0 & ~1) - 4 * sw;  // from il_idx(G, lo, 0)
+              if (p0 & 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const uint32_t th = h8[i], tl = l8[i];
+                  h8[i] = h8[i + 4];
+                  l8[i] = l8[i + 4];
+                  h8[i + 4] = th;
+                  l8[i + 4] = tl;
+                }
+              }
+              st_cs_u8(a.Yx + il_idx(G, 0, 0) + off, h8);
+              st_cs_u8(a.Yx + il_idx(G, 1, 0) + off, l8);
+            } else {
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                if (hh == 0 ? !has0 : !has1) continue;
+                const int a8 = a0 + hh;
                 const int64_t G = (((int64_t)(d >> 7) * a.kct + (a8 >> 2)) << 7) + (d & 127);
-                uint32_t h4[4], l4[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) split_h2(v[8 * hh + 2 * i] * f, v[8 * hh + 2 * i + 1] * f, h4[i], l4[i]);
-                st_cs_u4(a.Yx + il_idx(G, 0, 4 * (a8 & 3)), h4);
-                st_cs_u4(a.Yx + il_idx(G, 1, 4 * (a8 & 3)), l4);
+                st_cs_u4(a.Yx + il_idx(G, 0, 4 * (a8 & 3)), h8 + 4 * hh);
+                st_cs_u4(a.Yx + il_idx(G, 1, 4 * (a8 & 3)), l8 + 4 * hh);
               }
             }
           }
