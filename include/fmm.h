@@ -39,7 +39,7 @@ extern "C" {
 
 typedef struct fmm_ctx* fmm_handle;
 
-#define FMM_P2P_VARIANTS 14 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+#define FMM_P2P_VARIANTS 16 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
 
 typedef enum {
   FMM_OK = 0,
@@ -236,8 +236,11 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * instruction, (warps, chunk) = (4,256), (2,128), (2,256), (4,128), (8,128),
  * (8,256); variants 12, 13: packed, leaf-cooperative (a block of 8 warps
  * takes up to 8 work items of one leaf and stages each chunk of their common
- * sources once), chunks of 512 and 1024 sources.  They give the same sums up
- * to the grouping of FP32 partial sums.
+ * sources once), chunks of 512 and 1024 sources; variants 14, 15: packed,
+ * persistent (blocks of 4 warps, as many as fit on the GPU at once; every
+ * warp takes the next work item from a counter until none is left), (chunk,
+ * unroll) = (128, 4), (256, 2).  They give the same sums up to the grouping
+ * of FP32 partial sums.
  * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
  * FMM_P2P_VARIANTS mean launch times.  With a kernel other than 1/r

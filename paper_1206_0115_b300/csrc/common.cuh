@@ -40,6 +40,7 @@
 #define FMM_NT 316       // transfer vectors
 #define FMM_NT_CLASS 189 // transfer vectors of one child class
 #define FMM_TILE 128     // M2L target rows per tile
+#define CNT_P2P 126      // counters[] slot of the persistent P2P kernels' work counter (zeroed per launch)
 
 namespace fmm {
 

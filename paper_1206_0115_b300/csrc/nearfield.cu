@@ -316,25 +316,19 @@ __device__ __forceinline__ void p2p_pair_chunk(const ulonglong2* sA, const ulong
   p2p_pairs<G, false, U, GEN>(sA, sB, sC, sD, j0, np, TX, TY, TZ, LX, LY, LZ, gk, acc);
 }
 
-// GEN: the kernels of fmm_set_kernel other than 1/r (ks, kc); outputs scaled
-// by w^-s and w^-(s+1).
-template <int W, int CH, int U, bool GEN = false>
-__global__ void __launch_bounds__(W * 32)
-k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
-          int nitems,
-          const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-          float4* __restrict__ out, double ks = 1.0, double kc = 0.0) {
-  constexpr int NP = CH / 2;
-  __shared__ ulonglong2 sA[W][NP];
-  __shared__ ulonglong2 sB[W][NP];
-  __shared__ ulonglong2 sC[W][NP];
-  __shared__ f2_t sD[W][NP];
-  __shared__ int nb_first[W][27];
-  __shared__ int nb_pre[W][28];
-  __shared__ int8_t nb_off[W][27][3];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * W + warp;
-  if (item >= nitems) return;
+// One work item (32 targets of one leaf against its up to 27 near leaves) of
+// the packed-pair near field, by one warp, with the warp's own staging
+// arrays (sA..sD of CH / 2 pairs, the neighbour tables).  GEN: the kernels of
+// fmm_set_kernel other than 1/r (ks, kc); outputs scaled by w^-s and
+// w^-(s+1).
+template <int CH, int U, bool GEN>
+__device__ __forceinline__ void p2p32x2_item(int item, const LevelPtrs& lv, int leaf,
+                                             const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+                                             const float4* __restrict__ pos32, const float4* __restrict__ pos32lo,
+                                             const double* __restrict__ box, float4* __restrict__ out, double ks,
+                                             double kc, ulonglong2* sA, ulonglong2* sB, ulonglong2* sC, f2_t* sD,
+                                             int* nb_first, int* nb_pre, int8_t (*nb_off)[3]) {
+  const int lane = threadIdx.x & 31;
   const int T = leaf_of[item];  // the leaf holding this item
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
   const int tb = (item - items[T]) * 32;
@@ -363,14 +357,15 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     if (lane >= o) incl += v;
   }
   const int total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();  // the previous item's readers are done with the tables
   if (lane < 27) {
-    nb_first[warp][lane] = nf;
-    nb_pre[warp][lane] = incl - ncnt;
-    nb_off[warp][lane][0] = (int8_t)ox;
-    nb_off[warp][lane][1] = (int8_t)oy;
-    nb_off[warp][lane][2] = (int8_t)oz;
+    nb_first[lane] = nf;
+    nb_pre[lane] = incl - ncnt;
+    nb_off[lane][0] = (int8_t)ox;
+    nb_off[lane][1] = (int8_t)oy;
+    nb_off[lane][2] = (int8_t)oz;
   }
-  if (lane == 0) nb_pre[warp][27] = total;
+  if (lane == 0) nb_pre[27] = total;
   __syncwarp();
   const int own = tc;  // sources [0, own) are the target leaf's particles
 
@@ -400,14 +395,14 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     int lo = 0, hi = 26;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (nb_pre[warp][mid] <= s) lo = mid;
+      if (nb_pre[mid] <= s) lo = mid;
       else hi = mid - 1;
     }
-    const int j = nb_first[warp][lo] + (s - nb_pre[warp][lo]);
+    const int j = nb_first[lo] + (s - nb_pre[lo]);
     ph = pos32[j];
-    ph.x += (float)nb_off[warp][lo][0];
-    ph.y += (float)nb_off[warp][lo][1];
-    ph.z += (float)nb_off[warp][lo][2];
+    ph.x += (float)nb_off[lo][0];
+    ph.y += (float)nb_off[lo][1];
+    ph.z += (float)nb_off[lo][2];
     pl = pos32lo[j];
   };
   for (int c0 = 0; c0 < total; c0 += CH) {
@@ -423,27 +418,23 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
         h1 = make_float4(64.f, 64.f, 64.f, 0.f);
         l1 = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      sA[warp][m] = make_ulonglong2(f2pack(h0.x, h1.x), f2pack(h0.y, h1.y));
-      sB[warp][m] = make_ulonglong2(f2pack(h0.z, h1.z), f2pack(h0.w, h1.w));
-      sC[warp][m] = make_ulonglong2(f2pack(l0.x, l1.x), f2pack(l0.y, l1.y));
-      sD[warp][m] = f2pack(l0.z, l1.z);
+      sA[m] = make_ulonglong2(f2pack(h0.x, h1.x), f2pack(h0.y, h1.y));
+      sB[m] = make_ulonglong2(f2pack(h0.z, h1.z), f2pack(h0.w, h1.w));
+      sC[m] = make_ulonglong2(f2pack(l0.x, l1.x), f2pack(l0.y, l1.y));
+      sD[m] = f2pack(l0.z, l1.z);
     }
     __syncwarp();
     PairAcc acc{0ull, 0ull, 0ull, 0ull};
     // pairs [0, jown) may hold the target's own leaf (r = 0 pairs skipped)
     const int kown = min(cn, max(0, own - c0));
     const int jown = (kown + 1) >> 1;
-    const ulonglong2* A = &sA[warp][0];
-    const ulonglong2* B = &sB[warp][0];
-    const ulonglong2* Cc = &sC[warp][0];
-    const f2_t* D = &sD[warp][0];
     switch (g) {
-      case 1: p2p_pair_chunk<1, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
-      case 2: p2p_pair_chunk<2, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
-      case 4: p2p_pair_chunk<4, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
-      case 8: p2p_pair_chunk<8, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
-      case 16: p2p_pair_chunk<16, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
-      default: p2p_pair_chunk<32, U, GEN>(A, B, Cc, D, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 1: p2p_pair_chunk<1, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 2: p2p_pair_chunk<2, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 4: p2p_pair_chunk<4, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 8: p2p_pair_chunk<8, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      case 16: p2p_pair_chunk<16, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
+      default: p2p_pair_chunk<32, U, GEN>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc, gk); break;
     }
     const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
     kp.add(ph.x + ph.y);
@@ -463,6 +454,57 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
     const float s1 = GEN ? (float)pow(iw, ks) : (float)iw;
     const float s2 = GEN ? (float)(pow(iw, ks) * iw) : s1 * s1;
     out[tf + tb + ti] = make_float4(aphi * s1, ax * s2, ay * s2, az * s2);
+  }
+}
+
+// One warp per work item, W warps per block.
+template <int W, int CH, int U, bool GEN = false>
+__global__ void __launch_bounds__(W * 32)
+k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
+          int nitems,
+          const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
+          float4* __restrict__ out, double ks = 1.0, double kc = 0.0) {
+  constexpr int NP = CH / 2;
+  __shared__ ulonglong2 sA[W][NP];
+  __shared__ ulonglong2 sB[W][NP];
+  __shared__ ulonglong2 sC[W][NP];
+  __shared__ f2_t sD[W][NP];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
+  const int warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * W + warp;
+  if (item >= nitems) return;
+  p2p32x2_item<CH, U, GEN>(item, lv, leaf, items, leaf_of, pos32, pos32lo, box, out, ks, kc, sA[warp], sB[warp],
+                           sC[warp], sD[warp], nb_first[warp], nb_pre[warp], nb_off[warp]);
+}
+
+// Persistent warps: every warp takes the next work item from a counter
+// (items in leaf order, so warps running at the same time read neighbouring
+// leaves) until none is left, so no warp slot waits for the slowest warp of
+// its block and no wave of blocks leaves SMs idle at the end.  *counter is
+// zero at launch.
+template <int W, int CH, int U>
+__global__ void __launch_bounds__(W * 32)
+k_p2p32x2p(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of, int nitems,
+           const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
+           float4* __restrict__ out, int32_t* __restrict__ counter) {
+  constexpr int NP = CH / 2;
+  __shared__ ulonglong2 sA[W][NP];
+  __shared__ ulonglong2 sB[W][NP];
+  __shared__ ulonglong2 sC[W][NP];
+  __shared__ f2_t sD[W][NP];
+  __shared__ int nb_first[W][27];
+  __shared__ int nb_pre[W][28];
+  __shared__ int8_t nb_off[W][27][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) return;
+    p2p32x2_item<CH, U, false>(item, lv, leaf, items, leaf_of, pos32, pos32lo, box, out, 1.0, 0.0, sA[warp],
+                               sB[warp], sC[warp], sD[warp], nb_first[warp], nb_pre[warp], nb_off[warp]);
   }
 }
 
@@ -858,7 +900,7 @@ k_p2p64(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, co
 const int kP2PVariants[FMM_P2P_VARIANTS][4] = {{8, 128, 2, 4}, {4, 128, 2, 4}, {4, 256, 2, 2}, {4, 128, 2, 2},
                                                {8, 128, 2, 2}, {8, 256, 2, 2}, {4, 256, 1, 4}, {2, 128, 1, 4},
                                                {2, 256, 1, 4}, {4, 128, 1, 4}, {8, 128, 1, 4}, {8, 256, 1, 4},
-                                               {8, 512, 2, 4}, {8, 1024, 2, 4}};
+                                               {8, 512, 2, 4}, {8, 1024, 2, 4}, {4, 128, 2, 4}, {4, 256, 2, 2}};
 
 // Whether a kernel is one of the P2P kernels (graph nodes of the near field
 // get the low launch priority, see build_graph).
@@ -870,6 +912,7 @@ bool is_p2p_kernel(const void* f) {
                       (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                       (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
                       (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
+                      (const void*)k_p2p32x2p<4, 128, 4>, (const void*)k_p2p32x2p<4, 256, 2>,
                       (const void*)k_p2p32x2<8, 128, 4, true>, (const void*)k_p2p_stokes32<4, 128>,
                       (const void*)k_p2p64};
   for (const void* k : ks)
@@ -889,6 +932,7 @@ void p2p_carveout() {
                         (const void*)k_p2p32x2<4, 256, 2>, (const void*)k_p2p32x2<4, 128, 2>,
                         (const void*)k_p2p32x2<8, 128, 2>, (const void*)k_p2p32x2<8, 256, 2>,
                         (const void*)k_p2p32x2c<512, 4>,   (const void*)k_p2p32x2c<1024, 4>,
+                        (const void*)k_p2p32x2p<4, 128, 4>, (const void*)k_p2p32x2p<4, 256, 2>,
                         (const void*)k_p2p32x2<8, 128, 4, true>};
     for (const void* k : ks) cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaGetLastError();
@@ -937,6 +981,31 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
           k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
                                                                c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
         break;
+      case 14:
+      case 15: {
+        // persistent warps: as many blocks as fit on every SM at once, a zeroed work counter
+        static int occ[2] = {0, 0};
+        int& o = occ[c->p2p_variant - 14];
+        if (o == 0) {
+          if (c->p2p_variant == 14)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 128, 4>, 128, 0);
+          else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 256, 2>, 128, 0);
+          cudaGetLastError();
+          if (o <= 0) o = 4;
+        }
+        if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+        int32_t* ctr = c->counters + CNT_P2P;
+        FMM_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int32_t), s));
+        const int grid = std::min(ceil_div(c->p2p_nitems, 4), o * c->num_sms);
+        if (c->p2p_variant == 14)
+          k_p2p32x2p<4, 128, 4><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems, c->pos32,
+                                                     c->pos32lo, c->box, c->near32, ctr);
+        else
+          k_p2p32x2p<4, 256, 2><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems, c->pos32,
+                                                     c->pos32lo, c->box, c->near32, ctr);
+        break;
+      }
       default: P2P_LAUNCH2(8, 128, 4); break;
     }
 #undef P2P_LAUNCH

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
 FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FMM_FP64, FMM_MIXED = 0, 1
 FMM_M2L_FULL, FMM_M2L_SVD = 0, 1
-FMM_P2P_VARIANTS = 14
+FMM_P2P_VARIANTS = 16
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
                 -5: "FMM_ERR_TIMEOUT"}
 
