@@ -338,6 +338,20 @@ def p2p_roofline(p2p_pairs: int, p2p_ms: float, pk, kernel: str):
             "peak_fp32_tflops": fp["tflops"], "peak_source": "measured in this run (fp32_peak)"}
 
 
+def autotune(fmm, h):
+    """fmm_autotune: the near field's shape per occupancy bin (leaves of at
+    most 64 particles / larger leaves), each bin timed alone in every shape."""
+    choice, ttimes = fmm.fmm_autotune(h)
+    bins, bin_ms = fmm.fmm_get_p2p_bins(h)
+    rep = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
+           "sources_per_instruction": int(choice[3]), "unroll": int(choice[4]),
+           "variant_ms": [round(float(t), 4) for t in ttimes], "bins": {}}
+    for b, name in enumerate(("small_leaves", "large_leaves")):
+        rep["bins"][name] = {"items": int(bins[2 + b]), "variant": int(bins[b]),
+                             "variant_ms": [round(float(t), 4) for t in bin_ms[b]]}
+    return rep
+
+
 def sample_targets(n: int, k: int = ERR_TARGETS, seed: int = 5):
     import numpy as np
     return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
@@ -465,10 +479,7 @@ def measure_single(args, fmm, dev, workload: str, pk, rank: int = 0, main: bool 
     torch.cuda.synchronize()
     tuned = None
     if not args.no_autotune:
-        choice, ttimes = fmm.fmm_autotune(f.h)
-        tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
-                 "sources_per_instruction": int(choice[3]), "unroll": int(choice[4]),
-                 "variant_ms": [round(float(t), 4) for t in ttimes]}
+        tuned = autotune(fmm, f.h)
         step()
         torch.cuda.synchronize()
     work = fmm.fmm_get_work(f.h)
@@ -654,10 +665,7 @@ def measure_batched(args, fmm, dev, pk, rank: int = 0):
     torch.cuda.synchronize()
     tuned = None
     if not args.no_autotune:
-        choice, ttimes = fmm.fmm_autotune(f.h)
-        tuned = {"p2p_variant": int(choice[0]), "warps_per_block": int(choice[1]), "chunk": int(choice[2]),
-                 "sources_per_instruction": int(choice[3]), "unroll": int(choice[4]),
-                 "variant_ms": [round(float(t), 4) for t in ttimes]}
+        tuned = autotune(fmm, f.h)
         step()
         torch.cuda.synchronize()
     work = fmm.fmm_get_work(f.h)

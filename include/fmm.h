@@ -241,9 +241,19 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * warp takes the next work item from a counter until none is left), (chunk,
  * unroll) = (128, 4), (256, 2).  They give the same sums up to the grouping
  * of FP32 partial sums.
- * choice (may be NULL): [0] index, [1] warps per block, [2] sources per
+ * The work items are binned by leaf occupancy -- leaves of at most 64
+ * particles ("small") and larger ones -- and each bin is timed alone in
+ * every shape (the cooperative shapes on large leaves only) and keeps its
+ * fastest; later evaluations run the bins as two launches with their own
+ * shapes (one launch when the shapes agree), unless one launch of a single
+ * shape over every item -- the item shape with the least time over both
+ * bins, timed as one launch -- is faster; fmm_get_p2p_bins reports the
+ * result.
+ * choice (may be NULL): the small leaves' shape (the large leaves' if there
+ * are no small ones): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
- * FMM_P2P_VARIANTS mean launch times.  With a kernel other than 1/r
+ * FMM_P2P_VARIANTS mean times of each shape run over both bins (a
+ * cooperative shape with shape 14 on the small leaves).  With a kernel other than 1/r
  * (fmm_set_kernel) the near field has one shape (8 warps, 128-source chunks,
  * two sources per instruction): choice = {-1, 8, 128, 2, 4} and every time is
  * that shape's.  Synchronises the
@@ -261,8 +271,20 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms);
 fmm_status fmm_set_wait_limit(fmm_handle h, double seconds);
 
 /* Sets the P2P variant directly (0 .. FMM_P2P_VARIANTS-1; 0 is the default),
- * e.g. to reuse a choice fmm_autotune made on another handle. */
+ * e.g. to reuse a choice fmm_autotune made on another handle, for every
+ * leaf (a cooperative shape, 12 or 13, takes the large leaves and shape 14
+ * the small ones). */
 fmm_status fmm_set_p2p_variant(fmm_handle h, int variant);
+
+/* The near field's occupancy bins on the current tree (mixed precision,
+ * 1/r): out[0] = shape of the small leaves' work items (leaves of at most 64
+ * particles), out[1] = shape of the large leaves' items, out[2] / out[3] =
+ * work items (32 targets of one leaf each) in each bin; times_ms (may be
+ * NULL): [2][FMM_P2P_VARIANTS] per-bin times of the last fmm_autotune (-1:
+ * not timed).  The paper has no counterpart; it stands in for the
+ * calibration of Sec. 5 that lets its scheduler pick a worker per task.
+ * out: 4 int64, host.  Errors: FMM_ERR_STATE (no particles loaded). */
+fmm_status fmm_get_p2p_bins(fmm_handle h, int64_t* out, float* times_ms);
 
 /* Releases every device buffer that belongs to the current tree (particles,
  * cells, expansions, M2L work tables and projections, staging) and keeps the

@@ -251,6 +251,8 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
   std::vector<int64_t> s = {c->precision, c->timing, c->ntiles, c->leaf_tiles, c->n, m2l_kind(c), c->tc_nst,
                             c->p2p_nitems, (int64_t)(uintptr_t)c->p2p_items, c->leaf, c->forest,
                             (int64_t)(uintptr_t)c->fb_scale, c->p2p_variant, (int64_t)(uintptr_t)c->p2p_leaf,
+                            c->p2p_big_variant, c->p2p_nsmall, c->p2p_nlarge, (int64_t)(uintptr_t)c->p2p_small,
+                            (int64_t)(uintptr_t)c->p2p_large,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
                             (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p,
                             c->m2l_f16, (int64_t)c->wait_ns};
@@ -395,7 +397,10 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
     return s;
   };
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_bin0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_bin1, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_p2p, cudaEventDisableTiming) != cudaSuccess) {
@@ -455,7 +460,7 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
   void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pleaf, c->pos64, c->pos32, c->pos32lo,
-                  c->p2p_items,
+                  c->p2p_items, c->p2p_bins, c->p2p_small, c->p2p_large,
                   c->p2p_leaf, c->p2p_units, c->p2p_uoff,
                   c->near32,
                   c->near64,
@@ -479,6 +484,12 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->side) cudaStreamSynchronize(c->side);
   cudaGetLastError();
   pinned_release(c->pinned);
+  if (c->side2) {
+    cudaStreamSynchronize(c->side2);
+    cudaStreamDestroy(c->side2);
+  }
+  if (c->ev_bin0) cudaEventDestroy(c->ev_bin0);
+  if (c->ev_bin1) cudaEventDestroy(c->ev_bin1);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -783,8 +794,9 @@ fmm_status fmm_set_p2p_variant(fmm_handle h, int variant) {
   if (!h) return FMM_ERR_ARG;
   if (variant < 0 || variant >= FMM_P2P_VARIANTS)
     return set_err(h, FMM_ERR_ARG, "fmm_set_p2p_variant: %d outside 0..%d", variant, FMM_P2P_VARIANTS - 1);
-  if (variant != h->p2p_variant) {
+  if (variant != h->p2p_variant || h->p2p_big_variant != -1) {
     h->p2p_variant = variant;
+    h->p2p_big_variant = -1;  // one shape for every leaf
     h->graph_ok = false;
   }
   return FMM_OK;
@@ -824,39 +836,106 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
       for (int k = 0; k < FMM_P2P_VARIANTS; ++k) times_ms[k] = ms / 3.f;
     return FMM_OK;
   }
-  const int keep_prec = c->precision, keep_var = c->p2p_variant;
+  // Each occupancy bin (small leaves, large leaves) is timed alone in every
+  // shape (the cooperative shapes only on large leaves) and keeps its fastest.
+  const int keep_prec = c->precision, keep_var = c->p2p_variant, keep_big = c->p2p_big_variant;
   c->precision = FMM_MIXED;  // the variants are shapes of the mixed kernel
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  float best = -1.f;
-  int best_v = keep_var;
   fmm_status st = FMM_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "fmm_autotune: events");
-  for (int v = 0; v < FMM_P2P_VARIANTS && st == FMM_OK; ++v) {
-    c->p2p_variant = v;
-    float ms = 0.f;
-    st = launch_p2p(c, c->stream);  // warm-up
-    if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
-    for (int k = 0; k < 3 && st == FMM_OK; ++k) st = launch_p2p(c, c->stream);
-    if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-      st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
-    ms /= 3.f;
-    if (times_ms) times_ms[v] = ms;
-    if (st == FMM_OK && (best < 0.f || ms < best)) {
-      best = ms;
-      best_v = v;
+  const int nb[2] = {c->p2p_nsmall, c->p2p_nlarge};
+  int best[2] = {keep_var, keep_big};
+  for (int b = 0; b < 2; ++b) {
+    float bt = -1.f;
+    for (int v = 0; v < FMM_P2P_VARIANTS; ++v) {
+      c->p2p_bin_ms[b][v] = -1.f;
+      if (st != FMM_OK || nb[b] == 0 || (b == 0 && (v == 12 || v == 13))) continue;
+      float ms = 0.f;
+      st = launch_p2p_bin(c, c->stream, b, v);  // warm-up
+      if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
+      for (int k = 0; k < 3 && st == FMM_OK; ++k) st = launch_p2p_bin(c, c->stream, b, v);
+      if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
+      ms /= 3.f;
+      c->p2p_bin_ms[b][v] = ms;
+      if (st == FMM_OK && (bt < 0.f || ms < bt)) {
+        bt = ms;
+        best[b] = v;
+      }
+    }
+  }
+  // The bins against one launch over every item: the item shape with the
+  // least time over both bins, timed as one launch; kept if it beats the
+  // bins' two launches (a small bin whose leaves border large ones costs
+  // about as much per item as the large bin, and one launch balances better).
+  int one = -1;
+  float one_ms = -1.f, binned_ms = 0.f;
+  if (st == FMM_OK && nb[0] > 0 && nb[1] > 0) {
+    binned_ms = c->p2p_bin_ms[0][best[0]] + c->p2p_bin_ms[1][best[1]];
+    float est = -1.f;
+    for (int v = 0; v < FMM_P2P_VARIANTS; ++v) {
+      if (v == 12 || v == 13 || c->p2p_bin_ms[0][v] < 0.f || c->p2p_bin_ms[1][v] < 0.f) continue;
+      const float t = c->p2p_bin_ms[0][v] + c->p2p_bin_ms[1][v];
+      if (est < 0.f || t < est) {
+        est = t;
+        one = v;
+      }
+    }
+    if (one >= 0) {
+      c->p2p_variant = one;
+      c->p2p_big_variant = -1;
+      float ms = 0.f;
+      st = launch_p2p(c, c->stream);  // warm-up
+      if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
+      for (int k = 0; k < 3 && st == FMM_OK; ++k) st = launch_p2p(c, c->stream);
+      if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
+      one_ms = ms / 3.f;
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   c->precision = keep_prec;
-  c->p2p_variant = st == FMM_OK ? best_v : keep_var;
+  if (st == FMM_OK && one >= 0 && one_ms < binned_ms) {
+    c->p2p_variant = one;  // one launch over every item
+    c->p2p_big_variant = -1;
+  } else if (st == FMM_OK) {
+    // small leaves' shape (the large leaves' if there are no small ones), the large leaves' own
+    c->p2p_variant = nb[0] > 0 ? best[0] : (nb[1] > 0 && !(best[1] == 12 || best[1] == 13) ? best[1] : keep_var);
+    c->p2p_big_variant = nb[1] > 0 ? best[1] : -1;
+  } else {
+    c->p2p_variant = keep_var;
+    c->p2p_big_variant = keep_big;
+  }
   c->graph_ok = false;
   if (st != FMM_OK) return st;
+  if (times_ms)  // each shape used for every item, as fmm_set_p2p_variant would
+    for (int v = 0; v < FMM_P2P_VARIANTS; ++v) {
+      const float a = nb[0] > 0 ? c->p2p_bin_ms[0][(v == 12 || v == 13) ? 14 : v] : 0.f;
+      const float b = nb[1] > 0 ? c->p2p_bin_ms[1][v] : 0.f;
+      times_ms[v] = a + b;
+    }
   if (choice) {
-    choice[0] = best_v;
-    for (int k = 0; k < 4; ++k) choice[1 + k] = kP2PVariants[best_v][k];
+    choice[0] = c->p2p_variant;
+    for (int k = 0; k < 4; ++k) choice[1 + k] = kP2PVariants[c->p2p_variant][k];
   }
+  return FMM_OK;
+}
+
+fmm_status fmm_get_p2p_bins(fmm_handle h, int64_t* out, float* times_ms) {
+  if (!h || !out) return FMM_ERR_ARG;
+  Ctx* c = h;
+  if (!c->loaded) return set_err(c, FMM_ERR_STATE, "fmm_get_p2p_bins: no particles loaded");
+  const bool coop = c->p2p_variant == 12 || c->p2p_variant == 13;
+  out[0] = coop ? 14 : c->p2p_variant;
+  out[1] = c->p2p_big_variant >= 0 ? c->p2p_big_variant : c->p2p_variant;
+  out[2] = c->p2p_nsmall;
+  out[3] = c->p2p_nlarge;
+  if (times_ms)
+    for (int b = 0; b < 2; ++b)
+      for (int v = 0; v < FMM_P2P_VARIANTS; ++v) times_ms[b * FMM_P2P_VARIANTS + v] = c->p2p_bin_ms[b][v];
   return FMM_OK;
 }
 

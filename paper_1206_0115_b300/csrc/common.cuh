@@ -41,6 +41,9 @@
 #define FMM_NT_CLASS 189 // transfer vectors of one child class
 #define FMM_TILE 128     // M2L target rows per tile
 #define CNT_P2P 126      // counters[] slot of the persistent P2P kernels' work counter (zeroed per launch)
+#define CNT_P2P2 124     // the same for the small leaves' launch when the two bins run side by side
+#define CNT_PUNITS 125   // counters[] slot of the compressed M2L projection's unit count (per evaluation)
+#define P2P_BIG 64       // a leaf with more particles is "large" for the near field's bins
 
 namespace fmm {
 
@@ -108,6 +111,8 @@ struct fmm_ctx {
   int dev = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t side = nullptr;    // P2P branch
+  cudaStream_t side2 = nullptr;   // the small leaves' P2P bin beside the large leaves' one
+  cudaEvent_t ev_bin0 = nullptr, ev_bin1 = nullptr;  // its fork and join
   cudaStream_t cap = nullptr;     // graph capture
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_p2p = nullptr;  // where the P2P branch starts (after the compressed M2L projection)
@@ -135,7 +140,15 @@ struct fmm_ctx {
   int64_t p2p_units_cap = 0;
   int p2p_nunits = 0;
   int p2p_nitems = 0;
-  int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants)
+  // bins by leaf occupancy (P2P_BIG): per leaf its small and large items
+  // (scanned), and the items of each bin
+  unsigned long long* p2p_bins = nullptr;
+  int32_t* p2p_small = nullptr;
+  int32_t* p2p_large = nullptr;
+  int p2p_nsmall = 0, p2p_nlarge = 0;
+  int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants): small leaves (or all)
+  int p2p_big_variant = -1;      // shape for the large leaves' items (-1: p2p_variant)
+  float p2p_bin_ms[2][FMM_P2P_VARIANTS] = {{0.f}};  // the last fmm_autotune's per-bin times
   double4* near64 = nullptr;
   double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
   int64_t stage_in_cap = 0, stage_out_cap = 0;
@@ -350,6 +363,8 @@ fmm_status batch_layout(Ctx* c, int nprob, const int64_t* counts, const int32_t*
 fmm_status operators_init(Ctx* c);
 fmm_status operators_m2l(Ctx* c, int precision);
 fmm_status launch_p2p(Ctx* c, cudaStream_t s);
+// one occupancy bin of the mixed near field (0: leaves of at most P2P_BIG particles, 1: larger) in shape v
+fmm_status launch_p2p_bin(Ctx* c, cudaStream_t s, int bin, int v);
 bool is_p2p_kernel(const void* func);
 void p2p_carveout();
 extern const int kP2PVariants[FMM_P2P_VARIANTS][4];

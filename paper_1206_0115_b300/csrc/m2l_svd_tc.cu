@@ -88,8 +88,9 @@ struct McBase {
 };
 
 struct ProjArgs {
-  const ProjRec* recs;   // [ntiles][ngroups]: unit u = tile * ngroups + group, so that CTAs running
-                         // at the same time share a tile's multipoles in L2
+  const ProjRec* recs;   // the units, compact, a tile's groups one after another (CTAs running at
+                         // the same time share a tile's multipoles in L2)
+  const int32_t* nunits; // their number
   float* Y;              // TF32 form: the sources' Y rows
   // FP16 form: y goes to the expansion's operand layout Yx through the
   // destination map dst[src-list index][expansion row] (tile * 128 + row of
@@ -125,13 +126,13 @@ k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs 
              const int16_t* __restrict__ src_act, const int32_t* __restrict__ src_nact,
              const int16_t* __restrict__ src_t, const int32_t* __restrict__ t_ry,
              const int32_t* __restrict__ yoff, const int8_t* __restrict__ tvec, const int16_t* __restrict__ kap8,
-             ProjRec* __restrict__ recs, int32_t* __restrict__ err) {
+             ProjRec* __restrict__ recs, int32_t* __restrict__ nunits, int32_t* __restrict__ err) {
   __shared__ int16_t s_kap8[FMM_NT_CLASS];
   __shared__ int16_t s_yo8[FMM_NT_CLASS];
   __shared__ uint8_t s_ry8[FMM_NT_CLASS];
   __shared__ uint8_t s_kidx[FMM_NT_CLASS];
   __shared__ int16_t s_gs[FMM_NT_CLASS + 2];
-  __shared__ int s_ng;
+  __shared__ int s_ng, s_base;
   const int tile = blockIdx.x;
   const Tile tl = tiles[tile];
   const int nact = src_nact[tile];
@@ -159,12 +160,15 @@ k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs 
       ++members;
     }
     s_gs[n] = (int16_t)nact;
+    if (n > ngroups) atomicOr(err, 2);  // more groups than the bound (cannot happen by construction)
+    n = min(n, ngroups);
     s_ng = n;
-    if (n > ngroups) atomicOr(err, 2);  // more groups than the bound (cannot happen with ranks >= 16)
+    // the tile's units go to consecutive records of the compact list
+    s_base = n > 0 ? atomicAdd(nunits, n) : 0;
   }
   __syncthreads();
-  const int ng = min(s_ng, ngroups);
-  for (int gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+  const int ng = s_ng;
+  for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
     ProjRec r;
     r.crow = (int32_t)lv.row_off[tl.level];
     r.first = tl.first;
@@ -185,7 +189,7 @@ k_svd_groups(int ntiles, int ngroups, const Tile* __restrict__ tiles, LevelPtrs 
     }
     r.n = (int8_t)n;
     r.cols8 = (uint8_t)(cols / 8);
-    recs[(int64_t)tile * ngroups + gi] = r;
+    recs[s_base + gi] = r;
   }
 }
 
@@ -331,7 +335,7 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int nunits = a.ntiles * a.ngroups;
+  const int nunits = *a.nunits;  // the compact list's length (k_svd_groups)
 
   if (warp == SP_PROD) {
     // ---------------------------------------------------------- copy producer
@@ -1395,9 +1399,12 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.mscale = c->svd_mscale;
   p.vscale = c->svd_vscale;
   p.wait_ns = c->wait_ns;
+  int32_t* nunits = c->counters + CNT_PUNITS;
+  p.nunits = nunits;
+  FMM_CUDA(c, cudaMemsetAsync(nunits, 0, sizeof(int32_t), s));
   k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act, c->src_nact, c->src_t,
                                          c->svd_ry, c->svd_yoff, c->tvec, f16 ? c->svd_kap8 : nullptr,
-                                         (ProjRec*)c->svd_recs, c->tc_err);
+                                         (ProjRec*)c->svd_recs, nunits, c->tc_err);
   if (f16) {
     // destinations of the projections (and zeros where a target has no source)
     FMM_CUDA(c, cudaMemsetAsync(c->svd_dst, 0xFF, sizeof(int32_t) * FMM_NT_CLASS * (size_t)c->rows, s));

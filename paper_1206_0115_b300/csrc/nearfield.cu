@@ -92,15 +92,16 @@ __global__ void __launch_bounds__(W * 32)
 k_p2p32(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
         int nitems,
         const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-        float4* __restrict__ out) {
+        float4* __restrict__ out, const int32_t* __restrict__ ilist) {
   __shared__ float4 shi[W][CH];
   __shared__ float4 slo[W][CH];
   __shared__ int nb_first[W][27];
   __shared__ int nb_pre[W][28];
   __shared__ int8_t nb_off[W][27][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * W + warp;
-  if (item >= nitems) return;
+  const int idx = blockIdx.x * W + warp;
+  if (idx >= nitems) return;
+  const int item = ilist ? ilist[idx] : idx;  // ilist: the items of one bin
   const int T = leaf_of[item];  // the leaf holding this item
   const int tf = lv.first[leaf][T], tc = lv.count[leaf][T];
   const int tb = (item - items[T]) * 32;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(W * 32)
 k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
           int nitems,
           const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-          float4* __restrict__ out, double ks = 1.0, double kc = 0.0) {
+          float4* __restrict__ out, const int32_t* __restrict__ ilist = nullptr, double ks = 1.0, double kc = 0.0) {
   constexpr int NP = CH / 2;
   __shared__ ulonglong2 sA[W][NP];
   __shared__ ulonglong2 sB[W][NP];
@@ -473,22 +474,23 @@ k_p2p32x2(LevelPtrs lv, int leaf, int nleaf, const int32_t* __restrict__ items, 
   __shared__ int nb_pre[W][28];
   __shared__ int8_t nb_off[W][27][3];
   const int warp = threadIdx.x >> 5;
-  const int item = blockIdx.x * W + warp;
-  if (item >= nitems) return;
+  const int idx = blockIdx.x * W + warp;
+  if (idx >= nitems) return;
+  const int item = ilist ? ilist[idx] : idx;  // ilist: the items of one bin
   p2p32x2_item<CH, U, GEN>(item, lv, leaf, items, leaf_of, pos32, pos32lo, box, out, ks, kc, sA[warp], sB[warp],
                            sC[warp], sD[warp], nb_first[warp], nb_pre[warp], nb_off[warp]);
 }
 
-// Persistent warps: every warp takes the next work item from a counter
-// (items in leaf order, so warps running at the same time read neighbouring
-// leaves) until none is left, so no warp slot waits for the slowest warp of
+// Persistent warps: every warp takes the next work item (of ilist, if
+// given) from a counter (items in leaf order, so warps running at the same
+// time read neighbouring leaves) until none is left, so no warp slot waits for the slowest warp of
 // its block and no wave of blocks leaves SMs idle at the end.  *counter is
 // zero at launch.
 template <int W, int CH, int U>
 __global__ void __launch_bounds__(W * 32)
 k_p2p32x2p(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of, int nitems,
            const float4* __restrict__ pos32, const float4* __restrict__ pos32lo, const double* __restrict__ box,
-           float4* __restrict__ out, int32_t* __restrict__ counter) {
+           float4* __restrict__ out, int32_t* __restrict__ counter, const int32_t* __restrict__ ilist) {
   constexpr int NP = CH / 2;
   __shared__ ulonglong2 sA[W][NP];
   __shared__ ulonglong2 sB[W][NP];
@@ -499,10 +501,11 @@ k_p2p32x2p(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   __shared__ int8_t nb_off[W][27][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= nitems) return;
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(counter, 1);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= nitems) return;
+    const int item = ilist ? ilist[idx] : idx;  // ilist: the items of one bin
     p2p32x2_item<CH, U, false>(item, lv, leaf, items, leaf_of, pos32, pos32lo, box, out, 1.0, 0.0, sA[warp],
                                sB[warp], sC[warp], sD[warp], nb_first[warp], nb_pre[warp], nb_off[warp]);
   }
@@ -939,6 +942,84 @@ void p2p_carveout() {
   });
 }
 
+namespace {
+
+bool is_coop_variant(int v) { return v == 12 || v == 13; }
+
+// One mixed-precision 1/r near-field launch of shape v over the work items of
+// ilist (n of them; NULL: items 0 .. n-1) or, for the cooperative shapes,
+// over the large leaves' units.
+fmm_status launch_p2p_shape(Ctx* c, cudaStream_t s, int v, const int32_t* ilist, int n, int ctr_slot = CNT_P2P) {
+  const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
+  if (n <= 0) return FMM_OK;
+#define P2P_LAUNCH(W, CH)                                                                              \
+  k_p2p32<W, CH><<<ceil_div(n, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf, n, c->pos32,  \
+                                                  c->pos32lo, c->box, c->near32, ilist)
+#define P2P_LAUNCH2(W, CH, U)                                                                          \
+  k_p2p32x2<W, CH, U><<<ceil_div(n, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf, n,     \
+                                                       c->pos32, c->pos32lo, c->box, c->near32, ilist)
+  switch (v) {
+    case 1: P2P_LAUNCH2(4, 128, 4); break;
+    case 2: P2P_LAUNCH2(4, 256, 2); break;
+    case 3: P2P_LAUNCH2(4, 128, 2); break;
+    case 4: P2P_LAUNCH2(8, 128, 2); break;
+    case 5: P2P_LAUNCH2(8, 256, 2); break;
+    case 6: P2P_LAUNCH(4, 256); break;
+    case 7: P2P_LAUNCH(2, 128); break;
+    case 8: P2P_LAUNCH(2, 256); break;
+    case 9: P2P_LAUNCH(4, 128); break;
+    case 10: P2P_LAUNCH(8, 128); break;
+    case 11: P2P_LAUNCH(8, 256); break;
+    case 12:
+      if (c->p2p_nunits > 0)
+        k_p2p32x2c<512, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+                                                            c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
+      break;
+    case 13:
+      if (c->p2p_nunits > 0)
+        k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+                                                             c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
+      break;
+    case 14:
+    case 15: {
+      // persistent warps: as many blocks as fit on every SM at once, a zeroed work counter
+      static int occ[2] = {0, 0};
+      int& o = occ[v - 14];
+      if (o == 0) {
+        if (v == 14)
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 128, 4>, 128, 0);
+        else
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 256, 2>, 128, 0);
+        cudaGetLastError();
+        if (o <= 0) o = 4;
+      }
+      if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+      int32_t* ctr = c->counters + ctr_slot;
+      FMM_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int32_t), s));
+      const int grid = std::min(ceil_div(n, 4), o * c->num_sms);
+      if (v == 14)
+        k_p2p32x2p<4, 128, 4><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, n, c->pos32, c->pos32lo,
+                                                   c->box, c->near32, ctr, ilist);
+      else
+        k_p2p32x2p<4, 256, 2><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, n, c->pos32, c->pos32lo,
+                                                   c->box, c->near32, ctr, ilist);
+      break;
+    }
+    default: P2P_LAUNCH2(8, 128, 4); break;
+  }
+#undef P2P_LAUNCH
+#undef P2P_LAUNCH2
+  return cuda_err(c, cudaGetLastError(), "P2P launch");
+}
+
+}  // namespace
+
+// The near field.  Mixed precision, 1/r: the work items of small leaves
+// (at most P2P_BIG particles) run shape p2p_variant, those of large leaves
+// shape p2p_big_variant (-1: the same); one launch over all items when the
+// two agree.  The cooperative shapes take large leaves only (their blocks of
+// 8 warps share a leaf's sources); small leaves then take the persistent
+// shape 14.
 fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   const int Lf = c->leaf, nleaf = c->lv.ncell[Lf];
   if (nleaf == 0 || c->p2p_nitems == 0) return FMM_OK;
@@ -950,71 +1031,38 @@ fmm_status launch_p2p(Ctx* c, cudaStream_t s) {
   if (c->precision == FMM_MIXED && (c->kernel_s != 1.0 || c->kernel_c != 0.0)) {
     k_p2p32x2<8, 128, 4, true><<<ceil_div(c->p2p_nitems, 8), 256, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
                                                                            c->p2p_nitems, c->pos32, c->pos32lo, c->box,
-                                                                           c->near32, c->kernel_s, c->kernel_c);
-  } else if (c->precision == FMM_MIXED) {
-#define P2P_LAUNCH(W, CH)                                                                              \
-  k_p2p32<W, CH><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,   \
-                                                             c->p2p_nitems, c->pos32, c->pos32lo, c->box, c->near32)
-#define P2P_LAUNCH2(W, CH, U)                                                                          \
-  k_p2p32x2<W, CH, U><<<ceil_div(c->p2p_nitems, W), W * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items,         \
-                                                                  c->p2p_leaf, c->p2p_nitems, c->pos32,        \
-                                                                  c->pos32lo, c->box, c->near32)
-    switch (c->p2p_variant) {
-      case 1: P2P_LAUNCH2(4, 128, 4); break;
-      case 2: P2P_LAUNCH2(4, 256, 2); break;
-      case 3: P2P_LAUNCH2(4, 128, 2); break;
-      case 4: P2P_LAUNCH2(8, 128, 2); break;
-      case 5: P2P_LAUNCH2(8, 256, 2); break;
-      case 6: P2P_LAUNCH(4, 256); break;
-      case 7: P2P_LAUNCH(2, 128); break;
-      case 8: P2P_LAUNCH(2, 256); break;
-      case 9: P2P_LAUNCH(4, 128); break;
-      case 10: P2P_LAUNCH(8, 128); break;
-      case 11: P2P_LAUNCH(8, 256); break;
-      case 12:
-        if (c->p2p_nunits > 0)
-          k_p2p32x2c<512, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
-                                                              c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
-        break;
-      case 13:
-        if (c->p2p_nunits > 0)
-          k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
-                                                               c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
-        break;
-      case 14:
-      case 15: {
-        // persistent warps: as many blocks as fit on every SM at once, a zeroed work counter
-        static int occ[2] = {0, 0};
-        int& o = occ[c->p2p_variant - 14];
-        if (o == 0) {
-          if (c->p2p_variant == 14)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 128, 4>, 128, 0);
-          else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_p2p32x2p<4, 256, 2>, 128, 0);
-          cudaGetLastError();
-          if (o <= 0) o = 4;
-        }
-        if (c->num_sms == 0) FMM_CUDA(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
-        int32_t* ctr = c->counters + CNT_P2P;
-        FMM_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(int32_t), s));
-        const int grid = std::min(ceil_div(c->p2p_nitems, 4), o * c->num_sms);
-        if (c->p2p_variant == 14)
-          k_p2p32x2p<4, 128, 4><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems, c->pos32,
-                                                     c->pos32lo, c->box, c->near32, ctr);
-        else
-          k_p2p32x2p<4, 256, 2><<<grid, 128, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_nitems, c->pos32,
-                                                     c->pos32lo, c->box, c->near32, ctr);
-        break;
-      }
-      default: P2P_LAUNCH2(8, 128, 4); break;
-    }
-#undef P2P_LAUNCH
-#undef P2P_LAUNCH2
-  } else
+                                                                           c->near32, nullptr, c->kernel_s,
+                                                                           c->kernel_c);
+    return cuda_err(c, cudaGetLastError(), "P2P launch");
+  }
+  if (c->precision != FMM_MIXED) {
     k_p2p64<<<ceil_div(c->p2p_nitems, P2P_WARPS), P2P_WARPS * 32, 0, s>>>(c->lv, Lf, nleaf, c->p2p_items, c->p2p_leaf,
                                                                           c->p2p_nitems, c->pos64, c->kernel_s,
                                                                           c->kernel_c * c->kernel_c, c->near64);
-  return cuda_err(c, cudaGetLastError(), "P2P launch");
+    return cuda_err(c, cudaGetLastError(), "P2P launch");
+  }
+  int vs = c->p2p_variant;
+  const int vl = c->p2p_big_variant >= 0 ? c->p2p_big_variant : c->p2p_variant;
+  if (is_coop_variant(vs)) vs = 14;
+  if (vs == vl && !is_coop_variant(vl)) return launch_p2p_shape(c, s, vs, nullptr, c->p2p_nitems);
+  if (c->p2p_nsmall == 0) return launch_p2p_shape(c, s, vl, c->p2p_large, c->p2p_nlarge);
+  if (c->p2p_nlarge == 0) return launch_p2p_shape(c, s, vs, c->p2p_small, c->p2p_nsmall);
+  // the two bins run side by side: the small leaves' launch on a second
+  // stream, forked from and joined back into s (in a captured graph: two
+  // parallel nodes); the persistent shapes keep separate work counters
+  FMM_CUDA(c, cudaEventRecord(c->ev_bin0, s));
+  FMM_CUDA(c, cudaStreamWaitEvent(c->side2, c->ev_bin0, 0));
+  FMM_TRY(launch_p2p_shape(c, c->side2, vs, c->p2p_small, c->p2p_nsmall, CNT_P2P2));
+  FMM_TRY(launch_p2p_shape(c, s, vl, c->p2p_large, c->p2p_nlarge));
+  FMM_CUDA(c, cudaEventRecord(c->ev_bin1, c->side2));
+  FMM_CUDA(c, cudaStreamWaitEvent(s, c->ev_bin1, 0));
+  return FMM_OK;
+}
+
+// One bin of the near field alone (fmm_autotune): bin 0 small leaves, 1 large.
+fmm_status launch_p2p_bin(Ctx* c, cudaStream_t s, int bin, int v) {
+  if (bin == 0) return is_coop_variant(v) ? FMM_OK : launch_p2p_shape(c, s, v, c->p2p_small, c->p2p_nsmall);
+  return launch_p2p_shape(c, s, v, c->p2p_large, c->p2p_nlarge);
 }
 
 // Stokeslet near field of the loaded tree for forces f32 (Morton order,

@@ -32,6 +32,7 @@ constexpr int CNT_BAD = 127;  // counters[] slot of the non-finite-input flag
 constexpr int CNT_CLS = 16;   // counters[16 + 8 l + c] = cells of class c at level l
 constexpr int CNT_ITEMS = 120;  // counters[120] = P2P work items (leaf, 32-target batch)
 constexpr int CNT_UNITS = 121;  // counters[121] = cooperative P2P units (up to 8 items of one leaf)
+constexpr int CNT_BINS = 122;   // counters[122], [123] (one 64-bit word) = P2P items of small / large leaves
 
 __device__ inline double warp_min(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -768,23 +769,39 @@ __global__ void k_item_leaf(const int32_t* __restrict__ nleaf_ptr, int64_t cap, 
   for (int i = b; i < e; ++i) leaf_of[i] = (int32_t)T;
 }
 
-// Cooperative P2P units: up to P2P_UNIT consecutive work items of one leaf.
-// uoff[T] = units of leaf T (scanned afterwards); units[u] = first item of u.
+// P2P bins by leaf occupancy: the work items of leaves with at most
+// P2P_BIG particles ("small") and of larger leaves ("large") go to two lists,
+// so that each bin runs the near-field shape that suits it (fmm_autotune
+// picks one per bin).  Cooperative P2P units -- up to P2P_UNIT consecutive
+// work items of one leaf -- exist for large leaves only.
+// uoff[T] = units of leaf T; bins[T] = its small items (low word) and large
+// items (high word); both scanned afterwards.  units[u] = first item of u.
 constexpr int P2P_UNIT = 8;
 __global__ void k_unit_count(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
-                             int32_t* __restrict__ uoff) {
+                             int32_t* __restrict__ uoff, unsigned long long* __restrict__ bins) {
   const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= cap) return;
-  const int ni = T < *nleaf_ptr ? (count[T] + 31) >> 5 : 0;
-  uoff[T] = (ni + P2P_UNIT - 1) / P2P_UNIT;
+  const bool live = T < *nleaf_ptr;
+  const int ni = live ? (count[T] + 31) >> 5 : 0;
+  const bool big = live && count[T] > P2P_BIG;
+  uoff[T] = big ? (ni + P2P_UNIT - 1) / P2P_UNIT : 0;
+  bins[T] = big ? (unsigned long long)ni << 32 : (unsigned long long)ni;
 }
 __global__ void k_unit_write(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
                              const int32_t* __restrict__ items, const int32_t* __restrict__ uoff,
-                             int32_t* __restrict__ units) {
+                             const unsigned long long* __restrict__ bins, int32_t* __restrict__ units,
+                             int32_t* __restrict__ small, int32_t* __restrict__ large) {
   const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= cap || T >= *nleaf_ptr) return;
   const int ni = (count[T] + 31) >> 5;
-  for (int k = 0; k * P2P_UNIT < ni; ++k) units[uoff[T] + k] = items[T] + k * P2P_UNIT;
+  if (count[T] > P2P_BIG) {
+    for (int k = 0; k * P2P_UNIT < ni; ++k) units[uoff[T] + k] = items[T] + k * P2P_UNIT;
+    const int o = (int)(bins[T] >> 32);
+    for (int k = 0; k < ni; ++k) large[o + k] = items[T] + k;
+  } else {
+    const int o = (int)(bins[T] & 0xffffffffull);
+    for (int k = 0; k < ni; ++k) small[o + k] = items[T] + k;
+  }
 }
 
 __global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
@@ -1452,9 +1469,13 @@ void release_tree(Ctx* c) {
   c->p2p_leaf_cap = 0;
   rel(c->p2p_units, 4 * (size_t)c->p2p_units_cap);
   rel(c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
+  rel(c->p2p_bins, 8 * (size_t)c->p2p_units_cap);
+  rel(c->p2p_small, 4 * (size_t)c->p2p_units_cap);
+  rel(c->p2p_large, 4 * (size_t)c->p2p_units_cap);
   c->p2p_units_cap = 0;
   c->p2p_nunits = 0;
   c->p2p_nitems = 0;
+  c->p2p_nsmall = c->p2p_nlarge = 0;
   rel(c->stage_in, 8 * (size_t)c->stage_in_cap);
   rel(c->stage_out, 8 * (size_t)c->stage_out_cap);
   c->stage_in_cap = c->stage_out_cap = 0;
@@ -1573,11 +1594,16 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       c->p2p_leaf = (int32_t*)p;
       c->p2p_leaf_cap = cap;
     }
-    // units: at most one per leaf plus one per 8 items; offsets: one per leaf
+    // units: at most one per leaf plus one per 8 items; offsets and bin
+    // offsets: one per leaf; the bins' item lists: at most all items
     if (need > c->p2p_units_cap) {
       dfree(c, c->p2p_units, 4 * (size_t)c->p2p_units_cap);
       dfree(c, c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
-      c->p2p_units = c->p2p_uoff = nullptr;
+      dfree(c, c->p2p_bins, 8 * (size_t)c->p2p_units_cap);
+      dfree(c, c->p2p_small, 4 * (size_t)c->p2p_units_cap);
+      dfree(c, c->p2p_large, 4 * (size_t)c->p2p_units_cap);
+      c->p2p_units = c->p2p_uoff = c->p2p_small = c->p2p_large = nullptr;
+      c->p2p_bins = nullptr;
       c->p2p_units_cap = 0;
       void* p;
       const int64_t cap = need + need / 8 + 64;
@@ -1585,6 +1611,12 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       c->p2p_units = (int32_t*)p;
       FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
       c->p2p_uoff = (int32_t*)p;
+      FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
+      c->p2p_bins = (unsigned long long*)p;
+      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+      c->p2p_small = (int32_t*)p;
+      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
+      c->p2p_large = (int32_t*)p;
       c->p2p_units_cap = cap;
     }
   }
@@ -1667,10 +1699,14 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     scan_excl<int32_t>(s, c->p2p_items, ub[Lf], c->counters + CNT_ITEMS, (int32_t*)c->scratch, &c->launches_set);
     k_item_leaf<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
                                                      c->p2p_leaf);
-    k_unit_count<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_uoff);
+    k_unit_count<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_uoff,
+                                                      c->p2p_bins);
     scan_excl<int32_t>(s, c->p2p_uoff, ub[Lf], c->counters + CNT_UNITS, (int32_t*)c->scratch, &c->launches_set);
+    scan_excl<unsigned long long>(s, c->p2p_bins, ub[Lf], (unsigned long long*)(c->counters + CNT_BINS),
+                                  (unsigned long long*)c->scratch, &c->launches_set);
     k_unit_write<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
-                                                      c->p2p_uoff, c->p2p_units);
+                                                      c->p2p_uoff, c->p2p_bins, c->p2p_units, c->p2p_small,
+                                                      c->p2p_large);
     c->launches_set += 4;
     if (Lf >= 2) {
       ClassArgs ca;
@@ -1719,6 +1755,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   c->n = n;
   c->p2p_nitems = n > 0 ? c->counters_h[CNT_ITEMS] : 0;
   c->p2p_nunits = n > 0 ? c->counters_h[CNT_UNITS] : 0;
+  c->p2p_nsmall = n > 0 ? c->counters_h[CNT_BINS] : 0;
+  c->p2p_nlarge = n > 0 ? c->counters_h[CNT_BINS + 1] : 0;
   if (n > 0) {
     for (int d = 0; d < 4; ++d) c->box_host[d] = c->box_h[d];
   } else {

@@ -63,6 +63,7 @@ _SIGS = {
     "fmm_morton_order_noalloc": [C.c_int64, _vp, C.c_int, _vp, _vp, _vp],
     "fmm_measure_fp32_rate": [_vp],
     "fmm_set_wait_limit": [_vp, C.c_double],
+    "fmm_get_p2p_bins": [_vp, _vp, _vp],
 }
 _SIGS.update({
     "fmm_server_create": [_vp, C.POINTER(_vp)],
@@ -262,6 +263,14 @@ def fmm_get_m2l_kernel_times(h) -> np.ndarray:
     out = np.zeros(2, dtype=np.float32)
     _check(h, lib.fmm_get_m2l_kernel_times(h, _ptr(out)))
     return out
+
+
+def fmm_get_p2p_bins(h):
+    """(out[4]: small shape, large shape, small items, large items; times [2][variants])"""
+    out = np.zeros(4, dtype=np.int64)
+    times = np.zeros((2, FMM_P2P_VARIANTS), dtype=np.float32)
+    _check(h, lib.fmm_get_p2p_bins(h, _ptr(out), _ptr(times)))
+    return out, times
 
 
 def fmm_set_wait_limit(h, seconds: float) -> int:

@@ -252,7 +252,9 @@ def test_batched_workload_sampled(F):
 
 def test_p2p_variants_agree_and_autotune_picks_one(F):
     """Every shape of the mixed P2P kernel gives the same result up to the
-    grouping of FP32 partial sums; the autotuner keeps one of them."""
+    grouping of FP32 partial sums; the autotuner times each occupancy bin
+    (leaves of at most 64 particles, larger leaves) in every shape and keeps
+    each bin's fastest, and the binned evaluation agrees with the others."""
     import torch
     probs = _mixed_batch()
     counts, heights, xyz, q = _concat(probs)
@@ -269,15 +271,26 @@ def test_p2p_variants_agree_and_autotune_picks_one(F):
             out[v] = (phi.cpu().numpy().copy(), Fo.cpu().numpy().copy())
         choice, times = F.fmm_autotune(f.h)
         assert 0 <= choice[0] < F.FMM_P2P_VARIANTS and np.all(times > 0)
-        assert times[choice[0]] == times.min()
+        bins, bin_ms = F.fmm_get_p2p_bins(f.h)
+        assert bins[2] > 0 and bins[3] > 0, "the batch has small and large leaves"
+        best = []
+        for b in range(2):
+            timed = bin_ms[b][bin_ms[b] >= 0]
+            assert len(timed) == (F.FMM_P2P_VARIANTS - 2 if b == 0 else F.FMM_P2P_VARIANTS)
+            best.append(int(np.argmin(np.where(bin_ms[b] >= 0, bin_ms[b], np.inf))))
+        # either each bin's fastest shape, or one item shape for both bins
+        assert (int(bins[0]), int(bins[1])) == tuple(best) or (int(bins[0]) == int(bins[1]) and int(bins[0]) not in (12, 13))
+        assert int(choice[0]) == int(bins[0])
         f.evaluate(phi, Fo)
         torch.cuda.synchronize()
-        assert np.array_equal(phi.cpu().numpy(), out[int(choice[0])][0])
+        binned = (phi.cpu().numpy().copy(), Fo.cpu().numpy().copy())
         with pytest.raises(F.FMMError):
             F.fmm_set_p2p_variant(f.h, F.FMM_P2P_VARIANTS)
     for v in range(1, F.FMM_P2P_VARIANTS):
         assert oracle.rel_l2(out[v][0], out[0][0]) <= TOL_ALONE, v
         assert oracle.rel_l2(out[v][1], out[0][1]) <= TOL_ALONE, v
+    assert oracle.rel_l2(binned[0], out[0][0]) <= TOL_ALONE
+    assert oracle.rel_l2(binned[1], out[0][1]) <= TOL_ALONE
 
 
 def test_batch_problems_of_very_different_magnitude(F):
