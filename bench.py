@@ -284,7 +284,9 @@ def m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main: bool):
     tensor_pipe = None
     roofline_proj = None
     if m2l_kind == 5:
-        kernel_name = f"k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels"
+        kernel_name = (f"k_svd_expand16_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels"
+                       if math == "f16x3" else
+                       f"k_svd_expand_tc (compressed M2L expansion L += U y, tcgen05, {mlabel}), all levels")
         half_flop = m2l_flop / 2.0
         m2l_ms = float(kt[1])
         achieved = half_flop / (m2l_ms / 1e3) / 1e12
@@ -327,15 +329,30 @@ def m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main: bool):
     return roof, roofline_proj, tensor_pipe
 
 
-def p2p_roofline(p2p_pairs: int, p2p_ms: float, pk, kernel: str):
+def p2p_roofline(p2p_pairs: int, p2p_ms: float, pk, kernel: str, traffic=None):
+    """The near field against the FP32 pipe: achieved = 20 flop per directed
+    interaction (the paper's convention) over the P2P launch time, against
+    the FP32 rate measured in this run; also the fraction of the FP32
+    operation rate the kernel's 19 issued operations per interaction fill."""
     fp = pk["fp32"]
     ips = p2p_pairs / (p2p_ms / 1e3)
-    return {"bound": "alu", "kernel": kernel, "ms": p2p_ms, "interactions": p2p_pairs, "interactions_per_s": ips,
-            "achieved_gflops_20": 20.0 * ips / 1e9, "frac_20flop": 20.0 * ips / (fp["tflops"] * 1e12),
+    return {"bound": "alu", "kernel": kernel, "achieved": 20.0 * ips / 1e12, "peak": fp["tflops"],
+            "unit": "TFLOP/s", "frac": 20.0 * ips / (fp["tflops"] * 1e12), "traffic": traffic, "ms": p2p_ms,
+            "algorithmic": f"20 flop x {p2p_pairs} directed interactions = {20.0 * p2p_pairs:.4g} flop per launch",
+            "peak_source": "FP32 FMA rate measured in this run (fp32_peak)",
+            "interactions": p2p_pairs, "interactions_per_s": ips,
             "fp32_ops_per_interaction": P2P_FP32_OPS,
             "fp32_pipe_frac": P2P_FP32_OPS * ips / fp["ops_per_s"],
-            "fp32_pipe_frac_plain_13": P2P_FP32_OPS_PLAIN * ips / fp["ops_per_s"],
-            "peak_fp32_tflops": fp["tflops"], "peak_source": "measured in this run (fp32_peak)"}
+            "fp32_pipe_frac_plain_13": P2P_FP32_OPS_PLAIN * ips / fp["ops_per_s"]}
+
+
+def dominant(rooflines: dict):
+    """The roofline of the kernel with the longest launch time."""
+    best = None
+    for r in rooflines.values():
+        if r is not None and (best is None or r["ms"] > best["ms"]):
+            best = r
+    return best
 
 
 def autotune(fmm, h):
@@ -555,6 +572,13 @@ def measure_single(args, fmm, dev, workload: str, pk, rank: int = 0, main: bool 
     stage = np.array(stage)
     kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
     roof, roof_proj, tensor_pipe = m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main)
+    p2p_kernel = ("k_p2p32x2p / k_p2p32x2 / k_p2p32x2c (the near field in the autotuned shapes, run alone)"
+                  if tuned else "k_p2p32x2<8,128,4> (the near field, run alone)")
+    roof_p2p = p2p_roofline(int(work[0]), float(iso[5]), pk, p2p_kernel,
+                            profiled_traffic("paper_1206_0115_b300/csrc/nearfield.cu",
+                                             "profiles/p2p_cube_n1m_h6_p7.md", "// ---- the Stokeslet near field")
+                            if main else None)
+    kernels = {"m2l_expansion": roof, "m2l_projection": roof_proj, "p2p": roof_p2p}
     math = m2l_math(stats)
     res = {
         "value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
@@ -572,11 +596,13 @@ def measure_single(args, fmm, dev, workload: str, pk, rank: int = 0, main: bool 
                      "l2p_out": float(np.mean(stage[:, 6])), "evaluate": float(np.mean(stage[:, 7]))},
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
-        "roofline": roof,
+        # the kernel with the longest launch time; every one of the three below
+        "roofline": dominant(kernels),
+        "roofline_m2l_expansion": roof,
         "roofline_m2l_projection": roof_proj,
+        "roofline_p2p": roof_p2p,
         "tensor_pipe": tensor_pipe,
         "autotune": tuned,
-        "roofline_p2p": p2p_roofline(int(work[0]), float(iso[5]), pk, "k_p2p (the chosen shape, run alone)"),
         "roofline_stages": stage_rooflines(n, h, p, ncell, iso, build_ms, pk, args.precision),
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
         # evaluations that ran launch by launch after a failed graph capture (0 expected)
@@ -734,6 +760,22 @@ def measure_batched(args, fmm, dev, pk, rank: int = 0):
     peak, peak_note = tensor_peak(pk, math)
     kt = np.mean(np.array(ktimes), axis=0) if ktimes else None
     half_flop = 2.0 * C * int(work[13])
+    kexp = ("k_svd_expand16_tc" if math == "f16x3" else "k_svd_expand_tc")
+    kernels = {
+        "m2l_expansion": None if kt is None else {
+            "kernel": f"{kexp} (compressed M2L expansion, tcgen05, {mlabel}), all problems and levels",
+            "bound": "tensor", "achieved": half_flop / (kt[1] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": half_flop / (kt[1] / 1e3) / 1e12 / peak, "traffic": None, "ms": float(kt[1]),
+            "algorithmic": f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch",
+            "peak_source": peak_note},
+        "m2l_projection": None if kt is None else {
+            "kernel": f"k_svd_proj_tc (compressed M2L projection, tcgen05, {mlabel}), all problems and levels",
+            "bound": "tensor", "achieved": half_flop / (kt[0] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": half_flop / (kt[0] / 1e3) / 1e12 / peak, "traffic": None, "ms": float(kt[0]),
+            "algorithmic": f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch",
+            "peak_source": peak_note},
+        "p2p": p2p_roofline(int(work[0]), float(iso[5]), pk, "the near field in the autotuned shapes, run alone"),
+    }
     res = {
         "value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
@@ -750,21 +792,15 @@ def measure_batched(args, fmm, dev, pk, rank: int = 0):
         "set_batch_ms": float(np.mean(build_ms)),
         "stage_ms_isolated": {"upward": float(iso[0]), "m2l_main": float(iso[2]), "m2l_rest": float(iso[3]),
                               "l2l": float(iso[4]), "p2p": float(iso[5]), "l2p_out": float(iso[6])},
-        "roofline": None if kt is None else {
-            "kernel": f"k_svd_expand_tc (compressed M2L expansion, tcgen05, {mlabel}), all problems and levels",
-            "bound": "tensor", "achieved": half_flop / (kt[1] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": half_flop / (kt[1] / 1e3) / 1e12 / peak, "traffic": None, "ms": float(kt[1]),
-            "algorithmic": f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch",
-            "peak_source": peak_note},
-        "roofline_m2l_projection": None if kt is None else {
-            "kernel": "k_svd_proj_tc", "achieved": half_flop / (kt[0] / 1e3) / 1e12, "peak": peak,
-            "unit": "TFLOP/s", "frac": half_flop / (kt[0] / 1e3) / 1e12 / peak, "ms": float(kt[0])},
+        "roofline": dominant(kernels),
+        "roofline_m2l_expansion": kernels["m2l_expansion"],
+        "roofline_m2l_projection": kernels["m2l_projection"],
+        "roofline_p2p": kernels["p2p"],
         "tensor_pipe": None if kt is None else {
             "operands": math,
             "expansion_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[15]) / (kt[1] / 1e3) / 1e12 / peak,
             "projection_frac_of_peak": 3 * 2.0 * 128 * cpad * int(work[14]) / (kt[0] / 1e3) / 1e12 / peak},
         "autotune": tuned,
-        "roofline_p2p": p2p_roofline(int(work[0]), float(iso[5]), pk, "k_p2p (the chosen shape, run alone)"),
         "gpu_launches": int((stats[0] + stats[1]) * args.steps),
         "graph_fallbacks": int(stats[6]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(32 * n),
