@@ -366,6 +366,11 @@ def autotune(fmm, h):
     for b, name in enumerate(("small_leaves", "large_leaves")):
         rep["bins"][name] = {"items": int(bins[2 + b]), "variant": int(bins[b]),
                              "variant_ms": [round(float(t), 4) for t in bin_ms[b]]}
+    sched, sched_ms = fmm.fmm_get_schedule(h)
+    names = ("with_expansion", "at_start", "with_projection", "with_projection_2xstages")
+    rep["schedule"] = {"p2p_starts": names[sched],
+                       "evaluate_ms": {k: round(float(t), 4) for k, t in zip(
+                           list(names) + [n + "_nonpersistent" for n in names], sched_ms)}}
     return rep
 
 

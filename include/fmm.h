@@ -40,6 +40,7 @@ extern "C" {
 typedef struct fmm_ctx* fmm_handle;
 
 #define FMM_P2P_VARIANTS 16 /* shapes of the mixed-precision P2P kernel (fmm_autotune) */
+#define FMM_SCHED_CANDIDATES 8 /* evaluation schedules timed by fmm_autotune (fmm_get_schedule) */
 
 typedef enum {
   FMM_OK = 0,
@@ -249,6 +250,16 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * shape over every item -- the item shape with the least time over both
  * bins, timed as one launch -- is faster; fmm_get_p2p_bins reports the
  * result.
+ * Last, in mixed precision with a far field (height >= 3), the evaluation
+ * schedule: whole evaluations (each graph built once, then three timed
+ * runs) in each schedule of fmm_set_schedule (2 and 3 only with the
+ * compressed tensor-core M2L on FP16 operands), each with the chosen shapes
+ * and -- when those include a persistent shape (14, 15), whose blocks hold
+ * their SMs until the last work item is taken -- with the fastest
+ * non-persistent shapes per bin; the fastest candidate's schedule and
+ * shapes are kept (fmm_get_schedule).  The paper's schedulers decide where near- and
+ * far-field tasks run from measured costs (Sec. 4 and 5); this is the same
+ * decision for one GPU's fixed launch order.
  * choice (may be NULL): the small leaves' shape (the large leaves' if there
  * are no small ones): [0] index, [1] warps per block, [2] sources per
  * chunk, [3] sources per instruction, [4] unroll; times_ms (may be NULL):
@@ -285,6 +296,27 @@ fmm_status fmm_set_p2p_variant(fmm_handle h, int variant);
  * calibration of Sec. 5 that lets its scheduler pick a worker per task.
  * out: 4 int64, host.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_get_p2p_bins(fmm_handle h, int64_t* out, float* times_ms);
+
+/* Where the near-field branch (P2P, Sec. 2.1) starts in the evaluation
+ * graph, its blocks at the low launch priority: 0 (the default) with the
+ * compressed M2L's expansion kernel, after the projection; 1 at the start
+ * of the evaluation, beside the upward pass, filling the SMs that the
+ * upward pass and the M2L bookkeeping kernels leave idle; 2 with the
+ * projection, which then runs three pipeline stages instead of four so that
+ * P2P blocks fit beside its CTA on every SM; 3 as 2, and the expansion
+ * with two stages (room for P2P blocks beside it too).  With another M2L
+ * form, 2 and 3 act as 0.  The arithmetic is the same in every schedule:
+ * the results are bit-identical.  fmm_autotune sets it from measured
+ * evaluations.  The evaluation graph is rebuilt.  Errors: FMM_ERR_ARG
+ * (sched outside 0..3). */
+fmm_status fmm_set_schedule(fmm_handle h, int sched);
+
+/* The current schedule (*sched, host int32) and, in times_ms (may be NULL;
+ * FMM_SCHED_CANDIDATES floats, host), the mean evaluation time of each
+ * candidate of the last fmm_autotune: [k] schedule k with the chosen
+ * near-field shapes, [4 + k] schedule k with the fastest non-persistent
+ * shapes (k = 0..3); -1 where not timed. */
+fmm_status fmm_get_schedule(fmm_handle h, int32_t* sched, float* times_ms);
 
 /* Releases every device buffer that belongs to the current tree (particles,
  * cells, expansions, M2L work tables and projections, staging) and keeps the

@@ -216,29 +216,56 @@ fmm_status deliver(Ctx* c, void* dst, const void* devsrc, int64_t n) {
 }
 
 fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
-  // upward pass first; then P2P on the side branch overlaps M2L and L2L (the
-  // persistent tensor-core M2L leaves room on every SM for P2P blocks)
+  // The near field (P2P) runs on a side branch beside the far field.  Where
+  // it starts is the handle's schedule (p2p_sched, picked by fmm_autotune):
+  // 0, with the compressed M2L's expansion kernel (the branch waits for the
+  // projection); 1, at the start of the evaluation, so that its blocks fill
+  // the SMs that the upward pass and the M2L bookkeeping kernels leave idle
+  // (at the low launch priority, build_graph: the persistent M2L kernels
+  // take each SM as the P2P blocks on it finish); 2 and 3, with the
+  // projection, whose CTAs then leave shared memory for P2P blocks beside
+  // them (and, in 3, the expansion's too; launch_m2l_svd_tc).
   // timing mode 2 runs P2P alone first (no overlap) so that every stage is timed in isolation
   cudaStream_t ps = c->timing == 2 ? s : c->side;
+  const bool early = c->timing != 2 && c->p2p_sched == 1;
+  auto near_branch = [&](cudaEvent_t start) -> fmm_status {
+    FMM_CUDA(c, cudaStreamWaitEvent(c->side, start, 0));
+    if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], ps, cudaEventRecordExternal));
+    FMM_TRY(launch_p2p(c, ps));
+    if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], ps, cudaEventRecordExternal));
+    FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+    return FMM_OK;
+  };
   if (c->timing == 2) {
     FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], s, cudaEventRecordExternal));
     FMM_TRY(launch_p2p(c, s));
     FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], s, cudaEventRecordExternal));
   }
+  // the compressed M2L's tree-only bookkeeping on a third branch, beside
+  // the upward pass (launch_m2l joins it before the projection)
+  c->m2l_prep_done = false;
+  const bool prep = c->timing != 2 && m2l_has_prep(c);
+  if (early || prep) FMM_CUDA(c, cudaEventRecord(c->ev_start, s));
+  if (prep) {
+    FMM_CUDA(c, cudaStreamWaitEvent(c->side3, c->ev_start, 0));
+    FMM_TRY(launch_m2l_prep(c, c->side3));
+  }
+  if (early) FMM_TRY(near_branch(c->ev_start));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
   FMM_TRY(launch_upward(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
-  FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
+  if (!early) FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
   c->p2p_after_proj = false;
   FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
-  // the P2P branch starts with the persistent expansion kernel, so that its
-  // blocks fill the room beside the expansion's CTAs instead of holding the
-  // SMs the persistent kernels need (see launch_m2l_svd_tc)
-  FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->p2p_after_proj ? c->ev_p2p : c->ev_fork, 0));
-  if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], ps, cudaEventRecordExternal));
-  if (c->timing != 2) FMM_TRY(launch_p2p(c, ps));
-  if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], ps, cudaEventRecordExternal));
-  FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  // schedule 0: the P2P branch starts with the persistent expansion kernel,
+  // so that its blocks fill the room beside the expansion's CTAs instead of
+  // holding the SMs the persistent kernels need (see launch_m2l_svd_tc)
+  if (!early && c->timing == 2) {  // P2P ran alone above: an empty branch
+    FMM_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  } else if (!early) {
+    FMM_TRY(near_branch(c->p2p_after_proj ? c->ev_p2p : c->ev_fork));
+  }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
   FMM_TRY(launch_l2l(c, s));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[4], s, cudaEventRecordExternal));
@@ -255,7 +282,7 @@ std::vector<int64_t> graph_signature(const Ctx* c) {
                             (int64_t)(uintptr_t)c->p2p_large,
                             (int64_t)(uintptr_t)c->p2p_units, c->p2p_nunits,
                             (int64_t)(c->kernel_s * 1e6), (int64_t)(c->kernel_c * 1e9), c->skip_p2p,
-                            c->m2l_f16, (int64_t)c->wait_ns};
+                            c->m2l_f16, (int64_t)c->wait_ns, c->p2p_sched};
   for (int l = 0; l <= c->leaf; ++l) {
     s.push_back(c->lv.ncell[l]);
     s.push_back(c->lv.row_off[l]);
@@ -398,6 +425,9 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   };
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_bin0, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_bin1, cudaEventDisableTiming) != cudaSuccess ||
@@ -468,7 +498,7 @@ fmm_status fmm_destroy(fmm_handle h) {
                   c->L64, c->tiles, c->tile_src, c->tile_act, c->tile_nact, c->nodes64, c->cheb64, c->cheb32,
                   c->m2m64, c->m2m32, c->tvec, c->cls_t, c->K64, c->Khi, c->Klo, c->tc_partial, c->tc_err,
                   c->svd_W, c->svd_vals, c->svd_sm, c->svd_V64, c->svd_U64, c->svd_VThi,
-                  c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact,
+                  c->svd_Uhi, c->svd_ry, c->svd_Y, c->src_t, c->src_act, c->src_nact, c->tile_mask,
                   c->svd_recs, c->svd_Mcls, c->svd_eslot, c->svd_ekch, c->svd_yidx, c->svd_umax, c->svd_mscale, c->tc_mmax,
                   c->fb_pstart, c->fb_prob, c->fb_box, c->fb_scale, c->fb_frame, c->fb_thr, c->fb_sstart, c->fb_sprob,
                   c->fb_bstart, c->svd_Yx, c->svd_dst, c->svd_kap8, c->svd_Uc};
@@ -488,6 +518,12 @@ fmm_status fmm_destroy(fmm_handle h) {
     cudaStreamSynchronize(c->side2);
     cudaStreamDestroy(c->side2);
   }
+  if (c->side3) {
+    cudaStreamSynchronize(c->side3);
+    cudaStreamDestroy(c->side3);
+  }
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  if (c->ev_prep) cudaEventDestroy(c->ev_prep);
   if (c->ev_bin0) cudaEventDestroy(c->ev_bin0);
   if (c->ev_bin1) cudaEventDestroy(c->ev_bin1);
   if (c->side) cudaStreamDestroy(c->side);
@@ -802,6 +838,97 @@ fmm_status fmm_set_p2p_variant(fmm_handle h, int variant) {
   return FMM_OK;
 }
 
+}  // extern "C"
+
+namespace fmm {
+namespace {
+
+bool persistent_shape(int v) { return v == 14 || v == 15; }
+bool is_coop_shape(int v) { return v == 12 || v == 13; }
+
+// The evaluation schedule (fmm_autotune's last stage): whole evaluations in
+// up to eight candidates -- the near-field branch starting with the
+// compressed M2L's expansion (schedule 0), at the start (1), or with the
+// projection (2; 3 with two expansion stages), each with the shapes chosen
+// so far and with the fastest shapes per bin that hold no SM for the whole
+// launch (not the persistent 14, 15: their blocks stay until the last work
+// item is taken, so a persistent M2L kernel cannot start beside them) --
+// each run once to build its graph, then timed three times with CUDA events
+// on the handle's stream; the fastest is kept.
+fmm_status autotune_schedule(Ctx* c) {
+  for (int k = 0; k < FMM_SCHED_CANDIDATES; ++k) c->sched_ms[k] = -1.f;
+  if (c->leaf < 2 || c->n == 0 || !c->use_graph) return FMM_OK;  // no far field to order against
+  const int keep_timing = c->timing;
+  if (c->timing == 2) c->timing = 0;  // mode 2 runs P2P alone: no schedule to time
+  const int nb[2] = {(int)c->p2p_nsmall, (int)c->p2p_nlarge};
+  // the non-persistent alternative, per bin, from the bins' own times
+  int alt[2] = {-1, -1};
+  for (int b = 0; b < 2; ++b) {
+    float bt = -1.f;
+    for (int v = 0; v < FMM_P2P_VARIANTS; ++v) {
+      const float ms = c->p2p_bin_ms[b][v];
+      if (ms < 0.f || nb[b] == 0 || persistent_shape(v) || (b == 0 && is_coop_shape(v))) continue;
+      if (bt < 0.f || ms < bt) {
+        bt = ms;
+        alt[b] = v;
+      }
+    }
+  }
+  const int chosen_var = c->p2p_variant, chosen_big = c->p2p_big_variant;
+  int alt_var = nb[0] > 0 ? alt[0] : (alt[1] >= 0 && !is_coop_shape(alt[1]) ? alt[1] : 0);
+  int alt_big = nb[1] > 0 ? alt[1] : -1;
+  if (alt_big == alt_var) alt_big = -1;
+  const int eff_small = is_coop_shape(chosen_var) ? 14 : chosen_var;
+  const int eff_large = chosen_big >= 0 ? chosen_big : chosen_var;
+  const bool uses_persistent = (nb[0] > 0 && persistent_shape(eff_small)) || (nb[1] > 0 && persistent_shape(eff_large));
+  const bool have_alt = uses_persistent && (nb[0] == 0 || alt[0] >= 0) && (nb[1] == 0 || alt[1] >= 0);
+
+  fmm_status st = ensure_stage(c, &c->stage_out, &c->stage_out_cap, 4 * c->n);
+  double* phi = c->stage_out;
+  double* F = c->stage_out + c->n;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == FMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = cuda_err(c, cudaGetLastError(), "fmm_autotune: events");
+  int best = -1;
+  float best_ms = -1.f;
+  for (int k = 0; k < FMM_SCHED_CANDIDATES && st == FMM_OK; ++k) {
+    const bool use_alt = k >= 4;
+    if (use_alt && !have_alt) continue;
+    if ((k & 3) >= 2 && !(m2l_kind(c) == 5 && svd_wants_f16(c))) continue;  // the compressed FP16 M2L's stages
+    c->p2p_sched = k & 3;
+    c->p2p_variant = use_alt ? alt_var : chosen_var;
+    c->p2p_big_variant = use_alt ? alt_big : chosen_big;
+    c->graph_ok = false;
+    st = fmm_evaluate(c, phi, F);  // builds this candidate's graph
+    if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
+    for (int r = 0; r < 3 && st == FMM_OK; ++r) st = fmm_evaluate(c, phi, F);
+    float ms = 0.f;
+    if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
+    if (st != FMM_OK) break;
+    c->sched_ms[k] = ms / 3.f;
+    if (best < 0 || c->sched_ms[k] < best_ms) {
+      best = k;
+      best_ms = c->sched_ms[k];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->timing = keep_timing;
+  const int pick = best >= 0 ? best : 0;
+  c->p2p_sched = st == FMM_OK ? (pick & 3) : 0;
+  c->p2p_variant = (st == FMM_OK && pick >= 4) ? alt_var : chosen_var;
+  c->p2p_big_variant = (st == FMM_OK && pick >= 4) ? alt_big : chosen_big;
+  c->graph_ok = false;
+  return st;
+}
+
+}  // namespace
+}  // namespace fmm
+
+extern "C" {
+
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
@@ -911,6 +1038,7 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
   }
   c->graph_ok = false;
   if (st != FMM_OK) return st;
+  if (c->precision == FMM_MIXED) FMM_TRY(autotune_schedule(c));
   if (times_ms)  // each shape used for every item, as fmm_set_p2p_variant would
     for (int v = 0; v < FMM_P2P_VARIANTS; ++v) {
       const float a = nb[0] > 0 ? c->p2p_bin_ms[0][(v == 12 || v == 13) ? 14 : v] : 0.f;
@@ -921,6 +1049,27 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
     choice[0] = c->p2p_variant;
     for (int k = 0; k < 4; ++k) choice[1 + k] = kP2PVariants[c->p2p_variant][k];
   }
+  return FMM_OK;
+}
+
+fmm_status fmm_set_schedule(fmm_handle h, int sched) {
+  if (!h) return FMM_ERR_ARG;
+  Ctx* c = h;
+  c->err[0] = 0;
+  if (sched < 0 || sched > 3) return set_err(c, FMM_ERR_ARG, "fmm_set_schedule: %d outside 0..3", sched);
+  if (sched != c->p2p_sched) {
+    c->p2p_sched = sched;
+    c->graph_ok = false;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_get_schedule(fmm_handle h, int32_t* sched, float* times_ms) {
+  if (!h || !sched) return FMM_ERR_ARG;
+  Ctx* c = h;
+  *sched = c->p2p_sched;
+  if (times_ms)
+    for (int k = 0; k < FMM_SCHED_CANDIDATES; ++k) times_ms[k] = c->sched_ms[k];
   return FMM_OK;
 }
 

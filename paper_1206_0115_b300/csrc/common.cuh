@@ -116,7 +116,10 @@ struct fmm_ctx {
   cudaStream_t cap = nullptr;     // graph capture
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_p2p = nullptr;  // where the P2P branch starts (after the compressed M2L projection)
-  bool p2p_after_proj = false;   // ev_p2p was recorded by the M2L launch
+  cudaStream_t side3 = nullptr;   // the compressed M2L's tree-only bookkeeping beside the upward pass
+  cudaEvent_t ev_start = nullptr, ev_prep = nullptr;  // its fork (the evaluation's start) and join
+  bool m2l_prep_done = false;     // that bookkeeping was launched on side3 (ev_prep marks its end)
+  bool p2p_after_proj = false;   // ev_p2p was recorded by the M2L launch (the P2P branch starts there)
   char err[512] = {0};
   cudaError_t last_cuda = cudaSuccess;  // the CUDA error behind the last FMM_ERR_CUDA / FMM_ERR_OOM
 
@@ -149,6 +152,12 @@ struct fmm_ctx {
   int p2p_variant = 0;           // shape of the mixed P2P kernel (kP2PVariants): small leaves (or all)
   int p2p_big_variant = -1;      // shape for the large leaves' items (-1: p2p_variant)
   float p2p_bin_ms[2][FMM_P2P_VARIANTS] = {{0.f}};  // the last fmm_autotune's per-bin times
+  // where the near-field branch starts in the evaluation graph: 0 with the
+  // compressed M2L's expansion kernel, 1 at the start, beside the upward
+  // pass, 2 with the projection (three projection stages), 3 as 2 with two
+  // expansion stages (fmm_set_schedule)
+  int p2p_sched = 0;
+  float sched_ms[FMM_SCHED_CANDIDATES] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};  // the last fmm_autotune's evaluation times
   double4* near64 = nullptr;
   double *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
   int64_t stage_in_cap = 0, stage_out_cap = 0;
@@ -208,6 +217,7 @@ struct fmm_ctx {
   int32_t* tile_nact = nullptr; // [tile]
   int16_t* src_act = nullptr;   // [tile][189]: indices into src_t of the tile's cells as sources with a target
   int32_t* src_nact = nullptr;  // [tile]
+  uint32_t* tile_mask = nullptr; // [2][tile][6]: the setup's transfer-vector bit masks (targets, sources)
   int leaf_tiles = 0;           // tiles [0, leaf_tiles) belong to the leaf level
   int leaf_tile_end() const { return leaf_tiles; }
 
@@ -382,6 +392,10 @@ fmm_status m2l_svd_tc_prepare(Ctx* c);
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 // M2L of every level; `mid` separates the main kernel from the rest (see fmm_get_stage_times)
 fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid);
+fmm_status launch_m2l_prep(Ctx* c, cudaStream_t s);
+bool m2l_has_prep(const Ctx* c);
+fmm_status svd_tree_setup(Ctx* c, cudaStream_t s);
+bool svd_has_tree_setup(const Ctx* c);
 fmm_status launch_l2l(Ctx* c, cudaStream_t s);
 fmm_status launch_l2p_out(Ctx* c, cudaStream_t s, double* phi, double* F);
 fmm_status expansion_to_f64(Ctx* c, int level, int which, double* out);

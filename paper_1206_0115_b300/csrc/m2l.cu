@@ -33,6 +33,24 @@ fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   return run(c, s, c->leaf_tiles, c->ntiles - c->leaf_tiles);
 }
 
+// The part of the M2L bookkeeping that depends on the tree alone (not on
+// the multipoles), launched on its own branch so that it runs beside the
+// upward pass; launch_m2l then waits for it (c->ev_prep) instead of
+// launching it.  Only the compressed tensor-core form with FP16 operands has
+// such a part (its projection records and destination map).
+bool m2l_has_prep(const Ctx* c) {
+  return c->ntiles > 0 && c->n > 0 && m2l_kind(c) == 5 && svd_has_tree_setup(c);
+}
+
+fmm_status launch_m2l_prep(Ctx* c, cudaStream_t s) {
+  c->m2l_prep_done = false;
+  if (!m2l_has_prep(c)) return FMM_OK;
+  FMM_TRY(svd_tree_setup(c, s));
+  FMM_CUDA(c, cudaEventRecord(c->ev_prep, s));
+  c->m2l_prep_done = true;
+  return FMM_OK;
+}
+
 namespace {
 
 __global__ void __launch_bounds__(FMM_TILE)

@@ -1353,6 +1353,39 @@ fmm_status m2l_svd_tc_prepare(Ctx* c) {
 // reduction of its partial sums.
 bool svd_wants_f16(const Ctx* c) { return m2l_uses_f16(c) && c->use_tc && m2l_svd_tc_supported(c); }
 
+// Whether svd_tree_setup's work depends on the tree alone: the FP16 form
+// (the TF32 form's records are the same, but it has no destination map and
+// keeps them beside its other setup).
+bool svd_has_tree_setup(const Ctx* c) { return m2l_uses_f16(c); }
+
+// The projection's work records (k_svd_groups: per tile, groups of active
+// source transfer vectors; the unit count) and, in the FP16 form, its
+// destination map (k_svd_scatter_setup: per (source cell, t), the row of
+// the target tile's operand slab; zeros where a target has no source):
+// functions of the tree and the operators' ranks, not of the multipoles.
+fmm_status svd_tree_setup(Ctx* c, cudaStream_t s) {
+  const bool f16 = m2l_uses_f16(c);
+  McBase mb;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l)
+    for (int k = 0; k < 8; ++k) {
+      mb.base[l][k] = l >= 2 && l <= c->leaf ? c->svd_mcbase[l][k] : 0;
+      mb.clsoff[l][k] = c->cls_off[l][k];
+    }
+  int32_t* nunits = c->counters + CNT_PUNITS;
+  FMM_CUDA(c, cudaMemsetAsync(nunits, 0, sizeof(int32_t), s));
+  k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, sp_ngroups(c->svd_rp), c->tiles, c->lv, mb, c->src_act,
+                                         c->src_nact, c->src_t, c->svd_ry, c->svd_yoff, c->tvec,
+                                         f16 ? c->svd_kap8 : nullptr, (ProjRec*)c->svd_recs, nunits, c->tc_err);
+  if (f16) {
+    // destinations of the projections (and zeros where a target has no source)
+    FMM_CUDA(c, cudaMemsetAsync(c->svd_dst, 0xFF, sizeof(int32_t) * FMM_NT_CLASS * (size_t)c->rows, s));
+    k_svd_scatter_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(
+        c->tiles, c->tile_src, c->lv, c->cls_t, c->svd_ry, c->svd_kap8, c->svd_srcidx, c->svd_kct, c->rows,
+        c->svd_dst, (uint32_t*)c->svd_Yx);
+  }
+  return cuda_err(c, cudaGetLastError(), "compressed M2L setup");
+}
+
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp;
@@ -1401,18 +1434,18 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   p.wait_ns = c->wait_ns;
   int32_t* nunits = c->counters + CNT_PUNITS;
   p.nunits = nunits;
-  FMM_CUDA(c, cudaMemsetAsync(nunits, 0, sizeof(int32_t), s));
-  k_svd_groups<<<c->ntiles, 256, 0, s>>>(c->ntiles, p.ngroups, c->tiles, c->lv, mb, c->src_act, c->src_nact, c->src_t,
-                                         c->svd_ry, c->svd_yoff, c->tvec, f16 ? c->svd_kap8 : nullptr,
-                                         (ProjRec*)c->svd_recs, nunits, c->tc_err);
-  if (f16) {
-    // destinations of the projections (and zeros where a target has no source)
-    FMM_CUDA(c, cudaMemsetAsync(c->svd_dst, 0xFF, sizeof(int32_t) * FMM_NT_CLASS * (size_t)c->rows, s));
-    k_svd_scatter_setup<<<dim3(c->ntiles, (FMM_NT_CLASS + EXS_CHUNK - 1) / EXS_CHUNK), FMM_TILE, 0, s>>>(
-        c->tiles, c->tile_src, c->lv, c->cls_t, c->svd_ry, c->svd_kap8, c->svd_srcidx, c->svd_kct, c->rows,
-        c->svd_dst, (uint32_t*)c->svd_Yx);
-  }
+  if (c->m2l_prep_done) FMM_CUDA(c, cudaStreamWaitEvent(s, c->ev_prep, 0));  // svd_tree_setup ran beside
+  else FMM_TRY(svd_tree_setup(c, s));
   const int up = p.ntiles * p.ngroups;
+  // schedules 2 and 3 start the near field with the projection: three
+  // pipeline stages instead of four leave shared memory for P2P blocks on
+  // every SM beside the projection's CTA
+  const bool near_with_proj = c->timing != 2 && c->p2p_priority && c->p2p_sched >= 2;
+  if (near_with_proj) {
+    p.nst = std::min(p.nst, 3);
+    FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
+    c->p2p_after_proj = true;
+  }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[9], s, cudaEventRecordExternal));
   if (f16)
     k_svd_proj_tc<true><<<std::min(up, c->num_sms), SP_THREADS, sp_smem(p.nst), s>>>(p, c->lv);
@@ -1435,6 +1468,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     e.nh = cp / e.nhalf;
     e.cpad = cp;
     e.nst = x_nst(cp);
+    if (near_with_proj && c->p2p_sched == 3) e.nst = 2;  // room for P2P blocks beside the expansion too
     e.chain = x_chain(c);
     e.uscale = c->svd_uscale;
     e.wait_ns = c->wait_ns;
@@ -1443,7 +1477,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
     c->svd_x_groups = e.ngroups;
     const int ue = e.ngroups * c->ntiles * e.nh;
     if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[11], s, cudaEventRecordExternal));
-    if (c->timing != 2 && c->p2p_priority) {
+    if (c->timing != 2 && c->p2p_priority && !near_with_proj) {
       FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
       c->p2p_after_proj = true;
     }
@@ -1482,7 +1516,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   // the P2P branch is released here: its blocks and the expansion's CTAs
   // become ready together and the expansion's (higher launch priority) are
   // placed first, one per SM, with P2P blocks in the room beside them
-  if (c->timing != 2 && c->p2p_priority) {
+  if (c->timing != 2 && c->p2p_priority && !near_with_proj) {
     FMM_CUDA(c, cudaEventRecord(c->ev_p2p, s));
     c->p2p_after_proj = true;
   }

@@ -24,7 +24,7 @@
 // accuracy however small it is, also across leaf faces (a plain FP32
 // position would carry up to 2^-25 leaf widths of error, which dominates the
 // force of a particle with a very close neighbour).
-// 1/r by rsqrtf; per-chunk FP32 sums are added into FP32 totals with Kahan
+// 1/r by the MUFU rsqrt approximation; per-chunk FP32 sums are added into FP32 totals with Kahan
 // compensation; results are scaled by 1/w (phi) and 1/w^2 (F) at the end.
 // Sources are staged with the target's own leaf first: only those can hold
 // the particle itself (or a coincident one), so only they need the r > 0
@@ -42,6 +42,17 @@ namespace {
 // staged chunk) is one of the variants below, chosen per handle (fmm_autotune)
 constexpr int P2P_WARPS = 4;
 constexpr int P2P_CH = 256;
+
+// 1/sqrt(x) by the MUFU approximation with denormal inputs flushed: every
+// r^2 that reaches it is 0 (a pair of the target's own leaf, masked after)
+// or far above FP32's normal range (positions are accurate to ~2^-46 leaf
+// widths: distinct particles are at least ~2^-47 apart, r^2 >= 2^-94), so this is what rsqrtf
+// computes without its range-scaling instructions for denormal inputs.
+__device__ __forceinline__ float rsqrt_nf(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 struct Kahan {
   float s = 0.f, c = 0.f;
@@ -68,7 +79,7 @@ __device__ __forceinline__ void p2p_span(const float4* __restrict__ shi, const f
     const float dy = (th.y - sh.y) + (tl.y - sl.y);
     const float dz = (th.z - sh.z) + (tl.z - sl.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float inv = rsqrtf(r2);
+    float inv = rsqrt_nf(r2);
     if (SELF) inv = r2 > 0.f ? inv : 0.f;
     const float qi = sh.w * inv;
     const float qi3 = qi * inv * inv;
@@ -292,7 +303,7 @@ __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, con
       qi = f2mul(b.y, f2pack(p0, p1));
       qi3 = f2mul(f2mul(qi, gk.sk), f2pack(e0, e1));
     } else {
-      float i0 = rsqrtf(rr.x), i1 = rsqrtf(rr.y);
+      float i0 = rsqrt_nf(rr.x), i1 = rsqrt_nf(rr.y);
       if (SELF) {
         i0 = rr.x > 0.f ? i0 : 0.f;
         i1 = rr.y > 0.f ? i1 : 0.f;
@@ -673,7 +684,7 @@ __device__ __forceinline__ void p2p_span_stokes(const float4* __restrict__ shi, 
     const float dy = (th.y - sh.y) + (tl.y - sl.y);
     const float dz = (th.z - sh.z) + (tl.z - sl.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float inv = rsqrtf(r2);
+    float inv = rsqrt_nf(r2);
     if (SELF) inv = r2 > 0.f ? inv : 0.f;
     const float t = fmaf(dx, sf.x, fmaf(dy, sf.y, dz * sf.z)) * (inv * inv * inv);
     ux = fmaf(sf.x, inv, fmaf(dx, t, ux));

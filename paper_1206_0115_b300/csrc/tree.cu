@@ -804,11 +804,82 @@ __global__ void k_unit_write(const int32_t* __restrict__ nleaf_ptr, int64_t cap,
   }
 }
 
-__global__ void k_grid_set(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ keys,
-                           int32_t* __restrict__ grid, int clear) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= load_n(n_ptr, n_static)) return;
-  grid[keys[i]] = clear ? -1 : (int32_t)i;
+// The dense grids of several levels in one launch: thread i belongs to
+// level l with off[l] <= i < off[l + 1]; cell j = i - off[l] < n_l (n_l from
+// counts[l] on the device, else nstatic[l]) sets grid_l[key_l[j]] to j, or
+// to -1 when clearing the previous tree's entries.
+struct GridSetAll {
+  const uint32_t* key[FMM_MAX_LEVELS];
+  int32_t* grid[FMM_MAX_LEVELS];
+  int64_t off[FMM_MAX_LEVELS + 1];
+  int64_t nstatic[FMM_MAX_LEVELS];
+  const int32_t* counts;  // counters (cells of level l at [l]) or nullptr
+  int nlev, clear;
+};
+
+__global__ void k_grid_set_all(GridSetAll a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.off[a.nlev]) return;
+  int l = 0;
+  while (l + 1 < a.nlev && i >= a.off[l + 1]) ++l;
+  const int64_t j = i - a.off[l];
+  const int64_t n = a.counts ? a.counts[l] : a.nstatic[l];
+  if (j < n) a.grid[l][a.key[l][j]] = a.clear ? -1 : (int32_t)j;
+}
+
+// Levels lhi .. 0 of the tree from the cells of level lhi + 1 (counters[lhi
+// + 1] of them), by one block: per level, the unique prefixes key >> 3 in
+// Morton order (a cell per prefix, first = index of its first child), the
+// parent of every child, the children counts and counters[l].  The upper
+// levels hold few cells, where one launch per step of the multi-block path
+// (count, scan, write, counts) costs more than the work; every step here is
+// the same operation as there.
+constexpr int LU_THREADS = 1024;
+constexpr int64_t LU_MAX_IN = 65536;  // cells of the finest input level handled by one block
+
+__global__ void __launch_bounds__(LU_THREADS) k_levels_upper(LevelPtrs lv, int lhi, int32_t* __restrict__ counters) {
+  __shared__ int ws[LU_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int l = lhi; l >= 0; --l) {
+    const uint32_t* in = lv.key[l + 1];
+    const int nin = *(volatile int32_t*)(counters + l + 1);
+    int nout = 0;
+    for (int c0 = 0; c0 < nin; c0 += LU_THREADS) {
+      const int i = c0 + tid;
+      int flag = 0;
+      uint32_t k = 0;
+      if (i < nin) {
+        k = in[i] >> 3;
+        flag = (i == 0) || (k != (in[i - 1] >> 3));
+      }
+      int incl = flag;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane == 31) ws[w] = incl;
+      __syncthreads();
+      int woff = 0, tot = 0;
+      for (int q = 0; q < LU_THREADS / 32; ++q) {
+        woff += q < w ? ws[q] : 0;
+        tot += ws[q];
+      }
+      const int pos = nout + woff + incl - flag;  // this element's cell when flag, else the next one
+      if (flag) {
+        lv.key[l][pos] = k;
+        lv.first[l][pos] = i;
+      }
+      if (i < nin) lv.parent[l + 1][i] = pos + flag - 1;
+      nout += tot;
+      __syncthreads();  // ws is rewritten by the next chunk
+    }
+    for (int j = tid; j < nout; j += LU_THREADS) {
+      const int e = (j + 1 < nout) ? lv.first[l][j + 1] : nin;
+      lv.count[l][j] = e - lv.first[l][j];
+    }
+    if (tid == 0) counters[l] = nout;
+    __syncthreads();  // this level's cells are the next level's input
+  }
 }
 
 struct ClassArgs {
@@ -942,63 +1013,30 @@ __device__ inline void mask_to_list(const uint32_t* mask, int k, int16_t* out, i
 constexpr int SETUP_BATCH = 7;  // 189 = 27 x 7 independent grid lookups in flight per thread
 static_assert(FMM_NT_CLASS % SETUP_BATCH == 0, "setup batches cover the transfer vectors");
 
-// Per M2L tile: for each of the class's 189 transfer vectors the source cell
-// of every target row (the level's zero row when the source is absent or
-// outside the cube) and the list of transfer vectors with at least one
-// source.  One block of 128 threads (one per target row) per tile; each
-// thread looks its sources up in batches of independent loads, and a warp
-// ballot per transfer vector sets the tile's bit mask.
+// Per M2L tile and each of the class's 189 transfer vectors t: as targets,
+// the source cell S = T + t of every target row (the level's zero row when
+// the source is absent, outside the cube or in another problem) and whether
+// any row has one; as sources, whether any cell S of the tile has a target
+// T = S - t in the tree (the class's source list src_t).  Block (tile,
+// chunk, side) looks up SETUP_SPLIT_K transfer vectors for the tile's 128
+// rows in batches of independent loads, a warp ballot per transfer vector
+// sets the block's bits, and the block ORs them into the tile's mask in
+// global memory (zero at launch); k_m2l_setup_lists turns the masks into
+// the ordered lists of active transfer vectors.
+constexpr int SETUP_SPLIT_K = 3 * SETUP_BATCH;
+constexpr int SETUP_SPLIT = FMM_NT_CLASS / SETUP_SPLIT_K;
+constexpr int SETUP_WORDS = (FMM_NT_CLASS + 31) / 32;
+static_assert(FMM_NT_CLASS % SETUP_SPLIT_K == 0, "setup chunks cover the transfer vectors");
+
 __global__ void __launch_bounds__(FMM_TILE)
-k_m2l_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ cls_t,
-            const int8_t* __restrict__ tvec, int32_t* __restrict__ tile_src,
-            int16_t* __restrict__ tile_act, int32_t* __restrict__ tile_nact) {
+k_m2l_setup_split(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ cls_t,
+                  const int16_t* __restrict__ src_t, const int8_t* __restrict__ tvec, int32_t* __restrict__ tile_src,
+                  uint32_t* __restrict__ masks) {
   const Tile tl = tiles[blockIdx.x];
+  const int side = blockIdx.z, kb = blockIdx.y * SETUP_SPLIT_K;
   const int l = tl.level, row = threadIdx.x, lane = row & 31;
   const bool valid = row < tl.count;
   const int zero_row = lv.ncell[l];
-  int ix = 0, iy = 0, iz = 0, mine = 0;
-  if (valid) {
-    int cell = lv.cls[l][tl.first + row];
-    demorton3(lv.key[l][cell], ix, iy, iz);
-    mine = problem_of(lv, l, cell);
-  }
-  const int top = (1 << l) - 1;
-  __shared__ uint32_t mask[(FMM_NT_CLASS + 31) / 32];
-  if (row < (FMM_NT_CLASS + 31) / 32) mask[row] = 0u;
-  __syncthreads();
-  int32_t* out = tile_src + (int64_t)blockIdx.x * FMM_NT_CLASS * FMM_TILE + row;
-  for (int k0 = 0; k0 < FMM_NT_CLASS; k0 += SETUP_BATCH) {
-    int g[SETUP_BATCH];
-#pragma unroll
-    for (int j = 0; j < SETUP_BATCH; ++j) {
-      const int slot = cls_t[tl.cls * FMM_NT_CLASS + k0 + j];
-      const int sx = ix + tvec[3 * slot], sy = iy + tvec[3 * slot + 1], sz = iz + tvec[3 * slot + 2];
-      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top)
-                 ? lv.grid[l][morton3(sx, sy, sz)]
-                 : -1;
-    }
-#pragma unroll
-    for (int j = 0; j < SETUP_BATCH; ++j) {
-      const int src = (g[j] >= 0 && same_problem(lv, l, mine, g[j])) ? g[j] : zero_row;
-      out[(int64_t)(k0 + j) * FMM_TILE] = src;
-      const uint32_t any = __ballot_sync(0xffffffffu, src != zero_row);
-      if (lane == 0 && any) atomicOr(&mask[(k0 + j) >> 5], 1u << ((k0 + j) & 31));
-    }
-  }
-  __syncthreads();
-  for (int k = row; k < FMM_TILE * 2; k += FMM_TILE)
-    mask_to_list(mask, k, tile_act + (int64_t)blockIdx.x * FMM_NT_CLASS, tile_nact + blockIdx.x);
-}
-
-// The same for the tile's cells as sources: the transfer vectors of the
-// class's source list (src_t) for which at least one cell S of the tile has a
-// target T = S - t in the tree.
-__global__ void __launch_bounds__(FMM_TILE)
-k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __restrict__ src_t,
-                const int8_t* __restrict__ tvec, int16_t* __restrict__ src_act, int32_t* __restrict__ src_nact) {
-  const Tile tl = tiles[blockIdx.x];
-  const int l = tl.level, row = threadIdx.x, lane = row & 31;
-  const bool valid = row < tl.count;
   int ix = 0, iy = 0, iz = 0, mine = 0;
   if (valid) {
     const int cell = lv.cls[l][tl.first + row];
@@ -1006,29 +1044,47 @@ k_m2l_src_setup(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* __r
     mine = problem_of(lv, l, cell);
   }
   const int top = (1 << l) - 1;
-  __shared__ uint32_t mask[(FMM_NT_CLASS + 31) / 32];
-  if (row < (FMM_NT_CLASS + 31) / 32) mask[row] = 0u;
+  const int sgn = side == 0 ? 1 : -1;  // targets look at S = T + t, sources at T = S - t
+  const int16_t* list = side == 0 ? cls_t : src_t;
+  __shared__ uint32_t mask[SETUP_WORDS];
+  if (row < SETUP_WORDS) mask[row] = 0u;
   __syncthreads();
-  for (int k0 = 0; k0 < FMM_NT_CLASS; k0 += SETUP_BATCH) {
+  int32_t* out = tile_src + (int64_t)blockIdx.x * FMM_NT_CLASS * FMM_TILE + row;
+  for (int k0 = kb; k0 < kb + SETUP_SPLIT_K; k0 += SETUP_BATCH) {
     int g[SETUP_BATCH];
 #pragma unroll
     for (int j = 0; j < SETUP_BATCH; ++j) {
-      const int slot = src_t[tl.cls * FMM_NT_CLASS + k0 + j];
-      const int tx = ix - tvec[3 * slot], ty = iy - tvec[3 * slot + 1], tz = iz - tvec[3 * slot + 2];
-      g[j] = (valid && tx >= 0 && ty >= 0 && tz >= 0 && tx <= top && ty <= top && tz <= top)
-                 ? lv.grid[l][morton3(tx, ty, tz)]
+      const int slot = list[tl.cls * FMM_NT_CLASS + k0 + j];
+      const int sx = ix + sgn * tvec[3 * slot], sy = iy + sgn * tvec[3 * slot + 1], sz = iz + sgn * tvec[3 * slot + 2];
+      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top)
+                 ? lv.grid[l][morton3(sx, sy, sz)]
                  : -1;
     }
 #pragma unroll
     for (int j = 0; j < SETUP_BATCH; ++j) {
       const bool has = g[j] >= 0 && same_problem(lv, l, mine, g[j]);
+      if (side == 0) out[(int64_t)(k0 + j) * FMM_TILE] = has ? g[j] : zero_row;
       const uint32_t any = __ballot_sync(0xffffffffu, has);
       if (lane == 0 && any) atomicOr(&mask[(k0 + j) >> 5], 1u << ((k0 + j) & 31));
     }
   }
   __syncthreads();
-  for (int k = row; k < FMM_TILE * 2; k += FMM_TILE)
-    mask_to_list(mask, k, src_act + (int64_t)blockIdx.x * FMM_NT_CLASS, src_nact + blockIdx.x);
+  if (row < SETUP_WORDS && mask[row])
+    atomicOr(&masks[((int64_t)side * gridDim.x + blockIdx.x) * SETUP_WORDS + row], mask[row]);
+}
+
+__global__ void __launch_bounds__(2 * FMM_TILE)
+k_m2l_setup_lists(const uint32_t* __restrict__ masks, int ntiles, int16_t* __restrict__ tile_act,
+                  int32_t* __restrict__ tile_nact, int16_t* __restrict__ src_act, int32_t* __restrict__ src_nact) {
+  const int side = blockIdx.y;
+  __shared__ uint32_t mask[SETUP_WORDS];
+  if (threadIdx.x < SETUP_WORDS)
+    mask[threadIdx.x] = masks[((int64_t)side * ntiles + blockIdx.x) * SETUP_WORDS + threadIdx.x];
+  __syncthreads();
+  if (side == 0)
+    mask_to_list(mask, threadIdx.x, tile_act + (int64_t)blockIdx.x * FMM_NT_CLASS, tile_nact + blockIdx.x);
+  else
+    mask_to_list(mask, threadIdx.x, src_act + (int64_t)blockIdx.x * FMM_NT_CLASS, src_nact + blockIdx.x);
 }
 
 __global__ void k_zero_rows(int nrows, const int64_t* __restrict__ rows, int cpad, float* a, float* b,
@@ -1512,6 +1568,7 @@ void release_tree(Ctx* c) {
   rel(c->tile_nact, sizeof(int32_t) * tc);
   rel(c->src_act, sizeof(int16_t) * tc * FMM_NT_CLASS);
   rel(c->src_nact, sizeof(int32_t) * tc);
+  rel(c->tile_mask, sizeof(uint32_t) * 2 * SETUP_WORDS * tc);
   c->tiles_cap = 0;
   c->ntiles = c->leaf_tiles = 0;
   c->tiles_h.clear();
@@ -1549,14 +1606,22 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   c->loaded = false;
   FMM_TRY(ensure_particles(c, n > 0 ? n : 1));
 
-  // forget the previous tree in the dense grids
+  // forget the previous tree in the dense grids (every level in one launch)
   if (c->have_prev) {
-    for (int l = 0; l <= c->prev_leaf; ++l)
-      if (c->prev_ncell[l] > 0) {
-        k_grid_set<<<ceil_div(c->prev_ncell[l], 256), 256, 0, s>>>(nullptr, c->prev_ncell[l], c->lv.key[l],
-                                                                   c->lv.grid[l], 1);
-        c->launches_set++;
-      }
+    GridSetAll ga{};
+    ga.nlev = c->prev_leaf + 1;
+    ga.clear = 1;
+    ga.off[0] = 0;
+    for (int l = 0; l < ga.nlev; ++l) {
+      ga.key[l] = c->lv.key[l];
+      ga.grid[l] = c->lv.grid[l];
+      ga.nstatic[l] = c->prev_ncell[l];
+      ga.off[l + 1] = ga.off[l] + c->prev_ncell[l];
+    }
+    if (ga.off[ga.nlev] > 0) {
+      k_grid_set_all<<<ceil_div(ga.off[ga.nlev], 256), 256, 0, s>>>(ga);
+      c->launches_set++;
+    }
     c->have_prev = false;
   }
   c->prev_leaf = Lf;
@@ -1680,12 +1745,29 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, c->perm, c->pos64, c->pos32,
                                                 c->pos32lo);
     c->launches_set++;
-    // levels
+    // levels: the leaf cells from the particles, the levels above from the
+    // cells below, by the multi-block path while a level's input may hold
+    // more than LU_MAX_IN cells, the rest in one block
     FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, c->pleaf));
-    for (int l = Lf - 1; l >= 0; --l)
+    int l = Lf - 1;
+    for (; l >= 0 && ub[l + 1] > LU_MAX_IN; --l)
       FMM_TRY(unique_level(c, s, c->counters + l + 1, ub[l + 1], c->lv.key[l + 1], 3, l, c->lv.parent[l + 1]));
-    for (int l = 0; l <= Lf; ++l) {
-      k_grid_set<<<ceil_div(ub[l], 256), 256, 0, s>>>(c->counters + l, ub[l], c->lv.key[l], c->lv.grid[l], 0);
+    if (l >= 0) {
+      k_levels_upper<<<1, LU_THREADS, 0, s>>>(c->lv, l, c->counters);
+      c->launches_set++;
+    }
+    {
+      GridSetAll ga{};
+      ga.nlev = Lf + 1;
+      ga.clear = 0;
+      ga.counts = c->counters;
+      ga.off[0] = 0;
+      for (int k = 0; k <= Lf; ++k) {
+        ga.key[k] = c->lv.key[k];
+        ga.grid[k] = c->lv.grid[k];
+        ga.off[k + 1] = ga.off[k] + ub[k];
+      }
+      k_grid_set_all<<<ceil_div(ga.off[ga.nlev], 256), 256, 0, s>>>(ga);
       c->launches_set++;
     }
     if (c->forest)
@@ -1802,6 +1884,8 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     dfree(c, c->tile_nact, sizeof(int32_t) * (size_t)c->tiles_cap);
     dfree(c, c->src_act, sizeof(int16_t) * (size_t)c->tiles_cap * FMM_NT_CLASS);
     dfree(c, c->src_nact, sizeof(int32_t) * (size_t)c->tiles_cap);
+    dfree(c, c->tile_mask, sizeof(uint32_t) * 2 * SETUP_WORDS * (size_t)c->tiles_cap);
+    c->tile_mask = nullptr;
     c->src_act = nullptr;
     c->src_nact = nullptr;
     c->tiles = nullptr;
@@ -1822,13 +1906,18 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
     c->src_act = (int16_t*)p;
     FMM_TRY(dalloc(c, &p, sizeof(int32_t) * (size_t)cap));
     c->src_nact = (int32_t*)p;
+    FMM_TRY(dalloc(c, &p, sizeof(uint32_t) * 2 * SETUP_WORDS * (size_t)cap));
+    c->tile_mask = (uint32_t*)p;
     c->tiles_cap = cap;
   }
   if (c->ntiles > 0) {
     FMM_CUDA(c, cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s));
-    k_m2l_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->lv, c->cls_t, c->tvec, c->tile_src, c->tile_act,
-                                               c->tile_nact);
-    k_m2l_src_setup<<<c->ntiles, FMM_TILE, 0, s>>>(c->tiles, c->lv, c->src_t, c->tvec, c->src_act, c->src_nact);
+    uint32_t* masks = c->tile_mask;
+    FMM_CUDA(c, cudaMemsetAsync(masks, 0, sizeof(uint32_t) * 2 * SETUP_WORDS * (size_t)c->ntiles, s));
+    k_m2l_setup_split<<<dim3(c->ntiles, SETUP_SPLIT, 2), FMM_TILE, 0, s>>>(c->tiles, c->lv, c->cls_t, c->src_t,
+                                                                           c->tvec, c->tile_src, masks);
+    k_m2l_setup_lists<<<dim3(c->ntiles, 2), 2 * FMM_TILE, 0, s>>>(masks, c->ntiles, c->tile_act, c->tile_nact,
+                                                                   c->src_act, c->src_nact);
     c->launches_set += 2;
   }
   if (rows > 0) {

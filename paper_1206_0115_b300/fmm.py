@@ -22,6 +22,7 @@ FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT =
 FMM_FP64, FMM_MIXED = 0, 1
 FMM_M2L_FULL, FMM_M2L_SVD = 0, 1
 FMM_P2P_VARIANTS = 16
+FMM_SCHED_CANDIDATES = 8
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_STATE",
                 -5: "FMM_ERR_TIMEOUT"}
 
@@ -64,6 +65,8 @@ _SIGS = {
     "fmm_measure_fp32_rate": [_vp],
     "fmm_set_wait_limit": [_vp, C.c_double],
     "fmm_get_p2p_bins": [_vp, _vp, _vp],
+    "fmm_set_schedule": [_vp, C.c_int],
+    "fmm_get_schedule": [_vp, _vp, _vp],
 }
 _SIGS.update({
     "fmm_server_create": [_vp, C.POINTER(_vp)],
@@ -271,6 +274,18 @@ def fmm_get_p2p_bins(h):
     times = np.zeros((2, FMM_P2P_VARIANTS), dtype=np.float32)
     _check(h, lib.fmm_get_p2p_bins(h, _ptr(out), _ptr(times)))
     return out, times
+
+
+def fmm_set_schedule(h, sched: int) -> int:
+    return _check(h, lib.fmm_set_schedule(h, int(sched)))
+
+
+def fmm_get_schedule(h):
+    """(schedule, mean evaluation ms of each candidate of the last autotune)"""
+    sched = np.zeros(1, dtype=np.int32)
+    times = np.zeros(FMM_SCHED_CANDIDATES, dtype=np.float32)
+    _check(h, lib.fmm_get_schedule(h, _ptr(sched), _ptr(times)))
+    return int(sched[0]), times
 
 
 def fmm_set_wait_limit(h, seconds: float) -> int:

@@ -273,11 +273,18 @@ def test_p2p_variants_agree_and_autotune_picks_one(F):
         assert 0 <= choice[0] < F.FMM_P2P_VARIANTS and np.all(times > 0)
         bins, bin_ms = F.fmm_get_p2p_bins(f.h)
         assert bins[2] > 0 and bins[3] > 0, "the batch has small and large leaves"
+        sched, sched_ms = F.fmm_get_schedule(f.h)
+        assert sched in (0, 1, 2, 3) and sched_ms[0] > 0 and sched_ms[1] > 0
+        pick = int(np.argmin(np.where(sched_ms > 0, sched_ms, np.inf)))
+        assert sched == pick % 4
         best = []
         for b in range(2):
             timed = bin_ms[b][bin_ms[b] >= 0]
             assert len(timed) == (F.FMM_P2P_VARIANTS - 2 if b == 0 else F.FMM_P2P_VARIANTS)
-            best.append(int(np.argmin(np.where(bin_ms[b] >= 0, bin_ms[b], np.inf))))
+            ms = np.where(bin_ms[b] >= 0, bin_ms[b], np.inf)
+            if pick >= 4:  # the schedule stage kept the fastest non-persistent shapes
+                ms[[14, 15]] = np.inf
+            best.append(int(np.argmin(ms)))
         # either each bin's fastest shape, or one item shape for both bins
         assert (int(bins[0]), int(bins[1])) == tuple(best) or (int(bins[0]) == int(bins[1]) and int(bins[0]) not in (12, 13))
         assert int(choice[0]) == int(bins[0])

@@ -428,6 +428,51 @@ def test_reload_changes_tree(F):
             assert oracle.rel_l2(Fo, Fr) <= TOL_FP64
 
 
+@pytest.mark.parametrize("variant", [0, 14])
+def test_schedules_agree_bit_for_bit(F, variant):
+    """Where the near-field branch starts in the evaluation graph (with the
+    M2L expansion, at the start beside the upward pass, or with the
+    projection, whose pipelines then run fewer stages) changes the order in
+    which independent kernels run and the depth of the M2L pipelines, not
+    the arithmetic: every schedule gives the same bits, with a block-per-item
+    shape (0) and the persistent shape (14); the autotuner then picks one
+    from timed evaluations and its result agrees too."""
+    import torch
+    xyz, q = inputs.particles(60000, 41, "cube", "sym")
+    n = len(q)
+    res = {}
+    with F.FMM(5, 5, F.FMM_MIXED) as f:
+        f.set_particles(torch.from_numpy(xyz).cuda(), torch.from_numpy(q).cuda())
+        F.fmm_set_p2p_variant(f.h, variant)
+        phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Fo = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        for sched in (0, 1, 2, 3, 0):
+            F.fmm_set_schedule(f.h, sched)
+            assert F.fmm_get_schedule(f.h)[0] == sched
+            f.evaluate(phi, Fo)
+            torch.cuda.synchronize()
+            res.setdefault(sched, []).append((phi.cpu().numpy().copy(), Fo.cpu().numpy().copy()))
+            st = f.stats()
+            assert int(st[2]) == 1 and int(st[6]) == 0, list(st)
+        with pytest.raises(F.FMMError):
+            F.fmm_set_schedule(f.h, 4)
+        F.fmm_autotune(f.h)
+        sched, times = F.fmm_get_schedule(f.h)
+        assert sched in (0, 1, 2, 3) and (times[sched] > 0 or times[4 + sched] > 0)
+        assert np.all(times[:4] > 0)
+        f.evaluate(phi, Fo)
+        torch.cuda.synchronize()
+        tuned = (phi.cpu().numpy(), Fo.cpu().numpy())
+    for a in res[0][1:] + res[1] + res[2] + res[3]:
+        assert np.array_equal(a[0], res[0][0][0]) and np.array_equal(a[1], res[0][0][1])
+    assert oracle.rel_l2(tuned[0], res[0][0][0]) <= 1e-6
+    assert oracle.rel_l2(tuned[1], res[0][0][1]) <= 1e-6
+    with _oracle(xyz, q, 5, 5) as o:
+        rphi, rF = o.evaluate()
+    assert oracle.rel_l2(res[1][0][0], rphi) <= TOL_MIXED
+    assert oracle.rel_l2(res[1][0][1], rF) <= TOL_MIXED
+
+
 def test_evaluate_is_repeatable_and_precision_switch(F):
     xyz, q = inputs.particles(10000, 81, "cube", "sym")
     with F.FMM(4, 5, F.FMM_MIXED) as f:
