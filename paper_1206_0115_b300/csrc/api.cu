@@ -490,8 +490,8 @@ fmm_status fmm_destroy(fmm_handle h) {
   if (c->side) cudaStreamSynchronize(c->side);
   drop_graph(c);
   void* bufs[] = {c->key_a, c->key_b, c->idx_a, c->idx_b, c->perm, c->pleaf, c->pos64, c->pos32, c->pos32lo,
-                  c->p2p_items, c->p2p_bins, c->p2p_small, c->p2p_large,
-                  c->p2p_leaf, c->p2p_units, c->p2p_uoff,
+                  c->p2p_items, c->p2p_small, c->p2p_large,
+                  c->p2p_leaf, c->p2p_units,
                   c->near32,
                   c->near64,
                   c->stage_in, c->stage_out, c->stokes_buf, c->scratch, c->box, c->counters, c->Mhi, c->Mlo, c->L32, c->M64,

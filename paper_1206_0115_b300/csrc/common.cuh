@@ -139,13 +139,10 @@ struct fmm_ctx {
   int32_t* p2p_leaf = nullptr;   // per work item: its leaf
   int64_t p2p_leaf_cap = 0;
   int32_t* p2p_units = nullptr;  // cooperative P2P units: first item of each (up to 8 items of a leaf)
-  int32_t* p2p_uoff = nullptr;   // per leaf: its first unit
   int64_t p2p_units_cap = 0;
   int p2p_nunits = 0;
   int p2p_nitems = 0;
-  // bins by leaf occupancy (P2P_BIG): per leaf its small and large items
-  // (scanned), and the items of each bin
-  unsigned long long* p2p_bins = nullptr;
+  // bins by leaf occupancy (P2P_BIG): the items of each bin
   int32_t* p2p_small = nullptr;
   int32_t* p2p_large = nullptr;
   int p2p_nsmall = 0, p2p_nlarge = 0;

@@ -25,14 +25,13 @@ constexpr int BB_THREADS = 256;
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
-constexpr int U_THREADS = 256;
-constexpr int U_ITEMS = 8;
-constexpr int U_CHUNK = U_THREADS * U_ITEMS;
 constexpr int CNT_BAD = 127;  // counters[] slot of the non-finite-input flag
 constexpr int CNT_CLS = 16;   // counters[16 + 8 l + c] = cells of class c at level l
 constexpr int CNT_ITEMS = 120;  // counters[120] = P2P work items (leaf, 32-target batch)
 constexpr int CNT_UNITS = 121;  // counters[121] = cooperative P2P units (up to 8 items of one leaf)
 constexpr int CNT_BINS = 122;   // counters[122], [123] (one 64-bit word) = P2P items of small / large leaves
+// the work-list totals are 64-bit words: (items, units) and (small, large)
+static_assert(CNT_UNITS == CNT_ITEMS + 1 && CNT_ITEMS % 2 == 0 && CNT_BINS % 2 == 0, "64-bit counter words");
 
 __device__ inline double warp_min(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -276,8 +275,81 @@ __global__ void __launch_bounds__(1024) k_scan1(W* __restrict__ data, int64_t co
   if (t == 1023 && total) *total = part[1023];
 }
 
+// Exclusive prefix of v over the NT threads of a block (warp shuffles,
+// then warp 0 over the NT / 32 warp totals); total = the block's sum.
+// Every thread of the block calls it; ws: NT / 32 words of shared memory.
+template <int NT, typename W>
+__device__ __forceinline__ W block_excl_scan(W v, W* ws, W& total) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  W incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const W t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) ws[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    W y = lane < NW ? ws[lane] : W(0);
+    for (int o = 1; o < 32; o <<= 1) {
+      const W t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    if (lane < NW) ws[lane] = y;
+  }
+  __syncthreads();
+  const W before = w > 0 ? ws[w - 1] : W(0);
+  total = ws[NW - 1];
+  __syncthreads();  // ws is free for the next call
+  return before + incl - v;
+}
+
+// Exclusive scan of data[0..count) in place by one block of 1024 threads,
+// in chunks of 1024 x SB_ITEMS entries (each thread scans SB_ITEMS
+// consecutive ones) with a running carry; the next chunk's loads are issued
+// before the current chunk is scanned.  The total goes to *total (if not
+// NULL).  For counts up to SB_MAX, where the three-pass scan's launches cost
+// more than the work.
+constexpr int SB_ITEMS = 8;
+constexpr int SB_CHUNK = 1024 * SB_ITEMS;
+constexpr int64_t SB_MAX = 16384;
+
+template <typename W>
+__global__ void __launch_bounds__(1024) k_scan_block(W* __restrict__ data, int64_t count, W* total) {
+  __shared__ W ws[32];
+  const int tid = threadIdx.x;
+  W cur[SB_ITEMS], nxt[SB_ITEMS];
+#pragma unroll
+  for (int j = 0; j < SB_ITEMS; ++j) {
+    const int64_t i = (int64_t)tid * SB_ITEMS + j;
+    cur[j] = i < count ? data[i] : W(0);
+  }
+  W carry = 0;
+  for (int64_t c0 = 0; c0 < count; c0 += SB_CHUNK) {
+#pragma unroll
+    for (int j = 0; j < SB_ITEMS; ++j) {
+      const int64_t i = c0 + SB_CHUNK + (int64_t)tid * SB_ITEMS + j;
+      nxt[j] = i < count ? data[i] : W(0);
+    }
+    W sum = 0;
+#pragma unroll
+    for (int j = 0; j < SB_ITEMS; ++j) sum += cur[j];
+    W tot;
+    W run = carry + block_excl_scan<1024>(sum, ws, tot);
+#pragma unroll
+    for (int j = 0; j < SB_ITEMS; ++j) {
+      const int64_t i = c0 + (int64_t)tid * SB_ITEMS + j;
+      if (i < count) data[i] = run;
+      run += cur[j];
+      cur[j] = nxt[j];
+    }
+    carry += tot;
+  }
+  if (tid == 0 && total) *total = carry;
+}
+
 // Exclusive scan of long arrays in three passes: per-block sums of
-// SC_CHUNK-entry chunks (coalesced), k_scan1 over the block sums, and a
+// SC_CHUNK-entry chunks (coalesced), k_scan_block over the block sums, and a
 // per-block scan of each chunk staged through shared memory (coalesced loads
 // and stores; each thread scans SC_ITEMS consecutive entries).
 constexpr int SC_THREADS = 512;
@@ -349,14 +421,14 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_chunks(W* __restrict__ data
 // not NULL).  work: ceil(count / SC_CHUNK) words of scratch.
 template <typename W>
 void scan_excl(cudaStream_t s, W* data, int64_t count, W* total, W* work, int64_t* launches) {
-  if (count <= 4 * SC_CHUNK) {
-    k_scan1<W><<<1, 1024, 0, s>>>(data, count, total);
+  if (count <= SB_MAX) {
+    k_scan_block<W><<<1, 1024, 0, s>>>(data, count, total);
     *launches += 1;
     return;
   }
   const int nb = ceil_div(count, SC_CHUNK);
   k_scan_sums<W><<<nb, SC_THREADS, 0, s>>>(data, count, work);
-  k_scan1<W><<<1, 1024, 0, s>>>(work, nb, total);
+  k_scan_block<W><<<1, 1024, 0, s>>>(work, nb, total);
   k_scan_chunks<W><<<nb, SC_THREADS, 0, s>>>(data, count, work);
   *launches += 3;
 }
@@ -670,139 +742,8 @@ __global__ void k_cell_slot(const int32_t* __restrict__ n_ptr, const uint32_t* _
   out[i] = inside ? k : -1;
 }
 
-// ---- unique prefixes of a sorted key list --------------------------------------
+// ---- tree levels and work lists from the sorted keys -------------------------------
 
-__device__ inline int64_t load_n(const int32_t* p, int64_t s) { return p ? (int64_t)*p : s; }
-
-__device__ inline int block_sum(int v) {
-  __shared__ int ws[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) ws[w] = v;
-  __syncthreads();
-  int t = 0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws[k];
-  return t;
-}
-
-__global__ void __launch_bounds__(U_THREADS)
-k_unique_count(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ in, int shift,
-               int32_t* __restrict__ bsum) {
-  const int64_t n = load_n(n_ptr, n_static);
-  const int64_t base = (int64_t)blockIdx.x * U_CHUNK;
-  int cnt = 0;
-  for (int k = threadIdx.x; k < U_CHUNK; k += U_THREADS) {
-    int64_t i = base + k;
-    if (i < n) cnt += (i == 0) || ((in[i] >> shift) != (in[i - 1] >> shift));
-  }
-  cnt = block_sum(cnt);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = cnt;
-}
-
-// Writes each new prefix (key >> shift) with the index of its first element;
-// parent[i] (optional) receives the output index of element i's prefix.
-__global__ void __launch_bounds__(U_THREADS)
-k_unique_write(const int32_t* n_ptr, int64_t n_static, const uint32_t* __restrict__ in, int shift,
-               const int32_t* __restrict__ boff, uint32_t* __restrict__ out_key,
-               int32_t* __restrict__ out_first, int32_t* __restrict__ parent) {
-  const int64_t n = load_n(n_ptr, n_static);
-  const int64_t base = (int64_t)blockIdx.x * U_CHUNK + (int64_t)threadIdx.x * U_ITEMS;
-  int flags = 0, cnt = 0;
-  for (int k = 0; k < U_ITEMS; ++k) {
-    int64_t i = base + k;
-    int h = (i < n) && ((i == 0) || ((in[i] >> shift) != (in[i - 1] >> shift)));
-    flags |= h << k;
-    cnt += h;
-  }
-  // block-wide exclusive scan of cnt
-  __shared__ int ws[U_THREADS / 32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int incl = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) ws[w] = incl;
-  __syncthreads();
-  int woff = 0;
-  for (int k = 0; k < w; ++k) woff += ws[k];
-  int pos = boff[blockIdx.x] + woff + incl - cnt;
-  for (int k = 0; k < U_ITEMS; ++k) {
-    int64_t i = base + k;
-    if (i >= n) break;
-    if ((flags >> k) & 1) {
-      out_key[pos] = in[i] >> shift;
-      out_first[pos] = (int32_t)i;
-      ++pos;
-    }
-    if (parent) parent[i] = pos - 1;
-  }
-}
-
-__global__ void k_counts(const int32_t* __restrict__ nout_ptr, const int32_t* nin_ptr, int64_t nin_static,
-                         const int32_t* __restrict__ first, int32_t* __restrict__ count) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t nout = *nout_ptr, nin = load_n(nin_ptr, nin_static);
-  if (j >= nout) return;
-  int64_t e = (j + 1 < nout) ? first[j + 1] : nin;
-  count[j] = (int32_t)(e - first[j]);
-}
-
-// Work items of P2P: one per batch of up to 32 targets of a leaf.
-// Slots past the leaf count (up to the capacity bound `cap`) get 0 so the
-// scan over the whole bound yields the right total.
-__global__ void k_p2p_items(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
-                            int32_t* __restrict__ items) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= cap) return;
-  items[j] = j < *nleaf_ptr ? (count[j] + 31) >> 5 : 0;
-}
-
-// Leaf of every P2P work item (items[T] .. items[T] + ceil(count/32) - 1
-// belong to leaf T), so that a warp finds its leaf with one load.
-__global__ void k_item_leaf(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
-                            const int32_t* __restrict__ items, int32_t* __restrict__ leaf_of) {
-  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= cap || T >= *nleaf_ptr) return;
-  const int b = items[T], e = b + ((count[T] + 31) >> 5);
-  for (int i = b; i < e; ++i) leaf_of[i] = (int32_t)T;
-}
-
-// P2P bins by leaf occupancy: the work items of leaves with at most
-// P2P_BIG particles ("small") and of larger leaves ("large") go to two lists,
-// so that each bin runs the near-field shape that suits it (fmm_autotune
-// picks one per bin).  Cooperative P2P units -- up to P2P_UNIT consecutive
-// work items of one leaf -- exist for large leaves only.
-// uoff[T] = units of leaf T; bins[T] = its small items (low word) and large
-// items (high word); both scanned afterwards.  units[u] = first item of u.
-constexpr int P2P_UNIT = 8;
-__global__ void k_unit_count(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
-                             int32_t* __restrict__ uoff, unsigned long long* __restrict__ bins) {
-  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= cap) return;
-  const bool live = T < *nleaf_ptr;
-  const int ni = live ? (count[T] + 31) >> 5 : 0;
-  const bool big = live && count[T] > P2P_BIG;
-  uoff[T] = big ? (ni + P2P_UNIT - 1) / P2P_UNIT : 0;
-  bins[T] = big ? (unsigned long long)ni << 32 : (unsigned long long)ni;
-}
-__global__ void k_unit_write(const int32_t* __restrict__ nleaf_ptr, int64_t cap, const int32_t* __restrict__ count,
-                             const int32_t* __restrict__ items, const int32_t* __restrict__ uoff,
-                             const unsigned long long* __restrict__ bins, int32_t* __restrict__ units,
-                             int32_t* __restrict__ small, int32_t* __restrict__ large) {
-  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= cap || T >= *nleaf_ptr) return;
-  const int ni = (count[T] + 31) >> 5;
-  if (count[T] > P2P_BIG) {
-    for (int k = 0; k * P2P_UNIT < ni; ++k) units[uoff[T] + k] = items[T] + k * P2P_UNIT;
-    const int o = (int)(bins[T] >> 32);
-    for (int k = 0; k < ni; ++k) large[o + k] = items[T] + k;
-  } else {
-    const int o = (int)(bins[T] & 0xffffffffull);
-    for (int k = 0; k < ni; ++k) small[o + k] = items[T] + k;
-  }
-}
 
 // The dense grids of several levels in one launch: thread i belongs to
 // level l with off[l] <= i < off[l + 1]; cell j = i - off[l] < n_l (n_l from
@@ -827,58 +768,235 @@ __global__ void k_grid_set_all(GridSetAll a) {
   if (j < n) a.grid[l][a.key[l][j]] = a.clear ? -1 : (int32_t)j;
 }
 
-// Levels lhi .. 0 of the tree from the cells of level lhi + 1 (counters[lhi
-// + 1] of them), by one block: per level, the unique prefixes key >> 3 in
-// Morton order (a cell per prefix, first = index of its first child), the
-// parent of every child, the children counts and counters[l].  The upper
-// levels hold few cells, where one launch per step of the multi-block path
-// (count, scan, write, counts) costs more than the work; every step here is
-// the same operation as there.
-constexpr int LU_THREADS = 1024;
-constexpr int64_t LU_MAX_IN = 65536;  // cells of the finest input level handled by one block
+// Every level of the tree from the sorted particle keys in three passes
+// over the particles (in place of one unique pass per level).  Particle i
+// opens a cell at level l when its key differs from particle i - 1's in the
+// bits above 3 (Lf - l); that holds at every level from lmin(i) = Lf -
+// floor(hb / 3) down to the leaves, hb the highest differing bit (lmin = 0
+// for i = 0, none when the keys are equal).
+//  1. k_lv_count: per block of LV_TILE particles, the cells it opens at
+//     each level, level-major: sums[l * nb + b];
+//  2. one exclusive scan of sums (per-level offsets are differences);
+//  3. k_lv_write: each opening particle's cell index per level, with the
+//     cell's key (key >> 3 (Lf - l)), first (the particle at the leaves, the
+//     first child's index above), parent (the cell of the level above that
+//     holds the particle), every particle's leaf (pleaf) and counters[l].
+// k_lv_counts then derives the children (or particle) counts.  The results
+// are those of a unique pass per level, the same cells in Morton order.
+constexpr int LV_THREADS = 256;
+constexpr int LV_ITEMS = 8;
+constexpr int LV_TILE = LV_THREADS * LV_ITEMS;
+constexpr int LV_WORDS = 3;  // 16-bit fields, 4 levels per word: up to 12 levels
+static_assert(FMM_MAX_LEVELS <= 4 * LV_WORDS, "a field per level");
 
-__global__ void __launch_bounds__(LU_THREADS) k_levels_upper(LevelPtrs lv, int lhi, int32_t* __restrict__ counters) {
-  __shared__ int ws[LU_THREADS / 32];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int l = lhi; l >= 0; --l) {
-    const uint32_t* in = lv.key[l + 1];
-    const int nin = *(volatile int32_t*)(counters + l + 1);
-    int nout = 0;
-    for (int c0 = 0; c0 < nin; c0 += LU_THREADS) {
-      const int i = c0 + tid;
-      int flag = 0;
-      uint32_t k = 0;
-      if (i < nin) {
-        k = in[i] >> 3;
-        flag = (i == 0) || (k != (in[i - 1] >> 3));
-      }
-      int incl = flag;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      if (lane == 31) ws[w] = incl;
-      __syncthreads();
-      int woff = 0, tot = 0;
-      for (int q = 0; q < LU_THREADS / 32; ++q) {
-        woff += q < w ? ws[q] : 0;
-        tot += ws[q];
-      }
-      const int pos = nout + woff + incl - flag;  // this element's cell when flag, else the next one
-      if (flag) {
-        lv.key[l][pos] = k;
-        lv.first[l][pos] = i;
-      }
-      if (i < nin) lv.parent[l + 1][i] = pos + flag - 1;
-      nout += tot;
-      __syncthreads();  // ws is rewritten by the next chunk
+__device__ __forceinline__ int lv_open_level(const uint32_t* __restrict__ key, int64_t i, int Lf) {
+  if (i == 0) return 0;
+  const uint32_t d = key[i] ^ key[i - 1];
+  if (d == 0) return Lf + 1;
+  const int hb = 31 - __clz(d);
+  const int l = Lf - hb / 3;
+  return l < 0 ? 0 : l;
+}
+
+__global__ void __launch_bounds__(LV_THREADS)
+k_lv_count(int64_t n, const uint32_t* __restrict__ key, int Lf, int32_t* __restrict__ sums) {
+  __shared__ int cnt[FMM_MAX_LEVELS];
+  if (threadIdx.x < FMM_MAX_LEVELS) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int c[FMM_MAX_LEVELS];
+  for (int l = 0; l <= Lf; ++l) c[l] = 0;
+  const int64_t i0 = (int64_t)blockIdx.x * LV_TILE;
+  for (int k = threadIdx.x; k < LV_TILE; k += LV_THREADS) {
+    const int64_t i = i0 + k;
+    if (i >= n) break;
+    const int lo = lv_open_level(key, i, Lf);
+    for (int l = lo; l <= Lf; ++l) c[l]++;
+  }
+  for (int l = 0; l <= Lf; ++l) {
+    int v = c[l];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&cnt[l], v);
+  }
+  __syncthreads();
+  if (threadIdx.x <= Lf) sums[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// LevelOut: the per-level arrays written by k_lv_write.
+struct LevelOut {
+  uint32_t* key[FMM_MAX_LEVELS];
+  int32_t* first[FMM_MAX_LEVELS];
+  int32_t* parent[FMM_MAX_LEVELS];
+};
+
+__global__ void __launch_bounds__(LV_THREADS)
+k_lv_write(int64_t n, const uint32_t* __restrict__ key, int Lf, const int32_t* __restrict__ sums,
+           const int32_t* __restrict__ total, LevelOut out, int32_t* __restrict__ pleaf, int32_t* __restrict__ counters) {
+  __shared__ unsigned long long ws[LV_THREADS / 32];
+  __shared__ int base[FMM_MAX_LEVELS];
+  const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  if (tid <= Lf) {
+    const int s0 = sums[(int64_t)tid * nb];
+    base[tid] = sums[(int64_t)tid * nb + b] - s0;
+    if (b == 0) counters[tid] = (tid < Lf ? sums[(int64_t)(tid + 1) * nb] : *total) - s0;
+  }
+  // this thread's particles and the level at which each opens cells
+  const int64_t i0 = (int64_t)b * LV_TILE + (int64_t)tid * LV_ITEMS;
+  int lo[LV_ITEMS];
+  unsigned long long w[LV_WORDS] = {0ull, 0ull, 0ull};
+#pragma unroll
+  for (int j = 0; j < LV_ITEMS; ++j) {
+    const int64_t i = i0 + j;
+    lo[j] = i < n ? lv_open_level(key, i, Lf) : Lf + 1;
+    for (int l = lo[j]; l <= Lf; ++l) w[l >> 2] += 1ull << (16 * (l & 3));
+  }
+  unsigned long long pre[LV_WORDS];
+#pragma unroll
+  for (int q = 0; q < LV_WORDS; ++q) {
+    unsigned long long t;
+    pre[q] = block_excl_scan<LV_THREADS>(w[q], ws, t);
+  }
+  // run[l]: cells of level l opened before this particle (a running index)
+  int run[FMM_MAX_LEVELS];
+  for (int l = 0; l <= Lf; ++l) run[l] = base[l] + (int)((pre[l >> 2] >> (16 * (l & 3))) & 0xffffull);
+#pragma unroll
+  for (int j = 0; j < LV_ITEMS; ++j) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const uint32_t k = key[i];
+    for (int l = lo[j]; l <= Lf; ++l) ++run[l];  // run[l] - 1: the level-l cell holding i
+    for (int l = Lf; l >= lo[j]; --l) {
+      const int cell = run[l] - 1;
+      out.key[l][cell] = k >> (3 * (Lf - l));
+      out.first[l][cell] = l == Lf ? (int32_t)i : run[l + 1] - 1;
+      if (l >= 1) out.parent[l][cell] = run[l - 1] - 1;
     }
-    for (int j = tid; j < nout; j += LU_THREADS) {
-      const int e = (j + 1 < nout) ? lv.first[l][j + 1] : nin;
-      lv.count[l][j] = e - lv.first[l][j];
+    pleaf[i] = run[Lf] - 1;
+  }
+}
+
+// Children (particles at the leaves) per cell, every level in one launch:
+// thread t belongs to level l with off[l] <= t < off[l + 1].
+struct LevelCounts {
+  const int32_t* first[FMM_MAX_LEVELS];
+  int32_t* count[FMM_MAX_LEVELS];
+  int64_t off[FMM_MAX_LEVELS + 1];
+  int64_t n;
+  int nlev;
+};
+
+__global__ void k_lv_counts(LevelCounts a, const int32_t* __restrict__ counters) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.off[a.nlev]) return;
+  int l = 0;
+  while (l + 1 < a.nlev && t >= a.off[l + 1]) ++l;
+  const int64_t c = t - a.off[l];
+  const int nc = counters[l];
+  if (c >= nc) return;
+  const int64_t e = c + 1 < nc ? a.first[l][c + 1] : (l + 1 == a.nlev ? a.n : counters[l + 1]);
+  a.count[l][c] = (int32_t)(e - a.first[l][c]);
+}
+
+// The near field's work lists of the leaves (in place of k_p2p_items,
+// k_item_leaf, k_unit_count, k_unit_write and their three scans, with the
+// same results): per leaf T its first work item items[T] (one item per 32
+// targets), the leaf of every item, the cooperative units of large leaves
+// (more than P2P_BIG particles; up to P2P_UNIT items each) and the two
+// bins' item lists.  Two 64-bit sums per leaf -- (items | units << 32) and
+// (small items | large items << 32) -- are scanned: k_lw_count sums them per
+// block of LW_TILE leaves, two scans of the block sums give the blocks'
+// offsets and the totals (the 64-bit words at counters[CNT_ITEMS] and
+// [CNT_BINS]), and k_lw_write scans inside each block and writes the lists.
+constexpr int P2P_UNIT = 8;  // work items per cooperative unit (the near field's leaf-cooperative shapes)
+constexpr int LW_THREADS = 256;
+constexpr int LW_ITEMS = 4;
+constexpr int LW_TILE = LW_THREADS * LW_ITEMS;
+
+__device__ __forceinline__ void lw_leaf(const int32_t* __restrict__ count, int T, int nleaf, int& ni, bool& big,
+                                        unsigned long long& iu, unsigned long long& sl) {
+  const int cn = T < nleaf ? count[T] : 0;
+  ni = (cn + 31) >> 5;
+  big = cn > P2P_BIG;
+  const unsigned long long nu = big ? (unsigned long long)((ni + P2P_UNIT - 1) / P2P_UNIT) : 0ull;
+  iu = (unsigned long long)ni | (nu << 32);
+  sl = big ? (unsigned long long)ni << 32 : (unsigned long long)ni;
+}
+
+__global__ void __launch_bounds__(LW_THREADS)
+k_lw_count(const int32_t* __restrict__ nleaf_ptr, const int32_t* __restrict__ count,
+           unsigned long long* __restrict__ sums) {
+  const int nleaf = *nleaf_ptr, nb = gridDim.x;
+  unsigned long long iu = 0, sl = 0;
+  for (int k = threadIdx.x; k < LW_TILE; k += LW_THREADS) {
+    const int T = blockIdx.x * LW_TILE + k;
+    int ni;
+    bool big;
+    unsigned long long a, b;
+    lw_leaf(count, T, nleaf, ni, big, a, b);
+    iu += a;
+    sl += b;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    iu += __shfl_xor_sync(0xffffffffu, iu, o);
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+  }
+  __shared__ unsigned long long w0[LW_THREADS / 32], w1[LW_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) {
+    w0[threadIdx.x >> 5] = iu;
+    w1[threadIdx.x >> 5] = sl;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t0 = 0, t1 = 0;
+    for (int q = 0; q < LW_THREADS / 32; ++q) {
+      t0 += w0[q];
+      t1 += w1[q];
     }
-    if (tid == 0) counters[l] = nout;
-    __syncthreads();  // this level's cells are the next level's input
+    sums[blockIdx.x] = t0;
+    sums[nb + blockIdx.x] = t1;
+  }
+}
+
+__global__ void __launch_bounds__(LW_THREADS)
+k_lw_write(const int32_t* __restrict__ nleaf_ptr, const int32_t* __restrict__ count,
+           const unsigned long long* __restrict__ sums, int32_t* __restrict__ items, int32_t* __restrict__ leaf_of,
+           int32_t* __restrict__ units, int32_t* __restrict__ small, int32_t* __restrict__ large) {
+  __shared__ unsigned long long ws[LW_THREADS / 32];
+  const int nleaf = *nleaf_ptr, nb = gridDim.x;
+  if (blockIdx.x * LW_TILE >= nleaf) return;  // the whole block (uniform)
+  const int t0 = blockIdx.x * LW_TILE + threadIdx.x * LW_ITEMS;
+  int ni[LW_ITEMS];
+  bool big[LW_ITEMS];
+  unsigned long long iu = 0, sl = 0;
+#pragma unroll
+  for (int j = 0; j < LW_ITEMS; ++j) {
+    unsigned long long a, b;
+    lw_leaf(count, t0 + j, nleaf, ni[j], big[j], a, b);
+    iu += a;
+    sl += b;
+  }
+  unsigned long long tt;
+  unsigned long long piu = sums[blockIdx.x] + block_excl_scan<LW_THREADS>(iu, ws, tt);
+  unsigned long long psl = sums[nb + blockIdx.x] + block_excl_scan<LW_THREADS>(sl, ws, tt);
+#pragma unroll
+  for (int j = 0; j < LW_ITEMS; ++j) {
+    const int T = t0 + j;
+    if (T >= nleaf) break;
+    const int it = (int)(piu & 0xffffffffull), uo = (int)(piu >> 32);
+    items[T] = it;
+    for (int k = 0; k < ni[j]; ++k) leaf_of[it + k] = T;
+    if (big[j]) {
+      const int nu = (ni[j] + P2P_UNIT - 1) / P2P_UNIT;
+      for (int k = 0; k < nu; ++k) units[uo + k] = it + k * P2P_UNIT;
+      const int o = (int)(psl >> 32);
+      for (int k = 0; k < ni[j]; ++k) large[o + k] = it + k;
+      piu += (unsigned long long)ni[j] | ((unsigned long long)nu << 32);
+      psl += (unsigned long long)ni[j] << 32;
+    } else {
+      const int o = (int)(psl & 0xffffffffull);
+      for (int k = 0; k < ni[j]; ++k) small[o + k] = it + k;
+      piu += (unsigned long long)ni[j];
+      psl += (unsigned long long)ni[j];
+    }
   }
 }
 
@@ -1179,22 +1297,6 @@ fmm_status ensure_grids(Ctx* c, int Lf) {
   return FMM_OK;
 }
 
-// unique prefixes of in[0..n) (n from n_ptr on the device, bounded by n_ub)
-fmm_status unique_level(Ctx* c, cudaStream_t s, const int32_t* n_ptr, int64_t n_ub, const uint32_t* in,
-                        int shift, int lout, int32_t* parent) {
-  if (n_ub <= 0) return FMM_OK;
-  int nb = ceil_div(n_ub, U_CHUNK);
-  int32_t* bsum = (int32_t*)c->scratch;
-  k_unique_count<<<nb, U_THREADS, 0, s>>>(n_ptr, n_ub, in, shift, bsum);
-  k_scan1<int32_t><<<1, 1024, 0, s>>>(bsum, nb, c->counters + lout);
-  k_unique_write<<<nb, U_THREADS, 0, s>>>(n_ptr, n_ub, in, shift, bsum, c->lv.key[lout], c->lv.first[lout],
-                                          parent);
-  int64_t out_ub = n_ub < pow8(lout) ? n_ub : pow8(lout);
-  k_counts<<<ceil_div(out_ub, 256), 256, 0, s>>>(c->counters + lout, n_ptr, n_ub, c->lv.first[lout],
-                                                 c->lv.count[lout]);
-  c->launches_set += 4;
-  return FMM_OK;
-}
 
 }  // namespace
 
@@ -1524,8 +1626,6 @@ void release_tree(Ctx* c) {
   rel(c->p2p_leaf, 4 * (size_t)c->p2p_leaf_cap);
   c->p2p_leaf_cap = 0;
   rel(c->p2p_units, 4 * (size_t)c->p2p_units_cap);
-  rel(c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
-  rel(c->p2p_bins, 8 * (size_t)c->p2p_units_cap);
   rel(c->p2p_small, 4 * (size_t)c->p2p_units_cap);
   rel(c->p2p_large, 4 * (size_t)c->p2p_units_cap);
   c->p2p_units_cap = 0;
@@ -1659,25 +1759,18 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       c->p2p_leaf = (int32_t*)p;
       c->p2p_leaf_cap = cap;
     }
-    // units: at most one per leaf plus one per 8 items; offsets and bin
-    // offsets: one per leaf; the bins' item lists: at most all items
+    // units: at most one per leaf plus one per 8 items; the bins' item
+    // lists: at most all items
     if (need > c->p2p_units_cap) {
       dfree(c, c->p2p_units, 4 * (size_t)c->p2p_units_cap);
-      dfree(c, c->p2p_uoff, 4 * (size_t)c->p2p_units_cap);
-      dfree(c, c->p2p_bins, 8 * (size_t)c->p2p_units_cap);
       dfree(c, c->p2p_small, 4 * (size_t)c->p2p_units_cap);
       dfree(c, c->p2p_large, 4 * (size_t)c->p2p_units_cap);
-      c->p2p_units = c->p2p_uoff = c->p2p_small = c->p2p_large = nullptr;
-      c->p2p_bins = nullptr;
+      c->p2p_units = c->p2p_small = c->p2p_large = nullptr;
       c->p2p_units_cap = 0;
       void* p;
       const int64_t cap = need + need / 8 + 64;
       FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
       c->p2p_units = (int32_t*)p;
-      FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
-      c->p2p_uoff = (int32_t*)p;
-      FMM_TRY(dalloc(c, &p, 8 * (size_t)cap));
-      c->p2p_bins = (unsigned long long*)p;
       FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
       c->p2p_small = (int32_t*)p;
       FMM_TRY(dalloc(c, &p, 4 * (size_t)cap));
@@ -1745,16 +1838,31 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
       k_gather<<<ceil_div(n, 256), 256, 0, s>>>(n, ka, va, xyz, q, c->box, c->perm, c->pos64, c->pos32,
                                                 c->pos32lo);
     c->launches_set++;
-    // levels: the leaf cells from the particles, the levels above from the
-    // cells below, by the multi-block path while a level's input may hold
-    // more than LU_MAX_IN cells, the rest in one block
-    FMM_TRY(unique_level(c, s, nullptr, n, ka, 0, Lf, c->pleaf));
-    int l = Lf - 1;
-    for (; l >= 0 && ub[l + 1] > LU_MAX_IN; --l)
-      FMM_TRY(unique_level(c, s, c->counters + l + 1, ub[l + 1], c->lv.key[l + 1], 3, l, c->lv.parent[l + 1]));
-    if (l >= 0) {
-      k_levels_upper<<<1, LU_THREADS, 0, s>>>(c->lv, l, c->counters);
-      c->launches_set++;
+    // every level from the sorted keys (k_lv_count, one scan, k_lv_write),
+    // then the cells' counts
+    {
+      const int nb = ceil_div(n, LV_TILE);
+      const int64_t ns = (int64_t)(Lf + 1) * nb;
+      int32_t* sums = (int32_t*)c->scratch;
+      int32_t* tot = sums + ns;
+      k_lv_count<<<nb, LV_THREADS, 0, s>>>(n, ka, Lf, sums);
+      scan_excl<int32_t>(s, sums, ns, tot, tot + 1, &c->launches_set);
+      LevelOut lo{};
+      LevelCounts lc{};
+      lc.nlev = Lf + 1;
+      lc.n = n;
+      lc.off[0] = 0;
+      for (int k = 0; k <= Lf; ++k) {
+        lo.key[k] = c->lv.key[k];
+        lo.first[k] = c->lv.first[k];
+        lo.parent[k] = c->lv.parent[k];
+        lc.first[k] = c->lv.first[k];
+        lc.count[k] = c->lv.count[k];
+        lc.off[k + 1] = lc.off[k] + ub[k];
+      }
+      k_lv_write<<<nb, LV_THREADS, 0, s>>>(n, ka, Lf, sums, tot, lo, c->pleaf, c->counters);
+      k_lv_counts<<<ceil_div(lc.off[lc.nlev], 256), 256, 0, s>>>(lc, c->counters);
+      c->launches_set += 3;
     }
     {
       GridSetAll ga{};
@@ -1776,20 +1884,21 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
                                                          c->fb_sstart, c->fb_sprob, c->fb_prob, c->slot_buf[l]);
         c->launches_set++;
       }
-    // P2P items: exclusive offsets per leaf, total in counters[CNT_ITEMS]
-    k_p2p_items<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items);
-    scan_excl<int32_t>(s, c->p2p_items, ub[Lf], c->counters + CNT_ITEMS, (int32_t*)c->scratch, &c->launches_set);
-    k_item_leaf<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
-                                                     c->p2p_leaf);
-    k_unit_count<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_uoff,
-                                                      c->p2p_bins);
-    scan_excl<int32_t>(s, c->p2p_uoff, ub[Lf], c->counters + CNT_UNITS, (int32_t*)c->scratch, &c->launches_set);
-    scan_excl<unsigned long long>(s, c->p2p_bins, ub[Lf], (unsigned long long*)(c->counters + CNT_BINS),
-                                  (unsigned long long*)c->scratch, &c->launches_set);
-    k_unit_write<<<ceil_div(ub[Lf], 256), 256, 0, s>>>(c->counters + Lf, ub[Lf], c->lv.count[Lf], c->p2p_items,
-                                                      c->p2p_uoff, c->p2p_bins, c->p2p_units, c->p2p_small,
-                                                      c->p2p_large);
-    c->launches_set += 4;
+    // P2P work lists: per leaf its first item; totals at counters[CNT_ITEMS]
+    // (items | units << 32) and [CNT_BINS] (small | large items << 32)
+    {
+      const int nbw = ceil_div(ub[Lf], LW_TILE);
+      unsigned long long* sums = (unsigned long long*)c->scratch;
+      unsigned long long* work = sums + 2 * (int64_t)nbw;
+      k_lw_count<<<nbw, LW_THREADS, 0, s>>>(c->counters + Lf, c->lv.count[Lf], sums);
+      scan_excl<unsigned long long>(s, sums, nbw, (unsigned long long*)(c->counters + CNT_ITEMS), work,
+                                    &c->launches_set);
+      scan_excl<unsigned long long>(s, sums + nbw, nbw, (unsigned long long*)(c->counters + CNT_BINS), work,
+                                    &c->launches_set);
+      k_lw_write<<<nbw, LW_THREADS, 0, s>>>(c->counters + Lf, c->lv.count[Lf], sums, c->p2p_items, c->p2p_leaf,
+                                            c->p2p_units, c->p2p_small, c->p2p_large);
+      c->launches_set += 2;
+    }
     if (Lf >= 2) {
       ClassArgs ca;
       for (int l = 0; l < FMM_MAX_LEVELS; ++l) {
