@@ -234,6 +234,86 @@ k_p2m_warp(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, co
   }
 }
 
+// Mixed precision, a warp per leaf (4 per block), any leaf size: lanes
+// compute the interpolation weights of up to 32 particles at a time (the
+// charge folded into the x weights) into the warp's shared rows; then lane
+// L owns the (my, mz) pairs L, L + 32, ... and, per particle, adds
+// Sy[my] Sz[mz] q Sx[mx] into its P accumulators per pair -- the multipole
+// as a sum of outer products, M[mx][(my, mz)] = sum_j (q_j Sx_j[mx])
+// (Sy_j[my] Sz_j[mz]), with the particle's x row read once per particle and
+// shared by the lane's pairs.  The results are written per mx row, lanes on
+// consecutive coefficients.
+template <int P>
+__global__ void __launch_bounds__(128)
+k_p2m_pairs(LevelPtrs lv, int leaf, int nleaf, const float* __restrict__ cheb, int cpad,
+            const float4* __restrict__ pos32, float* __restrict__ Mhi, float* __restrict__ Mlo) {
+  constexpr int PP = P * P, NPAIR = (PP + 31) / 32, PX = (P + 3) / 4 * 4;
+  __shared__ __align__(16) float sX[4][32][PX];
+  __shared__ float sY[4][32][P], sZ[4][32][P];
+  __shared__ float sC[P * P];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < P * P; i += 128) sC[i] = cheb[i];
+  __syncthreads();
+  const int cell = blockIdx.x * 4 + warp;
+  if (cell >= nleaf) return;
+  const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
+  int my[NPAIR], mz[NPAIR];
+  bool own[NPAIR];
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    const int pr = lane + 32 * k;
+    own[k] = pr < PP;
+    my[k] = own[k] ? pr / P : 0;
+    mz[k] = own[k] ? pr % P : 0;
+  }
+  float acc[NPAIR][P];
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k)
+#pragma unroll
+    for (int mx = 0; mx < P; ++mx) acc[k][mx] = 0.f;
+  for (int b0 = 0; b0 < cnt; b0 += 32) {
+    const int nb = min(32, cnt - b0);
+    if (lane < nb) {
+      const float4 pp = pos32[first + b0 + lane];
+      float S[P];
+      interp_weights<P, float, false>(sC, 2.f * pp.x, S, nullptr);
+#pragma unroll
+      for (int m = 0; m < PX; ++m) sX[warp][lane][m] = m < P ? pp.w * S[m] : 0.f;
+      interp_weights<P, float, false>(sC, 2.f * pp.y, S, nullptr);
+#pragma unroll
+      for (int m = 0; m < P; ++m) sY[warp][lane][m] = S[m];
+      interp_weights<P, float, false>(sC, 2.f * pp.z, S, nullptr);
+#pragma unroll
+      for (int m = 0; m < P; ++m) sZ[warp][lane][m] = S[m];
+    }
+    __syncwarp();
+    for (int j = 0; j < nb; ++j) {
+      float x[PX];
+#pragma unroll
+      for (int m = 0; m < PX; m += 4) *(float4*)&x[m] = *(const float4*)&sX[warp][j][m];
+#pragma unroll
+      for (int k = 0; k < NPAIR; ++k) {
+        const float w = sY[warp][j][my[k]] * sZ[warp][j][mz[k]];
+#pragma unroll
+        for (int mx = 0; mx < P; ++mx) acc[k][mx] = fmaf(w, x[mx], acc[k][mx]);
+      }
+    }
+    __syncwarp();
+  }
+  const int64_t row = lv.row_off[leaf] + cell;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) {
+    if (!own[k]) continue;
+#pragma unroll
+    for (int mx = 0; mx < P; ++mx) {
+      const int m = mx * PP + lane + 32 * k;
+      const float hi = tf32_rna(acc[k][mx]);
+      Mhi[row * cpad + m] = hi;
+      Mlo[row * cpad + m] = tf32_rna(acc[k][mx] - hi);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- M2M
 
 // Children rows staged together (up to 8, within 16 KB of shared memory, so
@@ -321,6 +401,152 @@ k_m2m(LevelPtrs lv, int l, const T* __restrict__ A, int cpad, const T* __restric
       }
     }
   }
+}
+
+// Mixed precision, one block per parent, every child at once: the three
+// one-dimensional passes of the tensor-product M2M operator run over all
+// children together, and children that differ only in the bit of the axis
+// just transformed are added right after that pass (the operators of the
+// remaining axes do not depend on it): 8 staged children -> z pass, pairs
+// added -> 4 partial sums -> y pass -> 2 -> x pass -> the parent.  Three
+// block barriers per parent instead of three per child; 14 C one-dimensional
+// sums per parent instead of 24 C.
+template <int P>
+constexpr bool m2m_fused_fits() {
+  return (14 * P * P * P + 2 * P * P) * 4 <= 46 * 1024;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+k_m2m_fused(LevelPtrs lv, int l, const float* __restrict__ A, int cpad, float* __restrict__ Mhi,
+            float* __restrict__ Mlo) {
+  constexpr int C = P * P * P, PP = P * P;
+  __shared__ float sA[2 * PP];
+  __shared__ float sin_[8][C];
+  __shared__ float su[4][C];
+  __shared__ float sv[2][C];
+  const int cell = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < 2 * PP; i += 256) sA[i] = A[i];
+  const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
+  __shared__ int slot_of[8];
+  if (tid < 8) slot_of[tid] = -1;
+  __syncthreads();
+  if (tid < nc) slot_of[lv.key[l + 1][c0 + tid] & 7u] = c0 + tid;
+  __syncthreads();
+  for (int e = tid; e < 8 * C; e += 256) {
+    const int b = e / C, m = e - b * C;
+    const int ch = slot_of[b];
+    float v = 0.f;
+    if (ch >= 0) {
+      const int64_t row = lv.row_off[l + 1] + ch;
+      v = Mhi[row * cpad + m] + Mlo[row * cpad + m];
+    }
+    sin_[b][m] = v;
+  }
+  __syncthreads();
+  // z: u[g][x][y][mz] = sum over bit0 and q of Az_bit0[mz][q] in[2 g + bit0][x][y][q]
+  for (int e = tid; e < 4 * C; e += 256) {
+    const int g = e / C, m = e - g * C, xy = m / P, mz = m % P;
+    float s = 0.f;
+#pragma unroll
+    for (int b0 = 0; b0 < 2; ++b0) {
+      const float* Az = sA + b0 * PP + mz * P;
+      const float* in = sin_[2 * g + b0] + xy * P;
+#pragma unroll
+      for (int q = 0; q < P; ++q) s += Az[q] * in[q];
+    }
+    su[g][m] = s;
+  }
+  __syncthreads();
+  // y: v[g][x][my][z] = sum over bit1 and q of Ay_bit1[my][q] u[2 g + bit1][x][q][z]
+  for (int e = tid; e < 2 * C; e += 256) {
+    const int g = e / C, m = e - g * C, x = m / PP, my = (m / P) % P, z = m % P;
+    float s = 0.f;
+#pragma unroll
+    for (int b1 = 0; b1 < 2; ++b1) {
+      const float* Ay = sA + b1 * PP + my * P;
+      const float* u = su[2 * g + b1] + x * PP + z;
+#pragma unroll
+      for (int q = 0; q < P; ++q) s += Ay[q] * u[q * P];
+    }
+    sv[g][m] = s;
+  }
+  __syncthreads();
+  // x: parent[mx][y][z] = sum over bit2 and q of Ax_bit2[mx][q] v[bit2][q][y][z]
+  const int64_t prow = lv.row_off[l] + cell;
+  for (int m = tid; m < C; m += 256) {
+    const int mx = m / PP, yz = m % PP;
+    float s = 0.f;
+#pragma unroll
+    for (int b2 = 0; b2 < 2; ++b2) {
+      const float* Ax = sA + b2 * PP + mx * P;
+      const float* v = sv[b2] + yz;
+#pragma unroll
+      for (int q = 0; q < P; ++q) s += Ax[q] * v[q * PP];
+    }
+    const float hi = tf32_rna(s);
+    Mhi[prow * cpad + m] = hi;
+    Mlo[prow * cpad + m] = tf32_rna(s - hi);
+  }
+}
+
+// Mixed precision L2L, one block per parent, every child at once (the
+// mirror of k_m2m_fused): the parent's deviations through the z pass for
+// both values of a child's z bit (2 arrays), the y pass for both y bits (4),
+// then the x pass straight into each child's row (its own M2L part added);
+// the parent's mean passes to every child unchanged.
+template <int P>
+__global__ void __launch_bounds__(256)
+k_l2l_fused(LevelPtrs lv, int l, const float* __restrict__ A, int cpad, float* __restrict__ Lbuf) {
+  constexpr int C = P * P * P, PP = P * P;
+  __shared__ float sA[2 * PP];
+  __shared__ float sin_[C];
+  __shared__ float su[2][C];
+  __shared__ float sv[4][C];
+  __shared__ int bits[8];
+  const int cell = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < 2 * PP; i += 256) sA[i] = A[i];
+  const int64_t prow = lv.row_off[l] + cell;
+  for (int m = tid; m < C; m += 256) sin_[m] = Lbuf[prow * cpad + m];
+  const float mean = Lbuf[prow * cpad + C];
+  const int c0 = lv.first[l][cell], nc = lv.count[l][cell];
+  if (tid < nc) bits[tid] = (int)(lv.key[l + 1][c0 + tid] & 7u);
+  __syncthreads();
+  // z: u[b0][mx][my][z'] = sum_q Az_b0[q][z'] in[mx][my][q]
+  for (int e = tid; e < 2 * C; e += 256) {
+    const int b0 = e / C, m = e - b0 * C, xy = m / P, zp = m % P;
+    const float* Az = sA + b0 * PP + zp;
+    const float* in = sin_ + xy * P;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < P; ++q) s += Az[q * P] * in[q];
+    su[b0][m] = s;
+  }
+  __syncthreads();
+  // y: v[2 b1 + b0][mx][y'][z'] = sum_q Ay_b1[q][y'] u[b0][mx][q][z']
+  for (int e = tid; e < 4 * C; e += 256) {
+    const int g = e / C, m = e - g * C, x = m / PP, yp = (m / P) % P, z = m % P;
+    const float* Ay = sA + (g >> 1) * PP + yp;
+    const float* u = su[g & 1] + x * PP + z;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < P; ++q) s += Ay[q * P] * u[q * P];
+    sv[g][m] = s;
+  }
+  __syncthreads();
+  // x: L_child[x'][y'][z'] += sum_q Ax_b2[q][x'] v[child's (b1, b0)][q][y'][z']
+  for (int e = tid; e < nc * C; e += 256) {
+    const int k = e / C, m = e - k * C, xp = m / PP, yz = m % PP;
+    const int b = bits[k];
+    const float* Ax = sA + ((b >> 2) & 1) * PP + xp;
+    const float* v = sv[b & 3] + yz;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < P; ++q) s += Ax[q * P] * v[q * PP];
+    const int64_t crow = lv.row_off[l + 1] + c0 + k;
+    Lbuf[crow * cpad + m] += s;
+  }
+  if (tid < nc) Lbuf[(lv.row_off[l + 1] + c0 + tid) * cpad + C] += mean;
 }
 
 // ---------------------------------------------------------------- L2L
@@ -689,15 +915,15 @@ fmm_status upward_p(Ctx* c, cudaStream_t s) {
   const int nleaf = c->lv.ncell[Lf];
   const bool small = 10 * c->n < 6 * 32 * (int64_t)c->p2p_nitems;
   if (c->precision == FMM_MIXED) {
-    if (small)
-      k_p2m_warp<P, float, true><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad,
-                                                                    c->pos64, c->pos32, c->Mhi, c->Mlo);
-    else
-      k_p2m<P, float, true><<<nleaf, 128, 0, s>>>(c->lv, Lf, c->box, c->cheb32, c->cpad, c->pos64, c->pos32, c->Mhi,
-                                                  c->Mlo);
-    for (int l = Lf - 1; l >= 2; --l)
-      k_m2m<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo, c->Mhi,
-                                                           c->Mlo);
+    k_p2m_pairs<P><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->cheb32, c->cpad, c->pos32, c->Mhi,
+                                                      c->Mlo);
+    for (int l = Lf - 1; l >= 2; --l) {
+      if constexpr (m2m_fused_fits<P>())
+        k_m2m_fused<P><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo);
+      else
+        k_m2m<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo, c->Mhi,
+                                                             c->Mlo);
+    }
   } else {
     if (small)
       k_p2m_warp<P, double, false><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->box, c->cheb64, c->cpad,
@@ -715,9 +941,12 @@ fmm_status upward_p(Ctx* c, cudaStream_t s) {
 template <int P>
 fmm_status l2l_p(Ctx* c, cudaStream_t s) {
   for (int l = 2; l <= c->leaf - 1; ++l) {
-    if (c->precision == FMM_MIXED)
-      k_l2l<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->L32);
-    else
+    if (c->precision == FMM_MIXED) {
+      if constexpr (m2m_fused_fits<P>())
+        k_l2l_fused<P><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->L32);
+      else
+        k_l2l<P, float, true><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->L32);
+    } else
       k_l2l<P, double, false><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m64, c->cpad, c->L64);
   }
   return cuda_err(c, cudaGetLastError(), "L2L launch");
