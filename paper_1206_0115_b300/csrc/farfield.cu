@@ -534,17 +534,26 @@ k_l2l_fused(LevelPtrs lv, int l, const float* __restrict__ A, int cpad, float* _
     sv[g][m] = s;
   }
   __syncthreads();
-  // x: L_child[x'][y'][z'] += sum_q Ax_b2[q][x'] v[child's (b1, b0)][q][y'][z']
-  for (int e = tid; e < nc * C; e += 256) {
-    const int k = e / C, m = e - k * C, xp = m / PP, yz = m % PP;
-    const int b = bits[k];
-    const float* Ax = sA + ((b >> 2) & 1) * PP + xp;
-    const float* v = sv[b & 3] + yz;
-    float s = 0.f;
+  // x: L_child[x'][y'][z'] += sum_q Ax_b2[q][x'] v[child's (b1, b0)][q][y'][z']; thread (g, y'z')
+  // holds v[g][.][y'z'] in registers and serves the children of group g = (b1, b0)
+  for (int e = tid; e < 4 * PP; e += 256) {
+    const int g = e / PP, yz = e - g * PP;
+    float vr[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) s += Ax[q * P] * v[q * PP];
-    const int64_t crow = lv.row_off[l + 1] + c0 + k;
-    Lbuf[crow * cpad + m] += s;
+    for (int q = 0; q < P; ++q) vr[q] = sv[g][q * PP + yz];
+    for (int k = 0; k < nc; ++k) {
+      const int b = bits[k];
+      if ((b & 3) != g) continue;
+      const float* Ax = sA + ((b >> 2) & 1) * PP;
+      float* out = Lbuf + (lv.row_off[l + 1] + c0 + k) * cpad + yz;
+#pragma unroll
+      for (int xp = 0; xp < P; ++xp) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < P; ++q) s += Ax[q * P + xp] * vr[q];
+        out[xp * PP] += s;
+      }
+    }
   }
   if (tid < nc) Lbuf[(lv.row_off[l + 1] + c0 + tid) * cpad + C] += mean;
 }
@@ -747,6 +756,110 @@ k_l2p_out(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, con
       l2p_eval<P, T, MIXED>(myL, sC, xi, pf, ax, ay, az);
     }
     l2p_store<T, MIXED>(r, pf, ax, ay, az, a, ia, prob >= 0, lam, lam2, near32, near64, perm, phi, F);
+  }
+}
+
+// Mixed precision, a warp per leaf, the lanes on the leaf's particles (the
+// arithmetic of l2p_eval): the leaf's local expansion is staged in shared
+// memory as P^2 rows of the mz coefficients padded to a multiple of four,
+// and the Chebyshev table likewise, so that each row arrives by 16-byte
+// shared loads (two per row at P = 7, against seven 4-byte loads).
+template <int P>
+__device__ __forceinline__ void interp_weights_pad(const float* __restrict__ sCp, float xi, float* S, float* dS) {
+  constexpr int PX = (P + 3) / 4 * 4;
+  float Tn[PX], dTn[PX];
+  Tn[0] = 1.f;
+  if (P > 1) Tn[1] = xi;
+#pragma unroll
+  for (int n = 2; n < PX; ++n) Tn[n] = n < P ? 2.f * xi * Tn[n - 1] - Tn[n - 2] : 0.f;
+  float U0 = 1.f, U1 = 2.f * xi;
+  dTn[0] = 0.f;
+  if (P > 1) dTn[1] = 1.f;
+#pragma unroll
+  for (int n = 2; n < PX; ++n) {
+    dTn[n] = n < P ? (float)n * U1 : 0.f;
+    const float U2 = 2.f * xi * U1 - U0;
+    U0 = U1;
+    U1 = U2;
+  }
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    float row[PX];
+#pragma unroll
+    for (int n = 0; n < PX; n += 4) *(float4*)&row[n] = *(const float4*)&sCp[m * PX + n];
+    float s = 0.f, ds = 0.f;
+#pragma unroll
+    for (int n = 1; n < P; ++n) {
+      s += row[n] * Tn[n];
+      ds += row[n] * dTn[n];
+    }
+    S[m] = 1.f / (float)P + 2.f / (float)P * s;
+    dS[m] = 2.f / (float)P * ds;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 8)
+k_l2p_mixed(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, const float* __restrict__ cheb,
+            int cpad, const float* __restrict__ L, int has_far, const float4* __restrict__ pos32,
+            const float4* __restrict__ near32, const int32_t* __restrict__ perm, double* __restrict__ phi,
+            double* __restrict__ F, const double* __restrict__ fscale, double ks) {
+  constexpr int C = P * P * P, PP = P * P, PX = (P + 3) / 4 * 4;
+  __shared__ __align__(16) float sCp[P * PX];
+  __shared__ __align__(16) float sL[4][PP * PX];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < P * PX; i += 128) sCp[i] = (i % PX) < P ? cheb[(i / PX) * P + i % PX] : 0.f;
+  __syncthreads();
+  const int cell = blockIdx.x * 4 + warp;
+  if (cell >= nleaf) return;
+  float* myL = sL[warp];
+  float mean = 0.f;
+  if (has_far) {
+    const int64_t row = lv.row_off[leaf] + cell;
+    for (int e = lane; e < PP * PX; e += 32) {
+      const int r = e / PX, z = e - r * PX;
+      myL[e] = z < P ? L[row * cpad + r * P + z] : 0.f;
+    }
+    mean = L[row * cpad + C];
+  }
+  __syncwarp();
+  const int first = lv.first[leaf][cell], cnt = lv.count[leaf][cell];
+  const float ia = __double2float_rn(box[6]);
+  const int prob = fscale ? lv.slot[leaf][cell] : -1;
+  const double lam = prob >= 0 ? kernel_scale(fscale[prob], ks) : 1.0;
+  const double lam2 = prob >= 0 ? lam * fscale[prob] : 1.0;
+  for (int r = first + lane; r < first + cnt; r += 32) {
+    float pf = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    if (has_far) {
+      const float4 pp = pos32[r];
+      float Sx[P], Sy[P], Sz[P], dSx[P], dSy[P], dSz[P];
+      interp_weights_pad<P>(sCp, 2.f * pp.x, Sx, dSx);
+      interp_weights_pad<P>(sCp, 2.f * pp.y, Sy, dSy);
+      interp_weights_pad<P>(sCp, 2.f * pp.z, Sz, dSz);
+      float f = 0.f;
+#pragma unroll 1
+      for (int mx = 0; mx < P; ++mx) {
+#pragma unroll
+        for (int my = 0; my < P; ++my) {
+          float Lr[PX];
+#pragma unroll
+          for (int n = 0; n < PX; n += 4) *(float4*)&Lr[n] = *(const float4*)&myL[(mx * P + my) * PX + n];
+          float sz = 0.f, dz = 0.f;
+#pragma unroll
+          for (int mz = 0; mz < P; ++mz) {
+            sz += Lr[mz] * Sz[mz];
+            dz += Lr[mz] * dSz[mz];
+          }
+          const float sxy = Sx[mx] * Sy[my];
+          f += sxy * sz;
+          ax += dSx[mx] * Sy[my] * sz;
+          ay += Sx[mx] * dSy[my] * sz;
+          az += sxy * dz;
+        }
+      }
+      pf = f + mean;
+    }
+    l2p_store<float, true>(r, pf, ax, ay, az, 1.0, ia, prob >= 0, lam, lam2, near32, nullptr, perm, phi, F);
   }
 }
 
@@ -968,9 +1081,9 @@ fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
           c->lv, Lf, c->n, c->pleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32,
           c->near64, c->perm, phi, F, fs, c->kernel_s);
     else
-      k_l2p_out<P, float, true><<<ceil_div(nleaf, 4), 128, 4 * c->cpad * sizeof(float), s>>>(
-          c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32, has_far, c->pos64, c->pos32, c->near32, c->near64,
-          c->perm, phi, F, fs, c->kernel_s);
+      k_l2p_mixed<P><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->box, c->cheb32, c->cpad, c->L32,
+                                                        has_far, c->pos32, c->near32, c->perm, phi, F, fs,
+                                                        c->kernel_s);
   } else {
     if (pp)
       k_l2p_pp<P, double, false><<<ceil_div(c->n, 128), 128, 0, s>>>(

@@ -214,50 +214,59 @@ __global__ void k_gather_cls(int l, LevelPtrs lv, McBase mb, int cpad, int64_t r
 
 // k_gather_cls with FP16 operands: the same rows, 32 coefficients per row
 // (chunk kc = k / 32), two per 32-bit word, scaled by pow2_scale of the
-// cell's own max |M| (recorded per row for the projection's epilogue).  One
-// block of 128 threads per cell, a thread per pair of coefficients.
+// cell's own max |M| (recorded per row for the projection's epilogue).  A
+// warp per cell (four per block), a lane per pair of coefficients k, k + 1
+// (k = 2 lane + 64 i), each read once into registers.
 // ybound (FP16 form, may be NULL): the largest ||M_S||_2 of every (problem,
 // level), by atomic max.  A projection y = V^T M_S has |y_i| <= ||M_S||_2
 // (V has orthonormal columns), so a power of two taken from this bound keeps
 // every projection of the (problem, level) inside the FP16 range before the
 // projection runs.
+constexpr int GC_PAIRS = 8;  // pairs per lane: cpad <= 512
+
 __global__ void __launch_bounds__(128)
-k_gather_cls16(int l, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
+k_gather_cls16(int l, int ncell, LevelPtrs lv, McBase mb, int cpad, int64_t rows, const float* __restrict__ Mhi,
                const float* __restrict__ Mlo, uint32_t* __restrict__ Mc, float* __restrict__ mscale,
                uint32_t* __restrict__ ybound) {
-  __shared__ uint32_t s_max[4];
-  __shared__ float s_sq[4];
-  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (j >= ncell) return;
   const int cell = lv.cls[l][j];
   const int c = lv.key[l][cell] & 7;
   const int64_t row = mb.base[l][c] + (j - mb.clsoff[l][c]), src = (lv.row_off[l] + cell) * cpad;
+  float2 v[GC_PAIRS];
   float m = 0.f, sq = 0.f;
-  for (int k = threadIdx.x; k < cpad; k += blockDim.x) {
-    const float v = Mhi[src + k] + Mlo[src + k];
-    m = fmaxf(m, fabsf(v));
-    sq = fmaf(v, v, sq);
+#pragma unroll
+  for (int i = 0; i < GC_PAIRS; ++i) {
+    const int k = 2 * lane + 64 * i;
+    v[i] = make_float2(0.f, 0.f);
+    if (k < cpad) {
+      const float2 h = *(const float2*)&Mhi[src + k], o = *(const float2*)&Mlo[src + k];
+      v[i] = make_float2(h.x + o.x, h.y + o.y);
+      m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+      sq = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, sq));
+    }
   }
   const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // non-negative floats order like bits
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0) {
-    s_max[threadIdx.x >> 5] = wm;
-    s_sq[threadIdx.x >> 5] = sq;
-  }
-  __syncthreads();
-  const float sc = pow2_scale(__uint_as_float(max(max(s_max[0], s_max[1]), max(s_max[2], s_max[3]))));
-  if (threadIdx.x == 0) mscale[row] = sc;
-  if (threadIdx.x == 0 && ybound) {
+  const float sc = pow2_scale(__uint_as_float(wm));
+  if (lane == 0) mscale[row] = sc;
+  if (lane == 0 && ybound) {
     // the norm rounded up a little (FP32 sums of 343 squares): a bound, not an estimate
-    const float nrm = sqrtf(s_sq[0] + s_sq[1] + s_sq[2] + s_sq[3]) * 1.001f;
+    const float nrm = sqrtf(sq) * 1.001f;
     atomicMax(ybound + ymax_index(problem_of(lv, l, cell), l), __float_as_uint(nrm));
   }
-  for (int k = 2 * threadIdx.x; k < cpad; k += 2 * blockDim.x) {
-    const int64_t G = (int64_t)(k >> 5) * rows + row;
-    uint32_t hi, lo;
-    split_h2((Mhi[src + k] + Mlo[src + k]) * sc, (Mhi[src + k + 1] + Mlo[src + k + 1]) * sc, hi, lo);
-    const int w = (k & 31) >> 1;
-    Mc[il_idx(G, 0, w)] = hi;
-    Mc[il_idx(G, 1, w)] = lo;
+#pragma unroll
+  for (int i = 0; i < GC_PAIRS; ++i) {
+    const int k = 2 * lane + 64 * i;
+    if (k < cpad) {
+      const int64_t G = (int64_t)(k >> 5) * rows + row;
+      uint32_t hi, lo;
+      split_h2(v[i].x * sc, v[i].y * sc, hi, lo);
+      const int w = (k & 31) >> 1;
+      Mc[il_idx(G, 0, w)] = hi;
+      Mc[il_idx(G, 1, w)] = lo;
+    }
   }
 }
 
@@ -1400,13 +1409,15 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
       mb.clsoff[l][k] = c->cls_off[l][k];
     }
   if (f16) {
+    if (cp > 64 * GC_PAIRS) return set_err(c, FMM_ERR_STATE, "internal: %d coefficients per row exceed the gather's", cp);
     // the bound ||M||_2 per (problem, level), recorded afresh by the gather
     const int nslots = (c->forest ? c->nprob : 1) + 1;
     FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * nslots * FMM_MAX_LEVELS, s));
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
-        k_gather_cls16<<<c->lv.ncell[l], 128, 0, s>>>(l, c->lv, mb, cp, mrows, c->Mhi, c->Mlo,
-                                                       (uint32_t*)c->svd_Mcls, c->svd_mscale, c->svd_umax);
+        k_gather_cls16<<<ceil_div(c->lv.ncell[l], 4), 128, 0, s>>>(l, c->lv.ncell[l], c->lv, mb, cp, mrows, c->Mhi,
+                                                                   c->Mlo, (uint32_t*)c->svd_Mcls, c->svd_mscale,
+                                                                   c->svd_umax);
   } else {
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)

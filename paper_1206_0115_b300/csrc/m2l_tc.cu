@@ -381,6 +381,8 @@ k_m2l_tc(const __grid_constant__ CUtensorMap tm_khi, const __grid_constant__ CUt
 // L_T[m] = (1/a) * sum over the tile's groups of the partial sums: at most
 // three FP32 slices, added in FP32.  Block (tile, slice): rows 16*slice ..
 // 16*slice+15 of the tile, four coefficients per thread.
+constexpr int RED_BATCH = 8;  // partial slices loaded at once by the reduction
+
 __global__ void __launch_bounds__(256)
 k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_nact, LevelPtrs lv, int ntiles,
                 int gt, int cpad, int ncol, const float* __restrict__ partial, float* __restrict__ L,
@@ -397,13 +399,23 @@ k_m2l_tc_reduce(const Tile* __restrict__ tiles, const int32_t* __restrict__ tile
   const int nq = (ncol + 3) / 4;  // float4 columns (cpad is a multiple of 32)
   for (int idx = threadIdx.x; idx < nrow * nq; idx += blockDim.x) {
     const int row = r0 + idx / nq, c4 = 4 * (idx % nq);
+    // the slices' loads issued together (up to RED_BATCH in flight), then
+    // added in slice order
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int g = 0; g < ng; ++g) {
-      const float4 v = *(const float4*)&partial[(((int64_t)g * ntiles + tile) * FMM_TILE + row) * cpad + c4];
-      s.x += v.x;
-      s.y += v.y;
-      s.z += v.z;
-      s.w += v.w;
+    for (int g0 = 0; g0 < ng; g0 += RED_BATCH) {
+      float4 v[RED_BATCH];
+#pragma unroll
+      for (int k = 0; k < RED_BATCH; ++k)
+        if (g0 + k < ng)
+          v[k] = *(const float4*)&partial[(((int64_t)(g0 + k) * ntiles + tile) * FMM_TILE + row) * cpad + c4];
+#pragma unroll
+      for (int k = 0; k < RED_BATCH; ++k)
+        if (g0 + k < ng) {
+          s.x += v[k].x;
+          s.y += v[k].y;
+          s.z += v[k].z;
+          s.w += v[k].w;
+        }
     }
     const int cell = lv.cls[tl.level][tl.first + row];
     *(float4*)&L[(rbase + cell) * cpad + c4] = make_float4(s.x * inv_a, s.y * inv_a, s.z * inv_a, s.w * inv_a);
