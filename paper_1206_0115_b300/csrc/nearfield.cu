@@ -403,13 +403,12 @@ __device__ __forceinline__ void p2p32x2_item(int item, const LevelPtrs& lv, int 
   Kahan kp, kx, ky, kz;
   // staged source s of the chunk starting at c0: position (hi with the
   // neighbour shift, lo) and charge
+  // the neighbour leaf holding staged source s: the last lo with nb_pre[lo] <= s;
+  // a thread's s only grows (its pairs within a chunk, then later chunks), so
+  // its cursor moves forward from the previous answer
+  int lo = 0;
   auto fetch = [&](int s, float4& ph, float4& pl) {
-    int lo = 0, hi = 26;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (nb_pre[mid] <= s) lo = mid;
-      else hi = mid - 1;
-    }
+    while (lo < 26 && nb_pre[lo + 1] <= s) ++lo;
     const int j = nb_first[lo] + (s - nb_pre[lo]);
     ph = pos32[j];
     ph.x += (float)nb_off[lo][0];
@@ -601,13 +600,12 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   const f2_t TX = f2pack(th.x, th.x), TY = f2pack(th.y, th.y), TZ = f2pack(th.z, th.z);
   const f2_t LX = f2pack(tl.x, tl.x), LY = f2pack(tl.y, tl.y), LZ = f2pack(tl.z, tl.z);
   Kahan kp, kx, ky, kz;
+  // the neighbour leaf holding staged source s: the last lo with nb_pre[lo] <= s;
+  // a thread's s only grows (its pairs within a chunk, then later chunks), so
+  // its cursor moves forward from the previous answer
+  int lo = 0;
   auto fetch = [&](int s, float4& ph, float4& pl) {
-    int lo = 0, hi = 26;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (nb_pre[mid] <= s) lo = mid;
-      else hi = mid - 1;
-    }
+    while (lo < 26 && nb_pre[lo + 1] <= s) ++lo;
     const int j = nb_first[lo] + (s - nb_pre[lo]);
     ph = pos32[j];
     ph.x += (float)nb_off[lo][0];
