@@ -191,9 +191,10 @@ def dist_env():
     return ws, rank, local
 
 
-def profiled_traffic(kernel_file: str, profile: str, marker: str):
+def profiled_traffic(kernel_file: str, profile: str, marker: str, start: str = ""):
     """DRAM bytes per launch recorded in a profiles/ summary, or None when the
-    kernel source has changed since that capture."""
+    kernel source (the text of kernel_file from `start`, or its beginning, up
+    to `marker`) has changed since that capture."""
     import hashlib
     import re
     try:
@@ -201,8 +202,11 @@ def profiled_traffic(kernel_file: str, profile: str, marker: str):
         text = open(os.path.join(ROOT, profile)).read()
     except OSError:
         return None
-    cut = src.find(marker)
-    h = hashlib.sha256((src[:cut] if cut >= 0 else src).encode()).hexdigest()
+    a = src.find(start) if start else 0
+    cut = src.find(marker, max(a, 0))
+    if a < 0 or cut < 0:
+        return None
+    h = hashlib.sha256(src[a:cut].encode()).hexdigest()
     m = re.search(r"kernel-source-sha256: ([0-9a-f]{64})", text)
     t = re.search(r"dram-traffic-bytes-per-launch[^|\n]*\|[ |]*(\d+)", text)
     if not m or not t or m.group(1) != h:
@@ -293,7 +297,8 @@ def m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main: bool):
         m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
                    f"(the projection carries as much)")
         traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
-                                    "int sp_ngroups(int Rp)") if main else None)
+                                    "// Unit u -> (group g, tile, column half h)",
+                                    "// ---- expansion, FP16 form") if main else None)
         # MMA flop issued (three products per multiply, the padded shapes)
         hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
         hw_e = 3 * 2.0 * 128 * cpad * int(work[15])

@@ -231,7 +231,10 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   auto near_branch = [&](cudaEvent_t start) -> fmm_status {
     FMM_CUDA(c, cudaStreamWaitEvent(c->side, start, 0));
     if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[5], ps, cudaEventRecordExternal));
-    FMM_TRY(launch_p2p(c, ps));
+    {
+      NvtxRange r("fmm:p2p");
+      FMM_TRY(launch_p2p(c, ps));
+    }
     if (c->timing == 1) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[6], ps, cudaEventRecordExternal));
     FMM_CUDA(c, cudaEventRecord(c->ev_join, c->side));
     return FMM_OK;
@@ -252,11 +255,17 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
   }
   if (early) FMM_TRY(near_branch(c->ev_start));
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
-  FMM_TRY(launch_upward(c, s));
+  {
+    NvtxRange r("fmm:upward");
+    FMM_TRY(launch_upward(c, s));
+  }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
   if (!early) FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
   c->p2p_after_proj = false;
-  FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
+  {
+    NvtxRange r("fmm:m2l");
+    FMM_TRY(launch_m2l(c, s, c->timing ? c->tev[2] : nullptr));
+  }
   // schedule 0: the P2P branch starts with the persistent expansion kernel,
   // so that its blocks fill the room beside the expansion's CTAs instead of
   // holding the SMs the persistent kernels need (see launch_m2l_svd_tc)
@@ -267,7 +276,10 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
     FMM_TRY(near_branch(c->p2p_after_proj ? c->ev_p2p : c->ev_fork));
   }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[3], s, cudaEventRecordExternal));
-  FMM_TRY(launch_l2l(c, s));
+  {
+    NvtxRange r("fmm:l2l");
+    FMM_TRY(launch_l2l(c, s));
+  }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[4], s, cudaEventRecordExternal));
   FMM_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
   return FMM_OK;
@@ -607,6 +619,7 @@ fmm_status fmm_get_svd_ranks(fmm_handle h, int32_t* ranks) {
 }
 
 fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const double* q) {
+  NvtxRange nvtx_range("fmm:set_particles");
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
   c->err[0] = 0;
@@ -632,6 +645,7 @@ fmm_status fmm_set_particles(fmm_handle h, int64_t n, const double* xyz, const d
 
 fmm_status fmm_set_batch(fmm_handle h, int32_t nprob, const int64_t* counts, const int32_t* heights,
                          const double* xyz, const double* q) {
+  NvtxRange nvtx_range("fmm:set_batch");
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
   c->err[0] = 0;
@@ -705,6 +719,7 @@ fmm_status fmm_get_batch_info(fmm_handle h, int32_t k, int64_t* info, double* bo
 }
 
 fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F) {
+  NvtxRange nvtx_range("fmm:evaluate");
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
   c->err[0] = 0;
@@ -930,6 +945,7 @@ fmm_status autotune_schedule(Ctx* c) {
 extern "C" {
 
 fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
+  NvtxRange nvtx_range("fmm:autotune");
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;
   c->err[0] = 0;

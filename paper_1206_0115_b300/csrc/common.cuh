@@ -33,6 +33,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fmm.h"
 
 #define FMM_MAX_LEVELS 11
@@ -448,5 +450,15 @@ __host__ __device__ inline void demorton3(uint32_t k, int& x, int& y, int& z) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// An NVTX range over a scope ("fmm:<stage>"): the API calls and the stages
+// of an evaluation show up by name in a profiler's timeline (NVTX v3 is
+// header-only; without a tool attached a range costs a branch).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace fmm

@@ -658,13 +658,22 @@ k_svd_scatter_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ 
   const int l = tl.level, zero = lv.ncell[l];
   const int64_t rbase = lv.row_off[l];
   const uint32_t z[4] = {0u, 0u, 0u, 0u};
-  const int k_end = min(FMM_NT_CLASS, (int)(blockIdx.y + 1) * EXS_CHUNK);
-  for (int k = blockIdx.y * EXS_CHUNK; k < k_end; ++k) {
+  const int k0 = blockIdx.y * EXS_CHUNK, k_end = min(FMM_NT_CLASS, k0 + EXS_CHUNK);
+  // the chunk's sources, then their classes, each as independent loads in flight together
+  int srcs[EXS_CHUNK], cls[EXS_CHUNK];
+#pragma unroll
+  for (int j = 0; j < EXS_CHUNK; ++j)
+    srcs[j] = k0 + j < k_end ? tile_src[((int64_t)tile * FMM_NT_CLASS + k0 + j) * FMM_TILE + r] : zero;
+#pragma unroll
+  for (int j = 0; j < EXS_CHUNK; ++j) cls[j] = srcs[j] != zero ? (int)(lv.key[l][srcs[j]] & 7) : 0;
+#pragma unroll
+  for (int j = 0; j < EXS_CHUNK; ++j) {
+    const int k = k0 + j;
+    if (k >= k_end) break;
     const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
-    const int src = tile_src[((int64_t)tile * FMM_NT_CLASS + k) * FMM_TILE + r];
+    const int src = srcs[j];
     if (src != zero) {
-      const int cs = lv.key[l][src] & 7;
-      dst[(int64_t)srcidx[cs * FMM_NT + slot] * drows + rbase + src] = tile * FMM_TILE + r;
+      dst[(int64_t)srcidx[cls[j] * FMM_NT + slot] * drows + rbase + src] = tile * FMM_TILE + r;
     } else {
       const int k8 = kap8[tl.cls * FMM_NT + slot], n8 = t_ry[slot] / 8;
       for (int j = 0; j < n8; ++j) {
