@@ -1156,27 +1156,52 @@ k_m2l_setup_split(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* _
   const bool valid = row < tl.count;
   const int zero_row = lv.ncell[l];
   int ix = 0, iy = 0, iz = 0, mine = 0;
+  uint32_t key = 0;
   if (valid) {
     const int cell = lv.cls[l][tl.first + row];
-    demorton3(lv.key[l][cell], ix, iy, iz);
+    key = lv.key[l][cell];
+    demorton3(key, ix, iy, iz);
     mine = problem_of(lv, l, cell);
   }
   const int top = (1 << l) - 1;
   const int sgn = side == 0 ? 1 : -1;  // targets look at S = T + t, sources at T = S - t
   const int16_t* list = side == 0 ? cls_t : src_t;
+  // the chunk's offsets (with the side's sign) and each one's |component|
+  // spread to its axis's bits of a Morton key, so that the neighbour's key
+  // is the cell's key plus the offset in dilated arithmetic (per axis:
+  // ((key | ~mask) + d) & mask upwards, ((key & mask) - d) & mask downwards)
+  __shared__ int8_t s_t[SETUP_SPLIT_K][3];
+  __shared__ uint32_t s_d[SETUP_SPLIT_K][3];
   __shared__ uint32_t mask[SETUP_WORDS];
   if (row < SETUP_WORDS) mask[row] = 0u;
+  if (row < SETUP_SPLIT_K) {
+    const int slot = list[tl.cls * FMM_NT_CLASS + kb + row];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int t = sgn * tvec[3 * slot + a];
+      s_t[row][a] = (int8_t)t;
+      s_d[row][a] = spread3((uint32_t)(t < 0 ? -t : t)) << (2 - a);
+    }
+  }
   __syncthreads();
   int32_t* out = tile_src + (int64_t)blockIdx.x * FMM_NT_CLASS * FMM_TILE + row;
+  constexpr uint32_t MASK[3] = {0x24924924u, 0x12492492u, 0x09249249u};  // x, y, z bits of a key
   for (int k0 = kb; k0 < kb + SETUP_SPLIT_K; k0 += SETUP_BATCH) {
     int g[SETUP_BATCH];
 #pragma unroll
     for (int j = 0; j < SETUP_BATCH; ++j) {
-      const int slot = list[tl.cls * FMM_NT_CLASS + k0 + j];
-      const int sx = ix + sgn * tvec[3 * slot], sy = iy + sgn * tvec[3 * slot + 1], sz = iz + sgn * tvec[3 * slot + 2];
-      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top)
-                 ? lv.grid[l][morton3(sx, sy, sz)]
-                 : -1;
+      const int k = k0 + j - kb;
+      const int tx = s_t[k][0], ty = s_t[k][1], tz = s_t[k][2];
+      const int sx = ix + tx, sy = iy + ty, sz = iz + tz;
+      uint32_t skey = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int t = a == 0 ? tx : (a == 1 ? ty : tz);
+        const uint32_t d = s_d[k][a];
+        skey |= t < 0 ? ((key & MASK[a]) - d) & MASK[a] : ((key | ~MASK[a]) + d) & MASK[a];
+      }
+      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) ? lv.grid[l][skey]
+                                                                                               : -1;
     }
 #pragma unroll
     for (int j = 0; j < SETUP_BATCH; ++j) {
