@@ -528,16 +528,25 @@ k_p2p32x2p(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
 // leaf's sources are staged once per unit instead of once per item.
 constexpr int CW = 8;  // warps per block = items per unit
 
+// Double-buffered: chunk c + 1 is staged (into the other buffer, in dynamic
+// shared memory: 2 x CH / 2 pairs x 56 bytes) while chunk c is summed, with
+// one block barrier per chunk.
+template <int CH>
+constexpr int coop_smem_bytes() {
+  return 2 * (CH / 2) * (3 * (int)sizeof(ulonglong2) + (int)sizeof(f2_t));
+}
+
 template <int CH, int U>
 __global__ void __launch_bounds__(CW * 32)
 k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int32_t* __restrict__ leaf_of,
            const int32_t* __restrict__ units, int nunits, const float4* __restrict__ pos32,
            const float4* __restrict__ pos32lo, const double* __restrict__ box, float4* __restrict__ out) {
   constexpr int NP = CH / 2;
-  __shared__ ulonglong2 sA[NP];
-  __shared__ ulonglong2 sB[NP];
-  __shared__ ulonglong2 sC[NP];
-  __shared__ f2_t sD[NP];
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  ulonglong2* const bA = (ulonglong2*)coop_smem;  // [2][NP] each
+  ulonglong2* const bB = bA + 2 * NP;
+  ulonglong2* const bC = bB + 2 * NP;
+  f2_t* const bD = (f2_t*)(bC + 2 * NP);
   __shared__ int nb_first[27];
   __shared__ int nb_pre[28];
   __shared__ int8_t nb_off[27][3];
@@ -613,10 +622,12 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
     ph.z += (float)nb_off[lo][2];
     pl = pos32lo[j];
   };
-  for (int c0 = 0; c0 < total; c0 += CH) {
+  // stage the chunk starting at c0 into buffer b
+  auto stage = [&](int c0, int b) {
     const int cn = min(CH, total - c0);
     const int np = (cn + 1) >> 1;
-    __syncthreads();  // the previous chunk is no longer read
+    ulonglong2 *sA = bA + b * NP, *sB = bB + b * NP, *sC = bC + b * NP;
+    f2_t* sD = bD + b * NP;
     for (int m = tid; m < np; m += CW * 32) {
       float4 h0, l0, h1, l1;
       fetch(c0 + 2 * m, h0, l0);
@@ -631,24 +642,35 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
       sC[m] = make_ulonglong2(f2pack(l0.x, l1.x), f2pack(l0.y, l1.y));
       sD[m] = f2pack(l0.z, l1.z);
     }
-    __syncthreads();
-    if (!active) continue;
-    PairAcc acc{0ull, 0ull, 0ull, 0ull};
-    const int kown = min(cn, max(0, own - c0));
-    const int jown = (kown + 1) >> 1;
-    switch (g) {
-      case 1: p2p_pair_chunk<1, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 2: p2p_pair_chunk<2, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 4: p2p_pair_chunk<4, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 8: p2p_pair_chunk<8, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      case 16: p2p_pair_chunk<16, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
-      default: p2p_pair_chunk<32, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+  };
+  if (total > 0) stage(0, 0);
+  __syncthreads();
+  for (int c0 = 0, b = 0; c0 < total; c0 += CH, b ^= 1) {
+    const int cn = min(CH, total - c0);
+    const int np = (cn + 1) >> 1;
+    // the other buffer's last readers passed the barrier that ended the previous chunk
+    if (c0 + CH < total) stage(c0 + CH, b ^ 1);
+    const ulonglong2 *sA = bA + b * NP, *sB = bB + b * NP, *sC = bC + b * NP;
+    const f2_t* sD = bD + b * NP;
+    if (active) {
+      PairAcc acc{0ull, 0ull, 0ull, 0ull};
+      const int kown = min(cn, max(0, own - c0));
+      const int jown = (kown + 1) >> 1;
+      switch (g) {
+        case 1: p2p_pair_chunk<1, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+        case 2: p2p_pair_chunk<2, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+        case 4: p2p_pair_chunk<4, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+        case 8: p2p_pair_chunk<8, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+        case 16: p2p_pair_chunk<16, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+        default: p2p_pair_chunk<32, U>(sA, sB, sC, sD, sub, jown, np, TX, TY, TZ, LX, LY, LZ, acc); break;
+      }
+      const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
+      kp.add(ph.x + ph.y);
+      kx.add(px.x + px.y);
+      ky.add(py.x + py.y);
+      kz.add(pz.x + pz.y);
     }
-    const float2 ph = f2unpack(acc.phi), px = f2unpack(acc.fx), py = f2unpack(acc.fy), pz = f2unpack(acc.fz);
-    kp.add(ph.x + ph.y);
-    kx.add(px.x + px.y);
-    ky.add(py.x + py.y);
-    kz.add(pz.x + pz.y);
+    __syncthreads();  // the next chunk is staged; this one is no longer read
   }
   if (!active) return;
   float aphi = kp.s, ax = kx.s, ay = ky.s, az = kz.s;
@@ -981,12 +1003,14 @@ fmm_status launch_p2p_shape(Ctx* c, cudaStream_t s, int v, const int32_t* ilist,
     case 11: P2P_LAUNCH(8, 256); break;
     case 12:
       if (c->p2p_nunits > 0)
-        k_p2p32x2c<512, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+        k_p2p32x2c<512, 4><<<c->p2p_nunits, CW * 32, coop_smem_bytes<512>(), s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
                                                             c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
       break;
     case 13:
+      // double-buffered chunks of 1024 sources need more than the default 48 KB of shared memory
+      FMM_TRY(raise_smem_limit(c, (const void*)k_p2p32x2c<1024, 4>, coop_smem_bytes<1024>()));
       if (c->p2p_nunits > 0)
-        k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, 0, s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
+        k_p2p32x2c<1024, 4><<<c->p2p_nunits, CW * 32, coop_smem_bytes<1024>(), s>>>(c->lv, Lf, c->p2p_items, c->p2p_leaf, c->p2p_units,
                                                              c->p2p_nunits, c->pos32, c->pos32lo, c->box, c->near32);
       break;
     case 14:
