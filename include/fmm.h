@@ -297,6 +297,24 @@ fmm_status fmm_set_p2p_variant(fmm_handle h, int variant);
  * out: 4 int64, host.  Errors: FMM_ERR_STATE (no particles loaded). */
 fmm_status fmm_get_p2p_bins(fmm_handle h, int64_t* out, float* times_ms);
 
+/* 1 if this library is the debug build (compiled with FMM_DEBUG: bounds
+ * checks at the index computations of the tree build, the near field's
+ * staging and the compressed M2L's setup and projection, each recording its
+ * first failure and skipping the access it guards), 0 otherwise.  The paper
+ * has no counterpart; this is race- and bounds-checking without a
+ * sanitizer. */
+int fmm_debug_build(void);
+
+/* The first bounds check that failed since the previous call, as (site << 32
+ * | index), 0 if none (always 0 in the normal build); the record is cleared.
+ * Sites: 1 a particle's sorted index (tree gather), 2 a cell index (tree
+ * levels), 3 a staged near-field source outside its neighbour leaf, 4 a
+ * neighbour key outside a level's grid (M2L tile setup), 5 a
+ * destination-map index, 6 a projection's destination row (compressed M2L).
+ * Synchronises the device.  first_failure: host.  Errors: FMM_ERR_ARG
+ * (NULL), FMM_ERR_CUDA. */
+fmm_status fmm_debug_check(uint64_t* first_failure);
+
 /* Where the near-field branch (P2P, Sec. 2.1) starts in the evaluation
  * graph, its blocks at the low launch priority: 0 (the default) with the
  * compressed M2L's expansion kernel, after the projection; 1 at the start

@@ -1068,6 +1068,26 @@ fmm_status fmm_autotune(fmm_handle h, int32_t* choice, float* times_ms) {
   return FMM_OK;
 }
 
+int fmm_debug_build(void) {
+#ifdef FMM_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+fmm_status fmm_debug_check(uint64_t* first_failure) {
+  if (!first_failure) return set_err(nullptr, FMM_ERR_ARG, "fmm_debug_check: first_failure is NULL");
+  unsigned long long v = 0;
+  for (unsigned long long (*take)() : {fmm_debug_take_tree, fmm_debug_take_nearfield, fmm_debug_take_m2l_svd_tc}) {
+    const unsigned long long x = take();
+    if (x == ~0ull) return set_err(nullptr, FMM_ERR_CUDA, "fmm_debug_check: the check words could not be read");
+    if (!v) v = x;
+  }
+  *first_failure = v;
+  return FMM_OK;
+}
+
 fmm_status fmm_set_schedule(fmm_handle h, int sched) {
   if (!h) return FMM_ERR_ARG;
   Ctx* c = h;

@@ -451,6 +451,47 @@ __host__ __device__ inline void demorton3(uint32_t k, int& x, int& y, int& z) {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Bounds checks of the debug build (FMM_DEBUG; fmm_debug_check).  FMM_GUARD(
+// cond, site, idx) is `cond`: in the debug build a false condition also
+// records (site << 32 | idx) in this file's first-failure word, and callers
+// skip the access it guards; in the normal build it is `true` and costs
+// nothing.  The words are per compilation unit (no relocatable device code),
+// each read and cleared by its file's fmm_debug_take_<file>().
+#ifdef FMM_DEBUG
+static __device__ unsigned long long g_fmm_first_failure;
+__device__ __forceinline__ bool fmm_guard(bool cond, unsigned site, unsigned idx) {
+  if (!cond) atomicCAS(&g_fmm_first_failure, 0ull, ((unsigned long long)site << 32) | idx);
+  return cond;
+}
+#define FMM_GUARD(cond, site, idx) fmm_guard((cond), (site), (unsigned)(idx))
+#define FMM_DEBUG_TAKE_FN(name)                                                                      \
+  unsigned long long name() {                                                                       \
+    unsigned long long v = 0, z = 0;                                                                \
+    if (cudaMemcpyFromSymbol(&v, g_fmm_first_failure, sizeof(v)) != cudaSuccess ||                \
+        cudaMemcpyToSymbol(g_fmm_first_failure, &z, sizeof(z)) != cudaSuccess) {                   \
+      cudaGetLastError();                                                                           \
+      return ~0ull;                                                                                 \
+    }                                                                                               \
+    return v;                                                                                       \
+  }
+#else
+#define FMM_GUARD(cond, site, idx) true
+#define FMM_DEBUG_TAKE_FN(name) \
+  unsigned long long name() { return 0ull; }
+#endif
+// check sites (the high word of a recorded failure)
+enum : unsigned {
+  CHK_GATHER_INDEX = 1,      // k_gather: the sorted index of a particle outside [0, n)
+  CHK_LEVEL_CELL = 2,        // k_lv_write: a cell index below 0
+  CHK_P2P_SOURCE = 3,        // near field: a staged source outside its neighbour leaf's range
+  CHK_SETUP_KEY = 4,         // M2L tile setup: a neighbour key outside the level's grid
+  CHK_SCATTER_DST = 5,       // compressed M2L setup: a destination-map index outside the map
+  CHK_PROJ_DST = 6,          // compressed M2L projection: a destination row outside the expansion operand
+};
+unsigned long long fmm_debug_take_tree();
+unsigned long long fmm_debug_take_nearfield();
+unsigned long long fmm_debug_take_m2l_svd_tc();
+
 // An NVTX range over a scope ("fmm:<stage>"): the API calls and the stages
 // of an evaluation show up by name in a profiler's timeline (NVTX v3 is
 // header-only; without a tool attached a range costs a branch).

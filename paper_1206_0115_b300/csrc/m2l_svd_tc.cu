@@ -508,7 +508,8 @@ k_svd_proj_tc(ProjArgs a, LevelPtrs lv) {
           // Two groups of 8 that fill the same 32-byte sector of a Yx row (an
           // even and the next odd group of 8 in the row; the 64-byte swizzle
           // keeps such a pair together) leave in one 32-byte store.
-          const int d = epi_dst[q * 32 + lane];
+          int d = epi_dst[q * 32 + lane];
+          if (d >= 0 && !FMM_GUARD(d < a.ntiles * FMM_TILE, CHK_PROJ_DST, d)) d = -1;
           const int k8 = g.kap8[q];
           for (int c = c0 & ~15; c < c1; c += 16) {
             float v[16];
@@ -673,7 +674,8 @@ k_svd_scatter_setup(const Tile* __restrict__ tiles, const int32_t* __restrict__ 
     const int slot = cls_t[tl.cls * FMM_NT_CLASS + k];
     const int src = srcs[j];
     if (src != zero) {
-      dst[(int64_t)srcidx[cls[j] * FMM_NT + slot] * drows + rbase + src] = tile * FMM_TILE + r;
+      const int64_t di = (int64_t)srcidx[cls[j] * FMM_NT + slot] * drows + rbase + src;
+      if (FMM_GUARD(di >= 0 && di < (int64_t)FMM_NT_CLASS * drows, CHK_SCATTER_DST, k)) dst[di] = tile * FMM_TILE + r;
     } else {
       const int k8 = kap8[tl.cls * FMM_NT + slot], n8 = t_ry[slot] / 8;
       for (int j = 0; j < n8; ++j) {
@@ -1546,5 +1548,7 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (mid) FMM_CUDA(c, cudaEventRecordWithFlags(mid, s, cudaEventRecordExternal));
   return launch_m2l_tc_reduce(c, s, c->tc_partial, EX_GT);
 }
+
+FMM_DEBUG_TAKE_FN(fmm_debug_take_m2l_svd_tc)
 
 }  // namespace fmm

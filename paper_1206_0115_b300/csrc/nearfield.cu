@@ -409,6 +409,11 @@ __device__ __forceinline__ void p2p32x2_item(int item, const LevelPtrs& lv, int 
   int lo = 0;
   auto fetch = [&](int s, float4& ph, float4& pl) {
     while (lo < 26 && nb_pre[lo + 1] <= s) ++lo;
+    if (!FMM_GUARD(s >= nb_pre[lo] && s < nb_pre[lo + 1], CHK_P2P_SOURCE, s)) {
+      ph = make_float4(64.f, 64.f, 64.f, 0.f);  // skipped: no charge, far from every target
+      pl = make_float4(0.f, 0.f, 0.f, 0.f);
+      return;
+    }
     const int j = nb_first[lo] + (s - nb_pre[lo]);
     ph = pos32[j];
     ph.x += (float)nb_off[lo][0];
@@ -615,6 +620,11 @@ k_p2p32x2c(LevelPtrs lv, int leaf, const int32_t* __restrict__ items, const int3
   int lo = 0;
   auto fetch = [&](int s, float4& ph, float4& pl) {
     while (lo < 26 && nb_pre[lo + 1] <= s) ++lo;
+    if (!FMM_GUARD(s >= nb_pre[lo] && s < nb_pre[lo + 1], CHK_P2P_SOURCE, s)) {
+      ph = make_float4(64.f, 64.f, 64.f, 0.f);  // skipped: no charge, far from every target
+      pl = make_float4(0.f, 0.f, 0.f, 0.f);
+      return;
+    }
     const int j = nb_first[lo] + (s - nb_pre[lo]);
     ph = pos32[j];
     ph.x += (float)nb_off[lo][0];
@@ -1108,5 +1118,7 @@ fmm_status launch_p2p_stokes(Ctx* c, cudaStream_t s, const float4* f32, float4* 
                                                                     out);
   return cuda_err(c, cudaGetLastError(), "Stokes P2P launch");
 }
+
+FMM_DEBUG_TAKE_FN(fmm_debug_take_nearfield)
 
 }  // namespace fmm

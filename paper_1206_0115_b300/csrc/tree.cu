@@ -525,6 +525,7 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ skey, const uin
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   uint32_t i = sidx[r];
+  if (!FMM_GUARD((int64_t)i < n, CHK_GATHER_INDEX, r)) return;
   perm[r] = (int32_t)i;
   double x = xyz[3 * (int64_t)i], y = xyz[3 * (int64_t)i + 1], z = xyz[3 * (int64_t)i + 2];
   double qq = q[i];
@@ -703,6 +704,7 @@ __global__ void k_fgather(int64_t n, int nprob, const int64_t* __restrict__ psta
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint32_t i = sidx[r];
+  if (!FMM_GUARD((int64_t)i < n, CHK_GATHER_INDEX, r)) return;
   perm[r] = (int32_t)i;
   const int k = last_le(pstart, nprob, (int64_t)i);
   const BatchProb pb = prob[k];
@@ -866,6 +868,7 @@ k_lv_write(int64_t n, const uint32_t* __restrict__ key, int Lf, const int32_t* _
     for (int l = lo[j]; l <= Lf; ++l) ++run[l];  // run[l] - 1: the level-l cell holding i
     for (int l = Lf; l >= lo[j]; --l) {
       const int cell = run[l] - 1;
+      if (!FMM_GUARD(cell >= 0, CHK_LEVEL_CELL, i)) continue;
       out.key[l][cell] = k >> (3 * (Lf - l));
       out.first[l][cell] = l == Lf ? (int32_t)i : run[l + 1] - 1;
       if (l >= 1) out.parent[l][cell] = run[l - 1] - 1;
@@ -1200,8 +1203,8 @@ k_m2l_setup_split(const Tile* __restrict__ tiles, LevelPtrs lv, const int16_t* _
         const uint32_t d = s_d[k][a];
         skey |= t < 0 ? ((key & MASK[a]) - d) & MASK[a] : ((key | ~MASK[a]) + d) & MASK[a];
       }
-      g[j] = (valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top) ? lv.grid[l][skey]
-                                                                                               : -1;
+      const bool inside = valid && sx >= 0 && sy >= 0 && sz >= 0 && sx <= top && sy <= top && sz <= top;
+      g[j] = (inside && FMM_GUARD(skey < (1u << (3 * l)), CHK_SETUP_KEY, skey)) ? lv.grid[l][skey] : -1;
     }
 #pragma unroll
     for (int j = 0; j < SETUP_BATCH; ++j) {
@@ -2067,5 +2070,7 @@ fmm_status tree_build(Ctx* c, int64_t n, const double* xyz, const double* q) {
   c->loaded = true;
   return FMM_OK;
 }
+
+FMM_DEBUG_TAKE_FN(fmm_debug_take_tree)
 
 }  // namespace fmm

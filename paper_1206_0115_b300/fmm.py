@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfmm_b300.so")
+# FMM_LIBRARY=debug selects the debug build (bounds checks, fmm_debug_check)
+LIB_PATH = os.path.join(HERE, "libfmm_b300_debug.so" if os.environ.get("FMM_LIBRARY") == "debug"
+                        else "libfmm_b300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm.h")
 
 FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_STATE, FMM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
@@ -66,6 +68,8 @@ _SIGS = {
     "fmm_set_wait_limit": [_vp, C.c_double],
     "fmm_get_p2p_bins": [_vp, _vp, _vp],
     "fmm_set_schedule": [_vp, C.c_int],
+    "fmm_debug_build": [],
+    "fmm_debug_check": [_vp],
     "fmm_get_schedule": [_vp, _vp, _vp],
 }
 _SIGS.update({
@@ -286,6 +290,17 @@ def fmm_get_schedule(h):
     times = np.zeros(FMM_SCHED_CANDIDATES, dtype=np.float32)
     _check(h, lib.fmm_get_schedule(h, _ptr(sched), _ptr(times)))
     return int(sched[0]), times
+
+
+def fmm_debug_build() -> bool:
+    return bool(lib.fmm_debug_build())
+
+
+def fmm_debug_check() -> int:
+    """The first failed bounds check since the last call (site << 32 | index), 0 if none."""
+    out = np.zeros(1, dtype=np.uint64)
+    _check(None, lib.fmm_debug_check(_ptr(out)))
+    return int(out[0])
 
 
 def fmm_set_wait_limit(h, seconds: float) -> int:

@@ -115,3 +115,18 @@ def test_batch_plan_slots_are_aligned_disjoint_cells(F):
         F.fmm_batch_plan([1, 1], [10, 10])                             # 2 x 8^9 keys
     with pytest.raises(F.FMMError):
         F.fmm_batch_plan([1], [0])
+
+
+def test_debug_build_exports_the_same_entry_points(F):
+    """The bounds-checking build (FMM_DEBUG) is the same library with checks
+    compiled in: it exports every entry point the header declares, says so
+    through fmm_debug_build, and the normal build says it is not one."""
+    lib = build.build(debug=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in F.exported_symbols_of_header() if n not in exported]
+    assert not missing, missing
+    dbg = ctypes.CDLL(lib)
+    assert dbg.fmm_debug_build() == 1
+    assert F.lib.fmm_debug_build() == 0
+    assert F.lib.fmm_debug_check(None) == F.FMM_ERR_ARG
