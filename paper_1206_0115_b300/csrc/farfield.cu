@@ -836,9 +836,12 @@ k_l2p_mixed(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, c
       interp_weights_pad<P>(sCp, 2.f * pp.x, Sx, dSx);
       interp_weights_pad<P>(sCp, 2.f * pp.y, Sy, dSy);
       interp_weights_pad<P>(sCp, 2.f * pp.z, Sz, dSz);
+      // per mx: the z contraction of its P rows, then the y contraction
+      // (Ty = sum Sy sz, dTy = sum dSy sz, Tz = sum Sy dz), then x
       float f = 0.f;
 #pragma unroll 1
       for (int mx = 0; mx < P; ++mx) {
+        float Ty = 0.f, dTy = 0.f, Tz = 0.f;
 #pragma unroll
         for (int my = 0; my < P; ++my) {
           float Lr[PX];
@@ -850,12 +853,14 @@ k_l2p_mixed(LevelPtrs lv, int leaf, int nleaf, const double* __restrict__ box, c
             sz += Lr[mz] * Sz[mz];
             dz += Lr[mz] * dSz[mz];
           }
-          const float sxy = Sx[mx] * Sy[my];
-          f += sxy * sz;
-          ax += dSx[mx] * Sy[my] * sz;
-          ay += Sx[mx] * dSy[my] * sz;
-          az += sxy * dz;
+          Ty += Sy[my] * sz;
+          dTy += dSy[my] * sz;
+          Tz += Sy[my] * dz;
         }
+        f += Sx[mx] * Ty;
+        ax += dSx[mx] * Ty;
+        ay += Sx[mx] * dTy;
+        az += Sx[mx] * Tz;
       }
       pf = f + mean;
     }

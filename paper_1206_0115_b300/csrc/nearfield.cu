@@ -54,6 +54,18 @@ __device__ __forceinline__ float rsqrt_nf(float x) {
   return y;
 }
 
+// rsqrt_nf of both halves of a packed pair, the results formed as a pair in
+// one piece of PTX (so that they can land in the register pair the packed
+// products read).
+__device__ __forceinline__ unsigned long long rsqrt_nf2(unsigned long long x) {
+  unsigned long long y;
+  asm("{\n\t.reg .f32 a, b, c, d;\n\tmov.b64 {a, b}, %1;\n\trsqrt.approx.ftz.f32 c, a;\n\t"
+      "rsqrt.approx.ftz.f32 d, b;\n\tmov.b64 %0, {c, d};\n\t}"
+      : "=l"(y)
+      : "l"(x));
+  return y;
+}
+
 struct Kahan {
   float s = 0.f, c = 0.f;
   __device__ void add(float v) {
@@ -303,12 +315,15 @@ __device__ __forceinline__ void p2p_pairs(const ulonglong2* __restrict__ sA, con
       qi = f2mul(b.y, f2pack(p0, p1));
       qi3 = f2mul(f2mul(qi, gk.sk), f2pack(e0, e1));
     } else {
-      float i0 = rsqrt_nf(rr.x), i1 = rsqrt_nf(rr.y);
+      f2_t inv;
       if (SELF) {
+        float i0 = rsqrt_nf(rr.x), i1 = rsqrt_nf(rr.y);
         i0 = rr.x > 0.f ? i0 : 0.f;
         i1 = rr.y > 0.f ? i1 : 0.f;
+        inv = f2pack(i0, i1);
+      } else {
+        inv = rsqrt_nf2(r2);
       }
-      const f2_t inv = f2pack(i0, i1);
       qi = f2mul(b.y, inv);
       qi3 = f2mul(f2mul(qi, inv), inv);
     }
