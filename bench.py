@@ -373,9 +373,13 @@ def autotune(fmm, h):
                              "variant_ms": [round(float(t), 4) for t in bin_ms[b]]}
     sched, sched_ms = fmm.fmm_get_schedule(h)
     names = ("with_expansion", "at_start", "with_projection", "with_projection_2xstages")
-    rep["schedule"] = {"p2p_starts": names[sched],
-                       "evaluate_ms": {k: round(float(t), 4) for k, t in zip(
-                           list(names) + [n + "_nonpersistent" for n in names], sched_ms)}}
+    names = list(names) + [n + "_nonpersistent" for n in names]
+    # fmm_autotune keeps the fastest candidate (the first on a tie); candidates
+    # 4..7 are 0..3 with the near field's non-persistent shapes
+    timed = [(float(t), k) for k, t in enumerate(sched_ms) if t >= 0]
+    pick = min(timed)[1] if timed else int(sched)
+    rep["schedule"] = {"p2p_starts": names[pick], "candidate": pick,
+                       "evaluate_ms": {k: round(float(t), 4) for k, t in zip(names, sched_ms)}}
     return rep
 
 

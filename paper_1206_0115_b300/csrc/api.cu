@@ -254,10 +254,19 @@ fmm_status enqueue_eval(Ctx* c, cudaStream_t s) {
     FMM_TRY(launch_m2l_prep(c, c->side3));
   }
   if (early) FMM_TRY(near_branch(c->ev_start));
+  // the leaf level's FP16 class-order multipoles (compressed M2L) need P2M
+  // alone: a fourth branch runs that gather beside the M2M levels
+  // (launch_m2l joins it before the coarser levels' gathers)
+  c->leaf_gather_done = false;
+  const bool gather_apart = c->timing != 2 && svd_leaf_gather_apart(c);
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[0], s, cudaEventRecordExternal));
   {
     NvtxRange r("fmm:upward");
-    FMM_TRY(launch_upward(c, s));
+    FMM_TRY(launch_upward(c, s, gather_apart ? c->ev_p2m : nullptr));
+  }
+  if (gather_apart) {
+    FMM_CUDA(c, cudaStreamWaitEvent(c->side4, c->ev_p2m, 0));
+    FMM_TRY(launch_svd_leaf_gather(c, c->side4));
   }
   if (c->timing) FMM_CUDA(c, cudaEventRecordWithFlags(c->tev[1], s, cudaEventRecordExternal));
   if (!early) FMM_CUDA(c, cudaEventRecord(c->ev_fork, s));
@@ -438,6 +447,9 @@ fmm_status fmm_create(int height, int order, fmm_handle* out) {
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side4, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_p2m, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_gleaf, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -534,6 +546,12 @@ fmm_status fmm_destroy(fmm_handle h) {
     cudaStreamSynchronize(c->side3);
     cudaStreamDestroy(c->side3);
   }
+  if (c->side4) {
+    cudaStreamSynchronize(c->side4);
+    cudaStreamDestroy(c->side4);
+  }
+  if (c->ev_p2m) cudaEventDestroy(c->ev_p2m);
+  if (c->ev_gleaf) cudaEventDestroy(c->ev_gleaf);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   if (c->ev_prep) cudaEventDestroy(c->ev_prep);
   if (c->ev_bin0) cudaEventDestroy(c->ev_bin0);

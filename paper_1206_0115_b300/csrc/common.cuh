@@ -121,6 +121,9 @@ struct fmm_ctx {
   cudaStream_t side3 = nullptr;   // the compressed M2L's tree-only bookkeeping beside the upward pass
   cudaEvent_t ev_start = nullptr, ev_prep = nullptr;  // its fork (the evaluation's start) and join
   bool m2l_prep_done = false;     // that bookkeeping was launched on side3 (ev_prep marks its end)
+  cudaStream_t side4 = nullptr;   // the leaf level's FP16 class-order multipoles beside the M2M levels
+  cudaEvent_t ev_p2m = nullptr, ev_gleaf = nullptr;  // its fork (P2M done) and join
+  bool leaf_gather_done = false;  // that gather was launched on side4 (ev_gleaf marks its end)
   bool p2p_after_proj = false;   // ev_p2p was recorded by the M2L launch (the P2P branch starts there)
   char err[512] = {0};
   cudaError_t last_cuda = cudaSuccess;  // the CUDA error behind the last FMM_ERR_CUDA / FMM_ERR_OOM
@@ -377,7 +380,7 @@ fmm_status launch_p2p_bin(Ctx* c, cudaStream_t s, int bin, int v);
 bool is_p2p_kernel(const void* func);
 void p2p_carveout();
 extern const int kP2PVariants[FMM_P2P_VARIANTS][4];
-fmm_status launch_upward(Ctx* c, cudaStream_t s);      // P2M + M2M
+fmm_status launch_upward(Ctx* c, cudaStream_t s, cudaEvent_t after_p2m = nullptr);  // P2M + M2M
 fmm_status launch_m2l_simt(Ctx* c, cudaStream_t s, int first_tile, int ntiles);
 fmm_status svd_prepare(Ctx* c);        // SVD of the canonical operators (ranks to the host)
 fmm_status m2l_svd_prepare(Ctx* c);    // + factor banks and the Y layout of the current tree
@@ -393,6 +396,8 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 fmm_status launch_m2l(Ctx* c, cudaStream_t s, cudaEvent_t mid);
 fmm_status launch_m2l_prep(Ctx* c, cudaStream_t s);
 bool m2l_has_prep(const Ctx* c);
+bool svd_leaf_gather_apart(const Ctx* c);                  // the leaf-level gather may run beside M2M
+fmm_status launch_svd_leaf_gather(Ctx* c, cudaStream_t s);  // it, on s (records ev_gleaf)
 fmm_status svd_tree_setup(Ctx* c, cudaStream_t s);
 bool svd_has_tree_setup(const Ctx* c);
 fmm_status launch_l2l(Ctx* c, cudaStream_t s);

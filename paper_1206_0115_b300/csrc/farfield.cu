@@ -1027,7 +1027,7 @@ __global__ void k_rows_to_f64(int64_t nrows, int64_t row0, int C, int cpad, cons
 // ---------------------------------------------------------------- launchers
 
 template <int P>
-fmm_status upward_p(Ctx* c, cudaStream_t s) {
+fmm_status upward_p(Ctx* c, cudaStream_t s, cudaEvent_t after_p2m) {
   const int Lf = c->leaf;
   // leaves of a few particles (the same lane-utilisation rule as L2P): a warp per leaf
   const int nleaf = c->lv.ncell[Lf];
@@ -1035,6 +1035,7 @@ fmm_status upward_p(Ctx* c, cudaStream_t s) {
   if (c->precision == FMM_MIXED) {
     k_p2m_pairs<P><<<ceil_div(nleaf, 4), 128, 0, s>>>(c->lv, Lf, nleaf, c->cheb32, c->cpad, c->pos32, c->Mhi,
                                                       c->Mlo);
+    if (after_p2m) FMM_CUDA(c, cudaEventRecord(after_p2m, s));  // the leaf level's multipoles are final
     for (int l = Lf - 1; l >= 2; --l) {
       if constexpr (m2m_fused_fits<P>())
         k_m2m_fused<P><<<c->lv.ncell[l], 256, 0, s>>>(c->lv, l, c->m2m32, c->cpad, c->Mhi, c->Mlo);
@@ -1104,9 +1105,9 @@ fmm_status l2p_p(Ctx* c, cudaStream_t s, double* phi, double* F) {
 
 }  // namespace
 
-fmm_status launch_upward(Ctx* c, cudaStream_t s) {
+fmm_status launch_upward(Ctx* c, cudaStream_t s, cudaEvent_t after_p2m) {
   if (c->leaf < 2 || c->n == 0) return FMM_OK;
-#define CALL(P) upward_p<P>(c, s)
+#define CALL(P) upward_p<P>(c, s, after_p2m)
   switch (c->order) {
     case 2: return CALL(2);
     case 3: return CALL(3);

@@ -1406,6 +1406,52 @@ fmm_status svd_tree_setup(Ctx* c, cudaStream_t s) {
   return cuda_err(c, cudaGetLastError(), "compressed M2L setup");
 }
 
+// Where each class of each level starts in the class-ordered multipoles.
+static McBase mc_base(const Ctx* c) {
+  McBase mb;
+  for (int l = 0; l < FMM_MAX_LEVELS; ++l)
+    for (int k = 0; k < 8; ++k) {
+      mb.base[l][k] = l >= 2 && l <= c->leaf ? c->svd_mcbase[l][k] : 0;
+      mb.clsoff[l][k] = c->cls_off[l][k];
+    }
+  return mb;
+}
+
+// FP16 class-order copies of levels l0..l1 (k_gather_cls16), after zeroing
+// the bounds ||M||_2 per (problem, level) that the gathers record afresh
+// when zero_bounds (the first gather launch of an evaluation).
+static fmm_status svd_gather16(Ctx* c, cudaStream_t s, int l0, int l1, bool zero_bounds) {
+  const int cp = c->cpad;
+  if (cp > 64 * GC_PAIRS) return set_err(c, FMM_ERR_STATE, "internal: %d coefficients per row exceed the gather's", cp);
+  const McBase mb = mc_base(c);
+  if (zero_bounds) {
+    const int nslots = (c->forest ? c->nprob : 1) + 1;
+    FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * nslots * FMM_MAX_LEVELS, s));
+  }
+  for (int l = l0; l <= l1; ++l)
+    if (c->lv.ncell[l] > 0)
+      k_gather_cls16<<<ceil_div(c->lv.ncell[l], 4), 128, 0, s>>>(l, c->lv.ncell[l], c->lv, mb, cp, c->svd_mcls_rows,
+                                                                 c->Mhi, c->Mlo, (uint32_t*)c->svd_Mcls,
+                                                                 c->svd_mscale, c->svd_umax);
+  return cuda_err(c, cudaGetLastError(), "compressed M2L gather");
+}
+
+// The leaf level's gather reads the leaf multipoles alone, final once P2M
+// has run, so it may run on a branch of its own beside the M2M levels.
+bool svd_leaf_gather_apart(const Ctx* c) {
+  return c->ntiles > 0 && c->n > 0 && c->leaf >= 2 && c->precision == FMM_MIXED && m2l_kind(c) == 5 &&
+         m2l_uses_f16(c) && c->svd_bank_f16 && c->lv.ncell[c->leaf] > 0;
+}
+
+fmm_status launch_svd_leaf_gather(Ctx* c, cudaStream_t s) {
+  c->leaf_gather_done = false;
+  if (!svd_leaf_gather_apart(c)) return FMM_OK;
+  FMM_TRY(svd_gather16(c, s, c->leaf, c->leaf, true));
+  FMM_CUDA(c, cudaEventRecord(c->ev_gleaf, s));
+  c->leaf_gather_done = true;
+  return FMM_OK;
+}
+
 fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (c->ntiles == 0) return FMM_OK;
   const int cp = c->cpad, Rp = c->svd_rp;
@@ -1413,22 +1459,16 @@ fmm_status launch_m2l_svd_tc(Ctx* c, cudaStream_t s, cudaEvent_t mid) {
   if (f16 != c->svd_bank_f16) return set_err(c, FMM_ERR_STATE, "internal: compressed M2L banks in the other format");
   // multipoles in class order, every level with far field
   const int64_t mrows = c->svd_mcls_rows;
-  McBase mb;
-  for (int l = 0; l < FMM_MAX_LEVELS; ++l)
-    for (int k = 0; k < 8; ++k) {
-      mb.base[l][k] = l >= 2 && l <= c->leaf ? c->svd_mcbase[l][k] : 0;
-      mb.clsoff[l][k] = c->cls_off[l][k];
-    }
+  const McBase mb = mc_base(c);
   if (f16) {
-    if (cp > 64 * GC_PAIRS) return set_err(c, FMM_ERR_STATE, "internal: %d coefficients per row exceed the gather's", cp);
-    // the bound ||M||_2 per (problem, level), recorded afresh by the gather
-    const int nslots = (c->forest ? c->nprob : 1) + 1;
-    FMM_CUDA(c, cudaMemsetAsync(c->svd_umax, 0, sizeof(uint32_t) * nslots * FMM_MAX_LEVELS, s));
-    for (int l = 2; l <= c->leaf; ++l)
-      if (c->lv.ncell[l] > 0)
-        k_gather_cls16<<<ceil_div(c->lv.ncell[l], 4), 128, 0, s>>>(l, c->lv.ncell[l], c->lv, mb, cp, mrows, c->Mhi,
-                                                                   c->Mlo, (uint32_t*)c->svd_Mcls, c->svd_mscale,
-                                                                   c->svd_umax);
+    if (c->leaf_gather_done) {
+      // the leaf level ran beside the M2M levels, after zeroing the bounds
+      c->leaf_gather_done = false;
+      FMM_CUDA(c, cudaStreamWaitEvent(s, c->ev_gleaf, 0));
+      FMM_TRY(svd_gather16(c, s, 2, c->leaf - 1, false));
+    } else {
+      FMM_TRY(svd_gather16(c, s, 2, c->leaf, true));
+    }
   } else {
     for (int l = 2; l <= c->leaf; ++l)
       if (c->lv.ncell[l] > 0)
