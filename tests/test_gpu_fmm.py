@@ -435,8 +435,10 @@ def test_schedules_agree_bit_for_bit(F, variant):
     projection, whose pipelines then run fewer stages) changes the order in
     which independent kernels run and the depth of the M2L pipelines, not
     the arithmetic: every schedule gives the same bits, with a block-per-item
-    shape (0) and the persistent shape (14); the autotuner then picks one
-    from timed evaluations and its result agrees too."""
+    shape (0) and the persistent shape (14), and so do the stage-timing
+    modes (every stage alone on one stream; the timed normal schedule); the
+    autotuner then picks one from timed evaluations and its result agrees
+    too."""
     import torch
     xyz, q = inputs.particles(60000, 41, "cube", "sym")
     n = len(q)
@@ -454,6 +456,15 @@ def test_schedules_agree_bit_for_bit(F, variant):
             res.setdefault(sched, []).append((phi.cpu().numpy().copy(), Fo.cpu().numpy().copy()))
             st = f.stats()
             assert int(st[2]) == 1 and int(st[6]) == 0, list(st)
+        # timing mode 2 runs every stage alone on one stream (no side
+        # branches: neither the M2L bookkeeping nor the leaf-level gather
+        # beside the upward pass); mode 1 times the normal schedule
+        F.fmm_set_schedule(f.h, 0)
+        for mode in (2, 1, 0):
+            F.fmm_set_timing(f.h, mode)
+            f.evaluate(phi, Fo)
+            torch.cuda.synchronize()
+            res[0].append((phi.cpu().numpy().copy(), Fo.cpu().numpy().copy()))
         with pytest.raises(F.FMMError):
             F.fmm_set_schedule(f.h, 4)
         F.fmm_autotune(f.h)
