@@ -296,9 +296,10 @@ def m2l_rooflines(fmm, np, stats, work, kt, stage, p, pk, main: bool):
         achieved = half_flop / (m2l_ms / 1e3) / 1e12
         m2l_alg = (f"2 x {C} x sum of pair ranks {int(work[13])} = {half_flop:.4g} flop per launch "
                    f"(the projection carries as much)")
+        # the profile's counters are those of the FP16-operand kernel (k_svd_expand16_tc)
         traffic = (profiled_traffic("paper_1206_0115_b300/csrc/m2l_svd_tc.cu", "profiles/m2l_svd_cube_n1m_h6_p7.md",
                                     "// Unit u -> (group g, tile, column half h)",
-                                    "// ---- expansion, FP16 form") if main else None)
+                                    "// ---- expansion, FP16 form") if main and math == "f16x3" else None)
         # MMA flop issued (three products per multiply, the padded shapes)
         hw_p = 3 * 2.0 * 128 * cpad * int(work[14])
         hw_e = 3 * 2.0 * 128 * cpad * int(work[15])
