@@ -330,8 +330,10 @@ fmm_status fmm_debug_check(uint64_t* first_failure);
 fmm_status fmm_set_schedule(fmm_handle h, int sched);
 
 /* The current schedule (*sched, host int32) and, in times_ms (may be NULL;
- * FMM_SCHED_CANDIDATES floats, host), the mean evaluation time of each
- * candidate of the last fmm_autotune: [k] schedule k with the chosen
+ * FMM_SCHED_CANDIDATES floats, host), the evaluation time of each candidate
+ * of the last fmm_autotune (the larger of two passes' means of three runs,
+ * each pass with the candidate's graph built afresh; the smallest is kept,
+ * the first on a tie): [k] schedule k with the chosen
  * near-field shapes, [4 + k] schedule k with the fastest non-persistent
  * shapes (k = 0..3); -1 where not timed. */
 fmm_status fmm_get_schedule(fmm_handle h, int32_t* sched, float* times_ms);

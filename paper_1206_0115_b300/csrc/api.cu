@@ -10,6 +10,7 @@
 // followed by one plain launch of L2P, which adds the near field and scatters
 // phi and F to the caller's order (its arguments are the caller's output
 // pointers, which change from call to call).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -922,30 +923,38 @@ fmm_status autotune_schedule(Ctx* c) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == FMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     st = cuda_err(c, cudaGetLastError(), "fmm_autotune: events");
+  // Two passes over the candidates, each building every candidate's graph
+  // afresh; a candidate counts with the slower of its two times, so that a
+  // lead seen in one pass only (the order in which the block scheduler
+  // places the near field's blocks beside the M2L CTAs can differ between
+  // runs of the same graph) does not decide.
+  for (int pass = 0; pass < 2 && st == FMM_OK; ++pass)
+    for (int k = 0; k < FMM_SCHED_CANDIDATES && st == FMM_OK; ++k) {
+      const bool use_alt = k >= 4;
+      if (use_alt && !have_alt) continue;
+      if ((k & 3) >= 2 && !(m2l_kind(c) == 5 && svd_wants_f16(c))) continue;  // the compressed FP16 M2L's stages
+      c->p2p_sched = k & 3;
+      c->p2p_variant = use_alt ? alt_var : chosen_var;
+      c->p2p_big_variant = use_alt ? alt_big : chosen_big;
+      c->graph_ok = false;
+      st = fmm_evaluate(c, phi, F);  // builds this candidate's graph
+      if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess)
+        st = cuda_err(c, cudaGetLastError(), "event");
+      for (int r = 0; r < 3 && st == FMM_OK; ++r) st = fmm_evaluate(c, phi, F);
+      float ms = 0.f;
+      if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
+      if (st != FMM_OK) break;
+      c->sched_ms[k] = pass == 0 ? ms / 3.f : std::max(c->sched_ms[k], ms / 3.f);
+    }
   int best = -1;
   float best_ms = -1.f;
-  for (int k = 0; k < FMM_SCHED_CANDIDATES && st == FMM_OK; ++k) {
-    const bool use_alt = k >= 4;
-    if (use_alt && !have_alt) continue;
-    if ((k & 3) >= 2 && !(m2l_kind(c) == 5 && svd_wants_f16(c))) continue;  // the compressed FP16 M2L's stages
-    c->p2p_sched = k & 3;
-    c->p2p_variant = use_alt ? alt_var : chosen_var;
-    c->p2p_big_variant = use_alt ? alt_big : chosen_big;
-    c->graph_ok = false;
-    st = fmm_evaluate(c, phi, F);  // builds this candidate's graph
-    if (st == FMM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_err(c, cudaGetLastError(), "event");
-    for (int r = 0; r < 3 && st == FMM_OK; ++r) st = fmm_evaluate(c, phi, F);
-    float ms = 0.f;
-    if (st == FMM_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-      st = cuda_err(c, cudaGetLastError(), "fmm_autotune: timing");
-    if (st != FMM_OK) break;
-    c->sched_ms[k] = ms / 3.f;
-    if (best < 0 || c->sched_ms[k] < best_ms) {
+  for (int k = 0; k < FMM_SCHED_CANDIDATES && st == FMM_OK; ++k)
+    if (c->sched_ms[k] >= 0.f && (best < 0 || c->sched_ms[k] < best_ms)) {
       best = k;
       best_ms = c->sched_ms[k];
     }
-  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   c->timing = keep_timing;
