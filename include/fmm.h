@@ -251,8 +251,9 @@ fmm_status fmm_evaluate(fmm_handle h, double* phi, double* F);
  * bins, timed as one launch -- is faster; fmm_get_p2p_bins reports the
  * result.
  * Last, in mixed precision with a far field (height >= 3), the evaluation
- * schedule: whole evaluations (each graph built once, then three timed
- * runs) in each schedule of fmm_set_schedule (2 and 3 only with the
+ * schedule: whole evaluations (two passes over the candidates, each
+ * building the candidate's graph afresh and timing three runs; the slower
+ * pass counts) in each schedule of fmm_set_schedule (2 and 3 only with the
  * compressed tensor-core M2L on FP16 operands), each with the chosen shapes
  * and -- when those include a persistent shape (14, 15), whose blocks hold
  * their SMs until the last work item is taken -- with the fastest
